@@ -1,0 +1,331 @@
+"""Pins for the CPU oracle: checks against things fixed by the paper and by
+mathematics (hand-derived aggregations, closed forms, dense direct solves,
+invariants), not against the oracle itself."""
+
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from conftest import const_diag_grid, graph_from_spec, to_dense, coo_to_csr
+from oracle import oracle as O
+from paper_1209_0960_gb300 import problems as P
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _params(dim, **kw):
+    p = O.default_params(dim)
+    p.update(kw)
+    return p
+
+
+# ---------------------------------------------------------------------------
+# strength of connection (Sec. 2.1, Eq. symmetric_strong1/2)
+# ---------------------------------------------------------------------------
+
+def _jump_grid():
+    """3 x 3 weighted grid Laplacian + I; column x = 2 has K = 1e6, the rest
+    K = 1, face weights are harmonic means."""
+    K = np.array([1.0, 1.0, 1e6])
+    h = 2 * K[1] * K[2] / (K[1] + K[2])
+    rows, cols, vals = [], [], []
+    w = {}
+    for y in range(3):
+        for x in range(3):
+            i = x + 3 * y
+            if x < 2:
+                wx = 1.0 if x == 0 else h
+                w[(i, i + 1)] = w[(i + 1, i)] = wx
+            if y < 2:
+                wy = K[x]
+                w[(i, i + 3)] = w[(i + 3, i)] = wy
+    for i in range(9):
+        d = 1.0 + sum(v for (a, b), v in w.items() if a == i)
+        rows.append(i); cols.append(i); vals.append(d)
+    for (a, b), v in w.items():
+        rows.append(a); cols.append(b); vals.append(-v)
+    return coo_to_csr(9, rows, cols, vals), h
+
+
+def test_strength_jump_grid_hand_values():
+    (rp, ci, va), h = _jump_grid()
+    eta, iso, dirich, strong = O.strength(rp, ci, va, _params(2))
+    # hand-derived: A_00 = 3, A_01(cell (0,1)) = 4, A_10 = 3 + h
+    # eta((0,0)) = max(1/(3 (3+h)), 1/(3*4)) = 1/12
+    assert eta[0] == pytest.approx(1.0 / 12.0, rel=1e-15)
+    # eta((1,0)) = 1/(3 (3 + h)) (link to (0,0) dominates 1/((3+h)(4+h)))
+    assert eta[1] == pytest.approx(1.0 / (3.0 * (3.0 + h)), rel=1e-14)
+    # eta((1,1)) = 1/(4 (4 + h))
+    assert eta[4] == pytest.approx(1.0 / (4.0 * (4.0 + h)), rel=1e-14)
+    # column x = 2 is dominated by its 1e6 vertical links: eta close to 1/2
+    assert eta[2] == pytest.approx(1e12 / ((1e6 + h + 1) * (2e6 + h + 1)), rel=1e-14)
+    assert not iso.any() and not dirich.any()
+    # an edge is strong iff both ends lie in the same coefficient region
+    for i in range(9):
+        for k in range(rp[i], rp[i + 1]):
+            j = ci[k]
+            if j == i:
+                assert not strong[k]
+                continue
+            same = (i % 3 == 2) == (j % 3 == 2)
+            assert strong[k] == same, (i, j)
+
+
+def test_strength_is_invariant_under_power_of_two_symmetric_scaling():
+    p = P.lognormal3d((10, 9, 8), seed=3)
+    rng = np.random.default_rng(1)
+    e = rng.integers(-20, 20, size=p.n)
+    s = np.ldexp(1.0, e)
+    rows = np.repeat(np.arange(p.n), np.diff(p.row_ptr))
+    va2 = p.val * s[rows] * s[p.col]
+    prm = _params(3)
+    eta1, iso1, _, st1 = O.strength(p.row_ptr, p.col, p.val, prm)
+    eta2, iso2, _, st2 = O.strength(p.row_ptr, p.col, va2, prm)
+    assert np.array_equal(st1, st2) and np.array_equal(iso1, iso2)
+    assert np.array_equal(eta1, eta2)
+    a1, n1 = O.aggregate(p.row_ptr, p.col, p.val, prm)
+    a2, n2 = O.aggregate(p.row_ptr, p.col, va2, prm)
+    assert n1 == n2 and np.array_equal(a1, a2)
+
+
+# ---------------------------------------------------------------------------
+# aggregation (Algorithms 1-3): hand-derived maps and invariants
+# ---------------------------------------------------------------------------
+
+with open(os.path.join(GOLDEN, "aggregation_hand.json")) as f:
+    _HAND = json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _HAND, ids=[c["name"] for c in _HAND])
+def test_aggregation_hand_derived(case):
+    rp, ci, va = graph_from_spec(case["graph"])
+    prm = _params(2, **case["params"])
+    agg, nc = O.aggregate(rp, ci, va, prm)
+    assert nc == case["nc"]
+    assert agg.tolist() == case["agg"]
+
+
+def _bfs_diam(adj, verts):
+    verts = list(verts)
+    vs = set(verts)
+    best = 0
+    for s in verts:
+        dist = {s: 0}
+        q = [s]
+        while q:
+            u = q.pop(0)
+            for w in adj[u]:
+                if w in vs and w not in dist:
+                    dist[w] = dist[u] + 1
+                    q.append(w)
+        if len(dist) != len(vs):
+            return None
+        best = max(best, max(dist.values()))
+    return best
+
+
+def check_aggregation_invariants(rp, ci, va, agg, nc, prm, iso=None, dirich=None):
+    n = len(rp) - 1
+    adj = [[int(j) for j in ci[rp[i]:rp[i + 1]] if j != i] for i in range(n)]
+    if dirich is None:
+        _, iso, dirich, _ = O.strength(rp, ci, va, prm)
+    # every non-Dirichlet vertex in exactly one aggregate, ids consecutive
+    assert np.all((agg >= 0) == ~dirich)
+    assert set(agg[agg >= 0].tolist()) == set(range(nc))
+    members = [[] for _ in range(nc)]
+    for i in range(n):
+        if agg[i] >= 0:
+            members[agg[i]].append(i)
+    sizes = np.array([len(m) for m in members])
+    for m in members:
+        assert _bfs_diam(adj, m) is not None          # connected
+    iso_aggs = [k for k, m in enumerate(members) if all(iso[i] for i in m)]
+    for k in iso_aggs:
+        assert sizes[k] <= prm["s_min"]
+    return sizes
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: P.lognormal3d((14, 13, 12), seed=5),
+    lambda: P.layered3d((12, 12, 16), seed=2),
+    lambda: P.laplace2d_random_rhs(20),
+    lambda: P.anisotropic3d((10, 10, 10), seed=1),
+])
+def test_aggregation_invariants(maker):
+    p = maker()
+    prm = _params(p.dim)
+    agg, nc = O.aggregate(p.row_ptr, p.col, p.val, prm)
+    sizes = check_aggregation_invariants(p.row_ptr, p.col, p.val, agg, nc, prm)
+    # the greedy coarsening reaches a useful rate on these grids
+    assert p.n / nc > 2.5
+    assert sizes.max() <= prm["s_max"] + 6
+
+
+# ---------------------------------------------------------------------------
+# colouring
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("shape", [(7, 5), (6, 5, 4), (9,)])
+def test_colouring_is_red_black_on_structured_grids(shape):
+    rp, ci, va = const_diag_grid(shape, 2.0 * len(shape))
+    c, nc = O.colour(rp, ci)
+    n = len(rp) - 1
+    strides = [int(np.prod(shape[:a])) for a in range(len(shape))]
+    parity = np.array([sum((i // strides[a]) % shape[a] for a in range(len(shape))) % 2
+                       for i in range(n)])
+    assert nc == 2 and np.array_equal(c, parity)
+
+
+def test_colouring_is_proper_on_coarse_levels():
+    p = P.lognormal3d((12, 12, 12), seed=4)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=50))
+    assert H.num_levels >= 3
+    for l in range(H.num_levels - 1):
+        L = H.level(l)
+        rp, ci, col = L["row_ptr"], L["col"], L["colour"]
+        for i in range(L["n"]):
+            for j in ci[rp[i]:rp[i + 1]]:
+                if j != i:
+                    assert col[i] != col[j]
+        assert L["ncolours"] == col.max() + 1
+
+
+# ---------------------------------------------------------------------------
+# Galerkin product (Eq. prolongation and the coarse operator)
+# ---------------------------------------------------------------------------
+
+def test_galerkin_1d_pairs_is_tridiag():
+    rp, ci, va = const_diag_grid((10,), 2.0)
+    agg = np.arange(10) // 2
+    grp, gci, gva = O.galerkin(rp, ci, va, agg, 5)
+    G = to_dense(grp, gci, gva)
+    T = 2 * np.eye(5) - np.eye(5, k=1) - np.eye(5, k=-1)
+    assert np.array_equal(G, T)
+
+
+def test_galerkin_2d_2x2_blocks_doubles_the_stencil():
+    rp, ci, va = const_diag_grid((8, 8), 4.0)
+    x = np.arange(64) % 8
+    y = np.arange(64) // 8
+    agg = (x // 2) + 4 * (y // 2)
+    grp, gci, gva = O.galerkin(rp, ci, va, agg, 16)
+    G = to_dense(grp, gci, gva)
+    rpc, cic, vac = const_diag_grid((4, 4), 4.0)
+    assert np.array_equal(G, 2.0 * to_dense(rpc, cic, vac))
+
+
+def test_galerkin_pattern_row_sums_and_symmetry():
+    p = P.lognormal3d((12, 11, 10), seed=9)
+    prm = _params(3)
+    agg, nc = O.aggregate(p.row_ptr, p.col, p.val, prm)
+    grp, gci, gva = O.galerkin(p.row_ptr, p.col, p.val, agg, nc)
+    A = sp.csr_matrix((p.val, p.col, p.row_ptr), shape=(p.n, p.n))
+    Pm = sp.csr_matrix((np.ones(p.n), agg, np.arange(p.n + 1)), shape=(p.n, nc))
+    Gref = (Pm.T @ A @ Pm).tocsr()
+    Gref.sort_indices()
+    G = sp.csr_matrix((gva, gci, grp), shape=(nc, nc))
+    # pattern: every aggregate pair joined by a stored entry
+    pat = (Pm.T @ sp.csr_matrix((np.ones(p.nnz), p.col, p.row_ptr)) @ Pm).tocsr()
+    pat.sort_indices()
+    assert np.array_equal(pat.indptr, grp) and np.array_equal(pat.indices, gci)
+    assert np.all(np.diff(gci)[np.diff(np.repeat(np.arange(nc), np.diff(grp))) == 0] > 0)
+    # values agree with a sparse triple product to rounding
+    scale = np.abs(gva).max()
+    assert np.abs((G - Gref)).max() <= 1e-13 * scale
+    # row sums of P^T A P are the aggregated row sums of A
+    rs_fine = np.asarray(A.sum(axis=1)).ravel()
+    rs_agg = np.bincount(agg, weights=rs_fine, minlength=nc)
+    assert np.allclose(np.asarray(G.sum(axis=1)).ravel(), rs_agg, rtol=1e-12,
+                       atol=1e-12 * scale)
+    assert np.abs(G - G.T).max() <= 1e-13 * scale
+
+
+# ---------------------------------------------------------------------------
+# V-cycle and PCG (Sec. 2, Sec. 5 smoother choice)
+# ---------------------------------------------------------------------------
+
+def test_single_level_vcycle_is_the_direct_solve():
+    p = P.laplace2d_random_rhs(16)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(2, coarsen_target=10_000))
+    assert H.num_levels == 1 and H.status == 0
+    A = to_dense(p.row_ptr, p.col, p.val)
+    z = H.vcycle(p.b)
+    assert np.allclose(z, np.linalg.solve(A, p.b), rtol=1e-12, atol=0)
+    x, it, rel, trel = H.pcg(p.b, tol=1e-10)
+    assert it == 1 and trel < 1e-12
+
+
+def _vcycle_matrix(H, n):
+    return np.column_stack([H.vcycle(e) for e in np.eye(n)])
+
+
+@pytest.mark.parametrize("maker,dim", [
+    (lambda: P.laplace2d_random_rhs(12), 2),
+    (lambda: P.lognormal3d((7, 6, 5), seed=2), 3),
+])
+def test_vcycle_is_symmetric_positive_definite(maker, dim):
+    p = maker()
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(dim, coarsen_target=8))
+    assert H.num_levels >= 3
+    B = _vcycle_matrix(H, p.n)
+    assert np.abs(B - B.T).max() <= 1e-12 * np.abs(B).max()
+    assert np.linalg.eigvalsh(0.5 * (B + B.T)).min() > 0
+
+
+def test_vcycle_is_linear_and_two_level_iteration_contracts():
+    p = P.lognormal3d((9, 8, 7), seed=6)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=100))
+    assert H.num_levels == 2
+    A = to_dense(p.row_ptr, p.col, p.val)
+    rng = np.random.default_rng(0)
+    u, v = rng.standard_normal(p.n), rng.standard_normal(p.n)
+    assert np.allclose(H.vcycle(2 * u + v), 2 * H.vcycle(u) + H.vcycle(v), rtol=1e-11, atol=1e-14)
+    # spectral radius of I - B A below 1
+    B = _vcycle_matrix(H, p.n)
+    rho = np.abs(np.linalg.eigvals(np.eye(p.n) - B @ A)).max()
+    assert rho < 0.9
+
+
+@pytest.mark.parametrize("maker,dim", [
+    (lambda: P.laplace2d_random_rhs(32), 2),
+    (lambda: P.lognormal3d((12, 12, 12), seed=0), 3),
+    (lambda: P.layered3d((12, 12, 12), seed=1), 3),
+])
+def test_pcg_matches_dense_direct_solve(maker, dim):
+    p = maker()
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(dim, coarsen_target=100))
+    assert H.status == 0 and H.num_levels >= 2
+    A = to_dense(p.row_ptr, p.col, p.val)
+    xd = np.linalg.solve(A, p.b)
+    x, it, rel, trel = H.pcg(p.b, tol=1e-12, maxit=200)
+    assert 0 < it < 60
+    assert rel <= 1e-12
+    # forward error <= cond(A) * backward error; the log-normal and Laplace
+    # cases are well enough conditioned for 1e-9, the 1e6-contrast layers are not
+    cond = np.linalg.cond(A)
+    bound = 1e-9 if cond < 1e3 else 10 * cond * 1e-12
+    assert np.linalg.norm(x - xd) <= bound * np.linalg.norm(xd)
+
+
+def test_pcg_respects_initial_guess_and_maxit():
+    p = P.laplace2d_random_rhs(16)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(2, coarsen_target=20))
+    A = to_dense(p.row_ptr, p.col, p.val)
+    xd = np.linalg.solve(A, p.b)
+    x0 = xd + 1e-3 * np.random.default_rng(0).standard_normal(p.n)
+    x, it, rel, trel = H.pcg(p.b, tol=1e-10, x0=x0)
+    assert it > 0 and trel <= 1e-10 * 1.01
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    x, it, rel, trel = H.pcg(p.b, tol=1e-14, maxit=2)
+    assert it == -2
+
+
+def test_flexible_cg_matches_standard_cg_for_exact_preconditioner_arithmetic():
+    p = P.lognormal3d((10, 10, 10), seed=3)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3))
+    x1, it1, _, t1 = H.pcg(p.b, tol=1e-8)
+    x2, it2, _, t2 = H.pcg(p.b, tol=1e-8, flexible=True)
+    assert abs(it1 - it2) <= 1 and t1 <= 1e-8 * 1.01 and t2 <= 1e-8 * 1.01
