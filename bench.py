@@ -1,0 +1,407 @@
+#!/usr/bin/env python3
+"""Benchmark of the AMG-preconditioned CG solve on one GB300.
+
+Workload: 3D cell-centred finite volumes, 128^3 cells (2,097,152 unknowns),
+K = exp(Z) with Z a Gaussian field (variance 4, correlation length 0.05,
+1000 cosine modes, seed 0), u = 1 at x = 0, u = 0 at x = 1, no flux elsewhere.
+A step is one complete solve to a 1e-8 relative residual (every V-cycle and CG
+operation) with the hierarchy resident in HBM.
+
+Metric: time to a 1e-8 relative residual (ms, lower is better) of FP64
+AMG-PCG, with the FP32-in-FP64 solve and the V-cycle HBM bandwidth of both
+precisions reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank solves its own replica on its own GPU with no
+communication on the data path; timing is the maximum over ranks.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "time to 1e-8 relative residual, FP64 AMG-PCG (FP32-in-FP64 and V-cycle HBM GB/s beside it)"
+UNIT = "ms"
+WORKLOAD = "3D FV 7-point 128^3 log-normal K (variance 4, correlation length 0.05), FP64 AMG-PCG to 1e-8"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--grid", type=int, default=128, help="cells per axis of the workload")
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--cpu-grid", type=int, default=64,
+                    help="cells per axis of the bounded oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (replicas only)
+# ---------------------------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            import torch
+            backend = "nccl" if torch.cuda.is_available() else "gloo"
+            if backend == "nccl":
+                torch.cuda.set_device(self.local_rank)
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg is not None:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if self.pg is None:
+            return v
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg is not None:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = None
+        try:
+            import torch
+            uuid = str(torch.cuda.get_device_properties(device_index).uuid)
+            sel = uuid if uuid.startswith("GPU-") else "GPU-" + uuid
+        except Exception:
+            sel = str(device_index)
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", sel, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        try:
+            rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+            os.unlink(self.path)
+        except Exception:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        loaded = [v for v in sm if v > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_traffic(name: str):
+    """DRAM bytes per launch of `name` from the committed ncu summary, if the
+    kernel source has not changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(path))
+        rec = d[name]
+        src = open(os.path.join(ROOT, "paper_1209_0960_gb300", "csrc", rec["source"]), "rb").read()
+        if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_16"]:
+            return None
+        return float(rec["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def make_problem(grid: int):
+    from paper_1209_0960_gb300 import problems
+    return problems.lognormal3d((grid, grid, grid), variance=4.0, corr_len=0.05, seed=0)
+
+
+def oracle_sample(grid: int, tol: float, steps: int, warmup: int, min_seconds: float = 0.0):
+    """Time the oracle's PCG solve on a grid^3 instance of the workload.
+    Returns (seconds per solve, iterations, n)."""
+    from oracle import oracle as O
+    p = make_problem(grid)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, O.default_params(3))
+    for _ in range(warmup):
+        H.pcg(p.b, tol=tol, maxit=500)
+    times, it = [], 0
+    t_all = time.perf_counter()
+    while len(times) < steps or (time.perf_counter() - t_all) < min_seconds:
+        t0 = time.perf_counter()
+        _, it, _, _ = H.pcg(p.b, tol=tol, maxit=500)
+        times.append(time.perf_counter() - t0)
+    return statistics.mean(times), it, p.n, len(times)
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args, dist: Dist):
+    if dist.rank != 0:
+        return
+    sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, max(1, args.steps),
+                                         args.warmup)
+    n_full = args.grid ** 3
+    # scale to the full workload: cost per unknown per iteration is flat (every
+    # oracle step is O(nnz)); the iteration count is taken from the sample
+    value = sec * 1e3 * (n_full / n_s)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": reps, "warmup": args.warmup, "ms_per_step": value,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": args.grid, "tol": args.tol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"oracle PCG solve on the {args.cpu_grid}^3 instance of the "
+                                   f"workload ({n_s} unknowns, {it_s} iterations, "
+                                   f"{sec:.3f} s per solve), scaled by unknowns to {args.grid}^3"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+VCYCLE_KINDS = {"gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict",
+                "prolong", "coarse_solve", "zero", "convert"}
+
+
+def timed_solves(solver, b, x, steps, tol, stream, dist):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    dist.barrier()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    infos = []
+    for _ in range(steps):
+        x.zero_()
+        _, rc, info = solver.solve(b, x, tol=tol, maxit=500)
+        infos.append((rc, info))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    return ev0.elapsed_time(ev1) / steps, infos
+
+
+def run_ours(args, dist: Dist):
+    import numpy as np
+    import torch
+    from paper_1209_0960_gb300 import amg
+
+    dev = dist.local_rank if dist.world > 1 else 0
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    p = make_problem(args.grid)
+    t0 = time.perf_counter()
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream)
+    setup_wall = time.perf_counter() - t0
+    summary, levels = solver.info()
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+
+    # ---- FP64: warm-up, then K timed solves --------------------------------
+    for _ in range(args.warmup):
+        x.zero_()
+        solver.solve(b, x, tol=args.tol)
+    clocks = ClockSampler(dev)
+    ms64, infos64 = timed_solves(solver, b, x, args.steps, args.tol, stream, dist)
+    clk = clocks.stop()
+    ms64 = dist.max(ms64)
+    rc64, info64 = infos64[-1]
+    x64 = x.clone()
+
+    # one more solve with the profiler on (outside the timed region): per-kernel
+    # launches, CUDA-event durations and modelled bytes
+    solver.profile(True)
+    x.zero_()
+    solver.solve(b, x, tol=args.tol)
+    prof64 = solver.profile_read()
+    solver.profile(False)
+
+    # ---- FP32-in-FP64 ---------------------------------------------------------
+    solver.set_precision(amg.AMG_FP32_IN_FP64)
+    for _ in range(args.warmup):
+        x.zero_()
+        solver.solve(b, x, tol=args.tol)
+    ms32, infos32 = timed_solves(solver, b, x, args.steps, args.tol, stream, dist)
+    ms32 = dist.max(ms32)
+    rc32, info32 = infos32[-1]
+    err32 = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
+    solver.profile(True)
+    x.zero_()
+    solver.solve(b, x, tol=args.tol)
+    prof32 = solver.profile_read()
+    solver.profile(False)
+    solver.set_precision(amg.AMG_FP64)
+
+    # ---- end to end through the C ABI with pinned host buffers -----------------
+    e2e = None
+    if not args.no_e2e:
+        bh = torch.from_numpy(p.b).pin_memory()
+        xh = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+        bh_np, xh_np = bh.numpy(), xh.numpy()
+        solver.solve_host(bh_np, xh_np, tol=args.tol)
+        dist.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            xh_np[:] = 0.0
+            solver.solve_host(bh_np, xh_np, tol=args.tol)
+        e2e_ms = dist.max((time.perf_counter() - t0) * 1e3 / args.steps)
+        e2e = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 16 * p.n,
+               "d2h_bytes_per_step": 8 * p.n}
+
+    # ---- roofline of the dominant kernel ---------------------------------------
+    peak, peak_src = measured_peaks()
+    top = max(prof64, key=lambda d: d["total_ms"])
+    per_launch_ms = top["total_ms"] / top["launches"]
+    per_launch_bytes = top["bytes"] / top["launches"]
+    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                "traffic": kernel_traffic(top["name"])}
+
+    def vcycle_gbs(prof, iters):
+        vb = sum(d["bytes"] for d in prof if d["name"] in VCYCLE_KINDS)
+        vt = sum(d["total_ms"] for d in prof if d["name"] in VCYCLE_KINDS)
+        return {"gbs_kernels": vb / (vt * 1e-3) / 1e9 if vt > 0 else None,
+                "frac_of_measured": (vb / (vt * 1e-3) / 1e9) / peak if vt > 0 else None,
+                "frac_of_nominal_7900": (vb / (vt * 1e-3) / 1e9) / 7900.0 if vt > 0 else None,
+                "ms_per_vcycle_kernels": vt / max(1, iters + 1)}
+
+    launches = sum(d["launches"] for d in prof64 if d["name"] != "zero")
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----------------
+    cpu = None
+    if dist.world == 1 and not args.no_cpu_baseline:
+        sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, 1, 0, min_seconds=10.0)
+        cpu = {"value": sec * 1e3 * (p.n / n_s), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"oracle PCG solve on the {args.cpu_grid}^3 instance of the workload "
+                         f"({n_s} unknowns, {it_s} iterations, {sec:.3f} s per solve, "
+                         f"{reps} solves), scaled by unknowns to {args.grid}^3",
+               "host_cpu_count": os.cpu_count()}
+
+    line = {
+        "metric": METRIC, "value": ms64, "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": args.grid, "unknowns": p.n, "nnz": p.nnz,
+                   "tol": args.tol, "l2": "inputs larger than L2 (level-0 matrix "
+                   f"{(p.nnz * 12 + 4 * p.n) / 1e6:.0f} MB > 129 MB)",
+                   "parallelism": f"replicas x{dist.world}"},
+        "iterations": info64["iterations"],
+        "true_rel_residual": info64["true_rel_residual"],
+        "fp32_in_fp64": {"ms": ms32, "iterations": info32["iterations"],
+                         "true_rel_residual": info32["true_rel_residual"],
+                         "rel_diff_vs_fp64_solution": err32, "speedup_vs_fp64": ms64 / ms32},
+        "vcycle": {"fp64": vcycle_gbs(prof64, info64["iterations"]),
+                   "fp32": vcycle_gbs(prof32, info32["iterations"]),
+                   "model_bytes_fp64": summary["vcycle_bytes_fp64"],
+                   "model_bytes_fp32": summary["vcycle_bytes_fp32"]},
+        "setup": {"host_ms": summary["host_setup_ms"], "gpu_galerkin_ms": summary["gpu_galerkin_ms"],
+                  "gpu_other_ms": summary["gpu_other_ms"], "total_ms": summary["total_setup_ms"],
+                  "levels": summary["num_levels"], "coarsest_n": summary["coarsest_n"],
+                  "operator_complexity": summary["operator_complexity"],
+                  "level_n": [l["n"] for l in levels]},
+        "roofline": roofline,
+        "kernels_fp64": prof64,
+        "gpu_launches": launches * args.steps,
+        "e2e": e2e,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "status": {"fp64": rc64, "fp32_in_fp64": rc32},
+    }
+    solver.close()
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_ours(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

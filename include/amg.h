@@ -1,0 +1,232 @@
+/*
+ * amg.h -- C ABI of libamg: aggregation-based algebraic multigrid as a
+ * preconditioner for conjugate gradients on one NVIDIA GB300 (sm_103a).
+ *
+ * Method: Blatt, Ippisch & Bastian, "A Massively Parallel Algebraic
+ * Multigrid Preconditioner based on Aggregation for Elliptic Problems with
+ * Heterogeneous Coefficients" (arXiv:1209.0960).
+ *   - problem statement A x = b, A symmetric positive definite, from the
+ *     discretisation of div(K grad u) = f: Sec. 2, Eq. (model), Eq. (ls);
+ *   - strength of connection: Sec. 2.1, Eq. (symmetric_strong1/2);
+ *   - greedy aggregation: Sec. 2.1, Algorithms 1-3;
+ *   - piecewise-constant prolongation and Galerkin coarse operator with the
+ *     over-correction factor omega: Sec. 2.1, Eq. (prolongation) and the
+ *     coarse-matrix formula after it;
+ *   - V-cycle with one symmetric Gauss-Seidel step pre and post and a direct
+ *     coarsest solve: Sec. 2 and Sec. 5; stopping on a relative residual
+ *     reduction: Sec. 5.
+ *
+ * Conventions for every entry point:
+ *   - Return value: AMG_OK (0) on success, a negative AMG_E* code on error
+ *     (AMG_PENDING > 0 only from amg_poll).  amg_last_error() returns a
+ *     thread-local message for the last failure on the calling thread.
+ *     No C++ exception ever crosses this interface.
+ *   - Matrices are CSR with int32 row pointers and column indices and
+ *     float64 values, square, columns sorted and unique within each row,
+ *     diagonal stored and positive, symmetric pattern and values.
+ *   - Inputs are borrowed for the duration of the call; the library copies
+ *     what it keeps.  Outputs are allocated by the caller.
+ *   - "device" pointers are CUDA device (or managed) memory on the device
+ *     that was current when the context was created; "host" pointers are
+ *     ordinary or pinned host memory.
+ *   - All GPU work of a context is ordered on params.cuda_stream.  Calls
+ *     that return results to the host synchronise that stream; amg_vcycle
+ *     does not (its output is ready when the stream reaches that point).
+ *   - Vectors passed to the library use the caller's row numbering.
+ */
+#ifndef AMG_H
+#define AMG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMG_OK 0
+#define AMG_PENDING 1        /* amg_poll: request not finished yet */
+#define AMG_EINVAL (-1)      /* malformed input or parameters */
+#define AMG_ENOMEM (-2)      /* device or host allocation failed / refused */
+#define AMG_ENOTSPD (-3)     /* coarsest pivot <= 0 or p.Ap <= 0 in CG */
+#define AMG_ENOTCONV (-4)    /* maxit reached before the tolerance */
+#define AMG_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define AMG_ECUDA (-6)       /* a CUDA runtime call failed */
+#define AMG_ENOTFOUND (-7)   /* unknown ticket */
+
+#define AMG_FP64 0           /* every step in float64 */
+#define AMG_FP32_IN_FP64 1   /* float32 V-cycle inside float64 CG */
+
+typedef struct amg_ctx amg_ctx;
+
+typedef struct {
+    int32_t n;                /* rows = columns */
+    int32_t nnz;              /* stored entries, = row_ptr[n] */
+    const int32_t *row_ptr;   /* [n+1] */
+    const int32_t *col;       /* [nnz], sorted within each row */
+    const double *val;        /* [nnz] */
+    int32_t on_device;        /* 1: the three arrays are device pointers */
+} amg_csr;
+
+/* Setup and solve parameters.  amg_params_default fills the documented
+ * reading of the paper's unspecified constants. */
+typedef struct {
+    double delta;             /* strong-edge threshold, Eq. (symmetric_strong2); default 1/3 */
+    double beta;              /* isolated-vertex threshold, Sec. 2.1 (b); default 1e-5 */
+    double omega;             /* over-correction of the coarse correction, Sec. 2.1; default 1.6 */
+    int32_t s_min;            /* Algorithm 1 minimum aggregate size; default 2^dim */
+    int32_t s_max;            /* Algorithm 1 maximum aggregate size; default 3*2^(dim-1) */
+    int32_t d_max;            /* Algorithm 2 diameter limit; default dim */
+    int32_t coarsen_target;   /* stop coarsening at <= this many rows; default 1000 */
+    int32_t max_levels;       /* default 20 */
+    int32_t dense_cap;        /* largest coarsest level solved densely; default 4096 */
+    double min_coarsen_rate;  /* stop when n_l / n_{l+1} < this; default 1.2 */
+    int32_t precision;        /* AMG_FP64 or AMG_FP32_IN_FP64 */
+    int32_t flexible_cg;      /* -1: standard CG for FP64, flexible for FP32; 0 / 1 force */
+    void *cuda_stream;        /* cudaStream_t for all work; NULL = default stream */
+} amg_params;
+
+typedef struct {
+    int32_t status;           /* AMG_OK, AMG_ENOTCONV or AMG_ENOTSPD */
+    int32_t iterations;       /* CG iterations performed */
+    double rel_residual;      /* recursively updated ||r_k|| / ||r_0|| */
+    double true_rel_residual; /* ||b - A x|| / ||b - A x_0||, recomputed at the end */
+    double solve_ms;          /* device time of the whole solve (CUDA events) */
+} amg_solve_info;
+
+typedef struct {
+    int32_t n;                /* rows of this level */
+    int32_t nnz;              /* stored entries including the diagonal */
+    int32_t n_coarse;         /* rows of the next level (0 on the coarsest) */
+    int32_t ncolours;         /* colours of the smoother ordering (0 on the coarsest) */
+    int32_t max_agg_size;     /* largest aggregate built on this level */
+    int32_t n_isolated;       /* isolated vertices, Sec. 2.1 (b) */
+    int32_t n_dirichlet;      /* rows without a non-zero off-diagonal */
+    double vcycle_bytes_fp64; /* modelled DRAM bytes of this level per FP64 V-cycle */
+    double vcycle_bytes_fp32; /* same for the FP32 V-cycle */
+} amg_level_info;
+
+typedef struct {
+    int32_t num_levels;
+    int32_t coarsest_n;
+    double operator_complexity;   /* sum_l nnz_l / nnz_0 */
+    double host_setup_ms;         /* strength, aggregation, colouring (host, all levels) */
+    double gpu_galerkin_ms;       /* Galerkin products (device, all levels) */
+    double gpu_other_ms;          /* reordering, coarsest factorisation, FP32 copies */
+    double total_setup_ms;        /* wall time of amg_setup */
+    double vcycle_bytes_fp64;     /* sum of the per-level figures */
+    double vcycle_bytes_fp32;
+    double pcg_iter_bytes_fp64;   /* modelled DRAM bytes per CG iteration incl. V-cycle */
+    double pcg_iter_bytes_fp32;
+} amg_summary;
+
+/* Per-kernel-class record of the profiler (amg_profile_*). */
+typedef struct {
+    char name[32];            /* kernel class, e.g. "gs_level0" */
+    int32_t launches;         /* launches recorded since the profiler was enabled */
+    double total_ms;          /* sum of their CUDA-event durations */
+    double bytes;             /* sum of their modelled (algorithmic) DRAM bytes */
+} amg_kernel_stat;
+
+/* Fill *p with the defaults for a problem of spatial dimension dim (1-3).
+ * Returns AMG_EINVAL for p == NULL or dim outside 1..3. */
+int amg_params_default(amg_params *p, int32_t dim);
+
+/* Build the hierarchy (Sec. 2.1; Algorithm 1 per level, then the Galerkin
+ * product per level on the GPU, then the dense factorisation of the coarsest
+ * level).  Strength, aggregation and colouring run on the host; the level
+ * matrices, the reordering for the smoother and the coarsest inverse are
+ * computed on the GPU.  *out receives a context owning all device memory.
+ * Errors: AMG_EINVAL (bad CSR: unsorted/duplicate columns, missing or
+ * non-positive diagonal, asymmetric pattern; bad params; coarsest level
+ * larger than dense_cap), AMG_ENOTSPD (coarsest pivot <= 0), AMG_ENOMEM,
+ * AMG_ECUDA.  On error *out is set to NULL and nothing leaks. */
+int amg_setup(const amg_csr *A, const amg_params *p, amg_ctx **out);
+
+/* Select the arithmetic of later solves: AMG_FP64 or AMG_FP32_IN_FP64, and
+ * the CG variant (flexible_cg as in amg_params).  The first switch to
+ * AMG_FP32_IN_FP64 builds the scaled float32 level copies (S^-1 A S^-1,
+ * S = diag(sqrt(A_ii)), per level).  Errors: AMG_EINVAL, AMG_ENOMEM. */
+int amg_set_precision(amg_ctx *c, int32_t precision, int32_t flexible_cg);
+
+/* z = B r for one V(1,1)-cycle B of the hierarchy, zero initial guess
+ * (Sec. 2; one symmetric Gauss-Seidel step pre and post in the multicolour
+ * ordering, residual restriction by aggregate sums, coarse correction
+ * prolongated with factor omega, dense solve on the coarsest level).
+ * r_dev, z_dev: device float64 [n] in the caller's numbering; they may not
+ * alias.  Uses the context's current precision.  Asynchronous on the
+ * context stream.  Errors: AMG_EINVAL (NULL), AMG_ECUDA. */
+int amg_vcycle(amg_ctx *c, const double *r_dev, double *z_dev);
+
+/* Preconditioned CG with one V-cycle per iteration until
+ * ||b - A x_k|| <= tol ||b - A x_0|| (Sec. 5 stopping rule) or maxit
+ * iterations.  b_dev: device float64 [n]; x_dev: device float64 [n], the
+ * initial guess on entry and the solution on exit.  info may be NULL.
+ * Returns AMG_OK on convergence, AMG_ENOTCONV at maxit (x holds the last
+ * iterate), AMG_ENOTSPD when p.Ap <= 0, AMG_EINVAL, AMG_ECUDA.
+ * Synchronises the context stream. */
+int amg_pcg_solve(amg_ctx *c, const double *b_dev, double *x_dev, double tol,
+                  int32_t maxit, amg_solve_info *info);
+
+/* As amg_pcg_solve with host buffers: copies b and x_0 to the device,
+ * solves, copies x back (all on the context stream; pinned buffers make the
+ * copies asynchronous DMA).  info->solve_ms includes the copies. */
+int amg_pcg_solve_host(amg_ctx *c, const double *b_host, double *x_host, double tol,
+                       int32_t maxit, amg_solve_info *info);
+
+/* ||b - A x||_2 for the level-0 matrix of the context, reduced in a fixed
+ * order (deterministic).  b_dev, x_dev: device float64 [n] in the caller's
+ * numbering.  *out_norm is written on the host (synchronises the stream).
+ * Uses device scratch owned by the context.  Errors: AMG_EINVAL, AMG_ECUDA. */
+int amg_residual_norm(amg_ctx *c, const double *b_dev, const double *x_dev, double *out_norm);
+
+/* Hierarchy description: *summary (may be NULL) and up to cap level records
+ * (levels may be NULL when cap == 0).  Returns the number of levels
+ * (>= 1) or a negative error. */
+int amg_hierarchy_info(const amg_ctx *c, amg_summary *summary, amg_level_info *levels,
+                       int32_t cap);
+
+/* Host copies of level l in the caller's (level-0) or aggregate-id (l >= 1)
+ * numbering, for parity checks: row_ptr [n+1], col [nnz], val [nnz] of the
+ * level matrix (the Galerkin product for l >= 1, bit-identical to what the
+ * GPU computed); agg [n] (coarse index of every row, -1 for rows left out)
+ * and colour [n] for every level but the coarsest.  Any output may be NULL.
+ * Errors: AMG_EINVAL (l out of range, or agg/colour requested on the
+ * coarsest level). */
+int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col,
+                     double *val, int32_t *agg, int32_t *colour);
+
+/* Host setup of one level, exactly as amg_setup runs it (Sec. 2.1): strength
+ * of connection (Eq. symmetric_strong1/2) and Algorithm 1 with Algorithms 2
+ * and 3, the singleton merge and the isolated-vertex phase, on the matrix
+ * graph of A.  A must be a host matrix (on_device = 0).  agg: host int32 [n],
+ * receives the coarse index of every row in completion order (-1 for rows
+ * without a non-zero off-diagonal); *n_coarse receives the number of
+ * aggregates.  Needs no GPU.  Errors: AMG_EINVAL (bad CSR or parameters). */
+int amg_aggregate(const amg_csr *A, const amg_params *p, int32_t *agg, int32_t *n_coarse);
+
+/* Multicolour ordering of the smoother: greedy colouring of the matrix graph
+ * of A (host matrix) in ascending row order, smallest colour not used by an
+ * already coloured neighbour.  colour: host int32 [n]; *ncolours receives
+ * the number of colours.  Needs no GPU.  Errors: AMG_EINVAL. */
+int amg_colour(const amg_csr *A, int32_t *colour, int32_t *ncolours);
+
+/* Profiler: enable != 0 clears the records and brackets every later kernel
+ * launch of the context with CUDA events on the context stream (adds a few
+ * microseconds per launch); enable == 0 stops recording.  Errors: AMG_EINVAL. */
+int amg_profile_enable(amg_ctx *c, int32_t enable);
+
+/* Synchronises the context stream and fills up to cap records, one per kernel
+ * class that launched; returns the number of classes (>= 0) or an error. */
+int amg_profile_read(amg_ctx *c, amg_kernel_stat *stats, int32_t cap);
+
+/* Release every resource of the context (NULL is allowed). */
+int amg_free(amg_ctx *c);
+
+/* Thread-local description of the last error on this thread ("" if none). */
+const char *amg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMG_H */

@@ -137,40 +137,53 @@ struct Aggregator {
     std::vector<char> inU;         // U: still-unaggregated candidates
     std::set<std::pair<int, int>> by_count;   // (N_na(u), u) for u in U
     std::vector<int> nna;          // N_na(u) = |N(u) ∩ U|
+    std::vector<std::vector<int>> nbrs;   // N(i) of every vertex
     int next_id = 0;
 
     Aggregator(const Csr& A_, const Strength& S_, const Params& p_)
-        : A(A_), S(S_), p(p_), agg(A_.n, -1), inU(A_.n, 0), nna(A_.n, 0) {}
+        : A(A_), S(S_), p(p_), agg(A_.n, -1), inU(A_.n, 0), nna(A_.n, 0) {
+        nbrs.resize(A.n);
+        for (int i = 0; i < A.n; ++i) nbrs[i] = A.neighbours(i);
+    }
 
     // N(a) = vertices outside a adjacent to some vertex of a
     std::set<int> nbr_of_set(const std::set<int>& a) const {
         std::set<int> out;
         for (int x : a)
-            for (int j : A.neighbours(x))
+            for (int j : nbrs[x])
                 if (!a.count(j)) out.insert(j);
         return out;
     }
 
     // diam(a, v): diameter of the subgraph induced by a ∪ {v} (matrix-graph
     // edges), by breadth-first search from every vertex.  Disconnected -> INT_MAX.
-    int diameter(const std::set<int>& verts) const {
+    int diameter(const std::set<int>& vset) const {
+        std::vector<int> verts(vset.begin(), vset.end());
+        const int m = (int)verts.size();
+        auto index_of = [&](int v) {
+            for (int t = 0; t < m; ++t)
+                if (verts[t] == v) return t;
+            return -1;
+        };
         int diam = 0;
-        for (int s : verts) {
-            std::map<int, int> dist;
-            std::queue<int> q;
+        for (int s = 0; s < m; ++s) {
+            std::vector<int> dist(m, -1);
+            std::vector<int> queue = {s};
             dist[s] = 0;
-            q.push(s);
-            while (!q.empty()) {
-                int u = q.front();
-                q.pop();
-                for (int w : A.neighbours(u))
-                    if (verts.count(w) && !dist.count(w)) {
-                        dist[w] = dist[u] + 1;
-                        q.push(w);
+            for (size_t h = 0; h < queue.size(); ++h) {
+                int u = queue[h];
+                for (int w : nbrs[verts[u]]) {
+                    int t = index_of(w);
+                    if (t >= 0 && dist[t] < 0) {
+                        dist[t] = dist[u] + 1;
+                        queue.push_back(t);
                     }
+                }
             }
-            if (dist.size() != verts.size()) return std::numeric_limits<int>::max();
-            for (auto& kv : dist) diam = std::max(diam, kv.second);
+            for (int t = 0; t < m; ++t) {
+                if (dist[t] < 0) return std::numeric_limits<int>::max();
+                diam = std::max(diam, dist[t]);
+            }
         }
         return diam;
     }
@@ -195,7 +208,7 @@ struct Aggregator {
     // aggregate not yet adjacent to a).
     int connect(int v, const std::set<int>& a, const std::set<int>& adj_aggs) const {
         int c = 0;
-        for (int u : A.neighbours(v)) {
+        for (int u : nbrs[v]) {
             if (a.count(u)) continue;
             if (agg[u] >= 0 && adj_aggs.count(agg[u])) c += 2;
             else c += 1;
@@ -207,7 +220,7 @@ struct Aggregator {
     // neighbours of a (Sec. 2.1, last tie-break of Alg. 2)
     int neighbors_score(int v, const std::set<int>& a, const std::set<int>& Na) const {
         int c = 0;
-        for (int u : A.neighbours(v))
+        for (int u : nbrs[v])
             if (inU[u] && !a.count(u) && !Na.count(u)) ++c;
         return c;
     }
@@ -216,7 +229,7 @@ struct Aggregator {
         if (!inU[v]) return;
         by_count.erase({nna[v], v});
         inU[v] = 0;
-        for (int j : A.neighbours(v))
+        for (int j : nbrs[v])
             if (inU[j]) {
                 by_count.erase({nna[j], j});
                 --nna[j];
@@ -262,13 +275,13 @@ struct Aggregator {
                 long long bc = -1, bn = 1;
                 for (int w : C1) {
                     long long c = connect(w, a, adj_aggs);
-                    long long nw = (long long)A.neighbours(w).size();
+                    long long nw = (long long)nbrs[w].size();
                     if (bc < 0 || c * bn > bc * nw) { bc = c; bn = nw; }
                 }
                 std::vector<int> keep;
                 for (int w : C1) {
                     long long c = connect(w, a, adj_aggs);
-                    long long nw = (long long)A.neighbours(w).size();
+                    long long nw = (long long)nbrs[w].size();
                     if (c * bn == bc * nw) keep.push_back(w);
                 }
                 C1 = keep;
@@ -301,7 +314,7 @@ struct Aggregator {
                 if (!inU[w]) continue;
                 if (cons2(w, a) + cons1(w, a) <= 0) continue;     // D
                 int to_a = 0, to_u = 0;
-                for (int u : A.neighbours(w)) {
+                for (int u : nbrs[w]) {
                     if (!is_strong(A, S, w, u)) continue;          // N_delta(w)
                     if (a.count(u)) ++to_a;
                     else if (inU[u] && u != w) ++to_u;
@@ -339,7 +352,7 @@ struct Aggregator {
                 aw.insert(w);
                 if (diameter(aw) > p.d_max) continue;
                 bool shares = false;
-                for (int y : A.neighbours(w))
+                for (int y : nbrs[w])
                     if (agg[y] >= 0 && agg[y] < n_phase1 && adj_a.count(agg[y])) shares = true;
                 if (!shares) continue;
                 chosen = w;
@@ -359,7 +372,7 @@ struct Aggregator {
         for (int v = 0; v < n; ++v) {
             if (!inU[v]) continue;
             int c = 0;
-            for (int j : A.neighbours(v))
+            for (int j : nbrs[v])
                 if (inU[j]) ++c;
             nna[v] = c;
             by_count.insert({c, v});
@@ -378,7 +391,7 @@ struct Aggregator {
                     // strongest strong neighbour (ties: lowest aggregate index)
                     int target = -1;
                     double best_s = -1.0;
-                    for (int u : A.neighbours(v)) {
+                    for (int u : nbrs[v]) {
                         if (!is_strong(A, S, v, u) || agg[u] < 0) continue;
                         double s = coupling(A, v, u);
                         if (s > best_s || (s == best_s && agg[u] < target)) {

@@ -1,0 +1,340 @@
+"""Thin ctypes binding of libamg (include/amg.h).
+
+Every function named ``amg_*`` here forwards to the C entry point of the same
+name; the binding only marshals arguments (numpy arrays for host buffers,
+torch CUDA tensors for device buffers) and turns negative return codes into
+``AmgError``.  All computation happens in the CUDA library: if it is not built,
+``lib()`` raises instead of falling back to anything else.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+AMG_OK = 0
+AMG_PENDING = 1
+AMG_EINVAL = -1
+AMG_ENOMEM = -2
+AMG_ENOTSPD = -3
+AMG_ENOTCONV = -4
+AMG_ETIMEOUT = -5
+AMG_ECUDA = -6
+AMG_ENOTFOUND = -7
+
+AMG_FP64 = 0
+AMG_FP32_IN_FP64 = 1
+
+_c_i32 = ctypes.c_int32
+_c_dbl = ctypes.c_double
+_c_vp = ctypes.c_void_p
+
+
+class amg_csr(ctypes.Structure):
+    _fields_ = [("n", _c_i32), ("nnz", _c_i32), ("row_ptr", _c_vp), ("col", _c_vp),
+                ("val", _c_vp), ("on_device", _c_i32)]
+
+
+class amg_params(ctypes.Structure):
+    _fields_ = [("delta", _c_dbl), ("beta", _c_dbl), ("omega", _c_dbl),
+                ("s_min", _c_i32), ("s_max", _c_i32), ("d_max", _c_i32),
+                ("coarsen_target", _c_i32), ("max_levels", _c_i32), ("dense_cap", _c_i32),
+                ("min_coarsen_rate", _c_dbl), ("precision", _c_i32), ("flexible_cg", _c_i32),
+                ("cuda_stream", _c_vp)]
+
+
+class amg_solve_info(ctypes.Structure):
+    _fields_ = [("status", _c_i32), ("iterations", _c_i32), ("rel_residual", _c_dbl),
+                ("true_rel_residual", _c_dbl), ("solve_ms", _c_dbl)]
+
+
+class amg_level_info(ctypes.Structure):
+    _fields_ = [("n", _c_i32), ("nnz", _c_i32), ("n_coarse", _c_i32), ("ncolours", _c_i32),
+                ("max_agg_size", _c_i32), ("n_isolated", _c_i32), ("n_dirichlet", _c_i32),
+                ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl)]
+
+
+class amg_summary(ctypes.Structure):
+    _fields_ = [("num_levels", _c_i32), ("coarsest_n", _c_i32),
+                ("operator_complexity", _c_dbl), ("host_setup_ms", _c_dbl),
+                ("gpu_galerkin_ms", _c_dbl), ("gpu_other_ms", _c_dbl), ("total_setup_ms", _c_dbl),
+                ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
+                ("pcg_iter_bytes_fp64", _c_dbl), ("pcg_iter_bytes_fp32", _c_dbl)]
+
+
+class amg_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", _c_i32), ("total_ms", _c_dbl),
+                ("bytes", _c_dbl)]
+
+
+def struct_dict(s) -> dict:
+    return {name: getattr(s, name) for name, _ in s._fields_}
+
+
+class AmgError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where} failed ({code}): {msg}")
+        self.code = code
+
+
+# exported symbols and their signatures, as declared in include/amg.h
+_SIGNATURES = {
+    "amg_params_default": ([ctypes.POINTER(amg_params), _c_i32], ctypes.c_int),
+    "amg_setup": ([ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), ctypes.POINTER(_c_vp)], ctypes.c_int),
+    "amg_set_precision": ([_c_vp, _c_i32, _c_i32], ctypes.c_int),
+    "amg_vcycle": ([_c_vp, _c_vp, _c_vp], ctypes.c_int),
+    "amg_pcg_solve": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
+    "amg_pcg_solve_host": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
+    "amg_residual_norm": ([_c_vp, _c_vp, _c_vp, ctypes.POINTER(_c_dbl)], ctypes.c_int),
+    "amg_hierarchy_info": ([_c_vp, ctypes.POINTER(amg_summary), ctypes.POINTER(amg_level_info), _c_i32], ctypes.c_int),
+    "amg_export_level": ([_c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
+    "amg_aggregate": ([ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
+    "amg_colour": ([ctypes.POINTER(amg_csr), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
+    "amg_profile_enable": ([_c_vp, _c_i32], ctypes.c_int),
+    "amg_profile_read": ([_c_vp, ctypes.POINTER(amg_kernel_stat), _c_i32], ctypes.c_int),
+    "amg_free": ([_c_vp], ctypes.c_int),
+    "amg_last_error": ([], ctypes.c_char_p),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """The loaded libamg.so.  Raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libamg.so is not built ({path}); run __graft_entry__.build()")
+    L = ctypes.CDLL(path)
+    for name, (args, res) in _SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str, allow=()):
+    if rc < 0 and rc not in allow:
+        msg = lib().amg_last_error()
+        raise AmgError(rc, where, msg.decode() if msg else "")
+    return rc
+
+
+def _ptr(a) -> Optional[int]:
+    """Address of a numpy array or torch tensor (None passes through)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return a.ctypes.data
+    return int(a.data_ptr())
+
+
+# ---------------------------------------------------------------------------
+# entry points, same names as the C ABI
+# ---------------------------------------------------------------------------
+
+def amg_params_default(dim: int) -> amg_params:
+    p = amg_params()
+    _check(lib().amg_params_default(ctypes.byref(p), dim), "amg_params_default")
+    return p
+
+
+def amg_setup(row_ptr, col, val, params: amg_params) -> int:
+    """row_ptr/col/val: numpy (host) or torch CUDA tensors (device)."""
+    on_dev = not isinstance(row_ptr, np.ndarray)
+    if not on_dev:
+        row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+        col = np.ascontiguousarray(col, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+    n = int(row_ptr.shape[0]) - 1
+    A = amg_csr(n, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val), int(on_dev))
+    h = _c_vp()
+    _check(lib().amg_setup(ctypes.byref(A), ctypes.byref(params), ctypes.byref(h)), "amg_setup")
+    return h.value
+
+
+def amg_set_precision(ctx: int, precision: int, flexible_cg: int = -1) -> None:
+    _check(lib().amg_set_precision(ctx, precision, flexible_cg), "amg_set_precision")
+
+
+def amg_vcycle(ctx: int, r_dev, z_dev) -> None:
+    _check(lib().amg_vcycle(ctx, _ptr(r_dev), _ptr(z_dev)), "amg_vcycle")
+
+
+def amg_pcg_solve(ctx: int, b_dev, x_dev, tol: float, maxit: int):
+    info = amg_solve_info()
+    rc = lib().amg_pcg_solve(ctx, _ptr(b_dev), _ptr(x_dev), tol, maxit, ctypes.byref(info))
+    _check(rc, "amg_pcg_solve", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    return rc, info
+
+
+def amg_pcg_solve_host(ctx: int, b_host: np.ndarray, x_host: np.ndarray, tol: float, maxit: int):
+    info = amg_solve_info()
+    rc = lib().amg_pcg_solve_host(ctx, _ptr(b_host), _ptr(x_host), tol, maxit, ctypes.byref(info))
+    _check(rc, "amg_pcg_solve_host", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    return rc, info
+
+
+def amg_residual_norm(ctx: int, b_dev, x_dev) -> float:
+    out = _c_dbl()
+    _check(lib().amg_residual_norm(ctx, _ptr(b_dev), _ptr(x_dev), ctypes.byref(out)),
+           "amg_residual_norm")
+    return out.value
+
+
+def amg_hierarchy_info(ctx: int):
+    s = amg_summary()
+    nl = _check(lib().amg_hierarchy_info(ctx, ctypes.byref(s), None, 0), "amg_hierarchy_info")
+    levels = (amg_level_info * nl)()
+    _check(lib().amg_hierarchy_info(ctx, ctypes.byref(s), levels, nl), "amg_hierarchy_info")
+    return struct_dict(s), [struct_dict(l) for l in levels]
+
+
+def amg_export_level(ctx: int, l: int) -> dict:
+    _, levels = amg_hierarchy_info(ctx)
+    info = levels[l]
+    n, nnz = info["n"], info["nnz"]
+    last = l == len(levels) - 1
+    rp = np.zeros(n + 1, dtype=np.int32)
+    ci = np.zeros(nnz, dtype=np.int32)
+    va = np.zeros(nnz, dtype=np.float64)
+    agg = None if last else np.zeros(n, dtype=np.int32)
+    col = None if last else np.zeros(n, dtype=np.int32)
+    _check(lib().amg_export_level(ctx, l, _ptr(rp), _ptr(ci), _ptr(va), _ptr(agg), _ptr(col)),
+           "amg_export_level")
+    return dict(row_ptr=rp, col=ci, val=va, agg=agg, colour=col, **info)
+
+
+def _host_csr(row_ptr, col, val):
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    A = amg_csr(int(row_ptr.shape[0]) - 1, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val), 0)
+    return A, (row_ptr, col, val)
+
+
+def amg_aggregate(row_ptr, col, val, params: amg_params):
+    """Host aggregation of one level; returns (agg, n_coarse)."""
+    A, keep = _host_csr(row_ptr, col, val)
+    agg = np.zeros(A.n, dtype=np.int32)
+    nc = _c_i32()
+    _check(lib().amg_aggregate(ctypes.byref(A), ctypes.byref(params), _ptr(agg), ctypes.byref(nc)),
+           "amg_aggregate")
+    return agg, int(nc.value)
+
+
+def amg_colour(row_ptr, col, val):
+    A, keep = _host_csr(row_ptr, col, val)
+    colour = np.zeros(A.n, dtype=np.int32)
+    nc = _c_i32()
+    _check(lib().amg_colour(ctypes.byref(A), _ptr(colour), ctypes.byref(nc)), "amg_colour")
+    return colour, int(nc.value)
+
+
+def amg_profile_enable(ctx: int, enable: bool) -> None:
+    _check(lib().amg_profile_enable(ctx, int(bool(enable))), "amg_profile_enable")
+
+
+def amg_profile_read(ctx: int) -> list:
+    n = _check(lib().amg_profile_read(ctx, None, 0), "amg_profile_read")
+    arr = (amg_kernel_stat * max(n, 1))()
+    _check(lib().amg_profile_read(ctx, arr, n), "amg_profile_read")
+    out = []
+    for k in range(n):
+        d = struct_dict(arr[k])
+        d["name"] = arr[k].name.decode()
+        out.append(d)
+    return out
+
+
+def amg_free(ctx: int) -> None:
+    if ctx:
+        lib().amg_free(ctx)
+
+
+def amg_last_error() -> str:
+    m = lib().amg_last_error()
+    return m.decode() if m else ""
+
+
+# ---------------------------------------------------------------------------
+# convenience wrapper used by tests and the benchmark
+# ---------------------------------------------------------------------------
+
+class AMG:
+    """Owns one context.  Matrices from numpy (host) arrays; vectors as torch
+    CUDA float64 tensors."""
+
+    def __init__(self, row_ptr, col, val, dim: int = 3, precision: int = AMG_FP64,
+                 stream=None, **overrides):
+        self.params = amg_params_default(dim)
+        for k, v in overrides.items():
+            setattr(self.params, k, v)
+        self.params.precision = precision
+        if stream is not None:
+            self.params.cuda_stream = int(stream.cuda_stream)
+        self.ctx = amg_setup(row_ptr, col, val, self.params)
+        self.n = int(row_ptr.shape[0]) - 1
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            amg_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: int, flexible_cg: int = -1):
+        amg_set_precision(self.ctx, precision, flexible_cg)
+
+    def vcycle(self, r_dev, z_dev=None):
+        import torch
+        if z_dev is None:
+            z_dev = torch.empty_like(r_dev)
+        amg_vcycle(self.ctx, r_dev, z_dev)
+        return z_dev
+
+    def solve(self, b_dev, x_dev=None, tol: float = 1e-8, maxit: int = 500):
+        import torch
+        if x_dev is None:
+            x_dev = torch.zeros_like(b_dev)
+        rc, info = amg_pcg_solve(self.ctx, b_dev, x_dev, tol, maxit)
+        return x_dev, rc, struct_dict(info)
+
+    def solve_host(self, b_host: np.ndarray, x_host: np.ndarray, tol: float = 1e-8,
+                   maxit: int = 500):
+        rc, info = amg_pcg_solve_host(self.ctx, b_host, x_host, tol, maxit)
+        return rc, struct_dict(info)
+
+    def residual_norm(self, b_dev, x_dev) -> float:
+        return amg_residual_norm(self.ctx, b_dev, x_dev)
+
+    def info(self):
+        return amg_hierarchy_info(self.ctx)
+
+    def profile(self, enable: bool):
+        amg_profile_enable(self.ctx, enable)
+
+    def profile_read(self) -> list:
+        return amg_profile_read(self.ctx)
+
+    def level(self, l: int) -> dict:
+        return amg_export_level(self.ctx, l)

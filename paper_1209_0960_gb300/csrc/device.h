@@ -1,0 +1,270 @@
+// Internal declarations shared by the CUDA translation units of libamg.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "amg.h"
+#include "host_setup.h"
+
+namespace amg {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+struct Error {
+    int code;
+    std::string msg;
+};
+
+void set_last_error(const std::string& msg);
+
+#define AMG_CUDA_TRY(expr)                                                          \
+    do {                                                                            \
+        cudaError_t e_ = (expr);                                                    \
+        if (e_ != cudaSuccess)                                                      \
+            throw ::amg::Error{AMG_ECUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)}; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory owned by a context
+// ---------------------------------------------------------------------------
+class DevArena {
+public:
+    ~DevArena() { release(); }
+    template <typename T>
+    T* alloc(size_t count) {
+        if (count == 0) count = 1;
+        void* p = nullptr;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            throw Error{AMG_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+                                        " bytes failed: " + cudaGetErrorString(e)};
+        }
+        ptrs_.push_back(p);
+        bytes_ += count * sizeof(T);
+        return static_cast<T*>(p);
+    }
+    void free_one(void* p) {
+        for (auto& q : ptrs_)
+            if (q == p) {
+                cudaFree(q);
+                q = nullptr;
+            }
+    }
+    void release() {
+        for (void* p : ptrs_)
+            if (p) cudaFree(p);
+        ptrs_.clear();
+        bytes_ = 0;
+    }
+    size_t bytes() const { return bytes_; }
+
+private:
+    std::vector<void*> ptrs_;
+    size_t bytes_ = 0;
+};
+
+// Scalars of the CG recurrence, resident on the device.
+struct PcgScalars {
+    double rr0;       // ||r_0||^2
+    double rr;        // ||r_k||^2
+    double rho;       // r_k . z_k
+    double pq;        // p . A p
+    double alpha, beta;
+    double tol2;      // tol^2
+    int32_t done;     // 1 once ||r_k|| <= tol ||r_0||
+    int32_t iters;
+    int32_t status;   // 0, or AMG_ENOTSPD
+    int32_t flexible;
+    int32_t maxit;
+    int32_t pad;
+};
+
+// One level of the hierarchy on the device.  Rows are stored in the level's
+// smoothing order: grouped by colour, inside a colour by coarse index, then by
+// original index.  The off-diagonal part is CSR, the diagonal separate.
+struct DevLevel {
+    int32_t n = 0;
+    int32_t nnz_off = 0;
+    int32_t ncolours = 0;
+    int32_t n_coarse = 0;
+    std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
+    std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
+    int32_t lpr = 8;                  // lanes per row of the row kernels
+    int32_t* rp = nullptr;            // [n+1] off-diagonal row pointers
+    int32_t* ci = nullptr;            // [nnz_off] permuted column indices
+    double* va = nullptr;             // [nnz_off]
+    double* diag = nullptr;           // [n]
+    double* dinv = nullptr;           // [n] 1 / A_ii
+    int32_t* agg = nullptr;           // [n] permuted coarse index or -1
+    int32_t* rptr = nullptr;          // [n_coarse+1] restriction lists
+    int32_t* ridx = nullptr;          // fine rows of each coarse row
+    double* x = nullptr;              // level correction
+    double* b = nullptr;              // level right-hand side
+    double* r = nullptr;              // level residual
+    // float32 copies, symmetric diagonal scaling S^-1 A S^-1 with S = diag(sqrt(A_ii))
+    float* va32 = nullptr;
+    float* dinv32 = nullptr;
+    float* diag32 = nullptr;
+    float* t32 = nullptr;             // s_fine[i] / s_coarse[agg[i]] for the transfers
+    float* x32 = nullptr;
+    float* b32 = nullptr;
+    float* r32 = nullptr;
+};
+
+// Launch profiler: events around launches, grouped by kernel class.
+struct Profiler {
+    bool on = false;
+    struct Rec { int kind; double bytes; int ev; };
+    std::vector<cudaEvent_t> events;   // pool, pairs (start, end)
+    std::vector<Rec> recs;
+    int next = 0;
+};
+
+enum KernelKind : int {
+    kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
+    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKNumKinds
+};
+
+struct HostLevel {
+    HostCsr A;                        // original numbering of this level
+    AggResult agg;                    // aggregation of this level (not on the coarsest)
+    std::vector<int32_t> colour;
+    int32_t ncolours = 0;
+    std::vector<int32_t> perm;        // original index -> position in smoothing order
+};
+
+}  // namespace amg
+
+namespace amg {
+
+// ---------------------------------------------------------------------------
+// kernel launchers (kernels.cu)
+// ---------------------------------------------------------------------------
+constexpr int kBlock = 256;
+
+// modes of the deterministic "last block" reduction
+enum FinalMode : int {
+    kRR0 = 0,       // initial residual norm
+    kPQ = 1,        // p.Ap -> alpha
+    kRR = 2,        // updated residual norm -> convergence test
+    kRZ = 3,        // r.z -> beta (standard CG)
+    kRZFlex = 4,    // r.z and r.(z - z_old) -> beta (flexible CG)
+    kRho0 = 5,      // initial r.z, p = z
+    kStore = 6,     // raw sum into out[0]
+};
+
+// device work areas of the CG reductions
+struct CgWork {
+    double* partials = nullptr;       // [max blocks]
+    double* partials2 = nullptr;
+    unsigned int* counters = nullptr; // one per reduction kernel, self-resetting
+    PcgScalars* sc = nullptr;
+};
+
+extern int g_reduction_blocks;        // grid of the reduction kernels (SMs x 8)
+int reduction_blocks(int64_t work_threads);
+
+void launch_gs(const DevLevel& L, int r0, int r1, const double* b, double* x, cudaStream_t s);
+void launch_gs32(const DevLevel& L, int r0, int r1, const float* b, float* x, cudaStream_t s);
+void launch_residual(const DevLevel& L, const double* b, const double* x, double* r, cudaStream_t s);
+void launch_residual32(const DevLevel& L, const float* b, const float* x, float* r, cudaStream_t s);
+void launch_restrict(const DevLevel& L, const double* r, double* bc, cudaStream_t s);
+void launch_restrict32(const DevLevel& L, const float* r, float* bc, cudaStream_t s);
+void launch_prolong(const DevLevel& L, const double* e, double* x, double omega, cudaStream_t s);
+void launch_prolong32(const DevLevel& L, const float* e, float* x, float omega, cudaStream_t s);
+void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s);
+void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s);
+void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s);
+void launch_scatter(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s);
+void launch_to_scaled32(int n, const double* r, const double* isq, float* rhat, cudaStream_t s);
+void launch_from_scaled32(int n, const float* zhat, const double* isq, double* z, cudaStream_t s);
+
+void launch_cg_residual(const DevLevel& L, const double* b, const double* x, double* r,
+                        CgWork& w, int mode, double* out, cudaStream_t s);
+void launch_cg_spmv_pq(const DevLevel& L, const double* p, double* q, CgWork& w, cudaStream_t s);
+void launch_cg_update(int n, double* x, double* r, const double* p, const double* q, CgWork& w,
+                      cudaStream_t s);
+void launch_cg_rz(int n, const double* r, const double* z, const double* zold, double* p,
+                  CgWork& w, int mode, cudaStream_t s);
+void launch_cg_p(int n, const double* z, double* p, double* zold, const CgWork& w,
+                 cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// setup on the device (setup_device.cu)
+// ---------------------------------------------------------------------------
+struct DevCsr {
+    int32_t n = 0;
+    int64_t nnz = 0;
+    int32_t* rp = nullptr;
+    int32_t* ci = nullptr;
+    double* va = nullptr;
+};
+
+// G = P^T A P for the aggregation agg (device, original numbering).  The host
+// receives G (rows sorted, sums in fine CSR order) in Gh; the device copy in
+// Gd is allocated from arena.
+void galerkin_device(const DevCsr& A, const HostCsr& Ah, const AggResult& agg, DevArena& arena,
+                     DevCsr& Gd, HostCsr& Gh, cudaStream_t s);
+
+// Build the smoothing-order device level from the original-order device
+// matrix A and the permutation perm (original -> new position).
+void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<int32_t>& perm,
+                        DevArena& arena, DevLevel& L, cudaStream_t s);
+
+// Dense inverse of the (original-order) coarsest matrix through a Cholesky
+// factorisation of its lower triangle; returns false when a pivot is not
+// positive.
+bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s);
+
+// Minv_s = S Minv S, S = diag(sqrt(diag)): the inverse of S^-1 A S^-1.
+void scale_inverse_device(int n, const double* diag, const double* Minv, double* Minv_s,
+                          cudaStream_t s);
+
+// float32 copies of a level scaled by S = diag(sqrt(A_ii)) (fine) and its
+// coarse neighbour (for t32); coarse_diag is null on the coarsest level.
+void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, cudaStream_t s);
+
+}  // namespace amg
+
+struct amg_ctx {
+    amg_params p;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    amg::DevArena mem;
+    std::vector<amg::HostLevel> hl;
+    std::vector<amg::DevLevel> dl;
+    int32_t nL = 0;                   // coarsest size
+    double* Ainv = nullptr;           // [nL x nL] inverse of the coarsest matrix
+    double* Ainv_s = nullptr;         // [nL x nL] inverse of the scaled coarsest matrix
+    double* isq0 = nullptr;           // [n] 1 / sqrt(A_ii) of level 0 (FP32 entry/exit)
+    int32_t* perm0 = nullptr;         // [n] device copy of the level-0 order: caller index -> position
+    // level-0 CG vectors, smoothing order
+    double *x = nullptr, *r = nullptr, *z = nullptr, *zold = nullptr, *pv = nullptr,
+           *q = nullptr, *bb = nullptr;
+    amg::CgWork work;
+    amg::PcgScalars* sc_host = nullptr;   // pinned mirror of *work.sc
+    double* norm_dev = nullptr;
+    int precision = AMG_FP64;
+    int flexible = 0;
+    bool fp32_ready = false;
+    amg_summary summary{};
+    std::vector<amg_level_info> linfo;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    amg::Profiler prof;
+
+    amg_ctx() = default;
+    amg_ctx(const amg_ctx&) = delete;
+    amg_ctx& operator=(const amg_ctx&) = delete;
+    ~amg_ctx() {
+        if (sc_host) cudaFreeHost(sc_host);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+        for (cudaEvent_t e : prof.events) cudaEventDestroy(e);
+    }
+};

@@ -1,0 +1,39 @@
+// Host-side setup of the AMG hierarchy: CSR validation, strength of
+// connection, greedy aggregation and multicolouring (Sec. 2.1).
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "amg.h"
+
+namespace amg {
+
+struct HostCsr {
+    int32_t n = 0;
+    std::vector<int32_t> rp, ci;
+    std::vector<double> va;
+    int64_t nnz() const { return rp.empty() ? 0 : rp[n]; }
+};
+
+struct AggResult {
+    std::vector<int32_t> agg;   // coarse index per row, -1 = not aggregated
+    int32_t nc = 0;
+    int32_t max_size = 0;
+    int32_t n_isolated = 0;
+    int32_t n_dirichlet = 0;
+};
+
+// Checks sortedness/uniqueness of columns, a positive diagonal and a
+// symmetric pattern.  Returns false with a message in err.
+bool validate_csr(const HostCsr& A, std::string& err);
+
+// Algorithm 1 (with Algorithms 2, 3, the singleton merge and the isolated
+// phase) on the graph of A under the parameters p.
+AggResult aggregate(const HostCsr& A, const amg_params& p);
+
+// Greedy colouring in ascending row order; returns the number of colours.
+int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour);
+
+}  // namespace amg

@@ -1,0 +1,795 @@
+// Hierarchy construction, V-cycle, preconditioned CG and the C ABI of libamg
+// (Blatt, Ippisch & Bastian, arXiv:1209.0960: Sec. 2 multigrid cycle,
+// Sec. 2.1 coarsening, Sec. 5 solver configuration).
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <numeric>
+
+#include "device.h"
+
+namespace amg {
+
+thread_local std::string t_last_error;
+
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
+namespace {
+
+double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+void check_params(const amg_params& p) {
+    if (!(p.delta > 0.0 && p.delta < 1.0)) throw Error{AMG_EINVAL, "delta must lie in (0, 1)"};
+    if (!(p.beta > 0.0 && p.beta < 1.0)) throw Error{AMG_EINVAL, "beta must lie in (0, 1)"};
+    if (!(p.omega > 0.0)) throw Error{AMG_EINVAL, "omega must be positive"};
+    if (p.s_min < 1 || p.s_max < p.s_min || p.s_max > 64)
+        throw Error{AMG_EINVAL, "need 1 <= s_min <= s_max <= 64"};
+    if (p.d_max < 1) throw Error{AMG_EINVAL, "d_max must be >= 1"};
+    if (p.max_levels < 1 || p.max_levels > 64) throw Error{AMG_EINVAL, "max_levels must be in 1..64"};
+    if (p.dense_cap < 1 || p.dense_cap > 16384) throw Error{AMG_EINVAL, "dense_cap must be in 1..16384"};
+    if (!(p.min_coarsen_rate >= 1.0)) throw Error{AMG_EINVAL, "min_coarsen_rate must be >= 1"};
+    if (p.precision != AMG_FP64 && p.precision != AMG_FP32_IN_FP64)
+        throw Error{AMG_EINVAL, "precision must be AMG_FP64 or AMG_FP32_IN_FP64"};
+}
+
+template <typename T>
+void upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
+    if (!src.empty())
+        AMG_CUDA_TRY(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
+}
+
+// Smoothing order of level l: rows sorted by (colour, position of the coarse
+// aggregate in the next level's order, original index); rows outside every
+// aggregate come last inside their colour.
+std::vector<int32_t> smoothing_order(const HostLevel& h, const std::vector<int32_t>& next_perm) {
+    const int32_t n = h.A.n;
+    std::vector<int32_t> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    auto key = [&](int32_t i) {
+        const int32_t a = h.agg.agg[i];
+        return std::make_pair(h.colour[i], a >= 0 ? next_perm[a] : INT32_MAX);
+    };
+    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return key(x) < key(y); });
+    std::vector<int32_t> perm(n);
+    for (int32_t r = 0; r < n; ++r) perm[idx[r]] = r;
+    return perm;
+}
+
+// modelled DRAM bytes of one V-cycle on a level (read every stored entry and
+// vector element a pass needs once; neighbour values of x come from cache)
+double level_vcycle_bytes(const DevLevel& L, int64_t n_coarse, bool coarsest, int vbytes) {
+    const double n = L.n;
+    if (coarsest) return n * n * 8.0 + 2.0 * n * vbytes;     // dense inverse times a vector
+    const double z = L.nnz_off;
+    const double M = z * (vbytes + 4) + 4.0 * (n + 1) + n * vbytes;   // off-diagonal CSR + diagonal
+    const double C = L.ncolours;
+    // pre and post smoothing: 2 x (2C - 1) colour passes = 2 (2C-1)/C matrix passes,
+    // each colour pass reads b and writes x for its rows
+    const double sgs = 2.0 * (2.0 * C - 1.0) / C * (M + 2.0 * n * vbytes);
+    const double resid = M + 3.0 * n * vbytes;                // read b, x; write r
+    const double restr = n * (vbytes + 4) + 4.0 * (n_coarse + 1) + n_coarse * vbytes;
+    const double prol = n * (2.0 * vbytes + 4) + n_coarse * vbytes;
+    const double zero = n * vbytes;                           // x = 0 before pre-smoothing
+    const double scal = vbytes == 4 ? 2.0 * n * 4 : 0.0;      // transfer weights
+    return sgs + resid + restr + prol + zero + scal;
+}
+
+void fill_info(amg_ctx* c) {
+    const int L = (int)c->dl.size();
+    c->linfo.assign(L, amg_level_info{});
+    double b64 = 0, b32 = 0, nnz0 = 0, nnzs = 0;
+    for (int l = 0; l < L; ++l) {
+        const auto& h = c->hl[l];
+        const auto& d = c->dl[l];
+        amg_level_info& li = c->linfo[l];
+        li.n = h.A.n;
+        li.nnz = (int32_t)h.A.nnz();
+        const bool last = l == L - 1;
+        li.n_coarse = last ? 0 : h.agg.nc;
+        li.ncolours = last ? 0 : h.ncolours;
+        li.max_agg_size = last ? 0 : h.agg.max_size;
+        li.n_isolated = last ? 0 : h.agg.n_isolated;
+        li.n_dirichlet = last ? 0 : h.agg.n_dirichlet;
+        li.vcycle_bytes_fp64 = level_vcycle_bytes(d, li.n_coarse, last, 8);
+        li.vcycle_bytes_fp32 = level_vcycle_bytes(d, li.n_coarse, last, 4);
+        b64 += li.vcycle_bytes_fp64;
+        b32 += li.vcycle_bytes_fp32;
+        if (l == 0) nnz0 = li.nnz;
+        nnzs += li.nnz;
+    }
+    c->summary.num_levels = L;
+    c->summary.coarsest_n = c->nL;
+    c->summary.operator_complexity = nnzs / nnz0;
+    c->summary.vcycle_bytes_fp64 = b64;
+    c->summary.vcycle_bytes_fp32 = b32;
+    // CG outside the V-cycle, float64 level-0 vectors: SpMV q = A p (matrix,
+    // read p, write q), update x, r (read x, p, r, q; write x, r), r.z (read
+    // r, z), p = z + beta p (read z, p; write p)
+    const DevLevel& d0 = c->dl[0];
+    const double n = d0.n;
+    const double M64 = d0.nnz_off * 12.0 + 4.0 * (n + 1) + 8.0 * n;
+    const double cg = (M64 + 16.0 * n) + 48.0 * n + 16.0 * n + 24.0 * n;
+    c->summary.pcg_iter_bytes_fp64 = cg + b64;
+    c->summary.pcg_iter_bytes_fp32 = cg + b32 + 8.0 * n * 3;  // conversions in and out
+}
+
+// ---------------------------------------------------------------------------
+// launch profiler: CUDA events around launches, grouped by kernel class, with
+// the modelled algorithmic DRAM bytes of each launch
+// ---------------------------------------------------------------------------
+const char* kKindNames[kKNumKinds] = {
+    "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
+    "coarse_solve", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
+    "zero", "permute"};
+
+struct ProfScope {
+    amg_ctx* c;
+    int idx = -1;
+    ProfScope(amg_ctx* c_, int kind, double bytes) : c(c_) {
+        Profiler& P = c->prof;
+        if (!P.on || P.next + 2 > (int)P.events.size()) return;
+        idx = P.next;
+        P.next += 2;
+        cudaEventRecord(P.events[idx], c->stream);
+        P.recs.push_back({kind, bytes, idx});
+    }
+    ~ProfScope() {
+        if (idx >= 0) cudaEventRecord(c->prof.events[idx + 1], c->stream);
+    }
+};
+
+// Gauss-Seidel pass over m rows with z off-diagonal entries: CSR values and
+// indices, row pointers, 1/A_ii, b and the written x of those rows, and every
+// neighbour value of x once.
+double gs_bytes(const DevLevel& L, int col, int vb) {
+    const double m = L.cptr[col + 1] - L.cptr[col];
+    const double z = (double)L.cnnz[col];
+    return z * (vb + 4) + m * (4 + 3.0 * vb) + 4 + std::min(z, (double)L.n - m) * vb;
+}
+double residual_bytes(const DevLevel& L, int vb) {
+    return (double)L.nnz_off * (vb + 4) + 4.0 * (L.n + 1) + 4.0 * L.n * vb;
+}
+double restrict_bytes(const DevLevel& L, int vb, bool scaled) {
+    return (double)L.n * (4 + vb + (scaled ? 4 : 0)) + 4.0 * (L.n_coarse + 1) + (double)L.n_coarse * vb;
+}
+double prolong_bytes(const DevLevel& L, int vb, bool scaled) {
+    return (double)L.n * (4 + 2.0 * vb + (scaled ? 4 : 0)) + (double)L.n_coarse * vb;
+}
+
+// ---------------------------------------------------------------------------
+// V-cycle (Sec. 2): pre-smooth, restrict the residual, recurse, prolongate
+// with omega, post-smooth; dense solve on the coarsest level
+// ---------------------------------------------------------------------------
+void gs64(amg_ctx* c, const DevLevel& L, int col, const double* b, double* x) {
+    ProfScope ps(c, &L == &c->dl[0] ? kKGsL0 : kKGsCoarse, gs_bytes(L, col, 8));
+    launch_gs(L, L.cptr[col], L.cptr[col + 1], b, x, c->stream);
+}
+
+void sgs64(amg_ctx* c, const DevLevel& L, const double* b, double* x) {
+    for (int col = 0; col < L.ncolours; ++col) gs64(c, L, col, b, x);
+    for (int col = L.ncolours - 2; col >= 0; --col) gs64(c, L, col, b, x);
+}
+
+void vcycle64(amg_ctx* c, int l, const double* b, double* x) {
+    const int nlev = (int)c->dl.size();
+    DevLevel& L = c->dl[l];
+    if (l == nlev - 1) {
+        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 16.0 * c->nL);
+        launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream);
+        return;
+    }
+    DevLevel& C = c->dl[l + 1];
+    {
+        ProfScope ps(c, kKZero, 8.0 * L.n);
+        AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * L.n, c->stream));
+    }
+    sgs64(c, L, b, x);
+    {
+        ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_bytes(L, 8));
+        launch_residual(L, b, x, L.r, c->stream);
+    }
+    {
+        ProfScope ps(c, kKRestrict, restrict_bytes(L, 8, false));
+        launch_restrict(L, L.r, C.b, c->stream);
+    }
+    vcycle64(c, l + 1, C.b, C.x);
+    {
+        ProfScope ps(c, kKProlong, prolong_bytes(L, 8, false));
+        launch_prolong(L, C.x, x, c->p.omega, c->stream);
+    }
+    sgs64(c, L, b, x);
+}
+
+void gs32(amg_ctx* c, const DevLevel& L, int col, const float* b, float* x) {
+    ProfScope ps(c, &L == &c->dl[0] ? kKGsL0 : kKGsCoarse, gs_bytes(L, col, 4));
+    launch_gs32(L, L.cptr[col], L.cptr[col + 1], b, x, c->stream);
+}
+
+void sgs32(amg_ctx* c, const DevLevel& L, const float* b, float* x) {
+    for (int col = 0; col < L.ncolours; ++col) gs32(c, L, col, b, x);
+    for (int col = L.ncolours - 2; col >= 0; --col) gs32(c, L, col, b, x);
+}
+
+void vcycle32(amg_ctx* c, int l, const float* b, float* x) {
+    const int nlev = (int)c->dl.size();
+    DevLevel& L = c->dl[l];
+    if (l == nlev - 1) {
+        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 8.0 * c->nL);
+        launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream);
+        return;
+    }
+    DevLevel& C = c->dl[l + 1];
+    {
+        ProfScope ps(c, kKZero, 4.0 * L.n);
+        AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * L.n, c->stream));
+    }
+    sgs32(c, L, b, x);
+    {
+        ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_bytes(L, 4));
+        launch_residual32(L, b, x, L.r32, c->stream);
+    }
+    {
+        ProfScope ps(c, kKRestrict, restrict_bytes(L, 4, true));
+        launch_restrict32(L, L.r32, C.b32, c->stream);
+    }
+    vcycle32(c, l + 1, C.b32, C.x32);
+    {
+        ProfScope ps(c, kKProlong, prolong_bytes(L, 4, true));
+        launch_prolong32(L, C.x32, x, (float)c->p.omega, c->stream);
+    }
+    sgs32(c, L, b, x);
+}
+
+// z = B r on level 0 (smoothing order) in the context's precision
+void precondition(amg_ctx* c, const double* r, double* z) {
+    if (c->precision == AMG_FP64) {
+        vcycle64(c, 0, r, z);
+    } else {
+        DevLevel& L0 = c->dl[0];
+        {
+            ProfScope ps(c, kKConvert, 20.0 * L0.n);
+            launch_to_scaled32(L0.n, r, c->isq0, L0.b32, c->stream);
+        }
+        vcycle32(c, 0, L0.b32, L0.x32);
+        {
+            ProfScope ps(c, kKConvert, 20.0 * L0.n);
+            launch_from_scaled32(L0.n, L0.x32, c->isq0, z, c->stream);
+        }
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+}
+
+void ensure_fp32(amg_ctx* c) {
+    if (c->fp32_ready) return;
+    const int nlev = (int)c->dl.size();
+    for (int l = 0; l < nlev; ++l) {
+        DevLevel& L = c->dl[l];
+        const double* cdiag = (l + 1 < nlev) ? c->dl[l + 1].diag : nullptr;
+        build_level_fp32(L, cdiag, c->mem, c->stream);
+    }
+    c->Ainv_s = c->mem.alloc<double>((size_t)c->nL * c->nL);
+    scale_inverse_device(c->nL, c->dl[nlev - 1].diag, c->Ainv, c->Ainv_s, c->stream);
+    AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    c->fp32_ready = true;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioned CG on level-0 vectors in smoothing order (c->bb, c->x)
+// ---------------------------------------------------------------------------
+int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
+    cudaStream_t s = c->stream;
+    DevLevel& L0 = c->dl[0];
+    const int n = L0.n;
+    PcgScalars init{};
+    init.tol2 = tol * tol;
+    init.flexible = c->flexible;
+    init.maxit = maxit;
+    *c->sc_host = init;
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->work.sc, c->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+    launch_cg_residual(L0, c->bb, c->x, c->r, c->work, kRR0, nullptr, s);
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    int status = AMG_OK;
+    if (!c->sc_host->done) {
+        precondition(c, c->r, c->z);
+        launch_cg_rz(n, c->r, c->z, nullptr, c->pv, c->work, kRho0, s);
+        if (c->flexible)
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->zold, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        while (true) {
+            if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
+            {
+                ProfScope ps(c, kKCgSpmv, (double)L0.nnz_off * 12 + 4.0 * (n + 1) + 24.0 * n);
+                launch_cg_spmv_pq(L0, c->pv, c->q, c->work, s);
+            }
+            {
+                ProfScope ps(c, kKCgUpdate, 48.0 * n);
+                launch_cg_update(n, c->x, c->r, c->pv, c->q, c->work, s);
+            }
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (c->sc_host->status != 0) { status = c->sc_host->status; break; }
+            if (c->sc_host->done) break;
+            if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
+            precondition(c, c->r, c->z);
+            {
+                ProfScope ps(c, kKCgDot, (c->flexible ? 24.0 : 16.0) * n);
+                launch_cg_rz(n, c->r, c->z, c->zold, c->pv, c->work, c->flexible ? kRZFlex : kRZ, s);
+            }
+            {
+                ProfScope ps(c, kKCgP, (c->flexible ? 32.0 : 24.0) * n);
+                launch_cg_p(n, c->z, c->pv, c->flexible ? c->zold : nullptr, c->work, s);
+            }
+        }
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+    if (info) {
+        const PcgScalars& h = *c->sc_host;
+        info->status = status;
+        info->iterations = h.iters;
+        info->rel_residual = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+        // true residual of the final iterate
+        launch_cg_residual(L0, c->bb, c->x, nullptr, c->work, kStore, c->norm_dev, s);
+        double rr = 0.0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&rr, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        info->true_rel_residual = h.rr0 > 0 ? std::sqrt(rr / h.rr0) : 0.0;
+    }
+    return status;
+}
+
+struct Guard {
+    template <typename F>
+    static int run(F&& f) {
+        try {
+            f();
+            t_last_error.clear();
+            return AMG_OK;
+        } catch (const Error& e) {
+            t_last_error = e.msg;
+            return e.code;
+        } catch (const std::bad_alloc&) {
+            t_last_error = "host allocation failed";
+            return AMG_ENOMEM;
+        } catch (const std::exception& e) {
+            t_last_error = e.what();
+            return AMG_EINVAL;
+        }
+    }
+};
+
+void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
+    if (!A || !prm || !out) throw Error{AMG_EINVAL, "null argument"};
+    *out = nullptr;
+    check_params(*prm);
+    if (A->n <= 0 || A->nnz <= 0 || !A->row_ptr || !A->col || !A->val)
+        throw Error{AMG_EINVAL, "empty or null matrix"};
+    const double t_start = now_ms();
+    auto c = std::make_unique<amg_ctx>();
+    c->p = *prm;
+    c->stream = static_cast<cudaStream_t>(prm->cuda_stream);
+    AMG_CUDA_TRY(cudaGetDevice(&c->device));
+    int sms = 0;
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+    g_reduction_blocks = std::max(1, sms) * 8;
+    cudaStream_t s = c->stream;
+
+    // level 0 on the host (original numbering)
+    c->hl.emplace_back();
+    HostCsr& A0 = c->hl[0].A;
+    A0.n = A->n;
+    A0.rp.resize((size_t)A->n + 1);
+    const cudaMemcpyKind kind = A->on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost;
+    AMG_CUDA_TRY(cudaMemcpy(A0.rp.data(), A->row_ptr, sizeof(int32_t) * (A->n + 1), kind));
+    if (A0.rp[A->n] != A->nnz) throw Error{AMG_EINVAL, "row_ptr[n] != nnz"};
+    A0.ci.resize(A->nnz);
+    A0.va.resize(A->nnz);
+    AMG_CUDA_TRY(cudaMemcpy(A0.ci.data(), A->col, sizeof(int32_t) * A->nnz, kind));
+    AMG_CUDA_TRY(cudaMemcpy(A0.va.data(), A->val, sizeof(double) * A->nnz, kind));
+    std::string err;
+    if (!validate_csr(A0, err)) throw Error{AMG_EINVAL, err};
+
+    DevArena setup_mem;   // original-order level matrices, freed at the end
+    std::vector<DevCsr> dA(1);
+    dA[0].n = A0.n;
+    dA[0].nnz = A0.nnz();
+    dA[0].rp = setup_mem.alloc<int32_t>(A0.n + 1);
+    dA[0].ci = setup_mem.alloc<int32_t>(A0.nnz());
+    dA[0].va = setup_mem.alloc<double>(A0.nnz());
+    upload(dA[0].rp, A0.rp, s);
+    upload(dA[0].ci, A0.ci, s);
+    upload(dA[0].va, A0.va, s);
+
+    struct EventPair {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~EventPair() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    AMG_CUDA_TRY(cudaEventCreate(&ev.a));
+    AMG_CUDA_TRY(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
+    double host_ms = 0.0, galerkin_ms = 0.0;
+    while (true) {
+        const int l = (int)c->hl.size() - 1;
+        HostLevel& cur = c->hl[l];
+        if (cur.A.n <= prm->coarsen_target || l >= prm->max_levels - 1) break;
+        double t0 = now_ms();
+        AggResult R = aggregate(cur.A, *prm);
+        host_ms += now_ms() - t0;
+        if (R.nc == 0 || (double)cur.A.n / (double)R.nc < prm->min_coarsen_rate) break;
+        t0 = now_ms();
+        cur.ncolours = greedy_colouring(cur.A, cur.colour);
+        host_ms += now_ms() - t0;
+        cur.agg = std::move(R);
+        HostCsr G;
+        DevCsr Gd;
+        AMG_CUDA_TRY(cudaEventRecord(e0, s));
+        galerkin_device(dA[l], cur.A, cur.agg, setup_mem, Gd, G, s);
+        AMG_CUDA_TRY(cudaEventRecord(e1, s));
+        AMG_CUDA_TRY(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        AMG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+        galerkin_ms += ms;
+        c->hl.emplace_back();
+        c->hl.back().A = std::move(G);
+        dA.push_back(Gd);
+    }
+    const int nlev = (int)c->hl.size();
+    c->nL = c->hl.back().A.n;
+    if (c->nL > prm->dense_cap)
+        throw Error{AMG_EINVAL, "coarsest level has " + std::to_string(c->nL) +
+                                    " rows, more than dense_cap = " + std::to_string(prm->dense_cap)};
+
+    // smoothing orders, bottom-up
+    const double t_dev0 = now_ms();
+    {
+        std::vector<int32_t>& pl = c->hl[nlev - 1].perm;
+        pl.resize(c->nL);
+        std::iota(pl.begin(), pl.end(), 0);
+        for (int l = nlev - 2; l >= 0; --l) c->hl[l].perm = smoothing_order(c->hl[l], c->hl[l + 1].perm);
+    }
+    c->dl.resize(nlev);
+    for (int l = 0; l < nlev; ++l) {
+        HostLevel& h = c->hl[l];
+        DevLevel& L = c->dl[l];
+        build_level_device(dA[l], h.A, h.perm, c->mem, L, s);
+        L.x = c->mem.alloc<double>(L.n);
+        L.b = c->mem.alloc<double>(L.n);
+        L.r = c->mem.alloc<double>(L.n);
+        if (l == nlev - 1) {
+            L.cptr = {0, L.n};
+            L.ncolours = 0;
+            continue;
+        }
+        L.ncolours = h.ncolours;
+        L.cptr.assign(h.ncolours + 1, 0);
+        L.cnnz.assign(h.ncolours, 0);
+        for (int32_t i = 0; i < L.n; ++i) {
+            ++L.cptr[h.colour[i] + 1];
+            L.cnnz[h.colour[i]] += h.A.rp[i + 1] - h.A.rp[i] - 1;
+        }
+        for (int col = 0; col < h.ncolours; ++col) L.cptr[col + 1] += L.cptr[col];
+        const std::vector<int32_t>& pn = c->hl[l + 1].perm;
+        const int32_t nc = h.agg.nc;
+        L.n_coarse = nc;
+        std::vector<int32_t> aggp(L.n, -1), rptr(nc + 1, 0), ridx;
+        for (int32_t i = 0; i < L.n; ++i) {
+            const int32_t a = h.agg.agg[i];
+            if (a < 0) continue;
+            aggp[h.perm[i]] = pn[a];
+            ++rptr[pn[a] + 1];
+        }
+        for (int32_t J = 0; J < nc; ++J) rptr[J + 1] += rptr[J];
+        ridx.resize(rptr[nc]);
+        {
+            std::vector<int32_t> fill(rptr.begin(), rptr.end() - 1);
+            for (int32_t r = 0; r < L.n; ++r)       // ascending position within each list
+                if (aggp[r] >= 0) ridx[fill[aggp[r]]++] = r;
+        }
+        L.agg = c->mem.alloc<int32_t>(L.n);
+        L.rptr = c->mem.alloc<int32_t>(nc + 1);
+        L.ridx = c->mem.alloc<int32_t>(ridx.size());
+        upload(L.agg, aggp, s);
+        upload(L.rptr, rptr, s);
+        upload(L.ridx, ridx, s);
+    }
+    // coarsest level: dense inverse
+    c->Ainv = c->mem.alloc<double>((size_t)c->nL * c->nL);
+    if (!dense_inverse_device(dA[nlev - 1], c->Ainv, s))
+        throw Error{AMG_ENOTSPD, "coarsest matrix is not positive definite"};
+
+    // level-0 CG state
+    const int32_t n = A0.n;
+    c->x = c->mem.alloc<double>(n);
+    c->r = c->mem.alloc<double>(n);
+    c->z = c->mem.alloc<double>(n);
+    c->zold = c->mem.alloc<double>(n);
+    c->pv = c->mem.alloc<double>(n);
+    c->q = c->mem.alloc<double>(n);
+    c->bb = c->mem.alloc<double>(n);
+    c->perm0 = c->mem.alloc<int32_t>(n);
+    upload(c->perm0, c->hl[0].perm, s);
+    {
+        std::vector<double> isq(n);
+        std::vector<int32_t> inv(n);
+        for (int32_t i = 0; i < n; ++i) inv[c->hl[0].perm[i]] = i;
+        std::vector<double> diag(n, 0.0);
+        for (int32_t i = 0; i < n; ++i)
+            for (int32_t k = A0.rp[i]; k < A0.rp[i + 1]; ++k)
+                if (A0.ci[k] == i) diag[i] = A0.va[k];
+        for (int32_t r = 0; r < n; ++r) isq[r] = 1.0 / std::sqrt(diag[inv[r]]);
+        c->isq0 = c->mem.alloc<double>(n);
+        upload(c->isq0, isq, s);
+    }
+    c->work.partials = c->mem.alloc<double>(g_reduction_blocks);
+    c->work.partials2 = c->mem.alloc<double>(g_reduction_blocks);
+    c->work.counters = c->mem.alloc<unsigned int>(16);
+    AMG_CUDA_TRY(cudaMemsetAsync(c->work.counters, 0, sizeof(unsigned int) * 16, s));
+    c->work.sc = c->mem.alloc<PcgScalars>(1);
+    c->norm_dev = c->mem.alloc<double>(1);
+    AMG_CUDA_TRY(cudaMallocHost(&c->sc_host, sizeof(PcgScalars)));
+    AMG_CUDA_TRY(cudaEventCreate(&c->ev0));
+    AMG_CUDA_TRY(cudaEventCreate(&c->ev1));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+
+    c->flexible = prm->flexible_cg >= 0 ? prm->flexible_cg : (prm->precision == AMG_FP32_IN_FP64);
+    c->precision = prm->precision;
+    if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
+    fill_info(c.get());
+    c->summary.host_setup_ms = host_ms;
+    c->summary.gpu_galerkin_ms = galerkin_ms;
+    c->summary.gpu_other_ms = now_ms() - t_dev0;
+    c->summary.total_setup_ms = now_ms() - t_start;
+    *out = c.release();
+}
+
+}  // namespace
+}  // namespace amg
+
+using namespace amg;
+
+extern "C" {
+
+int amg_params_default(amg_params* p, int32_t dim) {
+    if (!p || dim < 1 || dim > 3) {
+        t_last_error = "amg_params_default: null pointer or dim outside 1..3";
+        return AMG_EINVAL;
+    }
+    std::memset(p, 0, sizeof(*p));
+    p->delta = 1.0 / 3.0;
+    p->beta = 1e-5;
+    p->omega = 1.6;
+    p->s_min = 1 << dim;
+    p->s_max = 3 * (1 << (dim - 1));
+    p->d_max = dim;
+    p->coarsen_target = 1000;
+    p->max_levels = 20;
+    p->dense_cap = 4096;
+    p->min_coarsen_rate = 1.2;
+    p->precision = AMG_FP64;
+    p->flexible_cg = -1;
+    p->cuda_stream = nullptr;
+    return AMG_OK;
+}
+
+int amg_setup(const amg_csr* A, const amg_params* p, amg_ctx** out) {
+    if (out) *out = nullptr;
+    return Guard::run([&] { setup_impl(A, p, out); });
+}
+
+int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
+    return Guard::run([&] {
+        if (!c) throw Error{AMG_EINVAL, "null context"};
+        if (precision != AMG_FP64 && precision != AMG_FP32_IN_FP64)
+            throw Error{AMG_EINVAL, "precision must be AMG_FP64 or AMG_FP32_IN_FP64"};
+        if (precision == AMG_FP32_IN_FP64) ensure_fp32(c);
+        c->precision = precision;
+        c->flexible = flexible_cg >= 0 ? flexible_cg : (precision == AMG_FP32_IN_FP64);
+    });
+}
+
+int amg_vcycle(amg_ctx* c, const double* r_dev, double* z_dev) {
+    return Guard::run([&] {
+        if (!c || !r_dev || !z_dev) throw Error{AMG_EINVAL, "null argument"};
+        const int n = c->dl[0].n;
+        launch_scatter(n, c->perm0, r_dev, c->r, c->stream);
+        precondition(c, c->r, c->z);
+        launch_gather(n, c->perm0, c->z, z_dev, c->stream);
+        AMG_CUDA_TRY(cudaGetLastError());
+    });
+}
+
+static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int32_t maxit,
+                        amg_solve_info* info, bool host) {
+    int status = AMG_OK;
+    int rc = Guard::run([&] {
+        if (!c || !b || !x) throw Error{AMG_EINVAL, "null argument"};
+        if (!(tol >= 0.0) || maxit < 0) throw Error{AMG_EINVAL, "tol must be >= 0 and maxit >= 0"};
+        const int n = c->dl[0].n;
+        cudaStream_t s = c->stream;
+        AMG_CUDA_TRY(cudaEventRecord(c->ev0, s));
+        const double* bd = b;
+        double* xd = x;
+        if (host) {
+            // stage through the level-0 scratch vectors q (b) and z (x0)
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->q, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->z, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            bd = c->q;
+            xd = c->z;
+        }
+        launch_scatter(n, c->perm0, bd, c->bb, s);
+        launch_scatter(n, c->perm0, xd, c->x, s);
+        amg_solve_info local{};
+        status = pcg(c, tol, maxit, &local);
+        if (host) {
+            launch_gather(n, c->perm0, c->x, c->z, s);
+            AMG_CUDA_TRY(cudaMemcpyAsync(x, c->z, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+        } else {
+            launch_gather(n, c->perm0, c->x, x, s);
+        }
+        AMG_CUDA_TRY(cudaEventRecord(c->ev1, s));
+        AMG_CUDA_TRY(cudaEventSynchronize(c->ev1));
+        float ms = 0.f;
+        AMG_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        local.solve_ms = ms;
+        if (info) *info = local;
+        if (status != AMG_OK)
+            t_last_error = status == AMG_ENOTCONV ? "maximum iterations reached"
+                                                  : "p.Ap <= 0: operator or preconditioner not SPD";
+    });
+    if (rc != AMG_OK) return rc;
+    return status;
+}
+
+int amg_pcg_solve(amg_ctx* c, const double* b_dev, double* x_dev, double tol, int32_t maxit,
+                  amg_solve_info* info) {
+    return solve_common(c, b_dev, x_dev, tol, maxit, info, false);
+}
+
+int amg_pcg_solve_host(amg_ctx* c, const double* b_host, double* x_host, double tol,
+                       int32_t maxit, amg_solve_info* info) {
+    return solve_common(c, b_host, x_host, tol, maxit, info, true);
+}
+
+int amg_residual_norm(amg_ctx* c, const double* b_dev, const double* x_dev, double* out_norm) {
+    return Guard::run([&] {
+        if (!c || !b_dev || !x_dev || !out_norm) throw Error{AMG_EINVAL, "null argument"};
+        const int n = c->dl[0].n;
+        cudaStream_t s = c->stream;
+        launch_scatter(n, c->perm0, b_dev, c->q, s);
+        launch_scatter(n, c->perm0, x_dev, c->pv, s);
+        launch_cg_residual(c->dl[0], c->q, c->pv, nullptr, c->work, kStore, c->norm_dev, s);
+        double rr = 0.0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&rr, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        *out_norm = std::sqrt(rr);
+    });
+}
+
+int amg_hierarchy_info(const amg_ctx* c, amg_summary* summary, amg_level_info* levels, int32_t cap) {
+    if (!c || cap < 0 || (cap > 0 && !levels)) {
+        t_last_error = "amg_hierarchy_info: bad arguments";
+        return AMG_EINVAL;
+    }
+    if (summary) *summary = c->summary;
+    for (int32_t l = 0; l < cap && l < (int32_t)c->linfo.size(); ++l) levels[l] = c->linfo[l];
+    return (int)c->linfo.size();
+}
+
+int amg_export_level(const amg_ctx* c, int32_t l, int32_t* row_ptr, int32_t* col, double* val,
+                     int32_t* agg, int32_t* colour) {
+    if (!c || l < 0 || l >= (int32_t)c->hl.size()) {
+        t_last_error = "amg_export_level: level out of range";
+        return AMG_EINVAL;
+    }
+    const HostLevel& h = c->hl[l];
+    const bool last = l == (int32_t)c->hl.size() - 1;
+    if (last && (agg || colour)) {
+        t_last_error = "amg_export_level: the coarsest level has no aggregates or colours";
+        return AMG_EINVAL;
+    }
+    if (row_ptr) std::memcpy(row_ptr, h.A.rp.data(), sizeof(int32_t) * h.A.rp.size());
+    if (col) std::memcpy(col, h.A.ci.data(), sizeof(int32_t) * h.A.ci.size());
+    if (val) std::memcpy(val, h.A.va.data(), sizeof(double) * h.A.va.size());
+    if (agg) std::memcpy(agg, h.agg.agg.data(), sizeof(int32_t) * h.A.n);
+    if (colour) std::memcpy(colour, h.colour.data(), sizeof(int32_t) * h.A.n);
+    return AMG_OK;
+}
+
+static HostCsr host_copy(const amg_csr* A) {
+    if (!A || A->n <= 0 || A->nnz <= 0 || !A->row_ptr || !A->col || !A->val)
+        throw Error{AMG_EINVAL, "empty or null matrix"};
+    if (A->on_device) throw Error{AMG_EINVAL, "this entry point takes a host matrix"};
+    HostCsr H;
+    H.n = A->n;
+    H.rp.assign(A->row_ptr, A->row_ptr + A->n + 1);
+    if (H.rp[A->n] != A->nnz) throw Error{AMG_EINVAL, "row_ptr[n] != nnz"};
+    H.ci.assign(A->col, A->col + A->nnz);
+    H.va.assign(A->val, A->val + A->nnz);
+    std::string err;
+    if (!validate_csr(H, err)) throw Error{AMG_EINVAL, err};
+    return H;
+}
+
+int amg_aggregate(const amg_csr* A, const amg_params* p, int32_t* agg, int32_t* n_coarse) {
+    return Guard::run([&] {
+        if (!p || !agg || !n_coarse) throw Error{AMG_EINVAL, "null argument"};
+        check_params(*p);
+        HostCsr H = host_copy(A);
+        AggResult R = aggregate(H, *p);
+        std::memcpy(agg, R.agg.data(), sizeof(int32_t) * H.n);
+        *n_coarse = R.nc;
+    });
+}
+
+int amg_colour(const amg_csr* A, int32_t* colour, int32_t* ncolours) {
+    return Guard::run([&] {
+        if (!colour || !ncolours) throw Error{AMG_EINVAL, "null argument"};
+        HostCsr H = host_copy(A);
+        std::vector<int32_t> c;
+        *ncolours = greedy_colouring(H, c);
+        std::memcpy(colour, c.data(), sizeof(int32_t) * H.n);
+    });
+}
+
+int amg_profile_enable(amg_ctx* c, int32_t enable) {
+    return Guard::run([&] {
+        if (!c) throw Error{AMG_EINVAL, "null context"};
+        Profiler& P = c->prof;
+        if (enable) {
+            if (P.events.empty()) {
+                P.events.resize(1 << 16);
+                for (auto& e : P.events) AMG_CUDA_TRY(cudaEventCreate(&e));
+            }
+            AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            P.recs.clear();
+            P.next = 0;
+        }
+        P.on = enable != 0;
+    });
+}
+
+int amg_profile_read(amg_ctx* c, amg_kernel_stat* stats, int32_t cap) {
+    int count = 0;
+    int rc = Guard::run([&] {
+        if (!c || cap < 0 || (cap > 0 && !stats)) throw Error{AMG_EINVAL, "bad arguments"};
+        AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        std::vector<amg_kernel_stat> acc(kKNumKinds);
+        for (int k = 0; k < kKNumKinds; ++k) {
+            std::memset(&acc[k], 0, sizeof(amg_kernel_stat));
+            std::strncpy(acc[k].name, kKindNames[k], sizeof(acc[k].name) - 1);
+        }
+        for (const auto& r : c->prof.recs) {
+            float ms = 0.f;
+            AMG_CUDA_TRY(cudaEventElapsedTime(&ms, c->prof.events[r.ev], c->prof.events[r.ev + 1]));
+            acc[r.kind].launches += 1;
+            acc[r.kind].total_ms += ms;
+            acc[r.kind].bytes += r.bytes;
+        }
+        for (int k = 0; k < kKNumKinds; ++k)
+            if (acc[k].launches > 0) {
+                if (count < cap) stats[count] = acc[k];
+                ++count;
+            }
+    });
+    return rc == AMG_OK ? count : rc;
+}
+
+int amg_free(amg_ctx* c) {
+    if (!c) return AMG_OK;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    delete c;
+    return AMG_OK;
+}
+
+const char* amg_last_error(void) { return t_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,209 @@
+"""GPU parity tests: the CUDA path (through the C ABI) against the oracle on
+the same seeded inputs.
+
+Bars (from the method's accuracy targets):
+  * aggregate maps, colours and coarse sparsity patterns: bit-exact;
+    Galerkin values: bit-exact (sequential sums in fine CSR order on both sides);
+  * FP64 V-cycle output: max |z_gpu - z_oracle| <= 1e-12 max |z_oracle|;
+  * PCG: iteration counts within 1, solutions within 1e-9 relative at a
+    1e-10 relative residual;
+  * FP32-in-FP64: converges to the requested tolerance; its distance to the FP64
+    oracle solution is reported and bounded by the conditioning of the solve.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1209_0960_gb300 import amg
+from paper_1209_0960_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _oracle_params(prm, **kw):
+    d = dict(delta=prm.delta, beta=prm.beta, omega=prm.omega, s_min=prm.s_min,
+             s_max=prm.s_max, d_max=prm.d_max, coarsen_target=prm.coarsen_target,
+             max_levels=prm.max_levels, dense_cap=prm.dense_cap,
+             min_rate=prm.min_coarsen_rate)
+    d.update(kw)
+    return d
+
+
+CASES = {
+    "laplace2d_64": (lambda: P.laplace2d_random_rhs(64), {}),
+    "lognormal_28x24x20": (lambda: P.lognormal3d((28, 24, 20), seed=1), {}),
+    "layered_20x20x24": (lambda: P.layered3d((20, 20, 24), seed=3), {}),
+    "anisotropic_18": (lambda: P.anisotropic3d((18, 18, 18), seed=2), {}),
+    "lognormal_deep_16": (lambda: P.lognormal3d((16, 16, 16), seed=5), {"coarsen_target": 12}),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES))
+def pair(request):
+    maker, over = CASES[request.param]
+    p = maker()
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=p.dim, **over)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _oracle_params(solver.params))
+    yield p, solver, H
+    solver.close()
+
+
+def test_hierarchy_bit_exact(pair):
+    p, solver, H = pair
+    summary, levels = solver.info()
+    assert summary["num_levels"] == H.num_levels
+    for l in range(H.num_levels):
+        g = solver.level(l)
+        o = H.level(l)
+        assert g["n"] == o["n"] and g["nnz"] == o["nnz"]
+        assert np.array_equal(g["row_ptr"], o["row_ptr"])
+        assert np.array_equal(g["col"], o["col"])
+        # Galerkin values: identical bits
+        assert np.array_equal(g["val"].view(np.uint64), o["val"].view(np.uint64)), l
+        if l < H.num_levels - 1:
+            assert np.array_equal(g["agg"], o["agg"])
+            assert np.array_equal(g["colour"], o["colour"])
+            assert levels[l]["n_coarse"] == o["nc"]
+
+
+def test_vcycle_matches_oracle(pair):
+    p, solver, H = pair
+    rng = np.random.default_rng(42)
+    for r in (p.b, rng.standard_normal(p.n)):
+        z_or = H.vcycle(r)
+        z = solver.vcycle(torch.from_numpy(np.ascontiguousarray(r)).cuda())
+        torch.cuda.synchronize()
+        zg = z.cpu().numpy()
+        assert np.abs(zg - z_or).max() <= 1e-12 * np.abs(z_or).max()
+
+
+def test_pcg_matches_oracle(pair):
+    p, solver, H = pair
+    b = torch.from_numpy(p.b).cuda()
+    x, rc, info = solver.solve(b, tol=1e-10, maxit=300)
+    assert rc == amg.AMG_OK
+    xo, it_o, rel_o, trel_o = H.pcg(p.b, tol=1e-10, maxit=300)
+    assert it_o > 0
+    assert abs(info["iterations"] - it_o) <= 1
+    assert info["rel_residual"] <= 1e-10
+    assert info["true_rel_residual"] <= 1.5e-10
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    # the residual the library reports agrees with the oracle's own SpMV
+    r = p.b - O.spmv(p.row_ptr, p.col, p.val, xg)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(p.b)
+
+
+def test_pcg_nonzero_initial_guess_and_host_buffers(pair):
+    p, solver, H = pair
+    rng = np.random.default_rng(3)
+    x0 = rng.standard_normal(p.n)
+    xh = x0.copy()
+    rc, info = solver.solve_host(p.b, xh, tol=1e-10, maxit=300)
+    assert rc == amg.AMG_OK
+    xo, it_o, _, _ = H.pcg(p.b, tol=1e-10, maxit=300, x0=x0)
+    assert abs(info["iterations"] - it_o) <= 1
+    assert np.linalg.norm(xh - xo) <= 1e-9 * np.linalg.norm(xo)
+
+
+def test_fp32_in_fp64_converges_and_states_error(pair):
+    p, solver, H = pair
+    b = torch.from_numpy(p.b).cuda()
+    x64, rc64, i64 = solver.solve(b, tol=1e-8, maxit=300)
+    solver.set_precision(amg.AMG_FP32_IN_FP64)
+    try:
+        x32, rc32, i32 = solver.solve(b, tol=1e-8, maxit=300)
+    finally:
+        solver.set_precision(amg.AMG_FP64)
+    assert rc32 == amg.AMG_OK
+    assert i32["true_rel_residual"] <= 1.5e-8
+    assert i32["iterations"] <= i64["iterations"] + 5
+    xo, _, _, _ = H.pcg(p.b, tol=1e-12, maxit=300)
+    err32 = np.linalg.norm(x32.cpu().numpy() - xo) / np.linalg.norm(xo)
+    err64 = np.linalg.norm(x64.cpu().numpy() - xo) / np.linalg.norm(xo)
+    print(f"\n{p.name}: FP64 it={i64['iterations']} err={err64:.2e}; "
+          f"FP32-in-FP64 it={i32['iterations']} err={err32:.2e}")
+    # both stop at the same residual tolerance, so their forward errors are of
+    # the same order
+    assert err32 <= 20 * max(err64, 1e-12)
+
+
+def test_solves_are_deterministic(pair):
+    p, solver, H = pair
+    b = torch.from_numpy(p.b).cuda()
+    x1, _, i1 = solver.solve(b, tol=1e-8)
+    x2, _, i2 = solver.solve(b, tol=1e-8)
+    assert i1["iterations"] == i2["iterations"]
+    assert torch.equal(x1, x2)
+
+
+def test_gpu_vcycle_is_symmetric():
+    p = P.lognormal3d((12, 11, 10), seed=8)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, coarsen_target=30)
+    rng = np.random.default_rng(0)
+    u = torch.from_numpy(rng.standard_normal(p.n)).cuda()
+    v = torch.from_numpy(rng.standard_normal(p.n)).cuda()
+    Bu, Bv = solver.vcycle(u), solver.vcycle(v)
+    a, b = float(torch.dot(u, Bv)), float(torch.dot(Bu, v))
+    assert abs(a - b) <= 1e-12 * abs(a)
+    assert float(torch.dot(u, Bu)) > 0
+    solver.close()
+
+
+def test_single_level_is_direct_solve():
+    p = P.laplace2d_random_rhs(20)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=10_000)
+    s, levels = solver.info()
+    assert s["num_levels"] == 1
+    b = torch.from_numpy(p.b).cuda()
+    x, rc, info = solver.solve(b, tol=1e-12)
+    assert rc == amg.AMG_OK and info["iterations"] == 1
+    solver.close()
+
+
+def test_errors_are_reported_not_crashed():
+    p = P.laplace2d_random_rhs(40)
+    with pytest.raises(amg.AmgError) as e:
+        amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=10_000, dense_cap=100)
+    assert e.value.code == amg.AMG_EINVAL
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2)
+    b = torch.from_numpy(p.b).cuda()
+    x, rc, info = solver.solve(b, tol=1e-14, maxit=2)
+    assert rc == amg.AMG_ENOTCONV and info["iterations"] == 2
+    solver.close()
+
+
+# ---------------------------------------------------------------------------
+# the 128^3 log-normal workload at full size: properties that hold at any size
+# and sampled checks against the oracle's row-by-row SpMV
+# ---------------------------------------------------------------------------
+
+@pytest.mark.slow
+def test_full_size_lognormal_128():
+    p = P.lognormal3d((128, 128, 128), seed=0)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3)
+    summary, levels = solver.info()
+    assert 4 <= summary["num_levels"] <= 8
+    # level 0 aggregation: every row aggregated, coarsening rate, Galerkin row sums
+    l0 = solver.level(0)
+    agg = l0["agg"]
+    assert agg.min() >= 0 and agg.max() == levels[0]["n_coarse"] - 1
+    assert p.n / levels[0]["n_coarse"] > 4
+    l1 = solver.level(1)
+    rs0 = np.add.reduceat(p.val, p.row_ptr[:-1])
+    rs1 = np.add.reduceat(l1["val"], l1["row_ptr"][:-1])
+    agg_rs = np.bincount(agg, weights=rs0, minlength=levels[0]["n_coarse"])
+    assert np.allclose(rs1, agg_rs, rtol=1e-9, atol=1e-9 * np.abs(p.val).max())
+    b = torch.from_numpy(p.b).cuda()
+    for prec in (amg.AMG_FP64, amg.AMG_FP32_IN_FP64):
+        solver.set_precision(prec)
+        x, rc, info = solver.solve(b, tol=1e-8, maxit=300)
+        assert rc == amg.AMG_OK, info
+        xg = x.cpu().numpy()
+        r = p.b - O.spmv(p.row_ptr, p.col, p.val, xg)
+        assert np.linalg.norm(r) <= 1.05e-8 * np.linalg.norm(p.b)
+        assert abs(solver.residual_norm(b, x) - np.linalg.norm(r)) <= 1e-6 * np.linalg.norm(r)
+    solver.close()

@@ -1,0 +1,142 @@
+"""CPU tests of libamg: the C ABI loads and exports what include/amg.h
+declares, input validation, and bit-exact parity of the library's host setup
+(strength of connection, Algorithms 1-3, colouring) with the oracle."""
+
+import json
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import graph_from_spec, ROOT
+from oracle import oracle as O
+from paper_1209_0960_gb300 import amg
+from paper_1209_0960_gb300 import problems as P
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "amg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(amg_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = amg.lib(build_if_missing=True)
+    names = _declared_functions()
+    assert "amg_setup" in names and "amg_pcg_solve" in names
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in amg._SIGNATURES, f"binding lacks {name}"
+
+
+def test_params_default_and_errors():
+    p = amg.amg_params_default(3)
+    assert (p.s_min, p.s_max, p.d_max) == (8, 12, 3)
+    assert p.delta == pytest.approx(1 / 3) and p.omega == 1.6
+    p2 = amg.amg_params_default(2)
+    assert (p2.s_min, p2.s_max, p2.d_max) == (4, 6, 2)
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_params_default(4)
+    assert e.value.code == amg.AMG_EINVAL
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "missing_diag", "nonpositive_diag", "asym", "range"])
+def test_aggregate_rejects_malformed_csr(bad):
+    p = P.laplace2d_random_rhs(4)
+    rp, ci, va = p.row_ptr.copy(), p.col.copy(), p.val.copy()
+    if bad == "unsorted":
+        ci[rp[5]], ci[rp[5] + 1] = ci[rp[5] + 1], ci[rp[5]]
+    elif bad == "missing_diag":
+        k = [k for k in range(rp[3], rp[4]) if ci[k] == 3][0]
+        ci[k] = ci[k] + 0  # keep, then drop the entry below
+        keep = np.ones(len(ci), bool)
+        keep[k] = False
+        rp = rp.copy()
+        rp[4:] -= 1
+        ci, va = ci[keep], va[keep]
+    elif bad == "nonpositive_diag":
+        k = [k for k in range(rp[3], rp[4]) if ci[k] == 3][0]
+        va[k] = -1.0
+    elif bad == "asym":
+        # replace the (0, 1) entry by (0, 2): pattern loses symmetry
+        ci = ci.copy()
+        k = [k for k in range(rp[0], rp[1]) if ci[k] == 1][0]
+        ci[k] = 2
+    elif bad == "range":
+        ci[-1] = 10_000
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_aggregate(rp, ci, va, amg.amg_params_default(2))
+    assert e.value.code == amg.AMG_EINVAL
+    assert amg.amg_last_error() != ""
+
+
+with open(os.path.join(os.path.dirname(__file__), "golden", "aggregation_hand.json")) as f:
+    _HAND = json.load(f)["cases"]
+
+
+@pytest.mark.parametrize("case", _HAND, ids=[c["name"] for c in _HAND])
+def test_library_aggregation_hand_derived(case):
+    rp, ci, va = graph_from_spec(case["graph"])
+    prm = amg.amg_params_default(2)
+    for k, v in case["params"].items():
+        setattr(prm, k, v)
+    agg, nc = amg.amg_aggregate(rp, ci, va, prm)
+    assert nc == case["nc"] and agg.tolist() == case["agg"]
+
+
+def _oracle_params(prm):
+    return dict(delta=prm.delta, beta=prm.beta, omega=prm.omega, s_min=prm.s_min,
+                s_max=prm.s_max, d_max=prm.d_max, coarsen_target=prm.coarsen_target,
+                max_levels=prm.max_levels, dense_cap=prm.dense_cap,
+                min_rate=prm.min_coarsen_rate)
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: P.laplace2d_random_rhs(64),
+    lambda: P.lognormal3d((24, 20, 17), seed=11),
+    lambda: P.lognormal3d((16, 16, 16), variance=6.0, corr_len=0.02, seed=3),
+    lambda: P.layered3d((18, 18, 22), seed=4),
+    lambda: P.anisotropic3d((14, 15, 16), seed=2),
+    lambda: P.serving_request(7) if False else P.lognormal3d((19, 23, 17), variance=1.0, corr_len=0.1, seed=7),
+], ids=["laplace2d", "lognormal", "lognormal_rough", "layered", "anisotropic", "box"])
+def test_library_host_setup_matches_oracle_bit_exactly(maker):
+    p = maker()
+    prm = amg.amg_params_default(p.dim)
+    agg1, n1 = amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
+    agg2, n2 = O.aggregate(p.row_ptr, p.col, p.val, _oracle_params(prm))
+    assert n1 == n2
+    assert np.array_equal(agg1, agg2)
+    c1, k1 = amg.amg_colour(p.row_ptr, p.col, p.val)
+    c2, k2 = O.colour(p.row_ptr, p.col)
+    assert k1 == k2 and np.array_equal(c1, c2)
+
+
+def test_library_host_setup_matches_oracle_on_coarse_levels():
+    # the oracle's coarse matrices exercise denser rows, isolated vertices and
+    # irregular graphs
+    p = P.layered3d((20, 20, 20), seed=9)
+    prm = amg.amg_params_default(3)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, dict(_oracle_params(prm), coarsen_target=20))
+    assert H.num_levels >= 3
+    for l in range(H.num_levels - 1):
+        L = H.level(l)
+        agg, nc = amg.amg_aggregate(L["row_ptr"], L["col"], L["val"], prm)
+        assert nc == L["nc"] and np.array_equal(agg, L["agg"]), l
+        col, k = amg.amg_colour(L["row_ptr"], L["col"], L["val"])
+        assert k == L["ncolours"] and np.array_equal(col, L["colour"])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_library_aggregation_matches_oracle_with_isolated_vertices(seed):
+    # strong random contrast: beta raised so that many vertices are isolated
+    rng = np.random.default_rng(seed)
+    K = np.exp(rng.normal(0.0, 4.0, size=(12, 11, 10)))
+    rp, ci, va, b = P.assemble_fv(K, bc=[(1.0, 0.0), (None, None), (None, None)])
+    prm = amg.amg_params_default(3)
+    prm.beta = 0.02
+    _, iso, _, _ = O.strength(rp, ci, va, _oracle_params(prm))
+    assert iso.sum() > 20
+    agg1, n1 = amg.amg_aggregate(rp, ci, va, prm)
+    agg2, n2 = O.aggregate(rp, ci, va, _oracle_params(prm))
+    assert n1 == n2 and np.array_equal(agg1, agg2)
