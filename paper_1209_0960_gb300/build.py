@@ -72,7 +72,7 @@ def build(force: bool = False, verbose: bool = False, extra_nvcc=None) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
         logs = list(ex.map(_run, jobs))
     tmp = LIB + f".tmp{os.getpid()}"
-    logs.append(_run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]))
+    logs.append(_run([nvcc, *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]))
     os.replace(tmp, LIB)
     if verbose:
         sys.stdout.write("".join(logs))

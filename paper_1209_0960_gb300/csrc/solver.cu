@@ -505,8 +505,9 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     if (!dense_inverse_device(dA[nlev - 1], c->Ainv, s))
         throw Error{AMG_ENOTSPD, "coarsest matrix is not positive definite"};
 
-    // level-0 CG state
-    const int32_t n = A0.n;
+    // level-0 CG state (c->hl has grown: take the level-0 matrix afresh)
+    const HostCsr& A0f = c->hl[0].A;
+    const int32_t n = A0f.n;
     c->x = c->mem.alloc<double>(n);
     c->r = c->mem.alloc<double>(n);
     c->z = c->mem.alloc<double>(n);
@@ -522,8 +523,8 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         for (int32_t i = 0; i < n; ++i) inv[c->hl[0].perm[i]] = i;
         std::vector<double> diag(n, 0.0);
         for (int32_t i = 0; i < n; ++i)
-            for (int32_t k = A0.rp[i]; k < A0.rp[i + 1]; ++k)
-                if (A0.ci[k] == i) diag[i] = A0.va[k];
+            for (int32_t k = A0f.rp[i]; k < A0f.rp[i + 1]; ++k)
+                if (A0f.ci[k] == i) diag[i] = A0f.va[k];
         for (int32_t r = 0; r < n; ++r) isq[r] = 1.0 / std::sqrt(diag[inv[r]]);
         c->isq0 = c->mem.alloc<double>(n);
         upload(c->isq0, isq, s);
