@@ -86,29 +86,36 @@ struct PcgScalars {
 };
 
 // One level of the hierarchy on the device.  Rows are stored in the level's
-// smoothing order: grouped by colour, inside a colour by coarse index, then by
-// original index.  The off-diagonal part is CSR, the diagonal separate.
+// smoothing order: grouped by colour, inside a colour by coarse aggregate,
+// then by original index.  The off-diagonal part is kept in a sliced-ELL
+// layout with 32-row slices (SELL-32): the k-th off-diagonal entry of the rows
+// of slice s sits at sptr[s] + 32 k + (row mod 32), so a warp reading entry k
+// of its 32 rows reads 32 consecutive values.  Slices are padded to their
+// longest row (padding: column = the row itself, value 0); rlen holds the true
+// row lengths so the padding costs no arithmetic.  The diagonal is separate.
 struct DevLevel {
     int32_t n = 0;
-    int32_t nnz_off = 0;
+    int64_t nnz_off = 0;              // true off-diagonal entries
+    int64_t padded = 0;               // entries of the padded SELL arrays
     int32_t ncolours = 0;
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
-    int32_t lpr = 8;                  // lanes per row of the row kernels
-    int32_t* rp = nullptr;            // [n+1] off-diagonal row pointers
-    int32_t* ci = nullptr;            // [nnz_off] permuted column indices
-    double* va = nullptr;             // [nnz_off]
+    int64_t* sptr = nullptr;          // [n/32 + 1] slice starts
+    uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
+    int32_t* scol = nullptr;          // [padded] permuted column indices
+    double* sval = nullptr;           // [padded]
     double* diag = nullptr;           // [n]
     double* dinv = nullptr;           // [n] 1 / A_ii
+    int32_t* cptr_dev = nullptr;      // device copy of cptr
     int32_t* agg = nullptr;           // [n] permuted coarse index or -1
     int32_t* rptr = nullptr;          // [n_coarse+1] restriction lists
-    int32_t* ridx = nullptr;          // fine rows of each coarse row
+    int32_t* ridx = nullptr;          // fine rows of colour >= 1 of each coarse row
     double* x = nullptr;              // level correction
     double* b = nullptr;              // level right-hand side
     double* r = nullptr;              // level residual
     // float32 copies, symmetric diagonal scaling S^-1 A S^-1 with S = diag(sqrt(A_ii))
-    float* va32 = nullptr;
+    float* sval32 = nullptr;
     float* dinv32 = nullptr;
     float* diag32 = nullptr;
     float* t32 = nullptr;             // s_fine[i] / s_coarse[agg[i]] for the transfers
@@ -116,6 +123,50 @@ struct DevLevel {
     float* b32 = nullptr;
     float* r32 = nullptr;
 };
+
+// Grid-wide barrier state of the persistent coarse-cycle kernel.
+struct GridBarrier {
+    unsigned int count;
+    unsigned int gen;
+    int err;
+    int pad;
+};
+
+// Level view used by the persistent coarse-cycle kernel (device resident).
+template <typename T>
+struct CoarseLevel {
+    int n, ncolours, n_coarse;
+    const int32_t* cptr;
+    const int64_t* sptr;
+    const uint16_t* rlen;
+    const int32_t* scol;
+    const T* sval;
+    const T* dinv;
+    const T* diag;
+    const int32_t* agg;
+    const int32_t* rptr;
+    const int32_t* ridx;
+    const T* t;
+    T* x;
+    T* b;
+};
+
+// Levels lf..lc (lc = coarsest) run inside one cooperative launch.
+struct CoarseCycle {
+    int lf = -1;                      // first level of the persistent kernel, -1 = none
+    int lc = 0;
+    int nL = 0;
+    int blocks = 0;
+    CoarseLevel<double>* lv64 = nullptr;   // device array indexed by level
+    CoarseLevel<float>* lv32 = nullptr;
+    GridBarrier* barrier = nullptr;
+};
+
+int coarse_cycle_blocks(int sms);
+void launch_coarse_cycle64(const CoarseCycle& cc, const double* Minv, double omega, PcgScalars* sc,
+                           cudaStream_t s);
+void launch_coarse_cycle32(const CoarseCycle& cc, const double* Minv, double omega, PcgScalars* sc,
+                           cudaStream_t s);
 
 // Launch profiler: events around launches, grouped by kernel class.
 struct Profiler {
@@ -128,7 +179,7 @@ struct Profiler {
 
 enum KernelKind : int {
     kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
-    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKNumKinds
+    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKCoarseCycle, kKNumKinds
 };
 
 struct HostLevel {
@@ -172,8 +223,14 @@ int reduction_blocks(int64_t work_threads);
 
 void launch_gs(const DevLevel& L, int r0, int r1, const double* b, double* x, cudaStream_t s);
 void launch_gs32(const DevLevel& L, int r0, int r1, const float* b, float* x, cudaStream_t s);
-void launch_residual(const DevLevel& L, const double* b, const double* x, double* r, cudaStream_t s);
-void launch_residual32(const DevLevel& L, const float* b, const float* x, float* r, cudaStream_t s);
+// first pre-smoothing pass from x = 0: x = b / A_ii on colour 0, 0 elsewhere
+void launch_gs_first(const DevLevel& L, const double* b, double* x, cudaStream_t s);
+void launch_gs_first32(const DevLevel& L, const float* b, float* x, cudaStream_t s);
+// r = b - A x on rows [r0, n)
+void launch_residual(const DevLevel& L, int r0, const double* b, const double* x, double* r,
+                     cudaStream_t s);
+void launch_residual32(const DevLevel& L, int r0, const float* b, const float* x, float* r,
+                       cudaStream_t s);
 void launch_restrict(const DevLevel& L, const double* r, double* bc, cudaStream_t s);
 void launch_restrict32(const DevLevel& L, const float* r, float* bc, cudaStream_t s);
 void launch_prolong(const DevLevel& L, const double* e, double* x, double omega, cudaStream_t s);
@@ -235,11 +292,19 @@ void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, c
 struct amg_ctx {
     amg_params p;
     int device = 0;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;        // the context's own stream (all library work)
+    cudaStream_t user_stream = nullptr;   // params.cuda_stream, ordered against `stream`
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // CUDA graphs of one CG iteration, [precision][flexible]: A = q = A p,
+    // alpha, x/r update, status copy; B = z = B r, beta, p update
+    cudaGraphExec_t graph_a[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t graph_b[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    bool use_graphs = true;
     amg::DevArena mem;
     std::vector<amg::HostLevel> hl;
     std::vector<amg::DevLevel> dl;
     int32_t nL = 0;                   // coarsest size
+    amg::CoarseCycle cc;              // persistent kernel for the small levels
     double* Ainv = nullptr;           // [nL x nL] inverse of the coarsest matrix
     double* Ainv_s = nullptr;         // [nL x nL] inverse of the scaled coarsest matrix
     double* isq0 = nullptr;           // [n] 1 / sqrt(A_ii) of level 0 (FP32 entry/exit)
@@ -266,5 +331,16 @@ struct amg_ctx {
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : prof.events) cudaEventDestroy(e);
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b) {
+                if (graph_a[a][b]) cudaGraphExecDestroy(graph_a[a][b]);
+                if (graph_b[a][b]) cudaGraphExecDestroy(graph_b[a][b]);
+            }
+        if (ev_in) cudaEventDestroy(ev_in);
+        if (ev_out) cudaEventDestroy(ev_out);
+        if (stream) {
+            cudaStreamSynchronize(stream);
+            cudaStreamDestroy(stream);
+        }
     }
 };

@@ -4,10 +4,13 @@
 // Sec. 5 Krylov iteration).
 //
 // Layout: every level stores its rows in the smoothing order (colour blocks,
-// then coarse index, then original index), the off-diagonal part as CSR with
-// int32 indices and the diagonal separately.  Row kernels assign LPR lanes to
-// a row so consecutive lanes read consecutive CSR entries (coalesced), and
-// reduce the row sum with warp shuffles.  All reductions are deterministic:
+// then coarse aggregate, then original index), the off-diagonal part in the
+// SELL-32 layout described in device.h and the diagonal separately.  Row
+// kernels give one thread to a row: for each k the 32 threads of a warp read
+// entry k of their 32 rows from 32 consecutive addresses, and the row sum is a
+// chain of fused multiply-adds with no cross-lane reduction (GB300 executes
+// float64 at 1/64 of the float32 rate, so the float64 path keeps the
+// arithmetic at one FMA per stored entry).  All reductions are deterministic:
 // per-block partial sums in a fixed grid, combined in a fixed order by the
 // last block to finish.
 
@@ -20,25 +23,28 @@ namespace {
 // ---------------------------------------------------------------------------
 // helpers
 // ---------------------------------------------------------------------------
-template <int LPR, typename T>
+template <int W, typename T>
 __device__ __forceinline__ T group_sum(T s) {
 #pragma unroll
-    for (int off = LPR / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, LPR);
+    for (int off = W / 2; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off, W);
     return s;
 }
 
-// sum_k va[k] x[ci[k]] over the off-diagonal entries of `row`, split over the
-// LPR lanes of a group (lane-strided); every lane returns the full sum.
-template <int LPR, typename T, typename X>
-__device__ __forceinline__ T row_sum(const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                                     const T* __restrict__ va, const X* x, int row, bool valid,
-                                     int lane) {
-    T s = T(0);
-    if (valid) {
-        const int k1 = rp[row + 1];
-        for (int k = rp[row] + lane; k < k1; k += LPR) s += va[k] * T(x[ci[k]]);
+__device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+
+// acc + sgn * sum_k A_row,k x_col(k) over the stored off-diagonal entries of a
+// SELL-32 row (base = slice start + row mod 32)
+template <bool NEG, typename T, typename X>
+__device__ __forceinline__ T sell_row(int64_t base, int len, const int32_t* __restrict__ scol,
+                                      const T* __restrict__ sval, const X* x, T acc) {
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
+        const int64_t e = base + 32 * (int64_t)k;
+        const T a = sval[e];
+        acc = fmad(NEG ? -a : a, T(x[scol[e]]), acc);
     }
-    return group_sum<LPR>(s);
+    return acc;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -128,36 +134,53 @@ __device__ void finish_reduction(double v0, double v1, double* partials, double*
 
 // One Gauss-Seidel update of rows [r0, r1) of one colour:
 //   x_i = (b_i - sum_{j != i} A_ij x_j) / A_ii.
-// Rows of one colour are not coupled, so they update in parallel.
-template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_gs(int r0, int r1, const int32_t* __restrict__ rp,
-                                               const int32_t* __restrict__ ci,
-                                               const T* __restrict__ va, const T* __restrict__ dinv,
+// Rows of one colour are not coupled, so they update in parallel.  Threads
+// start at the slice boundary below r0 so warps read whole slices.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs(int r0, int r1, const int64_t* __restrict__ sptr,
+                                               const uint16_t* __restrict__ rlen,
+                                               const int32_t* __restrict__ scol,
+                                               const T* __restrict__ sval,
+                                               const T* __restrict__ dinv,
                                                const T* __restrict__ b, T* x) {
-    const int lane = threadIdx.x & (LPR - 1);
-    const int row = r0 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR);
-    const bool valid = row < r1;
-    const T s = row_sum<LPR>(rp, ci, va, x, row, valid, lane);
-    if (valid && lane == 0) x[row] = (b[row] - s) * dinv[row];
+    const int row = (r0 & ~31) + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (row < r0 || row >= r1) return;
+    const int64_t base = sptr[row >> 5] + (row & 31);
+    const T s = sell_row<true>(base, rlen[row], scol, sval, x, b[row]);
+    x[row] = s * dinv[row];
 }
 
-// r = b - A x for all rows
-template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_residual(int n, const int32_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ ci,
-                                                     const T* __restrict__ va,
+// First Gauss-Seidel pass from a zero initial guess: the rows of colour 0
+// [0, c1) have only zero neighbours, so x_i = b_i / A_ii there, and every other
+// row starts at 0 (no matrix entries are read).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_first(int c1, int n, const T* __restrict__ dinv,
+                                                     const T* __restrict__ b, T* __restrict__ x) {
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    x[row] = row < c1 ? b[row] * dinv[row] : T(0);
+}
+
+// r = b - A x for rows [r0, n)
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_t* __restrict__ sptr,
+                                                     const uint16_t* __restrict__ rlen,
+                                                     const int32_t* __restrict__ scol,
+                                                     const T* __restrict__ sval,
                                                      const T* __restrict__ diag,
                                                      const T* __restrict__ b,
                                                      const T* __restrict__ x, T* __restrict__ r) {
-    const int lane = threadIdx.x & (LPR - 1);
-    const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / LPR);
-    const bool valid = row < n;
-    const T s = row_sum<LPR>(rp, ci, va, x, row, valid, lane);
-    if (valid && lane == 0) r[row] = b[row] - diag[row] * x[row] - s;
+    const int row = (r0 & ~31) + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (row < r0 || row >= n) return;
+    const int64_t base = sptr[row >> 5] + (row & 31);
+    const T s0 = fmad(-diag[row], x[row], b[row]);
+    r[row] = sell_row<true>(base, rlen[row], scol, sval, x, s0);
 }
 
 // coarse right-hand side: bc_J = sum over the fine rows i of aggregate J of
-// (t_i) r_i, summed in the stored order (Eq. prolongation: R = P^T)
+// (t_i) r_i, summed in the stored order (Eq. prolongation: R = P^T).  The lists
+// hold the rows of colour >= 1 only: the pre-smoother's last pass updates
+// colour 0, whose residual is therefore zero.
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __restrict__ rptr,
                                                      const int32_t* __restrict__ ridx,
@@ -165,24 +188,24 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __re
                                                      const T* __restrict__ r, T* __restrict__ bc) {
     const int J = blockIdx.x * blockDim.x + threadIdx.x;
     if (J >= nc) return;
-    const int k0 = rptr[J], k1 = rptr[J + 1];
-    int i = ridx[k0];
-    T s = SCALED ? t[i] * r[i] : r[i];
-    for (int k = k0 + 1; k < k1; ++k) {
-        i = ridx[k];
-        s += SCALED ? t[i] * r[i] : r[i];
+    T s = T(0);
+    for (int k = rptr[J]; k < rptr[J + 1]; ++k) {
+        const int i = ridx[k];
+        s = SCALED ? fmad(t[i], r[i], s) : s + r[i];
     }
     bc[J] = s;
 }
 
 // x_i += omega (t_i) e_{agg(i)}: piecewise-constant prolongation with the
-// over-correction factor omega
+// over-correction factor omega, on rows [r0, n).  The caller passes r0 = the
+// first row of colour 1: the post-smoother's first pass recomputes colour 0
+// without reading its old values.
 template <typename T, bool SCALED>
-__global__ void __launch_bounds__(kBlock) k_prolong(int n, const int32_t* __restrict__ agg,
+__global__ void __launch_bounds__(kBlock) k_prolong(int r0, int n, const int32_t* __restrict__ agg,
                                                     const T* __restrict__ t,
                                                     const T* __restrict__ e, T* __restrict__ x,
                                                     T omega) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = r0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= n) return;
     const int a = agg[i];
     if (a < 0) return;
@@ -235,11 +258,11 @@ __global__ void k_from_scaled32(int n, const float* __restrict__ zhat, const dou
 // CG kernels (level 0, float64, smoothing order)
 // ---------------------------------------------------------------------------
 
-// r = b - A x and ||r||^2 (grid-stride over row groups)
-template <int LPR>
-__global__ void __launch_bounds__(kBlock) k_cg_residual(int n, const int32_t* __restrict__ rp,
-                                                        const int32_t* __restrict__ ci,
-                                                        const double* __restrict__ va,
+// r = b - A x and ||r||^2 (grid-stride over rows)
+__global__ void __launch_bounds__(kBlock) k_cg_residual(int n, const int64_t* __restrict__ sptr,
+                                                        const uint16_t* __restrict__ rlen,
+                                                        const int32_t* __restrict__ scol,
+                                                        const double* __restrict__ sval,
                                                         const double* __restrict__ diag,
                                                         const double* __restrict__ b,
                                                         const double* __restrict__ x,
@@ -247,46 +270,35 @@ __global__ void __launch_bounds__(kBlock) k_cg_residual(int n, const int32_t* __
                                                         unsigned int* counter, PcgScalars* sc,
                                                         double* out, int mode) {
     __shared__ double sh[kBlock / 32];
-    const int lane = threadIdx.x & (LPR - 1);
-    const int gpb = kBlock / LPR;
     double acc = 0.0;
-    for (int base = blockIdx.x * gpb; base < n; base += gridDim.x * gpb) {
-        const int row = base + threadIdx.x / LPR;
-        const bool valid = row < n;
-        const double s = row_sum<LPR>(rp, ci, va, x, row, valid, lane);
-        if (valid && lane == 0) {
-            const double v = b[row] - diag[row] * x[row] - s;
-            if (r) r[row] = v;
-            acc += v * v;
-        }
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        const int64_t base = sptr[row >> 5] + (row & 31);
+        const double s0 = fmad(-diag[row], x[row], b[row]);
+        const double v = sell_row<true>(base, rlen[row], scol, sval, x, s0);
+        if (r) r[row] = v;
+        acc = fmad(v, v, acc);
     }
     const double t = block_sum(acc, sh);
     finish_reduction(t, 0.0, partials, nullptr, counter, sc, out, mode, sh);
 }
 
 // q = A p and p.q -> alpha
-template <int LPR>
-__global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, const int32_t* __restrict__ rp,
-                                                       const int32_t* __restrict__ ci,
-                                                       const double* __restrict__ va,
+__global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, const int64_t* __restrict__ sptr,
+                                                       const uint16_t* __restrict__ rlen,
+                                                       const int32_t* __restrict__ scol,
+                                                       const double* __restrict__ sval,
                                                        const double* __restrict__ diag,
                                                        const double* __restrict__ p,
                                                        double* __restrict__ q, double* partials,
                                                        unsigned int* counter, PcgScalars* sc) {
     __shared__ double sh[kBlock / 32];
-    const int lane = threadIdx.x & (LPR - 1);
-    const int gpb = kBlock / LPR;
     double acc = 0.0;
-    for (int base = blockIdx.x * gpb; base < n; base += gridDim.x * gpb) {
-        const int row = base + threadIdx.x / LPR;
-        const bool valid = row < n;
-        const double s = row_sum<LPR>(rp, ci, va, p, row, valid, lane);
-        if (valid && lane == 0) {
-            const double pi = p[row];
-            const double v = diag[row] * pi + s;
-            q[row] = v;
-            acc += pi * v;
-        }
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        const int64_t base = sptr[row >> 5] + (row & 31);
+        const double pi = p[row];
+        const double v = sell_row<false>(base, rlen[row], scol, sval, p, diag[row] * pi);
+        q[row] = v;
+        acc = fmad(pi, v, acc);
     }
     const double t = block_sum(acc, sh);
     finish_reduction(t, 0.0, partials, nullptr, counter, sc, nullptr, kPQ, sh);
@@ -306,7 +318,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, double* __restrict_
         x[i] += alpha * p[i];
         const double v = r[i] - alpha * q[i];
         r[i] = v;
-        acc += v * v;
+        acc = fmad(v, v, acc);
     }
     const double t = block_sum(acc, sh);
     finish_reduction(t, 0.0, partials, nullptr, counter, sc, nullptr, kRR, sh);
@@ -360,41 +372,32 @@ int reduction_blocks(int64_t work_threads) {
     return (int)std::min<int64_t>(b, g_reduction_blocks);
 }
 
-#define AMG_LPR_DISPATCH(lpr, KERNEL_CALL)              \
-    switch (lpr) {                                      \
-        case 2: { constexpr int LPR = 2; KERNEL_CALL; } break;   \
-        case 4: { constexpr int LPR = 4; KERNEL_CALL; } break;   \
-        case 8: { constexpr int LPR = 8; KERNEL_CALL; } break;   \
-        case 16: { constexpr int LPR = 16; KERNEL_CALL; } break; \
-        default: { constexpr int LPR = 32; KERNEL_CALL; } break; \
-    }
+inline int row_blocks(int r0, int r1) { return blocks_for((int64_t)(r1 - (r0 & ~31))); }
 
 void launch_gs(const DevLevel& L, int r0, int r1, const double* b, double* x, cudaStream_t s) {
     if (r1 <= r0) return;
-    const int grid = blocks_for((int64_t)(r1 - r0) * L.lpr);
-    AMG_LPR_DISPATCH(L.lpr, (k_gs<LPR, double><<<grid, kBlock, 0, s>>>(r0, r1, L.rp, L.ci, L.va,
-                                                                       L.dinv, b, x)));
+    k_gs<double><<<row_blocks(r0, r1), kBlock, 0, s>>>(r0, r1, L.sptr, L.rlen, L.scol, L.sval,
+                                                       L.dinv, b, x);
 }
 
 void launch_gs32(const DevLevel& L, int r0, int r1, const float* b, float* x, cudaStream_t s) {
     if (r1 <= r0) return;
-    const int grid = blocks_for((int64_t)(r1 - r0) * L.lpr);
-    AMG_LPR_DISPATCH(L.lpr, (k_gs<LPR, float><<<grid, kBlock, 0, s>>>(r0, r1, L.rp, L.ci, L.va32,
-                                                                      L.dinv32, b, x)));
+    k_gs<float><<<row_blocks(r0, r1), kBlock, 0, s>>>(r0, r1, L.sptr, L.rlen, L.scol, L.sval32,
+                                                      L.dinv32, b, x);
 }
 
-void launch_residual(const DevLevel& L, const double* b, const double* x, double* r,
+void launch_residual(const DevLevel& L, int r0, const double* b, const double* x, double* r,
                      cudaStream_t s) {
-    const int grid = blocks_for((int64_t)L.n * L.lpr);
-    AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, double><<<grid, kBlock, 0, s>>>(
-                                L.n, L.rp, L.ci, L.va, L.diag, b, x, r)));
+    if (L.n <= r0) return;
+    k_residual<double><<<row_blocks(r0, L.n), kBlock, 0, s>>>(r0, L.n, L.sptr, L.rlen, L.scol,
+                                                              L.sval, L.diag, b, x, r);
 }
 
-void launch_residual32(const DevLevel& L, const float* b, const float* x, float* r,
+void launch_residual32(const DevLevel& L, int r0, const float* b, const float* x, float* r,
                        cudaStream_t s) {
-    const int grid = blocks_for((int64_t)L.n * L.lpr);
-    AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, float><<<grid, kBlock, 0, s>>>(
-                                L.n, L.rp, L.ci, L.va32, L.diag32, b, x, r)));
+    if (L.n <= r0) return;
+    k_residual<float><<<row_blocks(r0, L.n), kBlock, 0, s>>>(r0, L.n, L.sptr, L.rlen, L.scol,
+                                                             L.sval32, L.diag32, b, x, r);
 }
 
 void launch_restrict(const DevLevel& L, const double* r, double* bc, cudaStream_t s) {
@@ -408,11 +411,25 @@ void launch_restrict32(const DevLevel& L, const float* r, float* bc, cudaStream_
 }
 
 void launch_prolong(const DevLevel& L, const double* e, double* x, double omega, cudaStream_t s) {
-    k_prolong<double, false><<<blocks_for(L.n), kBlock, 0, s>>>(L.n, L.agg, nullptr, e, x, omega);
+    const int r0 = L.cptr[1];
+    if (L.n <= r0) return;
+    k_prolong<double, false><<<blocks_for(L.n - r0), kBlock, 0, s>>>(r0, L.n, L.agg, nullptr, e, x,
+                                                                     omega);
 }
 
 void launch_prolong32(const DevLevel& L, const float* e, float* x, float omega, cudaStream_t s) {
-    k_prolong<float, true><<<blocks_for(L.n), kBlock, 0, s>>>(L.n, L.agg, L.t32, e, x, omega);
+    const int r0 = L.cptr[1];
+    if (L.n <= r0) return;
+    k_prolong<float, true><<<blocks_for(L.n - r0), kBlock, 0, s>>>(r0, L.n, L.agg, L.t32, e, x,
+                                                                   omega);
+}
+
+void launch_gs_first(const DevLevel& L, const double* b, double* x, cudaStream_t s) {
+    k_gs_first<double><<<blocks_for(L.n), kBlock, 0, s>>>(L.cptr[1], L.n, L.dinv, b, x);
+}
+
+void launch_gs_first32(const DevLevel& L, const float* b, float* x, cudaStream_t s) {
+    k_gs_first<float><<<blocks_for(L.n), kBlock, 0, s>>>(L.cptr[1], L.n, L.dinv32, b, x);
 }
 
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s) {
@@ -441,17 +458,15 @@ void launch_from_scaled32(int n, const float* zhat, const double* isq, double* z
 
 void launch_cg_residual(const DevLevel& L, const double* b, const double* x, double* r,
                         CgWork& w, int mode, double* out, cudaStream_t s) {
-    const int grid = reduction_blocks((int64_t)L.n * L.lpr);
-    AMG_LPR_DISPATCH(L.lpr, (k_cg_residual<LPR><<<grid, kBlock, 0, s>>>(
-                                L.n, L.rp, L.ci, L.va, L.diag, b, x, r, w.partials, w.counters,
-                                w.sc, out, mode)));
+    k_cg_residual<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sptr, L.rlen, L.scol, L.sval,
+                                                           L.diag, b, x, r, w.partials,
+                                                           w.counters, w.sc, out, mode);
 }
 
 void launch_cg_spmv_pq(const DevLevel& L, const double* p, double* q, CgWork& w, cudaStream_t s) {
-    const int grid = reduction_blocks((int64_t)L.n * L.lpr);
-    AMG_LPR_DISPATCH(L.lpr, (k_cg_spmv_pq<LPR><<<grid, kBlock, 0, s>>>(
-                                L.n, L.rp, L.ci, L.va, L.diag, p, q, w.partials, w.counters + 1,
-                                w.sc)));
+    k_cg_spmv_pq<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sptr, L.rlen, L.scol, L.sval,
+                                                          L.diag, p, q, w.partials,
+                                                          w.counters + 1, w.sc);
 }
 
 void launch_cg_update(int n, double* x, double* r, const double* p, const double* q, CgWork& w,

@@ -109,6 +109,29 @@ __global__ void k_reorder_rows(int n, const int32_t* __restrict__ inv, const int
     dinv[r] = 1.0 / d;
 }
 
+// Scatter the off-diagonal CSR rows into the SELL-32 arrays; padding entries
+// point at the row itself with value 0.
+__global__ void k_csr_to_sell(int n, const int32_t* __restrict__ nrp, const int32_t* __restrict__ nci,
+                              const double* __restrict__ nva, const int64_t* __restrict__ sptr,
+                              int32_t* __restrict__ scol, double* __restrict__ sval) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t s0 = sptr[r >> 5], s1 = sptr[(r >> 5) + 1];
+    const int width = (int)((s1 - s0) >> 5);
+    const int64_t base = s0 + (r & 31);
+    const int k0 = nrp[r], len = nrp[r + 1] - k0;
+    for (int k = 0; k < width; ++k) {
+        const int64_t e = base + 32 * (int64_t)k;
+        if (k < len) {
+            scol[e] = nci[k0 + k];
+            sval[e] = nva[k0 + k];
+        } else {
+            scol[e] = r;
+            sval[e] = 0.0;
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // coarsest level: dense Cholesky factor (lower triangle, row-major, in place)
 // and the inverse through two triangular solves per unit vector
@@ -183,15 +206,21 @@ __global__ void k_scale_inverse(int n, const double* __restrict__ diag, const do
 
 // float32 level: A^ = S^-1 A S^-1 (off-diagonal, diagonal and its inverse),
 // and the transfer weights t_i = s_i / s_coarse(agg(i)).
-__global__ void k_level_fp32(int n, const int32_t* __restrict__ rp, const int32_t* __restrict__ ci,
-                             const double* __restrict__ va, const double* __restrict__ diag,
+__global__ void k_level_fp32(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ scol,
+                             const double* __restrict__ sval, const double* __restrict__ diag,
                              const int32_t* __restrict__ agg, const double* __restrict__ cdiag,
-                             float* __restrict__ va32, float* __restrict__ diag32,
+                             float* __restrict__ sval32, float* __restrict__ diag32,
                              float* __restrict__ dinv32, float* __restrict__ t32) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double si = sqrt(diag[i]);
-    for (int k = rp[i]; k < rp[i + 1]; ++k) va32[k] = (float)(va[k] / (si * sqrt(diag[ci[k]])));
+    const int64_t s0 = sptr[i >> 5], s1 = sptr[(i >> 5) + 1];
+    const int width = (int)((s1 - s0) >> 5);
+    const int64_t base = s0 + (i & 31);
+    for (int k = 0; k < width; ++k) {
+        const int64_t e = base + 32 * (int64_t)k;
+        sval32[e] = (float)(sval[e] / (si * sqrt(diag[scol[e]])));
+    }
     const double dh = diag[i] / (si * si);
     diag32[i] = (float)dh;
     dinv32[i] = (float)(1.0 / dh);
@@ -283,29 +312,46 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
                         DevArena& arena, DevLevel& L, cudaStream_t s) {
     const int32_t n = Ah.n;
     std::vector<int32_t> inv(n), nrp(n + 1, 0);
+    std::vector<uint16_t> rlen(n);
     for (int32_t i = 0; i < n; ++i) inv[perm[i]] = i;
     for (int32_t r = 0; r < n; ++r) {
         const int32_t i = inv[r];
-        nrp[r + 1] = nrp[r] + (Ah.rp[i + 1] - Ah.rp[i] - 1);
+        const int32_t len = Ah.rp[i + 1] - Ah.rp[i] - 1;
+        if (len > 65535) throw Error{AMG_EINVAL, "a matrix row has more than 65535 off-diagonal entries"};
+        rlen[r] = (uint16_t)len;
+        nrp[r + 1] = nrp[r] + len;
+    }
+    const int32_t nslices = (n + 31) / 32;
+    std::vector<int64_t> sptr(nslices + 1, 0);
+    for (int32_t sl = 0; sl < nslices; ++sl) {
+        int w = 0;
+        for (int32_t r = sl * 32; r < std::min(n, sl * 32 + 32); ++r) w = std::max<int>(w, rlen[r]);
+        sptr[sl + 1] = sptr[sl] + 32 * (int64_t)w;
     }
     L.n = n;
     L.nnz_off = nrp[n];
-    L.rp = arena.alloc<int32_t>(n + 1);
-    L.ci = arena.alloc<int32_t>(L.nnz_off);
-    L.va = arena.alloc<double>(L.nnz_off);
+    L.padded = sptr[nslices];
+    L.sptr = arena.alloc<int64_t>(nslices + 1);
+    L.rlen = arena.alloc<uint16_t>(n);
+    L.scol = arena.alloc<int32_t>(L.padded);
+    L.sval = arena.alloc<double>(L.padded);
     L.diag = arena.alloc<double>(n);
     L.dinv = arena.alloc<double>(n);
     DevArena tmp;
     int32_t* d_inv = tmp.alloc<int32_t>(n);
     int32_t* d_perm = tmp.alloc<int32_t>(n);
+    int32_t* d_nrp = tmp.alloc<int32_t>(n + 1);
+    int32_t* d_nci = tmp.alloc<int32_t>(L.nnz_off);
+    double* d_nva = tmp.alloc<double>(L.nnz_off);
     AMG_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
-    AMG_CUDA_TRY(cudaMemcpyAsync(L.rp, nrp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
-    k_reorder_rows<<<blocks_for(n), kBlock, 0, s>>>(n, d_inv, d_perm, A.rp, A.ci, A.va, L.rp, L.ci,
-                                                    L.va, L.diag, L.dinv);
+    AMG_CUDA_TRY(cudaMemcpyAsync(d_nrp, nrp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L.sptr, sptr.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(L.rlen, rlen.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice, s));
+    k_reorder_rows<<<blocks_for(n), kBlock, 0, s>>>(n, d_inv, d_perm, A.rp, A.ci, A.va, d_nrp, d_nci,
+                                                    d_nva, L.diag, L.dinv);
+    k_csr_to_sell<<<blocks_for(n), kBlock, 0, s>>>(n, d_nrp, d_nci, d_nva, L.sptr, L.scol, L.sval);
     AMG_CUDA_TRY(cudaGetLastError());
-    const double avg = n > 0 ? (double)L.nnz_off / n : 0.0;
-    L.lpr = avg <= 2.0 ? 2 : avg <= 4.0 ? 4 : avg <= 8.0 ? 8 : avg <= 16.0 ? 16 : 32;
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 }
 
@@ -338,15 +384,15 @@ void scale_inverse_device(int n, const double* diag, const double* Minv, double*
 
 void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, cudaStream_t s) {
     const int n = L.n;
-    L.va32 = arena.alloc<float>(L.nnz_off);
+    L.sval32 = arena.alloc<float>(L.padded);
     L.diag32 = arena.alloc<float>(n);
     L.dinv32 = arena.alloc<float>(n);
     L.t32 = coarse_diag ? arena.alloc<float>(n) : nullptr;
     L.x32 = arena.alloc<float>(n);
     L.b32 = arena.alloc<float>(n);
     L.r32 = arena.alloc<float>(n);
-    k_level_fp32<<<blocks_for(n), kBlock, 0, s>>>(n, L.rp, L.ci, L.va, L.diag, L.agg, coarse_diag,
-                                                  L.va32, L.diag32, L.dinv32, L.t32);
+    k_level_fp32<<<blocks_for(n), kBlock, 0, s>>>(n, L.sptr, L.scol, L.sval, L.diag, L.agg, coarse_diag,
+                                                  L.sval32, L.diag32, L.dinv32, L.t32);
     AMG_CUDA_TRY(cudaGetLastError());
 }
 

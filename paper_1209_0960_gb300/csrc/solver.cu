@@ -8,6 +8,7 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <type_traits>
 
 #include "device.h"
 
@@ -44,16 +45,18 @@ void upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
         AMG_CUDA_TRY(cudaMemcpyAsync(dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice, s));
 }
 
-// Smoothing order of level l: rows sorted by (colour, position of the coarse
-// aggregate in the next level's order, original index); rows outside every
-// aggregate come last inside their colour.
-std::vector<int32_t> smoothing_order(const HostLevel& h, const std::vector<int32_t>& next_perm) {
+// Smoothing order of level l: rows sorted by (colour, coarse aggregate index,
+// original index).  Aggregates are numbered in the order the greedy front built
+// them, so consecutive rows stay spatially close (x gathers hit in cache) and
+// the members of one aggregate are contiguous inside each colour.  Rows outside
+// every aggregate come last inside their colour.
+std::vector<int32_t> smoothing_order(const HostLevel& h) {
     const int32_t n = h.A.n;
     std::vector<int32_t> idx(n);
     std::iota(idx.begin(), idx.end(), 0);
     auto key = [&](int32_t i) {
         const int32_t a = h.agg.agg[i];
-        return std::make_pair(h.colour[i], a >= 0 ? next_perm[a] : INT32_MAX);
+        return std::make_pair(h.colour[i], a >= 0 ? a : INT32_MAX);
     };
     std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return key(x) < key(y); });
     std::vector<int32_t> perm(n);
@@ -61,23 +64,54 @@ std::vector<int32_t> smoothing_order(const HostLevel& h, const std::vector<int32
     return perm;
 }
 
-// modelled DRAM bytes of one V-cycle on a level (read every stored entry and
-// vector element a pass needs once; neighbour values of x come from cache)
-double level_vcycle_bytes(const DevLevel& L, int64_t n_coarse, bool coarsest, int vbytes) {
-    const double n = L.n;
-    if (coarsest) return n * n * 8.0 + 2.0 * n * vbytes;     // dense inverse times a vector
-    const double z = L.nnz_off;
-    const double M = z * (vbytes + 4) + 4.0 * (n + 1) + n * vbytes;   // off-diagonal CSR + diagonal
-    const double C = L.ncolours;
-    // pre and post smoothing: 2 x (2C - 1) colour passes = 2 (2C-1)/C matrix passes,
-    // each colour pass reads b and writes x for its rows
-    const double sgs = 2.0 * (2.0 * C - 1.0) / C * (M + 2.0 * n * vbytes);
-    const double resid = M + 3.0 * n * vbytes;                // read b, x; write r
-    const double restr = n * (vbytes + 4) + 4.0 * (n_coarse + 1) + n_coarse * vbytes;
-    const double prol = n * (2.0 * vbytes + 4) + n_coarse * vbytes;
-    const double zero = n * vbytes;                           // x = 0 before pre-smoothing
-    const double scal = vbytes == 4 ? 2.0 * n * 4 : 0.0;      // transfer weights
-    return sgs + resid + restr + prol + zero + scal;
+// Gauss-Seidel pass over m rows with z off-diagonal entries: CSR values and
+// indices, row pointers, 1/A_ii, b and the written x of those rows, and every
+// neighbour value of x once.
+double gs_bytes(const DevLevel& L, int col, int vb) {
+    const double m = L.cptr[col + 1] - L.cptr[col];
+    const double z = (double)L.cnnz[col];
+    return z * (vb + 4) + m * (2 + 3.0 * vb) + std::min(z, (double)L.n - m) * vb;
+}
+// residual on the rows of colour >= 1: their entries, lengths, diagonal, b,
+// own x and written r, and every neighbour value once
+double residual_bytes(const DevLevel& L, int vb) {
+    const double m = L.n - L.cptr[1];
+    const double z = (double)(L.nnz_off - L.cnnz[0]);
+    return z * (vb + 4) + m * (2 + 4.0 * vb) + std::min(z, (double)L.cptr[1]) * vb;
+}
+
+double restrict_bytes(const DevLevel& L, int vb, bool scaled) {
+    const double m = L.n - L.cptr[1];
+    return m * (4 + vb + (scaled ? 4 : 0)) + 4.0 * (L.n_coarse + 1) + (double)L.n_coarse * vb;
+}
+double prolong_bytes(const DevLevel& L, int vb, bool scaled) {
+    const double m = L.n - L.cptr[1];
+    return m * (4 + 2.0 * vb + (scaled ? 4 : 0)) + (double)L.n_coarse * vb;
+}
+// first pass from a zero guess: b and 1/A_ii of colour 0, x written everywhere
+double first_pass_bytes(const DevLevel& L, int vb) {
+    return (double)L.cptr[1] * 2.0 * vb + (double)L.n * vb;
+}
+
+// modelled DRAM bytes of one V-cycle on a level: the sum of its passes (first
+// pass from zero, 2 (2C - 1) - 1 colour passes, residual, restriction,
+// prolongation);
+// the coarsest level reads its dense inverse once
+double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb) {
+    if (coarsest) return (double)L.n * L.n * 8.0 + 2.0 * L.n * vb;
+    double t = first_pass_bytes(L, vb);
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int col = pass == 0 ? 1 : 0; col < L.ncolours; ++col) t += gs_bytes(L, col, vb);
+        for (int col = L.ncolours - 2; col >= 0; --col) t += gs_bytes(L, col, vb);
+    }
+    return t + residual_bytes(L, vb) + restrict_bytes(L, vb, vb == 4) + prolong_bytes(L, vb, vb == 4);
+}
+
+// modelled bytes of everything the persistent kernel does on levels lf..lc
+double coarse_cycle_bytes(amg_ctx* c, int vb) {
+    double t = 0.0;
+    for (int l = c->cc.lf; l <= c->cc.lc; ++l) t += level_vcycle_bytes(c->dl[l], l == c->cc.lc, vb);
+    return t;
 }
 
 void fill_info(amg_ctx* c) {
@@ -96,8 +130,8 @@ void fill_info(amg_ctx* c) {
         li.max_agg_size = last ? 0 : h.agg.max_size;
         li.n_isolated = last ? 0 : h.agg.n_isolated;
         li.n_dirichlet = last ? 0 : h.agg.n_dirichlet;
-        li.vcycle_bytes_fp64 = level_vcycle_bytes(d, li.n_coarse, last, 8);
-        li.vcycle_bytes_fp32 = level_vcycle_bytes(d, li.n_coarse, last, 4);
+        li.vcycle_bytes_fp64 = level_vcycle_bytes(d, last, 8);
+        li.vcycle_bytes_fp32 = level_vcycle_bytes(d, last, 4);
         b64 += li.vcycle_bytes_fp64;
         b32 += li.vcycle_bytes_fp32;
         if (l == 0) nnz0 = li.nnz;
@@ -113,7 +147,7 @@ void fill_info(amg_ctx* c) {
     // r, z), p = z + beta p (read z, p; write p)
     const DevLevel& d0 = c->dl[0];
     const double n = d0.n;
-    const double M64 = d0.nnz_off * 12.0 + 4.0 * (n + 1) + 8.0 * n;
+    const double M64 = d0.nnz_off * 12.0 + 2.0 * n + 8.0 * n;
     const double cg = (M64 + 16.0 * n) + 48.0 * n + 16.0 * n + 24.0 * n;
     c->summary.pcg_iter_bytes_fp64 = cg + b64;
     c->summary.pcg_iter_bytes_fp32 = cg + b32 + 8.0 * n * 3;  // conversions in and out
@@ -126,7 +160,7 @@ void fill_info(amg_ctx* c) {
 const char* kKindNames[kKNumKinds] = {
     "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
     "coarse_solve", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
-    "zero", "permute"};
+    "zero", "permute", "coarse_cycle"};
 
 struct ProfScope {
     amg_ctx* c;
@@ -144,22 +178,80 @@ struct ProfScope {
     }
 };
 
-// Gauss-Seidel pass over m rows with z off-diagonal entries: CSR values and
-// indices, row pointers, 1/A_ii, b and the written x of those rows, and every
-// neighbour value of x once.
-double gs_bytes(const DevLevel& L, int col, int vb) {
-    const double m = L.cptr[col + 1] - L.cptr[col];
-    const double z = (double)L.cnnz[col];
-    return z * (vb + 4) + m * (4 + 3.0 * vb) + 4 + std::min(z, (double)L.n - m) * vb;
+// ---------------------------------------------------------------------------
+// persistent coarse cycle: levels with at most kPersistentRows rows (and all
+// coarser ones) run inside one cooperative launch
+// ---------------------------------------------------------------------------
+constexpr int32_t kPersistentRows = 600000;
+
+template <typename T>
+CoarseLevel<T> coarse_view(const DevLevel& L, bool fp32) {
+    CoarseLevel<T> v{};
+    v.n = L.n;
+    v.ncolours = L.ncolours;
+    v.n_coarse = L.n_coarse;
+    v.cptr = L.cptr_dev;
+    v.sptr = L.sptr;
+    v.rlen = L.rlen;
+    v.scol = L.scol;
+    v.agg = L.agg;
+    v.rptr = L.rptr;
+    v.ridx = L.ridx;
+    if constexpr (std::is_same<T, float>::value) {
+        v.sval = L.sval32;
+        v.dinv = L.dinv32;
+        v.diag = L.diag32;
+        v.t = L.t32;
+        v.x = L.x32;
+        v.b = L.b32;
+    } else {
+        (void)fp32;
+        v.sval = L.sval;
+        v.dinv = L.dinv;
+        v.diag = L.diag;
+        v.t = nullptr;
+        v.x = L.x;
+        v.b = L.b;
+    }
+    return v;
 }
-double residual_bytes(const DevLevel& L, int vb) {
-    return (double)L.nnz_off * (vb + 4) + 4.0 * (L.n + 1) + 4.0 * L.n * vb;
+
+template <typename T>
+CoarseLevel<T>* upload_views(amg_ctx* c) {
+    const int nlev = (int)c->dl.size();
+    std::vector<CoarseLevel<T>> v(nlev);
+    for (int l = c->cc.lf; l < nlev; ++l) v[l] = coarse_view<T>(c->dl[l], std::is_same<T, float>::value);
+    CoarseLevel<T>* d = c->mem.alloc<CoarseLevel<T>>(nlev);
+    AMG_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(CoarseLevel<T>) * nlev, cudaMemcpyHostToDevice,
+                                 c->stream));
+    AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    return d;
 }
-double restrict_bytes(const DevLevel& L, int vb, bool scaled) {
-    return (double)L.n * (4 + vb + (scaled ? 4 : 0)) + 4.0 * (L.n_coarse + 1) + (double)L.n_coarse * vb;
+
+void setup_coarse_cycle(amg_ctx* c, int sms) {
+    c->cc = CoarseCycle{};
+    const int nlev = (int)c->dl.size();
+    if (nlev < 2) return;
+    int lf = -1;
+    for (int l = 1; l < nlev; ++l)
+        if (c->dl[l].n <= kPersistentRows) {
+            lf = l;
+            break;
+        }
+    const int blocks = coarse_cycle_blocks(sms);
+    if (lf < 0 || blocks <= 0) return;
+    c->cc.lf = lf;
+    c->cc.lc = nlev - 1;
+    c->cc.nL = c->nL;
+    c->cc.blocks = blocks;
+    c->cc.barrier = c->mem.alloc<GridBarrier>(1);
+    AMG_CUDA_TRY(cudaMemsetAsync(c->cc.barrier, 0, sizeof(GridBarrier), c->stream));
+    c->cc.lv64 = upload_views<double>(c);
 }
-double prolong_bytes(const DevLevel& L, int vb, bool scaled) {
-    return (double)L.n * (4 + 2.0 * vb + (scaled ? 4 : 0)) + (double)L.n_coarse * vb;
+
+void reset_barrier(amg_ctx* c) {
+    if (c->cc.barrier)
+        AMG_CUDA_TRY(cudaMemsetAsync(c->cc.barrier, 0, sizeof(GridBarrier), c->stream));
 }
 
 // ---------------------------------------------------------------------------
@@ -179,6 +271,11 @@ void sgs64(amg_ctx* c, const DevLevel& L, const double* b, double* x) {
 void vcycle64(amg_ctx* c, int l, const double* b, double* x) {
     const int nlev = (int)c->dl.size();
     DevLevel& L = c->dl[l];
+    if (l == c->cc.lf) {
+        ProfScope ps(c, kKCoarseCycle, coarse_cycle_bytes(c, 8));
+        launch_coarse_cycle64(c->cc, c->Ainv, c->p.omega, c->work.sc, c->stream);
+        return;
+    }
     if (l == nlev - 1) {
         ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 16.0 * c->nL);
         launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream);
@@ -186,13 +283,14 @@ void vcycle64(amg_ctx* c, int l, const double* b, double* x) {
     }
     DevLevel& C = c->dl[l + 1];
     {
-        ProfScope ps(c, kKZero, 8.0 * L.n);
-        AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(double) * L.n, c->stream));
+        ProfScope ps(c, l == 0 ? kKGsL0 : kKGsCoarse, first_pass_bytes(L, 8));
+        launch_gs_first(L, b, x, c->stream);
     }
-    sgs64(c, L, b, x);
+    for (int col = 1; col < L.ncolours; ++col) gs64(c, L, col, b, x);
+    for (int col = L.ncolours - 2; col >= 0; --col) gs64(c, L, col, b, x);
     {
         ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_bytes(L, 8));
-        launch_residual(L, b, x, L.r, c->stream);
+        launch_residual(L, L.cptr[1], b, x, L.r, c->stream);
     }
     {
         ProfScope ps(c, kKRestrict, restrict_bytes(L, 8, false));
@@ -219,6 +317,11 @@ void sgs32(amg_ctx* c, const DevLevel& L, const float* b, float* x) {
 void vcycle32(amg_ctx* c, int l, const float* b, float* x) {
     const int nlev = (int)c->dl.size();
     DevLevel& L = c->dl[l];
+    if (l == c->cc.lf) {
+        ProfScope ps(c, kKCoarseCycle, coarse_cycle_bytes(c, 4));
+        launch_coarse_cycle32(c->cc, c->Ainv_s, c->p.omega, c->work.sc, c->stream);
+        return;
+    }
     if (l == nlev - 1) {
         ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 8.0 * c->nL);
         launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream);
@@ -226,13 +329,14 @@ void vcycle32(amg_ctx* c, int l, const float* b, float* x) {
     }
     DevLevel& C = c->dl[l + 1];
     {
-        ProfScope ps(c, kKZero, 4.0 * L.n);
-        AMG_CUDA_TRY(cudaMemsetAsync(x, 0, sizeof(float) * L.n, c->stream));
+        ProfScope ps(c, l == 0 ? kKGsL0 : kKGsCoarse, first_pass_bytes(L, 4));
+        launch_gs_first32(L, b, x, c->stream);
     }
-    sgs32(c, L, b, x);
+    for (int col = 1; col < L.ncolours; ++col) gs32(c, L, col, b, x);
+    for (int col = L.ncolours - 2; col >= 0; --col) gs32(c, L, col, b, x);
     {
         ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_bytes(L, 4));
-        launch_residual32(L, b, x, L.r32, c->stream);
+        launch_residual32(L, L.cptr[1], b, x, L.r32, c->stream);
     }
     {
         ProfScope ps(c, kKRestrict, restrict_bytes(L, 4, true));
@@ -276,7 +380,40 @@ void ensure_fp32(amg_ctx* c) {
     c->Ainv_s = c->mem.alloc<double>((size_t)c->nL * c->nL);
     scale_inverse_device(c->nL, c->dl[nlev - 1].diag, c->Ainv, c->Ainv_s, c->stream);
     AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (c->cc.lf >= 0) c->cc.lv32 = upload_views<float>(c);
     c->fp32_ready = true;
+}
+
+// Order the context stream after the caller's stream (enter) and the
+// caller's stream after the context stream (leave).
+void enter(amg_ctx* c) {
+    AMG_CUDA_TRY(cudaEventRecord(c->ev_in, c->user_stream));
+    AMG_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
+}
+void leave(amg_ctx* c) {
+    AMG_CUDA_TRY(cudaEventRecord(c->ev_out, c->stream));
+    AMG_CUDA_TRY(cudaStreamWaitEvent(c->user_stream, c->ev_out, 0));
+}
+
+// Capture the launches issued by f on the context stream into an executable
+// graph.
+template <typename F>
+cudaGraphExec_t capture_graph(amg_ctx* c, F&& f) {
+    AMG_CUDA_TRY(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    cudaGraph_t g = nullptr;
+    try {
+        f();
+    } catch (...) {
+        cudaStreamEndCapture(c->stream, &g);
+        if (g) cudaGraphDestroy(g);
+        throw;
+    }
+    AMG_CUDA_TRY(cudaStreamEndCapture(c->stream, &g));
+    cudaGraphExec_t e = nullptr;
+    cudaError_t err = cudaGraphInstantiate(&e, g, 0);
+    cudaGraphDestroy(g);
+    AMG_CUDA_TRY(err);
+    return e;
 }
 
 // ---------------------------------------------------------------------------
@@ -292,6 +429,7 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     init.maxit = maxit;
     *c->sc_host = init;
     AMG_CUDA_TRY(cudaMemcpyAsync(c->work.sc, c->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
+    reset_barrier(c);
     launch_cg_residual(L0, c->bb, c->x, c->r, c->work, kRR0, nullptr, s);
     AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -301,21 +439,19 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
         launch_cg_rz(n, c->r, c->z, nullptr, c->pv, c->work, kRho0, s);
         if (c->flexible)
             AMG_CUDA_TRY(cudaMemcpyAsync(c->zold, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        while (true) {
-            if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
+        auto part_a = [&] {
             {
-                ProfScope ps(c, kKCgSpmv, (double)L0.nnz_off * 12 + 4.0 * (n + 1) + 24.0 * n);
+                ProfScope ps(c, kKCgSpmv, (double)L0.nnz_off * 12 + 2.0 * n + 24.0 * n);
                 launch_cg_spmv_pq(L0, c->pv, c->q, c->work, s);
             }
             {
                 ProfScope ps(c, kKCgUpdate, 48.0 * n);
                 launch_cg_update(n, c->x, c->r, c->pv, c->q, c->work, s);
             }
-            AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
-            AMG_CUDA_TRY(cudaStreamSynchronize(s));
-            if (c->sc_host->status != 0) { status = c->sc_host->status; break; }
-            if (c->sc_host->done) break;
-            if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars),
+                                         cudaMemcpyDeviceToHost, s));
+        };
+        auto part_b = [&] {
             precondition(c, c->r, c->z);
             {
                 ProfScope ps(c, kKCgDot, (c->flexible ? 24.0 : 16.0) * n);
@@ -325,6 +461,22 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
                 ProfScope ps(c, kKCgP, (c->flexible ? 32.0 : 24.0) * n);
                 launch_cg_p(n, c->z, c->pv, c->flexible ? c->zold : nullptr, c->work, s);
             }
+        };
+        const bool graphs = c->use_graphs && !c->prof.on;
+        cudaGraphExec_t& ga = c->graph_a[c->precision][c->flexible];
+        cudaGraphExec_t& gb = c->graph_b[c->precision][c->flexible];
+        if (graphs && !ga) ga = capture_graph(c, part_a);
+        if (graphs && !gb) gb = capture_graph(c, part_b);
+        while (true) {
+            if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
+            if (graphs) AMG_CUDA_TRY(cudaGraphLaunch(ga, s));
+            else part_a();
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            if (c->sc_host->status != 0) { status = c->sc_host->status; break; }
+            if (c->sc_host->done) break;
+            if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
+            if (graphs) AMG_CUDA_TRY(cudaGraphLaunch(gb, s));
+            else part_b();
         }
     }
     AMG_CUDA_TRY(cudaGetLastError());
@@ -372,8 +524,12 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     const double t_start = now_ms();
     auto c = std::make_unique<amg_ctx>();
     c->p = *prm;
-    c->stream = static_cast<cudaStream_t>(prm->cuda_stream);
+    c->user_stream = static_cast<cudaStream_t>(prm->cuda_stream);
     AMG_CUDA_TRY(cudaGetDevice(&c->device));
+    AMG_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    AMG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    AMG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    enter(c.get());
     int sms = 0;
     AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     g_reduction_blocks = std::max(1, sms) * 8;
@@ -453,7 +609,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         std::vector<int32_t>& pl = c->hl[nlev - 1].perm;
         pl.resize(c->nL);
         std::iota(pl.begin(), pl.end(), 0);
-        for (int l = nlev - 2; l >= 0; --l) c->hl[l].perm = smoothing_order(c->hl[l], c->hl[l + 1].perm);
+        for (int l = nlev - 2; l >= 0; --l) c->hl[l].perm = smoothing_order(c->hl[l]);
     }
     c->dl.resize(nlev);
     for (int l = 0; l < nlev; ++l) {
@@ -466,6 +622,8 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         if (l == nlev - 1) {
             L.cptr = {0, L.n};
             L.ncolours = 0;
+            L.cptr_dev = c->mem.alloc<int32_t>(2);
+            upload(L.cptr_dev, L.cptr, s);
             continue;
         }
         L.ncolours = h.ncolours;
@@ -479,23 +637,27 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         const std::vector<int32_t>& pn = c->hl[l + 1].perm;
         const int32_t nc = h.agg.nc;
         L.n_coarse = nc;
+        // restriction lists: the rows of colour >= 1 of each aggregate (colour 0
+        // is smoothed last and has a zero residual), ascending positions
         std::vector<int32_t> aggp(L.n, -1), rptr(nc + 1, 0), ridx;
         for (int32_t i = 0; i < L.n; ++i) {
             const int32_t a = h.agg.agg[i];
             if (a < 0) continue;
             aggp[h.perm[i]] = pn[a];
-            ++rptr[pn[a] + 1];
+            if (h.colour[i] > 0) ++rptr[pn[a] + 1];
         }
         for (int32_t J = 0; J < nc; ++J) rptr[J + 1] += rptr[J];
         ridx.resize(rptr[nc]);
         {
             std::vector<int32_t> fill(rptr.begin(), rptr.end() - 1);
-            for (int32_t r = 0; r < L.n; ++r)       // ascending position within each list
+            for (int32_t r = L.cptr[1]; r < L.n; ++r)
                 if (aggp[r] >= 0) ridx[fill[aggp[r]]++] = r;
         }
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
         L.ridx = c->mem.alloc<int32_t>(ridx.size());
+        L.cptr_dev = c->mem.alloc<int32_t>(L.cptr.size());
+        upload(L.cptr_dev, L.cptr, s);
         upload(L.agg, aggp, s);
         upload(L.rptr, rptr, s);
         upload(L.ridx, ridx, s);
@@ -540,6 +702,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     AMG_CUDA_TRY(cudaEventCreate(&c->ev1));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 
+    setup_coarse_cycle(c.get(), sms);
     c->flexible = prm->flexible_cg >= 0 ? prm->flexible_cg : (prm->precision == AMG_FP32_IN_FP64);
     c->precision = prm->precision;
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
@@ -548,6 +711,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     c->summary.gpu_galerkin_ms = galerkin_ms;
     c->summary.gpu_other_ms = now_ms() - t_dev0;
     c->summary.total_setup_ms = now_ms() - t_start;
+    leave(c.get());
     *out = c.release();
 }
 
@@ -590,7 +754,11 @@ int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
         if (!c) throw Error{AMG_EINVAL, "null context"};
         if (precision != AMG_FP64 && precision != AMG_FP32_IN_FP64)
             throw Error{AMG_EINVAL, "precision must be AMG_FP64 or AMG_FP32_IN_FP64"};
-        if (precision == AMG_FP32_IN_FP64) ensure_fp32(c);
+        if (precision == AMG_FP32_IN_FP64) {
+            enter(c);
+            ensure_fp32(c);
+            leave(c);
+        }
         c->precision = precision;
         c->flexible = flexible_cg >= 0 ? flexible_cg : (precision == AMG_FP32_IN_FP64);
     });
@@ -600,10 +768,13 @@ int amg_vcycle(amg_ctx* c, const double* r_dev, double* z_dev) {
     return Guard::run([&] {
         if (!c || !r_dev || !z_dev) throw Error{AMG_EINVAL, "null argument"};
         const int n = c->dl[0].n;
+        enter(c);
+        reset_barrier(c);
         launch_scatter(n, c->perm0, r_dev, c->r, c->stream);
         precondition(c, c->r, c->z);
         launch_gather(n, c->perm0, c->z, z_dev, c->stream);
         AMG_CUDA_TRY(cudaGetLastError());
+        leave(c);
     });
 }
 
@@ -615,6 +786,7 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         if (!(tol >= 0.0) || maxit < 0) throw Error{AMG_EINVAL, "tol must be >= 0 and maxit >= 0"};
         const int n = c->dl[0].n;
         cudaStream_t s = c->stream;
+        enter(c);
         AMG_CUDA_TRY(cudaEventRecord(c->ev0, s));
         const double* bd = b;
         double* xd = x;
@@ -640,6 +812,7 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         float ms = 0.f;
         AMG_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
         local.solve_ms = ms;
+        leave(c);
         if (info) *info = local;
         if (status != AMG_OK)
             t_last_error = status == AMG_ENOTCONV ? "maximum iterations reached"
@@ -664,12 +837,14 @@ int amg_residual_norm(amg_ctx* c, const double* b_dev, const double* x_dev, doub
         if (!c || !b_dev || !x_dev || !out_norm) throw Error{AMG_EINVAL, "null argument"};
         const int n = c->dl[0].n;
         cudaStream_t s = c->stream;
+        enter(c);
         launch_scatter(n, c->perm0, b_dev, c->q, s);
         launch_scatter(n, c->perm0, x_dev, c->pv, s);
         launch_cg_residual(c->dl[0], c->q, c->pv, nullptr, c->work, kStore, c->norm_dev, s);
         double rr = 0.0;
         AMG_CUDA_TRY(cudaMemcpyAsync(&rr, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
         AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        leave(c);
         *out_norm = std::sqrt(rr);
     });
 }
@@ -785,9 +960,7 @@ int amg_profile_read(amg_ctx* c, amg_kernel_stat* stats, int32_t cap) {
 
 int amg_free(amg_ctx* c) {
     if (!c) return AMG_OK;
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    else cudaDeviceSynchronize();
-    delete c;
+    delete c;   // the destructor drains the context stream first
     return AMG_OK;
 }
 
