@@ -101,13 +101,13 @@ struct DevLevel {
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
+    int32_t lpr = 1;                  // lanes per row of the row kernels (1, 4 or 8)
     int64_t* sptr = nullptr;          // [n/32 + 1] slice starts
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
     double* sval = nullptr;           // [padded]
     double* diag = nullptr;           // [n]
     double* dinv = nullptr;           // [n] 1 / A_ii
-    int32_t* cptr_dev = nullptr;      // device copy of cptr
     int32_t* agg = nullptr;           // [n] permuted coarse index or -1
     int32_t* rptr = nullptr;          // [n_coarse+1] restriction lists
     int32_t* ridx = nullptr;          // fine rows of colour >= 1 of each coarse row
@@ -124,50 +124,6 @@ struct DevLevel {
     float* r32 = nullptr;
 };
 
-// Grid-wide barrier state of the persistent coarse-cycle kernel.
-struct GridBarrier {
-    unsigned int count;
-    unsigned int gen;
-    int err;
-    int pad;
-};
-
-// Level view used by the persistent coarse-cycle kernel (device resident).
-template <typename T>
-struct CoarseLevel {
-    int n, ncolours, n_coarse;
-    const int32_t* cptr;
-    const int64_t* sptr;
-    const uint16_t* rlen;
-    const int32_t* scol;
-    const T* sval;
-    const T* dinv;
-    const T* diag;
-    const int32_t* agg;
-    const int32_t* rptr;
-    const int32_t* ridx;
-    const T* t;
-    T* x;
-    T* b;
-};
-
-// Levels lf..lc (lc = coarsest) run inside one cooperative launch.
-struct CoarseCycle {
-    int lf = -1;                      // first level of the persistent kernel, -1 = none
-    int lc = 0;
-    int nL = 0;
-    int blocks = 0;
-    CoarseLevel<double>* lv64 = nullptr;   // device array indexed by level
-    CoarseLevel<float>* lv32 = nullptr;
-    GridBarrier* barrier = nullptr;
-};
-
-int coarse_cycle_blocks(int sms);
-void launch_coarse_cycle64(const CoarseCycle& cc, const double* Minv, double omega, PcgScalars* sc,
-                           cudaStream_t s);
-void launch_coarse_cycle32(const CoarseCycle& cc, const double* Minv, double omega, PcgScalars* sc,
-                           cudaStream_t s);
-
 // Launch profiler: events around launches, grouped by kernel class.
 struct Profiler {
     bool on = false;
@@ -179,7 +135,7 @@ struct Profiler {
 
 enum KernelKind : int {
     kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
-    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKCoarseCycle, kKNumKinds
+    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKNumKinds
 };
 
 struct HostLevel {
@@ -304,7 +260,6 @@ struct amg_ctx {
     std::vector<amg::HostLevel> hl;
     std::vector<amg::DevLevel> dl;
     int32_t nL = 0;                   // coarsest size
-    amg::CoarseCycle cc;              // persistent kernel for the small levels
     double* Ainv = nullptr;           // [nL x nL] inverse of the coarsest matrix
     double* Ainv_s = nullptr;         // [nL x nL] inverse of the scaled coarsest matrix
     double* isq0 = nullptr;           // [n] 1 / sqrt(A_ii) of level 0 (FP32 entry/exit)

@@ -47,6 +47,23 @@ __device__ __forceinline__ T sell_row(int64_t base, int len, const int32_t* __re
     return acc;
 }
 
+// Same sum split over the LPR lanes of a group (lane-strided entries, then a
+// shuffle reduction); acc is added once.  Every lane returns the full sum.
+template <int LPR, bool NEG, typename T, typename X>
+__device__ __forceinline__ T sell_row_group(int64_t base, int len, int lane,
+                                            const int32_t* __restrict__ scol,
+                                            const T* __restrict__ sval, const X* x, T acc) {
+    if (LPR == 1) return sell_row<NEG>(base, len, scol, sval, x, acc);
+    T s = lane == 0 ? acc : T(0);
+#pragma unroll 2
+    for (int k = lane; k < len; k += LPR) {
+        const int64_t e = base + 32 * (int64_t)k;
+        const T a = sval[e];
+        s = fmad(NEG ? -a : a, T(x[scol[e]]), s);
+    }
+    return group_sum<LPR>(s);
+}
+
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
@@ -134,20 +151,28 @@ __device__ void finish_reduction(double v0, double v1, double* partials, double*
 
 // One Gauss-Seidel update of rows [r0, r1) of one colour:
 //   x_i = (b_i - sum_{j != i} A_ij x_j) / A_ii.
-// Rows of one colour are not coupled, so they update in parallel.  Threads
-// start at the slice boundary below r0 so warps read whole slices.
-template <typename T>
+// Rows of one colour are not coupled, so they update in parallel.  LPR lanes
+// share a row (LPR = 1 on the fine level, where float64 arithmetic is the
+// scarce resource; 4 or 8 on the denser coarse levels, where the latency of
+// the gathers dominates).  Threads start at the slice boundary below r0 so
+// warps read whole slices.
+template <int LPR, typename T>
 __global__ void __launch_bounds__(kBlock) k_gs(int r0, int r1, const int64_t* __restrict__ sptr,
                                                const uint16_t* __restrict__ rlen,
                                                const int32_t* __restrict__ scol,
                                                const T* __restrict__ sval,
                                                const T* __restrict__ dinv,
                                                const T* __restrict__ b, T* x) {
-    const int row = (r0 & ~31) + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (row < r0 || row >= r1) return;
-    const int64_t base = sptr[row >> 5] + (row & 31);
-    const T s = sell_row<true>(base, rlen[row], scol, sval, x, b[row]);
-    x[row] = s * dinv[row];
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int row = (r0 & ~31) + (int)(t / LPR);
+    const int lane = (int)(t % LPR);
+    const bool valid = row >= r0 && row < r1;
+    if (LPR == 1 && !valid) return;
+    const int rr = valid ? row : r0;
+    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const T s = sell_row_group<LPR, true>(base, valid ? (int)rlen[rr] : 0, lane, scol, sval, x,
+                                          valid ? b[rr] : T(0));
+    if (valid && lane == 0) x[row] = s * dinv[row];
 }
 
 // First Gauss-Seidel pass from a zero initial guess: the rows of colour 0
@@ -162,7 +187,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_first(int c1, int n, const T* __r
 }
 
 // r = b - A x for rows [r0, n)
-template <typename T>
+template <int LPR, typename T>
 __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_t* __restrict__ sptr,
                                                      const uint16_t* __restrict__ rlen,
                                                      const int32_t* __restrict__ scol,
@@ -170,11 +195,16 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_
                                                      const T* __restrict__ diag,
                                                      const T* __restrict__ b,
                                                      const T* __restrict__ x, T* __restrict__ r) {
-    const int row = (r0 & ~31) + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (row < r0 || row >= n) return;
-    const int64_t base = sptr[row >> 5] + (row & 31);
-    const T s0 = fmad(-diag[row], x[row], b[row]);
-    r[row] = sell_row<true>(base, rlen[row], scol, sval, x, s0);
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int row = (r0 & ~31) + (int)(t / LPR);
+    const int lane = (int)(t % LPR);
+    const bool valid = row >= r0 && row < n;
+    if (LPR == 1 && !valid) return;
+    const int rr = valid ? row : r0;
+    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const T s0 = valid ? fmad(-diag[rr], x[rr], b[rr]) : T(0);
+    const T v = sell_row_group<LPR, true>(base, valid ? (int)rlen[rr] : 0, lane, scol, sval, x, s0);
+    if (valid && lane == 0) r[row] = v;
 }
 
 // coarse right-hand side: bc_J = sum over the fine rows i of aggregate J of
@@ -372,32 +402,39 @@ int reduction_blocks(int64_t work_threads) {
     return (int)std::min<int64_t>(b, g_reduction_blocks);
 }
 
-inline int row_blocks(int r0, int r1) { return blocks_for((int64_t)(r1 - (r0 & ~31))); }
+inline int row_blocks(int r0, int r1, int lpr) { return blocks_for((int64_t)(r1 - (r0 & ~31)) * lpr); }
+
+#define AMG_LPR_DISPATCH(lpr, CALL)                          \
+    switch (lpr) {                                           \
+        case 1: { constexpr int LPR = 1; CALL; } break;      \
+        case 4: { constexpr int LPR = 4; CALL; } break;      \
+        default: { constexpr int LPR = 8; CALL; } break;     \
+    }
 
 void launch_gs(const DevLevel& L, int r0, int r1, const double* b, double* x, cudaStream_t s) {
     if (r1 <= r0) return;
-    k_gs<double><<<row_blocks(r0, r1), kBlock, 0, s>>>(r0, r1, L.sptr, L.rlen, L.scol, L.sval,
-                                                       L.dinv, b, x);
+    AMG_LPR_DISPATCH(L.lpr, (k_gs<LPR, double><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
+                                r0, r1, L.sptr, L.rlen, L.scol, L.sval, L.dinv, b, x)));
 }
 
 void launch_gs32(const DevLevel& L, int r0, int r1, const float* b, float* x, cudaStream_t s) {
     if (r1 <= r0) return;
-    k_gs<float><<<row_blocks(r0, r1), kBlock, 0, s>>>(r0, r1, L.sptr, L.rlen, L.scol, L.sval32,
-                                                      L.dinv32, b, x);
+    AMG_LPR_DISPATCH(L.lpr, (k_gs<LPR, float><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
+                                r0, r1, L.sptr, L.rlen, L.scol, L.sval32, L.dinv32, b, x)));
 }
 
 void launch_residual(const DevLevel& L, int r0, const double* b, const double* x, double* r,
                      cudaStream_t s) {
     if (L.n <= r0) return;
-    k_residual<double><<<row_blocks(r0, L.n), kBlock, 0, s>>>(r0, L.n, L.sptr, L.rlen, L.scol,
-                                                              L.sval, L.diag, b, x, r);
+    AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, double><<<row_blocks(r0, L.n, LPR), kBlock, 0, s>>>(
+                                r0, L.n, L.sptr, L.rlen, L.scol, L.sval, L.diag, b, x, r)));
 }
 
 void launch_residual32(const DevLevel& L, int r0, const float* b, const float* x, float* r,
                        cudaStream_t s) {
     if (L.n <= r0) return;
-    k_residual<float><<<row_blocks(r0, L.n), kBlock, 0, s>>>(r0, L.n, L.sptr, L.rlen, L.scol,
-                                                             L.sval32, L.diag32, b, x, r);
+    AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, float><<<row_blocks(r0, L.n, LPR), kBlock, 0, s>>>(
+                                r0, L.n, L.sptr, L.rlen, L.scol, L.sval32, L.diag32, b, x, r)));
 }
 
 void launch_restrict(const DevLevel& L, const double* r, double* bc, cudaStream_t s) {

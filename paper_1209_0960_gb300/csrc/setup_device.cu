@@ -352,6 +352,10 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
                                                     d_nva, L.diag, L.dinv);
     k_csr_to_sell<<<blocks_for(n), kBlock, 0, s>>>(n, d_nrp, d_nci, d_nva, L.sptr, L.scol, L.sval);
     AMG_CUDA_TRY(cudaGetLastError());
+    // lanes per row: one on sparse rows (float64 arithmetic bound), several on
+    // the denser coarse rows (gather latency bound)
+    const double avg = n > 0 ? (double)L.nnz_off / n : 0.0;
+    L.lpr = avg <= 7.0 ? 1 : avg <= 16.0 ? 4 : 8;
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 }
 

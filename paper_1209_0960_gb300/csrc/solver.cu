@@ -107,13 +107,6 @@ double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb) {
     return t + residual_bytes(L, vb) + restrict_bytes(L, vb, vb == 4) + prolong_bytes(L, vb, vb == 4);
 }
 
-// modelled bytes of everything the persistent kernel does on levels lf..lc
-double coarse_cycle_bytes(amg_ctx* c, int vb) {
-    double t = 0.0;
-    for (int l = c->cc.lf; l <= c->cc.lc; ++l) t += level_vcycle_bytes(c->dl[l], l == c->cc.lc, vb);
-    return t;
-}
-
 void fill_info(amg_ctx* c) {
     const int L = (int)c->dl.size();
     c->linfo.assign(L, amg_level_info{});
@@ -160,7 +153,7 @@ void fill_info(amg_ctx* c) {
 const char* kKindNames[kKNumKinds] = {
     "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
     "coarse_solve", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
-    "zero", "permute", "coarse_cycle"};
+    "zero", "permute"};
 
 struct ProfScope {
     amg_ctx* c;
@@ -179,82 +172,6 @@ struct ProfScope {
 };
 
 // ---------------------------------------------------------------------------
-// persistent coarse cycle: levels with at most kPersistentRows rows (and all
-// coarser ones) run inside one cooperative launch
-// ---------------------------------------------------------------------------
-constexpr int32_t kPersistentRows = 600000;
-
-template <typename T>
-CoarseLevel<T> coarse_view(const DevLevel& L, bool fp32) {
-    CoarseLevel<T> v{};
-    v.n = L.n;
-    v.ncolours = L.ncolours;
-    v.n_coarse = L.n_coarse;
-    v.cptr = L.cptr_dev;
-    v.sptr = L.sptr;
-    v.rlen = L.rlen;
-    v.scol = L.scol;
-    v.agg = L.agg;
-    v.rptr = L.rptr;
-    v.ridx = L.ridx;
-    if constexpr (std::is_same<T, float>::value) {
-        v.sval = L.sval32;
-        v.dinv = L.dinv32;
-        v.diag = L.diag32;
-        v.t = L.t32;
-        v.x = L.x32;
-        v.b = L.b32;
-    } else {
-        (void)fp32;
-        v.sval = L.sval;
-        v.dinv = L.dinv;
-        v.diag = L.diag;
-        v.t = nullptr;
-        v.x = L.x;
-        v.b = L.b;
-    }
-    return v;
-}
-
-template <typename T>
-CoarseLevel<T>* upload_views(amg_ctx* c) {
-    const int nlev = (int)c->dl.size();
-    std::vector<CoarseLevel<T>> v(nlev);
-    for (int l = c->cc.lf; l < nlev; ++l) v[l] = coarse_view<T>(c->dl[l], std::is_same<T, float>::value);
-    CoarseLevel<T>* d = c->mem.alloc<CoarseLevel<T>>(nlev);
-    AMG_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(CoarseLevel<T>) * nlev, cudaMemcpyHostToDevice,
-                                 c->stream));
-    AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return d;
-}
-
-void setup_coarse_cycle(amg_ctx* c, int sms) {
-    c->cc = CoarseCycle{};
-    const int nlev = (int)c->dl.size();
-    if (nlev < 2) return;
-    int lf = -1;
-    for (int l = 1; l < nlev; ++l)
-        if (c->dl[l].n <= kPersistentRows) {
-            lf = l;
-            break;
-        }
-    const int blocks = coarse_cycle_blocks(sms);
-    if (lf < 0 || blocks <= 0) return;
-    c->cc.lf = lf;
-    c->cc.lc = nlev - 1;
-    c->cc.nL = c->nL;
-    c->cc.blocks = blocks;
-    c->cc.barrier = c->mem.alloc<GridBarrier>(1);
-    AMG_CUDA_TRY(cudaMemsetAsync(c->cc.barrier, 0, sizeof(GridBarrier), c->stream));
-    c->cc.lv64 = upload_views<double>(c);
-}
-
-void reset_barrier(amg_ctx* c) {
-    if (c->cc.barrier)
-        AMG_CUDA_TRY(cudaMemsetAsync(c->cc.barrier, 0, sizeof(GridBarrier), c->stream));
-}
-
-// ---------------------------------------------------------------------------
 // V-cycle (Sec. 2): pre-smooth, restrict the residual, recurse, prolongate
 // with omega, post-smooth; dense solve on the coarsest level
 // ---------------------------------------------------------------------------
@@ -271,11 +188,6 @@ void sgs64(amg_ctx* c, const DevLevel& L, const double* b, double* x) {
 void vcycle64(amg_ctx* c, int l, const double* b, double* x) {
     const int nlev = (int)c->dl.size();
     DevLevel& L = c->dl[l];
-    if (l == c->cc.lf) {
-        ProfScope ps(c, kKCoarseCycle, coarse_cycle_bytes(c, 8));
-        launch_coarse_cycle64(c->cc, c->Ainv, c->p.omega, c->work.sc, c->stream);
-        return;
-    }
     if (l == nlev - 1) {
         ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 16.0 * c->nL);
         launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream);
@@ -317,11 +229,6 @@ void sgs32(amg_ctx* c, const DevLevel& L, const float* b, float* x) {
 void vcycle32(amg_ctx* c, int l, const float* b, float* x) {
     const int nlev = (int)c->dl.size();
     DevLevel& L = c->dl[l];
-    if (l == c->cc.lf) {
-        ProfScope ps(c, kKCoarseCycle, coarse_cycle_bytes(c, 4));
-        launch_coarse_cycle32(c->cc, c->Ainv_s, c->p.omega, c->work.sc, c->stream);
-        return;
-    }
     if (l == nlev - 1) {
         ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 8.0 * c->nL);
         launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream);
@@ -380,7 +287,6 @@ void ensure_fp32(amg_ctx* c) {
     c->Ainv_s = c->mem.alloc<double>((size_t)c->nL * c->nL);
     scale_inverse_device(c->nL, c->dl[nlev - 1].diag, c->Ainv, c->Ainv_s, c->stream);
     AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (c->cc.lf >= 0) c->cc.lv32 = upload_views<float>(c);
     c->fp32_ready = true;
 }
 
@@ -429,7 +335,6 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     init.maxit = maxit;
     *c->sc_host = init;
     AMG_CUDA_TRY(cudaMemcpyAsync(c->work.sc, c->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-    reset_barrier(c);
     launch_cg_residual(L0, c->bb, c->x, c->r, c->work, kRR0, nullptr, s);
     AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -622,8 +527,6 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         if (l == nlev - 1) {
             L.cptr = {0, L.n};
             L.ncolours = 0;
-            L.cptr_dev = c->mem.alloc<int32_t>(2);
-            upload(L.cptr_dev, L.cptr, s);
             continue;
         }
         L.ncolours = h.ncolours;
@@ -656,8 +559,6 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
         L.ridx = c->mem.alloc<int32_t>(ridx.size());
-        L.cptr_dev = c->mem.alloc<int32_t>(L.cptr.size());
-        upload(L.cptr_dev, L.cptr, s);
         upload(L.agg, aggp, s);
         upload(L.rptr, rptr, s);
         upload(L.ridx, ridx, s);
@@ -702,7 +603,6 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     AMG_CUDA_TRY(cudaEventCreate(&c->ev1));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 
-    setup_coarse_cycle(c.get(), sms);
     c->flexible = prm->flexible_cg >= 0 ? prm->flexible_cg : (prm->precision == AMG_FP32_IN_FP64);
     c->precision = prm->precision;
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
@@ -769,8 +669,7 @@ int amg_vcycle(amg_ctx* c, const double* r_dev, double* z_dev) {
         if (!c || !r_dev || !z_dev) throw Error{AMG_EINVAL, "null argument"};
         const int n = c->dl[0].n;
         enter(c);
-        reset_barrier(c);
-        launch_scatter(n, c->perm0, r_dev, c->r, c->stream);
+            launch_scatter(n, c->perm0, r_dev, c->r, c->stream);
         precondition(c, c->r, c->z);
         launch_gather(n, c->perm0, c->z, z_dev, c->stream);
         AMG_CUDA_TRY(cudaGetLastError());
