@@ -292,6 +292,12 @@ def run_ours(args, dist: Dist):
     prof64 = solver.profile_read()
     solver.profile(False)
 
+    solver.profile(2)
+    x.zero_()
+    solver.solve(b, x, tol=args.tol)
+    graph64 = solver.profile_read()
+    solver.profile(0)
+
     # ---- FP32-in-FP64 ---------------------------------------------------------
     solver.set_precision(amg.AMG_FP32_IN_FP64)
     for _ in range(args.warmup):
@@ -305,7 +311,11 @@ def run_ours(args, dist: Dist):
     x.zero_()
     solver.solve(b, x, tol=args.tol)
     prof32 = solver.profile_read()
-    solver.profile(False)
+    solver.profile(2)
+    x.zero_()
+    solver.solve(b, x, tol=args.tol)
+    graph32 = solver.profile_read()
+    solver.profile(0)
     solver.set_precision(amg.AMG_FP64)
 
     # ---- end to end through the C ABI with pinned host buffers -----------------
@@ -343,7 +353,7 @@ def run_ours(args, dist: Dist):
                 "frac_of_nominal_7900": (vb / (vt * 1e-3) / 1e9) / 7900.0 if vt > 0 else None,
                 "ms_per_vcycle_kernels": vt / max(1, iters + 1)}
 
-    launches = sum(d["launches"] for d in prof64 if d["name"] != "zero")
+    launches = sum(d["launches"] for d in prof64 if d["name"] not in ("zero",))
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----------------
     cpu = None
@@ -380,6 +390,9 @@ def run_ours(args, dist: Dist):
                   "level_n": [l["n"] for l in levels]},
         "roofline": roofline,
         "kernels_fp64": prof64,
+        "graph_parts_ms": {
+            "fp64": {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in graph64},
+            "fp32": {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in graph32}},
         "gpu_launches": launches * args.steps,
         "e2e": e2e,
         "clocks": clk,

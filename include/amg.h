@@ -210,9 +210,14 @@ int amg_aggregate(const amg_csr *A, const amg_params *p, int32_t *agg, int32_t *
  * the number of colours.  Needs no GPU.  Errors: AMG_EINVAL. */
 int amg_colour(const amg_csr *A, int32_t *colour, int32_t *ncolours);
 
-/* Profiler: enable != 0 clears the records and brackets every later kernel
- * launch of the context with CUDA events on the context stream (adds a few
- * microseconds per launch); enable == 0 stops recording.  Errors: AMG_EINVAL. */
+/* Profiler.  enable == 1 clears the records and brackets every later kernel
+ * launch of the context with CUDA events on the context stream (the solve
+ * then launches kernels one by one instead of through CUDA graphs, and each
+ * launch costs a few microseconds more).  enable == 2 keeps the graphs and
+ * brackets each graph launch instead ("graph_cg_part": SpMV and updates,
+ * "graph_vcycle_part": V-cycle and direction update), and after every solve
+ * replays the levels >= 1 of the V-cycle ten times ("graph_coarse_levels").
+ * enable == 0 stops recording.  Errors: AMG_EINVAL. */
 int amg_profile_enable(amg_ctx *c, int32_t enable);
 
 /* Synchronises the context stream and fills up to cap records, one per kernel

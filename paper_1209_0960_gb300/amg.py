@@ -246,8 +246,9 @@ def amg_colour(row_ptr, col, val):
     return colour, int(nc.value)
 
 
-def amg_profile_enable(ctx: int, enable: bool) -> None:
-    _check(lib().amg_profile_enable(ctx, int(bool(enable))), "amg_profile_enable")
+def amg_profile_enable(ctx: int, enable) -> None:
+    """enable: 0 off, 1 (or True) per kernel, 2 per graph launch."""
+    _check(lib().amg_profile_enable(ctx, int(enable)), "amg_profile_enable")
 
 
 def amg_profile_read(ctx: int) -> list:
@@ -330,7 +331,7 @@ class AMG:
     def info(self):
         return amg_hierarchy_info(self.ctx)
 
-    def profile(self, enable: bool):
+    def profile(self, enable):
         amg_profile_enable(self.ctx, enable)
 
     def profile_read(self) -> list:

@@ -102,6 +102,7 @@ struct DevLevel {
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
     int32_t lpr = 1;                  // lanes per row of the row kernels (1, 4 or 8)
+    bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 1)
     int64_t* sptr = nullptr;          // [n/32 + 1] slice starts
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
@@ -126,7 +127,8 @@ struct DevLevel {
 
 // Launch profiler: events around launches, grouped by kernel class.
 struct Profiler {
-    bool on = false;
+    bool on = false;        // events around every launch (graphs off)
+    bool graphs = false;    // events around graph launches only (graphs on)
     struct Rec { int kind; double bytes; int ev; };
     std::vector<cudaEvent_t> events;   // pool, pairs (start, end)
     std::vector<Rec> recs;
@@ -135,7 +137,8 @@ struct Profiler {
 
 enum KernelKind : int {
     kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
-    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKNumKinds
+    kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKGraphA, kKGraphB,
+    kKGraphCoarse, kKNumKinds
 };
 
 struct HostLevel {
@@ -177,20 +180,28 @@ struct CgWork {
 extern int g_reduction_blocks;        // grid of the reduction kernels (SMs x 8)
 int reduction_blocks(int64_t work_threads);
 
-void launch_gs(const DevLevel& L, int r0, int r1, const double* b, double* x, cudaStream_t s);
-void launch_gs32(const DevLevel& L, int r0, int r1, const float* b, float* x, cudaStream_t s);
-// first pre-smoothing pass from x = 0: x = b / A_ii on colour 0, 0 elsewhere
-void launch_gs_first(const DevLevel& L, const double* b, double* x, cudaStream_t s);
-void launch_gs_first32(const DevLevel& L, const float* b, float* x, cudaStream_t s);
-// r = b - A x on rows [r0, n)
-void launch_residual(const DevLevel& L, int r0, const double* b, const double* x, double* r,
-                     cudaStream_t s);
-void launch_residual32(const DevLevel& L, int r0, const float* b, const float* x, float* r,
-                       cudaStream_t s);
-void launch_restrict(const DevLevel& L, const double* r, double* bc, cudaStream_t s);
-void launch_restrict32(const DevLevel& L, const float* r, float* bc, cudaStream_t s);
+// V-cycle passes (see kernels.cu).  first: the first two forward colour passes
+// from a zero guess (optionally zeroing the next level's right-hand side);
+// pass: one colour, neighbours at positions >= jmax taken as zero;
+// pass_prolong: colour 0 of a two-colour level reading the other colour's
+// prolongated values; residual_restrict: coarse right-hand side from the
+// residual of the rows of colour >= 1; prolong: x += omega P e on colour >= 1.
+void launch_first(const DevLevel& L, const double* b, double* x, double* bc_zero, int nc,
+                  cudaStream_t s);
+void launch_first32(const DevLevel& L, const float* b, float* x, float* bc_zero, int nc,
+                    cudaStream_t s);
+void launch_pass(const DevLevel& L, int col, int jmax, const double* b, double* x, cudaStream_t s);
+void launch_pass32(const DevLevel& L, int col, int jmax, const float* b, float* x, cudaStream_t s);
+void launch_pass_prolong(const DevLevel& L, const double* b, double* x, const double* e,
+                         double omega, cudaStream_t s);
+void launch_pass_prolong32(const DevLevel& L, const float* b, float* x, const float* e,
+                           double omega, cudaStream_t s);
+void launch_residual_restrict(const DevLevel& L, const double* b, const double* x, double* r,
+                              double* bc, cudaStream_t s);
+void launch_residual_restrict32(const DevLevel& L, const float* b, const float* x, float* r,
+                                float* bc, cudaStream_t s);
 void launch_prolong(const DevLevel& L, const double* e, double* x, double omega, cudaStream_t s);
-void launch_prolong32(const DevLevel& L, const float* e, float* x, float omega, cudaStream_t s);
+void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega, cudaStream_t s);
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s);
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s);
 void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s);
@@ -255,6 +266,7 @@ struct amg_ctx {
     // alpha, x/r update, status copy; B = z = B r, beta, p update
     cudaGraphExec_t graph_a[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphExec_t graph_b[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    cudaGraphExec_t graph_coarse[2] = {nullptr, nullptr};   // levels >= 1 only (profiling)
     bool use_graphs = true;
     amg::DevArena mem;
     std::vector<amg::HostLevel> hl;
@@ -291,6 +303,8 @@ struct amg_ctx {
                 if (graph_a[a][b]) cudaGraphExecDestroy(graph_a[a][b]);
                 if (graph_b[a][b]) cudaGraphExecDestroy(graph_b[a][b]);
             }
+        for (int a = 0; a < 2; ++a)
+            if (graph_coarse[a]) cudaGraphExecDestroy(graph_coarse[a]);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (stream) {

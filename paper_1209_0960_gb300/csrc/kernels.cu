@@ -14,6 +14,9 @@
 // per-block partial sums in a fixed grid, combined in a fixed order by the
 // last block to finish.
 
+#include <algorithm>
+#include <type_traits>
+
 #include "device.h"
 
 namespace amg {
@@ -45,23 +48,6 @@ __device__ __forceinline__ T sell_row(int64_t base, int len, const int32_t* __re
         acc = fmad(NEG ? -a : a, T(x[scol[e]]), acc);
     }
     return acc;
-}
-
-// Same sum split over the LPR lanes of a group (lane-strided entries, then a
-// shuffle reduction); acc is added once.  Every lane returns the full sum.
-template <int LPR, bool NEG, typename T, typename X>
-__device__ __forceinline__ T sell_row_group(int64_t base, int len, int lane,
-                                            const int32_t* __restrict__ scol,
-                                            const T* __restrict__ sval, const X* x, T acc) {
-    if (LPR == 1) return sell_row<NEG>(base, len, scol, sval, x, acc);
-    T s = lane == 0 ? acc : T(0);
-#pragma unroll 2
-    for (int k = lane; k < len; k += LPR) {
-        const int64_t e = base + 32 * (int64_t)k;
-        const T a = sval[e];
-        s = fmad(NEG ? -a : a, T(x[scol[e]]), s);
-    }
-    return group_sum<LPR>(s);
 }
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
@@ -149,41 +135,142 @@ __device__ void finish_reduction(double v0, double v1, double* partials, double*
 // V-cycle kernels
 // ---------------------------------------------------------------------------
 
-// One Gauss-Seidel update of rows [r0, r1) of one colour:
-//   x_i = (b_i - sum_{j != i} A_ij x_j) / A_ii.
-// Rows of one colour are not coupled, so they update in parallel.  LPR lanes
-// share a row (LPR = 1 on the fine level, where float64 arithmetic is the
-// scarce resource; 4 or 8 on the denser coarse levels, where the latency of
-// the gathers dominates).  Threads start at the slice boundary below r0 so
-// warps read whole slices.
-template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_gs(int r0, int r1, const int64_t* __restrict__ sptr,
-                                               const uint16_t* __restrict__ rlen,
-                                               const int32_t* __restrict__ scol,
-                                               const T* __restrict__ sval,
-                                               const T* __restrict__ dinv,
-                                               const T* __restrict__ b, T* x) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int row = (r0 & ~31) + (int)(t / LPR);
-    const int lane = (int)(t % LPR);
-    const bool valid = row >= r0 && row < r1;
-    if (LPR == 1 && !valid) return;
-    const int rr = valid ? row : r0;
-    const int64_t base = sptr[rr >> 5] + (rr & 31);
-    const T s = sell_row_group<LPR, true>(base, valid ? (int)rlen[rr] : 0, lane, scol, sval, x,
-                                          valid ? b[rr] : T(0));
-    if (valid && lane == 0) x[row] = s * dinv[row];
+// ---------------------------------------------------------------------------
+// V-cycle passes
+//
+// Row updates gather their neighbour values in unrolled batches: a lane first
+// loads the column indices and values of up to kUnroll of its entries, then
+// all the neighbour values, then does the FMAs.  On the coarse levels, where a
+// pass is a few thousand rows, the kernel time is the length of its chain of
+// dependent loads, and batching cuts that chain to three round trips.
+//
+// Neighbour values come in three forms:
+//   kNbrX        x_j for positions j < jmax; positions >= jmax hold rows of
+//                later colours, which are still zero during the forward sweep
+//                of pre-smoothing, and are skipped;
+//   kNbrFirst    b_j / A_jj for j < jmax: the colour-0 values of the first
+//                pass from a zero guess, recomputed instead of read back;
+//   kNbrProlong  x_j + omega t_j e_agg(j): the post-smoothing of a two-colour
+//                level reads the prolongated values of the other colour
+//                without writing them (the next pass overwrites that colour).
+// ---------------------------------------------------------------------------
+enum NbrMode : int { kNbrX = 0, kNbrFirst = 1, kNbrProlong = 2 };
+
+constexpr int kUnroll = 8;
+
+template <int LPR, int MODE, bool SCALED, typename T>
+__device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jmax,
+                                        const int32_t* __restrict__ scol,
+                                        const T* __restrict__ sval, const T* x,
+                                        const T* __restrict__ b, const T* __restrict__ dinv,
+                                        const int32_t* __restrict__ agg, const T* __restrict__ t,
+                                        const T* __restrict__ e, T omega, T acc) {
+    T s = lane == 0 ? acc : T(0);
+    for (int k0 = lane; k0 < len; k0 += LPR * kUnroll) {
+        int j[kUnroll];
+        T a[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int k = k0 + u * LPR;
+            j[u] = -1;
+            a[u] = T(0);
+            if (k < len) {
+                const int64_t ee = base + 32 * (int64_t)k;
+                const int jj = scol[ee];
+                if (jj < jmax) {
+                    j[u] = jj;
+                    a[u] = sval[ee];
+                }
+            }
+        }
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            v[u] = T(0);
+            if (j[u] >= 0) {
+                if (MODE == kNbrFirst) {
+                    v[u] = b[j[u]] * dinv[j[u]];
+                } else {
+                    v[u] = x[j[u]];
+                    if (MODE == kNbrProlong) {
+                        const int ag = agg[j[u]];
+                        if (ag >= 0) v[u] = fmad(SCALED ? omega * t[j[u]] : omega, e[ag], v[u]);
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (j[u] >= 0) s = fmad(-a[u], v[u], s);
+    }
+    return group_sum<LPR>(s);
 }
 
-// First Gauss-Seidel pass from a zero initial guess: the rows of colour 0
-// [0, c1) have only zero neighbours, so x_i = b_i / A_ii there, and every other
-// row starts at 0 (no matrix entries are read).
-template <typename T>
-__global__ void __launch_bounds__(kBlock) k_gs_first(int c1, int n, const T* __restrict__ dinv,
-                                                     const T* __restrict__ b, T* __restrict__ x) {
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    if (row >= n) return;
-    x[row] = row < c1 ? b[row] * dinv[row] : T(0);
+// Rows handled by a launch: LPR lanes per row, rows from r0 rounded down to a
+// slice boundary so that warps read whole slices.
+template <int LPR>
+struct RowOf {
+    int row, lane;
+    bool valid;
+    __device__ RowOf(int r0, int r1) {
+        const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        row = (r0 & ~31) + (int)(tt / LPR);
+        lane = (int)(tt % LPR);
+        valid = row >= r0 && row < r1;
+    }
+};
+
+// Fused first two forward passes of the pre-smoother from a zero initial
+// guess: rows of colour 0 ([0, c1)) have only zero neighbours, so
+// x_i = b_i / A_ii; rows of colour 1 ([c1, c2)) see colour-0 neighbours (their
+// new values b_j / A_jj) and zeros.  Optionally zeroes the next level's
+// right-hand side for the fused residual-restriction kernel.
+template <int LPR, typename T>
+__global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, const int64_t* __restrict__ sptr,
+                                                  const uint16_t* __restrict__ rlen,
+                                                  const int32_t* __restrict__ scol,
+                                                  const T* __restrict__ sval,
+                                                  const T* __restrict__ dinv,
+                                                  const T* __restrict__ b, T* __restrict__ x,
+                                                  T* __restrict__ bc_zero, int nc) {
+    if (bc_zero)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+            bc_zero[i] = T(0);
+    const RowOf<LPR> R(0, c2);
+    if (LPR == 1 && !R.valid) return;
+    const int rr = R.valid ? R.row : 0;
+    // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
+    // lane of the warp still reaches the shuffles of the group sum
+    const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
+    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const T s = row_update<LPR, kNbrFirst, false, T>(base, len, R.lane, c1, scol, sval, x, b, dinv,
+                                                     nullptr, nullptr, nullptr, T(0),
+                                                     R.valid ? b[rr] : T(0));
+    if (R.valid && R.lane == 0) x[rr] = s * dinv[rr];
+}
+
+// One Gauss-Seidel update of the rows [r0, r1) of one colour:
+//   x_i = (b_i - sum_{j != i, j < jmax} A_ij x_j) / A_ii.
+// Rows of one colour are not coupled, so they update in parallel.
+template <int LPR, int MODE, bool SCALED, typename T>
+__global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
+                                                    const int64_t* __restrict__ sptr,
+                                                    const uint16_t* __restrict__ rlen,
+                                                    const int32_t* __restrict__ scol,
+                                                    const T* __restrict__ sval,
+                                                    const T* __restrict__ dinv,
+                                                    const T* __restrict__ b, T* x,
+                                                    const int32_t* __restrict__ agg,
+                                                    const T* __restrict__ t,
+                                                    const T* __restrict__ e, T omega) {
+    const RowOf<LPR> R(r0, r1);
+    if (LPR == 1 && !R.valid) return;
+    const int rr = R.valid ? R.row : r0;
+    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)rlen[rr] : 0, R.lane, jmax,
+                                                 scol, sval, x, b, dinv, agg, t, e, omega,
+                                                 R.valid ? b[rr] : T(0));
+    if (R.valid && R.lane == 0) x[rr] = s * dinv[rr];
 }
 
 // r = b - A x for rows [r0, n)
@@ -195,22 +282,63 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_
                                                      const T* __restrict__ diag,
                                                      const T* __restrict__ b,
                                                      const T* __restrict__ x, T* __restrict__ r) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int row = (r0 & ~31) + (int)(t / LPR);
-    const int lane = (int)(t % LPR);
-    const bool valid = row >= r0 && row < n;
-    if (LPR == 1 && !valid) return;
-    const int rr = valid ? row : r0;
+    const RowOf<LPR> R(r0, n);
+    if (LPR == 1 && !R.valid) return;
+    const int rr = R.valid ? R.row : r0;
     const int64_t base = sptr[rr >> 5] + (rr & 31);
-    const T s0 = valid ? fmad(-diag[rr], x[rr], b[rr]) : T(0);
-    const T v = sell_row_group<LPR, true>(base, valid ? (int)rlen[rr] : 0, lane, scol, sval, x, s0);
-    if (valid && lane == 0) r[row] = v;
+    const T s0 = R.valid ? fmad(-diag[rr], x[rr], b[rr]) : T(0);
+    const T v = row_update<LPR, kNbrX, false, T>(base, R.valid ? (int)rlen[rr] : 0, R.lane, n, scol,
+                                                 sval, x, nullptr, nullptr, nullptr, nullptr,
+                                                 nullptr, T(0), s0);
+    if (R.valid && R.lane == 0) r[rr] = v;
+}
+
+// Residual and restriction in one pass (one thread per row): rows of colour
+// >= 1 ([c1, n)) are sorted by coarse index inside their colour, so the rows
+// of one aggregate are consecutive.  A warp sums (t_i) r_i over runs of equal
+// coarse index with a segmented shuffle scan and the last row of each run adds
+// the run's sum to bc (zeroed by the first pass).  A run never spans more than
+// two warps, so a coarse entry receives at most two additions onto zero, whose
+// result does not depend on their order: the sum stays deterministic.
+template <typename T, bool SCALED>
+__global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
+                                                              const int64_t* __restrict__ sptr,
+                                                              const uint16_t* __restrict__ rlen,
+                                                              const int32_t* __restrict__ scol,
+                                                              const T* __restrict__ sval,
+                                                              const T* __restrict__ diag,
+                                                              const T* __restrict__ b,
+                                                              const T* __restrict__ x,
+                                                              const int32_t* __restrict__ agg,
+                                                              const T* __restrict__ t,
+                                                              T* __restrict__ bc) {
+    const RowOf<1> R(c1, n);
+    int key = -1;
+    T v = T(0);
+    if (R.valid) {
+        const int rr = R.row;
+        const int64_t base = sptr[rr >> 5] + (rr & 31);
+        const T s0 = fmad(-diag[rr], x[rr], b[rr]);
+        const T ri = row_update<1, kNbrX, false, T>(base, rlen[rr], 0, n, scol, sval, x, nullptr,
+                                                    nullptr, nullptr, nullptr, nullptr, T(0), s0);
+        key = agg[rr];
+        v = SCALED ? t[rr] * ri : ri;
+    }
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T vo = __shfl_up_sync(0xffffffffu, v, off);
+        const int ko = __shfl_up_sync(0xffffffffu, key, off);
+        if (lane >= off && ko == key) v += vo;
+    }
+    const int knext = __shfl_down_sync(0xffffffffu, key, 1);
+    if (key >= 0 && (lane == 31 || knext != key)) atomicAdd(bc + key, v);
 }
 
 // coarse right-hand side: bc_J = sum over the fine rows i of aggregate J of
-// (t_i) r_i, summed in the stored order (Eq. prolongation: R = P^T).  The lists
-// hold the rows of colour >= 1 only: the pre-smoother's last pass updates
-// colour 0, whose residual is therefore zero.
+// (t_i) r_i, in the stored order (Eq. prolongation: R = P^T).  The lists hold
+// the rows of colour >= 1 only: the pre-smoother's last pass updates colour 0,
+// whose residual is therefore zero.
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __restrict__ rptr,
                                                      const int32_t* __restrict__ ridx,
@@ -218,16 +346,25 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __re
                                                      const T* __restrict__ r, T* __restrict__ bc) {
     const int J = blockIdx.x * blockDim.x + threadIdx.x;
     if (J >= nc) return;
+    const int k1 = rptr[J + 1];
     T s = T(0);
-    for (int k = rptr[J]; k < rptr[J + 1]; ++k) {
-        const int i = ridx[k];
-        s = SCALED ? fmad(t[i], r[i], s) : s + r[i];
+    for (int k0 = rptr[J]; k0 < k1; k0 += kUnroll) {
+        int i[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) i[u] = (k0 + u < k1) ? ridx[k0 + u] : -1;
+        T v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            v[u] = i[u] >= 0 ? (SCALED ? t[i[u]] * r[i[u]] : r[i[u]]) : T(0);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+            if (i[u] >= 0) s += v[u];
     }
     bc[J] = s;
 }
 
-// x_i += omega (t_i) e_{agg(i)}: piecewise-constant prolongation with the
-// over-correction factor omega, on rows [r0, n).  The caller passes r0 = the
+// x_i += omega (t_i) e_{agg(i)} on rows [r0, n): piecewise-constant
+// prolongation with the over-correction factor omega.  Callers pass r0 = the
 // first row of colour 1: the post-smoother's first pass recomputes colour 0
 // without reading its old values.
 template <typename T, bool SCALED>
@@ -239,8 +376,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int r0, int n, const int32_t
     if (i >= n) return;
     const int a = agg[i];
     if (a < 0) return;
-    const T c = SCALED ? omega * t[i] : omega;
-    x[i] += c * e[a];
+    x[i] = fmad(SCALED ? omega * t[i] : omega, e[a], x[i]);
 }
 
 // x = M b, M dense row-major (coarsest-level solve with the inverse formed at
@@ -402,7 +538,9 @@ int reduction_blocks(int64_t work_threads) {
     return (int)std::min<int64_t>(b, g_reduction_blocks);
 }
 
-inline int row_blocks(int r0, int r1, int lpr) { return blocks_for((int64_t)(r1 - (r0 & ~31)) * lpr); }
+inline int row_blocks(int r0, int r1, int lpr) {
+    return blocks_for((int64_t)(r1 - (r0 & ~31)) * lpr);
+}
 
 #define AMG_LPR_DISPATCH(lpr, CALL)                          \
     switch (lpr) {                                           \
@@ -411,62 +549,102 @@ inline int row_blocks(int r0, int r1, int lpr) { return blocks_for((int64_t)(r1 
         default: { constexpr int LPR = 8; CALL; } break;     \
     }
 
-void launch_gs(const DevLevel& L, int r0, int r1, const double* b, double* x, cudaStream_t s) {
+template <typename T>
+struct LevelArrays;
+template <>
+struct LevelArrays<double> {
+    const double *sval, *dinv, *diag, *t;
+    explicit LevelArrays(const DevLevel& L) : sval(L.sval), dinv(L.dinv), diag(L.diag), t(nullptr) {}
+};
+template <>
+struct LevelArrays<float> {
+    const float *sval, *dinv, *diag, *t;
+    explicit LevelArrays(const DevLevel& L) : sval(L.sval32), dinv(L.dinv32), diag(L.diag32), t(L.t32) {}
+};
+
+template <typename T>
+void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStream_t s) {
+    const LevelArrays<T> A(L);
+    const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
+    AMG_LPR_DISPATCH(L.lpr, (k_first<LPR, T><<<std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s>>>(
+                                c1, c2, L.sptr, L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero, nc)));
+}
+
+template <typename T, int MODE>
+void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* e, double omega,
+               cudaStream_t s) {
+    const LevelArrays<T> A(L);
+    const int r0 = L.cptr[col], r1 = L.cptr[col + 1];
     if (r1 <= r0) return;
-    AMG_LPR_DISPATCH(L.lpr, (k_gs<LPR, double><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
-                                r0, r1, L.sptr, L.rlen, L.scol, L.sval, L.dinv, b, x)));
+    constexpr bool SC = std::is_same<T, float>::value;
+    AMG_LPR_DISPATCH(L.lpr, (k_gs_pass<LPR, MODE, SC, T><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
+                                r0, r1, jmax, L.sptr, L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg,
+                                A.t, e, (T)omega)));
 }
 
-void launch_gs32(const DevLevel& L, int r0, int r1, const float* b, float* x, cudaStream_t s) {
-    if (r1 <= r0) return;
-    AMG_LPR_DISPATCH(L.lpr, (k_gs<LPR, float><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
-                                r0, r1, L.sptr, L.rlen, L.scol, L.sval32, L.dinv32, b, x)));
+template <typename T>
+void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* bc,
+                            cudaStream_t s) {
+    const LevelArrays<T> A(L);
+    const int c1 = L.cptr[1];
+    constexpr bool SC = std::is_same<T, float>::value;
+    if (L.fused_restrict) {
+        if (L.n > c1)
+            k_residual_restrict<T, SC><<<row_blocks(c1, L.n, 1), kBlock, 0, s>>>(
+                c1, L.n, L.sptr, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg, A.t, bc);
+        return;
+    }
+    if (L.n > c1)
+        AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, T><<<row_blocks(c1, L.n, LPR), kBlock, 0, s>>>(
+                                    c1, L.n, L.sptr, L.rlen, L.scol, A.sval, A.diag, b, x, r)));
+    k_restrict<T, SC><<<blocks_for(L.n_coarse), kBlock, 0, s>>>(L.n_coarse, L.rptr, L.ridx, A.t, r,
+                                                                bc);
 }
 
-void launch_residual(const DevLevel& L, int r0, const double* b, const double* x, double* r,
-                     cudaStream_t s) {
+template <typename T>
+void prolong_impl(const DevLevel& L, const T* e, T* x, double omega, cudaStream_t s) {
+    const LevelArrays<T> A(L);
+    const int r0 = L.cptr[1];
     if (L.n <= r0) return;
-    AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, double><<<row_blocks(r0, L.n, LPR), kBlock, 0, s>>>(
-                                r0, L.n, L.sptr, L.rlen, L.scol, L.sval, L.diag, b, x, r)));
+    constexpr bool SC = std::is_same<T, float>::value;
+    k_prolong<T, SC><<<blocks_for(L.n - r0), kBlock, 0, s>>>(r0, L.n, L.agg, A.t, e, x, (T)omega);
 }
 
-void launch_residual32(const DevLevel& L, int r0, const float* b, const float* x, float* r,
-                       cudaStream_t s) {
-    if (L.n <= r0) return;
-    AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, float><<<row_blocks(r0, L.n, LPR), kBlock, 0, s>>>(
-                                r0, L.n, L.sptr, L.rlen, L.scol, L.sval32, L.diag32, b, x, r)));
+void launch_first(const DevLevel& L, const double* b, double* x, double* bc_zero, int nc,
+                  cudaStream_t s) {
+    first_impl<double>(L, b, x, bc_zero, nc, s);
 }
-
-void launch_restrict(const DevLevel& L, const double* r, double* bc, cudaStream_t s) {
-    k_restrict<double, false><<<blocks_for(L.n_coarse), kBlock, 0, s>>>(L.n_coarse, L.rptr, L.ridx,
-                                                                        nullptr, r, bc);
+void launch_first32(const DevLevel& L, const float* b, float* x, float* bc_zero, int nc,
+                    cudaStream_t s) {
+    first_impl<float>(L, b, x, bc_zero, nc, s);
 }
-
-void launch_restrict32(const DevLevel& L, const float* r, float* bc, cudaStream_t s) {
-    k_restrict<float, true><<<blocks_for(L.n_coarse), kBlock, 0, s>>>(L.n_coarse, L.rptr, L.ridx,
-                                                                      L.t32, r, bc);
+void launch_pass(const DevLevel& L, int col, int jmax, const double* b, double* x, cudaStream_t s) {
+    pass_impl<double, kNbrX>(L, col, jmax, b, x, nullptr, 0.0, s);
 }
-
+void launch_pass32(const DevLevel& L, int col, int jmax, const float* b, float* x, cudaStream_t s) {
+    pass_impl<float, kNbrX>(L, col, jmax, b, x, nullptr, 0.0, s);
+}
+void launch_pass_prolong(const DevLevel& L, const double* b, double* x, const double* e,
+                         double omega, cudaStream_t s) {
+    pass_impl<double, kNbrProlong>(L, 0, L.n, b, x, e, omega, s);
+}
+void launch_pass_prolong32(const DevLevel& L, const float* b, float* x, const float* e,
+                           double omega, cudaStream_t s) {
+    pass_impl<float, kNbrProlong>(L, 0, L.n, b, x, e, omega, s);
+}
+void launch_residual_restrict(const DevLevel& L, const double* b, const double* x, double* r,
+                              double* bc, cudaStream_t s) {
+    residual_restrict_impl<double>(L, b, x, r, bc, s);
+}
+void launch_residual_restrict32(const DevLevel& L, const float* b, const float* x, float* r,
+                                float* bc, cudaStream_t s) {
+    residual_restrict_impl<float>(L, b, x, r, bc, s);
+}
 void launch_prolong(const DevLevel& L, const double* e, double* x, double omega, cudaStream_t s) {
-    const int r0 = L.cptr[1];
-    if (L.n <= r0) return;
-    k_prolong<double, false><<<blocks_for(L.n - r0), kBlock, 0, s>>>(r0, L.n, L.agg, nullptr, e, x,
-                                                                     omega);
+    prolong_impl<double>(L, e, x, omega, s);
 }
-
-void launch_prolong32(const DevLevel& L, const float* e, float* x, float omega, cudaStream_t s) {
-    const int r0 = L.cptr[1];
-    if (L.n <= r0) return;
-    k_prolong<float, true><<<blocks_for(L.n - r0), kBlock, 0, s>>>(r0, L.n, L.agg, L.t32, e, x,
-                                                                   omega);
-}
-
-void launch_gs_first(const DevLevel& L, const double* b, double* x, cudaStream_t s) {
-    k_gs_first<double><<<blocks_for(L.n), kBlock, 0, s>>>(L.cptr[1], L.n, L.dinv, b, x);
-}
-
-void launch_gs_first32(const DevLevel& L, const float* b, float* x, cudaStream_t s) {
-    k_gs_first<float><<<blocks_for(L.n), kBlock, 0, s>>>(L.cptr[1], L.n, L.dinv32, b, x);
+void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega, cudaStream_t s) {
+    prolong_impl<float>(L, e, x, omega, s);
 }
 
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s) {

@@ -64,47 +64,74 @@ std::vector<int32_t> smoothing_order(const HostLevel& h) {
     return perm;
 }
 
-// Gauss-Seidel pass over m rows with z off-diagonal entries: CSR values and
-// indices, row pointers, 1/A_ii, b and the written x of those rows, and every
-// neighbour value of x once.
-double gs_bytes(const DevLevel& L, int col, int vb) {
+// Modelled (algorithmic) DRAM bytes of the V-cycle passes: every stored entry
+// and vector element a pass needs is counted once; neighbour values gathered
+// several times are counted once (they are served from cache).  v = bytes of a
+// value, 4 per index, 2 per row length.
+
+// colour pass over the m rows of colour col (z entries) reading neighbour
+// values at positions < jmax: entries, lengths, b, 1/A_ii, x written, and the
+// neighbour values once
+double pass_bytes(const DevLevel& L, int col, int jmax, int vb) {
     const double m = L.cptr[col + 1] - L.cptr[col];
     const double z = (double)L.cnnz[col];
-    return z * (vb + 4) + m * (2 + 3.0 * vb) + std::min(z, (double)L.n - m) * vb;
+    const double nb = std::min(z, (double)jmax - (jmax > L.cptr[col] ? m : 0.0));
+    return z * (vb + 4) + m * (2 + 3.0 * vb) + std::max(0.0, nb) * vb;
 }
-// residual on the rows of colour >= 1: their entries, lengths, diagonal, b,
-// own x and written r, and every neighbour value once
-double residual_bytes(const DevLevel& L, int vb) {
+// fused first two forward passes: colour 0 reads b and 1/A_ii and writes x;
+// colour 1 reads its entries, b, 1/A_ii, writes x (colour-0 b and 1/A_ii are
+// already counted); the next level's right-hand side is zeroed when the
+// restriction is fused
+double first_bytes(const DevLevel& L, int vb) {
+    const double c1 = L.cptr[1];
+    const double m1 = L.ncolours > 1 ? L.cptr[2] - L.cptr[1] : 0.0;
+    const double z1 = L.ncolours > 1 ? (double)L.cnnz[1] : 0.0;
+    return c1 * 3.0 * vb + z1 * (vb + 4) + m1 * (2 + 3.0 * vb) +
+           (L.fused_restrict ? (double)L.n_coarse * vb : 0.0);
+}
+// colour 0 of a two-colour level with on-the-fly prolongation: its entries,
+// b, 1/A_ii, written x, and once per colour-1 row its x, coarse index (and
+// transfer weight), plus the coarse correction
+double pass_prolong_bytes(const DevLevel& L, int vb, bool scaled) {
+    const double m0 = L.cptr[1], m1 = L.n - L.cptr[1];
+    return (double)L.cnnz[0] * (vb + 4) + m0 * (2 + 3.0 * vb) +
+           m1 * (vb + 4 + (scaled ? 4 : 0)) + (double)L.n_coarse * vb;
+}
+// residual of the rows of colour >= 1 and restriction: entries, lengths, A_ii,
+// b, own x, colour-0 neighbour values once, then either the coarse index (and
+// weight) and one atomic add per aggregate (fused) or the written r, the
+// restriction lists, r again and the coarse right-hand side
+double residual_restrict_bytes(const DevLevel& L, int vb, bool scaled) {
     const double m = L.n - L.cptr[1];
     const double z = (double)(L.nnz_off - L.cnnz[0]);
-    return z * (vb + 4) + m * (2 + 4.0 * vb) + std::min(z, (double)L.cptr[1]) * vb;
-}
-
-double restrict_bytes(const DevLevel& L, int vb, bool scaled) {
-    const double m = L.n - L.cptr[1];
-    return m * (4 + vb + (scaled ? 4 : 0)) + 4.0 * (L.n_coarse + 1) + (double)L.n_coarse * vb;
+    const double core = z * (vb + 4) + m * (2 + 3.0 * vb) + std::min(z, (double)L.cptr[1]) * vb;
+    if (L.fused_restrict) return core + m * (4 + (scaled ? 4 : 0)) + (double)L.n_coarse * 2 * vb;
+    return core + m * vb + m * (4 + vb + (scaled ? 4 : 0)) + 4.0 * (L.n_coarse + 1) +
+           (double)L.n_coarse * vb;
 }
 double prolong_bytes(const DevLevel& L, int vb, bool scaled) {
     const double m = L.n - L.cptr[1];
     return m * (4 + 2.0 * vb + (scaled ? 4 : 0)) + (double)L.n_coarse * vb;
 }
-// first pass from a zero guess: b and 1/A_ii of colour 0, x written everywhere
-double first_pass_bytes(const DevLevel& L, int vb) {
-    return (double)L.cptr[1] * 2.0 * vb + (double)L.n * vb;
-}
 
-// modelled DRAM bytes of one V-cycle on a level: the sum of its passes (first
-// pass from zero, 2 (2C - 1) - 1 colour passes, residual, restriction,
-// prolongation);
-// the coarsest level reads its dense inverse once
+// modelled bytes of one V-cycle on a level, following the pass sequence of
+// vcycle64/vcycle32; the coarsest level reads its dense inverse once
 double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb) {
     if (coarsest) return (double)L.n * L.n * 8.0 + 2.0 * L.n * vb;
-    double t = first_pass_bytes(L, vb);
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int col = pass == 0 ? 1 : 0; col < L.ncolours; ++col) t += gs_bytes(L, col, vb);
-        for (int col = L.ncolours - 2; col >= 0; --col) t += gs_bytes(L, col, vb);
+    const bool scaled = vb == 4;
+    const int C = L.ncolours;
+    double t = first_bytes(L, vb);
+    for (int col = 2; col < C; ++col) t += pass_bytes(L, col, L.cptr[col], vb);
+    for (int col = C - 2; col >= 0; --col) t += pass_bytes(L, col, L.n, vb);
+    t += residual_restrict_bytes(L, vb, scaled);
+    if (C == 2) {
+        t += pass_prolong_bytes(L, vb, scaled) + pass_bytes(L, 1, L.n, vb) + pass_bytes(L, 0, L.n, vb);
+    } else {
+        t += prolong_bytes(L, vb, scaled);
+        for (int col = 0; col < C; ++col) t += pass_bytes(L, col, L.n, vb);
+        for (int col = C - 2; col >= 0; --col) t += pass_bytes(L, col, L.n, vb);
     }
-    return t + residual_bytes(L, vb) + restrict_bytes(L, vb, vb == 4) + prolong_bytes(L, vb, vb == 4);
+    return t;
 }
 
 void fill_info(amg_ctx* c) {
@@ -153,14 +180,15 @@ void fill_info(amg_ctx* c) {
 const char* kKindNames[kKNumKinds] = {
     "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
     "coarse_solve", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
-    "zero", "permute"};
+    "zero", "permute", "graph_cg_part", "graph_vcycle_part", "graph_coarse_levels"};
 
 struct ProfScope {
     amg_ctx* c;
     int idx = -1;
-    ProfScope(amg_ctx* c_, int kind, double bytes) : c(c_) {
+    ProfScope(amg_ctx* c_, int kind, double bytes, bool graph_level = false) : c(c_) {
         Profiler& P = c->prof;
-        if (!P.on || P.next + 2 > (int)P.events.size()) return;
+        const bool rec = graph_level ? P.graphs : P.on;
+        if (!rec || P.next + 2 > (int)P.events.size()) return;
         idx = P.next;
         P.next += 2;
         cudaEventRecord(P.events[idx], c->stream);
@@ -175,87 +203,108 @@ struct ProfScope {
 // V-cycle (Sec. 2): pre-smooth, restrict the residual, recurse, prolongate
 // with omega, post-smooth; dense solve on the coarsest level
 // ---------------------------------------------------------------------------
-void gs64(amg_ctx* c, const DevLevel& L, int col, const double* b, double* x) {
-    ProfScope ps(c, &L == &c->dl[0] ? kKGsL0 : kKGsCoarse, gs_bytes(L, col, 8));
-    launch_gs(L, L.cptr[col], L.cptr[col + 1], b, x, c->stream);
-}
+// One V-cycle on level l in precision T (double: FP64 path; float: the scaled
+// float32 levels).  Pass sequence on a level with C colours:
+//   pre   first (colours 0 and 1 from zero), colours 2..C-1 forward reading
+//         only earlier colours, colours C-2..0 backward;
+//   restrict the residual of colours >= 1 (colour 0 was smoothed last);
+//   recurse; then on two-colour levels colour 0 reads the prolongated values
+//         of colour 1 on the fly, followed by colour 1 and colour 0; on other
+//         levels x += omega P e on colours >= 1, then colours 0..C-1, C-2..0.
+template <typename T>
+struct Prec;
+template <>
+struct Prec<double> {
+    static double* x(DevLevel& L) { return L.x; }
+    static double* b(DevLevel& L) { return L.b; }
+    static double* r(DevLevel& L) { return L.r; }
+    static constexpr int vb = 8;
+};
+template <>
+struct Prec<float> {
+    static float* x(DevLevel& L) { return L.x32; }
+    static float* b(DevLevel& L) { return L.b32; }
+    static float* r(DevLevel& L) { return L.r32; }
+    static constexpr int vb = 4;
+};
 
-void sgs64(amg_ctx* c, const DevLevel& L, const double* b, double* x) {
-    for (int col = 0; col < L.ncolours; ++col) gs64(c, L, col, b, x);
-    for (int col = L.ncolours - 2; col >= 0; --col) gs64(c, L, col, b, x);
-}
+inline void k_first(const DevLevel& L, const double* b, double* x, double* bc, int nc, cudaStream_t s) { launch_first(L, b, x, bc, nc, s); }
+inline void k_first(const DevLevel& L, const float* b, float* x, float* bc, int nc, cudaStream_t s) { launch_first32(L, b, x, bc, nc, s); }
+inline void k_pass(const DevLevel& L, int col, int jmax, const double* b, double* x, cudaStream_t s) { launch_pass(L, col, jmax, b, x, s); }
+inline void k_pass(const DevLevel& L, int col, int jmax, const float* b, float* x, cudaStream_t s) { launch_pass32(L, col, jmax, b, x, s); }
+inline void k_pass_prolong(const DevLevel& L, const double* b, double* x, const double* e, double w, cudaStream_t s) { launch_pass_prolong(L, b, x, e, w, s); }
+inline void k_pass_prolong(const DevLevel& L, const float* b, float* x, const float* e, double w, cudaStream_t s) { launch_pass_prolong32(L, b, x, e, w, s); }
+inline void k_resres(const DevLevel& L, const double* b, const double* x, double* r, double* bc, cudaStream_t s) { launch_residual_restrict(L, b, x, r, bc, s); }
+inline void k_resres(const DevLevel& L, const float* b, const float* x, float* r, float* bc, cudaStream_t s) { launch_residual_restrict32(L, b, x, r, bc, s); }
+inline void k_prolong(const DevLevel& L, const double* e, double* x, double w, cudaStream_t s) { launch_prolong(L, e, x, w, s); }
+inline void k_prolong(const DevLevel& L, const float* e, float* x, double w, cudaStream_t s) { launch_prolong32(L, e, x, w, s); }
+inline void k_coarsest(amg_ctx* c, const double* b, double* x) { launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream); }
+inline void k_coarsest(amg_ctx* c, const float* b, float* x) { launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream); }
 
-void vcycle64(amg_ctx* c, int l, const double* b, double* x) {
+template <typename T>
+void vcycle(amg_ctx* c, int l, const T* b, T* x) {
+    using P = Prec<T>;
+    constexpr int vb = P::vb;
+    constexpr bool scaled = vb == 4;
     const int nlev = (int)c->dl.size();
     DevLevel& L = c->dl[l];
+    cudaStream_t s = c->stream;
     if (l == nlev - 1) {
-        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 16.0 * c->nL);
-        launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream);
+        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 2.0 * vb * c->nL);
+        k_coarsest(c, b, x);
         return;
     }
-    DevLevel& C = c->dl[l + 1];
+    DevLevel& N = c->dl[l + 1];
+    const int C = L.ncolours;
+    const int kind = l == 0 ? kKGsL0 : kKGsCoarse;
     {
-        ProfScope ps(c, l == 0 ? kKGsL0 : kKGsCoarse, first_pass_bytes(L, 8));
-        launch_gs_first(L, b, x, c->stream);
+        ProfScope ps(c, kind, first_bytes(L, vb));
+        k_first(L, b, x, L.fused_restrict ? P::b(N) : (T*)nullptr, N.n, s);
     }
-    for (int col = 1; col < L.ncolours; ++col) gs64(c, L, col, b, x);
-    for (int col = L.ncolours - 2; col >= 0; --col) gs64(c, L, col, b, x);
+    for (int col = 2; col < C; ++col) {
+        ProfScope ps(c, kind, pass_bytes(L, col, L.cptr[col], vb));
+        k_pass(L, col, L.cptr[col], b, x, s);
+    }
+    for (int col = C - 2; col >= 0; --col) {
+        ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+        k_pass(L, col, L.n, b, x, s);
+    }
     {
-        ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_bytes(L, 8));
-        launch_residual(L, L.cptr[1], b, x, L.r, c->stream);
+        ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_restrict_bytes(L, vb, scaled));
+        k_resres(L, b, x, P::r(L), P::b(N), s);
     }
-    {
-        ProfScope ps(c, kKRestrict, restrict_bytes(L, 8, false));
-        launch_restrict(L, L.r, C.b, c->stream);
-    }
-    vcycle64(c, l + 1, C.b, C.x);
-    {
-        ProfScope ps(c, kKProlong, prolong_bytes(L, 8, false));
-        launch_prolong(L, C.x, x, c->p.omega, c->stream);
-    }
-    sgs64(c, L, b, x);
-}
-
-void gs32(amg_ctx* c, const DevLevel& L, int col, const float* b, float* x) {
-    ProfScope ps(c, &L == &c->dl[0] ? kKGsL0 : kKGsCoarse, gs_bytes(L, col, 4));
-    launch_gs32(L, L.cptr[col], L.cptr[col + 1], b, x, c->stream);
-}
-
-void sgs32(amg_ctx* c, const DevLevel& L, const float* b, float* x) {
-    for (int col = 0; col < L.ncolours; ++col) gs32(c, L, col, b, x);
-    for (int col = L.ncolours - 2; col >= 0; --col) gs32(c, L, col, b, x);
-}
-
-void vcycle32(amg_ctx* c, int l, const float* b, float* x) {
-    const int nlev = (int)c->dl.size();
-    DevLevel& L = c->dl[l];
-    if (l == nlev - 1) {
-        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 8.0 * c->nL);
-        launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream);
+    vcycle<T>(c, l + 1, P::b(N), P::x(N));
+    if (C == 2) {
+        {
+            ProfScope ps(c, kind, pass_prolong_bytes(L, vb, scaled));
+            k_pass_prolong(L, b, x, P::x(N), c->p.omega, s);
+        }
+        {
+            ProfScope ps(c, kind, pass_bytes(L, 1, L.n, vb));
+            k_pass(L, 1, L.n, b, x, s);
+        }
+        {
+            ProfScope ps(c, kind, pass_bytes(L, 0, L.n, vb));
+            k_pass(L, 0, L.n, b, x, s);
+        }
         return;
     }
-    DevLevel& C = c->dl[l + 1];
     {
-        ProfScope ps(c, l == 0 ? kKGsL0 : kKGsCoarse, first_pass_bytes(L, 4));
-        launch_gs_first32(L, b, x, c->stream);
+        ProfScope ps(c, kKProlong, prolong_bytes(L, vb, scaled));
+        k_prolong(L, P::x(N), x, c->p.omega, s);
     }
-    for (int col = 1; col < L.ncolours; ++col) gs32(c, L, col, b, x);
-    for (int col = L.ncolours - 2; col >= 0; --col) gs32(c, L, col, b, x);
-    {
-        ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_bytes(L, 4));
-        launch_residual32(L, L.cptr[1], b, x, L.r32, c->stream);
+    for (int col = 0; col < C; ++col) {
+        ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+        k_pass(L, col, L.n, b, x, s);
     }
-    {
-        ProfScope ps(c, kKRestrict, restrict_bytes(L, 4, true));
-        launch_restrict32(L, L.r32, C.b32, c->stream);
+    for (int col = C - 2; col >= 0; --col) {
+        ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+        k_pass(L, col, L.n, b, x, s);
     }
-    vcycle32(c, l + 1, C.b32, C.x32);
-    {
-        ProfScope ps(c, kKProlong, prolong_bytes(L, 4, true));
-        launch_prolong32(L, C.x32, x, (float)c->p.omega, c->stream);
-    }
-    sgs32(c, L, b, x);
 }
+
+void vcycle64(amg_ctx* c, int l, const double* b, double* x) { vcycle<double>(c, l, b, x); }
+void vcycle32(amg_ctx* c, int l, const float* b, float* x) { vcycle<float>(c, l, b, x); }
 
 // z = B r on level 0 (smoothing order) in the context's precision
 void precondition(amg_ctx* c, const double* r, double* z) {
@@ -374,14 +423,36 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
         if (graphs && !gb) gb = capture_graph(c, part_b);
         while (true) {
             if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
-            if (graphs) AMG_CUDA_TRY(cudaGraphLaunch(ga, s));
-            else part_a();
+            if (graphs) {
+                ProfScope ps(c, kKGraphA, 0.0, true);
+                AMG_CUDA_TRY(cudaGraphLaunch(ga, s));
+            } else {
+                part_a();
+            }
             AMG_CUDA_TRY(cudaStreamSynchronize(s));
             if (c->sc_host->status != 0) { status = c->sc_host->status; break; }
             if (c->sc_host->done) break;
             if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
-            if (graphs) AMG_CUDA_TRY(cudaGraphLaunch(gb, s));
-            else part_b();
+            if (graphs) {
+                ProfScope ps(c, kKGraphB, 0.0, true);
+                AMG_CUDA_TRY(cudaGraphLaunch(gb, s));
+            } else {
+                part_b();
+            }
+        }
+        // graph-level profiling: time the levels >= 1 alone (diagnostic replays
+        // after the solve; they only rewrite coarse-level scratch vectors)
+        if (graphs && c->prof.graphs && c->dl.size() > 1) {
+            cudaGraphExec_t& gc = c->graph_coarse[c->precision];
+            if (!gc)
+                gc = capture_graph(c, [&] {
+                    if (c->precision == AMG_FP64) vcycle64(c, 1, c->dl[1].b, c->dl[1].x);
+                    else vcycle32(c, 1, c->dl[1].b32, c->dl[1].x32);
+                });
+            for (int rep = 0; rep < 10; ++rep) {
+                ProfScope ps(c, kKGraphCoarse, 0.0, true);
+                AMG_CUDA_TRY(cudaGraphLaunch(gc, s));
+            }
         }
     }
     AMG_CUDA_TRY(cudaGetLastError());
@@ -555,6 +626,11 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
             std::vector<int32_t> fill(rptr.begin(), rptr.end() - 1);
             for (int32_t r = L.cptr[1]; r < L.n; ++r)
                 if (aggp[r] >= 0) ridx[fill[aggp[r]]++] = r;
+        }
+        {
+            int32_t most = 0;
+            for (int32_t J = 0; J < nc; ++J) most = std::max(most, rptr[J + 1] - rptr[J]);
+            L.fused_restrict = L.lpr == 1 && most <= 32;
         }
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
@@ -827,7 +903,9 @@ int amg_profile_enable(amg_ctx* c, int32_t enable) {
             P.recs.clear();
             P.next = 0;
         }
-        P.on = enable != 0;
+        if (enable < 0 || enable > 2) throw Error{AMG_EINVAL, "enable must be 0, 1 or 2"};
+        P.on = enable == 1;
+        P.graphs = enable == 2;
     });
 }
 
