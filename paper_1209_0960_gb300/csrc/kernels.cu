@@ -293,9 +293,10 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_
     if (R.valid && R.lane == 0) r[rr] = v;
 }
 
-// Residual and restriction in one pass (one thread per row): rows of colour
-// >= 1 ([c1, n)) are sorted by coarse index inside their colour, so the rows
-// of one aggregate are consecutive.  A warp sums (t_i) r_i over runs of equal
+// Residual and restriction in one pass (one thread per row) on a two-colour
+// level: the rows of colour 1 ([c1, n)) are sorted by coarse index, so the rows
+// of one aggregate are consecutive (with more colours an aggregate would recur
+// in every colour block and a warp could see it twice).  A warp sums (t_i) r_i over runs of equal
 // coarse index with a segmented shuffle scan and the last row of each run adds
 // the run's sum to bc (zeroed by the first pass).  A run never spans more than
 // two warps, so a coarse entry receives at most two additions onto zero, whose

@@ -630,7 +630,9 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         {
             int32_t most = 0;
             for (int32_t J = 0; J < nc; ++J) most = std::max(most, rptr[J + 1] - rptr[J]);
-            L.fused_restrict = L.lpr == 1 && most <= 32;
+            // the fused kernel needs the rows of colour >= 1 to be one block
+            // sorted by coarse index (two colours) and runs shorter than a warp
+            L.fused_restrict = L.lpr == 1 && L.ncolours == 2 && most <= 32;
         }
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
