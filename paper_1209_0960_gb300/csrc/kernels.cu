@@ -158,6 +158,19 @@ enum NbrMode : int { kNbrX = 0, kNbrFirst = 1, kNbrProlong = 2 };
 
 constexpr int kUnroll = 8;
 
+template <int MODE, bool SCALED, typename T>
+__device__ __forceinline__ T nbr_value(int j, const T* x, const T* __restrict__ b,
+                                       const T* __restrict__ dinv, const int32_t* __restrict__ agg,
+                                       const T* __restrict__ t, const T* __restrict__ e, T omega) {
+    if (MODE == kNbrFirst) return b[j] * dinv[j];
+    T v = x[j];
+    if (MODE == kNbrProlong) {
+        const int ag = agg[j];
+        if (ag >= 0) v = fmad(SCALED ? omega * t[j] : omega, e[ag], v);
+    }
+    return v;
+}
+
 template <int LPR, int MODE, bool SCALED, typename T>
 __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jmax,
                                         const int32_t* __restrict__ scol,
@@ -165,6 +178,19 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jma
                                         const T* __restrict__ b, const T* __restrict__ dinv,
                                         const int32_t* __restrict__ agg, const T* __restrict__ t,
                                         const T* __restrict__ e, T omega, T acc) {
+    if (LPR == 1) {
+        // one thread per row (the fine level): a plain loop keeps the register
+        // count low, so enough warps stay resident to saturate DRAM
+        T s = acc;
+#pragma unroll 4
+        for (int k = 0; k < len; ++k) {
+            const int64_t ee = base + 32 * (int64_t)k;
+            const int j = scol[ee];
+            const T a = sval[ee];
+            if (j < jmax) s = fmad(-a, nbr_value<MODE, SCALED>(j, x, b, dinv, agg, t, e, omega), s);
+        }
+        return s;
+    }
     T s = lane == 0 ? acc : T(0);
     for (int k0 = lane; k0 < len; k0 += LPR * kUnroll) {
         int j[kUnroll];
@@ -172,36 +198,18 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jma
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int k = k0 + u * LPR;
-            j[u] = -1;
-            a[u] = T(0);
-            if (k < len) {
-                const int64_t ee = base + 32 * (int64_t)k;
-                const int jj = scol[ee];
-                if (jj < jmax) {
-                    j[u] = jj;
-                    a[u] = sval[ee];
-                }
-            }
+            const bool in = k < len;
+            const int64_t ee = base + 32 * (int64_t)(in ? k : 0);
+            j[u] = in ? scol[ee] : jmax;
+            a[u] = in ? sval[ee] : T(0);
         }
         T v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            v[u] = T(0);
-            if (j[u] >= 0) {
-                if (MODE == kNbrFirst) {
-                    v[u] = b[j[u]] * dinv[j[u]];
-                } else {
-                    v[u] = x[j[u]];
-                    if (MODE == kNbrProlong) {
-                        const int ag = agg[j[u]];
-                        if (ag >= 0) v[u] = fmad(SCALED ? omega * t[j[u]] : omega, e[ag], v[u]);
-                    }
-                }
-            }
-        }
+        for (int u = 0; u < kUnroll; ++u)
+            v[u] = j[u] < jmax ? nbr_value<MODE, SCALED>(j[u], x, b, dinv, agg, t, e, omega) : T(0);
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            if (j[u] >= 0) s = fmad(-a[u], v[u], s);
+            if (j[u] < jmax) s = fmad(-a[u], v[u], s);
     }
     return group_sum<LPR>(s);
 }
@@ -296,11 +304,12 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_
 // Residual and restriction in one pass (one thread per row) on a two-colour
 // level: the rows of colour 1 ([c1, n)) are sorted by coarse index, so the rows
 // of one aggregate are consecutive (with more colours an aggregate would recur
-// in every colour block and a warp could see it twice).  A warp sums (t_i) r_i over runs of equal
-// coarse index with a segmented shuffle scan and the last row of each run adds
-// the run's sum to bc (zeroed by the first pass).  A run never spans more than
-// two warps, so a coarse entry receives at most two additions onto zero, whose
-// result does not depend on their order: the sum stays deterministic.
+// in every colour block).  Each thread stores (t_i) r_i in shared memory; the
+// first row of every run of equal coarse index inside the block sums the run
+// in order and adds it to bc (zeroed by the first pass).  A run is shorter than
+// a block, so a coarse entry receives at most two additions onto zero (a run
+// cut by a block boundary), whose result does not depend on their order: the
+// sum stays deterministic.
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
                                                               const int64_t* __restrict__ sptr,
@@ -313,6 +322,8 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
                                                               const int32_t* __restrict__ agg,
                                                               const T* __restrict__ t,
                                                               T* __restrict__ bc) {
+    __shared__ T sv[kBlock];
+    __shared__ int sk[kBlock];
     const RowOf<1> R(c1, n);
     int key = -1;
     T v = T(0);
@@ -325,15 +336,14 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
         key = agg[rr];
         v = SCALED ? t[rr] * ri : ri;
     }
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const T vo = __shfl_up_sync(0xffffffffu, v, off);
-        const int ko = __shfl_up_sync(0xffffffffu, key, off);
-        if (lane >= off && ko == key) v += vo;
-    }
-    const int knext = __shfl_down_sync(0xffffffffu, key, 1);
-    if (key >= 0 && (lane == 31 || knext != key)) atomicAdd(bc + key, v);
+    const int tid = threadIdx.x;
+    sv[tid] = v;
+    sk[tid] = key;
+    __syncthreads();
+    if (key < 0 || (tid > 0 && sk[tid - 1] == key)) return;
+    T sum = v;
+    for (int u = tid + 1; u < kBlock && sk[u] == key; ++u) sum += sv[u];
+    atomicAdd(bc + key, sum);
 }
 
 // coarse right-hand side: bc_J = sum over the fine rows i of aggregate J of
