@@ -391,8 +391,8 @@ def run_ours(args, dist: Dist):
         "roofline": roofline,
         "kernels_fp64": prof64,
         "graph_parts_ms": {
-            "fp64": {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in graph64},
-            "fp32": {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in graph32}},
+            "fp64": {d["name"]: round(d["total_ms"] / max(1, d["launches"]), 4) for d in graph64},
+            "fp32": {d["name"]: round(d["total_ms"] / max(1, d["launches"]), 4) for d in graph32}},
         "gpu_launches": launches * args.steps,
         "e2e": e2e,
         "clocks": clk,

@@ -216,7 +216,7 @@ int amg_colour(const amg_csr *A, int32_t *colour, int32_t *ncolours);
  * launch costs a few microseconds more).  enable == 2 keeps the graphs and
  * brackets each graph launch instead ("graph_cg_part": SpMV and updates,
  * "graph_vcycle_part": V-cycle and direction update), and after every solve
- * replays the levels >= 1 of the V-cycle ten times ("graph_coarse_levels").
+ * replays the V-cycle from each level l >= 1 ten times ("graph_from_level_l").
  * enable == 0 stops recording.  Errors: AMG_EINVAL. */
 int amg_profile_enable(amg_ctx *c, int32_t enable);
 

@@ -138,7 +138,7 @@ struct Profiler {
 enum KernelKind : int {
     kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
     kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKGraphA, kKGraphB,
-    kKGraphCoarse, kKNumKinds
+    kKGraphFrom   // kKGraphFrom + l: V-cycle replayed from level l (graph profiling)
 };
 
 struct HostLevel {
@@ -266,7 +266,7 @@ struct amg_ctx {
     // alpha, x/r update, status copy; B = z = B r, beta, p update
     cudaGraphExec_t graph_a[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphExec_t graph_b[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
-    cudaGraphExec_t graph_coarse[2] = {nullptr, nullptr};   // levels >= 1 only (profiling)
+    std::vector<cudaGraphExec_t> graph_from[2];   // V-cycle from level l (profiling), per precision
     bool use_graphs = true;
     amg::DevArena mem;
     std::vector<amg::HostLevel> hl;
@@ -304,7 +304,8 @@ struct amg_ctx {
                 if (graph_b[a][b]) cudaGraphExecDestroy(graph_b[a][b]);
             }
         for (int a = 0; a < 2; ++a)
-            if (graph_coarse[a]) cudaGraphExecDestroy(graph_coarse[a]);
+            for (cudaGraphExec_t g : graph_from[a])
+                if (g) cudaGraphExecDestroy(g);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
         if (stream) {

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -177,10 +178,10 @@ void fill_info(amg_ctx* c) {
 // launch profiler: CUDA events around launches, grouped by kernel class, with
 // the modelled algorithmic DRAM bytes of each launch
 // ---------------------------------------------------------------------------
-const char* kKindNames[kKNumKinds] = {
+const char* kKindNames[kKGraphFrom] = {
     "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
     "coarse_solve", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
-    "zero", "permute", "graph_cg_part", "graph_vcycle_part", "graph_coarse_levels"};
+    "zero", "permute", "graph_cg_part", "graph_vcycle_part"};
 
 struct ProfScope {
     amg_ctx* c;
@@ -440,18 +441,22 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
                 part_b();
             }
         }
-        // graph-level profiling: time the levels >= 1 alone (diagnostic replays
-        // after the solve; they only rewrite coarse-level scratch vectors)
+        // graph-level profiling: time the V-cycle from each level l >= 1 alone
+        // (diagnostic replays after the solve; they rewrite only coarse-level
+        // scratch vectors, which the next V-cycle recomputes)
         if (graphs && c->prof.graphs && c->dl.size() > 1) {
-            cudaGraphExec_t& gc = c->graph_coarse[c->precision];
-            if (!gc)
-                gc = capture_graph(c, [&] {
-                    if (c->precision == AMG_FP64) vcycle64(c, 1, c->dl[1].b, c->dl[1].x);
-                    else vcycle32(c, 1, c->dl[1].b32, c->dl[1].x32);
-                });
-            for (int rep = 0; rep < 10; ++rep) {
-                ProfScope ps(c, kKGraphCoarse, 0.0, true);
-                AMG_CUDA_TRY(cudaGraphLaunch(gc, s));
+            auto& gv = c->graph_from[c->precision];
+            gv.resize(c->dl.size(), nullptr);
+            for (int l = 1; l < (int)c->dl.size(); ++l) {
+                if (!gv[l])
+                    gv[l] = capture_graph(c, [&] {
+                        if (c->precision == AMG_FP64) vcycle64(c, l, c->dl[l].b, c->dl[l].x);
+                        else vcycle32(c, l, c->dl[l].b32, c->dl[l].x32);
+                    });
+                for (int rep = 0; rep < 10; ++rep) {
+                    ProfScope ps(c, kKGraphFrom + l, 0.0, true);
+                    AMG_CUDA_TRY(cudaGraphLaunch(gv[l], s));
+                }
             }
         }
     }
@@ -916,10 +921,14 @@ int amg_profile_read(amg_ctx* c, amg_kernel_stat* stats, int32_t cap) {
     int rc = Guard::run([&] {
         if (!c || cap < 0 || (cap > 0 && !stats)) throw Error{AMG_EINVAL, "bad arguments"};
         AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-        std::vector<amg_kernel_stat> acc(kKNumKinds);
-        for (int k = 0; k < kKNumKinds; ++k) {
+        const int nk = kKGraphFrom + 64;
+        std::vector<amg_kernel_stat> acc(nk);
+        for (int k = 0; k < nk; ++k) {
             std::memset(&acc[k], 0, sizeof(amg_kernel_stat));
-            std::strncpy(acc[k].name, kKindNames[k], sizeof(acc[k].name) - 1);
+            if (k < kKGraphFrom)
+                std::strncpy(acc[k].name, kKindNames[k], sizeof(acc[k].name) - 1);
+            else
+                std::snprintf(acc[k].name, sizeof(acc[k].name), "graph_from_level_%d", k - kKGraphFrom);
         }
         for (const auto& r : c->prof.recs) {
             float ms = 0.f;
@@ -928,7 +937,7 @@ int amg_profile_read(amg_ctx* c, amg_kernel_stat* stats, int32_t cap) {
             acc[r.kind].total_ms += ms;
             acc[r.kind].bytes += r.bytes;
         }
-        for (int k = 0; k < kKNumKinds; ++k)
+        for (int k = 0; k < nk; ++k)
             if (acc[k].launches > 0) {
                 if (count < cap) stats[count] = acc[k];
                 ++count;
