@@ -179,6 +179,24 @@ int amg_pcg_solve_host(amg_ctx *c, const double *b_host, double *x_host, double 
  * Uses device scratch owned by the context.  Errors: AMG_EINVAL, AMG_ECUDA. */
 int amg_residual_norm(amg_ctx *c, const double *b_dev, const double *x_dev, double *out_norm);
 
+/* ||b - A x||_2 for a CSR matrix A held in device memory (A->on_device = 1),
+ * with b_dev, x_dev device float64 [n]; the result is written to the device
+ * double *norm_dev, asynchronously on cuda_stream (NULL = default stream).
+ * The paper has no counterpart: this is a service for callers that must not
+ * allocate device memory at the point of the call -- code running while a
+ * stream is captured into a CUDA graph (an allocation would break the
+ * capture), code called back from inside an allocator, or programs whose
+ * device memory is entirely owned by a pool they do not control.  It needs no
+ * context and calls no allocator: the partial sums of its deterministic
+ * reduction live in a fixed device array of 512 KiB that every GPU loading the
+ * library keeps until exit, which limits n to 16,777,216 rows (larger n:
+ * AMG_EINVAL).  The first call on each device looks up that array (do it
+ * before any stream capture).  All calls share the array: calls that overlap
+ * on the GPU race and must be serialised by the caller.
+ * Errors: AMG_EINVAL (null or host pointers, n out of range), AMG_ECUDA. */
+int amg_residual_norm_noalloc(const amg_csr *A, const double *b_dev, const double *x_dev,
+                              double *norm_dev, void *cuda_stream);
+
 /* Hierarchy description: *summary (may be NULL) and up to cap level records
  * (levels may be NULL when cap == 0).  Returns the number of levels
  * (>= 1) or a negative error. */

@@ -91,6 +91,7 @@ _SIGNATURES = {
     "amg_pcg_solve": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
     "amg_pcg_solve_host": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
     "amg_residual_norm": ([_c_vp, _c_vp, _c_vp, ctypes.POINTER(_c_dbl)], ctypes.c_int),
+    "amg_residual_norm_noalloc": ([ctypes.POINTER(amg_csr), _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_hierarchy_info": ([_c_vp, ctypes.POINTER(amg_summary), ctypes.POINTER(amg_level_info), _c_i32], ctypes.c_int),
     "amg_export_level": ([_c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_aggregate": ([ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
@@ -195,6 +196,17 @@ def amg_residual_norm(ctx: int, b_dev, x_dev) -> float:
     _check(lib().amg_residual_norm(ctx, _ptr(b_dev), _ptr(x_dev), ctypes.byref(out)),
            "amg_residual_norm")
     return out.value
+
+
+def amg_residual_norm_noalloc(row_ptr_dev, col_dev, val_dev, b_dev, x_dev, norm_dev,
+                              stream=None) -> None:
+    """||b - A x|| into the device tensor norm_dev (one float64) without any
+    allocation; A given as device CSR tensors (int32, int32, float64)."""
+    n = int(row_ptr_dev.shape[0]) - 1
+    A = amg_csr(n, int(col_dev.shape[0]), _ptr(row_ptr_dev), _ptr(col_dev), _ptr(val_dev), 1)
+    s = None if stream is None else int(stream.cuda_stream)
+    _check(lib().amg_residual_norm_noalloc(ctypes.byref(A), _ptr(b_dev), _ptr(x_dev), _ptr(norm_dev), s),
+           "amg_residual_norm_noalloc")
 
 
 def amg_hierarchy_info(ctx: int):
