@@ -137,6 +137,7 @@ struct Profiler {
 
 enum KernelKind : int {
     kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
+    kKFirstL0, kKPassProlongL0,
     kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKGraphA, kKGraphB,
     kKGraphFrom   // kKGraphFrom + l: V-cycle replayed from level l (graph profiling)
 };

@@ -192,7 +192,13 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jma
         return s;
     }
     T s = lane == 0 ? acc : T(0);
-    for (int k0 = lane; k0 < len; k0 += LPR * kUnroll) {
+    // every lane of the warp runs the same number of batches (the warp's
+    // longest row decides), so the warp-wide votes below see all 32 lanes
+    constexpr int per = LPR * kUnroll;
+    const int mine = len > lane ? (len - lane + per - 1) / per : 0;
+    const int batches = __reduce_max_sync(0xffffffffu, mine);
+    for (int it = 0; it < batches; ++it) {
+        const int k0 = lane + it * per;
         int j[kUnroll];
         T a[kUnroll];
 #pragma unroll
@@ -203,13 +209,18 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jma
             j[u] = in ? scol[ee] : jmax;
             a[u] = in ? sval[ee] : T(0);
         }
+        // slots past the longest row of the warp are skipped by a warp-uniform
+        // branch: a predicated-off float64 FMA would still occupy the pipe
         T v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            v[u] = j[u] < jmax ? nbr_value<MODE, SCALED>(j[u], x, b, dinv, agg, t, e, omega) : T(0);
+        for (int u = 0; u < kUnroll; ++u) {
+            v[u] = T(0);
+            if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax)
+                v[u] = nbr_value<MODE, SCALED>(j[u], x, b, dinv, agg, t, e, omega);
+        }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            if (j[u] < jmax) s = fmad(-a[u], v[u], s);
+            if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax) s = fmad(-a[u], v[u], s);
     }
     return group_sum<LPR>(s);
 }

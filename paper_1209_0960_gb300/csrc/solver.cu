@@ -180,7 +180,7 @@ void fill_info(amg_ctx* c) {
 // ---------------------------------------------------------------------------
 const char* kKindNames[kKGraphFrom] = {
     "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
-    "coarse_solve", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
+    "coarse_solve", "first_level0", "gs_prolong_level0", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
     "zero", "permute", "graph_cg_part", "graph_vcycle_part"};
 
 struct ProfScope {
@@ -259,7 +259,7 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     const int C = L.ncolours;
     const int kind = l == 0 ? kKGsL0 : kKGsCoarse;
     {
-        ProfScope ps(c, kind, first_bytes(L, vb));
+        ProfScope ps(c, l == 0 ? kKFirstL0 : kKGsCoarse, first_bytes(L, vb));
         k_first(L, b, x, L.fused_restrict ? P::b(N) : (T*)nullptr, N.n, s);
     }
     for (int col = 2; col < C; ++col) {
@@ -277,7 +277,7 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     vcycle<T>(c, l + 1, P::b(N), P::x(N));
     if (C == 2) {
         {
-            ProfScope ps(c, kind, pass_prolong_bytes(L, vb, scaled));
+            ProfScope ps(c, l == 0 ? kKPassProlongL0 : kKGsCoarse, pass_prolong_bytes(L, vb, scaled));
             k_pass_prolong(L, b, x, P::x(N), c->p.omega, s);
         }
         {
