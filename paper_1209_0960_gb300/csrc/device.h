@@ -109,7 +109,6 @@ struct DevLevel {
     double* sval = nullptr;           // [padded]
     double* diag = nullptr;           // [n]
     double* dinv = nullptr;           // [n] 1 / A_ii
-    int32_t* cptr_dev = nullptr;      // device copy of cptr
     int32_t* agg = nullptr;           // [n] permuted coarse index or -1
     int32_t* rptr = nullptr;          // [n_coarse+1] restriction lists
     int32_t* ridx = nullptr;          // fine rows of colour >= 1 of each coarse row
@@ -126,59 +125,6 @@ struct DevLevel {
     float* r32 = nullptr;
 };
 
-// ---------------------------------------------------------------------------
-// persistent kernels for the coarse levels (coarse.cu)
-// ---------------------------------------------------------------------------
-constexpr int kSmallBlock = 512;           // threads per CTA of the small-level cluster
-constexpr int kSmallSmem = 120 * 1024;     // dynamic shared memory requested: one CTA per SM
-
-// Level view read by the persistent kernels (device resident, one per level).
-template <typename T>
-struct LevelView {
-    int n, ncolours, n_coarse, lpr;
-    const int32_t* cptr;       // device copy of the colour block starts
-    const int64_t* sptr;
-    const uint16_t* rlen;
-    const int32_t* scol;
-    const T* sval;
-    const T* dinv;
-    const T* diag;
-    const int32_t* agg;
-    const int32_t* rptr;
-    const int32_t* ridx;
-    const T* t;                // transfer weights (float32 levels), else null
-    T* x;
-    T* b;
-    T* r;
-};
-
-// Grid barrier words of the cooperative kernel, each on its own 128-byte line.
-struct GridBarrier {
-    unsigned int arrive;
-    unsigned int pad0[31];
-    int err;
-    int pad1[31];
-};
-
-// Medium levels [lm0, ls) run in two cooperative launches per V-cycle (down,
-// up); small levels [ls, lc] (lc = coarsest) in one cluster launch.
-struct Persistent {
-    int lm0 = -1;
-    int ls = -1;
-    int lc = 0;
-    int coop_blocks = 0;
-    int cluster = 0;
-    LevelView<double>* lv64 = nullptr;
-    LevelView<float>* lv32 = nullptr;
-    GridBarrier* barrier = nullptr;
-};
-
-bool persistent_config(int sms, int& coop_blocks, int& cluster);
-void launch_medium64(const Persistent& P, int up, double omega, PcgScalars* sc, cudaStream_t s);
-void launch_medium32(const Persistent& P, int up, double omega, PcgScalars* sc, cudaStream_t s);
-void launch_small64(const Persistent& P, const double* M, double omega, cudaStream_t s);
-void launch_small32(const Persistent& P, const double* M, double omega, cudaStream_t s);
-
 // Launch profiler: events around launches, grouped by kernel class.
 struct Profiler {
     bool on = false;        // events around every launch (graphs off)
@@ -191,7 +137,7 @@ struct Profiler {
 
 enum KernelKind : int {
     kKGsL0 = 0, kKGsCoarse, kKResidualL0, kKResidualCoarse, kKRestrict, kKProlong, kKCoarseSolve,
-    kKFirstL0, kKPassProlongL0, kKMediumDown, kKMediumUp, kKSmall,
+    kKFirstL0, kKPassProlongL0,
     kKCgSpmv, kKCgUpdate, kKCgDot, kKCgP, kKConvert, kKZero, kKPermute, kKGraphA, kKGraphB,
     kKGraphFrom   // kKGraphFrom + l: V-cycle replayed from level l (graph profiling)
 };
@@ -327,7 +273,6 @@ struct amg_ctx {
     std::vector<amg::HostLevel> hl;
     std::vector<amg::DevLevel> dl;
     int32_t nL = 0;                   // coarsest size
-    amg::Persistent pers;             // persistent kernels for the coarse levels
     double* Ainv = nullptr;           // [nL x nL] inverse of the coarsest matrix
     double* Ainv_s = nullptr;         // [nL x nL] inverse of the scaled coarsest matrix
     double* isq0 = nullptr;           // [n] 1 / sqrt(A_ii) of level 0 (FP32 entry/exit)

@@ -135,12 +135,6 @@ double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb) {
     return t;
 }
 
-double levels_bytes(amg_ctx* c, int l0, int l1, int vb) {
-    double t = 0.0;
-    for (int l = l0; l <= l1; ++l) t += level_vcycle_bytes(c->dl[l], l == (int)c->dl.size() - 1, vb);
-    return t;
-}
-
 void fill_info(amg_ctx* c) {
     const int L = (int)c->dl.size();
     c->linfo.assign(L, amg_level_info{});
@@ -186,8 +180,7 @@ void fill_info(amg_ctx* c) {
 // ---------------------------------------------------------------------------
 const char* kKindNames[kKGraphFrom] = {
     "gs_level0", "gs_coarse", "residual_level0", "residual_coarse", "restrict", "prolong",
-    "coarse_solve", "first_level0", "gs_prolong_level0", "medium_levels_down",
-    "medium_levels_up", "small_levels", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
+    "coarse_solve", "first_level0", "gs_prolong_level0", "cg_spmv_dot", "cg_update_dot", "cg_dot", "cg_p_update", "convert",
     "zero", "permute", "graph_cg_part", "graph_vcycle_part"};
 
 struct ProfScope {
@@ -211,99 +204,6 @@ struct ProfScope {
 // V-cycle (Sec. 2): pre-smooth, restrict the residual, recurse, prolongate
 // with omega, post-smooth; dense solve on the coarsest level
 // ---------------------------------------------------------------------------
-// ---------------------------------------------------------------------------
-// persistent kernels for the coarse levels
-// ---------------------------------------------------------------------------
-constexpr int32_t kSmallRows = 50000;    // up to this: the single-cluster kernel
-constexpr int32_t kMediumRows = 600000;  // up to this: the cooperative kernels
-
-template <typename T>
-LevelView<T> level_view(DevLevel& L) {
-    LevelView<T> v{};
-    v.n = L.n;
-    v.ncolours = L.ncolours;
-    v.n_coarse = L.n_coarse;
-    v.lpr = L.lpr;
-    v.cptr = L.cptr_dev;
-    v.sptr = L.sptr;
-    v.rlen = L.rlen;
-    v.scol = L.scol;
-    v.agg = L.agg;
-    v.rptr = L.rptr;
-    v.ridx = L.ridx;
-    if constexpr (std::is_same<T, float>::value) {
-        v.sval = L.sval32;
-        v.dinv = L.dinv32;
-        v.diag = L.diag32;
-        v.t = L.t32;
-        v.x = L.x32;
-        v.b = L.b32;
-        v.r = L.r32;
-    } else {
-        v.sval = L.sval;
-        v.dinv = L.dinv;
-        v.diag = L.diag;
-        v.t = nullptr;
-        v.x = L.x;
-        v.b = L.b;
-        v.r = L.r;
-    }
-    return v;
-}
-
-template <typename T>
-LevelView<T>* upload_views(amg_ctx* c) {
-    const int nlev = (int)c->dl.size();
-    std::vector<LevelView<T>> v(nlev);
-    for (int l = 0; l < nlev; ++l) v[l] = level_view<T>(c->dl[l]);
-    LevelView<T>* d = c->mem.alloc<LevelView<T>>(nlev);
-    AMG_CUDA_TRY(cudaMemcpyAsync(d, v.data(), sizeof(LevelView<T>) * nlev, cudaMemcpyHostToDevice, c->stream));
-    AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    return d;
-}
-
-void setup_persistent(amg_ctx* c, int sms) {
-    Persistent& P = c->pers;
-    P = Persistent{};
-    const int nlev = (int)c->dl.size();
-    if (nlev < 2) return;
-    int coop = 0, cluster = 0;
-    if (!persistent_config(sms, coop, cluster)) return;
-    int ls = -1, lm0 = -1;
-    for (int l = 1; l < nlev; ++l) {
-        if (lm0 < 0 && c->dl[l].n <= kMediumRows && c->dl[l].n > kSmallRows) lm0 = l;
-        if (c->dl[l].n <= kSmallRows) {
-            ls = l;
-            break;
-        }
-    }
-    if (ls < 0) return;
-    P.ls = ls;
-    P.lm0 = lm0;
-    P.lc = nlev - 1;
-    P.coop_blocks = coop;
-    P.cluster = cluster;
-    P.barrier = c->mem.alloc<GridBarrier>(1);
-    AMG_CUDA_TRY(cudaMemsetAsync(P.barrier, 0, sizeof(GridBarrier), c->stream));
-    P.lv64 = upload_views<double>(c);
-}
-
-void reset_barrier(amg_ctx* c) {
-    if (c->pers.barrier)
-        AMG_CUDA_TRY(cudaMemsetAsync(c->pers.barrier, 0, sizeof(GridBarrier), c->stream));
-}
-
-double levels_bytes(amg_ctx* c, int l0, int l1, int vb);
-
-inline void k_persistent(amg_ctx* c, int up, double*) {
-    launch_medium64(c->pers, up, c->p.omega, c->work.sc, c->stream);
-}
-inline void k_persistent(amg_ctx* c, int up, float*) {
-    launch_medium32(c->pers, up, c->p.omega, c->work.sc, c->stream);
-}
-inline void k_small_levels(amg_ctx* c, double*) { launch_small64(c->pers, c->Ainv, c->p.omega, c->stream); }
-inline void k_small_levels(amg_ctx* c, float*) { launch_small32(c->pers, c->Ainv_s, c->p.omega, c->stream); }
-
 // One V-cycle on level l in precision T (double: FP64 path; float: the scaled
 // float32 levels).  Pass sequence on a level with C colours:
 //   pre   first (colours 0 and 1 from zero), colours 2..C-1 forward reading
@@ -350,23 +250,6 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     const int nlev = (int)c->dl.size();
     DevLevel& L = c->dl[l];
     cudaStream_t s = c->stream;
-    const Persistent& PP = c->pers;
-    if (PP.ls >= 0 && l == (PP.lm0 >= 0 ? PP.lm0 : PP.ls)) {
-        T* tag = nullptr;
-        if (PP.lm0 >= 0) {
-            ProfScope ps(c, kKMediumDown, levels_bytes(c, PP.lm0, PP.ls - 1, vb) * 0.5);
-            k_persistent(c, 0, tag);
-        }
-        {
-            ProfScope ps(c, kKSmall, levels_bytes(c, PP.ls, PP.lc, vb));
-            k_small_levels(c, tag);
-        }
-        if (PP.lm0 >= 0) {
-            ProfScope ps(c, kKMediumUp, levels_bytes(c, PP.lm0, PP.ls - 1, vb) * 0.5);
-            k_persistent(c, 1, tag);
-        }
-        return;
-    }
     if (l == nlev - 1) {
         ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 2.0 * vb * c->nL);
         k_coarsest(c, b, x);
@@ -454,7 +337,6 @@ void ensure_fp32(amg_ctx* c) {
     c->Ainv_s = c->mem.alloc<double>((size_t)c->nL * c->nL);
     scale_inverse_device(c->nL, c->dl[nlev - 1].diag, c->Ainv, c->Ainv_s, c->stream);
     AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    if (c->pers.ls >= 0) c->pers.lv32 = upload_views<float>(c);
     c->fp32_ready = true;
 }
 
@@ -503,7 +385,6 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     init.maxit = maxit;
     *c->sc_host = init;
     AMG_CUDA_TRY(cudaMemcpyAsync(c->work.sc, c->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-    reset_barrier(c);
     launch_cg_residual(L0, c->bb, c->x, c->r, c->work, kRR0, nullptr, s);
     AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -722,8 +603,6 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         if (l == nlev - 1) {
             L.cptr = {0, L.n};
             L.ncolours = 0;
-            L.cptr_dev = c->mem.alloc<int32_t>(2);
-            upload(L.cptr_dev, L.cptr, s);
             continue;
         }
         L.ncolours = h.ncolours;
@@ -760,8 +639,6 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
             // sorted by coarse index (two colours) and runs shorter than a warp
             L.fused_restrict = L.lpr == 1 && L.ncolours == 2 && most <= 32;
         }
-        L.cptr_dev = c->mem.alloc<int32_t>(L.cptr.size());
-        upload(L.cptr_dev, L.cptr, s);
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
         L.ridx = c->mem.alloc<int32_t>(ridx.size());
@@ -809,7 +686,6 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     AMG_CUDA_TRY(cudaEventCreate(&c->ev1));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 
-    setup_persistent(c.get(), sms);
     c->flexible = prm->flexible_cg >= 0 ? prm->flexible_cg : (prm->precision == AMG_FP32_IN_FP64);
     c->precision = prm->precision;
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
@@ -876,8 +752,7 @@ int amg_vcycle(amg_ctx* c, const double* r_dev, double* z_dev) {
         if (!c || !r_dev || !z_dev) throw Error{AMG_EINVAL, "null argument"};
         const int n = c->dl[0].n;
         enter(c);
-        reset_barrier(c);
-        launch_scatter(n, c->perm0, r_dev, c->r, c->stream);
+            launch_scatter(n, c->perm0, r_dev, c->r, c->stream);
         precondition(c, c->r, c->z);
         launch_gather(n, c->perm0, c->z, z_dev, c->stream);
         AMG_CUDA_TRY(cudaGetLastError());
