@@ -87,23 +87,25 @@ struct PcgScalars {
 
 // One level of the hierarchy on the device.  Rows are stored in the level's
 // smoothing order: grouped by colour, inside a colour by coarse aggregate,
-// then by original index.  The off-diagonal part is kept in a sliced-ELL
-// layout with 32-row slices (SELL-32): the k-th off-diagonal entry of the rows
-// of slice s sits at sptr[s] + 32 k + (row mod 32), so a warp reading entry k
-// of its 32 rows reads 32 consecutive values.  Slices are padded to their
-// longest row (padding: column = the row itself, value 0); rlen holds the true
-// row lengths so the padding costs no arithmetic.  The diagonal is separate.
+// then by original index.  The off-diagonal part is kept in a sliced layout
+// with 32-row slices of one common width W (the level's longest row): the k-th
+// off-diagonal entry of row r sits at (r / 32) * 32 W + 32 k + (r mod 32), so
+// a warp reading entry k of its 32 rows reads 32 consecutive values and the
+// address needs no pointer load.  Padding entries point at the row itself with
+// value 0; rlen holds the true row lengths so the padding costs no arithmetic.
+// The diagonal is separate.
 struct DevLevel {
     int32_t n = 0;
     int64_t nnz_off = 0;              // true off-diagonal entries
-    int64_t padded = 0;               // entries of the padded SELL arrays
+    int64_t padded = 0;               // entries of the padded sliced arrays
+    int32_t width = 0;                // common slice width W (longest row)
+    int64_t sw = 0;                   // slice stride 32 W
     int32_t ncolours = 0;
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
     int32_t lpr = 1;                  // lanes per row of the row kernels (1, 4 or 8)
     bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 1)
-    int64_t* sptr = nullptr;          // [n/32 + 1] slice starts
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
     double* sval = nullptr;           // [padded]

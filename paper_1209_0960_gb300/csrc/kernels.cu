@@ -5,7 +5,9 @@
 //
 // Layout: every level stores its rows in the smoothing order (colour blocks,
 // then coarse aggregate, then original index), the off-diagonal part in the
-// SELL-32 layout described in device.h and the diagonal separately.  Row
+// sliced layout described in device.h (32-row slices of a common width, so
+// the address of an entry is arithmetic: no pointer load precedes it) and the
+// diagonal separately.  Row
 // kernels give one thread to a row: for each k the 32 threads of a warp read
 // entry k of their 32 rows from 32 consecutive addresses, and the row sum is a
 // chain of fused multiply-adds with no cross-lane reduction (GB300 executes
@@ -245,7 +247,7 @@ struct RowOf {
 // new values b_j / A_jj) and zeros.  Optionally zeroes the next level's
 // right-hand side for the fused residual-restriction kernel.
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, const int64_t* __restrict__ sptr,
+__global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, int64_t sw,
                                                   const uint16_t* __restrict__ rlen,
                                                   const int32_t* __restrict__ scol,
                                                   const T* __restrict__ sval,
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, const int64_t*
     // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
     // lane of the warp still reaches the shuffles of the group sum
     const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
-    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
     const T s = row_update<LPR, kNbrFirst, false, T>(base, len, R.lane, c1, scol, sval, x, b, dinv,
                                                      nullptr, nullptr, nullptr, T(0),
                                                      R.valid ? b[rr] : T(0));
@@ -273,7 +275,7 @@ __global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, const int64_t*
 // Rows of one colour are not coupled, so they update in parallel.
 template <int LPR, int MODE, bool SCALED, typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
-                                                    const int64_t* __restrict__ sptr,
+                                                    int64_t sw,
                                                     const uint16_t* __restrict__ rlen,
                                                     const int32_t* __restrict__ scol,
                                                     const T* __restrict__ sval,
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
     const RowOf<LPR> R(r0, r1);
     if (LPR == 1 && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
-    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
     const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)rlen[rr] : 0, R.lane, jmax,
                                                  scol, sval, x, b, dinv, agg, t, e, omega,
                                                  R.valid ? b[rr] : T(0));
@@ -294,7 +296,7 @@ __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
 
 // r = b - A x for rows [r0, n)
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_t* __restrict__ sptr,
+__global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
                                                      const uint16_t* __restrict__ rlen,
                                                      const int32_t* __restrict__ scol,
                                                      const T* __restrict__ sval,
@@ -304,7 +306,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_
     const RowOf<LPR> R(r0, n);
     if (LPR == 1 && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
-    const int64_t base = sptr[rr >> 5] + (rr & 31);
+    const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
     const T s0 = R.valid ? fmad(-diag[rr], x[rr], b[rr]) : T(0);
     const T v = row_update<LPR, kNbrX, false, T>(base, R.valid ? (int)rlen[rr] : 0, R.lane, n, scol,
                                                  sval, x, nullptr, nullptr, nullptr, nullptr,
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, const int64_
 // sum stays deterministic.
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
-                                                              const int64_t* __restrict__ sptr,
+                                                              int64_t sw,
                                                               const uint16_t* __restrict__ rlen,
                                                               const int32_t* __restrict__ scol,
                                                               const T* __restrict__ sval,
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
     T v = T(0);
     if (R.valid) {
         const int rr = R.row;
-        const int64_t base = sptr[rr >> 5] + (rr & 31);
+        const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
         const T s0 = fmad(-diag[rr], x[rr], b[rr]);
         const T ri = row_update<1, kNbrX, false, T>(base, rlen[rr], 0, n, scol, sval, x, nullptr,
                                                     nullptr, nullptr, nullptr, nullptr, T(0), s0);
@@ -447,7 +449,7 @@ __global__ void k_from_scaled32(int n, const float* __restrict__ zhat, const dou
 // ---------------------------------------------------------------------------
 
 // r = b - A x and ||r||^2 (grid-stride over rows)
-__global__ void __launch_bounds__(kBlock) k_cg_residual(int n, const int64_t* __restrict__ sptr,
+__global__ void __launch_bounds__(kBlock) k_cg_residual(int n, int64_t sw,
                                                         const uint16_t* __restrict__ rlen,
                                                         const int32_t* __restrict__ scol,
                                                         const double* __restrict__ sval,
@@ -460,7 +462,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_residual(int n, const int64_t* __
     __shared__ double sh[kBlock / 32];
     double acc = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
-        const int64_t base = sptr[row >> 5] + (row & 31);
+        const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double s0 = fmad(-diag[row], x[row], b[row]);
         const double v = sell_row<true>(base, rlen[row], scol, sval, x, s0);
         if (r) r[row] = v;
@@ -471,7 +473,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_residual(int n, const int64_t* __
 }
 
 // q = A p and p.q -> alpha
-__global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, const int64_t* __restrict__ sptr,
+__global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, int64_t sw,
                                                        const uint16_t* __restrict__ rlen,
                                                        const int32_t* __restrict__ scol,
                                                        const double* __restrict__ sval,
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, const int64_t* __r
     __shared__ double sh[kBlock / 32];
     double acc = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
-        const int64_t base = sptr[row >> 5] + (row & 31);
+        const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double pi = p[row];
         const double v = sell_row<false>(base, rlen[row], scol, sval, p, diag[row] * pi);
         q[row] = v;
@@ -589,7 +591,7 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
     AMG_LPR_DISPATCH(L.lpr, (k_first<LPR, T><<<std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s>>>(
-                                c1, c2, L.sptr, L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero, nc)));
+                                c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero, nc)));
 }
 
 template <typename T, int MODE>
@@ -600,7 +602,7 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* 
     if (r1 <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
     AMG_LPR_DISPATCH(L.lpr, (k_gs_pass<LPR, MODE, SC, T><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
-                                r0, r1, jmax, L.sptr, L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg,
+                                r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg,
                                 A.t, e, (T)omega)));
 }
 
@@ -613,12 +615,12 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
     if (L.fused_restrict) {
         if (L.n > c1)
             k_residual_restrict<T, SC><<<row_blocks(c1, L.n, 1), kBlock, 0, s>>>(
-                c1, L.n, L.sptr, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg, A.t, bc);
+                c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg, A.t, bc);
         return;
     }
     if (L.n > c1)
         AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, T><<<row_blocks(c1, L.n, LPR), kBlock, 0, s>>>(
-                                    c1, L.n, L.sptr, L.rlen, L.scol, A.sval, A.diag, b, x, r)));
+                                    c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, r)));
     k_restrict<T, SC><<<blocks_for(L.n_coarse), kBlock, 0, s>>>(L.n_coarse, L.rptr, L.ridx, A.t, r,
                                                                 bc);
 }
@@ -695,13 +697,13 @@ void launch_from_scaled32(int n, const float* zhat, const double* isq, double* z
 
 void launch_cg_residual(const DevLevel& L, const double* b, const double* x, double* r,
                         CgWork& w, int mode, double* out, cudaStream_t s) {
-    k_cg_residual<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sptr, L.rlen, L.scol, L.sval,
+    k_cg_residual<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sw, L.rlen, L.scol, L.sval,
                                                            L.diag, b, x, r, w.partials,
                                                            w.counters, w.sc, out, mode);
 }
 
 void launch_cg_spmv_pq(const DevLevel& L, const double* p, double* q, CgWork& w, cudaStream_t s) {
-    k_cg_spmv_pq<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sptr, L.rlen, L.scol, L.sval,
+    k_cg_spmv_pq<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sw, L.rlen, L.scol, L.sval,
                                                           L.diag, p, q, w.partials,
                                                           w.counters + 1, w.sc);
 }

@@ -112,13 +112,11 @@ __global__ void k_reorder_rows(int n, const int32_t* __restrict__ inv, const int
 // Scatter the off-diagonal CSR rows into the SELL-32 arrays; padding entries
 // point at the row itself with value 0.
 __global__ void k_csr_to_sell(int n, const int32_t* __restrict__ nrp, const int32_t* __restrict__ nci,
-                              const double* __restrict__ nva, const int64_t* __restrict__ sptr,
+                              const double* __restrict__ nva, int width,
                               int32_t* __restrict__ scol, double* __restrict__ sval) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n) return;
-    const int64_t s0 = sptr[r >> 5], s1 = sptr[(r >> 5) + 1];
-    const int width = (int)((s1 - s0) >> 5);
-    const int64_t base = s0 + (r & 31);
+    const int64_t base = (int64_t)(r >> 5) * 32 * width + (r & 31);
     const int k0 = nrp[r], len = nrp[r + 1] - k0;
     for (int k = 0; k < width; ++k) {
         const int64_t e = base + 32 * (int64_t)k;
@@ -206,7 +204,7 @@ __global__ void k_scale_inverse(int n, const double* __restrict__ diag, const do
 
 // float32 level: A^ = S^-1 A S^-1 (off-diagonal, diagonal and its inverse),
 // and the transfer weights t_i = s_i / s_coarse(agg(i)).
-__global__ void k_level_fp32(int n, const int64_t* __restrict__ sptr, const int32_t* __restrict__ scol,
+__global__ void k_level_fp32(int n, int width, const int32_t* __restrict__ scol,
                              const double* __restrict__ sval, const double* __restrict__ diag,
                              const int32_t* __restrict__ agg, const double* __restrict__ cdiag,
                              float* __restrict__ sval32, float* __restrict__ diag32,
@@ -214,9 +212,7 @@ __global__ void k_level_fp32(int n, const int64_t* __restrict__ sptr, const int3
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double si = sqrt(diag[i]);
-    const int64_t s0 = sptr[i >> 5], s1 = sptr[(i >> 5) + 1];
-    const int width = (int)((s1 - s0) >> 5);
-    const int64_t base = s0 + (i & 31);
+    const int64_t base = (int64_t)(i >> 5) * 32 * width + (i & 31);
     for (int k = 0; k < width; ++k) {
         const int64_t e = base + 32 * (int64_t)k;
         sval32[e] = (float)(sval[e] / (si * sqrt(diag[scol[e]])));
@@ -322,16 +318,13 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
         nrp[r + 1] = nrp[r] + len;
     }
     const int32_t nslices = (n + 31) / 32;
-    std::vector<int64_t> sptr(nslices + 1, 0);
-    for (int32_t sl = 0; sl < nslices; ++sl) {
-        int w = 0;
-        for (int32_t r = sl * 32; r < std::min(n, sl * 32 + 32); ++r) w = std::max<int>(w, rlen[r]);
-        sptr[sl + 1] = sptr[sl] + 32 * (int64_t)w;
-    }
+    int width = 0;
+    for (int32_t r = 0; r < n; ++r) width = std::max<int>(width, rlen[r]);
     L.n = n;
     L.nnz_off = nrp[n];
-    L.padded = sptr[nslices];
-    L.sptr = arena.alloc<int64_t>(nslices + 1);
+    L.width = width;
+    L.sw = 32 * (int64_t)width;
+    L.padded = (int64_t)nslices * L.sw;
     L.rlen = arena.alloc<uint16_t>(n);
     L.scol = arena.alloc<int32_t>(L.padded);
     L.sval = arena.alloc<double>(L.padded);
@@ -346,11 +339,10 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
     AMG_CUDA_TRY(cudaMemcpyAsync(d_inv, inv.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(d_nrp, nrp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice, s));
-    AMG_CUDA_TRY(cudaMemcpyAsync(L.sptr, sptr.data(), sizeof(int64_t) * (nslices + 1), cudaMemcpyHostToDevice, s));
     AMG_CUDA_TRY(cudaMemcpyAsync(L.rlen, rlen.data(), sizeof(uint16_t) * n, cudaMemcpyHostToDevice, s));
     k_reorder_rows<<<blocks_for(n), kBlock, 0, s>>>(n, d_inv, d_perm, A.rp, A.ci, A.va, d_nrp, d_nci,
                                                     d_nva, L.diag, L.dinv);
-    k_csr_to_sell<<<blocks_for(n), kBlock, 0, s>>>(n, d_nrp, d_nci, d_nva, L.sptr, L.scol, L.sval);
+    k_csr_to_sell<<<blocks_for(n), kBlock, 0, s>>>(n, d_nrp, d_nci, d_nva, width, L.scol, L.sval);
     AMG_CUDA_TRY(cudaGetLastError());
     // lanes per row: one on sparse rows (float64 arithmetic bound), several on
     // the denser coarse rows (gather latency bound)
@@ -395,7 +387,7 @@ void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, c
     L.x32 = arena.alloc<float>(n);
     L.b32 = arena.alloc<float>(n);
     L.r32 = arena.alloc<float>(n);
-    k_level_fp32<<<blocks_for(n), kBlock, 0, s>>>(n, L.sptr, L.scol, L.sval, L.diag, L.agg, coarse_diag,
+    k_level_fp32<<<blocks_for(n), kBlock, 0, s>>>(n, L.width, L.scol, L.sval, L.diag, L.agg, coarse_diag,
                                                   L.sval32, L.diag32, L.dinv32, L.t32);
     AMG_CUDA_TRY(cudaGetLastError());
 }
