@@ -76,9 +76,9 @@ typedef struct {
     int32_t s_min;            /* Algorithm 1 minimum aggregate size; default 2^dim */
     int32_t s_max;            /* Algorithm 1 maximum aggregate size; default 3*2^(dim-1) */
     int32_t d_max;            /* Algorithm 2 diameter limit; default dim */
-    int32_t coarsen_target;   /* stop coarsening at <= this many rows; default 1000 */
+    int32_t coarsen_target;   /* stop coarsening at <= this many rows; default 5000 */
     int32_t max_levels;       /* default 20 */
-    int32_t dense_cap;        /* largest coarsest level solved densely; default 4096 */
+    int32_t dense_cap;        /* largest coarsest level solved densely; default 8192 */
     double min_coarsen_rate;  /* stop when n_l / n_{l+1} < this; default 1.2 */
     int32_t precision;        /* AMG_FP64 or AMG_FP32_IN_FP64 */
     int32_t flexible_cg;      /* -1: standard CG for FP64, flexible for FP32; 0 / 1 force */

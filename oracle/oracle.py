@@ -24,12 +24,12 @@ _lib = None
 
 # Default parameters of the reading documented in the oracle source:
 # delta = 1/3, beta = 1e-5, omega = 1.6, s_min = 2^d, s_max = 3 * 2^(d-1),
-# d_max = d, coarsening target 1000 rows, at most 20 levels, dense coarsest
-# solve up to 4096 rows, stop when n_l / n_{l+1} < 1.2.
+# d_max = d, coarsening target 5000 rows, at most 20 levels, dense coarsest
+# solve up to 8192 rows, stop when n_l / n_{l+1} < 1.2.
 def default_params(dim: int) -> dict:
     return dict(delta=1.0 / 3.0, beta=1e-5, omega=1.6,
                 s_min=2 ** dim, s_max=3 * 2 ** (dim - 1), d_max=dim,
-                coarsen_target=1000, max_levels=20, dense_cap=4096, min_rate=1.2)
+                coarsen_target=5000, max_levels=20, dense_cap=8192, min_rate=1.2)
 
 
 _ORDER = ["delta", "beta", "omega", "s_min", "s_max", "d_max",

@@ -174,23 +174,43 @@ __global__ void k_chol_col(int n, int j, double* __restrict__ L) {
     if (lane == 0) L[(size_t)i * n + j] = (ri[j] - s) / rj[j];
 }
 
-// Column c of the inverse: forward L y = e_c, then backward L^T x = y.
-// X is row-major with the column index fastest, so a warp's threads (columns
-// c..c+31) access consecutive addresses.
-__global__ void k_chol_inverse(int n, const double* __restrict__ L, double* __restrict__ X) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
-    for (int i = 0; i < n; ++i) {
-        double s = (i == c) ? 1.0 : 0.0;
+// U = L^T (row access to the columns of L in the backward substitution)
+__global__ void k_transpose(int n, const double* __restrict__ L, double* __restrict__ U) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n * n) return;
+    const int i = (int)(t / n), j = (int)(t % n);
+    U[(size_t)j * n + i] = L[t];
+}
+
+// Column c of the inverse, one warp per column: forward L y = e_c (y_k = 0
+// for k < c), then backward L^T x = y, with the column held in shared memory;
+// the lanes split each inner product.
+__global__ void k_chol_inverse(int n, const double* __restrict__ L, const double* __restrict__ U,
+                               double* __restrict__ X) {
+    extern __shared__ double y[];
+    const int c = blockIdx.x;
+    const int lane = threadIdx.x;
+    for (int k = lane; k < n; k += 32) y[k] = 0.0;
+    __syncwarp();
+    for (int i = c; i < n; ++i) {
         const double* li = L + (size_t)i * n;
-        for (int k = c; k < i; ++k) s -= li[k] * X[(size_t)k * n + c];
-        X[(size_t)i * n + c] = (i < c) ? 0.0 : s / li[i];
+        double s = 0.0;
+        for (int k = c + lane; k < i; k += 32) s = __fma_rn(li[k], y[k], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y[i] = ((i == c) ? 1.0 - s : -s) / li[i];
+        __syncwarp();
     }
     for (int i = n - 1; i >= 0; --i) {
-        double s = X[(size_t)i * n + c];
-        for (int k = i + 1; k < n; ++k) s -= L[(size_t)k * n + i] * X[(size_t)k * n + c];
-        X[(size_t)i * n + c] = s / L[(size_t)i * n + i];
+        const double* ui = U + (size_t)i * n;
+        double s = 0.0;
+        for (int k = i + 1 + lane; k < n; k += 32) s = __fma_rn(ui[k], y[k], s);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+        if (lane == 0) y[i] = (y[i] - s) / ui[i];
+        __syncwarp();
     }
+    for (int k = lane; k < n; k += 32) X[(size_t)k * n + c] = y[k];
 }
 
 // Minv_s = S Minv S with S = diag(sqrt(A_ii)): the inverse of S^-1 A S^-1
@@ -364,7 +384,12 @@ bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
         if (j + 1 < n) k_chol_col<<<blocks_for((int64_t)(n - j - 1) * 32), kBlock, 0, s>>>(n, j, L);
     }
     AMG_CUDA_TRY(cudaGetLastError());
-    k_chol_inverse<<<blocks_for(n, 32), 32, 0, s>>>(n, L, Minv);
+    double* U = tmp.alloc<double>((size_t)n * n);
+    k_transpose<<<blocks_for((int64_t)n * n), kBlock, 0, s>>>(n, L, U);
+    const size_t smem = sizeof(double) * (size_t)n;
+    if (smem > 48 * 1024)
+        AMG_CUDA_TRY(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_chol_inverse<<<n, 32, smem, s>>>(n, L, U, Minv);
     AMG_CUDA_TRY(cudaGetLastError());
     int herr = 0;
     AMG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));

@@ -717,9 +717,9 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->s_min = 1 << dim;
     p->s_max = 3 * (1 << (dim - 1));
     p->d_max = dim;
-    p->coarsen_target = 1000;
+    p->coarsen_target = 5000;
     p->max_levels = 20;
-    p->dense_cap = 4096;
+    p->dense_cap = 8192;
     p->min_coarsen_rate = 1.2;
     p->precision = AMG_FP64;
     p->flexible_cg = -1;

@@ -32,11 +32,14 @@ def _oracle_params(prm, **kw):
     return d
 
 
+# small coarsening targets keep these small cases multi-level; one case runs
+# with the library defaults
 CASES = {
-    "laplace2d_64": (lambda: P.laplace2d_random_rhs(64), {}),
+    "laplace2d_64": (lambda: P.laplace2d_random_rhs(64), {"coarsen_target": 200}),
     "lognormal_28x24x20": (lambda: P.lognormal3d((28, 24, 20), seed=1), {}),
-    "layered_20x20x24": (lambda: P.layered3d((20, 20, 24), seed=3), {}),
-    "anisotropic_18": (lambda: P.anisotropic3d((18, 18, 18), seed=2), {}),
+    "lognormal_28x24x20_3lev": (lambda: P.lognormal3d((28, 24, 20), seed=1), {"coarsen_target": 300}),
+    "layered_20x20x24": (lambda: P.layered3d((20, 20, 24), seed=3), {"coarsen_target": 200}),
+    "anisotropic_18": (lambda: P.anisotropic3d((18, 18, 18), seed=2), {"coarsen_target": 200}),
     "lognormal_deep_16": (lambda: P.lognormal3d((16, 16, 16), seed=5), {"coarsen_target": 12}),
 }
 
@@ -169,7 +172,7 @@ def test_errors_are_reported_not_crashed():
     with pytest.raises(amg.AmgError) as e:
         amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=10_000, dense_cap=100)
     assert e.value.code == amg.AMG_EINVAL
-    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=100)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=1e-14, maxit=2)
     assert rc == amg.AMG_ENOTCONV and info["iterations"] == 2
@@ -186,7 +189,7 @@ def test_full_size_lognormal_128():
     p = P.lognormal3d((128, 128, 128), seed=0)
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3)
     summary, levels = solver.info()
-    assert 4 <= summary["num_levels"] <= 8
+    assert 3 <= summary["num_levels"] <= 8
     # level 0 aggregation: every row aggregated, coarsening rate, Galerkin row sums
     l0 = solver.level(0)
     agg = l0["agg"]
