@@ -50,6 +50,8 @@ def parse_args():
                     help="cells per axis of the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--launch-overlap", type=int, choices=[0, 1], default=1,
+                    help="programmatic dependent launch between solve kernels")
     return ap.parse_args()
 
 
@@ -267,7 +269,8 @@ def run_ours(args, dist: Dist):
     stream = torch.cuda.current_stream()
     p = make_problem(args.grid)
     t0 = time.perf_counter()
-    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
+                     launch_overlap=args.launch_overlap)
     setup_wall = time.perf_counter() - t0
     summary, levels = solver.info()
     b = torch.from_numpy(p.b).cuda()
@@ -397,7 +400,7 @@ def run_ours(args, dist: Dist):
         "config": {"workload": WORKLOAD, "grid": args.grid, "unknowns": p.n, "nnz": p.nnz,
                    "tol": args.tol, "l2": "inputs larger than L2 (level-0 matrix "
                    f"{(p.nnz * 12 + 4 * p.n) / 1e6:.0f} MB > 129 MB)",
-                   "parallelism": f"replicas x{dist.world}"},
+                   "parallelism": f"replicas x{dist.world}", "launch_overlap": args.launch_overlap},
         "iterations": info64["iterations"],
         "true_rel_residual": info64["true_rel_residual"],
         "fp32_in_fp64": {"ms": ms32, "iterations": info32["iterations"],

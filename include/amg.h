@@ -83,6 +83,11 @@ typedef struct {
     int32_t precision;        /* AMG_FP64 or AMG_FP32_IN_FP64 */
     int32_t flexible_cg;      /* -1: standard CG for FP64, flexible for FP32; 0 / 1 force */
     void *cuda_stream;        /* cudaStream_t for all work; NULL = default stream */
+    int32_t launch_overlap;   /* 1 (default): consecutive solve kernels use programmatic
+                                 dependent launch (a kernel starts while its predecessor
+                                 drains and reads only setup-time data until the
+                                 predecessor has finished); 0: plain stream order.
+                                 Results are identical either way. */
 } amg_params;
 
 typedef struct {

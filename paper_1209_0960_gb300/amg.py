@@ -45,7 +45,7 @@ class amg_params(ctypes.Structure):
                 ("s_min", _c_i32), ("s_max", _c_i32), ("d_max", _c_i32),
                 ("coarsen_target", _c_i32), ("max_levels", _c_i32), ("dense_cap", _c_i32),
                 ("min_coarsen_rate", _c_dbl), ("precision", _c_i32), ("flexible_cg", _c_i32),
-                ("cuda_stream", _c_vp)]
+                ("cuda_stream", _c_vp), ("launch_overlap", _c_i32)]
 
 
 class amg_solve_info(ctypes.Structure):

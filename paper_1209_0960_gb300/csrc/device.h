@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "amg.h"
@@ -179,6 +180,33 @@ struct CgWork {
     unsigned int* counters = nullptr; // one per reduction kernel, self-resetting
     PcgScalars* sc = nullptr;
 };
+
+// Solve-phase launches.  With programmatic dependent launch (PDL) a kernel
+// may begin while its stream predecessor is still running: every solve kernel
+// signals its dependents as soon as it starts and, before it reads anything a
+// solve kernel writes (vectors, CG scalars, counters) or writes anything,
+// waits (griddepcontrol.wait) until all its predecessors have finished and
+// their writes are visible.  What it does before the wait reads only
+// matrices and index lists fixed at setup, so the overlap hides launch
+// latency and the first dependent loads of each kernel.  Set per calling
+// thread from the context at API entry.
+extern thread_local bool t_launch_overlap;
+
+template <typename... KArgs, typename... Args>
+void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                   Args&&... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = t_launch_overlap ? 1 : 0;
+    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+}
 
 extern int g_reduction_blocks;        // grid of the reduction kernels (SMs x 8)
 int reduction_blocks(int64_t work_threads);

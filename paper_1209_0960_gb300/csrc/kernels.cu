@@ -38,6 +38,21 @@ __device__ __forceinline__ T group_sum(T s) {
 __device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// programmatic dependent launch: let the next kernel of the stream start, and
+// wait for every predecessor to finish (both are no-ops without the launch
+// attribute)
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// load of setup-time per-row data (length, diagonal): evict-first on the
+// streamed fine level
+template <bool STREAM, typename T>
+__device__ __forceinline__ T ldm(const T* p) {
+    return STREAM ? __ldcs(p) : *p;
+}
+
 // acc + sgn * sum_k A_row,k x_col(k) over the stored off-diagonal entries of a
 // SELL-32 row (base = slice start + row mod 32)
 template <bool NEG, typename T, typename X>
@@ -46,8 +61,8 @@ __device__ __forceinline__ T sell_row(int64_t base, int len, const int32_t* __re
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
         const int64_t e = base + 32 * (int64_t)k;
-        const T a = sval[e];
-        acc = fmad(NEG ? -a : a, T(x[scol[e]]), acc);
+        const T a = __ldcs(sval + e);
+        acc = fmad(NEG ? -a : a, T(x[__ldcs(scol + e)]), acc);
     }
     return acc;
 }
@@ -161,9 +176,9 @@ enum NbrMode : int { kNbrX = 0, kNbrFirst = 1, kNbrProlong = 2 };
 constexpr int kUnroll = 8;
 
 template <int MODE, bool SCALED, typename T>
-__device__ __forceinline__ T nbr_value(int j, const T* x, const T* __restrict__ b,
+__device__ __forceinline__ T nbr_value(int j, const T* x, const T* b,
                                        const T* __restrict__ dinv, const int32_t* __restrict__ agg,
-                                       const T* __restrict__ t, const T* __restrict__ e, T omega) {
+                                       const T* __restrict__ t, const T* e, T omega) {
     if (MODE == kNbrFirst) return b[j] * dinv[j];
     T v = x[j];
     if (MODE == kNbrProlong) {
@@ -173,36 +188,42 @@ __device__ __forceinline__ T nbr_value(int j, const T* x, const T* __restrict__ 
     return v;
 }
 
-template <int LPR, int MODE, bool SCALED, typename T>
-__device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jmax,
+// The row sum starts from acc(), which reads vectors of the solve: it and all
+// neighbour values are read after pdl_wait().  With several lanes per row the
+// first batch of column indices and values (setup-time data) is loaded before
+// it, so those loads overlap the predecessor kernel.  The fine level (one
+// lane per row) streams its matrix with evict-first loads: it is read once
+// per pass and is larger than L2, and keeping it out of L2 leaves the
+// coarse levels resident there from one V-cycle to the next.
+template <int LPR, int MODE, bool SCALED, typename T, typename AccF>
+__device__ __forceinline__ T row_update(int64_t base, int len, int width, int lane, int jmax,
                                         const int32_t* __restrict__ scol,
                                         const T* __restrict__ sval, const T* x,
-                                        const T* __restrict__ b, const T* __restrict__ dinv,
+                                        const T* b, const T* __restrict__ dinv,
                                         const int32_t* __restrict__ agg, const T* __restrict__ t,
-                                        const T* __restrict__ e, T omega, T acc) {
+                                        const T* e, T omega, AccF acc) {
     if (LPR == 1) {
         // one thread per row (the fine level): a plain loop keeps the register
         // count low, so enough warps stay resident to saturate DRAM
-        T s = acc;
+        pdl_wait();
+        T s = acc();
 #pragma unroll 4
         for (int k = 0; k < len; ++k) {
             const int64_t ee = base + 32 * (int64_t)k;
-            const int j = scol[ee];
-            const T a = sval[ee];
+            const int j = __ldcs(scol + ee);
+            const T a = __ldcs(sval + ee);
             if (j < jmax) s = fmad(-a, nbr_value<MODE, SCALED>(j, x, b, dinv, agg, t, e, omega), s);
         }
         return s;
     }
-    T s = lane == 0 ? acc : T(0);
-    // every lane of the warp runs the same number of batches (the warp's
-    // longest row decides), so the warp-wide votes below see all 32 lanes
+    // every lane of the warp runs the same number of batches (the slice width
+    // bounds every row length), so the warp-wide votes below see all 32 lanes
     constexpr int per = LPR * kUnroll;
-    const int mine = len > lane ? (len - lane + per - 1) / per : 0;
-    const int batches = __reduce_max_sync(0xffffffffu, mine);
-    for (int it = 0; it < batches; ++it) {
+    const int batches = (width + per - 1) / per;
+    int j[kUnroll];
+    T a[kUnroll];
+    auto load_batch = [&](int it) {
         const int k0 = lane + it * per;
-        int j[kUnroll];
-        T a[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
             const int k = k0 + u * LPR;
@@ -211,6 +232,13 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jma
             j[u] = in ? scol[ee] : jmax;
             a[u] = in ? sval[ee] : T(0);
         }
+    };
+    load_batch(0);
+    pdl_wait();
+    // two partial sums halve the chain of dependent float64 FMAs
+    T s = lane == 0 ? acc() : T(0), s1 = T(0);
+    for (int it = 0; it < batches; ++it) {
+        if (it > 0) load_batch(it);
         // slots past the longest row of the warp are skipped by a warp-uniform
         // branch: a predicated-off float64 FMA would still occupy the pipe
         T v[kUnroll];
@@ -222,9 +250,12 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int lane, int jma
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
-            if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax) s = fmad(-a[u], v[u], s);
+            if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax) {
+                if (u & 1) s1 = fmad(-a[u], v[u], s1);
+                else s = fmad(-a[u], v[u], s);
+            }
     }
-    return group_sum<LPR>(s);
+    return group_sum<LPR>(s + s1);
 }
 
 // Rows handled by a launch: LPR lanes per row, rows from r0 rounded down to a
@@ -252,22 +283,26 @@ __global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, int64_t sw,
                                                   const int32_t* __restrict__ scol,
                                                   const T* __restrict__ sval,
                                                   const T* __restrict__ dinv,
-                                                  const T* __restrict__ b, T* __restrict__ x,
-                                                  T* __restrict__ bc_zero, int nc) {
-    if (bc_zero)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-            bc_zero[i] = T(0);
+                                                  const T* b, T* x,
+                                                  T* bc_zero, int nc) {
+    pdl_launch_dependents();
     const RowOf<LPR> R(0, c2);
-    if (LPR == 1 && !R.valid) return;
     const int rr = R.valid ? R.row : 0;
     // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
     // lane of the warp still reaches the shuffles of the group sum
-    const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
+    const int len = (R.valid && rr >= c1) ? (int)ldm<LPR == 1>(rlen + rr) : 0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T s = row_update<LPR, kNbrFirst, false, T>(base, len, R.lane, c1, scol, sval, x, b, dinv,
-                                                     nullptr, nullptr, nullptr, T(0),
-                                                     R.valid ? b[rr] : T(0));
-    if (R.valid && R.lane == 0) x[rr] = s * dinv[rr];
+    const T di = R.valid ? ldm<LPR == 1>(dinv + rr) : T(0);
+    if (LPR > 1 || R.valid) {
+        const T s = row_update<LPR, kNbrFirst, false, T>(
+            base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x, b, dinv, nullptr, nullptr, nullptr, T(0),
+            [&] { return R.valid ? b[rr] : T(0); });
+        if (R.valid && R.lane == 0) x[rr] = s * di;
+    }
+    pdl_wait();
+    if (bc_zero)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+            bc_zero[i] = T(0);
 }
 
 // One Gauss-Seidel update of the rows [r0, r1) of one colour:
@@ -280,18 +315,22 @@ __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
                                                     const int32_t* __restrict__ scol,
                                                     const T* __restrict__ sval,
                                                     const T* __restrict__ dinv,
-                                                    const T* __restrict__ b, T* x,
+                                                    const T* b, T* x,
                                                     const int32_t* __restrict__ agg,
                                                     const T* __restrict__ t,
-                                                    const T* __restrict__ e, T omega) {
+                                                    const T* e, T omega) {
+    pdl_launch_dependents();
     const RowOf<LPR> R(r0, r1);
     if (LPR == 1 && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)rlen[rr] : 0, R.lane, jmax,
+    const T di = R.valid ? ldm<LPR == 1>(dinv + rr) : T(0);
+    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)ldm<LPR == 1>(rlen + rr) : 0,
+                                                 (int)(sw >> 5),
+                                                 R.lane, jmax,
                                                  scol, sval, x, b, dinv, agg, t, e, omega,
-                                                 R.valid ? b[rr] : T(0));
-    if (R.valid && R.lane == 0) x[rr] = s * dinv[rr];
+                                                 [&] { return R.valid ? b[rr] : T(0); });
+    if (R.valid && R.lane == 0) x[rr] = s * di;
 }
 
 // r = b - A x for rows [r0, n)
@@ -301,16 +340,16 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
                                                      const int32_t* __restrict__ scol,
                                                      const T* __restrict__ sval,
                                                      const T* __restrict__ diag,
-                                                     const T* __restrict__ b,
-                                                     const T* __restrict__ x, T* __restrict__ r) {
+                                                     const T* b, const T* x, T* r) {
+    pdl_launch_dependents();
     const RowOf<LPR> R(r0, n);
     if (LPR == 1 && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T s0 = R.valid ? fmad(-diag[rr], x[rr], b[rr]) : T(0);
-    const T v = row_update<LPR, kNbrX, false, T>(base, R.valid ? (int)rlen[rr] : 0, R.lane, n, scol,
-                                                 sval, x, nullptr, nullptr, nullptr, nullptr,
-                                                 nullptr, T(0), s0);
+    const T dg = R.valid ? ldm<LPR == 1>(diag + rr) : T(0);
+    const T v = row_update<LPR, kNbrX, false, T>(
+        base, R.valid ? (int)ldm<LPR == 1>(rlen + rr) : 0, (int)(sw >> 5), R.lane, n, scol, sval, x, nullptr, nullptr, nullptr,
+        nullptr, nullptr, T(0), [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
     if (R.valid && R.lane == 0) r[rr] = v;
 }
 
@@ -330,25 +369,28 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
                                                               const int32_t* __restrict__ scol,
                                                               const T* __restrict__ sval,
                                                               const T* __restrict__ diag,
-                                                              const T* __restrict__ b,
-                                                              const T* __restrict__ x,
+                                                              const T* b, const T* x,
                                                               const int32_t* __restrict__ agg,
-                                                              const T* __restrict__ t,
-                                                              T* __restrict__ bc) {
+                                                              const T* __restrict__ t, T* bc) {
     __shared__ T sv[kBlock];
     __shared__ int sk[kBlock];
+    pdl_launch_dependents();
     const RowOf<1> R(c1, n);
     int key = -1;
     T v = T(0);
     if (R.valid) {
         const int rr = R.row;
         const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-        const T s0 = fmad(-diag[rr], x[rr], b[rr]);
-        const T ri = row_update<1, kNbrX, false, T>(base, rlen[rr], 0, n, scol, sval, x, nullptr,
-                                                    nullptr, nullptr, nullptr, nullptr, T(0), s0);
-        key = agg[rr];
-        v = SCALED ? t[rr] * ri : ri;
+        const T dg = __ldcs(diag + rr);
+        key = __ldcs(agg + rr);
+        const T ti = SCALED ? __ldcs(t + rr) : T(1);
+        const T ri = row_update<1, kNbrX, false, T>(base, __ldcs(rlen + rr), (int)(sw >> 5), 0, n, scol,
+                                                    sval, x, nullptr,
+                                                    nullptr, nullptr, nullptr, nullptr, T(0),
+                                                    [&] { return fmad(-dg, x[rr], b[rr]); });
+        v = SCALED ? ti * ri : ri;
     }
+    pdl_wait();
     const int tid = threadIdx.x;
     sv[tid] = v;
     sk[tid] = key;
@@ -367,15 +409,21 @@ template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __restrict__ rptr,
                                                      const int32_t* __restrict__ ridx,
                                                      const T* __restrict__ t,
-                                                     const T* __restrict__ r, T* __restrict__ bc) {
+                                                     const T* r, T* bc) {
+    pdl_launch_dependents();
     const int J = blockIdx.x * blockDim.x + threadIdx.x;
     if (J >= nc) return;
-    const int k1 = rptr[J + 1];
-    T s = T(0);
-    for (int k0 = rptr[J]; k0 < k1; k0 += kUnroll) {
-        int i[kUnroll];
+    const int kb = rptr[J], k1 = rptr[J + 1];
+    int i[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) i[u] = (k0 + u < k1) ? ridx[k0 + u] : -1;
+    for (int u = 0; u < kUnroll; ++u) i[u] = (kb + u < k1) ? ridx[kb + u] : -1;
+    pdl_wait();
+    T s = T(0);
+    for (int k0 = kb; k0 < k1; k0 += kUnroll) {
+        if (k0 > kb) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) i[u] = (k0 + u < k1) ? ridx[k0 + u] : -1;
+        }
         T v[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u)
@@ -394,54 +442,80 @@ __global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __re
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kBlock) k_prolong(int r0, int n, const int32_t* __restrict__ agg,
                                                     const T* __restrict__ t,
-                                                    const T* __restrict__ e, T* __restrict__ x,
-                                                    T omega) {
+                                                    const T* e, T* x, T omega) {
+    pdl_launch_dependents();
     const int i = r0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (i >= n) return;
     const int a = agg[i];
     if (a < 0) return;
-    x[i] = fmad(SCALED ? omega * t[i] : omega, e[a], x[i]);
+    const T w = SCALED ? omega * t[i] : omega;
+    pdl_wait();
+    x[i] = fmad(w, e[a], x[i]);
 }
 
 // x = M b, M dense row-major (coarsest-level solve with the inverse formed at
-// setup); one warp per row, float64 arithmetic.
+// setup); one warp per row, float64 arithmetic.  M is larger than L2 and read
+// once per V-cycle: evict-first loads keep it from displacing the coarse
+// levels.
 template <typename TB>
 __global__ void __launch_bounds__(kBlock) k_dense_gemv(int n, const double* __restrict__ M,
-                                                       const TB* __restrict__ b, TB* __restrict__ x) {
+                                                       const TB* b, TB* x) {
+    constexpr int kPre = 4;   // row entries per lane loaded before the wait
+    pdl_launch_dependents();
     const int lane = threadIdx.x & 31;
     const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (row >= n) return;
     const double* m = M + (size_t)row * n;
+    double m0[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) m0[u] = (lane + 32 * u < n) ? __ldcs(m + lane + 32 * u) : 0.0;
+    pdl_wait();
     double s = 0.0;
-    for (int k = lane; k < n; k += 32) s += m[k] * (double)b[k];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u)
+        if (lane + 32 * u < n) s += m0[u] * (double)b[lane + 32 * u];
+    for (int k = lane + 32 * kPre; k < n; k += 32) s += __ldcs(m + k) * (double)b[k];
     s = group_sum<32>(s);
     if (lane == 0) x[row] = (TB)s;
 }
 
-__global__ void k_gather(int n, const int32_t* __restrict__ idx, const double* __restrict__ x,
-                         double* __restrict__ y) {
+__global__ void k_gather(int n, const int32_t* __restrict__ idx, const double* x, double* y) {
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = x[idx[i]];
+    if (i >= n) return;
+    const int j = idx[i];
+    pdl_wait();
+    y[i] = x[j];
 }
 
-__global__ void k_scatter(int n, const int32_t* __restrict__ idx, const double* __restrict__ x,
-                          double* __restrict__ y) {
+__global__ void k_scatter(int n, const int32_t* __restrict__ idx, const double* x, double* y) {
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[idx[i]] = x[i];
+    if (i >= n) return;
+    const int j = idx[i];
+    pdl_wait();
+    y[j] = x[i];
 }
 
 // float64 -> scaled float32 at V-cycle entry: rhat = r / s, s = sqrt(A_ii)
-__global__ void k_to_scaled32(int n, const double* __restrict__ r, const double* __restrict__ isq,
-                              float* __restrict__ rhat) {
+__global__ void k_to_scaled32(int n, const double* r, const double* __restrict__ isq, float* rhat) {
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) rhat[i] = (float)(r[i] * isq[i]);
+    if (i >= n) return;
+    const double w = isq[i];
+    pdl_wait();
+    rhat[i] = (float)(r[i] * w);
 }
 
 // scaled float32 -> float64 at V-cycle exit: z = zhat / s
-__global__ void k_from_scaled32(int n, const float* __restrict__ zhat, const double* __restrict__ isq,
-                                double* __restrict__ z) {
+__global__ void k_from_scaled32(int n, const float* zhat, const double* __restrict__ isq,
+                                double* z) {
+    pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) z[i] = (double)zhat[i] * isq[i];
+    if (i >= n) return;
+    const double w = isq[i];
+    pdl_wait();
+    z[i] = (double)zhat[i] * w;
 }
 
 // ---------------------------------------------------------------------------
@@ -460,11 +534,13 @@ __global__ void __launch_bounds__(kBlock) k_cg_residual(int n, int64_t sw,
                                                         unsigned int* counter, PcgScalars* sc,
                                                         double* out, int mode) {
     __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
     double acc = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
-        const double s0 = fmad(-diag[row], x[row], b[row]);
-        const double v = sell_row<true>(base, rlen[row], scol, sval, x, s0);
+        const double s0 = fmad(-__ldcs(diag + row), x[row], b[row]);
+        const double v = sell_row<true>(base, __ldcs(rlen + row), scol, sval, x, s0);
         if (r) r[row] = v;
         acc = fmad(v, v, acc);
     }
@@ -482,11 +558,14 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, int64_t sw,
                                                        double* __restrict__ q, double* partials,
                                                        unsigned int* counter, PcgScalars* sc) {
     __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
     double acc = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double pi = p[row];
-        const double v = sell_row<false>(base, rlen[row], scol, sval, p, diag[row] * pi);
+        const double v = sell_row<false>(base, __ldcs(rlen + row), scol, sval, p,
+                                         __ldcs(diag + row) * pi);
         q[row] = v;
         acc = fmad(pi, v, acc);
     }
@@ -502,6 +581,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, double* __restrict_
                                                       double* partials, unsigned int* counter,
                                                       PcgScalars* sc) {
     __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
     const double alpha = sc->alpha;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -522,6 +603,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_rz(int n, const double* __restric
                                                   double* partials2, unsigned int* counter,
                                                   PcgScalars* sc, int mode) {
     __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
     double a = 0.0, b = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double ri = r[i], zi = z[i];
@@ -539,6 +622,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_rz(int n, const double* __restric
 __global__ void __launch_bounds__(kBlock) k_cg_p(int n, const double* __restrict__ z,
                                                  double* __restrict__ p, double* __restrict__ zold,
                                                  const PcgScalars* sc) {
+    pdl_launch_dependents();
+    pdl_wait();
     const double beta = sc->beta;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double zi = z[i];
@@ -554,6 +639,7 @@ inline int blocks_for(int64_t threads) { return (int)((threads + kBlock - 1) / k
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+thread_local bool t_launch_overlap = false;
 int g_reduction_blocks = 1216;
 
 int reduction_blocks(int64_t work_threads) {
@@ -590,7 +676,7 @@ template <typename T>
 void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStream_t s) {
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
-    AMG_LPR_DISPATCH(L.lpr, (k_first<LPR, T><<<std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s>>>(
+    AMG_LPR_DISPATCH(L.lpr, (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s, 
                                 c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero, nc)));
 }
 
@@ -601,7 +687,7 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* 
     const int r0 = L.cptr[col], r1 = L.cptr[col + 1];
     if (r1 <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
-    AMG_LPR_DISPATCH(L.lpr, (k_gs_pass<LPR, MODE, SC, T><<<row_blocks(r0, r1, LPR), kBlock, 0, s>>>(
+    AMG_LPR_DISPATCH(L.lpr, (launch_kernel(k_gs_pass<LPR, MODE, SC, T>, row_blocks(r0, r1, LPR), kBlock, 0, s, 
                                 r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg,
                                 A.t, e, (T)omega)));
 }
@@ -614,14 +700,14 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
     constexpr bool SC = std::is_same<T, float>::value;
     if (L.fused_restrict) {
         if (L.n > c1)
-            k_residual_restrict<T, SC><<<row_blocks(c1, L.n, 1), kBlock, 0, s>>>(
+            launch_kernel(k_residual_restrict<T, SC>, row_blocks(c1, L.n, 1), kBlock, 0, s, 
                 c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg, A.t, bc);
         return;
     }
     if (L.n > c1)
-        AMG_LPR_DISPATCH(L.lpr, (k_residual<LPR, T><<<row_blocks(c1, L.n, LPR), kBlock, 0, s>>>(
+        AMG_LPR_DISPATCH(L.lpr, (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR), kBlock, 0, s, 
                                     c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, r)));
-    k_restrict<T, SC><<<blocks_for(L.n_coarse), kBlock, 0, s>>>(L.n_coarse, L.rptr, L.ridx, A.t, r,
+    launch_kernel(k_restrict<T, SC>, blocks_for(L.n_coarse), kBlock, 0, s, L.n_coarse, L.rptr, L.ridx, A.t, r,
                                                                 bc);
 }
 
@@ -631,7 +717,7 @@ void prolong_impl(const DevLevel& L, const T* e, T* x, double omega, cudaStream_
     const int r0 = L.cptr[1];
     if (L.n <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
-    k_prolong<T, SC><<<blocks_for(L.n - r0), kBlock, 0, s>>>(r0, L.n, L.agg, A.t, e, x, (T)omega);
+    launch_kernel(k_prolong<T, SC>, blocks_for(L.n - r0), kBlock, 0, s, r0, L.n, L.agg, A.t, e, x, (T)omega);
 }
 
 void launch_first(const DevLevel& L, const double* b, double* x, double* bc_zero, int nc,
@@ -672,57 +758,57 @@ void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega,
 }
 
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s) {
-    k_dense_gemv<double><<<blocks_for((int64_t)n * 32), kBlock, 0, s>>>(n, M, b, x);
+    launch_kernel(k_dense_gemv<double>, blocks_for((int64_t)n * 32), kBlock, 0, s, n, M, b, x);
 }
 
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s) {
-    k_dense_gemv<float><<<blocks_for((int64_t)n * 32), kBlock, 0, s>>>(n, M, b, x);
+    launch_kernel(k_dense_gemv<float>, blocks_for((int64_t)n * 32), kBlock, 0, s, n, M, b, x);
 }
 
 void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s) {
-    k_gather<<<blocks_for(n), kBlock, 0, s>>>(n, idx, x, y);
+    launch_kernel(k_gather, blocks_for(n), kBlock, 0, s, n, idx, x, y);
 }
 
 void launch_scatter(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s) {
-    k_scatter<<<blocks_for(n), kBlock, 0, s>>>(n, idx, x, y);
+    launch_kernel(k_scatter, blocks_for(n), kBlock, 0, s, n, idx, x, y);
 }
 
 void launch_to_scaled32(int n, const double* r, const double* isq, float* rhat, cudaStream_t s) {
-    k_to_scaled32<<<blocks_for(n), kBlock, 0, s>>>(n, r, isq, rhat);
+    launch_kernel(k_to_scaled32, blocks_for(n), kBlock, 0, s, n, r, isq, rhat);
 }
 
 void launch_from_scaled32(int n, const float* zhat, const double* isq, double* z, cudaStream_t s) {
-    k_from_scaled32<<<blocks_for(n), kBlock, 0, s>>>(n, zhat, isq, z);
+    launch_kernel(k_from_scaled32, blocks_for(n), kBlock, 0, s, n, zhat, isq, z);
 }
 
 void launch_cg_residual(const DevLevel& L, const double* b, const double* x, double* r,
                         CgWork& w, int mode, double* out, cudaStream_t s) {
-    k_cg_residual<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sw, L.rlen, L.scol, L.sval,
+    launch_kernel(k_cg_residual, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol, L.sval,
                                                            L.diag, b, x, r, w.partials,
                                                            w.counters, w.sc, out, mode);
 }
 
 void launch_cg_spmv_pq(const DevLevel& L, const double* p, double* q, CgWork& w, cudaStream_t s) {
-    k_cg_spmv_pq<<<reduction_blocks(L.n), kBlock, 0, s>>>(L.n, L.sw, L.rlen, L.scol, L.sval,
+    launch_kernel(k_cg_spmv_pq, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol, L.sval,
                                                           L.diag, p, q, w.partials,
                                                           w.counters + 1, w.sc);
 }
 
 void launch_cg_update(int n, double* x, double* r, const double* p, const double* q, CgWork& w,
                       cudaStream_t s) {
-    k_cg_update<<<reduction_blocks(n), kBlock, 0, s>>>(n, x, r, p, q, w.partials, w.counters + 2,
+    launch_kernel(k_cg_update, reduction_blocks(n), kBlock, 0, s, n, x, r, p, q, w.partials, w.counters + 2,
                                                        w.sc);
 }
 
 void launch_cg_rz(int n, const double* r, const double* z, const double* zold, double* p,
                   CgWork& w, int mode, cudaStream_t s) {
-    k_cg_rz<<<reduction_blocks(n), kBlock, 0, s>>>(n, r, z, zold, p, w.partials, w.partials2,
+    launch_kernel(k_cg_rz, reduction_blocks(n), kBlock, 0, s, n, r, z, zold, p, w.partials, w.partials2,
                                                    w.counters + 3, w.sc, mode);
 }
 
 void launch_cg_p(int n, const double* z, double* p, double* zold, const CgWork& w,
                  cudaStream_t s) {
-    k_cg_p<<<reduction_blocks(n), kBlock, 0, s>>>(n, z, p, zold, w.sc);
+    launch_kernel(k_cg_p, reduction_blocks(n), kBlock, 0, s, n, z, p, zold, w.sc);
 }
 
 }  // namespace amg

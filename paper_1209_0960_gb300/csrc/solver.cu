@@ -343,6 +343,7 @@ void ensure_fp32(amg_ctx* c) {
 // Order the context stream after the caller's stream (enter) and the
 // caller's stream after the context stream (leave).
 void enter(amg_ctx* c) {
+    t_launch_overlap = c->p.launch_overlap != 0;
     AMG_CUDA_TRY(cudaEventRecord(c->ev_in, c->user_stream));
     AMG_CUDA_TRY(cudaStreamWaitEvent(c->stream, c->ev_in, 0));
 }
@@ -724,6 +725,7 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->precision = AMG_FP64;
     p->flexible_cg = -1;
     p->cuda_stream = nullptr;
+    p->launch_overlap = 1;
     return AMG_OK;
 }
 

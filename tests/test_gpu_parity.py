@@ -210,3 +210,24 @@ def test_full_size_lognormal_128():
         assert np.linalg.norm(r) <= 1.05e-8 * np.linalg.norm(p.b)
         assert abs(solver.residual_norm(b, x) - np.linalg.norm(r)) <= 1e-6 * np.linalg.norm(r)
     solver.close()
+
+
+def test_launch_overlap_changes_no_bits():
+    # programmatic dependent launch only changes when kernels start, never
+    # what they compute: both launch modes give identical bits
+    p = P.lognormal3d((28, 24, 20), seed=1)
+    b = torch.from_numpy(p.b).cuda()
+    res = []
+    for overlap in (0, 1):
+        solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, coarsen_target=300,
+                         launch_overlap=overlap)
+        out = []
+        for prec in (amg.AMG_FP64, amg.AMG_FP32_IN_FP64):
+            solver.set_precision(prec)
+            x, rc, info = solver.solve(b, tol=1e-10, maxit=300)
+            assert rc == amg.AMG_OK
+            out += [x, solver.vcycle(b), info["iterations"]]
+        solver.close()
+        res.append(out)
+    for u, v in zip(*res):
+        assert torch.equal(u, v) if isinstance(u, torch.Tensor) else u == v
