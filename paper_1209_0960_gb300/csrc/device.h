@@ -105,8 +105,12 @@ struct DevLevel {
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
-    int32_t lpr = 1;                  // lanes per row of the row kernels (1, 4 or 8)
-    bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 1)
+    int32_t lpr = 0;                  // lanes per row of the row kernels: 0 = one lane
+                                      // per row with a plain streamed loop (fine level),
+                                      // else 1, 2, 4 or 8 lanes with batched gathers
+    int32_t lpr_wide = 0;             // lanes per row of launches over >= wide_rows rows
+    int32_t wide_rows = 0x7fffffff;
+    bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 0)
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
     double* sval = nullptr;           // [padded]
@@ -191,6 +195,9 @@ struct CgWork {
 // latency and the first dependent loads of each kernel.  Set per calling
 // thread from the context at API entry.
 extern thread_local bool t_launch_overlap;
+// grids above this many blocks launch without the overlap: a wide grid that
+// starts early only occupies the SMs its predecessor is still using
+extern int g_overlap_max_blocks;
 
 template <typename... KArgs, typename... Args>
 void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
@@ -204,7 +211,7 @@ void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, c
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = t_launch_overlap ? 1 : 0;
+    cfg.numAttrs = (t_launch_overlap && grid <= g_overlap_max_blocks) ? 1 : 0;
     AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
 }
 

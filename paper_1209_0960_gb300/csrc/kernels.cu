@@ -191,10 +191,21 @@ __device__ __forceinline__ T nbr_value(int j, const T* x, const T* b,
 // The row sum starts from acc(), which reads vectors of the solve: it and all
 // neighbour values are read after pdl_wait().  With several lanes per row the
 // first batch of column indices and values (setup-time data) is loaded before
-// it, so those loads overlap the predecessor kernel.  The fine level (one
-// lane per row) streams its matrix with evict-first loads: it is read once
-// per pass and is larger than L2, and keeping it out of L2 leaves the
-// coarse levels resident there from one V-cycle to the next.
+// it, so those loads overlap the predecessor kernel.
+//
+// LPR = lanes per row (1, 2, 4 or 8), or kFine: one lane per row with a plain
+// loop over the row, for the fine level.  The fine level streams its matrix
+// with evict-first loads: it is read once per pass and is larger than L2, and
+// keeping it out of L2 leaves the coarse levels resident there from one
+// V-cycle to the next.
+constexpr int kFine = 0;
+template <int LPR>
+__host__ __device__ constexpr int lanes_of() { return LPR == kFine ? 1 : LPR; }
+// entries per lane gathered in one batch: with fewer lanes per row a lane
+// takes more of the row, still in one batch for the usual coarse widths
+template <int LPR>
+__host__ __device__ constexpr int unroll_of() { return LPR == 1 ? 24 : LPR == 2 ? 12 : kUnroll; }
+
 template <int LPR, int MODE, bool SCALED, typename T, typename AccF>
 __device__ __forceinline__ T row_update(int64_t base, int len, int width, int lane, int jmax,
                                         const int32_t* __restrict__ scol,
@@ -202,9 +213,9 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
                                         const T* b, const T* __restrict__ dinv,
                                         const int32_t* __restrict__ agg, const T* __restrict__ t,
                                         const T* e, T omega, AccF acc) {
-    if (LPR == 1) {
-        // one thread per row (the fine level): a plain loop keeps the register
-        // count low, so enough warps stay resident to saturate DRAM
+    if (LPR == kFine) {
+        // a plain loop keeps the register count low, so enough warps stay
+        // resident to saturate DRAM
         pdl_wait();
         T s = acc();
 #pragma unroll 4
@@ -218,15 +229,17 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
     }
     // every lane of the warp runs the same number of batches (the slice width
     // bounds every row length), so the warp-wide votes below see all 32 lanes
-    constexpr int per = LPR * kUnroll;
+    constexpr int G = lanes_of<LPR>();
+    constexpr int U = unroll_of<LPR>();
+    constexpr int per = G * U;
     const int batches = (width + per - 1) / per;
-    int j[kUnroll];
-    T a[kUnroll];
+    int j[U];
+    T a[U];
     auto load_batch = [&](int it) {
         const int k0 = lane + it * per;
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-            const int k = k0 + u * LPR;
+        for (int u = 0; u < U; ++u) {
+            const int k = k0 + u * G;
             const bool in = k < len;
             const int64_t ee = base + 32 * (int64_t)(in ? k : 0);
             j[u] = in ? scol[ee] : jmax;
@@ -241,21 +254,21 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
         if (it > 0) load_batch(it);
         // slots past the longest row of the warp are skipped by a warp-uniform
         // branch: a predicated-off float64 FMA would still occupy the pipe
-        T v[kUnroll];
+        T v[U];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
+        for (int u = 0; u < U; ++u) {
             v[u] = T(0);
             if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax)
                 v[u] = nbr_value<MODE, SCALED>(j[u], x, b, dinv, agg, t, e, omega);
         }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
+        for (int u = 0; u < U; ++u)
             if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax) {
                 if (u & 1) s1 = fmad(-a[u], v[u], s1);
                 else s = fmad(-a[u], v[u], s);
             }
     }
-    return group_sum<LPR>(s + s1);
+    return group_sum<G>(s + s1);
 }
 
 // Rows handled by a launch: LPR lanes per row, rows from r0 rounded down to a
@@ -265,9 +278,10 @@ struct RowOf {
     int row, lane;
     bool valid;
     __device__ RowOf(int r0, int r1) {
+        constexpr int G = lanes_of<LPR>();
         const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        row = (r0 & ~31) + (int)(tt / LPR);
-        lane = (int)(tt % LPR);
+        row = (r0 & ~31) + (int)(tt / G);
+        lane = (int)(tt % G);
         valid = row >= r0 && row < r1;
     }
 };
@@ -290,10 +304,10 @@ __global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, int64_t sw,
     const int rr = R.valid ? R.row : 0;
     // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
     // lane of the warp still reaches the shuffles of the group sum
-    const int len = (R.valid && rr >= c1) ? (int)ldm<LPR == 1>(rlen + rr) : 0;
+    const int len = (R.valid && rr >= c1) ? (int)ldm<LPR == kFine>(rlen + rr) : 0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T di = R.valid ? ldm<LPR == 1>(dinv + rr) : T(0);
-    if (LPR > 1 || R.valid) {
+    const T di = R.valid ? ldm<LPR == kFine>(dinv + rr) : T(0);
+    if (LPR != kFine || R.valid) {
         const T s = row_update<LPR, kNbrFirst, false, T>(
             base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x, b, dinv, nullptr, nullptr, nullptr, T(0),
             [&] { return R.valid ? b[rr] : T(0); });
@@ -321,11 +335,11 @@ __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
                                                     const T* e, T omega) {
     pdl_launch_dependents();
     const RowOf<LPR> R(r0, r1);
-    if (LPR == 1 && !R.valid) return;
+    if (LPR == kFine && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T di = R.valid ? ldm<LPR == 1>(dinv + rr) : T(0);
-    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)ldm<LPR == 1>(rlen + rr) : 0,
+    const T di = R.valid ? ldm<LPR == kFine>(dinv + rr) : T(0);
+    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)ldm<LPR == kFine>(rlen + rr) : 0,
                                                  (int)(sw >> 5),
                                                  R.lane, jmax,
                                                  scol, sval, x, b, dinv, agg, t, e, omega,
@@ -343,12 +357,12 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
                                                      const T* b, const T* x, T* r) {
     pdl_launch_dependents();
     const RowOf<LPR> R(r0, n);
-    if (LPR == 1 && !R.valid) return;
+    if (LPR == kFine && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T dg = R.valid ? ldm<LPR == 1>(diag + rr) : T(0);
+    const T dg = R.valid ? ldm<LPR == kFine>(diag + rr) : T(0);
     const T v = row_update<LPR, kNbrX, false, T>(
-        base, R.valid ? (int)ldm<LPR == 1>(rlen + rr) : 0, (int)(sw >> 5), R.lane, n, scol, sval, x, nullptr, nullptr, nullptr,
+        base, R.valid ? (int)ldm<LPR == kFine>(rlen + rr) : 0, (int)(sw >> 5), R.lane, n, scol, sval, x, nullptr, nullptr, nullptr,
         nullptr, nullptr, T(0), [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
     if (R.valid && R.lane == 0) r[rr] = v;
 }
@@ -375,7 +389,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
     __shared__ T sv[kBlock];
     __shared__ int sk[kBlock];
     pdl_launch_dependents();
-    const RowOf<1> R(c1, n);
+    const RowOf<kFine> R(c1, n);
     int key = -1;
     T v = T(0);
     if (R.valid) {
@@ -384,7 +398,7 @@ __global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
         const T dg = __ldcs(diag + rr);
         key = __ldcs(agg + rr);
         const T ti = SCALED ? __ldcs(t + rr) : T(1);
-        const T ri = row_update<1, kNbrX, false, T>(base, __ldcs(rlen + rr), (int)(sw >> 5), 0, n, scol,
+        const T ri = row_update<kFine, kNbrX, false, T>(base, __ldcs(rlen + rr), (int)(sw >> 5), 0, n, scol,
                                                     sval, x, nullptr,
                                                     nullptr, nullptr, nullptr, nullptr, T(0),
                                                     [&] { return fmad(-dg, x[rr], b[rr]); });
@@ -454,9 +468,7 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int r0, int n, const int32_t
 }
 
 // x = M b, M dense row-major (coarsest-level solve with the inverse formed at
-// setup); one warp per row, float64 arithmetic.  M is larger than L2 and read
-// once per V-cycle: evict-first loads keep it from displacing the coarse
-// levels.
+// setup); one warp per row, float64 arithmetic.
 template <typename TB>
 __global__ void __launch_bounds__(kBlock) k_dense_gemv(int n, const double* __restrict__ M,
                                                        const TB* b, TB* x) {
@@ -468,13 +480,13 @@ __global__ void __launch_bounds__(kBlock) k_dense_gemv(int n, const double* __re
     const double* m = M + (size_t)row * n;
     double m0[kPre];
 #pragma unroll
-    for (int u = 0; u < kPre; ++u) m0[u] = (lane + 32 * u < n) ? __ldcs(m + lane + 32 * u) : 0.0;
+    for (int u = 0; u < kPre; ++u) m0[u] = (lane + 32 * u < n) ? m[lane + 32 * u] : 0.0;
     pdl_wait();
     double s = 0.0;
 #pragma unroll
     for (int u = 0; u < kPre; ++u)
         if (lane + 32 * u < n) s += m0[u] * (double)b[lane + 32 * u];
-    for (int k = lane + 32 * kPre; k < n; k += 32) s += __ldcs(m + k) * (double)b[k];
+    for (int k = lane + 32 * kPre; k < n; k += 32) s += m[k] * (double)b[k];
     s = group_sum<32>(s);
     if (lane == 0) x[row] = (TB)s;
 }
@@ -640,6 +652,7 @@ inline int blocks_for(int64_t threads) { return (int)((threads + kBlock - 1) / k
 // launchers
 // ---------------------------------------------------------------------------
 thread_local bool t_launch_overlap = false;
+int g_overlap_max_blocks = 304;
 int g_reduction_blocks = 1216;
 
 int reduction_blocks(int64_t work_threads) {
@@ -649,12 +662,22 @@ int reduction_blocks(int64_t work_threads) {
 }
 
 inline int row_blocks(int r0, int r1, int lpr) {
-    return blocks_for((int64_t)(r1 - (r0 & ~31)) * lpr);
+    return blocks_for((int64_t)(r1 - (r0 & ~31)) * std::max(lpr, 1));
+}
+
+// lanes per row of a launch over `rows` rows: passes over many rows are
+// bound by float64 instruction throughput, which fewer lanes per row use
+// better (no cross-lane sums, no idle slots); short passes are bound by
+// latency, which more lanes per row shorten
+inline int launch_lpr(const DevLevel& L, int rows) {
+    return rows >= L.wide_rows ? L.lpr_wide : L.lpr;
 }
 
 #define AMG_LPR_DISPATCH(lpr, CALL)                          \
     switch (lpr) {                                           \
+        case kFine: { constexpr int LPR = kFine; CALL; } break; \
         case 1: { constexpr int LPR = 1; CALL; } break;      \
+        case 2: { constexpr int LPR = 2; CALL; } break;      \
         case 4: { constexpr int LPR = 4; CALL; } break;      \
         default: { constexpr int LPR = 8; CALL; } break;     \
     }
@@ -676,7 +699,7 @@ template <typename T>
 void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStream_t s) {
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
-    AMG_LPR_DISPATCH(L.lpr, (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s, 
+    AMG_LPR_DISPATCH(launch_lpr(L, c2), (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s, 
                                 c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero, nc)));
 }
 
@@ -687,7 +710,7 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* 
     const int r0 = L.cptr[col], r1 = L.cptr[col + 1];
     if (r1 <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
-    AMG_LPR_DISPATCH(L.lpr, (launch_kernel(k_gs_pass<LPR, MODE, SC, T>, row_blocks(r0, r1, LPR), kBlock, 0, s, 
+    AMG_LPR_DISPATCH(launch_lpr(L, r1 - r0), (launch_kernel(k_gs_pass<LPR, MODE, SC, T>, row_blocks(r0, r1, LPR), kBlock, 0, s, 
                                 r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg,
                                 A.t, e, (T)omega)));
 }
@@ -705,7 +728,7 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
         return;
     }
     if (L.n > c1)
-        AMG_LPR_DISPATCH(L.lpr, (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR), kBlock, 0, s, 
+        AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1), (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR), kBlock, 0, s, 
                                     c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, r)));
     launch_kernel(k_restrict<T, SC>, blocks_for(L.n_coarse), kBlock, 0, s, L.n_coarse, L.rptr, L.ridx, A.t, r,
                                                                 bc);

@@ -367,7 +367,8 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
     // lanes per row: one on sparse rows (float64 arithmetic bound), several on
     // the denser coarse rows (gather latency bound)
     const double avg = n > 0 ? (double)L.nnz_off / n : 0.0;
-    L.lpr = avg <= 7.0 ? 1 : avg <= 16.0 ? 4 : 8;
+    L.lpr = avg <= 7.0 ? 0 : avg <= 16.0 ? 4 : 8;
+    L.lpr_wide = L.lpr;
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 }
 

@@ -515,6 +515,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     int sms = 0;
     AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
     g_reduction_blocks = std::max(1, sms) * 8;
+    g_overlap_max_blocks = std::max(1, sms) * 2;
     cudaStream_t s = c->stream;
 
     // level 0 on the host (original numbering)
@@ -638,7 +639,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
             for (int32_t J = 0; J < nc; ++J) most = std::max(most, rptr[J + 1] - rptr[J]);
             // the fused kernel needs the rows of colour >= 1 to be one block
             // sorted by coarse index (two colours) and runs shorter than a warp
-            L.fused_restrict = L.lpr == 1 && L.ncolours == 2 && most <= 32;
+            L.fused_restrict = L.lpr == 0 && L.ncolours == 2 && most <= 32;
         }
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
