@@ -105,12 +105,14 @@ struct DevLevel {
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
-    int32_t lpr = 0;                  // lanes per row of the row kernels: 0 = one lane
-                                      // per row with a plain streamed loop (fine level),
-                                      // else 1, 2, 4 or 8 lanes with batched gathers
+    int32_t lpr = 0;                  // lanes per row of the row kernels: 0 = the fine
+                                      // level's kernels (one row per thread, slices staged
+                                      // in shared memory, width <= kFineMaxWidth), else
+                                      // 1, 2, 4 or 8 lanes with batched gathers
     int32_t lpr_wide = 0;             // lanes per row of launches over >= wide_rows rows
     int32_t wide_rows = 0x7fffffff;
     bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 0)
+    int32_t* err = nullptr;           // device status word for kernel-side errors (timeouts)
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
     double* sval = nullptr;           // [padded]
@@ -131,6 +133,10 @@ struct DevLevel {
     float* b32 = nullptr;
     float* r32 = nullptr;
 };
+
+// widest slice the fine-level (staged) kernels take: 256 rows x W entries of
+// index and value stay within one block's shared memory
+constexpr int kFineMaxWidth = 32;
 
 // Launch profiler: events around launches, grouped by kernel class.
 struct Profiler {

@@ -192,12 +192,8 @@ __device__ __forceinline__ T nbr_value(int j, const T* x, const T* b,
 // neighbour values are read after pdl_wait().  With several lanes per row the
 // first batch of column indices and values (setup-time data) is loaded before
 // it, so those loads overlap the predecessor kernel.
-//
-// LPR = lanes per row (1, 2, 4 or 8), or kFine: one lane per row with a plain
-// loop over the row, for the fine level.  The fine level streams its matrix
-// with evict-first loads: it is read once per pass and is larger than L2, and
-// keeping it out of L2 leaves the coarse levels resident there from one
-// V-cycle to the next.
+// LPR = lanes per row (1, 2, 4 or 8).  The fine level has kernels of its own
+// (below), with the matrix staged in shared memory.
 constexpr int kFine = 0;
 template <int LPR>
 __host__ __device__ constexpr int lanes_of() { return LPR == kFine ? 1 : LPR; }
@@ -213,20 +209,7 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
                                         const T* b, const T* __restrict__ dinv,
                                         const int32_t* __restrict__ agg, const T* __restrict__ t,
                                         const T* e, T omega, AccF acc) {
-    if (LPR == kFine) {
-        // a plain loop keeps the register count low, so enough warps stay
-        // resident to saturate DRAM
-        pdl_wait();
-        T s = acc();
-#pragma unroll 4
-        for (int k = 0; k < len; ++k) {
-            const int64_t ee = base + 32 * (int64_t)k;
-            const int j = __ldcs(scol + ee);
-            const T a = __ldcs(sval + ee);
-            if (j < jmax) s = fmad(-a, nbr_value<MODE, SCALED>(j, x, b, dinv, agg, t, e, omega), s);
-        }
-        return s;
-    }
+    static_assert(LPR != kFine, "the fine level uses the staged kernels");
     // every lane of the warp runs the same number of batches (the slice width
     // bounds every row length), so the warp-wide votes below see all 32 lanes
     constexpr int G = lanes_of<LPR>();
@@ -289,34 +272,26 @@ struct RowOf {
 // Fused first two forward passes of the pre-smoother from a zero initial
 // guess: rows of colour 0 ([0, c1)) have only zero neighbours, so
 // x_i = b_i / A_ii; rows of colour 1 ([c1, c2)) see colour-0 neighbours (their
-// new values b_j / A_jj) and zeros.  Optionally zeroes the next level's
-// right-hand side for the fused residual-restriction kernel.
+// new values b_j / A_jj) and zeros.
 template <int LPR, typename T>
 __global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, int64_t sw,
                                                   const uint16_t* __restrict__ rlen,
                                                   const int32_t* __restrict__ scol,
                                                   const T* __restrict__ sval,
                                                   const T* __restrict__ dinv,
-                                                  const T* b, T* x,
-                                                  T* bc_zero, int nc) {
+                                                  const T* b, T* x) {
     pdl_launch_dependents();
     const RowOf<LPR> R(0, c2);
     const int rr = R.valid ? R.row : 0;
     // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
     // lane of the warp still reaches the shuffles of the group sum
-    const int len = (R.valid && rr >= c1) ? (int)ldm<LPR == kFine>(rlen + rr) : 0;
+    const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T di = R.valid ? ldm<LPR == kFine>(dinv + rr) : T(0);
-    if (LPR != kFine || R.valid) {
-        const T s = row_update<LPR, kNbrFirst, false, T>(
-            base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x, b, dinv, nullptr, nullptr, nullptr, T(0),
-            [&] { return R.valid ? b[rr] : T(0); });
-        if (R.valid && R.lane == 0) x[rr] = s * di;
-    }
-    pdl_wait();
-    if (bc_zero)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-            bc_zero[i] = T(0);
+    const T di = R.valid ? dinv[rr] : T(0);
+    const T s = row_update<LPR, kNbrFirst, false, T>(
+        base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x, b, dinv, nullptr, nullptr, nullptr,
+        T(0), [&] { return R.valid ? b[rr] : T(0); });
+    if (R.valid && R.lane == 0) x[rr] = s * di;
 }
 
 // One Gauss-Seidel update of the rows [r0, r1) of one colour:
@@ -335,15 +310,12 @@ __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
                                                     const T* e, T omega) {
     pdl_launch_dependents();
     const RowOf<LPR> R(r0, r1);
-    if (LPR == kFine && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T di = R.valid ? ldm<LPR == kFine>(dinv + rr) : T(0);
-    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)ldm<LPR == kFine>(rlen + rr) : 0,
-                                                 (int)(sw >> 5),
-                                                 R.lane, jmax,
-                                                 scol, sval, x, b, dinv, agg, t, e, omega,
-                                                 [&] { return R.valid ? b[rr] : T(0); });
+    const T di = R.valid ? dinv[rr] : T(0);
+    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5),
+                                                 R.lane, jmax, scol, sval, x, b, dinv, agg, t, e,
+                                                 omega, [&] { return R.valid ? b[rr] : T(0); });
     if (R.valid && R.lane == 0) x[rr] = s * di;
 }
 
@@ -357,54 +329,220 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
                                                      const T* b, const T* x, T* r) {
     pdl_launch_dependents();
     const RowOf<LPR> R(r0, n);
-    if (LPR == kFine && !R.valid) return;
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T dg = R.valid ? ldm<LPR == kFine>(diag + rr) : T(0);
+    const T dg = R.valid ? diag[rr] : T(0);
     const T v = row_update<LPR, kNbrX, false, T>(
-        base, R.valid ? (int)ldm<LPR == kFine>(rlen + rr) : 0, (int)(sw >> 5), R.lane, n, scol, sval, x, nullptr, nullptr, nullptr,
-        nullptr, nullptr, T(0), [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
+        base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5), R.lane, n, scol, sval, x, nullptr,
+        nullptr, nullptr, nullptr, nullptr, T(0),
+        [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
     if (R.valid && R.lane == 0) r[rr] = v;
 }
 
-// Residual and restriction in one pass (one thread per row) on a two-colour
-// level: the rows of colour 1 ([c1, n)) are sorted by coarse index, so the rows
-// of one aggregate are consecutive (with more colours an aggregate would recur
-// in every colour block).  Each thread stores (t_i) r_i in shared memory; the
+// ---------------------------------------------------------------------------
+// Fine-level kernels: the matrix staged in shared memory by the bulk-copy
+// engine.
+//
+// A block of kBlock threads owns kBlock / 32 consecutive slices, one row per
+// thread.  Those slices are contiguous in scol and sval, so one thread starts
+// two cp.async.bulk copies of them into shared memory, completing on an
+// mbarrier, before the block waits for its predecessor kernel.  The matrix
+// stream (about two thirds of the bytes of a fine-level pass) is then in
+// flight without holding registers, in one request per array and block
+// instead of one per warp and entry.  The copies carry an evict-first L2
+// policy: the fine matrix is read once per pass and is larger than L2, and
+// keeping it out of L2 leaves the coarse levels resident there from one
+// V-cycle to the next.  Row lengths and diagonals are loaded evict-first too.
+// ---------------------------------------------------------------------------
+constexpr int kSlicesPerBlock = kBlock / 32;
+constexpr long long kStageSpinLimit = 1LL << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// Stage `nsl` slices starting at slice `slice0` (width W) into s_col / s_val.
+// Every thread of the block calls it.  Returns false, with AMG_ETIMEOUT
+// recorded in *err, if the copies have not completed within the spin limit.
+template <typename T>
+__device__ bool stage_slices(int64_t slice0, int nsl, int width, const int32_t* scol,
+                             const T* sval, int32_t* s_col, T* s_val, uint64_t* bar,
+                             int32_t* err) {
+    if (width == 0) return true;   // no off-diagonal entries: nothing to stage
+    const uint32_t ub = smem_u32(bar);
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
+        const uint32_t bc = ent * 4u, bv = ent * (uint32_t)sizeof(T);
+        const int64_t e0 = slice0 * 32 * width;
+        uint64_t pol, state;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                     : "=l"(state) : "r"(ub), "r"(bc + bv) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(bc), "r"(ub),
+            "l"(pol) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0), "r"(bv), "r"(ub),
+            "l"(pol) : "memory");
+    }
+    uint32_t done = 0;
+    for (long long it = 0; it < kStageSpinLimit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(ub) : "memory");
+    if (!done) atomicExch(err, AMG_ETIMEOUT);
+    return done != 0;
+}
+
+// The block's slices, its shared-memory tiles and this thread's row.
+template <typename T>
+struct FineTile {
+    int64_t slice0;
+    int nsl;
+    int row;
+    int loc;          // offset of this row's entry 0 in the tiles; entry k at loc + 32 k
+    int32_t* s_col;
+    T* s_val;
+    __device__ FineTile(int r0, int64_t nslices, int width, unsigned char* smem) {
+        slice0 = (int64_t)(r0 >> 5) + (int64_t)blockIdx.x * kSlicesPerBlock;
+        nsl = (int)min((int64_t)kSlicesPerBlock, nslices - slice0);
+        row = (int)(slice0 * 32) + (int)threadIdx.x;
+        loc = (int)(threadIdx.x >> 5) * 32 * width + (int)(threadIdx.x & 31);
+        s_col = reinterpret_cast<int32_t*>(smem);
+        s_val = reinterpret_cast<T*>(smem + (size_t)kBlock * width * sizeof(int32_t));
+    }
+};
+
+// acc - sum over the staged entries of this thread's row with j < jmax
+template <int MODE, bool SCALED, typename T>
+__device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, const T* x,
+                                      const T* b, const T* __restrict__ dinv,
+                                      const int32_t* __restrict__ agg, const T* __restrict__ t,
+                                      const T* e, T omega, T acc) {
+#pragma unroll 4
+    for (int k = 0; k < len; ++k) {
+        const int j = F.s_col[F.loc + 32 * k];
+        const T a = F.s_val[F.loc + 32 * k];
+        if (j < jmax) acc = fmad(-a, nbr_value<MODE, SCALED>(j, x, b, dinv, agg, t, e, omega), acc);
+    }
+    return acc;
+}
+
+// k_first on the fine level; also zeroes the next level's right-hand side
+// for the fused residual-restriction kernel.  Blocks with colour-0 rows only
+// need no matrix.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fine_first(int c1, int c2, int width, int64_t nslices,
+                                                       const uint16_t* __restrict__ rlen,
+                                                       const int32_t* scol, const T* sval,
+                                                       const T* __restrict__ dinv, const T* b,
+                                                       T* x, T* bc_zero, int nc, int32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    pdl_launch_dependents();
+    const FineTile<T> F(0, nslices, width, smem);
+    const bool valid = F.row < c2;
+    const int len = (valid && F.row >= c1) ? (int)__ldcs(rlen + F.row) : 0;
+    const T di = valid ? __ldcs(dinv + F.row) : T(0);
+    const bool staged = (F.slice0 + F.nsl) * 32 > c1;   // block-uniform
+    if (staged && !stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err))
+        return;
+    pdl_wait();
+    if (valid)
+        x[F.row] = fine_row<kNbrFirst, false, T>(F, len, c1, x, b, dinv, nullptr, nullptr, nullptr,
+                                              T(0), b[F.row]) * di;
+    if (bc_zero)
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
+            bc_zero[i] = T(0);
+}
+
+// k_gs_pass on the fine level
+template <int MODE, bool SCALED, typename T>
+__global__ void __launch_bounds__(kBlock) k_fine_pass(int r0, int r1, int jmax, int width,
+                                                      int64_t nslices,
+                                                      const uint16_t* __restrict__ rlen,
+                                                      const int32_t* scol, const T* sval,
+                                                      const T* __restrict__ dinv, const T* b, T* x,
+                                                      const int32_t* __restrict__ agg,
+                                                      const T* __restrict__ t, const T* e,
+                                                      T omega, int32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    pdl_launch_dependents();
+    const FineTile<T> F(r0, nslices, width, smem);
+    const bool valid = F.row >= r0 && F.row < r1;
+    const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
+    const T di = valid ? __ldcs(dinv + F.row) : T(0);
+    if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
+    pdl_wait();
+    if (!valid) return;
+    x[F.row] = fine_row<MODE, SCALED, T>(F, len, jmax, x, b, dinv, agg, t, e, omega, b[F.row]) * di;
+}
+
+// k_residual on the fine level
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fine_residual(int r0, int n, int width,
+                                                          int64_t nslices,
+                                                          const uint16_t* __restrict__ rlen,
+                                                          const int32_t* scol, const T* sval,
+                                                          const T* __restrict__ diag, const T* b,
+                                                          const T* x, T* r, int32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
+    pdl_launch_dependents();
+    const FineTile<T> F(r0, nslices, width, smem);
+    const bool valid = F.row >= r0 && F.row < n;
+    const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
+    const T dg = valid ? __ldcs(diag + F.row) : T(0);
+    if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
+    pdl_wait();
+    if (!valid) return;
+    r[F.row] = fine_row<kNbrX, false, T>(F, len, n, x, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                      T(0), fmad(-dg, x[F.row], b[F.row]));
+}
+
+// Residual and restriction in one pass on a two-colour fine level: the rows
+// of colour 1 ([c1, n)) are sorted by coarse index, so the rows of one
+// aggregate are consecutive (with more colours an aggregate would recur in
+// every colour block).  Each thread stores (t_i) r_i in shared memory; the
 // first row of every run of equal coarse index inside the block sums the run
-// in order and adds it to bc (zeroed by the first pass).  A run is shorter than
-// a block, so a coarse entry receives at most two additions onto zero (a run
-// cut by a block boundary), whose result does not depend on their order: the
-// sum stays deterministic.
+// in order and adds it to bc (zeroed by the first pass).  A run is shorter
+// than a block, so a coarse entry receives at most two additions onto zero (a
+// run cut by a block boundary), whose result does not depend on their order:
+// the sum stays deterministic.
 template <typename T, bool SCALED>
-__global__ void __launch_bounds__(kBlock) k_residual_restrict(int c1, int n,
-                                                              int64_t sw,
-                                                              const uint16_t* __restrict__ rlen,
-                                                              const int32_t* __restrict__ scol,
-                                                              const T* __restrict__ sval,
-                                                              const T* __restrict__ diag,
-                                                              const T* b, const T* x,
-                                                              const int32_t* __restrict__ agg,
-                                                              const T* __restrict__ t, T* bc) {
+__global__ void __launch_bounds__(kBlock) k_fine_residual_restrict(
+    int c1, int n, int width, int64_t nslices, const uint16_t* __restrict__ rlen,
+    const int32_t* scol, const T* sval, const T* __restrict__ diag, const T* b, const T* x,
+    const int32_t* __restrict__ agg, const T* __restrict__ t, T* bc, int32_t* err) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ uint64_t bar;
     __shared__ T sv[kBlock];
     __shared__ int sk[kBlock];
     pdl_launch_dependents();
-    const RowOf<kFine> R(c1, n);
-    int key = -1;
+    const FineTile<T> F(c1, nslices, width, smem);
+    const bool valid = F.row >= c1 && F.row < n;
+    const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
+    const T dg = valid ? __ldcs(diag + F.row) : T(0);
+    const int key = valid ? __ldcs(agg + F.row) : -1;
+    const T ti = (SCALED && valid) ? __ldcs(t + F.row) : T(1);
+    if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
+    pdl_wait();
     T v = T(0);
-    if (R.valid) {
-        const int rr = R.row;
-        const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-        const T dg = __ldcs(diag + rr);
-        key = __ldcs(agg + rr);
-        const T ti = SCALED ? __ldcs(t + rr) : T(1);
-        const T ri = row_update<kFine, kNbrX, false, T>(base, __ldcs(rlen + rr), (int)(sw >> 5), 0, n, scol,
-                                                    sval, x, nullptr,
-                                                    nullptr, nullptr, nullptr, nullptr, T(0),
-                                                    [&] { return fmad(-dg, x[rr], b[rr]); });
+    if (valid) {
+        const T ri = fine_row<kNbrX, false, T>(F, len, n, x, nullptr, nullptr, nullptr, nullptr,
+                                            nullptr, T(0), fmad(-dg, x[F.row], b[F.row]));
         v = SCALED ? ti * ri : ri;
     }
-    pdl_wait();
     const int tid = threadIdx.x;
     sv[tid] = v;
     sk[tid] = key;
@@ -675,7 +813,6 @@ inline int launch_lpr(const DevLevel& L, int rows) {
 
 #define AMG_LPR_DISPATCH(lpr, CALL)                          \
     switch (lpr) {                                           \
-        case kFine: { constexpr int LPR = kFine; CALL; } break; \
         case 1: { constexpr int LPR = 1; CALL; } break;      \
         case 2: { constexpr int LPR = 2; CALL; } break;      \
         case 4: { constexpr int LPR = 4; CALL; } break;      \
@@ -695,12 +832,33 @@ struct LevelArrays<float> {
     explicit LevelArrays(const DevLevel& L) : sval(L.sval32), dinv(L.dinv32), diag(L.diag32), t(L.t32) {}
 };
 
+// fine-level launches: one block per kBlock / 32 slices, the slices staged
+// in dynamic shared memory (column indices, then values)
+inline int fine_blocks(int r0, int r1) { return blocks_for((int64_t)r1 - (r0 & ~31)); }
+inline int64_t fine_nslices(const DevLevel& L) { return ((int64_t)L.n + 31) / 32; }
+template <typename K>
+size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
+    const size_t bytes = (size_t)kBlock * L.width * (sizeof(int32_t) + value_bytes);
+    if (bytes > 48 * 1024)
+        AMG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)bytes));
+    return bytes;
+}
+
 template <typename T>
 void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStream_t s) {
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
-    AMG_LPR_DISPATCH(launch_lpr(L, c2), (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock, 0, s, 
-                                c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero, nc)));
+    if (L.lpr == kFine) {
+        auto k = k_fine_first<T>;
+        launch_kernel(k, std::max(1, fine_blocks(0, c2)), kBlock, fine_smem(k, L, sizeof(T)), s, c1,
+                      c2, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero,
+                      nc, L.err);
+        return;
+    }
+    AMG_LPR_DISPATCH(launch_lpr(L, c2),
+                     (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock,
+                                    0, s, c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
 }
 
 template <typename T, int MODE>
@@ -710,9 +868,17 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* 
     const int r0 = L.cptr[col], r1 = L.cptr[col + 1];
     if (r1 <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
-    AMG_LPR_DISPATCH(launch_lpr(L, r1 - r0), (launch_kernel(k_gs_pass<LPR, MODE, SC, T>, row_blocks(r0, r1, LPR), kBlock, 0, s, 
-                                r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg,
-                                A.t, e, (T)omega)));
+    if (L.lpr == kFine) {
+        auto k = k_fine_pass<MODE, SC, T>;
+        launch_kernel(k, fine_blocks(r0, r1), kBlock, fine_smem(k, L, sizeof(T)), s, r0, r1, jmax,
+                      L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg, A.t,
+                      e, (T)omega, L.err);
+        return;
+    }
+    AMG_LPR_DISPATCH(launch_lpr(L, r1 - r0),
+                     (launch_kernel(k_gs_pass<LPR, MODE, SC, T>, row_blocks(r0, r1, LPR), kBlock, 0,
+                                    s, r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x,
+                                    L.agg, A.t, e, (T)omega)));
 }
 
 template <typename T>
@@ -722,16 +888,28 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
     const int c1 = L.cptr[1];
     constexpr bool SC = std::is_same<T, float>::value;
     if (L.fused_restrict) {
-        if (L.n > c1)
-            launch_kernel(k_residual_restrict<T, SC>, row_blocks(c1, L.n, 1), kBlock, 0, s, 
-                c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg, A.t, bc);
+        if (L.n > c1) {
+            auto k = k_fine_residual_restrict<T, SC>;
+            launch_kernel(k, fine_blocks(c1, L.n), kBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
+                          L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, L.agg,
+                          A.t, bc, L.err);
+        }
         return;
     }
-    if (L.n > c1)
-        AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1), (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR), kBlock, 0, s, 
-                                    c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x, r)));
-    launch_kernel(k_restrict<T, SC>, blocks_for(L.n_coarse), kBlock, 0, s, L.n_coarse, L.rptr, L.ridx, A.t, r,
-                                                                bc);
+    if (L.n > c1) {
+        if (L.lpr == kFine) {
+            auto k = k_fine_residual<T>;
+            launch_kernel(k, fine_blocks(c1, L.n), kBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
+                          L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, r, L.err);
+        } else {
+            AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1),
+                             (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR), kBlock, 0,
+                                            s, c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x,
+                                            r)));
+        }
+    }
+    launch_kernel(k_restrict<T, SC>, blocks_for(L.n_coarse), kBlock, 0, s, L.n_coarse, L.rptr,
+                  L.ridx, A.t, r, bc);
 }
 
 template <typename T>

@@ -364,10 +364,11 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
                                                     d_nva, L.diag, L.dinv);
     k_csr_to_sell<<<blocks_for(n), kBlock, 0, s>>>(n, d_nrp, d_nci, d_nva, width, L.scol, L.sval);
     AMG_CUDA_TRY(cudaGetLastError());
-    // lanes per row: one on sparse rows (float64 arithmetic bound), several on
-    // the denser coarse rows (gather latency bound)
+    // lanes per row: the staged one-row-per-thread kernels on sparse rows
+    // (bandwidth bound), several lanes on the denser coarse rows (gather
+    // latency bound)
     const double avg = n > 0 ? (double)L.nnz_off / n : 0.0;
-    L.lpr = avg <= 7.0 ? 0 : avg <= 16.0 ? 4 : 8;
+    L.lpr = (avg <= 7.0 && width <= kFineMaxWidth) ? 0 : avg <= 16.0 ? 4 : 8;
     L.lpr_wide = L.lpr;
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 }

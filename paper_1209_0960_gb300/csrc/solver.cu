@@ -3,6 +3,7 @@
 // Sec. 2.1 coarsening, Sec. 5 solver configuration).
 
 #include <algorithm>
+#include <cstddef>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -682,6 +683,12 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     c->work.counters = c->mem.alloc<unsigned int>(16);
     AMG_CUDA_TRY(cudaMemsetAsync(c->work.counters, 0, sizeof(unsigned int) * 16, s));
     c->work.sc = c->mem.alloc<PcgScalars>(1);
+    AMG_CUDA_TRY(cudaMemsetAsync(c->work.sc, 0, sizeof(PcgScalars), s));
+    // kernel-side errors (a bounded wait that ran out) land in the CG status
+    // word, which the iteration loop reads back every iteration
+    for (DevLevel& L : c->dl)
+        L.err = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(c->work.sc) +
+                                           offsetof(PcgScalars, status));
     c->norm_dev = c->mem.alloc<double>(1);
     AMG_CUDA_TRY(cudaMallocHost(&c->sc_host, sizeof(PcgScalars)));
     AMG_CUDA_TRY(cudaEventCreate(&c->ev0));
