@@ -52,6 +52,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--launch-overlap", type=int, choices=[0, 1], default=1,
                     help="programmatic dependent launch between solve kernels")
+    ap.add_argument("--profile-run", type=int, default=0, metavar="MAXIT",
+                    help="for profilers: set up the workload, run one FP64 solve capped at "
+                         "MAXIT iterations, print nothing else and exit")
     return ap.parse_args()
 
 
@@ -434,8 +437,25 @@ def run_ours(args, dist: Dist):
         print(json.dumps(line), flush=True)
 
 
+def profile_run(args):
+    """One capped FP64 solve of the workload, for ncu captures of single kernels."""
+    import torch
+    from paper_1209_0960_gb300 import amg
+    torch.cuda.set_device(0)
+    p = make_problem(args.grid)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap)
+    b = torch.from_numpy(p.b).cuda()
+    x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)
+    torch.cuda.synchronize()
+    print(f"profile run: rc {rc}, {info['iterations']} iterations")
+    solver.close()
+
+
 def main():
     args = parse_args()
+    if args.profile_run > 0:
+        profile_run(args)
+        return
     dist = Dist()
     try:
         if args.impl == "reference":

@@ -606,25 +606,39 @@ __global__ void __launch_bounds__(kBlock) k_prolong(int r0, int n, const int32_t
 }
 
 // x = M b, M dense row-major (coarsest-level solve with the inverse formed at
-// setup); one warp per row, float64 arithmetic.
+// setup); one warp per row, float64 arithmetic.  A float32 b is first copied,
+// converted to float64, into shared memory by the block: every row reads all
+// of b, and reading it as float32 would cost a conversion per matrix entry on
+// the float64 pipe.  A float64 b is read directly (L1 serves the rows of the
+// block).
 template <typename TB>
 __global__ void __launch_bounds__(kBlock) k_dense_gemv(int n, const double* __restrict__ M,
                                                        const TB* b, TB* x) {
     constexpr int kPre = 4;   // row entries per lane loaded before the wait
+    constexpr bool kStage = !std::is_same<TB, double>::value;
+    extern __shared__ double sbuf[];
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31;
     const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    if (row >= n) return;
-    const double* m = M + (size_t)row * n;
+    const double* m = M + (size_t)min(row, n - 1) * n;
     double m0[kPre];
 #pragma unroll
     for (int u = 0; u < kPre; ++u) m0[u] = (lane + 32 * u < n) ? m[lane + 32 * u] : 0.0;
     pdl_wait();
+    const double* sb;
+    if (kStage) {
+        for (int k = threadIdx.x; k < n; k += blockDim.x) sbuf[k] = (double)b[k];
+        __syncthreads();
+        sb = sbuf;
+    } else {
+        sb = reinterpret_cast<const double*>(b);
+    }
+    if (row >= n) return;
     double s = 0.0;
 #pragma unroll
     for (int u = 0; u < kPre; ++u)
-        if (lane + 32 * u < n) s += m0[u] * (double)b[lane + 32 * u];
-    for (int k = lane + 32 * kPre; k < n; k += 32) s += m[k] * (double)b[k];
+        if (lane + 32 * u < n) s += m0[u] * sb[lane + 32 * u];
+    for (int k = lane + 32 * kPre; k < n; k += 32) s += m[k] * sb[k];
     s = group_sum<32>(s);
     if (lane == 0) x[row] = (TB)s;
 }
@@ -958,12 +972,21 @@ void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega,
     prolong_impl<float>(L, e, x, omega, s);
 }
 
+template <typename TB>
+void dense_gemv_impl(int n, const double* M, const TB* b, TB* x, cudaStream_t s) {
+    auto k = k_dense_gemv<TB>;
+    const size_t smem = std::is_same<TB, double>::value ? 0 : sizeof(double) * (size_t)n;
+    if (smem > 48 * 1024)
+        AMG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch_kernel(k, blocks_for((int64_t)n * 32), kBlock, smem, s, n, M, b, x);
+}
+
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s) {
-    launch_kernel(k_dense_gemv<double>, blocks_for((int64_t)n * 32), kBlock, 0, s, n, M, b, x);
+    dense_gemv_impl<double>(n, M, b, x, s);
 }
 
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s) {
-    launch_kernel(k_dense_gemv<float>, blocks_for((int64_t)n * 32), kBlock, 0, s, n, M, b, x);
+    dense_gemv_impl<float>(n, M, b, x, s);
 }
 
 void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s) {
