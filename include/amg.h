@@ -250,6 +250,84 @@ int amg_profile_read(amg_ctx *c, amg_kernel_stat *stats, int32_t cap);
 /* Release every resource of the context (NULL is allowed). */
 int amg_free(amg_ctx *c);
 
+/* ---------------------------------------------------------------------------
+ * Serving: many independent solves A_k x_k = b_k with continuous batching.
+ *
+ * A server owns a scheduling thread and a pool of setup threads.  Submitted
+ * requests wait in FIFO order until a slot and enough device memory are free
+ * (admission by HBM: each request reserves an estimate of its hierarchy and
+ * Krylov state, replaced by the actual size after setup).  An admitted
+ * request is set up on a setup thread (host aggregation, then the GPU
+ * Galerkin products on the request's own stream) and then joins the running
+ * set; the scheduling thread advances every running solve one CG iteration
+ * at a time (CUDA graphs per request, on per-request streams, never blocking
+ * on any of them), so the iterations and V-cycles of all in-flight solves
+ * overlap on the device, new requests are admitted as soon as a finished one
+ * frees its slot, and a result is exactly the one amg_setup + amg_pcg_solve
+ * give for the same request alone.  The method per request is the one of the
+ * rest of this interface (Sec. 2, Sec. 5).
+ * ------------------------------------------------------------------------- */
+typedef struct amg_server amg_server;
+
+typedef struct {
+    amg_params params;        /* setup and solve parameters of every request
+                                 (cuda_stream is ignored: each request gets its
+                                 own stream) */
+    int32_t max_slots;        /* most requests admitted at once; default 32 */
+    int32_t setup_threads;    /* host threads running request setup; default 4 */
+    int32_t maxit;            /* CG iteration cap per request; default 500 */
+    double hbm_budget_bytes;  /* device memory the admitted requests may reserve;
+                                 <= 0: 80 % of the free device memory at creation */
+} amg_server_params;
+
+/* Timings of one request (host steady clock, milliseconds). */
+typedef struct {
+    double queue_ms;          /* submit -> admitted */
+    double setup_ms;          /* admitted -> hierarchy ready */
+    double solve_ms;          /* ready -> solution on the host */
+    double total_ms;          /* submit -> solution on the host */
+    double hbm_bytes;         /* device memory the request held */
+} amg_request_times;
+
+/* Server totals since creation. */
+typedef struct {
+    int64_t submitted, completed, failed;
+    int32_t queued, running, peak_running;
+    double hbm_reserved_bytes, hbm_budget_bytes;
+} amg_server_stats;
+
+/* Defaults: params = amg_params_default(dim) with precision
+ * AMG_FP32_IN_FP64 and a coarsening target of 1000 rows (the dense coarsest
+ * factorisation is per-request setup work), max_slots 32, setup_threads 4,
+ * maxit 500, hbm_budget_bytes 0.  Errors: AMG_EINVAL. */
+int amg_server_params_default(amg_server_params *p, int32_t dim);
+
+/* Create a server on the current device and start its threads.
+ * Errors: AMG_EINVAL (bad parameters), AMG_ECUDA. */
+int amg_server_create(const amg_server_params *p, amg_server **out);
+
+/* Queue the solve of A x = b to relative residual tol (x0 = 0).  A is a host
+ * CSR matrix (on_device must be 0), b a host vector of A->n doubles; both are
+ * copied before the call returns.  *ticket identifies the request.  Errors:
+ * AMG_EINVAL (malformed matrix, tol < 0, server stopping). */
+int amg_submit(amg_server *s, const amg_csr *A, const double *b, double tol, uint64_t *ticket);
+
+/* Non-blocking.  AMG_PENDING while the request is queued, being set up or
+ * solving.  Once it has finished: copies the solution (A->n doubles, caller
+ * numbering) to x_out and the solve record to info and the timings to times
+ * (each may be NULL), forgets the ticket and returns the request's status
+ * (AMG_OK, AMG_ENOTCONV, AMG_ENOTSPD, AMG_ENOMEM, ...).  Unknown or already
+ * collected tickets: AMG_ENOTFOUND. */
+int amg_poll(amg_server *s, uint64_t ticket, double *x_out, amg_solve_info *info,
+             amg_request_times *times);
+
+/* Snapshot of the server's counters.  Errors: AMG_EINVAL. */
+int amg_server_stats_read(amg_server *s, amg_server_stats *out);
+
+/* Stop the threads (running solves finish first; queued requests are
+ * dropped), release every resource.  NULL is allowed. */
+int amg_server_destroy(amg_server *s);
+
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *amg_last_error(void);
 

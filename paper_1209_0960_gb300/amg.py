@@ -72,6 +72,23 @@ class amg_kernel_stat(ctypes.Structure):
                 ("bytes", _c_dbl)]
 
 
+class amg_server_params(ctypes.Structure):
+    _fields_ = [("params", amg_params), ("max_slots", _c_i32), ("setup_threads", _c_i32),
+                ("maxit", _c_i32), ("hbm_budget_bytes", _c_dbl)]
+
+
+class amg_request_times(ctypes.Structure):
+    _fields_ = [("queue_ms", _c_dbl), ("setup_ms", _c_dbl), ("solve_ms", _c_dbl),
+                ("total_ms", _c_dbl), ("hbm_bytes", _c_dbl)]
+
+
+class amg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("queued", _c_i32), ("running", _c_i32),
+                ("peak_running", _c_i32), ("hbm_reserved_bytes", _c_dbl),
+                ("hbm_budget_bytes", _c_dbl)]
+
+
 def struct_dict(s) -> dict:
     return {name: getattr(s, name) for name, _ in s._fields_}
 
@@ -99,6 +116,13 @@ _SIGNATURES = {
     "amg_profile_enable": ([_c_vp, _c_i32], ctypes.c_int),
     "amg_profile_read": ([_c_vp, ctypes.POINTER(amg_kernel_stat), _c_i32], ctypes.c_int),
     "amg_free": ([_c_vp], ctypes.c_int),
+    "amg_server_params_default": ([ctypes.POINTER(amg_server_params), _c_i32], ctypes.c_int),
+    "amg_server_create": ([ctypes.POINTER(amg_server_params), ctypes.POINTER(_c_vp)], ctypes.c_int),
+    "amg_submit": ([_c_vp, ctypes.POINTER(amg_csr), _c_vp, _c_dbl, ctypes.POINTER(ctypes.c_uint64)], ctypes.c_int),
+    "amg_poll": ([_c_vp, ctypes.c_uint64, _c_vp, ctypes.POINTER(amg_solve_info),
+                  ctypes.POINTER(amg_request_times)], ctypes.c_int),
+    "amg_server_stats_read": ([_c_vp, ctypes.POINTER(amg_server_stats)], ctypes.c_int),
+    "amg_server_destroy": ([_c_vp], ctypes.c_int),
     "amg_last_error": ([], ctypes.c_char_p),
 }
 
@@ -351,3 +375,98 @@ class AMG:
 
     def level(self, l: int) -> dict:
         return amg_export_level(self.ctx, l)
+
+
+# ---------------------------------------------------------------------------
+# serving
+# ---------------------------------------------------------------------------
+
+def amg_server_params_default(dim: int) -> amg_server_params:
+    p = amg_server_params()
+    _check(lib().amg_server_params_default(ctypes.byref(p), dim), "amg_server_params_default")
+    return p
+
+
+def amg_server_create(params: amg_server_params) -> int:
+    h = _c_vp()
+    _check(lib().amg_server_create(ctypes.byref(params), ctypes.byref(h)), "amg_server_create")
+    return h.value
+
+
+def amg_submit(server: int, row_ptr, col, val, b, tol: float) -> int:
+    """Host (numpy) matrix and right-hand side; both are copied."""
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int32)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    A = amg_csr(int(row_ptr.shape[0]) - 1, int(col.shape[0]), _ptr(row_ptr), _ptr(col), _ptr(val), 0)
+    t = ctypes.c_uint64()
+    _check(lib().amg_submit(server, ctypes.byref(A), _ptr(b), float(tol), ctypes.byref(t)),
+           "amg_submit")
+    return t.value
+
+
+def amg_poll(server: int, ticket: int, x_out: Optional[np.ndarray]):
+    """Returns (rc, info dict, times dict); rc == AMG_PENDING while unfinished.
+    Negative solve statuses (ENOTCONV, ...) are returned, not raised; an
+    unknown ticket raises."""
+    info = amg_solve_info()
+    times = amg_request_times()
+    rc = lib().amg_poll(server, ticket, _ptr(x_out), ctypes.byref(info), ctypes.byref(times))
+    if rc == AMG_ENOTFOUND or rc == AMG_EINVAL:
+        _check(rc, "amg_poll")
+    return rc, struct_dict(info), struct_dict(times)
+
+
+def amg_server_stats_read(server: int) -> dict:
+    st = amg_server_stats()
+    _check(lib().amg_server_stats_read(server, ctypes.byref(st)), "amg_server_stats_read")
+    return struct_dict(st)
+
+
+def amg_server_destroy(server: int) -> None:
+    if server:
+        lib().amg_server_destroy(server)
+
+
+class Server:
+    """Owns one server.  submit() takes numpy CSR + b and returns a ticket;
+    poll() returns None while pending, else (status, x, info, times)."""
+
+    def __init__(self, dim: int = 3, **overrides):
+        self.params = amg_server_params_default(dim)
+        for k, v in overrides.items():
+            if hasattr(self.params.params, k) and k not in ("max_slots", "setup_threads", "maxit",
+                                                             "hbm_budget_bytes"):
+                setattr(self.params.params, k, v)
+            else:
+                setattr(self.params, k, v)
+        self.handle = amg_server_create(self.params)
+        self._n = {}
+
+    def submit(self, row_ptr, col, val, b, tol: float = 1e-8) -> int:
+        t = amg_submit(self.handle, row_ptr, col, val, b, tol)
+        self._n[t] = int(np.asarray(row_ptr).shape[0]) - 1
+        return t
+
+    def poll(self, ticket: int):
+        x = np.empty(self._n[ticket])
+        rc, info, times = amg_poll(self.handle, ticket, x)
+        if rc == AMG_PENDING:
+            return None
+        del self._n[ticket]
+        return rc, x, info, times
+
+    def stats(self) -> dict:
+        return amg_server_stats_read(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            amg_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

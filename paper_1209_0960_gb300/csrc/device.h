@@ -32,34 +32,42 @@ void set_last_error(const std::string& msg);
 
 // ---------------------------------------------------------------------------
 // device memory owned by a context
+//
+// Allocations are stream-ordered (cudaMallocAsync / cudaFreeAsync on the
+// owner's stream): freeing a context or a setup temporary does not wait for
+// the whole device, so contexts that set up or retire while others solve (the
+// server) do not stall them.  Without a stream the arena falls back to
+// cudaMalloc / cudaFree.
 // ---------------------------------------------------------------------------
 class DevArena {
 public:
+    DevArena() = default;
+    explicit DevArena(cudaStream_t s) : stream_(s), async_(true) {}
+    DevArena(const DevArena&) = delete;
+    DevArena& operator=(const DevArena&) = delete;
     ~DevArena() { release(); }
+    void set_stream(cudaStream_t s) {
+        stream_ = s;
+        async_ = true;
+    }
     template <typename T>
     T* alloc(size_t count) {
         if (count == 0) count = 1;
         void* p = nullptr;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        const size_t bytes = count * sizeof(T);
+        cudaError_t e = async_ ? cudaMallocAsync(&p, bytes, stream_) : cudaMalloc(&p, bytes);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            throw Error{AMG_ENOMEM, "cudaMalloc of " + std::to_string(count * sizeof(T)) +
+            throw Error{AMG_ENOMEM, "device allocation of " + std::to_string(bytes) +
                                         " bytes failed: " + cudaGetErrorString(e)};
         }
         ptrs_.push_back(p);
-        bytes_ += count * sizeof(T);
+        bytes_ += bytes;
         return static_cast<T*>(p);
-    }
-    void free_one(void* p) {
-        for (auto& q : ptrs_)
-            if (q == p) {
-                cudaFree(q);
-                q = nullptr;
-            }
     }
     void release() {
         for (void* p : ptrs_)
-            if (p) cudaFree(p);
+            if (p) async_ ? cudaFreeAsync(p, stream_) : cudaFree(p);
         ptrs_.clear();
         bytes_ = 0;
     }
@@ -68,7 +76,16 @@ public:
 private:
     std::vector<void*> ptrs_;
     size_t bytes_ = 0;
+    cudaStream_t stream_ = nullptr;
+    bool async_ = false;
 };
+
+// Pinned host memory from a process-wide pool: blocks are rounded up to a
+// power of two, reused after pinned_free and never returned to the driver
+// (freeing pinned memory can wait for the whole device, which would stall
+// other contexts' solves).  Thread-safe.
+void* pinned_alloc(size_t bytes);
+void pinned_free(void* p);
 
 // Scalars of the CG recurrence, resident on the device.
 struct PcgScalars {
@@ -300,6 +317,18 @@ void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, c
 
 }  // namespace amg
 
+// State of a CG solve driven one step at a time (pcg_async_*).
+struct AsyncCg {
+    enum State { kIdle, kStarted, kIterating, kFinishing, kDone };
+    State state = kIdle;
+    double tol = 0.0;
+    int32_t maxit = 0;
+    int status = 0;
+    amg_solve_info info{};
+    cudaEvent_t ev = nullptr;       // completes when the work of the current step is done
+    double* rr_host = nullptr;      // pinned: ||b - A x||^2 of the final iterate
+};
+
 struct amg_ctx {
     amg_params p;
     int device = 0;
@@ -333,12 +362,15 @@ struct amg_ctx {
     std::vector<amg_level_info> linfo;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     amg::Profiler prof;
+    AsyncCg acg;
 
     amg_ctx() = default;
     amg_ctx(const amg_ctx&) = delete;
     amg_ctx& operator=(const amg_ctx&) = delete;
     ~amg_ctx() {
-        if (sc_host) cudaFreeHost(sc_host);
+        if (sc_host) amg::pinned_free(sc_host);
+        if (acg.rr_host) amg::pinned_free(acg.rr_host);
+        if (acg.ev) cudaEventDestroy(acg.ev);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);
         for (cudaEvent_t e : prof.events) cudaEventDestroy(e);
@@ -352,9 +384,20 @@ struct amg_ctx {
                 if (g) cudaGraphExecDestroy(g);
         if (ev_in) cudaEventDestroy(ev_in);
         if (ev_out) cudaEventDestroy(ev_out);
+        mem.release();   // stream-ordered frees, before the stream goes away
         if (stream) {
             cudaStreamSynchronize(stream);
             cudaStreamDestroy(stream);
         }
     }
 };
+
+namespace amg {
+// CG driven one step at a time on a context's own stream (solver.cu); the
+// launches, and so the results, are those of amg_pcg_solve.  begin expects the
+// right-hand side in c->bb and the initial guess in c->x (smoothing order).
+// step never blocks: 0 = the previous step's work is still running, 1 = the
+// next step was issued, 2 = the solve has finished and c->acg.info is final.
+void pcg_async_begin(amg_ctx* c, double tol, int32_t maxit);
+int pcg_async_step(amg_ctx* c);
+}  // namespace amg

@@ -285,7 +285,7 @@ void galerkin_device(const DevCsr& A, const HostCsr& Ah, const AggResult& R, Dev
         AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
-    DevArena tmp;
+    DevArena tmp(s);
     int32_t* d_agg = tmp.alloc<int32_t>(n);
     int32_t* d_mptr = tmp.alloc<int32_t>(nc + 1);
     int32_t* d_mem = tmp.alloc<int32_t>(mem.size());
@@ -350,7 +350,7 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
     L.sval = arena.alloc<double>(L.padded);
     L.diag = arena.alloc<double>(n);
     L.dinv = arena.alloc<double>(n);
-    DevArena tmp;
+    DevArena tmp(s);
     int32_t* d_inv = tmp.alloc<int32_t>(n);
     int32_t* d_perm = tmp.alloc<int32_t>(n);
     int32_t* d_nrp = tmp.alloc<int32_t>(n + 1);
@@ -375,7 +375,7 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
 
 bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
     const int n = A.n;
-    DevArena tmp;
+    DevArena tmp(s);
     double* L = tmp.alloc<double>((size_t)n * n);
     int* err = tmp.alloc<int>(1);
     AMG_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(double) * (size_t)n * n, s));

@@ -8,7 +8,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <type_traits>
 
@@ -377,76 +379,112 @@ cudaGraphExec_t capture_graph(amg_ctx* c, F&& f) {
 // ---------------------------------------------------------------------------
 // preconditioned CG on level-0 vectors in smoothing order (c->bb, c->x)
 // ---------------------------------------------------------------------------
-int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
-    cudaStream_t s = c->stream;
+
+// One CG iteration is two parts.  A: q = A p, alpha, x/r update, copy of the
+// CG scalars to the host.  B: z = B r, beta, p update.
+void cg_part_a(amg_ctx* c) {
     DevLevel& L0 = c->dl[0];
     const int n = L0.n;
+    cudaStream_t s = c->stream;
+    {
+        ProfScope ps(c, kKCgSpmv, (double)L0.nnz_off * 12 + 2.0 * n + 24.0 * n);
+        launch_cg_spmv_pq(L0, c->pv, c->q, c->work, s);
+    }
+    {
+        ProfScope ps(c, kKCgUpdate, 48.0 * n);
+        launch_cg_update(n, c->x, c->r, c->pv, c->q, c->work, s);
+    }
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+}
+
+void cg_part_b(amg_ctx* c) {
+    const int n = c->dl[0].n;
+    cudaStream_t s = c->stream;
+    precondition(c, c->r, c->z);
+    {
+        ProfScope ps(c, kKCgDot, (c->flexible ? 24.0 : 16.0) * n);
+        launch_cg_rz(n, c->r, c->z, c->zold, c->pv, c->work, c->flexible ? kRZFlex : kRZ, s);
+    }
+    {
+        ProfScope ps(c, kKCgP, (c->flexible ? 32.0 : 24.0) * n);
+        launch_cg_p(n, c->z, c->pv, c->flexible ? c->zold : nullptr, c->work, s);
+    }
+}
+
+bool cg_graphs(const amg_ctx* c) { return c->use_graphs && !c->prof.on; }
+
+void run_part_a(amg_ctx* c) {
+    if (!cg_graphs(c)) return cg_part_a(c);
+    cudaGraphExec_t& ga = c->graph_a[c->precision][c->flexible];
+    if (!ga) ga = capture_graph(c, [&] { cg_part_a(c); });
+    ProfScope ps(c, kKGraphA, 0.0, true);
+    AMG_CUDA_TRY(cudaGraphLaunch(ga, c->stream));
+}
+
+void run_part_b(amg_ctx* c) {
+    if (!cg_graphs(c)) return cg_part_b(c);
+    cudaGraphExec_t& gb = c->graph_b[c->precision][c->flexible];
+    if (!gb) gb = capture_graph(c, [&] { cg_part_b(c); });
+    ProfScope ps(c, kKGraphB, 0.0, true);
+    AMG_CUDA_TRY(cudaGraphLaunch(gb, c->stream));
+}
+
+// CG start: scalars to the device, r = b - A x, ||r||^2 and the scalars back
+void cg_start(amg_ctx* c, double tol, int32_t maxit) {
+    cudaStream_t s = c->stream;
     PcgScalars init{};
     init.tol2 = tol * tol;
     init.flexible = c->flexible;
     init.maxit = maxit;
     *c->sc_host = init;
     AMG_CUDA_TRY(cudaMemcpyAsync(c->work.sc, c->sc_host, sizeof(PcgScalars), cudaMemcpyHostToDevice, s));
-    launch_cg_residual(L0, c->bb, c->x, c->r, c->work, kRR0, nullptr, s);
+    launch_cg_residual(c->dl[0], c->bb, c->x, c->r, c->work, kRR0, nullptr, s);
     AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+}
+
+// first preconditioning: z = B r, rho = r.z, p = z
+void cg_first_direction(amg_ctx* c) {
+    const int n = c->dl[0].n;
+    cudaStream_t s = c->stream;
+    precondition(c, c->r, c->z);
+    launch_cg_rz(n, c->r, c->z, nullptr, c->pv, c->work, kRho0, s);
+    if (c->flexible)
+        AMG_CUDA_TRY(cudaMemcpyAsync(c->zold, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+}
+
+// true residual of the final iterate into c->norm_dev
+void cg_true_residual(amg_ctx* c) {
+    launch_cg_residual(c->dl[0], c->bb, c->x, nullptr, c->work, kStore, c->norm_dev, c->stream);
+}
+
+void cg_fill_info(const amg_ctx* c, int status, double rr_true, amg_solve_info* info) {
+    const PcgScalars& h = *c->sc_host;
+    info->status = status;
+    info->iterations = h.iters;
+    info->rel_residual = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
+    info->true_rel_residual = h.rr0 > 0 ? std::sqrt(rr_true / h.rr0) : 0.0;
+}
+
+int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
+    cudaStream_t s = c->stream;
+    cg_start(c, tol, maxit);
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     int status = AMG_OK;
     if (!c->sc_host->done) {
-        precondition(c, c->r, c->z);
-        launch_cg_rz(n, c->r, c->z, nullptr, c->pv, c->work, kRho0, s);
-        if (c->flexible)
-            AMG_CUDA_TRY(cudaMemcpyAsync(c->zold, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        auto part_a = [&] {
-            {
-                ProfScope ps(c, kKCgSpmv, (double)L0.nnz_off * 12 + 2.0 * n + 24.0 * n);
-                launch_cg_spmv_pq(L0, c->pv, c->q, c->work, s);
-            }
-            {
-                ProfScope ps(c, kKCgUpdate, 48.0 * n);
-                launch_cg_update(n, c->x, c->r, c->pv, c->q, c->work, s);
-            }
-            AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars),
-                                         cudaMemcpyDeviceToHost, s));
-        };
-        auto part_b = [&] {
-            precondition(c, c->r, c->z);
-            {
-                ProfScope ps(c, kKCgDot, (c->flexible ? 24.0 : 16.0) * n);
-                launch_cg_rz(n, c->r, c->z, c->zold, c->pv, c->work, c->flexible ? kRZFlex : kRZ, s);
-            }
-            {
-                ProfScope ps(c, kKCgP, (c->flexible ? 32.0 : 24.0) * n);
-                launch_cg_p(n, c->z, c->pv, c->flexible ? c->zold : nullptr, c->work, s);
-            }
-        };
-        const bool graphs = c->use_graphs && !c->prof.on;
-        cudaGraphExec_t& ga = c->graph_a[c->precision][c->flexible];
-        cudaGraphExec_t& gb = c->graph_b[c->precision][c->flexible];
-        if (graphs && !ga) ga = capture_graph(c, part_a);
-        if (graphs && !gb) gb = capture_graph(c, part_b);
+        cg_first_direction(c);
         while (true) {
             if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
-            if (graphs) {
-                ProfScope ps(c, kKGraphA, 0.0, true);
-                AMG_CUDA_TRY(cudaGraphLaunch(ga, s));
-            } else {
-                part_a();
-            }
+            run_part_a(c);
             AMG_CUDA_TRY(cudaStreamSynchronize(s));
             if (c->sc_host->status != 0) { status = c->sc_host->status; break; }
             if (c->sc_host->done) break;
             if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
-            if (graphs) {
-                ProfScope ps(c, kKGraphB, 0.0, true);
-                AMG_CUDA_TRY(cudaGraphLaunch(gb, s));
-            } else {
-                part_b();
-            }
+            run_part_b(c);
         }
         // graph-level profiling: time the V-cycle from each level l >= 1 alone
         // (diagnostic replays after the solve; they rewrite only coarse-level
         // scratch vectors, which the next V-cycle recomputes)
-        if (graphs && c->prof.graphs && c->dl.size() > 1) {
+        if (cg_graphs(c) && c->prof.graphs && c->dl.size() > 1) {
             auto& gv = c->graph_from[c->precision];
             gv.resize(c->dl.size(), nullptr);
             for (int l = 1; l < (int)c->dl.size(); ++l) {
@@ -464,19 +502,86 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     }
     AMG_CUDA_TRY(cudaGetLastError());
     if (info) {
-        const PcgScalars& h = *c->sc_host;
-        info->status = status;
-        info->iterations = h.iters;
-        info->rel_residual = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
-        // true residual of the final iterate
-        launch_cg_residual(L0, c->bb, c->x, nullptr, c->work, kStore, c->norm_dev, s);
+        cg_true_residual(c);
         double rr = 0.0;
         AMG_CUDA_TRY(cudaMemcpyAsync(&rr, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
         AMG_CUDA_TRY(cudaStreamSynchronize(s));
-        info->true_rel_residual = h.rr0 > 0 ? std::sqrt(rr / h.rr0) : 0.0;
+        cg_fill_info(c, status, rr, info);
     }
     return status;
 }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// the same CG, one step at a time, for the server: every step issues work on
+// the context's stream and records an event; the next step runs once that
+// event has completed, so the host never blocks and many contexts iterate
+// concurrently on the device.  The issued launches, and so the results, are
+// exactly those of pcg().
+// ---------------------------------------------------------------------------
+void pcg_async_begin(amg_ctx* c, double tol, int32_t maxit) {
+    AsyncCg& a = c->acg;
+    if (!a.ev) AMG_CUDA_TRY(cudaEventCreateWithFlags(&a.ev, cudaEventDisableTiming));
+    if (!a.rr_host) a.rr_host = static_cast<double*>(pinned_alloc(sizeof(double)));
+    a.tol = tol;
+    a.maxit = maxit;
+    a.status = AMG_OK;
+    t_launch_overlap = c->p.launch_overlap != 0;
+    cg_start(c, tol, maxit);
+    AMG_CUDA_TRY(cudaEventRecord(a.ev, c->stream));
+    a.state = AsyncCg::kStarted;
+}
+
+// issues the true-residual computation and its copy to the host
+static void async_finish(amg_ctx* c, int status) {
+    AsyncCg& a = c->acg;
+    a.status = status;
+    cg_true_residual(c);
+    AMG_CUDA_TRY(cudaMemcpyAsync(a.rr_host, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost,
+                                 c->stream));
+    AMG_CUDA_TRY(cudaEventRecord(a.ev, c->stream));
+    a.state = AsyncCg::kFinishing;
+}
+
+int pcg_async_step(amg_ctx* c) {
+    AsyncCg& a = c->acg;
+    if (a.state == AsyncCg::kDone) return 2;
+    if (a.state == AsyncCg::kIdle) throw Error{AMG_EINVAL, "no solve in progress"};
+    const cudaError_t q = cudaEventQuery(a.ev);
+    if (q == cudaErrorNotReady) return 0;
+    AMG_CUDA_TRY(q);
+    t_launch_overlap = c->p.launch_overlap != 0;
+    const PcgScalars& h = *c->sc_host;
+    switch (a.state) {
+        case AsyncCg::kStarted:
+            if (h.done) { async_finish(c, AMG_OK); break; }
+            cg_first_direction(c);
+            if (h.iters >= a.maxit) { async_finish(c, AMG_ENOTCONV); break; }
+            run_part_a(c);
+            AMG_CUDA_TRY(cudaEventRecord(a.ev, c->stream));
+            a.state = AsyncCg::kIterating;
+            break;
+        case AsyncCg::kIterating:
+            if (h.status != 0) { async_finish(c, h.status); break; }
+            if (h.done) { async_finish(c, AMG_OK); break; }
+            if (h.iters >= a.maxit) { async_finish(c, AMG_ENOTCONV); break; }
+            run_part_b(c);
+            run_part_a(c);
+            AMG_CUDA_TRY(cudaEventRecord(a.ev, c->stream));
+            break;
+        case AsyncCg::kFinishing:
+            cg_fill_info(c, a.status, *a.rr_host, &a.info);
+            a.state = AsyncCg::kDone;
+            return 2;
+        default:
+            break;
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+    return 1;
+}
+
+namespace {
 
 struct Guard {
     template <typename F>
@@ -498,6 +603,57 @@ struct Guard {
     }
 };
 
+std::mutex g_pinned_mu;
+std::map<size_t, std::vector<void*>> g_pinned_free;   // size class -> free blocks
+std::map<void*, size_t> g_pinned_class;                // block -> size class
+
+}  // namespace
+
+void* pinned_alloc(size_t bytes) {
+    size_t cls = 256;
+    while (cls < bytes) cls <<= 1;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto& fl = g_pinned_free[cls];
+    if (!fl.empty()) {
+        void* p = fl.back();
+        fl.pop_back();
+        return p;
+    }
+    void* p = nullptr;
+    const cudaError_t e = cudaMallocHost(&p, cls);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{AMG_ENOMEM, "pinned host allocation of " + std::to_string(cls) + " bytes failed"};
+    }
+    g_pinned_class[p] = cls;
+    return p;
+}
+
+void pinned_free(void* p) {
+    if (!p) return;
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto it = g_pinned_class.find(p);
+    if (it != g_pinned_class.end()) g_pinned_free[it->second].push_back(p);
+}
+
+namespace {
+
+// Stream-ordered allocations come from the device's default memory pool; keep
+// freed blocks in the pool (no release at synchronisation points), so
+// contexts that come and go reuse them.  The setting lasts for this process.
+void init_device_pool(int device) {
+    static std::once_flag once[64];
+    if (device < 0 || device >= 64) return;
+    std::call_once(once[device], [device] {
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        cudaGetLastError();
+    });
+}
+
 void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     if (!A || !prm || !out) throw Error{AMG_EINVAL, "null argument"};
     *out = nullptr;
@@ -510,13 +666,20 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     c->user_stream = static_cast<cudaStream_t>(prm->cuda_stream);
     AMG_CUDA_TRY(cudaGetDevice(&c->device));
     AMG_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    init_device_pool(c->device);
+    c->mem.set_stream(c->stream);
     AMG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     AMG_CUDA_TRY(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     enter(c.get());
     int sms = 0;
     AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
-    g_reduction_blocks = std::max(1, sms) * 8;
-    g_overlap_max_blocks = std::max(1, sms) * 2;
+    // launch shapes from the SM count, set once per process (contexts are set
+    // up concurrently by the server's threads while others launch)
+    static std::once_flag shapes_once;
+    std::call_once(shapes_once, [sms] {
+        g_reduction_blocks = std::max(1, sms) * 8;
+        g_overlap_max_blocks = std::max(1, sms) * 2;
+    });
     cudaStream_t s = c->stream;
 
     // level 0 on the host (original numbering)
@@ -534,7 +697,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     std::string err;
     if (!validate_csr(A0, err)) throw Error{AMG_EINVAL, err};
 
-    DevArena setup_mem;   // original-order level matrices, freed at the end
+    DevArena setup_mem(s);   // original-order level matrices, freed at the end
     std::vector<DevCsr> dA(1);
     dA[0].n = A0.n;
     dA[0].nnz = A0.nnz();
@@ -690,7 +853,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         L.err = reinterpret_cast<int32_t*>(reinterpret_cast<char*>(c->work.sc) +
                                            offsetof(PcgScalars, status));
     c->norm_dev = c->mem.alloc<double>(1);
-    AMG_CUDA_TRY(cudaMallocHost(&c->sc_host, sizeof(PcgScalars)));
+    c->sc_host = static_cast<PcgScalars*>(pinned_alloc(sizeof(PcgScalars)));
     AMG_CUDA_TRY(cudaEventCreate(&c->ev0));
     AMG_CUDA_TRY(cudaEventCreate(&c->ev1));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));

@@ -251,12 +251,12 @@ def anisotropic3d(shape=(512, 512, 512), variance: float = 6.0, corr_len: float 
                         zfac=zfac, seed=seed))
 
 
-def serving_request(seed: int) -> Problem:
-    """One request of the serving stream: box sides ~ U{16..96} independently,
-    variance ~ U[1, 6], correlation length 0.1, boundary conditions as
-    ``lognormal3d``."""
+def serving_request(seed: int, lo: int = 16, hi: int = 96) -> Problem:
+    """One request of the serving stream: box sides ~ U{lo..hi} independently
+    (16..96 for the serving workload), variance ~ U[1, 6], correlation length
+    0.1, boundary conditions as ``lognormal3d``."""
     rng = np.random.default_rng(10_000 + seed)
-    shape = tuple(int(s) for s in rng.integers(16, 97, size=3))
+    shape = tuple(int(s) for s in rng.integers(lo, hi + 1, size=3))
     variance = float(rng.uniform(1.0, 6.0))
     p = lognormal3d(shape, variance=variance, corr_len=0.1, seed=seed)
     p.meta.update(kind="serving", request=seed)
