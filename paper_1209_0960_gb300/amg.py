@@ -413,7 +413,7 @@ def amg_poll(server: int, ticket: int, x_out: Optional[np.ndarray]):
     info = amg_solve_info()
     times = amg_request_times()
     rc = lib().amg_poll(server, ticket, _ptr(x_out), ctypes.byref(info), ctypes.byref(times))
-    if rc == AMG_ENOTFOUND or rc == AMG_EINVAL:
+    if rc == AMG_ENOTFOUND:
         _check(rc, "amg_poll")
     return rc, struct_dict(info), struct_dict(times)
 
