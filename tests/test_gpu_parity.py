@@ -231,3 +231,61 @@ def test_launch_overlap_changes_no_bits():
         res.append(out)
     for u, v in zip(*res):
         assert torch.equal(u, v) if isinstance(u, torch.Tensor) else u == v
+
+
+# ---------------------------------------------------------------------------
+# the 256^3 layered (contrast 1e6) and 512^3 anisotropic workloads at full
+# size: FP64 and FP32-in-FP64 to 1e-8, residuals recomputed with the oracle's
+# SpMV, the float32 solution's distance to the float64 one stated
+# ---------------------------------------------------------------------------
+
+def _full_size_pair(p, label):
+    import time as _time
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3)
+    summary, levels = solver.info()
+    assert summary["num_levels"] >= 3
+    # Galerkin row-sum invariant on level 1 (stored G = P^T A P)
+    l0, l1 = solver.level(0), solver.level(1)
+    rs0 = np.add.reduceat(p.val, p.row_ptr[:-1])
+    rs1 = np.add.reduceat(l1["val"], l1["row_ptr"][:-1])
+    agg = l0["agg"]
+    keep = agg >= 0
+    agg_rs = np.bincount(agg[keep], weights=rs0[keep], minlength=levels[0]["n_coarse"])
+    assert np.allclose(rs1, agg_rs, rtol=1e-9, atol=1e-9 * np.abs(p.val).max())
+    b = torch.from_numpy(p.b).cuda()
+    out = {}
+    for prec in (amg.AMG_FP64, amg.AMG_FP32_IN_FP64):
+        solver.set_precision(prec)
+        x, rc, info = solver.solve(b, tol=1e-8, maxit=500)      # warm (graphs captured)
+        torch.cuda.synchronize()
+        t0 = _time.perf_counter()
+        x, rc, info = solver.solve(b, tol=1e-8, maxit=500)
+        torch.cuda.synchronize()
+        ms = (_time.perf_counter() - t0) * 1e3
+        assert rc == amg.AMG_OK, info
+        xg = x.cpu().numpy()
+        r = p.b - O.spmv(p.row_ptr, p.col, p.val, xg)
+        assert np.linalg.norm(r) <= 1.05e-8 * np.linalg.norm(p.b)
+        out[prec] = (xg, info["iterations"], ms)
+    x64, it64, ms64 = out[amg.AMG_FP64]
+    x32, it32, ms32 = out[amg.AMG_FP32_IN_FP64]
+    diff = np.linalg.norm(x32 - x64) / np.linalg.norm(x64)
+    print(f"\n{label}: n={p.n} levels={summary['num_levels']} FP64 {it64} it {ms64:.1f} ms; "
+          f"FP32-in-FP64 {it32} it {ms32:.1f} ms; |x32-x64|/|x64| = {diff:.2e}")
+    # both stop at the same residual tolerance: their difference is of the
+    # order of the forward error that tolerance allows
+    assert diff <= 1e-3
+    solver.close()
+    return ms64, ms32
+
+
+@pytest.mark.slow
+def test_full_size_layered_256():
+    p = P.layered3d((256, 256, 256), seed=0)
+    _full_size_pair(p, "layered 256^3")
+
+
+@pytest.mark.slow
+def test_full_size_anisotropic_512():
+    p = P.anisotropic3d((512, 512, 512), seed=0)
+    _full_size_pair(p, "anisotropic 512^3")
