@@ -823,6 +823,77 @@ int oracle_pcg(void* h, const double* b, double* x, double tol, int maxit,
     return status < 0 ? status : it;
 }
 
+// Preconditioned BiCGSTAB (van der Vorst 1992; the preconditioned form of
+// the Templates book), the Krylov method of the paper's experiments (Sec. 5),
+// with the V-cycle as the preconditioner B: two V-cycles per iteration.
+//   r = b - A x, rt = r; per iteration i:
+//     rho = rt.r; p = r (i = 1) or p = r + (rho/rho_prev)(alpha/w)(p - w v);
+//     y = B p; v = A y; alpha = rho / rt.v; s = r - alpha v;
+//     if ||s|| <= tol ||r_0||: x += alpha y, stop (the half iteration counts);
+//     z = B s; t = A z; w = t.s / t.t; x += alpha y + w z; r = s - w t;
+//     stop when ||r|| <= tol ||r_0||.
+// out[0] = recursive relative residual, out[1] = true relative residual,
+// out[2] = V-cycles applied.  Returns the iteration count, -1 on a breakdown
+// (rho, rt.v or t.t zero), -2 when maxit is reached.
+int oracle_bicgstab(void* h, const double* b, double* x, double tol, int maxit, double* out) {
+    Hierarchy* H = (Hierarchy*)h;
+    const Csr& A = H->levels[0].A;
+    int n = A.n;
+    std::vector<double> xv(x, x + n), r(n), rt(n), p(n, 0.0), v(n, 0.0), y(n), s(n), z(n), t(n);
+    spmv(A, xv.data(), t.data());
+    for (int i = 0; i < n; ++i) r[i] = b[i] - t[i];
+    rt = r;
+    const double r0 = std::sqrt(dot(r, r));
+    int it = 0, status = 0, vcycles = 0;
+    double rel = r0 > 0.0 ? 1.0 : 0.0;
+    double rho_prev = 1.0, alpha = 1.0, w = 1.0;
+    while (rel > tol) {
+        if (it >= maxit) { status = -2; break; }
+        const double rho = dot(rt, r);
+        if (rho == 0.0) { status = -1; break; }
+        if (it == 0) {
+            p = r;
+        } else {
+            const double beta = (rho / rho_prev) * (alpha / w);
+            for (int i = 0; i < n; ++i) p[i] = r[i] + beta * (p[i] - w * v[i]);
+        }
+        vcycle(*H, 0, p.data(), y.data());
+        ++vcycles;
+        spmv(A, y.data(), v.data());
+        const double rtv = dot(rt, v);
+        if (rtv == 0.0) { status = -1; break; }
+        alpha = rho / rtv;
+        for (int i = 0; i < n; ++i) s[i] = r[i] - alpha * v[i];
+        ++it;
+        const double srel = std::sqrt(dot(s, s)) / r0;
+        if (srel <= tol) {
+            for (int i = 0; i < n; ++i) xv[i] = xv[i] + alpha * y[i];
+            rel = srel;
+            break;
+        }
+        vcycle(*H, 0, s.data(), z.data());
+        ++vcycles;
+        spmv(A, z.data(), t.data());
+        const double tt = dot(t, t);
+        if (tt == 0.0) { status = -1; break; }
+        w = dot(t, s) / tt;
+        for (int i = 0; i < n; ++i) {
+            xv[i] = xv[i] + alpha * y[i] + w * z[i];
+            r[i] = s[i] - w * t[i];
+        }
+        rel = std::sqrt(dot(r, r)) / r0;
+        rho_prev = rho;
+    }
+    std::vector<double> q(n);
+    spmv(A, xv.data(), q.data());
+    for (int i = 0; i < n; ++i) q[i] = b[i] - q[i];
+    out[0] = rel;
+    out[1] = r0 > 0.0 ? std::sqrt(dot(q, q)) / r0 : 0.0;
+    out[2] = vcycles;
+    for (int i = 0; i < n; ++i) x[i] = xv[i];
+    return status < 0 ? status : it;
+}
+
 void oracle_free(void* h) { delete (Hierarchy*)h; }
 
 }  // extern "C"

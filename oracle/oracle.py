@@ -76,6 +76,8 @@ def _load():
     lib.oracle_vcycle.argtypes = [P, P, P]
     lib.oracle_pcg.argtypes = [P, P, P, D, I, I, P]
     lib.oracle_pcg.restype = I
+    lib.oracle_bicgstab.argtypes = [P, P, P, D, I, P]
+    lib.oracle_bicgstab.restype = I
     lib.oracle_free.argtypes = [P]
     _lib = lib
     return lib
@@ -201,3 +203,14 @@ class Hierarchy:
         it = self._lib.oracle_pcg(self._h, _ptr(b), _ptr(x), float(tol), int(maxit),
                                   int(bool(flexible)), _ptr(out))
         return x, int(it), float(out[0]), float(out[1])
+
+    def bicgstab(self, b: np.ndarray, tol: float = 1e-8, maxit: int = 500,
+                 x0: Optional[np.ndarray] = None):
+        """Preconditioned BiCGSTAB (Sec. 5).  Returns (x, iterations or
+        negative status, recursive rel. residual, true rel. residual,
+        V-cycles applied)."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x = np.zeros(self.n) if x0 is None else np.array(x0, dtype=np.float64)
+        out = np.zeros(3)
+        it = self._lib.oracle_bicgstab(self._h, _ptr(b), _ptr(x), float(tol), int(maxit), _ptr(out))
+        return x, int(it), float(out[0]), float(out[1]), int(out[2])

@@ -329,3 +329,52 @@ def test_flexible_cg_matches_standard_cg_for_exact_preconditioner_arithmetic():
     x1, it1, _, t1 = H.pcg(p.b, tol=1e-8)
     x2, it2, _, t2 = H.pcg(p.b, tol=1e-8, flexible=True)
     assert abs(it1 - it2) <= 1 and t1 <= 1e-8 * 1.01 and t2 <= 1e-8 * 1.01
+
+
+# ---------------------------------------------------------------------------
+# BiCGSTAB (Sec. 5: the Krylov method of the paper's experiments)
+# ---------------------------------------------------------------------------
+
+def test_bicgstab_with_exact_preconditioner_stops_after_half_an_iteration():
+    # B = A^-1: y = A^-1 r0, v = r0, alpha = rt.r0 / rt.r0 = 1, s = 0
+    p = P.laplace2d_random_rhs(16)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(2, coarsen_target=10_000))
+    x, it, rel, trel, vc = H.bicgstab(p.b, tol=1e-10)
+    assert (it, vc) == (1, 1) and trel < 1e-12
+
+
+@pytest.mark.parametrize("maker,dim", [
+    (lambda: P.laplace2d_random_rhs(32), 2),
+    (lambda: P.lognormal3d((12, 12, 12), seed=0), 3),
+    (lambda: P.layered3d((12, 12, 12), seed=1), 3),
+])
+def test_bicgstab_matches_dense_direct_solve_and_pcg(maker, dim):
+    p = maker()
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(dim, coarsen_target=100))
+    A = to_dense(p.row_ptr, p.col, p.val)
+    xd = np.linalg.solve(A, p.b)
+    x, it, rel, trel, vc = H.bicgstab(p.b, tol=1e-12, maxit=200)
+    assert 0 < it < 60 and vc in (2 * it, 2 * it - 1)
+    assert rel <= 1e-12 and trel <= 1e-11
+    cond = np.linalg.cond(A)
+    bound = 1e-9 if cond < 1e3 else 10 * cond * 1e-12
+    assert np.linalg.norm(x - xd) <= bound * np.linalg.norm(xd)
+    # two V-cycles per iteration: fewer iterations than PCG, comparable V-cycles
+    xc, itc, _, _ = H.pcg(p.b, tol=1e-12, maxit=200)
+    assert it <= itc and vc <= 2 * itc
+
+
+def test_bicgstab_initial_guess_and_maxit():
+    p = P.laplace2d_random_rhs(16)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(2, coarsen_target=20))
+    A = to_dense(p.row_ptr, p.col, p.val)
+    xd = np.linalg.solve(A, p.b)
+    x0 = xd + 1e-3 * np.random.default_rng(0).standard_normal(p.n)
+    x, it, rel, trel, vc = H.bicgstab(p.b, tol=1e-10, x0=x0)
+    assert it > 0 and trel <= 1e-10 * 1.01
+    assert np.linalg.norm(x - xd) <= 1e-9 * np.linalg.norm(xd)
+    # a zero residual at the start: no iteration
+    x, it, rel, trel, vc = H.bicgstab(np.zeros(p.n), tol=1e-10)
+    assert (it, vc) == (0, 0) and not x.any()
+    x, it, rel, trel, vc = H.bicgstab(p.b, tol=1e-14, maxit=1)
+    assert it == -2
