@@ -175,6 +175,14 @@ int amg_pcg_solve(amg_ctx *c, const double *b_dev, double *x_dev, double tol,
 /* As amg_pcg_solve with host buffers: copies b and x_0 to the device,
  * solves, copies x back (all on the context stream; pinned buffers make the
  * copies asynchronous DMA).  info->solve_ms includes the copies. */
+/* Preconditioned BiCGSTAB (the Krylov method of the paper's experiments,
+ * Sec. 5) with the same V-cycle, two V-cycles per iteration; arguments,
+ * stopping rule and errors as amg_pcg_solve (a half iteration that meets the
+ * tolerance counts as an iteration).  A breakdown (rt.r, rt.v or t.t zero)
+ * returns AMG_ENOTCONV with the reason in amg_last_error(). */
+int amg_bicgstab_solve(amg_ctx *c, const double *b_dev, double *x_dev, double tol,
+                       int32_t maxit, amg_solve_info *info);
+
 int amg_pcg_solve_host(amg_ctx *c, const double *b_host, double *x_host, double tol,
                        int32_t maxit, amg_solve_info *info);
 

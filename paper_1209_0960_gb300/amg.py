@@ -106,6 +106,7 @@ _SIGNATURES = {
     "amg_set_precision": ([_c_vp, _c_i32, _c_i32], ctypes.c_int),
     "amg_vcycle": ([_c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_pcg_solve": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
+    "amg_bicgstab_solve": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
     "amg_pcg_solve_host": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
     "amg_residual_norm": ([_c_vp, _c_vp, _c_vp, ctypes.POINTER(_c_dbl)], ctypes.c_int),
     "amg_residual_norm_noalloc": ([ctypes.POINTER(amg_csr), _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
@@ -205,6 +206,13 @@ def amg_pcg_solve(ctx: int, b_dev, x_dev, tol: float, maxit: int):
     info = amg_solve_info()
     rc = lib().amg_pcg_solve(ctx, _ptr(b_dev), _ptr(x_dev), tol, maxit, ctypes.byref(info))
     _check(rc, "amg_pcg_solve", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    return rc, info
+
+
+def amg_bicgstab_solve(ctx: int, b_dev, x_dev, tol: float, maxit: int):
+    info = amg_solve_info()
+    rc = lib().amg_bicgstab_solve(ctx, _ptr(b_dev), _ptr(x_dev), tol, maxit, ctypes.byref(info))
+    _check(rc, "amg_bicgstab_solve", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
     return rc, info
 
 
@@ -354,6 +362,13 @@ class AMG:
         if x_dev is None:
             x_dev = torch.zeros_like(b_dev)
         rc, info = amg_pcg_solve(self.ctx, b_dev, x_dev, tol, maxit)
+        return x_dev, rc, struct_dict(info)
+
+    def solve_bicgstab(self, b_dev, x_dev=None, tol: float = 1e-8, maxit: int = 500):
+        import torch
+        if x_dev is None:
+            x_dev = torch.zeros_like(b_dev)
+        rc, info = amg_bicgstab_solve(self.ctx, b_dev, x_dev, tol, maxit)
         return x_dev, rc, struct_dict(info)
 
     def solve_host(self, b_host: np.ndarray, x_host: np.ndarray, tol: float = 1e-8,

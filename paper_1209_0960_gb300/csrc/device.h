@@ -280,6 +280,20 @@ void launch_cg_rz(int n, const double* r, const double* z, const double* zold, d
 void launch_cg_p(int n, const double* z, double* p, double* zold, const CgWork& w,
                  cudaStream_t s);
 
+// BiCGSTAB vector operations (level 0, float64); `out` receives up to two dot
+// products (device memory).  bi_spmv: y = A x, out = {w.y, y.y};
+// bi_axpy: outv = u + c v, out = {outv.outv}; bi_update: x += alpha y + w z,
+// r = s - w t, out = {r.r, rt.r}; bi_direction: p = r + beta (p - w v).
+void launch_bi_spmv(const DevLevel& L, const double* x, double* y, const double* w, bool self_dot,
+                    CgWork& wk, double* out, cudaStream_t s);
+void launch_bi_axpy(int n, const double* u, double c, const double* v, double* outv, CgWork& wk,
+                    double* out, cudaStream_t s);
+void launch_bi_update(int n, double* x, const double* y, const double* z, double alpha, double w,
+                      const double* sv, const double* t, double* r, const double* rt, CgWork& wk,
+                      double* out, cudaStream_t s);
+void launch_bi_direction(int n, const double* r, double beta, double w, const double* v, double* p,
+                         cudaStream_t s);
+
 // ---------------------------------------------------------------------------
 // setup on the device (setup_device.cu)
 // ---------------------------------------------------------------------------
@@ -363,6 +377,10 @@ struct amg_ctx {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     amg::Profiler prof;
     AsyncCg acg;
+    // BiCGSTAB vectors (level 0, smoothing order), allocated on first use
+    double *rt = nullptr, *bv = nullptr, *by = nullptr, *bs = nullptr, *bt = nullptr;
+    double* dots = nullptr;           // [2] device dot products
+    double* dots_host = nullptr;      // [2] pinned mirror
 
     amg_ctx() = default;
     amg_ctx(const amg_ctx&) = delete;
@@ -370,6 +388,7 @@ struct amg_ctx {
     ~amg_ctx() {
         if (sc_host) amg::pinned_free(sc_host);
         if (acg.rr_host) amg::pinned_free(acg.rr_host);
+        if (dots_host) amg::pinned_free(dots_host);
         if (acg.ev) cudaEventDestroy(acg.ev);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);

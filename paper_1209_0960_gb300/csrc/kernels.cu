@@ -796,6 +796,113 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(int n, const double* __restrict
     }
 }
 
+// ---------------------------------------------------------------------------
+// BiCGSTAB vector operations (level 0, float64, smoothing order).  Each
+// returns up to two dot products through the deterministic last-block
+// reduction: per-block sums in a fixed grid, combined in block order.
+// ---------------------------------------------------------------------------
+__device__ void finish_dots(double v0, double v1, double* partials, double* partials2,
+                            unsigned int* counter, double* out, double* sh) {
+    __shared__ bool last;
+    if (threadIdx.x == 0) {
+        partials[blockIdx.x] = v0;
+        partials2[blockIdx.x] = v1;
+        __threadfence();
+        const unsigned int t = atomicAdd(counter, 1u);
+        last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!last) return;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+        a += __ldcg(partials + i);
+        b += __ldcg(partials2 + i);
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x != 0) return;
+    *counter = 0u;
+    out[0] = a;
+    out[1] = b;
+}
+
+// y = A x; out[0] = w.y (w may be null), out[1] = y.y when self_dot
+__global__ void __launch_bounds__(kBlock) k_bi_spmv(int n, int64_t sw,
+                                                    const uint16_t* __restrict__ rlen,
+                                                    const int32_t* __restrict__ scol,
+                                                    const double* __restrict__ sval,
+                                                    const double* __restrict__ diag,
+                                                    const double* x, double* y, const double* w,
+                                                    int self_dot, double* partials,
+                                                    double* partials2, unsigned int* counter,
+                                                    double* out) {
+    __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
+    double a = 0.0, b = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
+        const double v = sell_row<false>(base, __ldcs(rlen + row), scol, sval, x,
+                                         __ldcs(diag + row) * x[row]);
+        y[row] = v;
+        if (w) a = fmad(w[row], v, a);
+        if (self_dot) b = fmad(v, v, b);
+    }
+    const double ta = block_sum(a, sh);
+    const double tb = block_sum(b, sh);
+    finish_dots(ta, tb, partials, partials2, counter, out, sh);
+}
+
+// out_vec = u + c v; out[0] = out_vec.out_vec
+__global__ void __launch_bounds__(kBlock) k_bi_axpy(int n, const double* u, double c,
+                                                    const double* v, double* outv,
+                                                    double* partials, double* partials2,
+                                                    unsigned int* counter, double* out) {
+    __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
+    double a = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double o = fmad(c, v[i], u[i]);
+        outv[i] = o;
+        a = fmad(o, o, a);
+    }
+    const double ta = block_sum(a, sh);
+    finish_dots(ta, 0.0, partials, partials2, counter, out, sh);
+}
+
+// x += alpha y + w z; r = s - w t; out[0] = r.r, out[1] = rt.r
+__global__ void __launch_bounds__(kBlock) k_bi_update(int n, double* x, const double* y,
+                                                      const double* z, double alpha, double w,
+                                                      const double* s, const double* t,
+                                                      double* r, const double* rt,
+                                                      double* partials, double* partials2,
+                                                      unsigned int* counter, double* out) {
+    __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
+    double a = 0.0, b = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        x[i] = x[i] + alpha * y[i] + w * z[i];
+        const double ri = s[i] - w * t[i];
+        r[i] = ri;
+        a = fmad(ri, ri, a);
+        b = fmad(rt[i], ri, b);
+    }
+    const double ta = block_sum(a, sh);
+    const double tb = block_sum(b, sh);
+    finish_dots(ta, tb, partials, partials2, counter, out, sh);
+}
+
+// p = r + beta (p - w v)
+__global__ void __launch_bounds__(kBlock) k_bi_direction(int n, const double* r, double beta,
+                                                         double w, const double* v, double* p) {
+    pdl_launch_dependents();
+    pdl_wait();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = r[i] + beta * (p[i] - w * v[i]);
+}
+
 inline int blocks_for(int64_t threads) { return (int)((threads + kBlock - 1) / kBlock); }
 
 }  // namespace
@@ -1033,6 +1140,31 @@ void launch_cg_rz(int n, const double* r, const double* z, const double* zold, d
 void launch_cg_p(int n, const double* z, double* p, double* zold, const CgWork& w,
                  cudaStream_t s) {
     launch_kernel(k_cg_p, reduction_blocks(n), kBlock, 0, s, n, z, p, zold, w.sc);
+}
+
+void launch_bi_spmv(const DevLevel& L, const double* x, double* y, const double* w, bool self_dot,
+                    CgWork& wk, double* out, cudaStream_t s) {
+    launch_kernel(k_bi_spmv, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol,
+                  L.sval, L.diag, x, y, w, (int)self_dot, wk.partials, wk.partials2,
+                  wk.counters + 4, out);
+}
+
+void launch_bi_axpy(int n, const double* u, double c, const double* v, double* outv, CgWork& wk,
+                    double* out, cudaStream_t s) {
+    launch_kernel(k_bi_axpy, reduction_blocks(n), kBlock, 0, s, n, u, c, v, outv, wk.partials,
+                  wk.partials2, wk.counters + 5, out);
+}
+
+void launch_bi_update(int n, double* x, const double* y, const double* z, double alpha, double w,
+                      const double* sv, const double* t, double* r, const double* rt, CgWork& wk,
+                      double* out, cudaStream_t s) {
+    launch_kernel(k_bi_update, reduction_blocks(n), kBlock, 0, s, n, x, y, z, alpha, w, sv, t, r,
+                  rt, wk.partials, wk.partials2, wk.counters + 6, out);
+}
+
+void launch_bi_direction(int n, const double* r, double beta, double w, const double* v, double* p,
+                         cudaStream_t s) {
+    launch_kernel(k_bi_direction, reduction_blocks(n), kBlock, 0, s, n, r, beta, w, v, p);
 }
 
 }  // namespace amg

@@ -511,6 +511,90 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     return status;
 }
 
+// ---------------------------------------------------------------------------
+// preconditioned BiCGSTAB (Sec. 5: the Krylov method of the paper's
+// experiments), two V-cycles per iteration; vectors in smoothing order
+// (c->bb = b, c->x = x0 in, x out).  The scalars are formed on the host from
+// the dot products, each read back once per half iteration.
+// ---------------------------------------------------------------------------
+int bicgstab(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info, std::string& why) {
+    DevLevel& L0 = c->dl[0];
+    const int n = L0.n;
+    cudaStream_t s = c->stream;
+    if (!c->rt) {
+        c->rt = c->mem.alloc<double>(n);
+        c->bv = c->mem.alloc<double>(n);
+        c->by = c->mem.alloc<double>(n);
+        c->bs = c->mem.alloc<double>(n);
+        c->bt = c->mem.alloc<double>(n);
+        c->dots = c->mem.alloc<double>(2);
+        c->dots_host = static_cast<double*>(pinned_alloc(2 * sizeof(double)));
+    }
+    auto read_dots = [&] {
+        AMG_CUDA_TRY(cudaMemcpyAsync(c->dots_host, c->dots, 2 * sizeof(double),
+                                     cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    };
+    double* x = c->x;
+    double* r = c->r;
+    double* p = c->pv;
+    double* z = c->z;
+    // r = b - A x, rt = r
+    launch_cg_residual(L0, c->bb, x, r, c->work, kStore, c->dots, s);
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->rt, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    read_dots();
+    const double r0 = std::sqrt(c->dots_host[0]);
+    double rel = r0 > 0.0 ? 1.0 : 0.0;
+    double rho = c->dots_host[0], rho_prev = 1.0, alpha = 1.0, w = 1.0;
+    int it = 0, status = AMG_OK;
+    while (rel > tol) {
+        if (it >= maxit) { status = AMG_ENOTCONV; break; }
+        if (rho == 0.0) { status = AMG_ENOTCONV; why = "BiCGSTAB breakdown: rt.r = 0"; break; }
+        if (it == 0)
+            AMG_CUDA_TRY(cudaMemcpyAsync(p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        else
+            launch_bi_direction(n, r, (rho / rho_prev) * (alpha / w), w, c->bv, p, s);
+        precondition(c, p, c->by);
+        launch_bi_spmv(L0, c->by, c->bv, c->rt, false, c->work, c->dots, s);
+        read_dots();
+        const double rtv = c->dots_host[0];
+        if (rtv == 0.0) { status = AMG_ENOTCONV; why = "BiCGSTAB breakdown: rt.v = 0"; break; }
+        alpha = rho / rtv;
+        launch_bi_axpy(n, r, -alpha, c->bv, c->bs, c->work, c->dots, s);
+        read_dots();
+        ++it;
+        const double srel = std::sqrt(c->dots_host[0]) / r0;
+        if (srel <= tol) {
+            launch_bi_axpy(n, x, alpha, c->by, x, c->work, c->dots, s);
+            rel = srel;
+            break;
+        }
+        precondition(c, c->bs, z);
+        launch_bi_spmv(L0, z, c->bt, c->bs, true, c->work, c->dots, s);
+        read_dots();
+        const double ts = c->dots_host[0], tt = c->dots_host[1];
+        if (tt == 0.0) { status = AMG_ENOTCONV; why = "BiCGSTAB breakdown: t.t = 0"; break; }
+        w = ts / tt;
+        launch_bi_update(n, x, c->by, z, alpha, w, c->bs, c->bt, r, c->rt, c->work, c->dots, s);
+        read_dots();
+        rel = std::sqrt(c->dots_host[0]) / r0;
+        rho_prev = rho;
+        rho = c->dots_host[1];
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+    if (info) {
+        cg_true_residual(c);
+        double rr = 0.0;
+        AMG_CUDA_TRY(cudaMemcpyAsync(&rr, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        info->status = status;
+        info->iterations = it;
+        info->rel_residual = rel;
+        info->true_rel_residual = r0 > 0.0 ? std::sqrt(rr) / r0 : 0.0;
+    }
+    return status;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
@@ -934,8 +1018,9 @@ int amg_vcycle(amg_ctx* c, const double* r_dev, double* z_dev) {
 }
 
 static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int32_t maxit,
-                        amg_solve_info* info, bool host) {
+                        amg_solve_info* info, bool host, bool use_bicgstab = false) {
     int status = AMG_OK;
+    std::string why;
     int rc = Guard::run([&] {
         if (!c || !b || !x) throw Error{AMG_EINVAL, "null argument"};
         if (!(tol >= 0.0) || maxit < 0) throw Error{AMG_EINVAL, "tol must be >= 0 and maxit >= 0"};
@@ -955,7 +1040,7 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         launch_scatter(n, c->perm0, bd, c->bb, s);
         launch_scatter(n, c->perm0, xd, c->x, s);
         amg_solve_info local{};
-        status = pcg(c, tol, maxit, &local);
+        status = use_bicgstab ? bicgstab(c, tol, maxit, &local, why) : pcg(c, tol, maxit, &local);
         if (host) {
             launch_gather(n, c->perm0, c->x, c->z, s);
             AMG_CUDA_TRY(cudaMemcpyAsync(x, c->z, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -969,17 +1054,23 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         local.solve_ms = ms;
         leave(c);
         if (info) *info = local;
-        if (status != AMG_OK)
-            t_last_error = status == AMG_ENOTCONV ? "maximum iterations reached"
-                                                  : "p.Ap <= 0: operator or preconditioner not SPD";
+        if (status != AMG_OK && why.empty())
+            why = status == AMG_ENOTCONV ? "maximum iterations reached"
+                                         : "p.Ap <= 0: operator or preconditioner not SPD";
     });
     if (rc != AMG_OK) return rc;
+    if (status != AMG_OK) t_last_error = why;   // after the guard, which clears it on success
     return status;
 }
 
 int amg_pcg_solve(amg_ctx* c, const double* b_dev, double* x_dev, double tol, int32_t maxit,
                   amg_solve_info* info) {
     return solve_common(c, b_dev, x_dev, tol, maxit, info, false);
+}
+
+int amg_bicgstab_solve(amg_ctx* c, const double* b_dev, double* x_dev, double tol,
+                       int32_t maxit, amg_solve_info* info) {
+    return solve_common(c, b_dev, x_dev, tol, maxit, info, false, true);
 }
 
 int amg_pcg_solve_host(amg_ctx* c, const double* b_host, double* x_host, double tol,

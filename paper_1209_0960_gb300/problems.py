@@ -97,13 +97,30 @@ def gaussian_field(shape: Sequence[int], variance: float, corr_len: float,
 # finite-volume assembly
 # ---------------------------------------------------------------------------
 
+def cell_centres(phys_shape) -> list:
+    """Coordinates of the cell centres of the unit square/cube, as arrays of
+    the array shape (reversed physical axes), one per physical axis."""
+    axes = [(np.arange(m) + 0.5) / m for m in phys_shape]
+    grids = np.meshgrid(*axes[::-1], indexing="ij")     # array axes (z, y, x)
+    return grids[::-1]                                  # physical order (x, y, z)
+
+
+def _face_centres(phys_shape, pa, side, sl):
+    """Coordinates of the boundary face centres of the cells in slice ``sl``
+    (the low or high face normal to physical axis ``pa``)."""
+    pts = [c[sl] for c in cell_centres(phys_shape)]
+    pts[pa] = np.full_like(pts[pa], 0.0 if side == 0 else 1.0)
+    return pts
+
+
 def assemble_fv(K: np.ndarray, bc: Sequence, f: Optional[np.ndarray] = None,
                 aniso: Optional[Sequence[float]] = None):
     """Assemble the cell-centred FV matrix for coefficient array ``K``.
 
     ``K`` has array axes (z, y, x) (reversed physical axes).  ``bc[a]`` is a
-    pair (low, high) for physical axis a; each side is ``None`` (no flux) or a
-    float g (Dirichlet value).  ``aniso[a]`` multiplies every transmissibility
+    pair (low, high) for physical axis a; each side is ``None`` (no flux), a
+    float g (Dirichlet value) or a callable g(x, y, z) of the face-centre
+    coordinates (Dirichlet data varying along the face).  ``aniso[a]`` multiplies every transmissibility
     of faces normal to physical axis a.  Returns (row_ptr, col, val, b).
     """
     K = np.asarray(K, dtype=np.float64)
@@ -139,7 +156,10 @@ def assemble_fv(K: np.ndarray, bc: Sequence, f: Optional[np.ndarray] = None,
             sl = tuple(sl)
             tb = 2.0 * fac * K[sl]
             diag[sl] += tb
-            b[sl] += tb * float(g)
+            if callable(g):
+                b[sl] += tb * g(*_face_centres(phys_shape, pa, side, sl))
+            else:
+                b[sl] += tb * float(g)
     n = K.size
     strides = [int(np.prod(K.shape[ax + 1:])) for ax in range(d)]
     nslot = 2 * d + 1
@@ -261,6 +281,40 @@ def serving_request(seed: int, lo: int = 16, hi: int = 96) -> Problem:
     p = lognormal3d(shape, variance=variance, corr_len=0.1, seed=seed)
     p.meta.update(kind="serving", request=seed)
     return p
+
+
+def poisson_exp3d(n: int) -> Problem:
+    """Poisson problem of the paper's second machine (Sec. 5, helics3a):
+    -Laplace u = f on the unit cube, u = g on the boundary, K = 1.  The printed
+    right-hand side (6 - 4|x|) e^|x| matches no closed form with the printed
+    boundary data e^|x|; this reads the pair as u = e^(|x|^2), for which
+    -Laplace u = -(6 + 4 |x|^2) e^(|x|^2) exactly."""
+    shape = (n, n, n)
+    X, Y, Z = cell_centres(shape)
+    r2 = X * X + Y * Y + Z * Z
+    f = -(6.0 + 4.0 * r2) * np.exp(r2)
+    g = lambda x, y, z: np.exp(x * x + y * y + z * z)
+    rp, ci, va, b = assemble_fv(np.ones(shape[::-1]), bc=[(g, g)] * 3, f=f)
+    return Problem("poisson_exp3d_%d" % n, shape, rp, ci, va, b,
+                   dict(kind="poisson_exp3d", u_exact=np.exp(r2).ravel()))
+
+
+def cube_in_cube3d(n: int) -> Problem:
+    """Heterogeneous diffusion problem of the paper's Sec. 5 (after Griebel,
+    Metsch and Schweitzer): K = 1e3 in the centred cube of width 0.8,
+    K = 1e-2 in the eight corner cubes of width 0.1, K = 1 elsewhere.  The
+    paper names Dirichlet conditions without values and no source; this
+    takes u = 0 on the boundary and f = 1."""
+    shape = (n, n, n)
+    X, Y, Z = cell_centres(shape)
+    K = np.ones(shape[::-1])
+    inner = (np.abs(X - 0.5) < 0.4) & (np.abs(Y - 0.5) < 0.4) & (np.abs(Z - 0.5) < 0.4)
+    K[inner] = 1e3
+    corner = ((np.minimum(X, 1 - X) < 0.1) & (np.minimum(Y, 1 - Y) < 0.1)
+              & (np.minimum(Z, 1 - Z) < 0.1))
+    K[corner] = 1e-2
+    rp, ci, va, b = assemble_fv(K, bc=[(0.0, 0.0)] * 3, f=np.ones(shape[::-1]))
+    return Problem("cube_in_cube3d_%d" % n, shape, rp, ci, va, b, dict(kind="cube_in_cube3d"))
 
 
 def laplacian_1d(n: int) -> tuple:

@@ -41,6 +41,8 @@ CASES = {
     "layered_20x20x24": (lambda: P.layered3d((20, 20, 24), seed=3), {"coarsen_target": 200}),
     "anisotropic_18": (lambda: P.anisotropic3d((18, 18, 18), seed=2), {"coarsen_target": 200}),
     "lognormal_deep_16": (lambda: P.lognormal3d((16, 16, 16), seed=5), {"coarsen_target": 12}),
+    "poisson_exp_24": (lambda: P.poisson_exp3d(24), {"coarsen_target": 200}),
+    "cube_in_cube_24": (lambda: P.cube_in_cube3d(24), {"coarsen_target": 200}),
 }
 
 
@@ -289,3 +291,17 @@ def test_full_size_layered_256():
 def test_full_size_anisotropic_512():
     p = P.anisotropic3d((512, 512, 512), seed=0)
     _full_size_pair(p, "anisotropic 512^3")
+
+
+def test_bicgstab_matches_oracle(pair):
+    p, solver, H = pair
+    b = torch.from_numpy(p.b).cuda()
+    x, rc, info = solver.solve_bicgstab(b, tol=1e-10, maxit=300)
+    assert rc == amg.AMG_OK
+    xo, it_o, rel_o, trel_o, vc_o = H.bicgstab(p.b, tol=1e-10, maxit=300)
+    assert it_o > 0 and abs(info["iterations"] - it_o) <= 1
+    assert info["true_rel_residual"] <= 1.5e-10
+    xg = x.cpu().numpy()
+    assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
+    r = p.b - O.spmv(p.row_ptr, p.col, p.val, xg)
+    assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(p.b)

@@ -378,3 +378,34 @@ def test_bicgstab_initial_guess_and_maxit():
     assert (it, vc) == (0, 0) and not x.any()
     x, it, rel, trel, vc = H.bicgstab(p.b, tol=1e-14, maxit=1)
     assert it == -2
+
+
+# ---------------------------------------------------------------------------
+# second workloads of Sec. 5: the Poisson problem with a closed-form solution
+# and the cube-in-cube coefficient jumps
+# ---------------------------------------------------------------------------
+
+def test_poisson_exp_converges_to_the_closed_form_at_second_order():
+    # the solver's solution of the discrete problem approaches u = e^(|x|^2)
+    # at O(h^2): the right-hand side and boundary data are consistent
+    errs = []
+    for n in (12, 24):
+        p = P.poisson_exp3d(n)
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=200))
+        x, it, rel, trel = H.pcg(p.b, tol=1e-12, maxit=300)
+        assert it > 0 and trel <= 1e-12 * 1.01
+        errs.append(np.abs(x - p.meta["u_exact"]).max())
+    assert errs[1] < 0.03 and errs[0] / errs[1] > 3.0
+
+
+def test_cube_in_cube_coefficients_and_solve():
+    p = P.cube_in_cube3d(20)
+    A = to_dense(p.row_ptr, p.col, p.val)
+    assert np.allclose(A, A.T)
+    # the jump 1e3 : 1 : 1e-2 shows in the transmissibilities (h^-2 = 400)
+    off = -p.val[p.col != np.repeat(np.arange(p.n), np.diff(p.row_ptr))]
+    assert np.isclose(off.max(), 1e3 * 400) and np.isclose(off.min(), 1e-2 * 400)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=100))
+    x, it, rel, trel = H.pcg(p.b, tol=1e-10, maxit=300)
+    xd = np.linalg.solve(A, p.b)
+    assert 0 < it < 100 and np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
