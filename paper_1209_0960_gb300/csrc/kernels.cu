@@ -354,7 +354,8 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
 // keeping it out of L2 leaves the coarse levels resident there from one
 // V-cycle to the next.  Row lengths and diagonals are loaded evict-first too.
 // ---------------------------------------------------------------------------
-constexpr int kSlicesPerBlock = kBlock / 32;
+constexpr int kFineBlock = 256;                    // rows (threads) per fine-level block
+constexpr int kSlicesPerBlock = kFineBlock / 32;
 constexpr long long kStageSpinLimit = 1LL << 22;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -418,7 +419,7 @@ struct FineTile {
         row = (int)(slice0 * 32) + (int)threadIdx.x;
         loc = (int)(threadIdx.x >> 5) * 32 * width + (int)(threadIdx.x & 31);
         s_col = reinterpret_cast<int32_t*>(smem);
-        s_val = reinterpret_cast<T*>(smem + (size_t)kBlock * width * sizeof(int32_t));
+        s_val = reinterpret_cast<T*>(smem + (size_t)kFineBlock * width * sizeof(int32_t));
     }
 };
 
@@ -441,7 +442,7 @@ __device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, c
 // for the fused residual-restriction kernel.  Blocks with colour-0 rows only
 // need no matrix.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fine_first(int c1, int c2, int width, int64_t nslices,
+__global__ void __launch_bounds__(kFineBlock) k_fine_first(int c1, int c2, int width, int64_t nslices,
                                                        const uint16_t* __restrict__ rlen,
                                                        const int32_t* scol, const T* sval,
                                                        const T* __restrict__ dinv, const T* b,
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_first(int c1, int c2, int width
 
 // k_gs_pass on the fine level
 template <int MODE, bool SCALED, typename T>
-__global__ void __launch_bounds__(kBlock) k_fine_pass(int r0, int r1, int jmax, int width,
+__global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jmax, int width,
                                                       int64_t nslices,
                                                       const uint16_t* __restrict__ rlen,
                                                       const int32_t* scol, const T* sval,
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_pass(int r0, int r1, int jmax, 
 
 // k_residual on the fine level
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fine_residual(int r0, int n, int width,
+__global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int width,
                                                           int64_t nslices,
                                                           const uint16_t* __restrict__ rlen,
                                                           const int32_t* scol, const T* sval,
@@ -520,14 +521,14 @@ __global__ void __launch_bounds__(kBlock) k_fine_residual(int r0, int n, int wid
 // run cut by a block boundary), whose result does not depend on their order:
 // the sum stays deterministic.
 template <typename T, bool SCALED>
-__global__ void __launch_bounds__(kBlock) k_fine_residual_restrict(
+__global__ void __launch_bounds__(kFineBlock) k_fine_residual_restrict(
     int c1, int n, int width, int64_t nslices, const uint16_t* __restrict__ rlen,
     const int32_t* scol, const T* sval, const T* __restrict__ diag, const T* b, const T* x,
     const int32_t* __restrict__ agg, const T* __restrict__ t, T* bc, int32_t* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
-    __shared__ T sv[kBlock];
-    __shared__ int sk[kBlock];
+    __shared__ T sv[kFineBlock];
+    __shared__ int sk[kFineBlock];
     pdl_launch_dependents();
     const FineTile<T> F(c1, nslices, width, smem);
     const bool valid = F.row >= c1 && F.row < n;
@@ -549,7 +550,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_residual_restrict(
     __syncthreads();
     if (key < 0 || (tid > 0 && sk[tid - 1] == key)) return;
     T sum = v;
-    for (int u = tid + 1; u < kBlock && sk[u] == key; ++u) sum += sv[u];
+    for (int u = tid + 1; u < kFineBlock && sk[u] == key; ++u) sum += sv[u];
     atomicAdd(bc + key, sum);
 }
 
@@ -953,13 +954,15 @@ struct LevelArrays<float> {
     explicit LevelArrays(const DevLevel& L) : sval(L.sval32), dinv(L.dinv32), diag(L.diag32), t(L.t32) {}
 };
 
-// fine-level launches: one block per kBlock / 32 slices, the slices staged
+// fine-level launches: one block per kFineBlock / 32 slices, the slices staged
 // in dynamic shared memory (column indices, then values)
-inline int fine_blocks(int r0, int r1) { return blocks_for((int64_t)r1 - (r0 & ~31)); }
+inline int fine_blocks(int r0, int r1) {
+    return (int)(((int64_t)r1 - (r0 & ~31) + kFineBlock - 1) / kFineBlock);
+}
 inline int64_t fine_nslices(const DevLevel& L) { return ((int64_t)L.n + 31) / 32; }
 template <typename K>
 size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
-    const size_t bytes = (size_t)kBlock * L.width * (sizeof(int32_t) + value_bytes);
+    const size_t bytes = (size_t)kFineBlock * L.width * (sizeof(int32_t) + value_bytes);
     if (bytes > 48 * 1024)
         AMG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)bytes));
@@ -972,7 +975,7 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
     if (L.lpr == kFine) {
         auto k = k_fine_first<T>;
-        launch_kernel(k, std::max(1, fine_blocks(0, c2)), kBlock, fine_smem(k, L, sizeof(T)), s, c1,
+        launch_kernel(k, std::max(1, fine_blocks(0, c2)), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1,
                       c2, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero,
                       nc, L.err);
         return;
@@ -991,7 +994,7 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* 
     constexpr bool SC = std::is_same<T, float>::value;
     if (L.lpr == kFine) {
         auto k = k_fine_pass<MODE, SC, T>;
-        launch_kernel(k, fine_blocks(r0, r1), kBlock, fine_smem(k, L, sizeof(T)), s, r0, r1, jmax,
+        launch_kernel(k, fine_blocks(r0, r1), kFineBlock, fine_smem(k, L, sizeof(T)), s, r0, r1, jmax,
                       L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg, A.t,
                       e, (T)omega, L.err);
         return;
@@ -1011,7 +1014,7 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
     if (L.fused_restrict) {
         if (L.n > c1) {
             auto k = k_fine_residual_restrict<T, SC>;
-            launch_kernel(k, fine_blocks(c1, L.n), kBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
+            launch_kernel(k, fine_blocks(c1, L.n), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
                           L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, L.agg,
                           A.t, bc, L.err);
         }
@@ -1020,7 +1023,7 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
     if (L.n > c1) {
         if (L.lpr == kFine) {
             auto k = k_fine_residual<T>;
-            launch_kernel(k, fine_blocks(c1, L.n), kBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
+            launch_kernel(k, fine_blocks(c1, L.n), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
                           L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, r, L.err);
         } else {
             AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1),
