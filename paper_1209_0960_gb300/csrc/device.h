@@ -235,7 +235,13 @@ void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, c
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = (t_launch_overlap && grid <= g_overlap_max_blocks) ? 1 : 0;
-    AMG_CUDA_TRY(cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...));
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{AMG_ECUDA, std::string("kernel launch (grid ") + std::to_string(grid) +
+                                   ", block " + std::to_string(block) + ", shared " +
+                                   std::to_string(smem) + " B) failed: " + cudaGetErrorString(e)};
+    }
 }
 
 extern int g_reduction_blocks;        // grid of the reduction kernels (SMs x 8)

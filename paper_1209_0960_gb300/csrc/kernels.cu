@@ -400,8 +400,11 @@ __device__ bool stage_slices(int64_t slice0, int nsl, int width, const int32_t* 
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(ub) : "memory");
-    if (!done) atomicExch(err, AMG_ETIMEOUT);
-    return done != 0;
+    // one decision for the whole block, so that no thread waits at a later
+    // barrier for threads that gave up
+    const int all = __syncthreads_and((int)done);
+    if (!all && threadIdx.x == 0) atomicExch(err, AMG_ETIMEOUT);
+    return all != 0;
 }
 
 // The block's slices, its shared-memory tiles and this thread's row.
@@ -954,6 +957,10 @@ struct LevelArrays<float> {
     explicit LevelArrays(const DevLevel& L) : sval(L.sval32), dinv(L.dinv32), diag(L.diag32), t(L.t32) {}
 };
 
+// dynamic shared memory a kernel gets without opting in, with room for its
+// static shared memory inside the 48 KB default
+constexpr size_t kDefaultDynSmem = 40 * 1024;
+
 // fine-level launches: one block per kFineBlock / 32 slices, the slices staged
 // in dynamic shared memory (column indices, then values)
 inline int fine_blocks(int r0, int r1) {
@@ -963,7 +970,8 @@ inline int64_t fine_nslices(const DevLevel& L) { return ((int64_t)L.n + 31) / 32
 template <typename K>
 size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
     const size_t bytes = (size_t)kFineBlock * L.width * (sizeof(int32_t) + value_bytes);
-    if (bytes > 48 * 1024)
+    // the 48 KB default covers static and dynamic shared memory together
+    if (bytes > kDefaultDynSmem)
         AMG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)bytes));
     return bytes;
@@ -1086,7 +1094,7 @@ template <typename TB>
 void dense_gemv_impl(int n, const double* M, const TB* b, TB* x, cudaStream_t s) {
     auto k = k_dense_gemv<TB>;
     const size_t smem = std::is_same<TB, double>::value ? 0 : sizeof(double) * (size_t)n;
-    if (smem > 48 * 1024)
+    if (smem > kDefaultDynSmem)
         AMG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     launch_kernel(k, blocks_for((int64_t)n * 32), kBlock, smem, s, n, M, b, x);
 }

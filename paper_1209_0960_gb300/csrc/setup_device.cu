@@ -281,7 +281,7 @@ void galerkin_device(const DevCsr& A, const HostCsr& Ah, const AggResult& R, Dev
                                     " fine entries, more than the shared-memory staging holds"};
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, smem_limit / per_warp));
     const size_t smem = per_warp * wpb;
-    if (smem > 48 * 1024) {
+    if (smem > 40 * 1024) {   // the 48 KB default also holds static shared memory
         AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     }
@@ -389,7 +389,7 @@ bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
     double* U = tmp.alloc<double>((size_t)n * n);
     k_transpose<<<blocks_for((int64_t)n * n), kBlock, 0, s>>>(n, L, U);
     const size_t smem = sizeof(double) * (size_t)n;
-    if (smem > 48 * 1024)
+    if (smem > 40 * 1024)   // the 48 KB default also holds static shared memory
         AMG_CUDA_TRY(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     k_chol_inverse<<<n, 32, smem, s>>>(n, L, U, Minv);
     AMG_CUDA_TRY(cudaGetLastError());

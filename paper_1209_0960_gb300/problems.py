@@ -317,6 +317,29 @@ def cube_in_cube3d(n: int) -> Problem:
     return Problem("cube_in_cube3d_%d" % n, shape, rp, ci, va, b, dict(kind="cube_in_cube3d"))
 
 
+def hub_graph2d(n: int, degree: int = 24, seed: int = 0) -> Problem:
+    """2D 5-point Laplacian (u = 0 on the boundary) plus one extra vertex
+    coupled to ``degree`` random cells with weight 1 (symmetric, diagonally
+    dominant): a sparse matrix with one long row, for kernels whose tiles are
+    sized by the longest row."""
+    rp, ci, va = grid_laplacian((n, n))
+    N = n * n
+    rng = np.random.default_rng(seed)
+    nb = np.sort(rng.choice(N, size=degree, replace=False))
+    rows, cols, vals = [], [], []
+    for i in range(N):
+        for k in range(rp[i], rp[i + 1]):
+            rows.append(i); cols.append(int(ci[k]))
+            vals.append(float(va[k]) + (1.0 if ci[k] == i and i in set(nb.tolist()) else 0.0))
+    for j in nb:
+        rows += [N, int(j)]; cols += [int(j), N]; vals += [-1.0, -1.0]
+    rows.append(N); cols.append(N); vals.append(degree + 1.0)
+    rp2, ci2, va2 = _coo_to_csr(N + 1, rows, cols, vals)
+    b = rng.uniform(-1.0, 1.0, size=N + 1)
+    return Problem("hub_graph2d_%d_%d" % (n, degree), (n, n), rp2, ci2, va2, b,
+                   dict(kind="hub_graph2d", degree=degree, seed=seed))
+
+
 def laplacian_1d(n: int) -> tuple:
     """tridiag(-1, 2, -1) of order n as CSR (a closed-form test matrix)."""
     rows, cols, vals = [], [], []

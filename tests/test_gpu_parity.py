@@ -43,6 +43,9 @@ CASES = {
     "lognormal_deep_16": (lambda: P.lognormal3d((16, 16, 16), seed=5), {"coarsen_target": 12}),
     "poisson_exp_24": (lambda: P.poisson_exp3d(24), {"coarsen_target": 200}),
     "cube_in_cube_24": (lambda: P.cube_in_cube3d(24), {"coarsen_target": 200}),
+    # one row of 24 off-diagonals on a sparse fine level: staged tiles above
+    # the default 48 KB of shared memory
+    "hub_graph2d_48": (lambda: P.hub_graph2d(48), {"coarsen_target": 100}),
 }
 
 
