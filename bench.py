@@ -53,8 +53,10 @@ def parse_args():
     ap.add_argument("--launch-overlap", type=int, choices=[0, 1], default=1,
                     help="programmatic dependent launch between solve kernels")
     ap.add_argument("--profile-run", type=int, default=0, metavar="MAXIT",
-                    help="for profilers: set up the workload, run one FP64 solve capped at "
+                    help="for profilers: set up the workload, run one solve capped at "
                          "MAXIT iterations, print nothing else and exit")
+    ap.add_argument("--profile-fp32", action="store_true",
+                    help="with --profile-run: the FP32-in-FP64 solve instead of FP64")
     ap.add_argument("--serving", type=int, default=0, metavar="N",
                     help="serving workload instead: N independent requests (box sides "
                          "U{16..96}, variance U[1,6]) with Poisson arrivals at --load times the "
@@ -446,12 +448,14 @@ def run_ours(args, dist: Dist):
 
 
 def profile_run(args):
-    """One capped FP64 solve of the workload, for ncu captures of single kernels."""
+    """One capped solve of the workload, for ncu captures of single kernels."""
     import torch
     from paper_1209_0960_gb300 import amg
     torch.cuda.set_device(0)
     p = make_problem(args.grid)
-    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap)
+    prec = amg.AMG_FP32_IN_FP64 if args.profile_fp32 else amg.AMG_FP64
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap,
+                     precision=prec)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)
     torch.cuda.synchronize()

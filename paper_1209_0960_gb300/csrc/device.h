@@ -250,8 +250,7 @@ int reduction_blocks(int64_t work_threads);
 // V-cycle passes (see kernels.cu).  first: the first two forward colour passes
 // from a zero guess (optionally zeroing the next level's right-hand side);
 // pass: one colour, neighbours at positions >= jmax taken as zero;
-// pass_prolong: colour 0 of a two-colour level reading the other colour's
-// prolongated values; residual_restrict: coarse right-hand side from the
+// residual_restrict: coarse right-hand side from the
 // residual of the rows of colour >= 1; prolong: x += omega P e on colour >= 1.
 void launch_first(const DevLevel& L, const double* b, double* x, double* bc_zero, int nc,
                   cudaStream_t s);
@@ -259,10 +258,13 @@ void launch_first32(const DevLevel& L, const float* b, float* x, float* bc_zero,
                     cudaStream_t s);
 void launch_pass(const DevLevel& L, int col, int jmax, const double* b, double* x, cudaStream_t s);
 void launch_pass32(const DevLevel& L, int col, int jmax, const float* b, float* x, cudaStream_t s);
-void launch_pass_prolong(const DevLevel& L, const double* b, double* x, const double* e,
-                         double omega, cudaStream_t s);
-void launch_pass_prolong32(const DevLevel& L, const float* b, float* x, const float* e,
-                           double omega, cudaStream_t s);
+// fine level of the float32 V-cycle: the first pass forms b = r / s from the
+// float64 residual (isq = 1/s), and the last pass over each colour also
+// writes z = x / s in float64 (the V-cycle's output)
+void launch_first32_from64(const DevLevel& L, const double* r, const double* isq, float* b,
+                           float* x, float* bc_zero, int nc, cudaStream_t s);
+void launch_pass32_to64(const DevLevel& L, int col, int jmax, const float* b, float* x,
+                        double* z, const double* isq, cudaStream_t s);
 void launch_residual_restrict(const DevLevel& L, const double* b, const double* x, double* r,
                               double* bc, cudaStream_t s);
 void launch_residual_restrict32(const DevLevel& L, const float* b, const float* x, float* r,

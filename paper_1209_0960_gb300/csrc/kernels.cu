@@ -166,26 +166,19 @@ __device__ void finish_reduction(double v0, double v1, double* partials, double*
 //                later colours, which are still zero during the forward sweep
 //                of pre-smoothing, and are skipped;
 //   kNbrFirst    b_j / A_jj for j < jmax: the colour-0 values of the first
-//                pass from a zero guess, recomputed instead of read back;
-//   kNbrProlong  x_j + omega t_j e_agg(j): the post-smoothing of a two-colour
-//                level reads the prolongated values of the other colour
-//                without writing them (the next pass overwrites that colour).
+//                pass from a zero guess, recomputed instead of read back.
+// (Prolongating the other colour's values on the fly inside the first
+// post-smoothing pass of a two-colour level was measured slower than a
+// separate prolongation kernel: six gathers of agg, t and e per row.)
 // ---------------------------------------------------------------------------
-enum NbrMode : int { kNbrX = 0, kNbrFirst = 1, kNbrProlong = 2 };
+enum NbrMode : int { kNbrX = 0, kNbrFirst = 1 };
 
 constexpr int kUnroll = 8;
 
-template <int MODE, bool SCALED, typename T>
-__device__ __forceinline__ T nbr_value(int j, const T* x, const T* b,
-                                       const T* __restrict__ dinv, const int32_t* __restrict__ agg,
-                                       const T* __restrict__ t, const T* e, T omega) {
+template <int MODE, typename T>
+__device__ __forceinline__ T nbr_value(int j, const T* x, const T* b, const T* __restrict__ dinv) {
     if (MODE == kNbrFirst) return b[j] * dinv[j];
-    T v = x[j];
-    if (MODE == kNbrProlong) {
-        const int ag = agg[j];
-        if (ag >= 0) v = fmad(SCALED ? omega * t[j] : omega, e[ag], v);
-    }
-    return v;
+    return x[j];
 }
 
 // The row sum starts from acc(), which reads vectors of the solve: it and all
@@ -202,13 +195,11 @@ __host__ __device__ constexpr int lanes_of() { return LPR == kFine ? 1 : LPR; }
 template <int LPR>
 __host__ __device__ constexpr int unroll_of() { return LPR == 1 ? 24 : LPR == 2 ? 12 : kUnroll; }
 
-template <int LPR, int MODE, bool SCALED, typename T, typename AccF>
+template <int LPR, int MODE, typename T, typename AccF>
 __device__ __forceinline__ T row_update(int64_t base, int len, int width, int lane, int jmax,
                                         const int32_t* __restrict__ scol,
                                         const T* __restrict__ sval, const T* x,
-                                        const T* b, const T* __restrict__ dinv,
-                                        const int32_t* __restrict__ agg, const T* __restrict__ t,
-                                        const T* e, T omega, AccF acc) {
+                                        const T* b, const T* __restrict__ dinv, AccF acc) {
     static_assert(LPR != kFine, "the fine level uses the staged kernels");
     // every lane of the warp runs the same number of batches (the slice width
     // bounds every row length), so the warp-wide votes below see all 32 lanes
@@ -242,7 +233,7 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
         for (int u = 0; u < U; ++u) {
             v[u] = T(0);
             if (__any_sync(0xffffffffu, j[u] < jmax) && j[u] < jmax)
-                v[u] = nbr_value<MODE, SCALED>(j[u], x, b, dinv, agg, t, e, omega);
+                v[u] = nbr_value<MODE, T>(j[u], x, b, dinv);
         }
 #pragma unroll
         for (int u = 0; u < U; ++u)
@@ -288,34 +279,30 @@ __global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, int64_t sw,
     const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
     const T di = R.valid ? dinv[rr] : T(0);
-    const T s = row_update<LPR, kNbrFirst, false, T>(
-        base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x, b, dinv, nullptr, nullptr, nullptr,
-        T(0), [&] { return R.valid ? b[rr] : T(0); });
+    const T s = row_update<LPR, kNbrFirst, T>(base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x,
+                                               b, dinv, [&] { return R.valid ? b[rr] : T(0); });
     if (R.valid && R.lane == 0) x[rr] = s * di;
 }
 
 // One Gauss-Seidel update of the rows [r0, r1) of one colour:
 //   x_i = (b_i - sum_{j != i, j < jmax} A_ij x_j) / A_ii.
 // Rows of one colour are not coupled, so they update in parallel.
-template <int LPR, int MODE, bool SCALED, typename T>
+template <int LPR, typename T>
 __global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
                                                     int64_t sw,
                                                     const uint16_t* __restrict__ rlen,
                                                     const int32_t* __restrict__ scol,
                                                     const T* __restrict__ sval,
                                                     const T* __restrict__ dinv,
-                                                    const T* b, T* x,
-                                                    const int32_t* __restrict__ agg,
-                                                    const T* __restrict__ t,
-                                                    const T* e, T omega) {
+                                                    const T* b, T* x) {
     pdl_launch_dependents();
     const RowOf<LPR> R(r0, r1);
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
     const T di = R.valid ? dinv[rr] : T(0);
-    const T s = row_update<LPR, MODE, SCALED, T>(base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5),
-                                                 R.lane, jmax, scol, sval, x, b, dinv, agg, t, e,
-                                                 omega, [&] { return R.valid ? b[rr] : T(0); });
+    const T s = row_update<LPR, kNbrX, T>(base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5),
+                                          R.lane, jmax, scol, sval, x, b, dinv,
+                                          [&] { return R.valid ? b[rr] : T(0); });
     if (R.valid && R.lane == 0) x[rr] = s * di;
 }
 
@@ -332,9 +319,9 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
     const int rr = R.valid ? R.row : r0;
     const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
     const T dg = R.valid ? diag[rr] : T(0);
-    const T v = row_update<LPR, kNbrX, false, T>(
-        base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5), R.lane, n, scol, sval, x, nullptr,
-        nullptr, nullptr, nullptr, nullptr, T(0),
+    const T v = row_update<LPR, kNbrX, T>(
+        base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5), R.lane, n, scol, sval, x,
+        (const T*)nullptr, (const T*)nullptr,
         [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
     if (R.valid && R.lane == 0) r[rr] = v;
 }
@@ -426,30 +413,33 @@ struct FineTile {
     }
 };
 
-// acc - sum over the staged entries of this thread's row with j < jmax
-template <int MODE, bool SCALED, typename T>
-__device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, const T* x,
-                                      const T* b, const T* __restrict__ dinv,
-                                      const int32_t* __restrict__ agg, const T* __restrict__ t,
-                                      const T* e, T omega, T acc) {
+// acc - sum over the staged entries of this thread's row with j < jmax of
+// A_ij nbr(j)
+template <typename T, typename Nbr>
+__device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, Nbr nbr, T acc) {
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
         const int j = F.s_col[F.loc + 32 * k];
         const T a = F.s_val[F.loc + 32 * k];
-        if (j < jmax) acc = fmad(-a, nbr_value<MODE, SCALED>(j, x, b, dinv, agg, t, e, omega), acc);
+        if (j < jmax) acc = fmad(-a, nbr(j), acc);
     }
     return acc;
 }
 
 // k_first on the fine level; also zeroes the next level's right-hand side
 // for the fused residual-restriction kernel.  Blocks with colour-0 rows only
-// need no matrix.
+// need no matrix.  With r_in set (float32 V-cycle inside float64 CG) the
+// right-hand side is the scaled residual b_i = r_i / s_i (isq = 1/s), formed
+// here for each row and neighbour and stored to b for the later passes.
 template <typename T>
 __global__ void __launch_bounds__(kFineBlock) k_fine_first(int c1, int c2, int width, int64_t nslices,
                                                        const uint16_t* __restrict__ rlen,
                                                        const int32_t* scol, const T* sval,
-                                                       const T* __restrict__ dinv, const T* b,
-                                                       T* x, T* bc_zero, int nc, int32_t* err) {
+                                                       const T* __restrict__ dinv, T* b,
+                                                       T* x, T* bc_zero, int nc,
+                                                       const double* r_in,
+                                                       const double* __restrict__ isq,
+                                                       int32_t* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     pdl_launch_dependents();
@@ -461,24 +451,32 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_first(int c1, int c2, int w
     if (staged && !stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err))
         return;
     pdl_wait();
-    if (valid)
-        x[F.row] = fine_row<kNbrFirst, false, T>(F, len, c1, x, b, dinv, nullptr, nullptr, nullptr,
-                                              T(0), b[F.row]) * di;
+    if (valid) {
+        if (r_in) {
+            auto bj = [&](int j) { return (T)(r_in[j] * isq[j]); };
+            const T bi = bj(F.row);
+            b[F.row] = bi;
+            x[F.row] = fine_row<T>(F, len, c1, [&](int j) { return bj(j) * dinv[j]; }, bi) * di;
+        } else {
+            x[F.row] = fine_row<T>(F, len, c1, [&](int j) { return b[j] * dinv[j]; }, b[F.row]) * di;
+        }
+    }
     if (bc_zero)
         for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
             bc_zero[i] = T(0);
 }
 
-// k_gs_pass on the fine level
-template <int MODE, bool SCALED, typename T>
+// k_gs_pass on the fine level.  With z_out set (the last pass over these rows
+// in a float32 V-cycle) the new value also goes out unscaled in float64:
+// z_i = x_i / s_i (isq = 1/s).
+template <typename T>
 __global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jmax, int width,
                                                       int64_t nslices,
                                                       const uint16_t* __restrict__ rlen,
                                                       const int32_t* scol, const T* sval,
                                                       const T* __restrict__ dinv, const T* b, T* x,
-                                                      const int32_t* __restrict__ agg,
-                                                      const T* __restrict__ t, const T* e,
-                                                      T omega, int32_t* err) {
+                                                      double* z_out, const double* __restrict__ isq,
+                                                      int32_t* err) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     pdl_launch_dependents();
@@ -489,7 +487,9 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jm
     if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
     pdl_wait();
     if (!valid) return;
-    x[F.row] = fine_row<MODE, SCALED, T>(F, len, jmax, x, b, dinv, agg, t, e, omega, b[F.row]) * di;
+    const T xi = fine_row<T>(F, len, jmax, [&](int j) { return x[j]; }, b[F.row]) * di;
+    x[F.row] = xi;
+    if (z_out) z_out[F.row] = (double)xi * isq[F.row];
 }
 
 // k_residual on the fine level
@@ -510,8 +510,7 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int
     if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
     pdl_wait();
     if (!valid) return;
-    r[F.row] = fine_row<kNbrX, false, T>(F, len, n, x, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                      T(0), fmad(-dg, x[F.row], b[F.row]));
+    r[F.row] = fine_row<T>(F, len, n, [&](int j) { return x[j]; }, fmad(-dg, x[F.row], b[F.row]));
 }
 
 // Residual and restriction in one pass on a two-colour fine level: the rows
@@ -543,8 +542,8 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_residual_restrict(
     pdl_wait();
     T v = T(0);
     if (valid) {
-        const T ri = fine_row<kNbrX, false, T>(F, len, n, x, nullptr, nullptr, nullptr, nullptr,
-                                            nullptr, T(0), fmad(-dg, x[F.row], b[F.row]));
+        const T ri = fine_row<T>(F, len, n, [&](int j) { return x[j]; },
+                                 fmad(-dg, x[F.row], b[F.row]));
         v = SCALED ? ti * ri : ri;
     }
     const int tid = threadIdx.x;
@@ -977,40 +976,45 @@ size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
     return bytes;
 }
 
+// r_in / isq (fine level only): form b = r * isq in the first pass (the
+// float32 V-cycle's entry); b is then written, not read
 template <typename T>
-void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStream_t s) {
+void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStream_t s,
+                const double* r_in = nullptr, const double* isq = nullptr) {
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
     if (L.lpr == kFine) {
         auto k = k_fine_first<T>;
         launch_kernel(k, std::max(1, fine_blocks(0, c2)), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1,
-                      c2, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, bc_zero,
-                      nc, L.err);
+                      c2, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, const_cast<T*>(b),
+                      x, bc_zero, nc, r_in, isq, L.err);
         return;
     }
+    if (r_in) throw Error{AMG_EINVAL, "the fused float32 entry needs the fine-level kernels"};
     AMG_LPR_DISPATCH(launch_lpr(L, c2),
                      (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock,
                                     0, s, c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
 }
 
-template <typename T, int MODE>
-void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, const T* e, double omega,
-               cudaStream_t s) {
+// z_out / isq (fine level only): also write z = x * isq in float64 for the
+// rows of this pass (the float32 V-cycle's exit)
+template <typename T>
+void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, cudaStream_t s,
+               double* z_out = nullptr, const double* isq = nullptr) {
     const LevelArrays<T> A(L);
     const int r0 = L.cptr[col], r1 = L.cptr[col + 1];
     if (r1 <= r0) return;
-    constexpr bool SC = std::is_same<T, float>::value;
     if (L.lpr == kFine) {
-        auto k = k_fine_pass<MODE, SC, T>;
+        auto k = k_fine_pass<T>;
         launch_kernel(k, fine_blocks(r0, r1), kFineBlock, fine_smem(k, L, sizeof(T)), s, r0, r1, jmax,
-                      L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, L.agg, A.t,
-                      e, (T)omega, L.err);
+                      L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, z_out, isq,
+                      L.err);
         return;
     }
+    if (z_out) throw Error{AMG_EINVAL, "the fused float32 exit needs the fine-level kernels"};
     AMG_LPR_DISPATCH(launch_lpr(L, r1 - r0),
-                     (launch_kernel(k_gs_pass<LPR, MODE, SC, T>, row_blocks(r0, r1, LPR), kBlock, 0,
-                                    s, r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x,
-                                    L.agg, A.t, e, (T)omega)));
+                     (launch_kernel(k_gs_pass<LPR, T>, row_blocks(r0, r1, LPR), kBlock, 0, s, r0, r1,
+                                    jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
 }
 
 template <typename T>
@@ -1062,18 +1066,18 @@ void launch_first32(const DevLevel& L, const float* b, float* x, float* bc_zero,
     first_impl<float>(L, b, x, bc_zero, nc, s);
 }
 void launch_pass(const DevLevel& L, int col, int jmax, const double* b, double* x, cudaStream_t s) {
-    pass_impl<double, kNbrX>(L, col, jmax, b, x, nullptr, 0.0, s);
+    pass_impl<double>(L, col, jmax, b, x, s);
 }
 void launch_pass32(const DevLevel& L, int col, int jmax, const float* b, float* x, cudaStream_t s) {
-    pass_impl<float, kNbrX>(L, col, jmax, b, x, nullptr, 0.0, s);
+    pass_impl<float>(L, col, jmax, b, x, s);
 }
-void launch_pass_prolong(const DevLevel& L, const double* b, double* x, const double* e,
-                         double omega, cudaStream_t s) {
-    pass_impl<double, kNbrProlong>(L, 0, L.n, b, x, e, omega, s);
+void launch_first32_from64(const DevLevel& L, const double* r, const double* isq, float* b,
+                           float* x, float* bc_zero, int nc, cudaStream_t s) {
+    first_impl<float>(L, b, x, bc_zero, nc, s, r, isq);
 }
-void launch_pass_prolong32(const DevLevel& L, const float* b, float* x, const float* e,
-                           double omega, cudaStream_t s) {
-    pass_impl<float, kNbrProlong>(L, 0, L.n, b, x, e, omega, s);
+void launch_pass32_to64(const DevLevel& L, int col, int jmax, const float* b, float* x,
+                        double* z, const double* isq, cudaStream_t s) {
+    pass_impl<float>(L, col, jmax, b, x, s, z, isq);
 }
 void launch_residual_restrict(const DevLevel& L, const double* b, const double* x, double* r,
                               double* bc, cudaStream_t s) {

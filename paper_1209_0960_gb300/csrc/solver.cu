@@ -93,14 +93,6 @@ double first_bytes(const DevLevel& L, int vb) {
     return c1 * 3.0 * vb + z1 * (vb + 4) + m1 * (2 + 3.0 * vb) +
            (L.fused_restrict ? (double)L.n_coarse * vb : 0.0);
 }
-// colour 0 of a two-colour level with on-the-fly prolongation: its entries,
-// b, 1/A_ii, written x, and once per colour-1 row its x, coarse index (and
-// transfer weight), plus the coarse correction
-double pass_prolong_bytes(const DevLevel& L, int vb, bool scaled) {
-    const double m0 = L.cptr[1], m1 = L.n - L.cptr[1];
-    return (double)L.cnnz[0] * (vb + 4) + m0 * (2 + 3.0 * vb) +
-           m1 * (vb + 4 + (scaled ? 4 : 0)) + (double)L.n_coarse * vb;
-}
 // residual of the rows of colour >= 1 and restriction: entries, lengths, A_ii,
 // b, own x, colour-0 neighbour values once, then either the coarse index (and
 // weight) and one atomic add per aggregate (fused) or the written r, the
@@ -128,13 +120,9 @@ double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb) {
     for (int col = 2; col < C; ++col) t += pass_bytes(L, col, L.cptr[col], vb);
     for (int col = C - 2; col >= 0; --col) t += pass_bytes(L, col, L.n, vb);
     t += residual_restrict_bytes(L, vb, scaled);
-    if (C == 2) {
-        t += pass_prolong_bytes(L, vb, scaled) + pass_bytes(L, 1, L.n, vb) + pass_bytes(L, 0, L.n, vb);
-    } else {
-        t += prolong_bytes(L, vb, scaled);
-        for (int col = 0; col < C; ++col) t += pass_bytes(L, col, L.n, vb);
-        for (int col = C - 2; col >= 0; --col) t += pass_bytes(L, col, L.n, vb);
-    }
+    t += prolong_bytes(L, vb, scaled);
+    for (int col = 0; col < C; ++col) t += pass_bytes(L, col, L.n, vb);
+    for (int col = C - 2; col >= 0; --col) t += pass_bytes(L, col, L.n, vb);
     return t;
 }
 
@@ -212,9 +200,9 @@ struct ProfScope {
 //   pre   first (colours 0 and 1 from zero), colours 2..C-1 forward reading
 //         only earlier colours, colours C-2..0 backward;
 //   restrict the residual of colours >= 1 (colour 0 was smoothed last);
-//   recurse; then on two-colour levels colour 0 reads the prolongated values
-//         of colour 1 on the fly, followed by colour 1 and colour 0; on other
-//         levels x += omega P e on colours >= 1, then colours 0..C-1, C-2..0.
+//   recurse; then x += omega P e on colours >= 1 (colour 0 is recomputed
+//         by the next pass without reading its old values), then colours
+//         0..C-1, C-2..0.
 template <typename T>
 struct Prec;
 template <>
@@ -236,8 +224,6 @@ inline void k_first(const DevLevel& L, const double* b, double* x, double* bc, i
 inline void k_first(const DevLevel& L, const float* b, float* x, float* bc, int nc, cudaStream_t s) { launch_first32(L, b, x, bc, nc, s); }
 inline void k_pass(const DevLevel& L, int col, int jmax, const double* b, double* x, cudaStream_t s) { launch_pass(L, col, jmax, b, x, s); }
 inline void k_pass(const DevLevel& L, int col, int jmax, const float* b, float* x, cudaStream_t s) { launch_pass32(L, col, jmax, b, x, s); }
-inline void k_pass_prolong(const DevLevel& L, const double* b, double* x, const double* e, double w, cudaStream_t s) { launch_pass_prolong(L, b, x, e, w, s); }
-inline void k_pass_prolong(const DevLevel& L, const float* b, float* x, const float* e, double w, cudaStream_t s) { launch_pass_prolong32(L, b, x, e, w, s); }
 inline void k_resres(const DevLevel& L, const double* b, const double* x, double* r, double* bc, cudaStream_t s) { launch_residual_restrict(L, b, x, r, bc, s); }
 inline void k_resres(const DevLevel& L, const float* b, const float* x, float* r, float* bc, cudaStream_t s) { launch_residual_restrict32(L, b, x, r, bc, s); }
 inline void k_prolong(const DevLevel& L, const double* e, double* x, double w, cudaStream_t s) { launch_prolong(L, e, x, w, s); }
@@ -278,21 +264,6 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
         k_resres(L, b, x, P::r(L), P::b(N), s);
     }
     vcycle<T>(c, l + 1, P::b(N), P::x(N));
-    if (C == 2) {
-        {
-            ProfScope ps(c, l == 0 ? kKPassProlongL0 : kKGsCoarse, pass_prolong_bytes(L, vb, scaled));
-            k_pass_prolong(L, b, x, P::x(N), c->p.omega, s);
-        }
-        {
-            ProfScope ps(c, kind, pass_bytes(L, 1, L.n, vb));
-            k_pass(L, 1, L.n, b, x, s);
-        }
-        {
-            ProfScope ps(c, kind, pass_bytes(L, 0, L.n, vb));
-            k_pass(L, 0, L.n, b, x, s);
-        }
-        return;
-    }
     {
         ProfScope ps(c, kKProlong, prolong_bytes(L, vb, scaled));
         k_prolong(L, P::x(N), x, c->p.omega, s);
@@ -310,10 +281,59 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
 void vcycle64(amg_ctx* c, int l, const double* b, double* x) { vcycle<double>(c, l, b, x); }
 void vcycle32(amg_ctx* c, int l, const float* b, float* x) { vcycle<float>(c, l, b, x); }
 
+// The float32 V-cycle with its float64 entry and exit folded into the
+// fine-level passes: the first pass forms b = r / s itself, and the last
+// pass over each colour writes z = x / s (same values as separate conversion
+// kernels, two launches and a vector round trip fewer).
+void vcycle32_fused(amg_ctx* c, const double* r, double* z) {
+    DevLevel& L = c->dl[0];
+    DevLevel& N = c->dl[1];
+    cudaStream_t s = c->stream;
+    const int C = L.ncolours;
+    const double* isq = c->isq0;
+    float* b = L.b32;
+    float* x = L.x32;
+    {
+        ProfScope ps(c, kKFirstL0, first_bytes(L, 4) + 12.0 * L.n);
+        launch_first32_from64(L, r, isq, b, x, L.fused_restrict ? N.b32 : nullptr, N.n, s);
+    }
+    for (int col = 2; col < C; ++col) {
+        ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.cptr[col], 4));
+        launch_pass32(L, col, L.cptr[col], b, x, s);
+    }
+    for (int col = C - 2; col >= 0; --col) {
+        ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.n, 4));
+        launch_pass32(L, col, L.n, b, x, s);
+    }
+    {
+        ProfScope ps(c, kKResidualL0, residual_restrict_bytes(L, 4, true));
+        launch_residual_restrict32(L, b, x, L.r32, N.b32, s);
+    }
+    vcycle32(c, 1, N.b32, N.x32);
+    {
+        ProfScope ps(c, kKProlong, prolong_bytes(L, 4, true));
+        launch_prolong32(L, N.x32, x, c->p.omega, s);
+    }
+    // the last pass over each colour also writes z
+    for (int col = 0; col < C; ++col) {
+        const bool last = col == C - 1;
+        ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.n, 4) + (last ? 16.0 * (L.cptr[col + 1] - L.cptr[col]) : 0.0));
+        if (last) launch_pass32_to64(L, col, L.n, b, x, z, isq, s);
+        else launch_pass32(L, col, L.n, b, x, s);
+    }
+    for (int col = C - 2; col >= 0; --col) {
+        ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.n, 4) + 16.0 * (L.cptr[col + 1] - L.cptr[col]));
+        launch_pass32_to64(L, col, L.n, b, x, z, isq, s);
+    }
+}
+
 // z = B r on level 0 (smoothing order) in the context's precision
 void precondition(amg_ctx* c, const double* r, double* z) {
     if (c->precision == AMG_FP64) {
         vcycle64(c, 0, r, z);
+    } else if (c->dl.size() > 1 && c->dl[0].lpr == 0 && c->dl[0].ncolours == 2) {
+        // (two colours: the first pass covers every row, so it can form all of b)
+        vcycle32_fused(c, r, z);
     } else {
         DevLevel& L0 = c->dl[0];
         {
