@@ -65,6 +65,9 @@ struct Params {
     int max_levels;
     int dense_cap;         // largest coarsest level solved densely
     double min_rate;       // stop when n_l / n_{l+1} falls below this
+    int smoother = 0;      // 0: multicolour symmetric GS (the GPU's order);
+                           // 1: sequential symmetric GS in index order (the
+                           //    paper's hybrid smoother on a single process)
 };
 
 // ---------------------------------------------------------------------------
@@ -572,6 +575,30 @@ void sgs(const Level& lv, const double* b, double* x) {
     for (int c = lv.ncolours - 2; c >= 0; --c) gs_colour(lv, c, b, x);
 }
 
+// One symmetric Gauss-Seidel step in index order (Sec. 3.2: inside each
+// process the hybrid smoother is a sequential GS sweep; on one process it is
+// exactly this): rows 0..n-1 forward, then n-1..0 backward, each using the
+// newest values of its neighbours.
+void gs_row(const Csr& A, int i, const double* b, double* x) {
+    double t = b[i];
+    double d = 0.0;
+    for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+        if (A.ci[k] == i) d = A.va[k];
+        else t -= A.va[k] * x[A.ci[k]];
+    }
+    x[i] = t / d;
+}
+
+void sgs_sequential(const Level& lv, const double* b, double* x) {
+    for (int i = 0; i < lv.A.n; ++i) gs_row(lv.A, i, b, x);
+    for (int i = lv.A.n - 1; i >= 0; --i) gs_row(lv.A, i, b, x);
+}
+
+void smooth(const Hierarchy& H, const Level& lv, const double* b, double* x) {
+    if (H.p.smoother == 1) sgs_sequential(lv, b, x);
+    else sgs(lv, b, x);
+}
+
 void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     const Level& lv = H.levels[l];
     int n = lv.A.n;
@@ -580,7 +607,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
         return;
     }
     std::fill(x, x + n, 0.0);
-    sgs(lv, b, x);                                   // pre-smoothing, one step
+    smooth(H, lv, b, x);                             // pre-smoothing, one step
     std::vector<double> r(n);
     spmv(lv.A, x, r.data());
     for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
@@ -597,7 +624,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
         int I = lv.agg[i];
         if (I >= 0) x[i] = x[i] + H.p.omega * ec[I];
     }
-    sgs(lv, b, x);                                   // post-smoothing, one step
+    smooth(H, lv, b, x);                             // post-smoothing, one step
 }
 
 double dot(const std::vector<double>& a, const std::vector<double>& b) {
@@ -627,6 +654,7 @@ Params make_params(const double* q) {
     p.max_levels = (int)q[7];
     p.dense_cap = (int)q[8];
     p.min_rate = q[9];
+    p.smoother = (int)q[10];
     return p;
 }
 
@@ -635,7 +663,7 @@ Params make_params(const double* q) {
 // ---------------------------------------------------------------------------
 // C entry points (called through ctypes by the tests and the benchmark)
 // params: [delta, beta, omega, s_min, s_max, d_max, coarsen_target,
-//          max_levels, dense_cap, min_rate]
+//          max_levels, dense_cap, min_rate, smoother]
 // ---------------------------------------------------------------------------
 extern "C" {
 

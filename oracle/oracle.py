@@ -29,15 +29,18 @@ _lib = None
 def default_params(dim: int) -> dict:
     return dict(delta=1.0 / 3.0, beta=1e-5, omega=1.6,
                 s_min=2 ** dim, s_max=3 * 2 ** (dim - 1), d_max=dim,
-                coarsen_target=5000, max_levels=20, dense_cap=8192, min_rate=1.2)
+                coarsen_target=5000, max_levels=20, dense_cap=8192, min_rate=1.2,
+                smoother=0)
 
 
 _ORDER = ["delta", "beta", "omega", "s_min", "s_max", "d_max",
-          "coarsen_target", "max_levels", "dense_cap", "min_rate"]
+          "coarsen_target", "max_levels", "dense_cap", "min_rate", "smoother"]
 
 
 def _param_array(p: dict) -> np.ndarray:
-    return np.array([float(p[k]) for k in _ORDER], dtype=np.float64)
+    # smoother: 0 multicolour symmetric GS (the GPU's order), 1 sequential
+    # symmetric GS in index order
+    return np.array([float(p.get(k, 0)) for k in _ORDER], dtype=np.float64)
 
 
 def build(force: bool = False) -> str:

@@ -409,3 +409,68 @@ def test_cube_in_cube_coefficients_and_solve():
     x, it, rel, trel = H.pcg(p.b, tol=1e-10, maxit=300)
     xd = np.linalg.solve(A, p.b)
     assert 0 < it < 100 and np.linalg.norm(x - xd) <= 1e-6 * np.linalg.norm(xd)
+
+
+# ---------------------------------------------------------------------------
+# smoother ordering: the GPU's multicolour symmetric GS against the paper's
+# sequential (single-process hybrid) symmetric GS, same hierarchy otherwise
+# ---------------------------------------------------------------------------
+
+def _gs_sweep(A, b, x, order):
+    x = x.copy()
+    for i in order:
+        x[i] = (b[i] - A[i] @ x + A[i, i] * x[i]) / A[i, i]
+    return x
+
+
+def _two_level_vcycle(A, Ac, agg, omega, b, fwd, bwd):
+    """V(1,1) with an exact coarse solve, written out densely: symmetric GS
+    sweeps in the given row orders, r_c = P^T r, x += omega P A_c^-1 r_c."""
+    n = A.shape[0]
+    P_ = np.zeros((n, Ac.shape[0]))
+    P_[np.arange(n)[agg >= 0], agg[agg >= 0]] = 1.0
+    x = _gs_sweep(A, b, np.zeros(n), fwd)
+    x = _gs_sweep(A, b, x, bwd)
+    x = x + omega * P_ @ np.linalg.solve(Ac, P_.T @ (b - A @ x))
+    x = _gs_sweep(A, b, x, fwd)
+    return _gs_sweep(A, b, x, bwd)
+
+
+@pytest.mark.parametrize("smoother", [0, 1])
+def test_two_level_vcycle_matches_its_dense_formula(smoother):
+    # pins the smoother order: sequential symmetric GS sweeps rows 0..n-1 and
+    # back; the multicolour one sweeps colour blocks 0..C-1 and C-2..0 (rows
+    # of one colour are uncoupled, so their order inside a block is free)
+    p = P.lognormal3d((7, 6, 5), seed=4)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=40, smoother=smoother))
+    assert H.num_levels == 2
+    l0, l1 = H.level(0), H.level(1)
+    A = to_dense(p.row_ptr, p.col, p.val)
+    Ac = to_dense(l1["row_ptr"], l1["col"], l1["val"])
+    if smoother == 1:
+        fwd = list(range(p.n))
+        bwd = fwd[::-1]
+    else:
+        col = l0["colour"]
+        fwd = sorted(range(p.n), key=lambda i: (col[i], i))
+        bwd = sorted(range(p.n), key=lambda i: (-col[i], i))
+    z = _two_level_vcycle(A, Ac, l0["agg"], 1.6, p.b, fwd, bwd)
+    assert np.abs(H.vcycle(p.b) - z).max() <= 1e-11 * np.abs(z).max()
+
+
+@pytest.mark.parametrize("maker,dim", [
+    (lambda: P.lognormal3d((20, 20, 20), seed=0), 3),
+    (lambda: P.layered3d((20, 20, 20), seed=1), 3),
+    (lambda: P.cube_in_cube3d(24), 3),
+    (lambda: P.anisotropic3d((20, 20, 20), seed=0), 3),
+])
+def test_multicolour_sgs_costs_few_iterations_over_sequential_sgs(maker, dim):
+    p = maker()
+    its = []
+    for sm in (0, 1):
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(dim, coarsen_target=200, smoother=sm))
+        x, it, rel, trel = H.pcg(p.b, tol=1e-8, maxit=500)
+        assert it > 0 and trel <= 1.01e-8
+        its.append(it)
+    multicolour, sequential = its
+    assert multicolour <= 1.25 * sequential + 1
