@@ -250,7 +250,7 @@ def run_reference(args, dist: Dist):
 # our arm
 # ---------------------------------------------------------------------------
 
-VCYCLE_KINDS = {"gs_level0", "first_level0", "gs_prolong_level0", "gs_coarse", "residual_level0",
+VCYCLE_KINDS = {"gs_level0", "first_level0", "gs_coarse", "residual_level0",
                 "residual_coarse", "restrict", "prolong", "coarse_solve", "zero", "convert"}
 
 
@@ -430,7 +430,7 @@ def run_ours(args, dist: Dist):
                   "level_n": [l["n"] for l in levels]},
         "roofline": roofline,
         "roofline_level0": {k: kernel_roofline(k) for k in
-                            ("gs_level0", "first_level0", "gs_prolong_level0", "residual_level0",
+                            ("gs_level0", "first_level0", "residual_level0", "prolong",
                              "cg_spmv_dot")},
         "kernels_fp64": prof64,
         "graph_parts_ms": {
