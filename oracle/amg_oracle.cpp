@@ -65,6 +65,8 @@ struct Params {
     int max_levels;
     int dense_cap;         // largest coarsest level solved densely
     double min_rate;       // stop when n_l / n_{l+1} falls below this
+    int agg_tile = 0;      // > 0: decoupled aggregation in tiles of this many
+                           // consecutive rows (Alg. 4), else one sequential pass
     int smoother = 0;      // 0: multicolour symmetric GS (the GPU's order);
                            // 1: sequential symmetric GS in index order (the
                            //    paper's hybrid smoother on a single process)
@@ -655,7 +657,48 @@ Params make_params(const double* q) {
     p.dense_cap = (int)q[8];
     p.min_rate = q[9];
     p.smoother = (int)q[10];
+    p.agg_tile = (int)q[11];
     return p;
+}
+
+// Decoupled aggregation (Alg. 4, "ParallelAggregation"): the rows split into
+// consecutive tiles of `tile` rows, each aggregated by the sequential
+// Algorithm 1 on the tile's induced submatrix (edges that leave the tile
+// dropped, strength recomputed on the submatrix); aggregates are numbered tile
+// by tile and, inside a tile, in completion order.  isolated / dirichlet
+// report the per-tile classification.
+int aggregate_tiled(const Csr& A, const Params& p, int tile, std::vector<int>& agg,
+                    std::vector<char>& isolated, std::vector<char>& dirichlet) {
+    const int n = A.n;
+    agg.assign(n, -1);
+    isolated.assign(n, 0);
+    dirichlet.assign(n, 0);
+    int nc = 0;
+    for (int t0 = 0; t0 < n; t0 += tile) {
+        const int t1 = std::min(n, t0 + tile);
+        Csr sub;
+        sub.n = t1 - t0;
+        sub.rp.assign(sub.n + 1, 0);
+        for (int i = t0; i < t1; ++i) {
+            for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                const int j = A.ci[k];
+                if (j < t0 || j >= t1) continue;
+                sub.ci.push_back(j - t0);
+                sub.va.push_back(A.va[k]);
+            }
+            sub.rp[i - t0 + 1] = (int)sub.ci.size();
+        }
+        Strength S = compute_strength(sub, p);
+        Aggregator G(sub, S, p);
+        const int k = G.run();
+        for (int i = 0; i < sub.n; ++i) {
+            agg[t0 + i] = G.agg[i] >= 0 ? nc + G.agg[i] : -1;
+            isolated[t0 + i] = S.isolated[i];
+            dirichlet[t0 + i] = S.dirichlet[i];
+        }
+        nc += k;
+    }
+    return nc;
 }
 
 }  // namespace
@@ -663,7 +706,7 @@ Params make_params(const double* q) {
 // ---------------------------------------------------------------------------
 // C entry points (called through ctypes by the tests and the benchmark)
 // params: [delta, beta, omega, s_min, s_max, d_max, coarsen_target,
-//          max_levels, dense_cap, min_rate, smoother]
+//          max_levels, dense_cap, min_rate, smoother, agg_tile]
 // ---------------------------------------------------------------------------
 extern "C" {
 
@@ -685,6 +728,13 @@ int oracle_aggregate(int n, const int* rp, const int* ci, const double* va,
                      const double* params, int* agg) {
     Csr A = make_csr(n, rp, ci, va);
     Params p = make_params(params);
+    if (p.agg_tile > 0) {
+        std::vector<int> a;
+        std::vector<char> iso, dir;
+        const int nc = aggregate_tiled(A, p, p.agg_tile, a, iso, dir);
+        for (int i = 0; i < n; ++i) agg[i] = a[i];
+        return nc;
+    }
     Strength S = compute_strength(A, p);
     Aggregator G(A, S, p);
     int nc = G.run();
@@ -741,14 +791,24 @@ void* oracle_setup(int n, const int* rp, const int* ci, const double* va,
         int lidx = (int)H->levels.size() - 1;
         if (cur.A.n <= H->p.coarsen_target) break;
         if (lidx >= H->p.max_levels - 1) break;
-        Strength S = compute_strength(cur.A, H->p);
-        Aggregator G(cur.A, S, H->p);
-        int nc = G.run();
+        std::vector<int> agg;
+        std::vector<char> iso, dir;
+        int nc;
+        if (H->p.agg_tile > 0) {
+            nc = aggregate_tiled(cur.A, H->p, H->p.agg_tile, agg, iso, dir);
+        } else {
+            Strength S = compute_strength(cur.A, H->p);
+            Aggregator G(cur.A, S, H->p);
+            nc = G.run();
+            agg = G.agg;
+            iso = S.isolated;
+            dir = S.dirichlet;
+        }
         if (nc == 0 || (double)cur.A.n / (double)nc < H->p.min_rate) break;
-        cur.agg = G.agg;
+        cur.agg = agg;
         cur.nc = nc;
-        cur.isolated = S.isolated;
-        cur.dirichlet = S.dirichlet;
+        cur.isolated = iso;
+        cur.dirichlet = dir;
         cur.ncolours = greedy_colour(cur.A, cur.colour);
         Level next;
         next.A = galerkin(cur.A, cur.agg, nc);

@@ -34,12 +34,13 @@ def default_params(dim: int) -> dict:
 
 
 _ORDER = ["delta", "beta", "omega", "s_min", "s_max", "d_max",
-          "coarsen_target", "max_levels", "dense_cap", "min_rate", "smoother"]
+          "coarsen_target", "max_levels", "dense_cap", "min_rate", "smoother", "agg_tile"]
 
 
 def _param_array(p: dict) -> np.ndarray:
     # smoother: 0 multicolour symmetric GS (the GPU's order), 1 sequential
-    # symmetric GS in index order
+    # symmetric GS in index order; agg_tile: > 0 decoupled aggregation in
+    # tiles of that many consecutive rows (Alg. 4), 0 one sequential pass
     return np.array([float(p.get(k, 0)) for k in _ORDER], dtype=np.float64)
 
 

@@ -474,3 +474,58 @@ def test_multicolour_sgs_costs_few_iterations_over_sequential_sgs(maker, dim):
         its.append(it)
     multicolour, sequential = its
     assert multicolour <= 1.25 * sequential + 1
+
+
+# ---------------------------------------------------------------------------
+# decoupled aggregation in tiles of consecutive rows (Alg. 4)
+# ---------------------------------------------------------------------------
+
+def _induced(p, t0, t1):
+    rp, ci, va = [0], [], []
+    for i in range(t0, t1):
+        for k in range(p.row_ptr[i], p.row_ptr[i + 1]):
+            j = p.col[k]
+            if t0 <= j < t1:
+                ci.append(j - t0)
+                va.append(p.val[k])
+        rp.append(len(ci))
+    return np.array(rp, np.int32), np.array(ci, np.int32), np.array(va)
+
+
+@pytest.mark.parametrize("tile", [64, 100, 512])
+def test_tiled_aggregation_is_the_sequential_one_per_tile(tile):
+    p = P.lognormal3d((10, 9, 8), seed=2)
+    prm = _params(3, agg_tile=tile)
+    agg, nc = O.aggregate(p.row_ptr, p.col, p.val, prm)
+    # tile by tile: the sequential aggregation of the induced submatrix,
+    # numbered after the aggregates of the earlier tiles
+    off = 0
+    for t0 in range(0, p.n, tile):
+        t1 = min(p.n, t0 + tile)
+        a, k = O.aggregate(*_induced(p, t0, t1), _params(3))
+        want = np.where(a >= 0, a + off, -1)
+        assert np.array_equal(agg[t0:t1], want)
+        off += k
+    assert off == nc
+    # no aggregate crosses a tile boundary
+    for J in range(nc):
+        rows = np.flatnonzero(agg == J)
+        assert rows.min() // tile == rows.max() // tile
+
+
+def test_tiled_aggregation_with_one_tile_is_the_sequential_one():
+    p = P.lognormal3d((9, 9, 9), seed=1)
+    a0, n0 = O.aggregate(p.row_ptr, p.col, p.val, _params(3))
+    a1, n1 = O.aggregate(p.row_ptr, p.col, p.val, _params(3, agg_tile=p.n))
+    assert n0 == n1 and np.array_equal(a0, a1)
+
+
+def test_tiled_hierarchy_converges_like_the_sequential_one():
+    p = P.lognormal3d((20, 20, 20), seed=0)
+    its = []
+    for tile in (0, 1024):
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=200, agg_tile=tile))
+        x, it, rel, trel = H.pcg(p.b, tol=1e-8)
+        assert it > 0 and trel <= 1.01e-8
+        its.append(it)
+    assert its[1] <= 1.3 * its[0] + 1
