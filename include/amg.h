@@ -88,6 +88,15 @@ typedef struct {
                                  drains and reads only setup-time data until the
                                  predecessor has finished); 0: plain stream order.
                                  Results are identical either way. */
+    int32_t aggregation_tile; /* 0 (default): Algorithm 1 over the whole level on one host
+                                 thread.  > 0: decoupled aggregation (Alg. 4): the rows of a
+                                 level split into consecutive tiles of this many rows, each
+                                 aggregated by Algorithm 1 on its own induced submatrix
+                                 (edges leaving the tile dropped), aggregates numbered tile
+                                 by tile.  A different hierarchy, built in parallel. */
+    int32_t aggregation_device; /* with aggregation_tile > 0: 1 = the tiles run on the GPU
+                                 (one thread per tile), 0 = on the host threads.  Same
+                                 result either way. */
 } amg_params;
 
 typedef struct {
@@ -114,7 +123,8 @@ typedef struct {
     int32_t num_levels;
     int32_t coarsest_n;
     double operator_complexity;   /* sum_l nnz_l / nnz_0 */
-    double host_setup_ms;         /* strength, aggregation, colouring (host, all levels) */
+    double host_setup_ms;         /* strength, aggregation, colouring, all levels (the
+                                     aggregation on the device when aggregation_device = 1) */
     double gpu_galerkin_ms;       /* Galerkin products (device, all levels) */
     double gpu_other_ms;          /* reordering, coarsest factorisation, FP32 copies */
     double total_setup_ms;        /* wall time of amg_setup */
@@ -122,6 +132,8 @@ typedef struct {
     double vcycle_bytes_fp32;
     double pcg_iter_bytes_fp64;   /* modelled DRAM bytes per CG iteration incl. V-cycle */
     double pcg_iter_bytes_fp32;
+    double aggregation_ms;        /* strength and aggregation alone, all levels (part of
+                                     host_setup_ms) */
 } amg_summary;
 
 /* Per-kernel-class record of the profiler (amg_profile_*). */
@@ -226,13 +238,17 @@ int amg_hierarchy_info(const amg_ctx *c, amg_summary *summary, amg_level_info *l
 int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col,
                      double *val, int32_t *agg, int32_t *colour);
 
-/* Host setup of one level, exactly as amg_setup runs it (Sec. 2.1): strength
+/* Aggregation of one level, exactly as amg_setup runs it (Sec. 2.1): strength
  * of connection (Eq. symmetric_strong1/2) and Algorithm 1 with Algorithms 2
  * and 3, the singleton merge and the isolated-vertex phase, on the matrix
- * graph of A.  A must be a host matrix (on_device = 0).  agg: host int32 [n],
- * receives the coarse index of every row in completion order (-1 for rows
- * without a non-zero off-diagonal); *n_coarse receives the number of
- * aggregates.  Needs no GPU.  Errors: AMG_EINVAL (bad CSR or parameters). */
+ * graph of A -- or, with p->aggregation_tile > 0, on each tile's induced
+ * submatrix (Alg. 4).  A must be a host matrix (on_device = 0).  agg: host
+ * int32 [n], receives the coarse index of every row in completion order (-1
+ * for rows left out: no non-zero off-diagonal inside the graph aggregated);
+ * *n_coarse receives the number of aggregates.  Runs on the host and needs no
+ * GPU, except with aggregation_tile > 0 and aggregation_device = 1, where the
+ * tiles run on the GPU on p->cuda_stream (the map is the same).  Errors:
+ * AMG_EINVAL (bad CSR or parameters), AMG_ECUDA / AMG_ENOMEM (device path). */
 int amg_aggregate(const amg_csr *A, const amg_params *p, int32_t *agg, int32_t *n_coarse);
 
 /* Multicolour ordering of the smoother: greedy colouring of the matrix graph

@@ -45,7 +45,8 @@ class amg_params(ctypes.Structure):
                 ("s_min", _c_i32), ("s_max", _c_i32), ("d_max", _c_i32),
                 ("coarsen_target", _c_i32), ("max_levels", _c_i32), ("dense_cap", _c_i32),
                 ("min_coarsen_rate", _c_dbl), ("precision", _c_i32), ("flexible_cg", _c_i32),
-                ("cuda_stream", _c_vp), ("launch_overlap", _c_i32)]
+                ("cuda_stream", _c_vp), ("launch_overlap", _c_i32),
+                ("aggregation_tile", _c_i32), ("aggregation_device", _c_i32)]
 
 
 class amg_solve_info(ctypes.Structure):
@@ -64,7 +65,8 @@ class amg_summary(ctypes.Structure):
                 ("operator_complexity", _c_dbl), ("host_setup_ms", _c_dbl),
                 ("gpu_galerkin_ms", _c_dbl), ("gpu_other_ms", _c_dbl), ("total_setup_ms", _c_dbl),
                 ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
-                ("pcg_iter_bytes_fp64", _c_dbl), ("pcg_iter_bytes_fp32", _c_dbl)]
+                ("pcg_iter_bytes_fp64", _c_dbl), ("pcg_iter_bytes_fp32", _c_dbl),
+                ("aggregation_ms", _c_dbl)]
 
 
 class amg_kernel_stat(ctypes.Structure):

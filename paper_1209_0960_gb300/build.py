@@ -20,7 +20,8 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["kernels.cu", "setup_device.cu", "solver.cu", "noalloc.cu", "server.cu"]
+CU_SOURCES = ["kernels.cu", "setup_device.cu", "solver.cu", "noalloc.cu", "server.cu",
+              "aggregate_device.cu"]
 CPP_SOURCES = ["host_setup.cpp"]
 HEADERS = ["device.h", "host_setup.h"]
 

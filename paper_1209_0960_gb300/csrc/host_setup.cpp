@@ -40,6 +40,8 @@
 #include <cmath>
 #include <functional>
 #include <queue>
+#include <atomic>
+#include <thread>
 
 namespace amg {
 
@@ -489,6 +491,50 @@ AggResult aggregate(const HostCsr& A, const amg_params& p) {
     compute_strength(A, p, S);
     Aggregation G(A, S, p);
     return G.run();
+}
+
+AggResult aggregate_tiled(const HostCsr& A, const amg_params& p, int32_t tile, int threads) {
+    const int32_t n = A.n;
+    const int32_t ntiles = (n + tile - 1) / tile;
+    std::vector<AggResult> parts(ntiles);
+    auto work = [&](int32_t t) {
+        const int32_t t0 = t * tile, t1 = std::min(n, t0 + tile);
+        HostCsr sub;
+        sub.n = t1 - t0;
+        sub.rp.assign(sub.n + 1, 0);
+        for (int32_t i = t0; i < t1; ++i) {
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                const int32_t j = A.ci[k];
+                if (j < t0 || j >= t1) continue;
+                sub.ci.push_back(j - t0);
+                sub.va.push_back(A.va[k]);
+            }
+            sub.rp[i - t0 + 1] = (int32_t)sub.ci.size();
+        }
+        parts[t] = aggregate(sub, p);
+    };
+    std::atomic<int32_t> next{0};
+    auto worker = [&] {
+        for (int32_t t = next++; t < ntiles; t = next++) work(t);
+    };
+    const int nth = std::max(1, std::min<int>(threads, ntiles));
+    std::vector<std::thread> pool;
+    for (int i = 1; i < nth; ++i) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    AggResult R;
+    R.agg.assign(n, -1);
+    for (int32_t t = 0; t < ntiles; ++t) {
+        const AggResult& P = parts[t];
+        const int32_t t0 = t * tile;
+        for (size_t i = 0; i < P.agg.size(); ++i)
+            R.agg[t0 + i] = P.agg[i] >= 0 ? R.nc + P.agg[i] : -1;
+        R.nc += P.nc;
+        R.max_size = std::max(R.max_size, P.max_size);
+        R.n_isolated += P.n_isolated;
+        R.n_dirichlet += P.n_dirichlet;
+    }
+    return R;
 }
 
 int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour) {

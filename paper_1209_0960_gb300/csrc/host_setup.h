@@ -33,6 +33,12 @@ bool validate_csr(const HostCsr& A, std::string& err);
 // phase) on the graph of A under the parameters p.
 AggResult aggregate(const HostCsr& A, const amg_params& p);
 
+// Decoupled aggregation (Alg. 4): the rows split into consecutive tiles of
+// `tile` rows, each aggregated on its own induced submatrix by `aggregate`;
+// aggregates are numbered tile by tile.  Tiles run on up to `threads` host
+// threads; the result does not depend on the thread count.
+AggResult aggregate_tiled(const HostCsr& A, const amg_params& p, int32_t tile, int threads);
+
 // Greedy colouring in ascending row order; returns the number of colours.
 int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour);
 

@@ -12,6 +12,7 @@
 #include <memory>
 #include <mutex>
 #include <numeric>
+#include <thread>
 #include <type_traits>
 
 #include "device.h"
@@ -41,6 +42,20 @@ void check_params(const amg_params& p) {
     if (!(p.min_coarsen_rate >= 1.0)) throw Error{AMG_EINVAL, "min_coarsen_rate must be >= 1"};
     if (p.precision != AMG_FP64 && p.precision != AMG_FP32_IN_FP64)
         throw Error{AMG_EINVAL, "precision must be AMG_FP64 or AMG_FP32_IN_FP64"};
+    if (p.launch_overlap != 0 && p.launch_overlap != 1)
+        throw Error{AMG_EINVAL, "launch_overlap must be 0 or 1"};
+    if (p.aggregation_tile < 0) throw Error{AMG_EINVAL, "aggregation_tile must be >= 0"};
+    if (p.aggregation_device != 0 && p.aggregation_device != 1)
+        throw Error{AMG_EINVAL, "aggregation_device must be 0 or 1"};
+}
+
+// aggregation of one level under the parameters (Algorithm 1, or Alg. 4 in
+// tiles on host threads or on the device)
+AggResult aggregate_level(const HostCsr& A, const DevCsr* Ad, const amg_params& p, cudaStream_t s) {
+    if (p.aggregation_tile <= 0) return aggregate(A, p);
+    if (p.aggregation_device && Ad) return aggregate_tiles_device(*Ad, p, s);
+    const unsigned hw = std::thread::hardware_concurrency();
+    return aggregate_tiled(A, p, p.aggregation_tile, (int)std::max(1u, std::min(hw, 64u)));
 }
 
 template <typename T>
@@ -822,13 +837,14 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     AMG_CUDA_TRY(cudaEventCreate(&ev.a));
     AMG_CUDA_TRY(cudaEventCreate(&ev.b));
     cudaEvent_t e0 = ev.a, e1 = ev.b;
-    double host_ms = 0.0, galerkin_ms = 0.0;
+    double host_ms = 0.0, galerkin_ms = 0.0, agg_ms = 0.0;
     while (true) {
         const int l = (int)c->hl.size() - 1;
         HostLevel& cur = c->hl[l];
         if (cur.A.n <= prm->coarsen_target || l >= prm->max_levels - 1) break;
         double t0 = now_ms();
-        AggResult R = aggregate(cur.A, *prm);
+        AggResult R = aggregate_level(cur.A, &dA[l], *prm, s);
+        agg_ms += now_ms() - t0;
         host_ms += now_ms() - t0;
         if (R.nc == 0 || (double)cur.A.n / (double)R.nc < prm->min_coarsen_rate) break;
         t0 = now_ms();
@@ -967,6 +983,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
     fill_info(c.get());
     c->summary.host_setup_ms = host_ms;
+    c->summary.aggregation_ms = agg_ms;
     c->summary.gpu_galerkin_ms = galerkin_ms;
     c->summary.gpu_other_ms = now_ms() - t_dev0;
     c->summary.total_setup_ms = now_ms() - t_start;
@@ -1001,6 +1018,8 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->flexible_cg = -1;
     p->cuda_stream = nullptr;
     p->launch_overlap = 1;
+    p->aggregation_tile = 0;
+    p->aggregation_device = 0;
     return AMG_OK;
 }
 
@@ -1165,7 +1184,23 @@ int amg_aggregate(const amg_csr* A, const amg_params* p, int32_t* agg, int32_t* 
         if (!p || !agg || !n_coarse) throw Error{AMG_EINVAL, "null argument"};
         check_params(*p);
         HostCsr H = host_copy(A);
-        AggResult R = aggregate(H, *p);
+        AggResult R;
+        if (p->aggregation_tile > 0 && p->aggregation_device) {
+            cudaStream_t s = static_cast<cudaStream_t>(p->cuda_stream);
+            DevArena mem(s);
+            DevCsr D;
+            D.n = H.n;
+            D.nnz = H.nnz();
+            D.rp = mem.alloc<int32_t>(H.n + 1);
+            D.ci = mem.alloc<int32_t>(H.nnz());
+            D.va = mem.alloc<double>(H.nnz());
+            upload(D.rp, H.rp, s);
+            upload(D.ci, H.ci, s);
+            upload(D.va, H.va, s);
+            R = aggregate_level(H, &D, *p, s);
+        } else {
+            R = aggregate_level(H, nullptr, *p, nullptr);
+        }
         std::memcpy(agg, R.agg.data(), sizeof(int32_t) * H.n);
         *n_coarse = R.nc;
     });

@@ -140,3 +140,51 @@ def test_library_aggregation_matches_oracle_with_isolated_vertices(seed):
     agg1, n1 = amg.amg_aggregate(rp, ci, va, prm)
     agg2, n2 = O.aggregate(rp, ci, va, _oracle_params(prm))
     assert n1 == n2 and np.array_equal(agg1, agg2)
+
+
+_TILED = {
+    "lognormal_tile64": (lambda: P.lognormal3d((14, 13, 12), seed=6), 64),
+    "lognormal_tile_ragged": (lambda: P.lognormal3d((14, 13, 12), seed=6), 331),
+    "layered_tile_plane": (lambda: P.layered3d((16, 16, 10), seed=1), 256),
+    "laplace2d_tile1": (lambda: P.laplace2d_random_rhs(12), 1),
+    "laplace2d_tile_gt_n": (lambda: P.laplace2d_random_rhs(20), 1000),
+    "hub_graph": (lambda: P.hub_graph2d(40), 97),
+}
+
+
+@pytest.mark.parametrize("case", list(_TILED))
+def test_library_tiled_aggregation_matches_oracle(case):
+    maker, tile = _TILED[case]
+    p = maker()
+    prm = amg.amg_params_default(p.dim)
+    prm.aggregation_tile = tile
+    agg1, n1 = amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
+    agg2, n2 = O.aggregate(p.row_ptr, p.col, p.val, dict(_oracle_params(prm), agg_tile=tile))
+    assert n1 == n2 and np.array_equal(agg1, agg2)
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_library_tiled_aggregation_with_isolated_vertices(seed):
+    rng = np.random.default_rng(10 + seed)
+    K = np.exp(rng.normal(0.0, 4.0, size=(12, 11, 10)))
+    rp, ci, va, b = P.assemble_fv(K, bc=[(1.0, 0.0), (None, None), (None, None)])
+    prm = amg.amg_params_default(3)
+    prm.beta = 0.02
+    prm.aggregation_tile = 150
+    agg1, n1 = amg.amg_aggregate(rp, ci, va, prm)
+    agg2, n2 = O.aggregate(rp, ci, va, dict(_oracle_params(prm), agg_tile=150))
+    assert n1 == n2 and np.array_equal(agg1, agg2)
+
+
+def test_tiled_aggregation_parameters_are_checked():
+    p = P.laplace2d_random_rhs(8)
+    prm = amg.amg_params_default(2)
+    prm.aggregation_tile = -1
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
+    assert e.value.code == amg.AMG_EINVAL
+    prm.aggregation_tile = 16
+    prm.aggregation_device = 2
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
+    assert e.value.code == amg.AMG_EINVAL
