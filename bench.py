@@ -65,7 +65,15 @@ def parse_args():
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--setup-threads", type=int, default=0,
                     help="server setup threads (0: host cores - 3)")
-    return ap.parse_args()
+    ap.add_argument("--aggregation-tile", type=int, default=-1, metavar="T",
+                    help="decoupled aggregation (Alg. 4) in tiles of T consecutive rows "
+                         "(0: Algorithm 1 over whole levels; default 0, and 4096 with --serving)")
+    ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
+                    help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
+    args = ap.parse_args()
+    if args.aggregation_tile < 0:
+        args.aggregation_tile = 4096 if args.serving > 0 else 0
+    return args
 
 
 # ---------------------------------------------------------------------------
@@ -283,7 +291,8 @@ def run_ours(args, dist: Dist):
     p = make_problem(args.grid)
     t0 = time.perf_counter()
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
-                     launch_overlap=args.launch_overlap)
+                     launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
+                     aggregation_device=args.aggregation_device)
     setup_wall = time.perf_counter() - t0
     summary, levels = solver.info()
     b = torch.from_numpy(p.b).cuda()
@@ -423,7 +432,10 @@ def run_ours(args, dist: Dist):
                    "fp32": vcycle_gbs(prof32, g32, summary["vcycle_bytes_fp32"], 40.0 * p.n + 40.0 * p.n),
                    "model_bytes_fp64": summary["vcycle_bytes_fp64"],
                    "model_bytes_fp32": summary["vcycle_bytes_fp32"]},
-        "setup": {"host_ms": summary["host_setup_ms"], "gpu_galerkin_ms": summary["gpu_galerkin_ms"],
+        "setup": {"host_ms": summary["host_setup_ms"], "aggregation_ms": summary["aggregation_ms"],
+                  "aggregation_tile": args.aggregation_tile,
+                  "aggregation_device": args.aggregation_device,
+                  "gpu_galerkin_ms": summary["gpu_galerkin_ms"],
                   "gpu_other_ms": summary["gpu_other_ms"], "total_ms": summary["total_setup_ms"],
                   "levels": summary["num_levels"], "coarsest_n": summary["coarsest_n"],
                   "operator_complexity": summary["operator_complexity"],
@@ -484,7 +496,9 @@ def run_serving(args):
     from paper_1209_0960_gb300 import amg
     torch.cuda.set_device(0)
     threads = args.setup_threads or max(1, (os.cpu_count() or 4) - 3)
-    srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads)
+    srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads,
+                     aggregation_tile=args.aggregation_tile,
+                     aggregation_device=args.aggregation_device)
 
     def drain(tickets, results):
         while len(results) < len(tickets):
@@ -541,6 +555,7 @@ def run_serving(args):
         "median_ms": {k: float(np.median([r[3][k] for r in res2.values()]))
                       for k in ("queue_ms", "setup_ms", "solve_ms")},
         "peak_in_flight": stats["peak_running"], "slots": args.slots, "setup_threads": threads,
+        "aggregation_tile": args.aggregation_tile, "aggregation_device": args.aggregation_device,
         "unknowns": {"min": int(min(sizes)), "median": int(np.median(sizes)), "max": int(max(sizes))},
         "dtype": "f32 V-cycle in f64 CG", "data": "synthetic",
         "config": {"workload": "serving stream: independent 3D 7-point FV solves, box sides "
