@@ -68,6 +68,9 @@ def parse_args():
     ap.add_argument("--aggregation-tile", type=int, default=-1, metavar="T",
                     help="decoupled aggregation (Alg. 4) in tiles of T consecutive rows "
                          "(0: Algorithm 1 over whole levels; default 0, and 4096 with --serving)")
+    ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
+                    help="time the launch shapes of every level at setup and keep the fastest "
+                         "(0: the fixed rules)")
     ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
                     help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
     args = ap.parse_args()
@@ -292,7 +295,7 @@ def run_ours(args, dist: Dist):
     t0 = time.perf_counter()
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
-                     aggregation_device=args.aggregation_device)
+                     aggregation_device=args.aggregation_device, autotune=args.autotune)
     setup_wall = time.perf_counter() - t0
     summary, levels = solver.info()
     b = torch.from_numpy(p.b).cuda()
@@ -439,7 +442,9 @@ def run_ours(args, dist: Dist):
                   "gpu_other_ms": summary["gpu_other_ms"], "total_ms": summary["total_setup_ms"],
                   "levels": summary["num_levels"], "coarsest_n": summary["coarsest_n"],
                   "operator_complexity": summary["operator_complexity"],
-                  "level_n": [l["n"] for l in levels]},
+                  "level_n": [l["n"] for l in levels],
+                  "autotune": args.autotune, "autotune_ms": summary["autotune_ms"],
+                  "lanes_per_row": [l["lanes_per_row"] for l in levels[:-1]]},
         "roofline": roofline,
         "roofline_level0": {k: kernel_roofline(k) for k in
                             ("gs_level0", "first_level0", "residual_level0", "prolong",
@@ -498,7 +503,7 @@ def run_serving(args):
     threads = args.setup_threads or max(1, (os.cpu_count() or 4) - 3)
     srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads,
                      aggregation_tile=args.aggregation_tile,
-                     aggregation_device=args.aggregation_device)
+                     aggregation_device=args.aggregation_device, autotune=args.autotune)
 
     def drain(tickets, results):
         while len(results) < len(tickets):
@@ -556,6 +561,7 @@ def run_serving(args):
                       for k in ("queue_ms", "setup_ms", "solve_ms")},
         "peak_in_flight": stats["peak_running"], "slots": args.slots, "setup_threads": threads,
         "aggregation_tile": args.aggregation_tile, "aggregation_device": args.aggregation_device,
+        "autotune": args.autotune,
         "unknowns": {"min": int(min(sizes)), "median": int(np.median(sizes)), "max": int(max(sizes))},
         "dtype": "f32 V-cycle in f64 CG", "data": "synthetic",
         "config": {"workload": "serving stream: independent 3D 7-point FV solves, box sides "

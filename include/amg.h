@@ -95,8 +95,17 @@ typedef struct {
                                  (edges leaving the tile dropped), aggregates numbered tile
                                  by tile.  A different hierarchy, built in parallel. */
     int32_t aggregation_device; /* with aggregation_tile > 0: 1 = the tiles run on the GPU
-                                 (one thread per tile), 0 = on the host threads.  Same
+                                 (one warp per tile), 0 = on the host threads.  Same
                                  result either way. */
+    int32_t autotune;         /* 0 (default): launch shapes of the smoother and residual
+                                 kernels from fixed rules on the level's row lengths.
+                                 1: amg_setup times each candidate shape per level (the
+                                 V-cycle from that level, replayed as a CUDA graph in the
+                                 context's precision) and keeps the fastest; choices are
+                                 cached per process by level signature (precision, size
+                                 class, slice width, mean row length, colours), so later
+                                 setups of similar levels reuse them.  Shapes change the
+                                 order of floating-point sums only. */
 } amg_params;
 
 typedef struct {
@@ -117,6 +126,9 @@ typedef struct {
     int32_t n_dirichlet;      /* rows without a non-zero off-diagonal */
     double vcycle_bytes_fp64; /* modelled DRAM bytes of this level per FP64 V-cycle */
     double vcycle_bytes_fp32; /* same for the FP32 V-cycle */
+    int32_t lanes_per_row;    /* launch shape of the level's smoother and residual kernels:
+                                 0 = one row per thread with the matrix slices staged in
+                                 shared memory, else 1, 2, 4 or 8 lanes per row */
 } amg_level_info;
 
 typedef struct {
@@ -134,6 +146,8 @@ typedef struct {
     double pcg_iter_bytes_fp32;
     double aggregation_ms;        /* strength and aggregation alone, all levels (part of
                                      host_setup_ms) */
+    double autotune_ms;           /* launch-shape tuning (part of gpu_other_ms; 0 when
+                                     autotune = 0 or every level came from the cache) */
 } amg_summary;
 
 /* Per-kernel-class record of the profiler (amg_profile_*). */
@@ -237,6 +251,15 @@ int amg_hierarchy_info(const amg_ctx *c, amg_summary *summary, amg_level_info *l
  * coarsest level). */
 int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col,
                      double *val, int32_t *agg, int32_t *colour);
+
+/* Launch shape of level l's smoother and residual kernels (0 <= l < number of
+ * levels - 1; the coarsest level is the dense solve).  lanes_per_row: 0 = one
+ * row per thread with the slices staged in shared memory (levels whose longest
+ * row has at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row.  Results
+ * differ only in the order of floating-point sums.  The CUDA graphs of the
+ * context are rebuilt on the next solve.  Errors: AMG_EINVAL (l or
+ * lanes_per_row out of range, 0 on a level with longer rows). */
+int amg_set_level_shape(amg_ctx *c, int32_t l, int32_t lanes_per_row);
 
 /* Aggregation of one level, exactly as amg_setup runs it (Sec. 2.1): strength
  * of connection (Eq. symmetric_strong1/2) and Algorithm 1 with Algorithms 2

@@ -46,7 +46,8 @@ class amg_params(ctypes.Structure):
                 ("coarsen_target", _c_i32), ("max_levels", _c_i32), ("dense_cap", _c_i32),
                 ("min_coarsen_rate", _c_dbl), ("precision", _c_i32), ("flexible_cg", _c_i32),
                 ("cuda_stream", _c_vp), ("launch_overlap", _c_i32),
-                ("aggregation_tile", _c_i32), ("aggregation_device", _c_i32)]
+                ("aggregation_tile", _c_i32), ("aggregation_device", _c_i32),
+                ("autotune", _c_i32)]
 
 
 class amg_solve_info(ctypes.Structure):
@@ -57,7 +58,8 @@ class amg_solve_info(ctypes.Structure):
 class amg_level_info(ctypes.Structure):
     _fields_ = [("n", _c_i32), ("nnz", _c_i32), ("n_coarse", _c_i32), ("ncolours", _c_i32),
                 ("max_agg_size", _c_i32), ("n_isolated", _c_i32), ("n_dirichlet", _c_i32),
-                ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl)]
+                ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
+                ("lanes_per_row", _c_i32)]
 
 
 class amg_summary(ctypes.Structure):
@@ -66,7 +68,7 @@ class amg_summary(ctypes.Structure):
                 ("gpu_galerkin_ms", _c_dbl), ("gpu_other_ms", _c_dbl), ("total_setup_ms", _c_dbl),
                 ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
                 ("pcg_iter_bytes_fp64", _c_dbl), ("pcg_iter_bytes_fp32", _c_dbl),
-                ("aggregation_ms", _c_dbl)]
+                ("aggregation_ms", _c_dbl), ("autotune_ms", _c_dbl)]
 
 
 class amg_kernel_stat(ctypes.Structure):
@@ -114,6 +116,7 @@ _SIGNATURES = {
     "amg_residual_norm_noalloc": ([ctypes.POINTER(amg_csr), _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_hierarchy_info": ([_c_vp, ctypes.POINTER(amg_summary), ctypes.POINTER(amg_level_info), _c_i32], ctypes.c_int),
     "amg_export_level": ([_c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
+    "amg_set_level_shape": ([_c_vp, _c_i32, _c_i32], ctypes.c_int),
     "amg_aggregate": ([ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
     "amg_colour": ([ctypes.POINTER(amg_csr), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
     "amg_profile_enable": ([_c_vp, _c_i32], ctypes.c_int),
@@ -249,6 +252,10 @@ def amg_hierarchy_info(ctx: int):
     levels = (amg_level_info * nl)()
     _check(lib().amg_hierarchy_info(ctx, ctypes.byref(s), levels, nl), "amg_hierarchy_info")
     return struct_dict(s), [struct_dict(l) for l in levels]
+
+
+def amg_set_level_shape(ctx: int, l: int, lanes_per_row: int) -> None:
+    _check(lib().amg_set_level_shape(ctx, l, lanes_per_row), "amg_set_level_shape")
 
 
 def amg_export_level(ctx: int, l: int) -> dict:
@@ -392,6 +399,9 @@ class AMG:
 
     def level(self, l: int) -> dict:
         return amg_export_level(self.ctx, l)
+
+    def set_level_shape(self, l: int, lanes_per_row: int) -> None:
+        amg_set_level_shape(self.ctx, l, lanes_per_row)
 
 
 # ---------------------------------------------------------------------------

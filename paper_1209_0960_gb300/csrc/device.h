@@ -129,6 +129,8 @@ struct DevLevel {
     int32_t lpr_wide = 0;             // lanes per row of launches over >= wide_rows rows
     int32_t wide_rows = 0x7fffffff;
     bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 0)
+    bool fused_ok = false;            // the level allows the fused kernel (two colours,
+                                      // aggregates of at most 32 rows of colour 1)
     int32_t* err = nullptr;           // device status word for kernel-side errors (timeouts)
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
@@ -387,6 +389,10 @@ struct amg_ctx {
     int precision = AMG_FP64;
     int flexible = 0;
     bool fp32_ready = false;
+    // launch shape (DevLevel::lpr) of every level but the coarsest, per
+    // precision, and whether the autotuner has chosen them
+    std::vector<int32_t> shapes[2];
+    bool tuned[2] = {false, false};
     amg_summary summary{};
     std::vector<amg_level_info> linfo;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -13,6 +13,7 @@
 #include <mutex>
 #include <numeric>
 #include <thread>
+#include <tuple>
 #include <type_traits>
 
 #include "device.h"
@@ -47,6 +48,7 @@ void check_params(const amg_params& p) {
     if (p.aggregation_tile < 0) throw Error{AMG_EINVAL, "aggregation_tile must be >= 0"};
     if (p.aggregation_device != 0 && p.aggregation_device != 1)
         throw Error{AMG_EINVAL, "aggregation_device must be 0 or 1"};
+    if (p.autotune != 0 && p.autotune != 1) throw Error{AMG_EINVAL, "autotune must be 0 or 1"};
 }
 
 // aggregation of one level under the parameters (Algorithm 1, or Alg. 4 in
@@ -159,6 +161,7 @@ void fill_info(amg_ctx* c) {
         li.n_dirichlet = last ? 0 : h.agg.n_dirichlet;
         li.vcycle_bytes_fp64 = level_vcycle_bytes(d, last, 8);
         li.vcycle_bytes_fp32 = level_vcycle_bytes(d, last, 4);
+        li.lanes_per_row = last ? 0 : d.lpr;
         b64 += li.vcycle_bytes_fp64;
         b32 += li.vcycle_bytes_fp32;
         if (l == 0) nnz0 = li.nnz;
@@ -409,6 +412,155 @@ cudaGraphExec_t capture_graph(amg_ctx* c, F&& f) {
     cudaGraphDestroy(g);
     AMG_CUDA_TRY(err);
     return e;
+}
+
+// ---------------------------------------------------------------------------
+// launch shapes: fixed rules at setup, optional autotuning
+// ---------------------------------------------------------------------------
+
+void drop_graphs(amg_ctx* c) {
+    for (int a = 0; a < 2; ++a) {
+        for (int b = 0; b < 2; ++b) {
+            if (c->graph_a[a][b]) cudaGraphExecDestroy(c->graph_a[a][b]);
+            if (c->graph_b[a][b]) cudaGraphExecDestroy(c->graph_b[a][b]);
+            c->graph_a[a][b] = c->graph_b[a][b] = nullptr;
+        }
+        for (cudaGraphExec_t& g : c->graph_from[a]) {
+            if (g) cudaGraphExecDestroy(g);
+            g = nullptr;
+        }
+    }
+}
+
+constexpr int kStaged = 0;   // DevLevel::lpr of the staged one-row-per-thread kernels
+
+bool shape_allowed(const DevLevel& L, int lanes) {
+    if (lanes == kStaged) return L.width <= kFineMaxWidth;
+    return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8;
+}
+
+void set_shape(DevLevel& L, int lanes) {
+    L.lpr = lanes;
+    L.lpr_wide = lanes;
+    L.fused_restrict = lanes == kStaged && L.fused_ok;
+}
+
+// Level signature for the process-wide cache of tuned shapes: levels that
+// agree on it run the same kernels over similar slices.
+struct ShapeKey {
+    int precision, size_class, width, mean_x4, ncolours, fine;
+    bool operator<(const ShapeKey& o) const {
+        return std::tie(precision, size_class, width, mean_x4, ncolours, fine) <
+               std::tie(o.precision, o.size_class, o.width, o.mean_x4, o.ncolours, o.fine);
+    }
+};
+
+ShapeKey shape_key(const amg_ctx* c, int l) {
+    const DevLevel& L = c->dl[l];
+    // half-octave size classes
+    const int size_class = (int)std::floor(2.0 * std::log2(std::max(1, L.n)));
+    const int mean_x4 = (int)std::lround(4.0 * (double)L.nnz_off / std::max(1, L.n));
+    return {c->precision, size_class, L.width, mean_x4, L.ncolours, l == 0 ? 1 : 0};
+}
+
+std::mutex g_shape_mu;
+std::map<ShapeKey, int> g_shape_cache;
+
+// Device time of one replay of the V-cycle from level l (the whole
+// preconditioner for l = 0), as a CUDA graph: the minimum over three batches
+// sized to about 0.3 ms each.
+double time_vcycle_from(amg_ctx* c, int l) {
+    cudaStream_t s = c->stream;
+    cudaGraphExec_t g = capture_graph(c, [&] {
+        if (l == 0) precondition(c, c->r, c->z);
+        else if (c->precision == AMG_FP64) vcycle64(c, l, c->dl[l].b, c->dl[l].x);
+        else vcycle32(c, l, c->dl[l].b32, c->dl[l].x32);
+    });
+    struct GraphGuard {
+        cudaGraphExec_t g;
+        ~GraphGuard() { cudaGraphExecDestroy(g); }
+    } guard{g};
+    float ms = 0.f;
+    AMG_CUDA_TRY(cudaGraphLaunch(g, s));   // warm-up
+    AMG_CUDA_TRY(cudaEventRecord(c->ev0, s));
+    AMG_CUDA_TRY(cudaGraphLaunch(g, s));
+    AMG_CUDA_TRY(cudaEventRecord(c->ev1, s));
+    AMG_CUDA_TRY(cudaEventSynchronize(c->ev1));
+    AMG_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+    const int reps = std::max(1, std::min(64, (int)std::ceil(0.3 / std::max(1e-3, (double)ms))));
+    double best = 1e30;
+    for (int batch = 0; batch < 3; ++batch) {
+        AMG_CUDA_TRY(cudaEventRecord(c->ev0, s));
+        for (int r = 0; r < reps; ++r) AMG_CUDA_TRY(cudaGraphLaunch(g, s));
+        AMG_CUDA_TRY(cudaEventRecord(c->ev1, s));
+        AMG_CUDA_TRY(cudaEventSynchronize(c->ev1));
+        AMG_CUDA_TRY(cudaEventElapsedTime(&ms, c->ev0, c->ev1));
+        best = std::min(best, (double)ms / reps);
+    }
+    return best;
+}
+
+// Pick each level's shape by timing, coarse levels first, so that the
+// V-cycle below the level being tuned already runs its final shapes.  The
+// rule's shape is kept unless a candidate is more than 3 % faster, which keeps
+// the choice stable against timing noise.  Returns the milliseconds spent.
+double autotune_shapes(amg_ctx* c) {
+    const int nlev = (int)c->dl.size();
+    if (nlev < 2) return 0.0;
+    const double t0 = now_ms();
+    cudaStream_t s = c->stream;
+    bool timed = false;
+    auto zero_inputs = [&] {
+        // zero right-hand sides: the kernels do the same work for any values
+        AMG_CUDA_TRY(cudaMemsetAsync(c->r, 0, sizeof(double) * c->dl[0].n, s));
+        for (DevLevel& L : c->dl) {
+            AMG_CUDA_TRY(cudaMemsetAsync(L.b, 0, sizeof(double) * L.n, s));
+            if (L.b32) AMG_CUDA_TRY(cudaMemsetAsync(L.b32, 0, sizeof(float) * L.n, s));
+        }
+    };
+    for (int l = nlev - 2; l >= 0; --l) {
+        DevLevel& L = c->dl[l];
+        const ShapeKey key = shape_key(c, l);
+        {
+            std::lock_guard<std::mutex> lk(g_shape_mu);
+            auto it = g_shape_cache.find(key);
+            if (it != g_shape_cache.end() && shape_allowed(L, it->second)) {
+                set_shape(L, it->second);
+                continue;
+            }
+        }
+        if (!timed) {
+            zero_inputs();
+            timed = true;
+        }
+        const int rule = L.lpr;
+        double t_rule = 1e30, t_best = 1e30;
+        int best = rule;
+        for (int lanes : {kStaged, 1, 2, 4, 8}) {
+            if (!shape_allowed(L, lanes)) continue;
+            set_shape(L, lanes);
+            const double t = time_vcycle_from(c, l);
+            if (lanes == rule) t_rule = t;
+            if (t < t_best) {
+                t_best = t;
+                best = lanes;
+            }
+        }
+        if (t_rule <= 1.03 * t_best) best = rule;
+        set_shape(L, best);
+        std::lock_guard<std::mutex> lk(g_shape_mu);
+        g_shape_cache.emplace(key, best);
+    }
+    for (int l = 0; l + 1 < nlev; ++l) c->shapes[c->precision][l] = c->dl[l].lpr;
+    c->tuned[c->precision] = true;
+    drop_graphs(c);
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    return timed ? now_ms() - t0 : 0.0;
+}
+
+// Make the levels run the shapes of the context's precision.
+void apply_shapes(amg_ctx* c) {
+    for (int l = 0; l + 1 < (int)c->dl.size(); ++l) set_shape(c->dl[l], c->shapes[c->precision][l]);
 }
 
 // ---------------------------------------------------------------------------
@@ -923,7 +1075,8 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
             for (int32_t J = 0; J < nc; ++J) most = std::max(most, rptr[J + 1] - rptr[J]);
             // the fused kernel needs the rows of colour >= 1 to be one block
             // sorted by coarse index (two colours) and runs shorter than a warp
-            L.fused_restrict = L.lpr == 0 && L.ncolours == 2 && most <= 32;
+            L.fused_ok = L.ncolours == 2 && most <= 32;
+            L.fused_restrict = L.lpr == 0 && L.fused_ok;
         }
         L.agg = c->mem.alloc<int32_t>(L.n);
         L.rptr = c->mem.alloc<int32_t>(nc + 1);
@@ -981,7 +1134,13 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     c->flexible = prm->flexible_cg >= 0 ? prm->flexible_cg : (prm->precision == AMG_FP32_IN_FP64);
     c->precision = prm->precision;
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
+    for (int pr = 0; pr < 2; ++pr) {
+        c->shapes[pr].assign(nlev - 1, 0);
+        for (int l = 0; l + 1 < nlev; ++l) c->shapes[pr][l] = c->dl[l].lpr;
+    }
+    const double tune_ms = prm->autotune ? autotune_shapes(c.get()) : 0.0;
     fill_info(c.get());
+    c->summary.autotune_ms = tune_ms;
     c->summary.host_setup_ms = host_ms;
     c->summary.aggregation_ms = agg_ms;
     c->summary.gpu_galerkin_ms = galerkin_ms;
@@ -1020,6 +1179,7 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->launch_overlap = 1;
     p->aggregation_tile = 0;
     p->aggregation_device = 0;
+    p->autotune = 0;
     return AMG_OK;
 }
 
@@ -1033,13 +1193,18 @@ int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
         if (!c) throw Error{AMG_EINVAL, "null context"};
         if (precision != AMG_FP64 && precision != AMG_FP32_IN_FP64)
             throw Error{AMG_EINVAL, "precision must be AMG_FP64 or AMG_FP32_IN_FP64"};
-        if (precision == AMG_FP32_IN_FP64) {
-            enter(c);
-            ensure_fp32(c);
-            leave(c);
-        }
+        enter(c);
+        if (precision == AMG_FP32_IN_FP64) ensure_fp32(c);
         c->precision = precision;
         c->flexible = flexible_cg >= 0 ? flexible_cg : (precision == AMG_FP32_IN_FP64);
+        AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
+        if (c->p.autotune && !c->tuned[precision]) {
+            apply_shapes(c);
+            c->summary.autotune_ms += autotune_shapes(c);
+        }
+        apply_shapes(c);
+        for (int l = 0; l + 1 < (int)c->dl.size(); ++l) c->linfo[l].lanes_per_row = c->dl[l].lpr;
+        leave(c);
     });
 }
 
@@ -1177,6 +1342,24 @@ static HostCsr host_copy(const amg_csr* A) {
     std::string err;
     if (!validate_csr(H, err)) throw Error{AMG_EINVAL, err};
     return H;
+}
+
+int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row) {
+    return Guard::run([&] {
+        if (!c) throw Error{AMG_EINVAL, "null context"};
+        if (l < 0 || l >= (int32_t)c->dl.size() - 1)
+            throw Error{AMG_EINVAL, "level out of range (the coarsest level has no shape)"};
+        if (!shape_allowed(c->dl[l], lanes_per_row))
+            throw Error{AMG_EINVAL, "lanes_per_row must be 1, 2, 4 or 8, or 0 on a level whose "
+                                    "rows have at most 32 off-diagonals"};
+        enter(c);
+        AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
+        drop_graphs(c);
+        set_shape(c->dl[l], lanes_per_row);
+        c->shapes[c->precision][l] = lanes_per_row;
+        c->linfo[l].lanes_per_row = lanes_per_row;
+        leave(c);
+    });
 }
 
 int amg_aggregate(const amg_csr* A, const amg_params* p, int32_t* agg, int32_t* n_coarse) {

@@ -1,0 +1,122 @@
+"""Launch shapes of the smoother and residual kernels: every shape a level
+allows gives the oracle's V-cycle within the FP64 bar, and the autotuner's
+choices keep the parity bars and are reused from its cache."""
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1209_0960_gb300 import amg
+from paper_1209_0960_gb300 import problems as P
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def _oracle_params(prm, **kw):
+    d = dict(delta=prm.delta, beta=prm.beta, omega=prm.omega, s_min=prm.s_min,
+             s_max=prm.s_max, d_max=prm.d_max, coarsen_target=prm.coarsen_target,
+             max_levels=prm.max_levels, dense_cap=prm.dense_cap,
+             min_rate=prm.min_coarsen_rate)
+    d.update(kw)
+    return d
+
+
+CASES = {
+    "lognormal_3lev": (lambda: P.lognormal3d((28, 24, 20), seed=1), {"coarsen_target": 300}),
+    "laplace2d_64": (lambda: P.laplace2d_random_rhs(64), {"coarsen_target": 200}),
+    "hub_graph2d_48": (lambda: P.hub_graph2d(48), {"coarsen_target": 100}),
+}
+
+
+def _vcycle_err(solver, H, r):
+    z = solver.vcycle(torch.from_numpy(np.ascontiguousarray(r)).cuda())
+    torch.cuda.synchronize()
+    z_or = H.vcycle(r)
+    return np.abs(z.cpu().numpy() - z_or).max() / np.abs(z_or).max()
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_every_shape_matches_oracle(case):
+    maker, over = CASES[case]
+    p = maker()
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=p.dim, **over)
+    try:
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _oracle_params(solver.params))
+        _, levels = solver.info()
+        r = np.random.default_rng(7).standard_normal(p.n)
+        tried = 0
+        for l in range(len(levels) - 1):
+            rule = levels[l]["lanes_per_row"]
+            for lanes in (0, 1, 2, 4, 8):
+                try:
+                    solver.set_level_shape(l, lanes)
+                except amg.AmgError as e:
+                    assert lanes == 0 and e.code == amg.AMG_EINVAL
+                    continue
+                assert solver.info()[1][l]["lanes_per_row"] == lanes
+                assert _vcycle_err(solver, H, r) <= 1e-12, (l, lanes)
+                tried += 1
+            solver.set_level_shape(l, rule)
+        assert tried >= 4 * (len(levels) - 1)
+        # a mixed assignment through the solve (CUDA graphs rebuilt)
+        for l in range(len(levels) - 1):
+            solver.set_level_shape(l, (1, 2, 4, 8)[l % 4])
+        x, rc, info = solver.solve(torch.from_numpy(p.b).cuda(), tol=1e-10, maxit=300)
+        assert rc == amg.AMG_OK
+        xo, it_o, _, _ = H.pcg(p.b, tol=1e-10, maxit=300)
+        assert abs(info["iterations"] - it_o) <= 1
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+        # the float32 V-cycle under the same shapes
+        solver.set_precision(amg.AMG_FP32_IN_FP64)
+        x, rc, info = solver.solve(torch.from_numpy(p.b).cuda(), tol=1e-8, maxit=300)
+        assert rc == amg.AMG_OK and info["true_rel_residual"] <= 1.05e-8
+    finally:
+        solver.close()
+
+
+def test_shape_errors():
+    p = P.laplace2d_random_rhs(32)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=100)
+    try:
+        nlev = solver.info()[0]["num_levels"]
+        for l, lanes in ((-1, 4), (nlev - 1, 4), (0, 3), (0, 16)):
+            with pytest.raises(amg.AmgError) as e:
+                solver.set_level_shape(l, lanes)
+            assert e.value.code == amg.AMG_EINVAL
+    finally:
+        solver.close()
+
+
+@pytest.mark.parametrize("precision", [amg.AMG_FP64, amg.AMG_FP32_IN_FP64])
+def test_autotuned_shapes_keep_parity_and_are_cached(precision):
+    p = P.lognormal3d((40, 36, 32), seed=4)
+    a = amg.AMG(p.row_ptr, p.col, p.val, dim=3, precision=precision, autotune=1,
+                coarsen_target=300)
+    try:
+        sa, la = a.info()
+        shapes = [l["lanes_per_row"] for l in la[:-1]]
+        assert all(s in (0, 1, 2, 4, 8) for s in shapes)
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _oracle_params(a.params))
+        xo, it_o, _, _ = H.pcg(p.b, tol=1e-10, maxit=300)
+        if precision == amg.AMG_FP64:
+            r = np.random.default_rng(3).standard_normal(p.n)
+            assert _vcycle_err(a, H, r) <= 1e-12
+            x, rc, info = a.solve(torch.from_numpy(p.b).cuda(), tol=1e-10, maxit=300)
+            assert rc == amg.AMG_OK and abs(info["iterations"] - it_o) <= 1
+            assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+        else:
+            x, rc, info = a.solve(torch.from_numpy(p.b).cuda(), tol=1e-8, maxit=300)
+            assert rc == amg.AMG_OK and info["true_rel_residual"] <= 1.05e-8
+        # a second setup of the same matrix takes every shape from the cache
+        b = amg.AMG(p.row_ptr, p.col, p.val, dim=3, precision=precision, autotune=1,
+                    coarsen_target=300)
+        try:
+            sb, lb = b.info()
+            assert [l["lanes_per_row"] for l in lb[:-1]] == shapes
+            assert sb["autotune_ms"] == 0.0
+        finally:
+            b.close()
+    finally:
+        a.close()
