@@ -274,10 +274,14 @@ int amg_set_level_shape(amg_ctx *c, int32_t l, int32_t lanes_per_row);
  * AMG_EINVAL (bad CSR or parameters), AMG_ECUDA / AMG_ENOMEM (device path). */
 int amg_aggregate(const amg_csr *A, const amg_params *p, int32_t *agg, int32_t *n_coarse);
 
-/* Multicolour ordering of the smoother: greedy colouring of the matrix graph
- * of A (host matrix) in ascending row order, smallest colour not used by an
- * already coloured neighbour.  colour: host int32 [n]; *ncolours receives
- * the number of colours.  Needs no GPU.  Errors: AMG_EINVAL. */
+/* Multicolour ordering of the smoother (the GPU form of the Gauss-Seidel
+ * smoother of Sec. 3.2), as amg_setup forms it on every level: the greedy
+ * colouring of the matrix graph of A (host matrix) in ascending row order
+ * (smallest colour not used by an already coloured neighbour), replaced by the
+ * DSATUR colouring (next row: most distinct colours among its neighbours, then
+ * more neighbours, then the lower index) when that needs fewer colours.
+ * colour: host int32 [n]; *ncolours receives the number of colours.  Needs no
+ * GPU.  Errors: AMG_EINVAL. */
 int amg_colour(const amg_csr *A, int32_t *colour, int32_t *ncolours);
 
 /* Profiler.  enable == 1 clears the records and brackets every later kernel

@@ -24,6 +24,7 @@
 #include <map>
 #include <queue>
 #include <set>
+#include <tuple>
 #include <utility>
 #include <vector>
 
@@ -434,9 +435,15 @@ struct Aggregator {
 };
 
 // ---------------------------------------------------------------------------
-// Multicolour ordering for the Gauss-Seidel smoother: greedy, rows in
-// ascending order, smallest colour not used by an already coloured neighbour.
+// Multicolour ordering for the Gauss-Seidel smoother.  The paper smooths each
+// process's rows in their natural order (Sec. 3.2); the GPU needs rows that
+// can be updated at once, so both sides use the same colouring.  Two greedy
+// colourings are formed and the one with fewer colours is kept (ties: the
+// first), because every colour costs the GPU one dependent pass per sweep.
 // ---------------------------------------------------------------------------
+
+// Greedy in ascending row order: each row takes the smallest colour no
+// already coloured neighbour has (red-black on the structured grids).
 int greedy_colour(const Csr& A, std::vector<int>& colour) {
     colour.assign(A.n, -1);
     int nc = 0;
@@ -448,6 +455,51 @@ int greedy_colour(const Csr& A, std::vector<int>& colour) {
         while (used.count(c)) ++c;
         colour[i] = c;
         nc = std::max(nc, c + 1);
+    }
+    return nc;
+}
+
+// DSATUR (Brelaz, 1979): repeatedly colour the uncoloured row whose
+// neighbours already show the most distinct colours (its saturation); ties go
+// to the row with more neighbours, then to the lower index.  The row takes the
+// smallest colour none of its neighbours has.
+int dsatur_colour(const Csr& A, std::vector<int>& colour) {
+    const int n = A.n;
+    colour.assign(n, -1);
+    std::vector<std::set<int>> seen(n);   // colours among the coloured neighbours
+    std::vector<int> deg(n);
+    std::set<std::tuple<int, int, int>> order;   // (-saturation, -degree, row)
+    for (int i = 0; i < n; ++i) {
+        deg[i] = (int)A.neighbours(i).size();
+        order.insert(std::make_tuple(0, -deg[i], i));
+    }
+    int nc = 0;
+    while (!order.empty()) {
+        const int v = std::get<2>(*order.begin());
+        order.erase(order.begin());
+        int c = 0;
+        while (seen[v].count(c)) ++c;
+        colour[v] = c;
+        nc = std::max(nc, c + 1);
+        for (int j : A.neighbours(v)) {
+            if (colour[j] >= 0 || seen[j].count(c)) continue;
+            order.erase(std::make_tuple(-(int)seen[j].size(), -deg[j], j));
+            seen[j].insert(c);
+            order.insert(std::make_tuple(-(int)seen[j].size(), -deg[j], j));
+        }
+    }
+    return nc;
+}
+
+// The smoother's colouring: DSATUR when it needs fewer colours than the
+// ascending-order greedy, else the greedy one.
+int smoother_colour(const Csr& A, std::vector<int>& colour) {
+    const int nc = greedy_colour(A, colour);
+    std::vector<int> alt;
+    const int na = dsatur_colour(A, alt);
+    if (na < nc) {
+        colour.swap(alt);
+        return na;
     }
     return nc;
 }
@@ -742,14 +794,16 @@ int oracle_aggregate(int n, const int* rp, const int* ci, const double* va,
     return nc;
 }
 
-int oracle_colour(int n, const int* rp, const int* ci, int* colour) {
+// method: 0 = the smoother's colouring, 1 = ascending-order greedy, 2 = DSATUR
+int oracle_colour(int n, const int* rp, const int* ci, int* colour, int method) {
     Csr A;
     A.n = n;
     A.rp.assign(rp, rp + n + 1);
     A.ci.assign(ci, ci + rp[n]);
     A.va.assign(rp[n], 0.0);
     std::vector<int> c;
-    int nc = greedy_colour(A, c);
+    const int nc = method == 1 ? greedy_colour(A, c) : method == 2 ? dsatur_colour(A, c)
+                                                                    : smoother_colour(A, c);
     for (int i = 0; i < n; ++i) colour[i] = c[i];
     return nc;
 }
@@ -809,7 +863,7 @@ void* oracle_setup(int n, const int* rp, const int* ci, const double* va,
         cur.nc = nc;
         cur.isolated = iso;
         cur.dirichlet = dir;
-        cur.ncolours = greedy_colour(cur.A, cur.colour);
+        cur.ncolours = smoother_colour(cur.A, cur.colour);
         Level next;
         next.A = galerkin(cur.A, cur.agg, nc);
         H->levels.push_back(next);

@@ -66,7 +66,7 @@ def _load():
     lib.oracle_strength.argtypes = [I, P, P, P, P, P, P, P, P]
     lib.oracle_aggregate.argtypes = [I, P, P, P, P, P]
     lib.oracle_aggregate.restype = I
-    lib.oracle_colour.argtypes = [I, P, P, P]
+    lib.oracle_colour.argtypes = [I, P, P, P, I]
     lib.oracle_colour.restype = I
     lib.oracle_galerkin.argtypes = [I, P, P, P, P, I, P, P, P]
     lib.oracle_galerkin.restype = I
@@ -122,12 +122,17 @@ def aggregate(rp, ci, va, params: dict):
     return agg, int(nc)
 
 
-def colour(rp, ci):
+COLOUR_SMOOTHER, COLOUR_GREEDY, COLOUR_DSATUR = 0, 1, 2
+
+
+def colour(rp, ci, method: int = COLOUR_SMOOTHER):
+    """Colouring of the matrix graph: the smoother's (fewer colours of the
+    two below), ascending-order greedy, or DSATUR."""
     rp = np.ascontiguousarray(rp, dtype=np.int32)
     ci = np.ascontiguousarray(ci, dtype=np.int32)
     n = rp.shape[0] - 1
     c = np.zeros(n, dtype=np.int32)
-    nc = _load().oracle_colour(n, _ptr(rp), _ptr(ci), _ptr(c))
+    nc = _load().oracle_colour(n, _ptr(rp), _ptr(ci), _ptr(c), int(method))
     return c, int(nc)
 
 

@@ -559,4 +559,90 @@ int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour) {
     return nc;
 }
 
+
+
+namespace {
+
+// colours seen among the coloured neighbours of a row: a 64-bit mask for
+// colours below 64, a sorted list above (only rows of very high degree get
+// there)
+struct SeenColours {
+    uint64_t low = 0;
+    std::vector<int32_t> high;
+    bool has(int32_t c) const {
+        if (c < 64) return (low >> c) & 1u;
+        return std::binary_search(high.begin(), high.end(), c);
+    }
+    void add(int32_t c) {
+        if (c < 64) low |= uint64_t(1) << c;
+        else high.insert(std::lower_bound(high.begin(), high.end(), c), c);
+    }
+    int32_t smallest_free() const {
+        if (~low) return (int32_t)__builtin_ctzll(~low);
+        int32_t c = 64;
+        for (int32_t h : high) {
+            if (h != c) break;
+            ++c;
+        }
+        return c;
+    }
+};
+
+}  // namespace
+
+int32_t dsatur_colouring(const HostCsr& A, std::vector<int32_t>& colour) {
+    const int32_t n = A.n;
+    colour.assign(n, -1);
+    std::vector<int32_t> deg(n, 0), sat(n, 0);
+    for (int32_t i = 0; i < n; ++i)
+        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+            if (A.ci[k] != i) ++deg[i];
+    std::vector<SeenColours> seen(n);
+    // one max-heap per saturation value, keyed by (degree, -index), with lazy
+    // deletion: an entry is live while its row is uncoloured and still has
+    // that saturation
+    auto key = [&](int32_t i) { return ((uint64_t)(uint32_t)deg[i] << 32) | (uint32_t)(~(uint32_t)i); };
+    std::vector<std::priority_queue<uint64_t>> buckets(1);
+    for (int32_t i = 0; i < n; ++i) buckets[0].push(key(i));
+    int32_t top = 0, nc = 0;
+    for (int32_t done = 0; done < n; ++done) {
+        int32_t v = -1;
+        while (v < 0) {
+            auto& h = buckets[top];
+            if (h.empty()) {
+                --top;
+                continue;
+            }
+            const int32_t i = (int32_t)~(uint32_t)(h.top() & 0xffffffffu);
+            h.pop();
+            if (colour[i] < 0 && sat[i] == top) v = i;
+        }
+        const int32_t c = seen[v].smallest_free();
+        colour[v] = c;
+        nc = std::max(nc, c + 1);
+        for (int32_t k = A.rp[v]; k < A.rp[v + 1]; ++k) {
+            const int32_t j = A.ci[k];
+            if (j == v || colour[j] >= 0 || seen[j].has(c)) continue;
+            seen[j].add(c);
+            const int32_t s = ++sat[j];
+            if (s >= (int32_t)buckets.size()) buckets.resize(s + 1);
+            buckets[s].push(key(j));
+            top = std::max(top, s);
+        }
+    }
+    return nc;
+}
+
+int32_t smoother_colouring(const HostCsr& A, std::vector<int32_t>& colour) {
+    const int32_t nc = greedy_colouring(A, colour);
+    if (nc <= 2) return nc;   // DSATUR cannot use fewer colours than two here
+    std::vector<int32_t> alt;
+    const int32_t na = dsatur_colouring(A, alt);
+    if (na < nc) {
+        colour.swap(alt);
+        return na;
+    }
+    return nc;
+}
+
 }  // namespace amg

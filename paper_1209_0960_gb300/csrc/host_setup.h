@@ -42,4 +42,13 @@ AggResult aggregate_tiled(const HostCsr& A, const amg_params& p, int32_t tile, i
 // Greedy colouring in ascending row order; returns the number of colours.
 int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour);
 
+// DSATUR colouring (Brelaz): the uncoloured row with the most distinct
+// colours among its neighbours next, ties to more neighbours, then the lower
+// index; returns the number of colours.
+int32_t dsatur_colouring(const HostCsr& A, std::vector<int32_t>& colour);
+
+// The smoother's colouring: DSATUR when it needs fewer colours than the
+// ascending-order greedy, else the greedy one.
+int32_t smoother_colouring(const HostCsr& A, std::vector<int32_t>& colour);
+
 }  // namespace amg

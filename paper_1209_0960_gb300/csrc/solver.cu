@@ -1000,7 +1000,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         host_ms += now_ms() - t0;
         if (R.nc == 0 || (double)cur.A.n / (double)R.nc < prm->min_coarsen_rate) break;
         t0 = now_ms();
-        cur.ncolours = greedy_colouring(cur.A, cur.colour);
+        cur.ncolours = smoother_colouring(cur.A, cur.colour);
         host_ms += now_ms() - t0;
         cur.agg = std::move(R);
         HostCsr G;
@@ -1394,7 +1394,7 @@ int amg_colour(const amg_csr* A, int32_t* colour, int32_t* ncolours) {
         if (!colour || !ncolours) throw Error{AMG_EINVAL, "null argument"};
         HostCsr H = host_copy(A);
         std::vector<int32_t> c;
-        *ncolours = greedy_colouring(H, c);
+        *ncolours = smoother_colouring(H, c);
         std::memcpy(colour, c.data(), sizeof(int32_t) * H.n);
     });
 }

@@ -104,3 +104,14 @@ def to_dense(rp, ci, va):
         for k in range(rp[i], rp[i + 1]):
             A[i, ci[k]] += va[k]
     return A
+
+
+def oracle_iterate(H, b, it_gpu, it_o, xo, x0=None):
+    """The oracle's CG iterate after the GPU's iteration count.  The bar on
+    iterations (within 1) lets the two stop one step apart, and the step
+    between them can exceed the solution bar on badly conditioned problems,
+    so solutions are compared at the same step."""
+    if it_gpu == it_o:
+        return xo
+    x, _, _, _ = H.pcg(b, tol=1e-300, maxit=it_gpu, x0=x0)
+    return x

@@ -193,6 +193,78 @@ def test_colouring_is_proper_on_coarse_levels():
         assert L["ncolours"] == col.max() + 1
 
 
+def _graph(n, edges):
+    """Symmetric pattern with a diagonal from an undirected edge list."""
+    rows, cols = list(range(n)), list(range(n))
+    for a, b in edges:
+        rows += [a, b]
+        cols += [b, a]
+    rp, ci, _ = coo_to_csr(n, rows, cols, np.ones(len(rows)))
+    return rp, ci
+
+
+def _proper(rp, ci, col):
+    return all(col[i] != col[j] for i in range(len(rp) - 1) for j in ci[rp[i]:rp[i + 1]] if j != i)
+
+
+def test_dsatur_on_a_path_follows_saturation_degree_index():
+    # path 0-1-2-3: row 1 first (degree 2, lower index than 2) takes colour 0;
+    # rows 0 and 2 then see one colour, row 2 has more neighbours: colour 1;
+    # rows 0 and 3 both see one colour with one neighbour: row 0 (colour 1),
+    # then row 3 (colour 0)
+    rp, ci = _graph(4, [(0, 1), (1, 2), (2, 3)])
+    c, nc = O.colour(rp, ci, O.COLOUR_DSATUR)
+    assert nc == 2 and c.tolist() == [1, 0, 1, 0]
+    g, ng = O.colour(rp, ci, O.COLOUR_GREEDY)
+    assert ng == 2 and g.tolist() == [0, 1, 0, 1]
+    # equal counts: the smoother keeps the ascending-order greedy colouring
+    s, ns = O.colour(rp, ci)
+    assert ns == 2 and s.tolist() == [0, 1, 0, 1]
+
+
+@pytest.mark.parametrize("name,n,edges,chi", [
+    ("odd_cycle_7", 7, [(i, (i + 1) % 7) for i in range(7)], 3),
+    ("complete_5", 5, [(i, j) for i in range(5) for j in range(i + 1, 5)], 5),
+    ("wheel_6", 7, [(i, (i + 1) % 6) for i in range(6)] + [(6, i) for i in range(6)], 3),
+    ("wheel_7", 8, [(i, (i + 1) % 7) for i in range(7)] + [(7, i) for i in range(7)], 4),
+    ("tree", 9, [(0, 1), (0, 2), (1, 3), (1, 4), (2, 5), (5, 6), (5, 7), (7, 8)], 2),
+])
+def test_dsatur_is_exact_on_small_graphs(name, n, edges, chi):
+    # DSATUR colours cycles, wheels, complete and bipartite graphs with their
+    # chromatic number
+    rp, ci = _graph(n, edges)
+    c, nc = O.colour(rp, ci, O.COLOUR_DSATUR)
+    assert nc == chi and _proper(rp, ci, c)
+
+
+def test_smoother_colouring_takes_dsatur_on_a_crown_graph():
+    # crown graph (K_{m,m} minus a perfect matching) numbered u0 v0 u1 v1 ...:
+    # the ascending-order greedy needs m colours, DSATUR two (u's 0, v's 1)
+    m = 6
+    edges = [(2 * i, 2 * j + 1) for i in range(m) for j in range(m) if i != j]
+    rp, ci = _graph(2 * m, edges)
+    g, ng = O.colour(rp, ci, O.COLOUR_GREEDY)
+    assert ng == m
+    c, nc = O.colour(rp, ci)
+    assert nc == 2 and c.tolist() == [0, 1] * m
+
+
+def test_dsatur_is_red_black_on_grids_and_never_worse_on_coarse_levels():
+    rp, ci, _ = const_diag_grid((6, 5, 4), 6.0)
+    c, nc = O.colour(rp, ci, O.COLOUR_DSATUR)
+    assert nc == 2 and _proper(rp, ci, c)
+    p = P.lognormal3d((20, 20, 20), seed=0)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=60))
+    fewer = 0
+    for l in range(H.num_levels - 1):
+        L = H.level(l)
+        _, ng = O.colour(L["row_ptr"], L["col"], O.COLOUR_GREEDY)
+        _, nd = O.colour(L["row_ptr"], L["col"], O.COLOUR_DSATUR)
+        assert L["ncolours"] == min(ng, nd)
+        fewer += nd < ng
+    assert fewer >= 1
+
+
 # ---------------------------------------------------------------------------
 # Galerkin product (Eq. prolongation and the coarse operator)
 # ---------------------------------------------------------------------------
