@@ -444,7 +444,8 @@ def run_ours(args, dist: Dist):
                   "operator_complexity": summary["operator_complexity"],
                   "level_n": [l["n"] for l in levels],
                   "autotune": args.autotune, "autotune_ms": summary["autotune_ms"],
-                  "lanes_per_row": [l["lanes_per_row"] for l in levels[:-1]]},
+                  "lanes_per_row": [l["lanes_per_row"] for l in levels[:-1]],
+                  "colours": [l["ncolours"] for l in levels[:-1]]},
         "roofline": roofline,
         "roofline_level0": {k: kernel_roofline(k) for k in
                             ("gs_level0", "first_level0", "residual_level0", "prolong",

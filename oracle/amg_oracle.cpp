@@ -461,21 +461,26 @@ int greedy_colour(const Csr& A, std::vector<int>& colour) {
 
 // DSATUR (Brelaz, 1979): repeatedly colour the uncoloured row whose
 // neighbours already show the most distinct colours (its saturation); ties go
-// to the row with more neighbours, then to the lower index.  The row takes the
-// smallest colour none of its neighbours has.
+// to the row with more neighbours, then to the row whose saturation reached
+// its value first (initially: the lower index; a colouring step raises its
+// neighbours' saturations in column order).  The row takes the smallest
+// colour none of its neighbours has.
 int dsatur_colour(const Csr& A, std::vector<int>& colour) {
     const int n = A.n;
     colour.assign(n, -1);
     std::vector<std::set<int>> seen(n);   // colours among the coloured neighbours
-    std::vector<int> deg(n);
-    std::set<std::tuple<int, int, int>> order;   // (-saturation, -degree, row)
+    std::vector<int> deg(n), stamp(n);
+    std::set<std::tuple<int, int, int>> order;   // (-saturation, -degree, stamp)
+    std::map<int, int> row_of;                   // stamp -> row
     for (int i = 0; i < n; ++i) {
         deg[i] = (int)A.neighbours(i).size();
+        stamp[i] = i;
+        row_of[i] = i;
         order.insert(std::make_tuple(0, -deg[i], i));
     }
-    int nc = 0;
+    int clock = n, nc = 0;
     while (!order.empty()) {
-        const int v = std::get<2>(*order.begin());
+        const int v = row_of[std::get<2>(*order.begin())];
         order.erase(order.begin());
         int c = 0;
         while (seen[v].count(c)) ++c;
@@ -483,9 +488,11 @@ int dsatur_colour(const Csr& A, std::vector<int>& colour) {
         nc = std::max(nc, c + 1);
         for (int j : A.neighbours(v)) {
             if (colour[j] >= 0 || seen[j].count(c)) continue;
-            order.erase(std::make_tuple(-(int)seen[j].size(), -deg[j], j));
+            order.erase(std::make_tuple(-(int)seen[j].size(), -deg[j], stamp[j]));
             seen[j].insert(c);
-            order.insert(std::make_tuple(-(int)seen[j].size(), -deg[j], j));
+            stamp[j] = clock++;
+            row_of[stamp[j]] = j;
+            order.insert(std::make_tuple(-(int)seen[j].size(), -deg[j], stamp[j]));
         }
     }
     return nc;

@@ -561,75 +561,118 @@ int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour) {
 
 
 
-namespace {
-
-// colours seen among the coloured neighbours of a row: a 64-bit mask for
-// colours below 64, a sorted list above (only rows of very high degree get
-// there)
-struct SeenColours {
-    uint64_t low = 0;
-    std::vector<int32_t> high;
-    bool has(int32_t c) const {
-        if (c < 64) return (low >> c) & 1u;
-        return std::binary_search(high.begin(), high.end(), c);
-    }
-    void add(int32_t c) {
-        if (c < 64) low |= uint64_t(1) << c;
-        else high.insert(std::lower_bound(high.begin(), high.end(), c), c);
-    }
-    int32_t smallest_free() const {
-        if (~low) return (int32_t)__builtin_ctzll(~low);
-        int32_t c = 64;
-        for (int32_t h : high) {
-            if (h != c) break;
-            ++c;
-        }
-        return c;
-    }
-};
-
-}  // namespace
-
 int32_t dsatur_colouring(const HostCsr& A, std::vector<int32_t>& colour) {
     const int32_t n = A.n;
-    colour.assign(n, -1);
-    std::vector<int32_t> deg(n, 0), sat(n, 0);
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
-            if (A.ci[k] != i) ++deg[i];
-    std::vector<SeenColours> seen(n);
-    // one max-heap per saturation value, keyed by (degree, -index), with lazy
-    // deletion: an entry is live while its row is uncoloured and still has
-    // that saturation
-    auto key = [&](int32_t i) { return ((uint64_t)(uint32_t)deg[i] << 32) | (uint32_t)(~(uint32_t)i); };
-    std::vector<std::priority_queue<uint64_t>> buckets(1);
-    for (int32_t i = 0; i < n; ++i) buckets[0].push(key(i));
+    // per-row state in one record, so that a neighbour update touches one
+    // cache line; colours >= 64 seen by a row go to an overflow list
+    struct Row {
+        uint64_t low = 0;        // colours < 64 among the coloured neighbours
+        uint32_t stamp = 0;      // when the saturation last changed
+        int32_t sat = 0;
+        int32_t deg = 0;
+        int32_t colour = -1;
+    };
+    std::vector<Row> R(n);
+    std::vector<std::vector<int32_t>> high;   // sorted colours >= 64, by overflow slot
+    std::vector<int32_t> high_slot;           // row -> overflow slot (-1: none)
+    auto has = [&](int32_t j, int32_t c) {
+        if (c < 64) return ((R[j].low >> c) & 1u) != 0;
+        if (high_slot.empty() || high_slot[j] < 0) return false;
+        const auto& h = high[high_slot[j]];
+        return std::binary_search(h.begin(), h.end(), c);
+    };
+    auto add = [&](int32_t j, int32_t c) {
+        if (c < 64) {
+            R[j].low |= uint64_t(1) << c;
+            return;
+        }
+        if (high_slot.empty()) high_slot.assign(n, -1);
+        if (high_slot[j] < 0) {
+            high_slot[j] = (int32_t)high.size();
+            high.emplace_back();
+        }
+        auto& h = high[high_slot[j]];
+        h.insert(std::lower_bound(h.begin(), h.end(), c), c);
+    };
+    auto smallest_free = [&](int32_t v) {
+        if (~R[v].low) return (int32_t)__builtin_ctzll(~R[v].low);
+        int32_t c = 64;
+        if (!high_slot.empty() && high_slot[v] >= 0)
+            for (int32_t h : high[high_slot[v]]) {
+                if (h != c) break;
+                ++c;
+            }
+        return c;
+    };
+    int32_t maxdeg = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t d = 0;
+        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) d += A.ci[k] != i;
+        R[i].deg = d;
+        R[i].stamp = (uint32_t)i;
+        maxdeg = std::max(maxdeg, d);
+    }
+    // FIFO buckets by (saturation, degree) with lazy deletion: an entry is
+    // live while its row is uncoloured and its stamp is the row's latest, so a
+    // bucket's first live entry is the row that reached it first
+    struct Bucket {
+        std::vector<std::pair<int32_t, uint32_t>> q;   // (row, stamp)
+        size_t head = 0;
+        int64_t live = 0;
+    };
+    const int32_t D = maxdeg + 1;
+    std::vector<std::vector<Bucket>> buckets(1, std::vector<Bucket>(D));
+    std::vector<int32_t> dtop(1, -1);   // highest degree with live entries, per saturation
+    for (int32_t i = 0; i < n; ++i) {
+        Bucket& b = buckets[0][R[i].deg];
+        b.q.emplace_back(i, (uint32_t)i);
+        ++b.live;
+        dtop[0] = std::max(dtop[0], R[i].deg);
+    }
+    uint32_t clock = (uint32_t)n;
     int32_t top = 0, nc = 0;
     for (int32_t done = 0; done < n; ++done) {
         int32_t v = -1;
         while (v < 0) {
-            auto& h = buckets[top];
-            if (h.empty()) {
+            int32_t& d = dtop[top];
+            while (d >= 0 && buckets[top][d].live == 0) --d;
+            if (d < 0) {
                 --top;
                 continue;
             }
-            const int32_t i = (int32_t)~(uint32_t)(h.top() & 0xffffffffu);
-            h.pop();
-            if (colour[i] < 0 && sat[i] == top) v = i;
+            Bucket& b = buckets[top][d];
+            while (true) {
+                const auto e = b.q[b.head++];
+                if (R[e.first].colour < 0 && R[e.first].stamp == e.second) {
+                    v = e.first;
+                    break;
+                }
+            }
+            --b.live;
         }
-        const int32_t c = seen[v].smallest_free();
-        colour[v] = c;
+        const int32_t c = smallest_free(v);
+        R[v].colour = c;
         nc = std::max(nc, c + 1);
         for (int32_t k = A.rp[v]; k < A.rp[v + 1]; ++k) {
             const int32_t j = A.ci[k];
-            if (j == v || colour[j] >= 0 || seen[j].has(c)) continue;
-            seen[j].add(c);
-            const int32_t s = ++sat[j];
-            if (s >= (int32_t)buckets.size()) buckets.resize(s + 1);
-            buckets[s].push(key(j));
+            if (j == v || R[j].colour >= 0 || has(j, c)) continue;
+            add(j, c);
+            --buckets[R[j].sat][R[j].deg].live;
+            const int32_t s = ++R[j].sat;
+            if (s >= (int32_t)buckets.size()) {
+                buckets.emplace_back(D);
+                dtop.push_back(-1);
+            }
+            R[j].stamp = clock++;
+            Bucket& b = buckets[s][R[j].deg];
+            b.q.emplace_back(j, R[j].stamp);
+            ++b.live;
+            dtop[s] = std::max(dtop[s], R[j].deg);
             top = std::max(top, s);
         }
     }
+    colour.resize(n);
+    for (int32_t i = 0; i < n; ++i) colour[i] = R[i].colour;
     return nc;
 }
 

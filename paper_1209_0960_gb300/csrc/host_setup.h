@@ -43,8 +43,10 @@ AggResult aggregate_tiled(const HostCsr& A, const amg_params& p, int32_t tile, i
 int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour);
 
 // DSATUR colouring (Brelaz): the uncoloured row with the most distinct
-// colours among its neighbours next, ties to more neighbours, then the lower
-// index; returns the number of colours.
+// colours among its neighbours next, ties to more neighbours, then to the row
+// whose saturation reached its value first (initially the lower index;
+// colouring a row raises its neighbours' saturations in column order);
+// returns the number of colours.
 int32_t dsatur_colouring(const HostCsr& A, std::vector<int32_t>& colour);
 
 // The smoother's colouring: DSATUR when it needs fewer colours than the
