@@ -224,6 +224,16 @@ extern thread_local bool t_launch_overlap;
 // starts early only occupies the SMs its predecessor is still using
 extern int g_overlap_max_blocks;
 
+// Dynamic shared memory above the default needs a per-function attribute,
+// which is process-wide state: contexts set up and solved on several threads
+// at once must never lower it under another thread's launch.  This raises
+// the function's limit to at least `bytes` (never lowers it), once per size.
+void raise_dyn_smem(const void* func, size_t bytes);
+template <typename... KArgs>
+void raise_dyn_smem(void (*kernel)(KArgs...), size_t bytes) {
+    raise_dyn_smem(reinterpret_cast<const void*>(kernel), bytes);
+}
+
 template <typename... KArgs, typename... Args>
 void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
                    Args&&... args) {

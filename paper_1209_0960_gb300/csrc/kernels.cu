@@ -19,6 +19,9 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <map>
+#include <mutex>
+
 #include "device.h"
 
 namespace amg {
@@ -913,6 +916,18 @@ inline int blocks_for(int64_t threads) { return (int)((threads + kBlock - 1) / k
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
+void raise_dyn_smem(const void* func, size_t bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<int, const void*>, size_t> limit;   // (device, function) -> bytes
+    int dev = 0;
+    AMG_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    size_t& cur = limit[{dev, func}];
+    if (bytes <= cur) return;
+    AMG_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cur = bytes;
+}
+
 thread_local bool t_launch_overlap = false;
 int g_overlap_max_blocks = 304;
 int g_reduction_blocks = 1216;
@@ -970,9 +985,7 @@ template <typename K>
 size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
     const size_t bytes = (size_t)kFineBlock * L.width * (sizeof(int32_t) + value_bytes);
     // the 48 KB default covers static and dynamic shared memory together
-    if (bytes > kDefaultDynSmem)
-        AMG_CUDA_TRY(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)bytes));
+    if (bytes > kDefaultDynSmem) raise_dyn_smem(kernel, bytes);
     return bytes;
 }
 
@@ -1098,8 +1111,7 @@ template <typename TB>
 void dense_gemv_impl(int n, const double* M, const TB* b, TB* x, cudaStream_t s) {
     auto k = k_dense_gemv<TB>;
     const size_t smem = std::is_same<TB, double>::value ? 0 : sizeof(double) * (size_t)n;
-    if (smem > kDefaultDynSmem)
-        AMG_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (smem > kDefaultDynSmem) raise_dyn_smem(k, smem);
     launch_kernel(k, blocks_for((int64_t)n * 32), kBlock, smem, s, n, M, b, x);
 }
 

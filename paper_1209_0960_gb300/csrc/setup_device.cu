@@ -282,8 +282,8 @@ void galerkin_device(const DevCsr& A, const HostCsr& Ah, const AggResult& R, Dev
     int wpb = (int)std::max<size_t>(1, std::min<size_t>(8, smem_limit / per_warp));
     const size_t smem = per_warp * wpb;
     if (smem > 40 * 1024) {   // the 48 KB default also holds static shared memory
-        AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        AMG_CUDA_TRY(cudaFuncSetAttribute(k_galerkin<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        raise_dyn_smem(k_galerkin<false>, smem);
+        raise_dyn_smem(k_galerkin<true>, smem);
     }
     DevArena tmp(s);
     int32_t* d_agg = tmp.alloc<int32_t>(n);
@@ -390,7 +390,7 @@ bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
     k_transpose<<<blocks_for((int64_t)n * n), kBlock, 0, s>>>(n, L, U);
     const size_t smem = sizeof(double) * (size_t)n;
     if (smem > 40 * 1024)   // the 48 KB default also holds static shared memory
-        AMG_CUDA_TRY(cudaFuncSetAttribute(k_chol_inverse, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        raise_dyn_smem(k_chol_inverse, smem);
     k_chol_inverse<<<n, 32, smem, s>>>(n, L, U, Minv);
     AMG_CUDA_TRY(cudaGetLastError());
     int herr = 0;

@@ -448,19 +448,20 @@ void set_shape(DevLevel& L, int lanes) {
 // Level signature for the process-wide cache of tuned shapes: levels that
 // agree on it run the same kernels over similar slices.
 struct ShapeKey {
-    int precision, size_class, width, mean_x4, ncolours, fine;
+    int precision, size_class, width_class, mean, ncolours, fine;
     bool operator<(const ShapeKey& o) const {
-        return std::tie(precision, size_class, width, mean_x4, ncolours, fine) <
-               std::tie(o.precision, o.size_class, o.width, o.mean_x4, o.ncolours, o.fine);
+        return std::tie(precision, size_class, width_class, mean, ncolours, fine) <
+               std::tie(o.precision, o.size_class, o.width_class, o.mean, o.ncolours, o.fine);
     }
 };
 
 ShapeKey shape_key(const amg_ctx* c, int l) {
     const DevLevel& L = c->dl[l];
-    // half-octave size classes
-    const int size_class = (int)std::floor(2.0 * std::log2(std::max(1, L.n)));
-    const int mean_x4 = (int)std::lround(4.0 * (double)L.nnz_off / std::max(1, L.n));
-    return {c->precision, size_class, L.width, mean_x4, L.ncolours, l == 0 ? 1 : 0};
+    // octave size classes, slice widths in steps of 4, whole mean row lengths:
+    // coarse enough that requests of similar grids share their tuning
+    const int size_class = (int)std::floor(std::log2(std::max(1, L.n)));
+    const int mean = (int)std::lround((double)L.nnz_off / std::max(1, L.n));
+    return {c->precision, size_class, (L.width + 3) / 4, mean, L.ncolours, l == 0 ? 1 : 0};
 }
 
 std::mutex g_shape_mu;
@@ -547,9 +548,11 @@ double autotune_shapes(amg_ctx* c) {
             }
         }
         if (t_rule <= 1.03 * t_best) best = rule;
-        set_shape(L, best);
+        // a context tuning the same signature concurrently may have stored
+        // its choice first: every context then runs the stored one
         std::lock_guard<std::mutex> lk(g_shape_mu);
-        g_shape_cache.emplace(key, best);
+        const int stored = g_shape_cache.emplace(key, best).first->second;
+        set_shape(L, shape_allowed(L, stored) ? stored : best);
     }
     for (int l = 0; l + 1 < nlev; ++l) c->shapes[c->precision][l] = c->dl[l].lpr;
     c->tuned[c->precision] = true;

@@ -37,7 +37,8 @@ def _drain(server, tickets, timeout_s=180.0):
 def _standalone(p, server_params):
     prm = server_params.params
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, precision=prm.precision,
-                     coarsen_target=prm.coarsen_target, dense_cap=prm.dense_cap)
+                     coarsen_target=prm.coarsen_target, dense_cap=prm.dense_cap,
+                     autotune=prm.autotune, aggregation_tile=prm.aggregation_tile)
     x = np.zeros(p.n)
     rc, info = solver.solve_host(p.b, x, tol=TOL, maxit=server_params.maxit)
     solver.close()
@@ -61,6 +62,27 @@ def test_results_are_the_same_alone_and_in_the_mix():
         r = p.b - O.spmv(p.row_ptr, p.col, p.val, x)
         assert np.linalg.norm(r) <= 1.05 * TOL * np.linalg.norm(p.b)
         assert times["total_ms"] >= times["solve_ms"] >= 0 and times["hbm_bytes"] > 0
+        rc1, x1, info1 = _standalone(p, params)
+        assert rc1 == amg.AMG_OK and info1["iterations"] == info["iterations"]
+        assert np.array_equal(x, x1), p.name
+
+
+def test_tuned_shapes_and_tiled_aggregation_in_the_mix():
+    # setups tune launch shapes and aggregate in tiles on several threads while
+    # other requests solve; shapes of a level signature are shared through the
+    # process-wide cache, so a standalone run reproduces each result exactly
+    reqs = [P.serving_request(k, lo=12, hi=40) for k in range(60, 84)]
+    server = amg.Server(dim=3, max_slots=8, setup_threads=6, autotune=1, aggregation_tile=512)
+    tickets = [server.submit(p.row_ptr, p.col, p.val, p.b, TOL) for p in reqs]
+    res = _drain(server, tickets, timeout_s=300.0)
+    st = server.stats()
+    params = server.params
+    server.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    for p, t in zip(reqs, tickets):
+        rc, x, info, times = res[t]
+        assert rc == amg.AMG_OK, amg.amg_last_error()
+        assert info["true_rel_residual"] <= 1.5 * TOL
         rc1, x1, info1 = _standalone(p, params)
         assert rc1 == amg.AMG_OK and info1["iterations"] == info["iterations"]
         assert np.array_equal(x, x1), p.name
