@@ -71,9 +71,15 @@ def parse_args():
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="time the launch shapes of every level at setup and keep the fastest "
                          "(0: the fixed rules)")
+    ap.add_argument("--lanes-per-row", type=str, default="", metavar="L0,L1,...",
+                    help="fixed launch shapes per level instead of tuning (0 = staged "
+                         "kernels, else 1/2/4/8 lanes per row), for reproducible profiles")
     ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
                     help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
     args = ap.parse_args()
+    args.lanes = [int(v) for v in args.lanes_per_row.split(",") if v.strip()]
+    if args.lanes:
+        args.autotune = 0
     if args.aggregation_tile < 0:
         args.aggregation_tile = 4096 if args.serving > 0 else 0
     return args
@@ -283,6 +289,11 @@ def timed_solves(solver, b, x, steps, tol, stream, dist):
     return ev0.elapsed_time(ev1) / steps, infos
 
 
+def apply_lanes(solver, args):
+    for l, lanes in enumerate(args.lanes):
+        solver.set_level_shape(l, lanes)
+
+
 def run_ours(args, dist: Dist):
     import numpy as np
     import torch
@@ -296,6 +307,7 @@ def run_ours(args, dist: Dist):
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune)
+    apply_lanes(solver, args)
     setup_wall = time.perf_counter() - t0
     summary, levels = solver.info()
     b = torch.from_numpy(p.b).cuda()
@@ -473,7 +485,8 @@ def profile_run(args):
     p = make_problem(args.grid)
     prec = amg.AMG_FP32_IN_FP64 if args.profile_fp32 else amg.AMG_FP64
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap,
-                     precision=prec)
+                     precision=prec, autotune=args.autotune)
+    apply_lanes(solver, args)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)
     torch.cuda.synchronize()
