@@ -165,11 +165,20 @@ private:
 
     // set membership by stamps
     std::vector<uint32_t> in_a_, in_na_, adj_mark_;
-    uint32_t stamp_a_ = 0, stamp_na_ = 0, stamp_adj_ = 0;
+    uint32_t stamp_a_ = 0, stamp_na_ = 0;
+    // aggregates (ids below adj_limit_) holding a vertex of N(a) carry
+    // adj_mark_ == stamp_na_; the isolated phase counts only the aggregates of
+    // non-isolated vertices
+    int32_t adj_limit_ = INT_MAX;
     std::vector<int32_t> pos_in_a_;
 
     std::vector<int32_t> a_;          // members of the aggregate being built
     std::vector<int32_t> na_;         // N(a)
+    // links into the aggregate being built, kept up to date as members join
+    // (valid where lstamp_ == stamp_a_): cons_2, cons_1 and the strong links
+    // from the row into a; and the strong links from each row of U into U
+    std::vector<uint32_t> lstamp_;
+    std::vector<int32_t> lc2_, lc1_, lsa_, su_;
     int32_t maxa_ = 0;
     std::vector<int32_t> dist_;       // all-pairs distances inside a, maxa_ x maxa_
 
@@ -184,6 +193,8 @@ private:
             int32_t c = --nna_[j];
             buckets_[c].push(j);
             if (c < min_bucket_) min_bucket_ = c;
+            const int32_t t = S_.tpos[k];
+            if (t >= 0 && S_.strong[t]) --su_[j];
         }
     }
 
@@ -204,13 +215,42 @@ private:
     void start_aggregate(int32_t v) {
         ++stamp_a_;
         a_.clear();
+        ++stamp_na_;
+        na_.clear();
         add_member_plain(v);
         dist_[0] = 0;
     }
+    // v joins a.  N(a) grows by v's neighbours outside a; v itself stays in
+    // the list (every reader skips members: they are not in U, and not
+    // unaggregated isolated vertices), so the list is N(a) plus former
+    // members, in the order they were reached.
     void add_member_plain(int32_t v) {
         in_a_[v] = stamp_a_;
         pos_in_a_[v] = (int32_t)a_.size();
         a_.push_back(v);
+        for (int32_t k = A_.rp[v]; k < A_.rp[v + 1]; ++k) {
+            const int32_t j = A_.ci[k];
+            if (j == v || in_a(j) || in_na_[j] == stamp_na_) continue;
+            in_na_[j] = stamp_na_;
+            na_.push_back(j);
+            const int32_t g = agg_[j];
+            if (g >= 0 && g < adj_limit_) adj_mark_[g] = stamp_na_;
+        }
+        // the new member's links as its neighbours see them: s1 = (w, v)
+        // strong, s2 = (v, w) strong, counted only where w's row stores v
+        for (int32_t k = A_.rp[v]; k < A_.rp[v + 1]; ++k) {
+            const int32_t w = A_.ci[k];
+            const int32_t t = S_.tpos[k];
+            if (w == v || t < 0) continue;
+            if (lstamp_[w] != stamp_a_) {
+                lstamp_[w] = stamp_a_;
+                lc2_[w] = lc1_[w] = lsa_[w] = 0;
+            }
+            const bool s1 = S_.strong[t] != 0, s2 = S_.strong[k] != 0;
+            if (s1 && s2) ++lc2_[w];
+            else if (s1 != s2) ++lc1_[w];
+            lsa_[w] += s1;
+        }
     }
 
     // distances from w (not in a) to every member through edges into a
@@ -247,31 +287,14 @@ private:
         add_member_plain(w);
     }
 
-    void build_na() {
-        ++stamp_na_;
-        na_.clear();
-        for (int32_t x : a_)
-            for (int32_t k = A_.rp[x]; k < A_.rp[x + 1]; ++k) {
-                int32_t j = A_.ci[k];
-                if (j == x || in_a(j) || in_na_[j] == stamp_na_) continue;
-                in_na_[j] = stamp_na_;
-                na_.push_back(j);
-            }
-    }
-
+    // cons_2 / cons_1 of w with respect to a: links (w, u), u in a, strong both
+    // ways / one way (kept up to date by add_member_plain)
     void cons(int32_t w, int32_t& c2, int32_t& c1) const {
-        c2 = 0;
-        c1 = 0;
-        for (int32_t k = A_.rp[w]; k < A_.rp[w + 1]; ++k) {
-            int32_t u = A_.ci[k];
-            if (u == w || !in_a(u)) continue;
-            bool s1 = S_.strong[k] != 0;
-            int32_t t = S_.tpos[k];
-            bool s2 = t >= 0 && S_.strong[t] != 0;
-            if (s1 && s2) ++c2;
-            else if (s1 != s2) ++c1;
-        }
+        const bool live = lstamp_[w] == stamp_a_;
+        c2 = live ? lc2_[w] : 0;
+        c1 = live ? lc1_[w] : 0;
     }
+    int32_t strong_into_a(int32_t w) const { return lstamp_[w] == stamp_a_ ? lsa_[w] : 0; }
 
     void grow();
     void round_aggregate();
@@ -284,10 +307,6 @@ void Aggregation::grow() {
     std::vector<int32_t> dws;      // distance rows of the candidates
     std::vector<int32_t> dw(maxa_);
     while ((int32_t)a_.size() < p_.s_min) {
-        build_na();
-        ++stamp_adj_;
-        for (int32_t y : na_)
-            if (agg_[y] >= 0) adj_mark_[agg_[y]] = stamp_adj_;
         cands.clear();
         dws.clear();
         const int32_t m = (int32_t)a_.size();
@@ -315,7 +334,7 @@ void Aggregation::grow() {
             for (int32_t k = A_.rp[w]; k < A_.rp[w + 1]; ++k) {
                 int32_t u = A_.ci[k];
                 if (u == w || in_a(u)) continue;
-                conn += (agg_[u] >= 0 && adj_mark_[agg_[u]] == stamp_adj_) ? 2 : 1;
+                conn += (agg_[u] >= 0 && adj_mark_[agg_[u]] == stamp_na_) ? 2 : 1;
                 if (inU_[u] && in_na_[u] != stamp_na_) ++nb;
             }
             int64_t deg = S_.deg[w];
@@ -340,21 +359,14 @@ void Aggregation::grow() {
 
 void Aggregation::round_aggregate() {
     while ((int32_t)a_.size() < p_.s_max) {
-        build_na();
         int32_t chosen = INT_MAX;
         for (int32_t w : na_) {
             if (!inU_[w] || w >= chosen) continue;
             int32_t c2, c1;
             cons(w, c2, c1);
             if (c2 + c1 <= 0) continue;
-            int32_t to_a = 0, to_u = 0;
-            for (int32_t k = A_.rp[w]; k < A_.rp[w + 1]; ++k) {
-                int32_t u = A_.ci[k];
-                if (u == w || !S_.strong[k]) continue;
-                if (in_a(u)) ++to_a;
-                else if (inU_[u]) ++to_u;
-            }
-            if (to_a > to_u) chosen = w;
+            // strong links from w into a and into U (members of a have left U)
+            if (strong_into_a(w) > su_[w]) chosen = w;
         }
         if (chosen == INT_MAX) break;
         add_member_plain(chosen);   // distances are not needed after Algorithm 2
@@ -365,10 +377,6 @@ void Aggregation::round_aggregate() {
 void Aggregation::grow_iso(int32_t n_phase1) {
     std::vector<int32_t> dw(maxa_), best_dw(maxa_);
     while ((int32_t)a_.size() < p_.s_min) {
-        build_na();
-        ++stamp_adj_;
-        for (int32_t y : na_)
-            if (agg_[y] >= 0 && agg_[y] < n_phase1) adj_mark_[agg_[y]] = stamp_adj_;
         int32_t chosen = INT_MAX;
         const int32_t m = (int32_t)a_.size();
         for (int32_t w : na_) {
@@ -380,7 +388,7 @@ void Aggregation::grow_iso(int32_t n_phase1) {
                 int32_t y = A_.ci[k];
                 if (y == w) continue;
                 int32_t g = agg_[y];
-                if (g >= 0 && g < n_phase1 && adj_mark_[g] == stamp_adj_) shares = true;
+                if (g >= 0 && g < n_phase1 && adj_mark_[g] == stamp_na_) shares = true;
             }
             if (!shares) continue;
             chosen = w;
@@ -400,6 +408,11 @@ AggResult Aggregation::run() {
     in_na_.assign(n_, 0);
     adj_mark_.assign(n_, 0);
     pos_in_a_.assign(n_, 0);
+    lstamp_.assign(n_, 0);
+    lc2_.assign(n_, 0);
+    lc1_.assign(n_, 0);
+    lsa_.assign(n_, 0);
+    su_.assign(n_, 0);
     maxa_ = std::max(p_.s_max, p_.s_min) + 2;
     dist_.assign((size_t)maxa_ * maxa_, 0);
 
@@ -414,11 +427,15 @@ AggResult Aggregation::run() {
     buckets_.assign(maxdeg + 1, {});
     for (int32_t v = 0; v < n_; ++v) {
         if (!inU_[v]) continue;
-        int32_t c = 0;
+        int32_t c = 0, su = 0;
         for (int32_t k = A_.rp[v]; k < A_.rp[v + 1]; ++k) {
             int32_t j = A_.ci[k];
-            if (j != v && inU_[j]) ++c;
+            if (j != v && inU_[j]) {
+                ++c;
+                su += S_.strong[k] != 0;
+            }
         }
+        su_[v] = su;
         nna_[v] = c;
         buckets_[c].push(v);
         ++remaining_;
@@ -460,8 +477,7 @@ AggResult Aggregation::run() {
                 ++next_id_;
             }
             if (remaining_ == 0) break;
-            build_na();
-            int32_t seed = -1;
+                int32_t seed = -1;
             for (int32_t y : na_)
                 if (inU_[y] && (seed < 0 || nna_[y] < nna_[seed] || (nna_[y] == nna_[seed] && y < seed)))
                     seed = y;
@@ -469,6 +485,7 @@ AggResult Aggregation::run() {
         }
     }
     const int32_t n_phase1 = next_id_;
+    adj_limit_ = n_phase1;
     for (int32_t v = 0; v < n_; ++v) {
         if (!S_.isolated[v] || S_.dirichlet[v] || agg_[v] >= 0) continue;
         start_aggregate(v);
