@@ -71,6 +71,8 @@ def parse_args():
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="time the launch shapes of every level at setup and keep the fastest "
                          "(0: the fixed rules)")
+    ap.add_argument("--coarsen-target", type=int, default=0, metavar="N",
+                    help="stop coarsening at N rows (0: the library default)")
     ap.add_argument("--lanes-per-row", type=str, default="", metavar="L0,L1,...",
                     help="fixed launch shapes per level instead of tuning (0 = staged "
                          "kernels, else 1/2/4/8 lanes per row), for reproducible profiles")
@@ -218,12 +220,14 @@ def make_problem(grid: int):
     return problems.lognormal3d((grid, grid, grid), variance=4.0, corr_len=0.05, seed=0)
 
 
-def oracle_sample(grid: int, tol: float, steps: int, warmup: int, min_seconds: float = 0.0):
-    """Time the oracle's PCG solve on a grid^3 instance of the workload.
-    Returns (seconds per solve, iterations, n)."""
+def oracle_sample(grid: int, tol: float, steps: int, warmup: int, min_seconds: float = 0.0,
+                  openmp: bool = False):
+    """Time the oracle's PCG solve on a grid^3 instance of the workload (the
+    serial build, or the OpenMP build of the same source on all host cores).
+    Returns (seconds per solve, iterations, n, solves)."""
     from oracle import oracle as O
     p = make_problem(grid)
-    H = O.Hierarchy(p.row_ptr, p.col, p.val, O.default_params(3))
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, O.default_params(3), openmp=openmp)
     for _ in range(warmup):
         H.pcg(p.b, tol=tol, maxit=500)
     times, it = [], 0
@@ -306,7 +310,8 @@ def run_ours(args, dist: Dist):
     t0 = time.perf_counter()
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
-                     aggregation_device=args.aggregation_device, autotune=args.autotune)
+                     aggregation_device=args.aggregation_device, autotune=args.autotune,
+                     **({"coarsen_target": args.coarsen_target} if args.coarsen_target else {}))
     apply_lanes(solver, args)
     setup_wall = time.perf_counter() - t0
     summary, levels = solver.info()
@@ -421,6 +426,7 @@ def run_ours(args, dist: Dist):
 
     # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----------------
     cpu = None
+    cpu_omp = None
     if dist.world == 1 and not args.no_cpu_baseline:
         sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, 1, 0, min_seconds=10.0)
         cpu = {"value": sec * 1e3 * (p.n / n_s), "unit": UNIT, "cores": 1, "kind": "oracle",
@@ -428,6 +434,14 @@ def run_ours(args, dist: Dist):
                          f"({n_s} unknowns, {it_s} iterations, {sec:.3f} s per solve, "
                          f"{reps} solves), scaled by unknowns to {args.grid}^3",
                "host_cpu_count": os.cpu_count()}
+        from oracle import oracle as O
+        threads = O.threads(os.cpu_count() or 1)
+        sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, 1, 0, min_seconds=5.0,
+                                             openmp=True)
+        cpu_omp = {"value": sec * 1e3 * (p.n / n_s), "unit": UNIT, "cores": threads,
+                   "kind": "oracle (OpenMP build of the same source)",
+                   "sample": f"as cpu_baseline, {threads} threads: {it_s} iterations, "
+                             f"{sec:.3f} s per solve, {reps} solves"}
 
     line = {
         "metric": METRIC, "value": ms64, "unit": UNIT, "n_gpus": dist.world,
@@ -470,6 +484,7 @@ def run_ours(args, dist: Dist):
         "e2e": e2e,
         "clocks": clk,
         "cpu_baseline": cpu,
+        "cpu_baseline_openmp": cpu_omp,
         "status": {"fp64": rc64, "fp32_in_fp64": rc32},
     }
     solver.close()

@@ -11,6 +11,13 @@
 // garbled or ambiguous, the documented reading is used; the readings are listed
 // at each step below.  Compile with -ffp-contract=off so no FMA is introduced.
 //
+// The same source also builds with -fopenmp, for the CPU baseline on all host
+// cores only: the SpMV, the rows of one colour in a Gauss-Seidel sweep, the
+// residual, the prolongation and the CG vector updates then run in parallel
+// (each row or element is computed exactly as in the serial build); the
+// restriction, the dot products and the coarsest triangular solves stay
+// sequential.  The serial build ignores the pragmas.
+//
 // Parity status: strength, aggregation, colouring, Galerkin product, V-cycle
 // and PCG are pinned by tests against closed forms, hand-derived maps, dense
 // direct solves and invariants.  The aggregation's tie-breaking on large
@@ -27,6 +34,9 @@
 #include <tuple>
 #include <utility>
 #include <vector>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 namespace {
 
@@ -605,6 +615,7 @@ struct Hierarchy {
 };
 
 void spmv(const Csr& A, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A.n; ++i) {
         double s = 0.0;
         for (int k = A.rp[i]; k < A.rp[i + 1]; ++k) s += A.va[k] * x[A.ci[k]];
@@ -616,6 +627,7 @@ void spmv(const Csr& A, const double* x, double* y) {
 //   x_i = (b_i - sum_{j != i} A_ij x_j) / A_ii
 void gs_colour(const Level& lv, int c, const double* b, double* x) {
     const Csr& A = lv.A;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < A.n; ++i) {
         if (lv.colour[i] != c) continue;
         double t = b[i];
@@ -671,6 +683,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
     smooth(H, lv, b, x);                             // pre-smoothing, one step
     std::vector<double> r(n);
     spmv(lv.A, x, r.data());
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) r[i] = b[i] - r[i];  // residual
     std::vector<double> rc(lv.nc, 0.0), ec(lv.nc, 0.0);
     std::vector<char> started(lv.nc, 0);
@@ -681,6 +694,7 @@ void vcycle(const Hierarchy& H, int l, const double* b, double* x) {
         else rc[I] = rc[I] + r[i];
     }
     vcycle(H, l + 1, rc.data(), ec.data());
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < n; ++i) {                    // x += omega P e
         int I = lv.agg[i];
         if (I >= 0) x[i] = x[i] + H.p.omega * ec[I];
@@ -941,6 +955,7 @@ int oracle_pcg(void* h, const double* b, double* x, double tol, int maxit,
             double pq = dot(p, q);
             if (!(pq > 0.0)) { status = -1; break; }
             double alpha = rho / pq;
+#pragma omp parallel for schedule(static)
             for (int i = 0; i < n; ++i) {
                 xv[i] = xv[i] + alpha * p[i];
                 r[i] = r[i] - alpha * q[i];
@@ -959,6 +974,7 @@ int oracle_pcg(void* h, const double* b, double* x, double tol, int maxit,
             } else {
                 beta = rho_new / rho;
             }
+#pragma omp parallel for schedule(static)
             for (int i = 0; i < n; ++i) p[i] = z[i] + beta * p[i];
             rho = rho_new;
         }
@@ -1044,5 +1060,17 @@ int oracle_bicgstab(void* h, const double* b, double* x, double tol, int maxit, 
 }
 
 void oracle_free(void* h) { delete (Hierarchy*)h; }
+
+// threads the OpenMP build uses (returns the count in effect; 1 in the serial
+// build)
+int oracle_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
 
 }  // extern "C"

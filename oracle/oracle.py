@@ -20,7 +20,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "amg_oracle.cpp")
 _OUT = os.path.join(_HERE, "_build", "liboracle.so")
+_OUT_OMP = os.path.join(_HERE, "_build", "liboracle_omp.so")
 _lib = None
+_lib_omp = None
 
 # Default parameters of the reading documented in the oracle source:
 # delta = 1/3, beta = 1e-5, omega = 1.6, s_min = 2^d, s_max = 3 * 2^(d-1),
@@ -44,22 +46,25 @@ def _param_array(p: dict) -> np.ndarray:
     return np.array([float(p.get(k, 0)) for k in _ORDER], dtype=np.float64)
 
 
-def build(force: bool = False) -> str:
-    """Compile the oracle with g++ (no FMA contraction, plain -O2)."""
-    if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
-        os.makedirs(os.path.dirname(_OUT), exist_ok=True)
-        tmp = _OUT + f".tmp{os.getpid()}"
+def build(force: bool = False, openmp: bool = False) -> str:
+    """Compile the oracle with g++ (no FMA contraction, plain -O2); openmp:
+    the same source with -fopenmp, for the CPU baseline on all host cores."""
+    out = _OUT_OMP if openmp else _OUT
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        os.makedirs(os.path.dirname(out), exist_ok=True)
+        tmp = out + f".tmp{os.getpid()}"
+        flags = ["-fopenmp"] if openmp else []
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-ffp-contract=off", "-fPIC",
-                               "-shared", _SRC, "-o", tmp])
-        os.replace(tmp, _OUT)
-    return _OUT
+                               *flags, "-shared", _SRC, "-o", tmp])
+        os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+def _load(openmp: bool = False):
+    global _lib, _lib_omp
+    if (_lib_omp if openmp else _lib) is not None:
+        return _lib_omp if openmp else _lib
+    lib = ctypes.CDLL(build(openmp=openmp))
     P = ctypes.c_void_p
     I = ctypes.c_int
     D = ctypes.c_double
@@ -83,8 +88,18 @@ def _load():
     lib.oracle_bicgstab.argtypes = [P, P, P, D, I, P]
     lib.oracle_bicgstab.restype = I
     lib.oracle_free.argtypes = [P]
-    _lib = lib
+    lib.oracle_threads.argtypes = [I]
+    lib.oracle_threads.restype = I
+    if openmp:
+        _lib_omp = lib
+    else:
+        _lib = lib
     return lib
+
+
+def threads(n: int = 0) -> int:
+    """Set (n > 0) and return the thread count of the OpenMP build."""
+    return int(_load(openmp=True).oracle_threads(int(n)))
 
 
 def _ptr(a: Optional[np.ndarray]):
@@ -161,13 +176,15 @@ def spmv(rp, ci, va, x):
 class Hierarchy:
     """The oracle's AMG hierarchy for one matrix."""
 
-    def __init__(self, rp, ci, va, params: dict):
+    def __init__(self, rp, ci, va, params: dict, openmp: bool = False):
+        """openmp: run on the OpenMP build of the same source (CPU baseline
+        on all cores; see threads())."""
         rp, ci, va = _csr(rp, ci, va)
         self.n = rp.shape[0] - 1
         self._keep = (rp, ci, va)
         pa = _param_array(params)
         st = ctypes.c_int(0)
-        self._lib = _load()
+        self._lib = _load(openmp)
         self._h = self._lib.oracle_setup(self.n, _ptr(rp), _ptr(ci), _ptr(va), _ptr(pa),
                                          ctypes.byref(st))
         self.status = st.value

@@ -601,3 +601,18 @@ def test_tiled_hierarchy_converges_like_the_sequential_one():
         assert it > 0 and trel <= 1.01e-8
         its.append(it)
     assert its[1] <= 1.3 * its[0] + 1
+
+
+# ---------------------------------------------------------------------------
+# the OpenMP build (CPU baseline on all cores) computes what the serial one does
+# ---------------------------------------------------------------------------
+
+def test_openmp_build_reproduces_the_serial_oracle():
+    p = P.lognormal3d((20, 18, 16), seed=3)
+    O.threads(4)
+    H = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=300))
+    Ho = O.Hierarchy(p.row_ptr, p.col, p.val, _params(3, coarsen_target=300), openmp=True)
+    assert H.num_levels == Ho.num_levels >= 3
+    x, it, rel, _ = H.pcg(p.b, tol=1e-10)
+    xo, ito, relo, _ = Ho.pcg(p.b, tol=1e-10)
+    assert it == ito and rel == relo and np.array_equal(x, xo)
