@@ -23,7 +23,11 @@
  *     No C++ exception ever crosses this interface.
  *   - Matrices are CSR with int32 row pointers and column indices and
  *     float64 values, square, columns sorted and unique within each row,
- *     diagonal stored and positive, symmetric pattern and values.
+ *     diagonal stored and positive, symmetric pattern and values.  The
+ *     pattern is always checked; with the environment variable AMG_CHECK
+ *     set (to anything but 0) amg_setup and amg_aggregate also require
+ *     A_ij == A_ji exactly and return AMG_EINVAL naming the first entry that
+ *     differs.
  *   - Inputs are borrowed for the duration of the call; the library copies
  *     what it keeps.  Outputs are allocated by the caller.
  *   - "device" pointers are CUDA device (or managed) memory on the device
@@ -168,7 +172,8 @@ int amg_params_default(amg_params *p, int32_t dim);
  * matrices, the reordering for the smoother and the coarsest inverse are
  * computed on the GPU.  *out receives a context owning all device memory.
  * Errors: AMG_EINVAL (bad CSR: unsorted/duplicate columns, missing or
- * non-positive diagonal, asymmetric pattern; bad params; coarsest level
+ * non-positive diagonal, asymmetric pattern, asymmetric values under
+ * AMG_CHECK; bad params; coarsest level
  * larger than dense_cap), AMG_ENOTSPD (coarsest pivot <= 0), AMG_ENOMEM,
  * AMG_ECUDA.  On error *out is set to NULL and nothing leaks. */
 int amg_setup(const amg_csr *A, const amg_params *p, amg_ctx **out);

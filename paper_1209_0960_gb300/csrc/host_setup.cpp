@@ -37,6 +37,7 @@
 
 #include <algorithm>
 #include <climits>
+#include <cstdlib>
 #include <cmath>
 #include <functional>
 #include <queue>
@@ -79,6 +80,25 @@ bool validate_csr(const HostCsr& A, std::string& err) {
             const int32_t* e = A.ci.data() + A.rp[j + 1];
             if (!std::binary_search(b, e, i)) {
                 err = "pattern not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")";
+                return false;
+            }
+        }
+    return true;
+}
+
+bool check_values_symmetric(const HostCsr& A, std::string& err) {
+    const char* env = std::getenv("AMG_CHECK");
+    if (!env || !*env || std::string(env) == "0") return true;
+    for (int32_t i = 0; i < A.n; ++i)
+        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+            const int32_t j = A.ci[k];
+            if (j <= i) continue;
+            const int32_t* b = A.ci.data() + A.rp[j];
+            const int32_t* e = A.ci.data() + A.rp[j + 1];
+            const int32_t t = (int32_t)(std::lower_bound(b, e, i) - A.ci.data());
+            if (!(A.va[t] == A.va[k])) {
+                err = "matrix values not symmetric at (" + std::to_string(i) + "," +
+                      std::to_string(j) + ")";
                 return false;
             }
         }

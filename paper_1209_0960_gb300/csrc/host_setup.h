@@ -39,6 +39,12 @@ AggResult aggregate(const HostCsr& A, const amg_params& p);
 // threads; the result does not depend on the thread count.
 AggResult aggregate_tiled(const HostCsr& A, const amg_params& p, int32_t tile, int threads);
 
+// With the environment variable AMG_CHECK set to a value other than 0:
+// every stored A_ij equals A_ji exactly (the method assumes a symmetric
+// matrix; validate_csr checks the pattern only).  Returns false and names the
+// first offending entry otherwise.
+bool check_values_symmetric(const HostCsr& A, std::string& err);
+
 // Greedy colouring in ascending row order; returns the number of colours.
 int32_t greedy_colouring(const HostCsr& A, std::vector<int32_t>& colour);
 

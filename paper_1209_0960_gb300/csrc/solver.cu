@@ -969,7 +969,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     AMG_CUDA_TRY(cudaMemcpy(A0.ci.data(), A->col, sizeof(int32_t) * A->nnz, kind));
     AMG_CUDA_TRY(cudaMemcpy(A0.va.data(), A->val, sizeof(double) * A->nnz, kind));
     std::string err;
-    if (!validate_csr(A0, err)) throw Error{AMG_EINVAL, err};
+    if (!validate_csr(A0, err) || !check_values_symmetric(A0, err)) throw Error{AMG_EINVAL, err};
 
     DevArena setup_mem(s);   // original-order level matrices, freed at the end
     std::vector<DevCsr> dA(1);
@@ -1343,7 +1343,7 @@ static HostCsr host_copy(const amg_csr* A) {
     H.ci.assign(A->col, A->col + A->nnz);
     H.va.assign(A->val, A->val + A->nnz);
     std::string err;
-    if (!validate_csr(H, err)) throw Error{AMG_EINVAL, err};
+    if (!validate_csr(H, err) || !check_values_symmetric(H, err)) throw Error{AMG_EINVAL, err};
     return H;
 }
 

@@ -188,3 +188,20 @@ def test_tiled_aggregation_parameters_are_checked():
     with pytest.raises(amg.AmgError) as e:
         amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
     assert e.value.code == amg.AMG_EINVAL
+
+
+def test_value_symmetry_is_checked_under_amg_check(monkeypatch):
+    p = P.lognormal3d((6, 5, 4), seed=1)
+    va = p.val.copy()
+    # perturb one off-diagonal entry (0, j) but not (j, 0)
+    k = [k for k in range(p.row_ptr[0], p.row_ptr[1]) if p.col[k] != 0][0]
+    va[k] *= 1.0 + 1e-12
+    prm = amg.amg_params_default(3)
+    monkeypatch.delenv("AMG_CHECK", raising=False)
+    amg.amg_aggregate(p.row_ptr, p.col, va, prm)          # pattern only: accepted
+    monkeypatch.setenv("AMG_CHECK", "1")
+    amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)       # symmetric values: accepted
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_aggregate(p.row_ptr, p.col, va, prm)
+    assert e.value.code == amg.AMG_EINVAL
+    assert "not symmetric" in amg.amg_last_error()
