@@ -1,6 +1,7 @@
 """The multi-process path of bench.py on CPU (gloo, world size 2): replicas
 only, a barrier around the timed region and the maximum over ranks."""
 
+import multiprocessing
 import os
 import socket
 import sys
@@ -42,7 +43,7 @@ def _rank_main(rank: int, world: int, port: int, out):
 
 def test_two_rank_max_and_barrier():
     port = _free_port()
-    with mp.Manager() as mgr:
+    with multiprocessing.get_context("spawn").Manager() as mgr:
         out = mgr.dict()
         mp.start_processes(_rank_main, args=(2, port, out), nprocs=2, join=True,
                            start_method="spawn")
