@@ -337,10 +337,10 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
                         DevArena& arena, DevLevel& L, cudaStream_t s);
 
 // Decoupled aggregation (Alg. 4) on the device: the rows of A (original
-// order) split into consecutive tiles of p.aggregation_tile rows, one GPU
-// thread per tile running Algorithm 1 (with the strength of connection) on
-// the tile's induced submatrix; the same result as aggregate_tiled on the
-// host.  Returns the map on the host.
+// order) split into consecutive tiles of p.aggregation_tile rows, one warp per
+// tile running Algorithm 1 (with the strength of connection) on the tile's
+// induced submatrix; the same result as aggregate_tiled on the host.  Returns
+// the map on the host.
 AggResult aggregate_tiles_device(const DevCsr& A, const amg_params& p, cudaStream_t s);
 
 // Dense inverse of the (original-order) coarsest matrix through a Cholesky

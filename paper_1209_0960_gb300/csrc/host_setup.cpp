@@ -29,9 +29,14 @@
 //     non-isolated vertices with it.
 //   * Coarse indices are numbered in the order the aggregates are completed.
 //
-// This implementation keeps incremental state (bucket queues for the global
-// N_na minimum, stamp arrays for set membership, all-pairs distances inside the
-// growing aggregate for the diameter test) so that it runs in near-linear time.
+// This implementation keeps incremental state so that it runs in near-linear
+// time: bucket queues for the global N_na minimum, stamp arrays for set
+// membership, all-pairs distances inside the growing aggregate for the
+// diameter test, and N(a), the aggregates adjacent to it, cons_1 / cons_2 and
+// the strong-link counts of Algorithm 3, all updated as members join.
+//
+// The smoother's colouring is the ascending-order greedy colouring, replaced
+// by DSATUR when that needs fewer colours (smoother_colouring).
 
 #include "host_setup.h"
 
