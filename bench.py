@@ -477,6 +477,7 @@ def run_ours(args, dist: Dist):
                             ("gs_level0", "first_level0", "residual_level0", "prolong",
                              "cg_spmv_dot")},
         "kernels_fp64": prof64,
+        "kernels_fp32": prof32,
         "graph_parts_ms": {
             "fp64": {d["name"]: round(d["total_ms"] / max(1, d["launches"]), 4) for d in graph64},
             "fp32": {d["name"]: round(d["total_ms"] / max(1, d["launches"]), 4) for d in graph32}},

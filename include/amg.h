@@ -85,7 +85,10 @@ typedef struct {
     int32_t dense_cap;        /* largest coarsest level solved densely; default 8192 */
     double min_coarsen_rate;  /* stop when n_l / n_{l+1} < this; default 1.2 */
     int32_t precision;        /* AMG_FP64 or AMG_FP32_IN_FP64 */
-    int32_t flexible_cg;      /* -1: standard CG for FP64, flexible for FP32; 0 / 1 force */
+    int32_t flexible_cg;      /* 1: flexible beta = r.(z - z_old) / rho; 0 or -1 (default):
+                                 standard beta in both precisions (the float32
+                                 V-cycle is symmetric up to rounding; measured on four
+                                 workloads, flexible beta saved no iteration) */
     void *cuda_stream;        /* cudaStream_t for all work; NULL = default stream */
     int32_t launch_overlap;   /* 1 (default): consecutive solve kernels use programmatic
                                  dependent launch (a kernel starts while its predecessor

@@ -755,7 +755,24 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int n, double* __restrict_
     pdl_wait();
     const double alpha = sc->alpha;
     double acc = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    // pairs of elements through 128-bit accesses (the vectors are 256-byte
+    // aligned allocations), the odd last element by the first thread
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    double2* x2 = reinterpret_cast<double2*>(x);
+    double2* r2 = reinterpret_cast<double2*>(r);
+    const double2* p2 = reinterpret_cast<const double2*>(p);
+    const double2* q2 = reinterpret_cast<const double2*>(q);
+#pragma unroll 2
+    for (int i = tid; i < (n >> 1); i += stride) {
+        const double2 xv = x2[i], pv = p2[i], rv = r2[i], qv = q2[i];
+        x2[i] = make_double2(xv.x + alpha * pv.x, xv.y + alpha * pv.y);
+        const double2 v = make_double2(rv.x - alpha * qv.x, rv.y - alpha * qv.y);
+        r2[i] = v;
+        acc = fmad(v.x, v.x, acc);
+        acc = fmad(v.y, v.y, acc);
+    }
+    if ((n & 1) && tid == 0) {
+        const int i = n - 1;
         x[i] += alpha * p[i];
         const double v = r[i] - alpha * q[i];
         r[i] = v;
@@ -776,7 +793,26 @@ __global__ void __launch_bounds__(kBlock) k_cg_rz(int n, const double* __restric
     pdl_launch_dependents();
     pdl_wait();
     double a = 0.0, b = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    // pairs of elements through 128-bit accesses, the odd last element by the
+    // first thread
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const double2* r2 = reinterpret_cast<const double2*>(r);
+    const double2* z2 = reinterpret_cast<const double2*>(z);
+    const double2* o2 = reinterpret_cast<const double2*>(zold);
+#pragma unroll 2
+    for (int i = tid; i < (n >> 1); i += stride) {
+        const double2 rv = r2[i], zv = z2[i];
+        a += rv.x * zv.x;
+        a += rv.y * zv.y;
+        if (mode == kRZFlex) {
+            const double2 ov = o2[i];
+            b += rv.x * (zv.x - ov.x);
+            b += rv.y * (zv.y - ov.y);
+        }
+        if (mode == kRho0) reinterpret_cast<double2*>(p)[i] = zv;
+    }
+    if ((n & 1) && tid == 0) {
+        const int i = n - 1;
         const double ri = r[i], zi = z[i];
         a += ri * zi;
         if (mode == kRZFlex) b += ri * (zi - zold[i]);
@@ -795,7 +831,17 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(int n, const double* __restrict
     pdl_launch_dependents();
     pdl_wait();
     const double beta = sc->beta;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
+    const double2* z2 = reinterpret_cast<const double2*>(z);
+    double2* p2 = reinterpret_cast<double2*>(p);
+#pragma unroll 2
+    for (int i = tid; i < (n >> 1); i += stride) {
+        const double2 zv = z2[i], pv = p2[i];
+        p2[i] = make_double2(zv.x + beta * pv.x, zv.y + beta * pv.y);
+        if (zold) reinterpret_cast<double2*>(zold)[i] = zv;
+    }
+    if ((n & 1) && tid == 0) {
+        const int i = n - 1;
         const double zi = z[i];
         p[i] = zi + beta * p[i];
         if (zold) zold[i] = zi;

@@ -1134,7 +1134,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     AMG_CUDA_TRY(cudaEventCreate(&c->ev1));
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 
-    c->flexible = prm->flexible_cg >= 0 ? prm->flexible_cg : (prm->precision == AMG_FP32_IN_FP64);
+    c->flexible = prm->flexible_cg > 0 ? 1 : 0;
     c->precision = prm->precision;
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
     for (int pr = 0; pr < 2; ++pr) {
@@ -1199,7 +1199,7 @@ int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
         enter(c);
         if (precision == AMG_FP32_IN_FP64) ensure_fp32(c);
         c->precision = precision;
-        c->flexible = flexible_cg >= 0 ? flexible_cg : (precision == AMG_FP32_IN_FP64);
+        c->flexible = flexible_cg > 0 ? 1 : 0;
         AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
         if (c->p.autotune && !c->tuned[precision]) {
             apply_shapes(c);

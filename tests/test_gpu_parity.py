@@ -317,3 +317,21 @@ def test_bicgstab_matches_oracle(pair):
     assert np.linalg.norm(xg - xo) <= 1e-9 * np.linalg.norm(xo)
     r = p.b - O.spmv(p.row_ptr, p.col, p.val, xg)
     assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(p.b)
+
+
+def test_fp32_standard_and_flexible_cg_agree():
+    # the float32 V-cycle is symmetric up to rounding: standard beta (the
+    # default) and flexible beta converge alike
+    p = P.lognormal3d((28, 24, 20), seed=1)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, precision=amg.AMG_FP32_IN_FP64)
+    try:
+        b = torch.from_numpy(p.b).cuda()
+        its = []
+        for flex in (0, 1):
+            solver.set_precision(amg.AMG_FP32_IN_FP64, flex)
+            x, rc, info = solver.solve(b, tol=1e-8, maxit=300)
+            assert rc == amg.AMG_OK and info["true_rel_residual"] <= 1.05e-8
+            its.append(info["iterations"])
+        assert abs(its[0] - its[1]) <= 1
+    finally:
+        solver.close()
