@@ -429,44 +429,33 @@ __device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, N
     return acc;
 }
 
-// k_first on the fine level; also zeroes the next level's right-hand side
-// for the fused residual-restriction kernel.  Blocks with colour-0 rows only
-// need no matrix.  With r_in set (float32 V-cycle inside float64 CG) the
-// right-hand side is the scaled residual b_i = r_i / s_i (isq = 1/s), formed
-// here for each row and neighbour and stored to b for the later passes.
+// First forward pass from a zero guess on a level with the staged kernels,
+// colour 0 (rows [0, c1)): x_i = b_i / A_ii; the colour-1 rows follow as an
+// ordinary staged pass whose later-colour neighbours (positions >= c1) are
+// still zero.  With r_in set (float32 V-cycle inside float64 CG) this kernel
+// first forms the scaled right-hand side b_i = r_i / s_i (isq = 1/s) of every
+// row.  It also zeroes the next level's right-hand side for the fused
+// residual-restriction kernel.
 template <typename T>
-__global__ void __launch_bounds__(kFineBlock) k_fine_first(int c1, int c2, int width, int64_t nslices,
-                                                       const uint16_t* __restrict__ rlen,
-                                                       const int32_t* scol, const T* sval,
-                                                       const T* __restrict__ dinv, T* b,
-                                                       T* x, T* bc_zero, int nc,
-                                                       const double* r_in,
-                                                       const double* __restrict__ isq,
-                                                       int32_t* err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
+__global__ void __launch_bounds__(kBlock) k_fine_first0(int c1, int nb, const T* __restrict__ dinv,
+                                                        T* b, T* x, T* bc_zero, int nc,
+                                                        const double* r_in,
+                                                        const double* __restrict__ isq) {
     pdl_launch_dependents();
-    const FineTile<T> F(0, nslices, width, smem);
-    const bool valid = F.row < c2;
-    const int len = (valid && F.row >= c1) ? (int)__ldcs(rlen + F.row) : 0;
-    const T di = valid ? __ldcs(dinv + F.row) : T(0);
-    const bool staged = (F.slice0 + F.nsl) * 32 > c1;   // block-uniform
-    if (staged && !stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err))
-        return;
     pdl_wait();
-    if (valid) {
+    const int stride = gridDim.x * blockDim.x;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
+        T bi;
         if (r_in) {
-            auto bj = [&](int j) { return (T)(r_in[j] * isq[j]); };
-            const T bi = bj(F.row);
-            b[F.row] = bi;
-            x[F.row] = fine_row<T>(F, len, c1, [&](int j) { return bj(j) * dinv[j]; }, bi) * di;
+            bi = (T)(r_in[i] * isq[i]);
+            b[i] = bi;
         } else {
-            x[F.row] = fine_row<T>(F, len, c1, [&](int j) { return b[j] * dinv[j]; }, b[F.row]) * di;
+            bi = b[i];
         }
+        if (i < c1) x[i] = bi * dinv[i];
     }
     if (bc_zero)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += gridDim.x * blockDim.x)
-            bc_zero[i] = T(0);
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) bc_zero[i] = T(0);
 }
 
 // k_gs_pass on the fine level.  With z_out set (the last pass over these rows
@@ -1043,10 +1032,15 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
     if (L.lpr == kFine) {
-        auto k = k_fine_first<T>;
-        launch_kernel(k, std::max(1, fine_blocks(0, c2)), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1,
-                      c2, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, const_cast<T*>(b),
-                      x, bc_zero, nc, r_in, isq, L.err);
+        const int nb = r_in ? L.n : c1;
+        launch_kernel(k_fine_first0<T>, std::max(1, blocks_for(std::max(nb, nc))), kBlock, 0, s, c1,
+                      nb, A.dinv, const_cast<T*>(b), x, bc_zero, nc, r_in, isq);
+        if (c2 > c1) {
+            auto k = k_fine_pass<T>;
+            launch_kernel(k, fine_blocks(c1, c2), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, c2,
+                          c1, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x,
+                          (double*)nullptr, (const double*)nullptr, L.err);
+        }
         return;
     }
     if (r_in) throw Error{AMG_EINVAL, "the fused float32 entry needs the fine-level kernels"};
