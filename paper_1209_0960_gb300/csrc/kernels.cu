@@ -352,6 +352,55 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
+// Start the copy of `nsl` slices from slice `slice0` (width W) into s_col /
+// s_val, completing on the mbarrier `bar` (initialised here; the caller
+// synchronises the block before any thread waits on it).  Thread 0 only.
+template <typename T>
+__device__ void stage_issue(int64_t slice0, int nsl, int width, const int32_t* scol, const T* sval,
+                            int32_t* s_col, T* s_val, uint64_t* bar) {
+    const uint32_t ub = smem_u32(bar);
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (width == 0 || nsl <= 0) {
+        uint64_t st;
+        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(ub) : "memory");
+        return;
+    }
+    const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
+    const uint32_t bc = ent * 4u, bv = ent * (uint32_t)sizeof(T);
+    const int64_t e0 = slice0 * 32 * width;
+    uint64_t pol, state;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                 : "=l"(state) : "r"(ub), "r"(bc + bv) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(bc), "r"(ub),
+        "l"(pol) : "memory");
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0), "r"(bv), "r"(ub),
+        "l"(pol) : "memory");
+}
+
+// Every thread of the block: wait (bounded) for the copies on `bar`.  Returns
+// false, with AMG_ETIMEOUT recorded in *err, if they have not completed within
+// the spin limit; the decision is one for the whole block, so that no thread
+// waits at a later barrier for threads that gave up.
+__device__ bool stage_wait(uint64_t* bar, int32_t* err) {
+    const uint32_t ub = smem_u32(bar);
+    uint32_t done = 0;
+    for (long long it = 0; it < kStageSpinLimit && !done; ++it)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(ub) : "memory");
+    const int all = __syncthreads_and((int)done);
+    if (!all && threadIdx.x == 0) atomicExch(err, AMG_ETIMEOUT);
+    return all != 0;
+}
+
 // Stage `nsl` slices starting at slice `slice0` (width W) into s_col / s_val.
 // Every thread of the block calls it.  Returns false, with AMG_ETIMEOUT
 // recorded in *err, if the copies have not completed within the spin limit.
@@ -360,41 +409,9 @@ __device__ bool stage_slices(int64_t slice0, int nsl, int width, const int32_t* 
                              const T* sval, int32_t* s_col, T* s_val, uint64_t* bar,
                              int32_t* err) {
     if (width == 0) return true;   // no off-diagonal entries: nothing to stage
-    const uint32_t ub = smem_u32(bar);
-    if (threadIdx.x == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    }
+    if (threadIdx.x == 0) stage_issue(slice0, nsl, width, scol, sval, s_col, s_val, bar);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
-        const uint32_t bc = ent * 4u, bv = ent * (uint32_t)sizeof(T);
-        const int64_t e0 = slice0 * 32 * width;
-        uint64_t pol, state;
-        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                     : "=l"(state) : "r"(ub), "r"(bc + bv) : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(bc), "r"(ub),
-            "l"(pol) : "memory");
-        asm volatile(
-            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0), "r"(bv), "r"(ub),
-            "l"(pol) : "memory");
-    }
-    uint32_t done = 0;
-    for (long long it = 0; it < kStageSpinLimit && !done; ++it)
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}" : "=r"(done) : "r"(ub) : "memory");
-    // one decision for the whole block, so that no thread waits at a later
-    // barrier for threads that gave up
-    const int all = __syncthreads_and((int)done);
-    if (!all && threadIdx.x == 0) atomicExch(err, AMG_ETIMEOUT);
-    return all != 0;
+    return stage_wait(bar, err);
 }
 
 // The block's slices, its shared-memory tiles and this thread's row.
