@@ -62,6 +62,10 @@ def parse_args():
                          "U{16..96}, variance U[1,6]) with Poisson arrivals at --load times the "
                          "measured saturated rate; prints its own JSON line")
     ap.add_argument("--load", type=float, default=0.8)
+    ap.add_argument("--rate", type=float, default=0.0,
+                    help="offered requests/s of the Poisson phase (0: --load times the saturated rate)")
+    ap.add_argument("--host-threads", type=int, default=0,
+                    help="host threads per setup for tiled aggregation (0: all host cores)")
     ap.add_argument("--slots", type=int, default=32)
     ap.add_argument("--setup-threads", type=int, default=0,
                     help="server setup threads (0: host cores - 3)")
@@ -533,7 +537,8 @@ def run_serving(args):
     threads = args.setup_threads or max(1, (os.cpu_count() or 4) - 3)
     srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads,
                      aggregation_tile=args.aggregation_tile,
-                     aggregation_device=args.aggregation_device, autotune=args.autotune)
+                     aggregation_device=args.aggregation_device, autotune=args.autotune,
+                     host_threads=args.host_threads)
 
     def drain(tickets, results):
         while len(results) < len(tickets):
@@ -553,7 +558,7 @@ def run_serving(args):
     sat_rate = len(burst) / (time.perf_counter() - t0)
 
     # phase 2: Poisson arrivals
-    rate = args.load * sat_rate
+    rate = args.rate if args.rate > 0 else args.load * sat_rate
     rng = np.random.default_rng(1)
     arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n_req))
     res2, pending = {}, []
@@ -591,7 +596,7 @@ def run_serving(args):
                       for k in ("queue_ms", "setup_ms", "solve_ms")},
         "peak_in_flight": stats["peak_running"], "slots": args.slots, "setup_threads": threads,
         "aggregation_tile": args.aggregation_tile, "aggregation_device": args.aggregation_device,
-        "autotune": args.autotune,
+        "autotune": args.autotune, "host_threads": args.host_threads,
         "unknowns": {"min": int(min(sizes)), "median": int(np.median(sizes)), "max": int(max(sizes))},
         "dtype": "f32 V-cycle in f64 CG", "data": "synthetic",
         "config": {"workload": "serving stream: independent 3D 7-point FV solves, box sides "

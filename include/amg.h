@@ -104,6 +104,9 @@ typedef struct {
     int32_t aggregation_device; /* with aggregation_tile > 0: 1 = the tiles run on the GPU
                                  (one warp per tile), 0 = on the host threads.  Same
                                  result either way. */
+    int32_t host_threads;     /* host threads of the tiled aggregation (aggregation_tile > 0,
+                                 aggregation_device = 0); 0 (default): one per host core,
+                                 at most 64.  The map does not depend on it. */
     int32_t autotune;         /* 0 (default): launch shapes of the smoother and residual
                                  kernels from fixed rules on the level's row lengths.
                                  1: amg_setup times each candidate shape per level (the

@@ -49,6 +49,8 @@ void check_params(const amg_params& p) {
     if (p.aggregation_device != 0 && p.aggregation_device != 1)
         throw Error{AMG_EINVAL, "aggregation_device must be 0 or 1"};
     if (p.autotune != 0 && p.autotune != 1) throw Error{AMG_EINVAL, "autotune must be 0 or 1"};
+    if (p.host_threads < 0 || p.host_threads > 256)
+        throw Error{AMG_EINVAL, "host_threads must be in [0, 256]"};
 }
 
 // aggregation of one level under the parameters (Algorithm 1, or Alg. 4 in
@@ -57,7 +59,8 @@ AggResult aggregate_level(const HostCsr& A, const DevCsr* Ad, const amg_params& 
     if (p.aggregation_tile <= 0) return aggregate(A, p);
     if (p.aggregation_device && Ad) return aggregate_tiles_device(*Ad, p, s);
     const unsigned hw = std::thread::hardware_concurrency();
-    return aggregate_tiled(A, p, p.aggregation_tile, (int)std::max(1u, std::min(hw, 64u)));
+    const int threads = p.host_threads > 0 ? p.host_threads : (int)std::max(1u, std::min(hw, 64u));
+    return aggregate_tiled(A, p, p.aggregation_tile, threads);
 }
 
 template <typename T>
@@ -1183,6 +1186,7 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->aggregation_tile = 0;
     p->aggregation_device = 0;
     p->autotune = 0;
+    p->host_threads = 0;
     return AMG_OK;
 }
 

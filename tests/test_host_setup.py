@@ -205,3 +205,17 @@ def test_value_symmetry_is_checked_under_amg_check(monkeypatch):
         amg.amg_aggregate(p.row_ptr, p.col, va, prm)
     assert e.value.code == amg.AMG_EINVAL
     assert "not symmetric" in amg.amg_last_error()
+
+
+def test_tiled_aggregation_does_not_depend_on_host_threads():
+    p = P.lognormal3d((16, 15, 14), seed=3)
+    prm = amg.amg_params_default(3)
+    prm.aggregation_tile = 300
+    maps = []
+    for t in (1, 3, 0):
+        prm.host_threads = t
+        maps.append(amg.amg_aggregate(p.row_ptr, p.col, p.val, prm))
+    assert all(m[1] == maps[0][1] and np.array_equal(m[0], maps[0][0]) for m in maps)
+    prm.host_threads = -1
+    with pytest.raises(amg.AmgError):
+        amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
