@@ -229,6 +229,20 @@ int amg_pcg_solve_host(amg_ctx *c, const double *b_host, double *x_host, double 
  * Uses device scratch owned by the context.  Errors: AMG_EINVAL, AMG_ECUDA. */
 int amg_residual_norm(amg_ctx *c, const double *b_dev, const double *x_dev, double *out_norm);
 
+/* Self-test of the library's failure detection.  The staged fine-level
+ * kernels wait for their shared-memory copies on an mbarrier with a bounded
+ * number of polls; when the limit runs out they record AMG_ETIMEOUT in the CG
+ * status word and return instead of hanging.  This call runs that same wait
+ * in a one-block kernel against an mbarrier whose copies are never issued,
+ * with at most `polls` polls (0: the kernels' own limit, 2^18, about one second
+ * on GB300), on
+ * cuda_stream (NULL: the legacy default stream).  *status receives what the
+ * kernel recorded (AMG_ETIMEOUT when the wait ran out) and *elapsed_ms the
+ * kernel's time.  Nothing faults or hangs and the device stays usable.
+ * Errors: AMG_EINVAL (null outputs, polls < 0), AMG_ECUDA. */
+int amg_selftest_bounded_wait(int64_t polls, void *cuda_stream, int32_t *status,
+                              double *elapsed_ms);
+
 /* ||b - A x||_2 for a CSR matrix A held in device memory (A->on_device = 1),
  * with b_dev, x_dev device float64 [n]; the result is written to the device
  * double *norm_dev, asynchronously on cuda_stream (NULL = default stream).

@@ -117,6 +117,8 @@ _SIGNATURES = {
     "amg_hierarchy_info": ([_c_vp, ctypes.POINTER(amg_summary), ctypes.POINTER(amg_level_info), _c_i32], ctypes.c_int),
     "amg_export_level": ([_c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_set_level_shape": ([_c_vp, _c_i32, _c_i32], ctypes.c_int),
+    "amg_selftest_bounded_wait": ([ctypes.c_int64, _c_vp, ctypes.POINTER(_c_i32),
+                                   ctypes.POINTER(_c_dbl)], ctypes.c_int),
     "amg_aggregate": ([ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
     "amg_colour": ([ctypes.POINTER(amg_csr), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
     "amg_profile_enable": ([_c_vp, _c_i32], ctypes.c_int),
@@ -252,6 +254,15 @@ def amg_hierarchy_info(ctx: int):
     levels = (amg_level_info * nl)()
     _check(lib().amg_hierarchy_info(ctx, ctypes.byref(s), levels, nl), "amg_hierarchy_info")
     return struct_dict(s), [struct_dict(l) for l in levels]
+
+
+def amg_selftest_bounded_wait(polls: int, stream=None):
+    """Returns (status recorded by the kernel, kernel milliseconds)."""
+    st = _c_i32(0)
+    ms = _c_dbl(0.0)
+    _check(lib().amg_selftest_bounded_wait(int(polls), stream, ctypes.byref(st), ctypes.byref(ms)),
+           "amg_selftest_bounded_wait")
+    return st.value, ms.value
 
 
 def amg_set_level_shape(ctx: int, l: int, lanes_per_row: int) -> None:

@@ -256,6 +256,11 @@ void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, c
     }
 }
 
+// Runs the staged kernels' bounded wait against an mbarrier that no copy
+// completes (at most `limit` polls; 0: the kernels' own limit) and returns the
+// status the kernel recorded and the kernel's time (kernels.cu).
+void wait_selftest(long long limit, cudaStream_t s, int32_t* status, double* elapsed_ms);
+
 extern int g_reduction_blocks;        // grid of the reduction kernels (SMs x 8)
 int reduction_blocks(int64_t work_threads);
 

@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
 // ---------------------------------------------------------------------------
 constexpr int kFineBlock = 256;                    // rows (threads) per fine-level block
 constexpr int kSlicesPerBlock = kFineBlock / 32;
-constexpr long long kStageSpinLimit = 1LL << 22;
+constexpr long long kStageSpinLimit = 1LL << 18;   // about 1 s of polls on GB300
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -388,10 +388,10 @@ __device__ void stage_issue(int64_t slice0, int nsl, int width, const int32_t* s
 // false, with AMG_ETIMEOUT recorded in *err, if they have not completed within
 // the spin limit; the decision is one for the whole block, so that no thread
 // waits at a later barrier for threads that gave up.
-__device__ bool stage_wait(uint64_t* bar, int32_t* err) {
+__device__ bool stage_wait(uint64_t* bar, int32_t* err, long long limit = kStageSpinLimit) {
     const uint32_t ub = smem_u32(bar);
     uint32_t done = 0;
-    for (long long it = 0; it < kStageSpinLimit && !done; ++it)
+    for (long long it = 0; it < limit && !done; ++it)
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], 0;\n\t"
@@ -412,6 +412,23 @@ __device__ bool stage_slices(int64_t slice0, int nsl, int width, const int32_t* 
     if (threadIdx.x == 0) stage_issue(slice0, nsl, width, scol, sval, s_col, s_val, bar);
     __syncthreads();
     return stage_wait(bar, err);
+}
+
+// Self-test of the bounded wait: an mbarrier that expects 16 bytes of copies
+// that are never issued, so the wait runs out after `limit` polls and records
+// AMG_ETIMEOUT.  No copy is in flight when the block exits.
+__global__ void k_wait_selftest(int32_t* err, long long limit) {
+    __shared__ uint64_t bar;
+    const uint32_t ub = smem_u32(&bar);
+    if (threadIdx.x == 0) {
+        uint64_t state;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                     : "=l"(state) : "r"(ub), "r"(16u) : "memory");
+    }
+    __syncthreads();
+    stage_wait(&bar, err, limit > 0 ? limit : kStageSpinLimit);
 }
 
 // The block's slices, its shared-memory tiles and this thread's row.
@@ -1207,6 +1224,31 @@ void launch_cg_spmv_pq(const DevLevel& L, const double* p, double* q, CgWork& w,
     launch_kernel(k_cg_spmv_pq, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol, L.sval,
                                                           L.diag, p, q, w.partials,
                                                           w.counters + 1, w.sc);
+}
+
+void wait_selftest(long long limit, cudaStream_t s, int32_t* status, double* elapsed_ms) {
+    DevArena mem(s);
+    int32_t* err = mem.alloc<int32_t>(1);
+    AMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int32_t), s));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    AMG_CUDA_TRY(cudaEventCreate(&e0));
+    AMG_CUDA_TRY(cudaEventCreate(&e1));
+    struct Ev {
+        cudaEvent_t a, b;
+        ~Ev() {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+        }
+    } guard{e0, e1};
+    AMG_CUDA_TRY(cudaEventRecord(e0, s));
+    k_wait_selftest<<<1, kBlock, 0, s>>>(err, limit);
+    AMG_CUDA_TRY(cudaGetLastError());
+    AMG_CUDA_TRY(cudaEventRecord(e1, s));
+    AMG_CUDA_TRY(cudaMemcpyAsync(status, err, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    AMG_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *elapsed_ms = ms;
 }
 
 void launch_cg_update(int n, double* x, double* r, const double* p, const double* q, CgWork& w,

@@ -1351,6 +1351,14 @@ static HostCsr host_copy(const amg_csr* A) {
     return H;
 }
 
+int amg_selftest_bounded_wait(int64_t polls, void* cuda_stream, int32_t* status,
+                              double* elapsed_ms) {
+    return Guard::run([&] {
+        if (!status || !elapsed_ms || polls < 0) throw Error{AMG_EINVAL, "null output or polls < 0"};
+        wait_selftest((long long)polls, static_cast<cudaStream_t>(cuda_stream), status, elapsed_ms);
+    });
+}
+
 int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row) {
     return Guard::run([&] {
         if (!c) throw Error{AMG_EINVAL, "null context"};

@@ -219,3 +219,9 @@ def test_tiled_aggregation_does_not_depend_on_host_threads():
     prm.host_threads = -1
     with pytest.raises(amg.AmgError):
         amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
+
+
+def test_bounded_wait_selftest_rejects_bad_arguments():
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_selftest_bounded_wait(-1)
+    assert e.value.code == amg.AMG_EINVAL
