@@ -104,10 +104,14 @@ class Dist:
         if self.world > 1:
             import torch.distributed as dist
             import torch
+            from datetime import timedelta
             backend = "nccl" if torch.cuda.is_available() else "gloo"
             if backend == "nccl":
                 torch.cuda.set_device(self.local_rank)
-            dist.init_process_group(backend)
+            # a rank that dies makes the others' next collective fail within
+            # this time instead of waiting forever
+            timeout = float(os.environ.get("BENCH_PG_TIMEOUT_S", "900"))
+            dist.init_process_group(backend, timeout=timedelta(seconds=timeout))
             self.pg = dist
 
     def barrier(self):

@@ -48,3 +48,42 @@ def test_two_rank_max_and_barrier():
         mp.start_processes(_rank_main, args=(2, port, out), nprocs=2, join=True,
                            start_method="spawn")
         assert dict(out) == {0: 20.0, 1: 20.0}
+
+
+def _rank_dies(rank: int, world: int, port: int, out):
+    os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
+                      MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), BENCH_PG_TIMEOUT_S="20")
+    sys.path.insert(0, ROOT)
+    import bench
+    d = bench.Dist()
+    if rank == 1:
+        os._exit(3)                 # leaves between steps, with nothing in flight
+    try:
+        d.barrier()
+        d.max(1.0)
+        out[rank] = "no error"
+    except Exception as e:          # the peer's loss surfaces as an error
+        out[rank] = type(e).__name__
+    finally:
+        try:
+            d.close()
+        except Exception:
+            pass
+
+
+def test_a_dead_rank_ends_the_others_collectives_with_an_error():
+    port = _free_port()
+    ctx = multiprocessing.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        procs = [ctx.Process(target=_rank_dies, args=(r, 2, port, out)) for r in range(2)]
+        for pr in procs:
+            pr.start()
+        for pr in procs:
+            pr.join(timeout=120)
+        alive = [pr for pr in procs if pr.is_alive()]
+        for pr in alive:
+            pr.kill()
+        assert not alive, "the surviving rank hung"
+        assert procs[1].exitcode == 3
+        assert 0 in out and out[0] != "no error"
