@@ -599,7 +599,8 @@ AggResult aggregate_tiles_device(const DevCsr& A, const amg_params& p, cudaStrea
     for (int32_t i = 0; i < n; ++i) maxdeg = std::max(maxdeg, rp[i + 1] - rp[i]);
     DevArena mem(s);
     TileScratch S{};
-    S.maxa = std::max(p.s_max, p.s_min) + 2;
+    // an aggregate holds at most max(s_min, s_max) rows, and never more than a tile
+    S.maxa = std::min(std::max(p.s_max, p.s_min), tile) + 2;
     // N(a) lies inside the tile and within the neighbourhoods of the members
     S.maxna = (int32_t)std::min<int64_t>((int64_t)S.maxa * std::max(1, maxdeg), tile);
     S.diag = mem.alloc<double>(n);
