@@ -478,6 +478,7 @@ def run_ours(args, dist: Dist):
                   "operator_complexity": summary["operator_complexity"],
                   "level_n": [l["n"] for l in levels],
                   "autotune": args.autotune, "autotune_ms": summary["autotune_ms"],
+                  "coarsest_inverse_ms": summary["coarsest_inverse_ms"],
                   "lanes_per_row": [l["lanes_per_row"] for l in levels[:-1]],
                   "colours": [l["ncolours"] for l in levels[:-1]]},
         "roofline": roofline,

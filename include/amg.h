@@ -158,6 +158,8 @@ typedef struct {
                                      host_setup_ms) */
     double autotune_ms;           /* launch-shape tuning (part of gpu_other_ms; 0 when
                                      autotune = 0 or every level came from the cache) */
+    double coarsest_inverse_ms;   /* Cholesky factorisation and explicit inverse of the
+                                     coarsest level (part of gpu_other_ms) */
 } amg_summary;
 
 /* Per-kernel-class record of the profiler (amg_profile_*). */

@@ -68,7 +68,8 @@ class amg_summary(ctypes.Structure):
                 ("gpu_galerkin_ms", _c_dbl), ("gpu_other_ms", _c_dbl), ("total_setup_ms", _c_dbl),
                 ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
                 ("pcg_iter_bytes_fp64", _c_dbl), ("pcg_iter_bytes_fp32", _c_dbl),
-                ("aggregation_ms", _c_dbl), ("autotune_ms", _c_dbl)]
+                ("aggregation_ms", _c_dbl), ("autotune_ms", _c_dbl),
+                ("coarsest_inverse_ms", _c_dbl)]
 
 
 class amg_kernel_stat(ctypes.Structure):

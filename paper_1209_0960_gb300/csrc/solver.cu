@@ -1093,8 +1093,10 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     }
     // coarsest level: dense inverse
     c->Ainv = c->mem.alloc<double>((size_t)c->nL * c->nL);
+    const double t_inv0 = now_ms();
     if (!dense_inverse_device(dA[nlev - 1], c->Ainv, s))
         throw Error{AMG_ENOTSPD, "coarsest matrix is not positive definite"};
+    const double inverse_ms = now_ms() - t_inv0;
 
     // level-0 CG state (c->hl has grown: take the level-0 matrix afresh)
     const HostCsr& A0f = c->hl[0].A;
@@ -1147,6 +1149,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     const double tune_ms = prm->autotune ? autotune_shapes(c.get()) : 0.0;
     fill_info(c.get());
     c->summary.autotune_ms = tune_ms;
+    c->summary.coarsest_inverse_ms = inverse_ms;
     c->summary.host_setup_ms = host_ms;
     c->summary.aggregation_ms = agg_ms;
     c->summary.gpu_galerkin_ms = galerkin_ms;
