@@ -158,3 +158,26 @@ def test_ragged_tiny_grid_many_levels():
     rp, ci, va, b = P.assemble_fv(K, bc=[(1.0, 0.0), (None, None)])
     s, levels = _check_against_oracle(rp, ci, va, b, 2, coarsen_target=2, min_coarsen_rate=1.0)
     assert s["num_levels"] >= 3
+
+
+def test_device_resident_matrix_gives_the_same_hierarchy():
+    p = P.lognormal3d((16, 15, 14), seed=8)
+    host = amg.AMG(p.row_ptr, p.col, p.val, dim=3, coarsen_target=100)
+    dev = amg.AMG(torch.from_numpy(p.row_ptr).cuda(), torch.from_numpy(p.col).cuda(),
+                  torch.from_numpy(p.val).cuda(), dim=3, coarsen_target=100)
+    try:
+        sh, _ = host.info()
+        sd, _ = dev.info()
+        assert sh["num_levels"] == sd["num_levels"]
+        for l in range(sh["num_levels"]):
+            a, b = host.level(l), dev.level(l)
+            assert np.array_equal(a["row_ptr"], b["row_ptr"]) and np.array_equal(a["col"], b["col"])
+            assert np.array_equal(a["val"].view(np.uint64), b["val"].view(np.uint64))
+        bt = torch.from_numpy(p.b).cuda()
+        x1, rc1, i1 = host.solve(bt, tol=1e-10)
+        x2, rc2, i2 = dev.solve(bt, tol=1e-10)
+        assert rc1 == rc2 == amg.AMG_OK and i1["iterations"] == i2["iterations"]
+        assert torch.equal(x1, x2)
+    finally:
+        host.close()
+        dev.close()
