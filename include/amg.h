@@ -37,6 +37,11 @@
  *     that return results to the host synchronise that stream; amg_vcycle
  *     does not (its output is ready when the stream reaches that point).
  *   - Vectors passed to the library use the caller's row numbering.
+ *   - Threads: different contexts may be used from different threads at the
+ *     same time (the server does so); one context must not be used by two
+ *     threads at once.  Setup, aggregation and colouring calls are
+ *     reentrant.  The process-wide state (the tuned-shape cache, kernel
+ *     attributes) is guarded internally.
  */
 #ifndef AMG_H
 #define AMG_H
