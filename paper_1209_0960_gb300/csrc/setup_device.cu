@@ -141,76 +141,220 @@ __global__ void k_dense_from_csr(int n, const int32_t* __restrict__ rp, const in
     for (int k = rp[i]; k < rp[i + 1]; ++k) M[(size_t)i * n + ci[k]] = va[k];
 }
 
-// L_jj = sqrt(M_jj - sum_{k<j} L_jk^2); one warp
-__global__ void k_chol_diag(int n, int j, double* __restrict__ L, int* __restrict__ err) {
+// ---------------------------------------------------------------------------
+// Dense inverse of the coarsest matrix M (n x n, row-major), float64:
+// blocked Cholesky M = L L^T in 32-column panels, then Y = L^-1 by blocked
+// forward substitution and M^-1 = Y^T Y.  Work is n^3/6 fused multiply-adds
+// per phase, almost all of it in 64 x 64 (or 32 x 32) output tiles staged in
+// shared memory.  Only the lower triangle of the working matrix W is read.
+// ---------------------------------------------------------------------------
+constexpr int kPanel = 32;
+
+// Factor the diagonal block W[k0.., k0..] (m <= 32 rows) in shared memory,
+// one warp, lane = row; write L_kk back (upper part zero) and D = L_kk^-1 to
+// Dk (32 x 32, row-major).  A pivot <= 0 sets *err and continues with 1.
+__global__ void k_potrf_block(int n, int k0, double* __restrict__ W, double* __restrict__ Dk,
+                              int* __restrict__ err) {
+    __shared__ double T[kPanel][kPanel + 1];
+    __shared__ double Y[kPanel][kPanel + 1];
     const int lane = threadIdx.x;
-    const double* row = L + (size_t)j * n;
-    double s = 0.0;
-    for (int k = lane; k < j; k += 32) s += row[k] * row[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) {
-        const double d = row[j] - s;
-        if (!(d > 0.0)) {
-            *err = 1;
-            L[(size_t)j * n + j] = 1.0;
-        } else {
-            L[(size_t)j * n + j] = sqrt(d);
+    const int m = min(kPanel, n - k0);
+    for (int r = 0; r < kPanel; ++r)
+        T[r][lane] = (r < m && lane <= r) ? W[(size_t)(k0 + r) * n + k0 + lane] : 0.0;
+    __syncwarp();
+    for (int j = 0; j < m; ++j) {
+        if (lane == j) {
+            double d = T[j][j];
+            if (!(d > 0.0)) {
+                *err = 1;
+                d = 1.0;
+            }
+            T[j][j] = sqrt(d);
+        }
+        __syncwarp();
+        if (lane > j && lane < m) T[lane][j] /= T[j][j];
+        __syncwarp();
+        if (lane > j && lane < m)
+            for (int l = j + 1; l <= lane; ++l) T[lane][l] -= T[lane][j] * T[l][j];
+        __syncwarp();
+    }
+    // column `lane` of L_kk^-1: y_c = 1/L_cc, y_i = -(sum_{c<=t<i} L_it y_t)/L_ii
+    const int c = lane;
+    for (int i = 0; i < kPanel; ++i) Y[i][c] = 0.0;
+    if (c < m) {
+        Y[c][c] = 1.0 / T[c][c];
+        for (int i = c + 1; i < m; ++i) {
+            double sum = 0.0;
+            for (int t = c; t < i; ++t) sum += T[i][t] * Y[t][c];
+            Y[i][c] = -sum / T[i][i];
         }
     }
-}
-
-// L_ij = (M_ij - sum_{k<j} L_ik L_jk) / L_jj for i > j; one warp per row i
-__global__ void k_chol_col(int n, int j, double* __restrict__ L) {
-    const int lane = threadIdx.x & 31;
-    const int i = j + 1 + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    if (i >= n) return;
-    const double* ri = L + (size_t)i * n;
-    const double* rj = L + (size_t)j * n;
-    double s = 0.0;
-    for (int k = lane; k < j; k += 32) s += ri[k] * rj[k];
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-    if (lane == 0) L[(size_t)i * n + j] = (ri[j] - s) / rj[j];
-}
-
-// U = L^T (row access to the columns of L in the backward substitution)
-__global__ void k_transpose(int n, const double* __restrict__ L, double* __restrict__ U) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= (int64_t)n * n) return;
-    const int i = (int)(t / n), j = (int)(t % n);
-    U[(size_t)j * n + i] = L[t];
-}
-
-// Column c of the inverse, one warp per column: forward L y = e_c (y_k = 0
-// for k < c), then backward L^T x = y, with the column held in shared memory;
-// the lanes split each inner product.
-__global__ void k_chol_inverse(int n, const double* __restrict__ L, const double* __restrict__ U,
-                               double* __restrict__ X) {
-    extern __shared__ double y[];
-    const int c = blockIdx.x;
-    const int lane = threadIdx.x;
-    for (int k = lane; k < n; k += 32) y[k] = 0.0;
     __syncwarp();
-    for (int i = c; i < n; ++i) {
-        const double* li = L + (size_t)i * n;
-        double s = 0.0;
-        for (int k = c + lane; k < i; k += 32) s = __fma_rn(li[k], y[k], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) y[i] = ((i == c) ? 1.0 - s : -s) / li[i];
-        __syncwarp();
+    if (lane < m)
+        for (int r = 0; r < m; ++r) W[(size_t)(k0 + r) * n + k0 + lane] = T[r][lane];
+    for (int r = 0; r < kPanel; ++r) Dk[r * kPanel + lane] = Y[r][lane];
+}
+
+// Panel below the diagonal block: W[i, k0:k0+m] <- W[i, k0:k0+m] D^T for
+// i >= k0 + m (solves x L_kk^T = a), one warp per row, lane = column.
+__global__ void __launch_bounds__(kBlock) k_panel(int n, int k0, int m, double* __restrict__ W,
+                                                  const double* __restrict__ Dk) {
+    __shared__ double D[kPanel][kPanel + 1];
+    const int lane = threadIdx.x & 31;
+    for (int t = threadIdx.x; t < kPanel * kPanel; t += blockDim.x)
+        D[t / kPanel][t % kPanel] = Dk[t];
+    __syncthreads();
+    const int i = k0 + m + (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    if (i >= n) return;
+    double* row = W + (size_t)i * n + k0;
+    const double a = lane < m ? row[lane] : 0.0;
+    double out = 0.0;
+    for (int t = 0; t < m; ++t) {
+        const double at = __shfl_sync(0xffffffffu, a, t);
+        if (t <= lane) out = fma(at, D[lane][t], out);
     }
-    for (int i = n - 1; i >= 0; --i) {
-        const double* ui = U + (size_t)i * n;
-        double s = 0.0;
-        for (int k = i + 1 + lane; k < n; k += 32) s = __fma_rn(ui[k], y[k], s);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-        if (lane == 0) y[i] = (y[i] - s) / ui[i];
-        __syncwarp();
+    if (lane < m) row[lane] = out;
+}
+
+// Tile index of the lower-triangle tile pair number b: (I, J), I >= J.
+__device__ __forceinline__ void tri_pair(int b, int& I, int& J) {
+    I = (int)((sqrt(8.0 * (double)b + 1.0) - 1.0) * 0.5);
+    while ((I + 1) * (I + 2) / 2 <= b) ++I;
+    while (I * (I + 1) / 2 > b) --I;
+    J = b - I * (I + 1) / 2;
+}
+
+// Trailing update W[i][j] -= sum_t P[i][t] P[j][t] over the lower tiles of
+// rows/columns >= r0 (P = the panel W[:, k0:k0+m]); 64 x 64 tiles, 256
+// threads, 4 x 4 outputs per thread.
+__global__ void __launch_bounds__(256) k_syrk(int n, int r0, int k0, int m, double* __restrict__ W) {
+    __shared__ double Pa[64][kPanel + 1];
+    __shared__ double Pb[64][kPanel + 1];
+    int I, J;
+    tri_pair((int)blockIdx.x, I, J);
+    const int i0 = r0 + 64 * I, j0 = r0 + 64 * J;
+    for (int t = threadIdx.x; t < 64 * kPanel; t += blockDim.x) {
+        const int r = t / kPanel, q = t % kPanel;
+        Pa[r][q] = (i0 + r < n && q < m) ? W[(size_t)(i0 + r) * n + k0 + q] : 0.0;
+        Pb[r][q] = (j0 + r < n && q < m) ? W[(size_t)(j0 + r) * n + k0 + q] : 0.0;
     }
-    for (int k = lane; k < n; k += 32) X[(size_t)k * n + c] = y[k];
+    __syncthreads();
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    double acc[4][4] = {};
+    for (int q = 0; q < m; ++q) {
+        double av[4], bv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            av[u] = Pa[ty * 4 + u][q];
+            bv[u] = Pb[tx * 4 + u][q];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+            if (i < n && j < n && j <= i) W[(size_t)i * n + j] -= acc[u][v];
+        }
+}
+
+// Block row i0 of Y = L^-1 (rows i0..i0+m-1), column tile c (32 wide) with
+// c0 < i0: Y[i0.., c0..] = -D_i sum_{c0 <= t < i0} L[i0.., t] Y[t, c0..];
+// the tile c0 = i0 is D_i itself.  256 threads, 4 outputs each.
+__global__ void __launch_bounds__(256) k_trinv_row(int n, int i0, int m, const double* __restrict__ L,
+                                                   double* __restrict__ Y,
+                                                   const double* __restrict__ Di) {
+    __shared__ double A[kPanel][kPanel + 1];
+    __shared__ double B[kPanel][kPanel + 1];
+    const int c0 = kPanel * (int)blockIdx.x;
+    const int tid = threadIdx.x;
+    const int r = tid >> 3, cq = (tid & 7) * 4;   // output row r, columns cq..cq+3
+    if (c0 == i0) {
+        for (int t = tid; t < kPanel * kPanel; t += blockDim.x) {
+            const int rr = t / kPanel, cc = t % kPanel;
+            if (rr < m && c0 + cc < n) Y[(size_t)(i0 + rr) * n + c0 + cc] = Di[t];
+        }
+        return;
+    }
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int t0 = c0; t0 < i0; t0 += kPanel) {
+        for (int t = tid; t < kPanel * kPanel; t += blockDim.x) {
+            const int rr = t / kPanel, cc = t % kPanel;
+            A[rr][cc] = (rr < m) ? L[(size_t)(i0 + rr) * n + t0 + cc] : 0.0;
+            B[rr][cc] = Y[(size_t)(t0 + rr) * n + c0 + cc];
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int q = 0; q < kPanel; ++q) {
+            const double a = A[r][q];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[v] = fma(a, B[q][cq + v], acc[v]);
+        }
+        __syncthreads();
+    }
+    // out = -D_i acc (D_i lower triangular)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) B[r][cq + v] = acc[v];
+    for (int t = tid; t < kPanel * kPanel; t += blockDim.x) A[t / kPanel][t % kPanel] = Di[t];
+    __syncthreads();
+    if (r < m) {
+        double out[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int q = 0; q <= r; ++q) {
+            const double d = A[r][q];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) out[v] = fma(d, B[q][cq + v], out[v]);
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Y[(size_t)(i0 + r) * n + c0 + cq + v] = -out[v];
+    }
+}
+
+// X = Y^T Y for the lower tiles (I >= J) of 64 x 64, mirrored to the upper
+// part: X[i][j] = sum_{k >= 64 I} Y[k][i] Y[k][j] (Y is lower triangular).
+__global__ void __launch_bounds__(256) k_yty(int n, const double* __restrict__ Y, double* __restrict__ X) {
+    __shared__ double Ya[kPanel][64 + 1];
+    __shared__ double Yb[kPanel][64 + 1];
+    int I, J;
+    tri_pair((int)blockIdx.x, I, J);
+    const int i0 = 64 * I, j0 = 64 * J;
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    double acc[4][4] = {};
+    for (int k0 = i0; k0 < n; k0 += kPanel) {
+        for (int t = threadIdx.x; t < kPanel * 64; t += blockDim.x) {
+            const int kk = t / 64, c = t % 64;
+            const bool ok = k0 + kk < n;
+            Ya[kk][c] = (ok && i0 + c < n) ? Y[(size_t)(k0 + kk) * n + i0 + c] : 0.0;
+            Yb[kk][c] = (ok && j0 + c < n) ? Y[(size_t)(k0 + kk) * n + j0 + c] : 0.0;
+        }
+        __syncthreads();
+        for (int q = 0; q < kPanel; ++q) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                av[u] = Ya[q][ty * 4 + u];
+                bv[u] = Yb[q][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+            if (i < n && j < n && j <= i) {
+                X[(size_t)i * n + j] = acc[u][v];
+                X[(size_t)j * n + i] = acc[u][v];
+            }
+        }
 }
 
 // Minv_s = S Minv S with S = diag(sqrt(A_ii)): the inverse of S^-1 A S^-1
@@ -375,23 +519,34 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
 
 bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
     const int n = A.n;
+    const int np = (n + kPanel - 1) / kPanel;
     DevArena tmp(s);
-    double* L = tmp.alloc<double>((size_t)n * n);
+    double* W = tmp.alloc<double>((size_t)n * n);
+    double* Y = tmp.alloc<double>((size_t)n * n);
+    double* D = tmp.alloc<double>((size_t)np * kPanel * kPanel);
     int* err = tmp.alloc<int>(1);
-    AMG_CUDA_TRY(cudaMemsetAsync(L, 0, sizeof(double) * (size_t)n * n, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(W, 0, sizeof(double) * (size_t)n * n, s));
+    AMG_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * n, s));
     AMG_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), s));
-    k_dense_from_csr<<<blocks_for(n), kBlock, 0, s>>>(n, A.rp, A.ci, A.va, L);
-    for (int j = 0; j < n; ++j) {
-        k_chol_diag<<<1, 32, 0, s>>>(n, j, L, err);
-        if (j + 1 < n) k_chol_col<<<blocks_for((int64_t)(n - j - 1) * 32), kBlock, 0, s>>>(n, j, L);
+    k_dense_from_csr<<<blocks_for(n), kBlock, 0, s>>>(n, A.rp, A.ci, A.va, W);
+    // Cholesky, right-looking by 32-column panels
+    for (int p = 0; p < np; ++p) {
+        const int k0 = p * kPanel, m = std::min(kPanel, n - k0), r0 = k0 + m;
+        k_potrf_block<<<1, 32, 0, s>>>(n, k0, W, D + (size_t)p * kPanel * kPanel, err);
+        if (r0 < n) {
+            k_panel<<<blocks_for((int64_t)(n - r0) * 32), kBlock, 0, s>>>(n, k0, m, W,
+                                                                           D + (size_t)p * kPanel * kPanel);
+            const int t = (n - r0 + 63) / 64;
+            k_syrk<<<t * (t + 1) / 2, 256, 0, s>>>(n, r0, k0, m, W);
+        }
     }
-    AMG_CUDA_TRY(cudaGetLastError());
-    double* U = tmp.alloc<double>((size_t)n * n);
-    k_transpose<<<blocks_for((int64_t)n * n), kBlock, 0, s>>>(n, L, U);
-    const size_t smem = sizeof(double) * (size_t)n;
-    if (smem > 40 * 1024)   // the 48 KB default also holds static shared memory
-        raise_dyn_smem(k_chol_inverse, smem);
-    k_chol_inverse<<<n, 32, smem, s>>>(n, L, U, Minv);
+    // Y = L^-1, one launch per block row; then M^-1 = Y^T Y
+    for (int p = 0; p < np; ++p) {
+        const int i0 = p * kPanel, m = std::min(kPanel, n - i0);
+        k_trinv_row<<<p + 1, 256, 0, s>>>(n, i0, m, W, Y, D + (size_t)p * kPanel * kPanel);
+    }
+    const int t = (n + 63) / 64;
+    k_yty<<<t * (t + 1) / 2, 256, 0, s>>>(n, Y, Minv);
     AMG_CUDA_TRY(cudaGetLastError());
     int herr = 0;
     AMG_CUDA_TRY(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
