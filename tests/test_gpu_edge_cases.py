@@ -181,3 +181,44 @@ def test_device_resident_matrix_gives_the_same_hierarchy():
     finally:
         host.close()
         dev.close()
+
+
+def test_indefinite_coarsest_level_is_reported():
+    # symmetric with a positive diagonal but indefinite (eigenvalues 3 and -1):
+    # the coarsest Cholesky meets a non-positive pivot
+    rp = np.array([0, 2, 4], np.int32)
+    ci = np.array([0, 1, 0, 1], np.int32)
+    va = np.array([1.0, 2.0, 2.0, 1.0])
+    with pytest.raises(amg.AmgError) as e:
+        amg.AMG(rp, ci, va, dim=2)
+    assert e.value.code == amg.AMG_ENOTSPD
+    # the device keeps working
+    p = P.laplace2d_random_rhs(16)
+    s = amg.AMG(p.row_ptr, p.col, p.val, dim=2)
+    try:
+        x, rc, info = s.solve(torch.from_numpy(p.b).cuda(), tol=1e-10)
+        assert rc == amg.AMG_OK
+    finally:
+        s.close()
+
+
+@pytest.mark.parametrize("n", [31, 33, 64, 97, 130])
+def test_coarsest_inverse_against_numpy(n):
+    # one directly solved level of n rows: the solve applies the blocked
+    # inverse; its result matches a dense solve (tile edges of 32 and 64)
+    rng = np.random.default_rng(n)
+    B = sp.random(n, n, density=0.2, random_state=int(n)).toarray()
+    M = -(np.abs(B) + np.abs(B.T))
+    np.fill_diagonal(M, 0.0)
+    M += np.diag(-M.sum(axis=1) + 1.0 + rng.random(n))
+    rp, ci, va = _csr(M)
+    solver = amg.AMG(rp, ci, va, dim=3, coarsen_target=1000)
+    try:
+        assert solver.info()[0]["num_levels"] == 1
+        b = rng.standard_normal(n)
+        z = solver.vcycle(torch.from_numpy(b).cuda())
+        torch.cuda.synchronize()
+        ref = np.linalg.solve(M, b)
+        assert np.abs(z.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max() * np.linalg.cond(M)
+    finally:
+        solver.close()
