@@ -151,19 +151,22 @@ __global__ void k_dense_from_csr(int n, const int32_t* __restrict__ rp, const in
 constexpr int kPanel = 32;
 
 // Factor the diagonal block W[k0.., k0..] (m <= 32 rows) in shared memory,
-// one warp, lane = row; write L_kk back (upper part zero) and D = L_kk^-1 to
-// Dk (32 x 32, row-major).  A pivot <= 0 sets *err and continues with 1.
-__global__ void k_potrf_block(int n, int k0, double* __restrict__ W, double* __restrict__ Dk,
-                              int* __restrict__ err) {
+// one thread per entry (32 x 32 threads); write L_kk back (upper part zero)
+// and D = L_kk^-1 to Dk (32 x 32, row-major).  A pivot <= 0 sets *err and
+// continues with 1.
+__global__ void __launch_bounds__(kPanel * kPanel) k_potrf_block(int n, int k0, double* __restrict__ W,
+                                                                 double* __restrict__ Dk,
+                                                                 int* __restrict__ err) {
     __shared__ double T[kPanel][kPanel + 1];
     __shared__ double Y[kPanel][kPanel + 1];
-    const int lane = threadIdx.x;
+    const int r = threadIdx.x / kPanel, c = threadIdx.x % kPanel;
     const int m = min(kPanel, n - k0);
-    for (int r = 0; r < kPanel; ++r)
-        T[r][lane] = (r < m && lane <= r) ? W[(size_t)(k0 + r) * n + k0 + lane] : 0.0;
-    __syncwarp();
+    T[r][c] = (r < m && c <= r) ? W[(size_t)(k0 + r) * n + k0 + c] : 0.0;
+    Y[r][c] = (r == c && r < m) ? 1.0 : 0.0;
+    __syncthreads();
+    // right-looking Cholesky: column j, then the rank-1 update of the rest
     for (int j = 0; j < m; ++j) {
-        if (lane == j) {
+        if (r == j && c == j) {
             double d = T[j][j];
             if (!(d > 0.0)) {
                 *err = 1;
@@ -171,28 +174,21 @@ __global__ void k_potrf_block(int n, int k0, double* __restrict__ W, double* __r
             }
             T[j][j] = sqrt(d);
         }
-        __syncwarp();
-        if (lane > j && lane < m) T[lane][j] /= T[j][j];
-        __syncwarp();
-        if (lane > j && lane < m)
-            for (int l = j + 1; l <= lane; ++l) T[lane][l] -= T[lane][j] * T[l][j];
-        __syncwarp();
+        __syncthreads();
+        if (c == j && r > j && r < m) T[r][j] /= T[j][j];
+        __syncthreads();
+        if (r > j && r < m && c > j && c <= r) T[r][c] -= T[r][j] * T[c][j];
+        __syncthreads();
     }
-    // column `lane` of L_kk^-1: y_c = 1/L_cc, y_i = -(sum_{c<=t<i} L_it y_t)/L_ii
-    const int c = lane;
-    for (int i = 0; i < kPanel; ++i) Y[i][c] = 0.0;
-    if (c < m) {
-        Y[c][c] = 1.0 / T[c][c];
-        for (int i = c + 1; i < m; ++i) {
-            double sum = 0.0;
-            for (int t = c; t < i; ++t) sum += T[i][t] * Y[t][c];
-            Y[i][c] = -sum / T[i][i];
-        }
+    // D = L_kk^-1 by forward elimination on the identity, row j at a time
+    for (int j = 0; j < m; ++j) {
+        if (r == j && c <= j) Y[j][c] /= T[j][j];
+        __syncthreads();
+        if (r > j && r < m && c <= j) Y[r][c] -= T[r][j] * Y[j][c];
+        __syncthreads();
     }
-    __syncwarp();
-    if (lane < m)
-        for (int r = 0; r < m; ++r) W[(size_t)(k0 + r) * n + k0 + lane] = T[r][lane];
-    for (int r = 0; r < kPanel; ++r) Dk[r * kPanel + lane] = Y[r][lane];
+    if (r < m && c < m) W[(size_t)(k0 + r) * n + k0 + c] = T[r][c];
+    Dk[r * kPanel + c] = Y[r][c];
 }
 
 // Panel below the diagonal block: W[i, k0:k0+m] <- W[i, k0:k0+m] D^T for
@@ -262,55 +258,71 @@ __global__ void __launch_bounds__(256) k_syrk(int n, int r0, int k0, int m, doub
         }
 }
 
-// Block row i0 of Y = L^-1 (rows i0..i0+m-1), column tile c (32 wide) with
-// c0 < i0: Y[i0.., c0..] = -D_i sum_{c0 <= t < i0} L[i0.., t] Y[t, c0..];
-// the tile c0 = i0 is D_i itself.  256 threads, 4 outputs each.
-__global__ void __launch_bounds__(256) k_trinv_row(int n, int i0, int m, const double* __restrict__ L,
-                                                   double* __restrict__ Y,
-                                                   const double* __restrict__ Di) {
-    __shared__ double A[kPanel][kPanel + 1];
-    __shared__ double B[kPanel][kPanel + 1];
+// Y = L^-1, right-looking by 32-row block rows.  Row block j of Y holds
+// the running sums S_jc = sum_{c <= t < i} L_jt Y_tc until its turn; then
+// Y_jc = -D_j S_jc for c < j and Y_jj = D_j.
+//
+// Finalise block row i0 (m rows): column tile c = blockIdx.x (c0 <= i0).
+// 32 x 32 threads, one output each.
+__global__ void __launch_bounds__(kPanel * kPanel) k_trinv_final(int n, int i0, int m,
+                                                                 double* __restrict__ Y,
+                                                                 const double* __restrict__ Di) {
+    __shared__ double D[kPanel][kPanel + 1];
+    __shared__ double S[kPanel][kPanel + 1];
+    const int r = threadIdx.x / kPanel, c = threadIdx.x % kPanel;
     const int c0 = kPanel * (int)blockIdx.x;
-    const int tid = threadIdx.x;
-    const int r = tid >> 3, cq = (tid & 7) * 4;   // output row r, columns cq..cq+3
+    D[r][c] = Di[r * kPanel + c];
     if (c0 == i0) {
-        for (int t = tid; t < kPanel * kPanel; t += blockDim.x) {
-            const int rr = t / kPanel, cc = t % kPanel;
-            if (rr < m && c0 + cc < n) Y[(size_t)(i0 + rr) * n + c0 + cc] = Di[t];
-        }
+        if (r < m && c0 + c < n) Y[(size_t)(i0 + r) * n + c0 + c] = D[r][c];
         return;
     }
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int t0 = c0; t0 < i0; t0 += kPanel) {
-        for (int t = tid; t < kPanel * kPanel; t += blockDim.x) {
-            const int rr = t / kPanel, cc = t % kPanel;
-            A[rr][cc] = (rr < m) ? L[(size_t)(i0 + rr) * n + t0 + cc] : 0.0;
-            B[rr][cc] = Y[(size_t)(t0 + rr) * n + c0 + cc];
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int q = 0; q < kPanel; ++q) {
-            const double a = A[r][q];
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[v] = fma(a, B[q][cq + v], acc[v]);
-        }
-        __syncthreads();
-    }
-    // out = -D_i acc (D_i lower triangular)
-#pragma unroll
-    for (int v = 0; v < 4; ++v) B[r][cq + v] = acc[v];
-    for (int t = tid; t < kPanel * kPanel; t += blockDim.x) A[t / kPanel][t % kPanel] = Di[t];
+    S[r][c] = (r < m) ? Y[(size_t)(i0 + r) * n + c0 + c] : 0.0;
     __syncthreads();
-    if (r < m) {
-        double out[4] = {0.0, 0.0, 0.0, 0.0};
-        for (int q = 0; q <= r; ++q) {
-            const double d = A[r][q];
+    if (r >= m) return;
+    double out = 0.0;
+    for (int q = 0; q <= r; ++q) out = fma(D[r][q], S[q][c], out);
+    Y[(size_t)(i0 + r) * n + c0 + c] = -out;
+}
+
+// Update after block row i0 is final: S_jc += L_j,i Y_i,c for the block rows
+// j > i0 and column tiles c <= i0, 64 x 64 output tiles of (rows >= i0 + m,
+// columns < i0 + m), K = m; 256 threads, 4 x 4 outputs each.
+__global__ void __launch_bounds__(256) k_trinv_update(int n, int i0, int m, const double* __restrict__ L,
+                                                      double* __restrict__ Y) {
+    __shared__ double Pa[64][kPanel + 1];   // L[j rows, i0 .. i0+m)
+    __shared__ double Pb[kPanel][64 + 1];   // Y[i0 .. i0+m, c columns]
+    const int r0 = i0 + m, ncol = i0 + m;
+    const int tiles_c = (ncol + 63) / 64;
+    const int J = (int)blockIdx.x / tiles_c, C = (int)blockIdx.x % tiles_c;
+    const int j0 = r0 + 64 * J, c0 = 64 * C;
+    for (int t = threadIdx.x; t < 64 * kPanel; t += blockDim.x) {
+        const int rr = t / kPanel, q = t % kPanel;
+        Pa[rr][q] = (j0 + rr < n && q < m) ? L[(size_t)(j0 + rr) * n + i0 + q] : 0.0;
+        const int qq = t / 64, cc = t % 64;
+        Pb[qq][cc] = (qq < m && c0 + cc < ncol) ? Y[(size_t)(i0 + qq) * n + c0 + cc] : 0.0;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+    double acc[4][4] = {};
+    for (int q = 0; q < m; ++q) {
+        double av[4], bv[4];
 #pragma unroll
-            for (int v = 0; v < 4; ++v) out[v] = fma(d, B[q][cq + v], out[v]);
+        for (int u = 0; u < 4; ++u) {
+            av[u] = Pa[ty * 4 + u][q];
+            bv[u] = Pb[q][tx * 4 + u];
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) Y[(size_t)(i0 + r) * n + c0 + cq + v] = -out[v];
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int j = j0 + ty * 4 + u, cc = c0 + tx * 4 + v;
+            if (j < n && cc < ncol) Y[(size_t)j * n + cc] += acc[u][v];
+        }
 }
 
 // X = Y^T Y for the lower tiles (I >= J) of 64 x 64, mirrored to the upper
@@ -532,7 +544,7 @@ bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
     // Cholesky, right-looking by 32-column panels
     for (int p = 0; p < np; ++p) {
         const int k0 = p * kPanel, m = std::min(kPanel, n - k0), r0 = k0 + m;
-        k_potrf_block<<<1, 32, 0, s>>>(n, k0, W, D + (size_t)p * kPanel * kPanel, err);
+        k_potrf_block<<<1, kPanel * kPanel, 0, s>>>(n, k0, W, D + (size_t)p * kPanel * kPanel, err);
         if (r0 < n) {
             k_panel<<<blocks_for((int64_t)(n - r0) * 32), kBlock, 0, s>>>(n, k0, m, W,
                                                                            D + (size_t)p * kPanel * kPanel);
@@ -540,10 +552,14 @@ bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
             k_syrk<<<t * (t + 1) / 2, 256, 0, s>>>(n, r0, k0, m, W);
         }
     }
-    // Y = L^-1, one launch per block row; then M^-1 = Y^T Y
+    // Y = L^-1 (Y starts at zero: the running sums), then M^-1 = Y^T Y
     for (int p = 0; p < np; ++p) {
-        const int i0 = p * kPanel, m = std::min(kPanel, n - i0);
-        k_trinv_row<<<p + 1, 256, 0, s>>>(n, i0, m, W, Y, D + (size_t)p * kPanel * kPanel);
+        const int i0 = p * kPanel, m = std::min(kPanel, n - i0), r0 = i0 + m;
+        k_trinv_final<<<p + 1, kPanel * kPanel, 0, s>>>(n, i0, m, Y, D + (size_t)p * kPanel * kPanel);
+        if (r0 < n) {
+            const int tiles = ((n - r0 + 63) / 64) * ((r0 + 63) / 64);
+            k_trinv_update<<<tiles, 256, 0, s>>>(n, i0, m, W, Y);
+        }
     }
     const int t = (n + 63) / 64;
     k_yty<<<t * (t + 1) / 2, 256, 0, s>>>(n, Y, Minv);
