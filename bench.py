@@ -79,11 +79,13 @@ def parse_args():
                     help="stop coarsening at N rows (0: the library default)")
     ap.add_argument("--lanes-per-row", type=str, default="", metavar="L0,L1,...",
                     help="fixed launch shapes per level instead of tuning (0 = staged "
-                         "kernels, else 1/2/4/8 lanes per row), for reproducible profiles")
+                         "kernels, else 1/2/4/8 lanes per row, with a suffix h for blocks of "
+                         "128 threads, e.g. 0,2h,4h), for reproducible profiles")
     ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
                     help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
     args = ap.parse_args()
-    args.lanes = [int(v) for v in args.lanes_per_row.split(",") if v.strip()]
+    args.lanes = [(int(v.strip().rstrip("h")), 128 if v.strip().endswith("h") else 0)
+                  for v in args.lanes_per_row.split(",") if v.strip()]
     if args.lanes:
         args.autotune = 0
     if args.aggregation_tile < 0:
@@ -302,8 +304,8 @@ def timed_solves(solver, b, x, steps, tol, stream, dist):
 
 
 def apply_lanes(solver, args):
-    for l, lanes in enumerate(args.lanes):
-        solver.set_level_shape(l, lanes)
+    for l, (lanes, threads) in enumerate(args.lanes):
+        solver.set_level_shape(l, lanes, threads)
 
 
 def run_ours(args, dist: Dist):
@@ -480,6 +482,7 @@ def run_ours(args, dist: Dist):
                   "autotune": args.autotune, "autotune_ms": summary["autotune_ms"],
                   "coarsest_inverse_ms": summary["coarsest_inverse_ms"],
                   "lanes_per_row": [l["lanes_per_row"] for l in levels[:-1]],
+                  "threads_per_block": [l["threads_per_block"] for l in levels[:-1]],
                   "colours": [l["ncolours"] for l in levels[:-1]]},
         "roofline": roofline,
         "roofline_level0": {k: kernel_roofline(k) for k in

@@ -144,6 +144,8 @@ typedef struct {
     int32_t lanes_per_row;    /* launch shape of the level's smoother and residual kernels:
                                  0 = one row per thread with the matrix slices staged in
                                  shared memory, else 1, 2, 4 or 8 lanes per row */
+    int32_t threads_per_block; /* threads per block of those kernels with lanes_per_row >= 1
+                                 (256, or 128 when the autotuner chose it) */
 } amg_level_info;
 
 typedef struct {
@@ -287,11 +289,13 @@ int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col
 /* Launch shape of level l's smoother and residual kernels (0 <= l < number of
  * levels - 1; the coarsest level is the dense solve).  lanes_per_row: 0 = one
  * row per thread with the slices staged in shared memory (levels whose longest
- * row has at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row.  Results
- * differ only in the order of floating-point sums.  The CUDA graphs of the
- * context are rebuilt on the next solve.  Errors: AMG_EINVAL (l or
- * lanes_per_row out of range, 0 on a level with longer rows). */
-int amg_set_level_shape(amg_ctx *c, int32_t l, int32_t lanes_per_row);
+ * row has at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row;
+ * threads_per_block: 256 or 128 for lanes_per_row >= 1 (0 means 256; the
+ * staged kernels always use 256).  Results differ only in the order of
+ * floating-point sums.  The CUDA graphs of the context are rebuilt on the next
+ * solve.  Errors: AMG_EINVAL (l, lanes_per_row or threads_per_block out of
+ * range, 0 lanes on a level with longer rows). */
+int amg_set_level_shape(amg_ctx *c, int32_t l, int32_t lanes_per_row, int32_t threads_per_block);
 
 /* Aggregation of one level, exactly as amg_setup runs it (Sec. 2.1): strength
  * of connection (Eq. symmetric_strong1/2) and Algorithm 1 with Algorithms 2

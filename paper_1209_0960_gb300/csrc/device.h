@@ -126,6 +126,7 @@ struct DevLevel {
                                       // level's kernels (one row per thread, slices staged
                                       // in shared memory, width <= kFineMaxWidth), else
                                       // 1, 2, 4 or 8 lanes with batched gathers
+    int32_t block = 256;              // threads per block of the row kernels (lpr >= 1): 256 or 128
     int32_t lpr_wide = 0;             // lanes per row of launches over >= wide_rows rows
     int32_t wide_rows = 0x7fffffff;
     bool fused_restrict = false;      // residual and restriction in one kernel (lpr == 0)

@@ -1007,8 +1007,9 @@ int reduction_blocks(int64_t work_threads) {
     return (int)std::min<int64_t>(b, g_reduction_blocks);
 }
 
-inline int row_blocks(int r0, int r1, int lpr) {
-    return blocks_for((int64_t)(r1 - (r0 & ~31)) * std::max(lpr, 1));
+inline int row_blocks(int r0, int r1, int lpr, int block = kBlock) {
+    const int64_t threads = (int64_t)(r1 - (r0 & ~31)) * std::max(lpr, 1);
+    return (int)((threads + block - 1) / block);
 }
 
 // lanes per row of a launch over `rows` rows: passes over many rows are
@@ -1079,8 +1080,9 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
     }
     if (r_in) throw Error{AMG_EINVAL, "the fused float32 entry needs the fine-level kernels"};
     AMG_LPR_DISPATCH(launch_lpr(L, c2),
-                     (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR)), kBlock,
-                                    0, s, c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
+                     (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR, L.block)),
+                                    L.block, 0, s, c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b,
+                                    x)));
 }
 
 // z_out / isq (fine level only): also write z = x * isq in float64 for the
@@ -1100,8 +1102,8 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, cudaStrea
     }
     if (z_out) throw Error{AMG_EINVAL, "the fused float32 exit needs the fine-level kernels"};
     AMG_LPR_DISPATCH(launch_lpr(L, r1 - r0),
-                     (launch_kernel(k_gs_pass<LPR, T>, row_blocks(r0, r1, LPR), kBlock, 0, s, r0, r1,
-                                    jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
+                     (launch_kernel(k_gs_pass<LPR, T>, row_blocks(r0, r1, LPR, L.block), L.block, 0,
+                                    s, r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
 }
 
 template <typename T>
@@ -1126,9 +1128,9 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
                           L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, r, L.err);
         } else {
             AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1),
-                             (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR), kBlock, 0,
-                                            s, c1, L.n, L.sw, L.rlen, L.scol, A.sval, A.diag, b, x,
-                                            r)));
+                             (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR, L.block),
+                                            L.block, 0, s, c1, L.n, L.sw, L.rlen, L.scol, A.sval,
+                                            A.diag, b, x, r)));
         }
     }
     launch_kernel(k_restrict<T, SC>, blocks_for(L.n_coarse), kBlock, 0, s, L.n_coarse, L.rptr,

@@ -165,6 +165,7 @@ void fill_info(amg_ctx* c) {
         li.vcycle_bytes_fp64 = level_vcycle_bytes(d, last, 8);
         li.vcycle_bytes_fp32 = level_vcycle_bytes(d, last, 4);
         li.lanes_per_row = last ? 0 : d.lpr;
+        li.threads_per_block = last ? 0 : d.block;
         b64 += li.vcycle_bytes_fp64;
         b32 += li.vcycle_bytes_fp32;
         if (l == 0) nnz0 = li.nnz;
@@ -437,14 +438,27 @@ void drop_graphs(amg_ctx* c) {
 
 constexpr int kStaged = 0;   // DevLevel::lpr of the staged one-row-per-thread kernels
 
-bool shape_allowed(const DevLevel& L, int lanes) {
-    if (lanes == kStaged) return L.width <= kFineMaxWidth;
+// A launch shape as one code: lanes per row (0 = staged kernels, 1, 2, 4 or
+// 8) plus kHalfBlock for blocks of 128 instead of 256 threads (row kernels
+// only).
+constexpr int kHalfBlock = 16;
+inline int shape_lanes(int code) { return code & (kHalfBlock - 1); }
+inline int shape_block(int code) { return (code & kHalfBlock) ? 128 : 256; }
+
+bool shape_allowed(const DevLevel& L, int code) {
+    const int lanes = shape_lanes(code);
+    if (code & ~(kHalfBlock | (kHalfBlock - 1))) return false;
+    if (lanes == kStaged) return code == kStaged && L.width <= kFineMaxWidth;
     return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8;
 }
 
-void set_shape(DevLevel& L, int lanes) {
+int shape_of(const DevLevel& L) { return L.lpr | (L.block == 128 ? kHalfBlock : 0); }
+
+void set_shape(DevLevel& L, int code) {
+    const int lanes = shape_lanes(code);
     L.lpr = lanes;
     L.lpr_wide = lanes;
+    L.block = shape_block(code);
     L.fused_restrict = lanes == kStaged && L.fused_ok;
 }
 
@@ -540,7 +554,8 @@ double autotune_shapes(amg_ctx* c) {
         const int rule = L.lpr;
         double t_rule = 1e30, t_best = 1e30;
         int best = rule;
-        for (int lanes : {kStaged, 1, 2, 4, 8}) {
+        for (int lanes : {kStaged, 1, 1 | kHalfBlock, 2, 2 | kHalfBlock, 4, 4 | kHalfBlock, 8,
+                          8 | kHalfBlock}) {
             if (!shape_allowed(L, lanes)) continue;
             set_shape(L, lanes);
             const double t = time_vcycle_from(c, l);
@@ -557,7 +572,7 @@ double autotune_shapes(amg_ctx* c) {
         const int stored = g_shape_cache.emplace(key, best).first->second;
         set_shape(L, shape_allowed(L, stored) ? stored : best);
     }
-    for (int l = 0; l + 1 < nlev; ++l) c->shapes[c->precision][l] = c->dl[l].lpr;
+    for (int l = 0; l + 1 < nlev; ++l) c->shapes[c->precision][l] = shape_of(c->dl[l]);
     c->tuned[c->precision] = true;
     drop_graphs(c);
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1144,7 +1159,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     if (c->precision == AMG_FP32_IN_FP64) ensure_fp32(c.get());
     for (int pr = 0; pr < 2; ++pr) {
         c->shapes[pr].assign(nlev - 1, 0);
-        for (int l = 0; l + 1 < nlev; ++l) c->shapes[pr][l] = c->dl[l].lpr;
+        for (int l = 0; l + 1 < nlev; ++l) c->shapes[pr][l] = shape_of(c->dl[l]);
     }
     const double tune_ms = prm->autotune ? autotune_shapes(c.get()) : 0.0;
     fill_info(c.get());
@@ -1213,7 +1228,10 @@ int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
             c->summary.autotune_ms += autotune_shapes(c);
         }
         apply_shapes(c);
-        for (int l = 0; l + 1 < (int)c->dl.size(); ++l) c->linfo[l].lanes_per_row = c->dl[l].lpr;
+        for (int l = 0; l + 1 < (int)c->dl.size(); ++l) {
+            c->linfo[l].lanes_per_row = c->dl[l].lpr;
+            c->linfo[l].threads_per_block = c->dl[l].block;
+        }
         leave(c);
     });
 }
@@ -1362,20 +1380,24 @@ int amg_selftest_bounded_wait(int64_t polls, void* cuda_stream, int32_t* status,
     });
 }
 
-int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row) {
+int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row, int32_t threads_per_block) {
     return Guard::run([&] {
         if (!c) throw Error{AMG_EINVAL, "null context"};
         if (l < 0 || l >= (int32_t)c->dl.size() - 1)
             throw Error{AMG_EINVAL, "level out of range (the coarsest level has no shape)"};
-        if (!shape_allowed(c->dl[l], lanes_per_row))
-            throw Error{AMG_EINVAL, "lanes_per_row must be 1, 2, 4 or 8, or 0 on a level whose "
-                                    "rows have at most 32 off-diagonals"};
+        if (threads_per_block != 0 && threads_per_block != 256 && threads_per_block != 128)
+            throw Error{AMG_EINVAL, "threads_per_block must be 0, 256 or 128"};
+        const int code = lanes_per_row | (threads_per_block == 128 ? kHalfBlock : 0);
+        if (lanes_per_row < 0 || lanes_per_row > 8 || !shape_allowed(c->dl[l], code))
+            throw Error{AMG_EINVAL, "lanes_per_row must be 1, 2, 4 or 8, or 0 (256 threads) on a "
+                                    "level whose rows have at most 32 off-diagonals"};
         enter(c);
         AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
         drop_graphs(c);
-        set_shape(c->dl[l], lanes_per_row);
-        c->shapes[c->precision][l] = lanes_per_row;
-        c->linfo[l].lanes_per_row = lanes_per_row;
+        set_shape(c->dl[l], code);
+        c->shapes[c->precision][l] = code;
+        c->linfo[l].lanes_per_row = c->dl[l].lpr;
+        c->linfo[l].threads_per_block = c->dl[l].block;
         leave(c);
     });
 }

@@ -50,17 +50,20 @@ def test_every_shape_matches_oracle(case):
         tried = 0
         for l in range(len(levels) - 1):
             rule = levels[l]["lanes_per_row"]
-            for lanes in (0, 1, 2, 4, 8):
+            for lanes, threads in ((0, 0), (1, 0), (2, 0), (4, 0), (8, 0), (1, 128), (4, 128),
+                                   (8, 128)):
                 try:
-                    solver.set_level_shape(l, lanes)
+                    solver.set_level_shape(l, lanes, threads)
                 except amg.AmgError as e:
                     assert lanes == 0 and e.code == amg.AMG_EINVAL
                     continue
-                assert solver.info()[1][l]["lanes_per_row"] == lanes
-                assert _vcycle_err(solver, H, r) <= 1e-12, (l, lanes)
+                info_l = solver.info()[1][l]
+                assert info_l["lanes_per_row"] == lanes
+                assert info_l["threads_per_block"] == (threads or 256)
+                assert _vcycle_err(solver, H, r) <= 1e-12, (l, lanes, threads)
                 tried += 1
             solver.set_level_shape(l, rule)
-        assert tried >= 4 * (len(levels) - 1)
+        assert tried >= 7 * (len(levels) - 1)
         # a mixed assignment through the solve (CUDA graphs rebuilt)
         for l in range(len(levels) - 1):
             solver.set_level_shape(l, (1, 2, 4, 8)[l % 4])
@@ -83,9 +86,10 @@ def test_shape_errors():
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=100)
     try:
         nlev = solver.info()[0]["num_levels"]
-        for l, lanes in ((-1, 4), (nlev - 1, 4), (0, 3), (0, 16)):
+        for l, lanes, threads in ((-1, 4, 0), (nlev - 1, 4, 0), (0, 3, 0), (0, 16, 0), (0, 17, 0),
+                                  (0, 4, 64), (0, 0, 128)):
             with pytest.raises(amg.AmgError) as e:
-                solver.set_level_shape(l, lanes)
+                solver.set_level_shape(l, lanes, threads)
             assert e.value.code == amg.AMG_EINVAL
     finally:
         solver.close()
