@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--aggregation-tile", type=int, default=-1, metavar="T",
                     help="decoupled aggregation (Alg. 4) in tiles of T consecutive rows "
                          "(0: Algorithm 1 over whole levels; default 0, and 4096 with --serving)")
+    ap.add_argument("--coarsest-fp32", type=int, choices=[0, 1], default=0,
+                    help="float32 V-cycle: apply the coarsest inverse as a float32 matrix "
+                         "(default 0: float64 matrix)")
     ap.add_argument("--autotune", type=int, choices=[0, 1], default=1,
                     help="time the launch shapes of every level at setup and keep the fastest "
                          "(0: the fixed rules)")
@@ -321,6 +324,7 @@ def run_ours(args, dist: Dist):
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune,
+                     coarsest_fp32=args.coarsest_fp32,
                      **({"coarsen_target": args.coarsen_target} if args.coarsen_target else {}))
     apply_lanes(solver, args)
     setup_wall = time.perf_counter() - t0
@@ -461,7 +465,8 @@ def run_ours(args, dist: Dist):
         "config": {"workload": WORKLOAD, "grid": args.grid, "unknowns": p.n, "nnz": p.nnz,
                    "tol": args.tol, "l2": "inputs larger than L2 (level-0 matrix "
                    f"{(p.nnz * 12 + 4 * p.n) / 1e6:.0f} MB > 129 MB)",
-                   "parallelism": f"replicas x{dist.world}", "launch_overlap": args.launch_overlap},
+                   "parallelism": f"replicas x{dist.world}", "launch_overlap": args.launch_overlap,
+                   "coarsest_fp32": args.coarsest_fp32},
         "iterations": info64["iterations"],
         "true_rel_residual": info64["true_rel_residual"],
         "fp32_in_fp64": {"ms": ms32, "iterations": info32["iterations"],
@@ -513,7 +518,7 @@ def profile_run(args):
     p = make_problem(args.grid)
     prec = amg.AMG_FP32_IN_FP64 if args.profile_fp32 else amg.AMG_FP64
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap,
-                     precision=prec, autotune=args.autotune)
+                     precision=prec, autotune=args.autotune, coarsest_fp32=args.coarsest_fp32)
     apply_lanes(solver, args)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)

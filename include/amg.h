@@ -112,6 +112,10 @@ typedef struct {
     int32_t host_threads;     /* host threads of the tiled aggregation (aggregation_tile > 0,
                                  aggregation_device = 0); 0 (default): one per host core,
                                  at most 64.  The map does not depend on it. */
+    int32_t coarsest_fp32;    /* with AMG_FP32_IN_FP64: 1 applies the coarsest-level inverse
+                                 (computed in float64 from the float64 Cholesky factor) as
+                                 a float32 matrix with float32 sums, like the rest of the
+                                 float32 V-cycle; 0 (default): the float64 matrix. */
     int32_t autotune;         /* 0 (default): launch shapes of the smoother and residual
                                  kernels from fixed rules on the level's row lengths.
                                  1: amg_setup times each candidate shape per level (the
@@ -140,7 +144,8 @@ typedef struct {
     int32_t n_isolated;       /* isolated vertices, Sec. 2.1 (b) */
     int32_t n_dirichlet;      /* rows without a non-zero off-diagonal */
     double vcycle_bytes_fp64; /* modelled DRAM bytes of this level per FP64 V-cycle */
-    double vcycle_bytes_fp32; /* same for the FP32 V-cycle */
+    double vcycle_bytes_fp32; /* same for the FP32 V-cycle (coarsest inverse at 4 bytes
+                                 an entry with coarsest_fp32) */
     int32_t lanes_per_row;    /* launch shape of the level's smoother and residual kernels:
                                  0 = one row per thread with the matrix slices staged in
                                  shared memory, else 1, 2, 4 or 8 lanes per row */

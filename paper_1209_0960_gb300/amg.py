@@ -47,7 +47,7 @@ class amg_params(ctypes.Structure):
                 ("min_coarsen_rate", _c_dbl), ("precision", _c_i32), ("flexible_cg", _c_i32),
                 ("cuda_stream", _c_vp), ("launch_overlap", _c_i32),
                 ("aggregation_tile", _c_i32), ("aggregation_device", _c_i32),
-                ("host_threads", _c_i32), ("autotune", _c_i32)]
+                ("host_threads", _c_i32), ("coarsest_fp32", _c_i32), ("autotune", _c_i32)]
 
 
 class amg_solve_info(ctypes.Structure):

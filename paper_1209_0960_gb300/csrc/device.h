@@ -291,6 +291,11 @@ void launch_prolong(const DevLevel& L, const double* e, double* x, double omega,
 void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega, cudaStream_t s);
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s);
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s);
+// x = M b with a float32 matrix of row stride ld (a multiple of 4, zero
+// beyond column n) and float32 sums (one warp per row)
+void launch_dense_gemv_f32(int n, int ld, const float* M, const float* b, float* x, cudaStream_t s);
+// out[i*ld + j] = (float) in[i*n + j] for j < n, 0 for n <= j < ld (setup_device.cu)
+void to_float_padded_device(int n, int ld, const double* in, float* out, cudaStream_t s);
 void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s);
 void launch_scatter(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s);
 void launch_to_scaled32(int n, const double* r, const double* isq, float* rhat, cudaStream_t s);
@@ -394,6 +399,8 @@ struct amg_ctx {
     int32_t nL = 0;                   // coarsest size
     double* Ainv = nullptr;           // [nL x nL] inverse of the coarsest matrix
     double* Ainv_s = nullptr;         // [nL x nL] inverse of the scaled coarsest matrix
+    float* Ainv_s32 = nullptr;        // its float32 copy, rows of ld32 floats (coarsest_fp32 only)
+    int ld32 = 0;                     // nL rounded up to a multiple of 4
     double* isq0 = nullptr;           // [n] 1 / sqrt(A_ii) of level 0 (FP32 entry/exit)
     int32_t* perm0 = nullptr;         // [n] device copy of the level-0 order: caller index -> position
     // level-0 CG vectors, smoothing order

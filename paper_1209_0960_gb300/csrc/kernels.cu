@@ -672,6 +672,58 @@ __global__ void __launch_bounds__(kBlock) k_dense_gemv(int n, const double* __re
     if (lane == 0) x[row] = (TB)s;
 }
 
+// Coarsest solve of the float32 V-cycle with the float32 copy of the inverse
+// (coarsest_fp32): rows of ld = n rounded up to 4 floats, zero beyond n, read
+// as float4 beside the matching float4 of b (16-byte aligned; its last
+// partial group read by scalars); one warp per row, float32 products and sums.
+__device__ __forceinline__ float4 b_group(const float* __restrict__ b, int n, int q) {
+    if (4 * q + 3 < n) return reinterpret_cast<const float4*>(b)[q];
+    float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (4 * q < n) {
+        c.x = b[4 * q];
+        if (4 * q + 1 < n) c.y = b[4 * q + 1];
+        if (4 * q + 2 < n) c.z = b[4 * q + 2];
+    }
+    return c;
+}
+
+__global__ void __launch_bounds__(kBlock) k_dense_gemv_f32(int n, int ld, const float* __restrict__ M,
+                                                           const float* __restrict__ b, float* x) {
+    constexpr int kU = 4;   // float4 groups of the row per lane in flight
+    pdl_launch_dependents();
+    const int lane = threadIdx.x & 31;
+    const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+    const int q4 = ld >> 2;
+    const float4* m = reinterpret_cast<const float4*>(M + (size_t)min(row, n - 1) * ld);
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    float4 v[kU];
+#pragma unroll
+    for (int u = 0; u < kU; ++u) v[u] = lane + 32 * u < q4 ? m[lane + 32 * u] : zero;
+    pdl_wait();
+    if (row >= n) return;
+    float acc[kU] = {};
+    for (int q = lane;; q += 32 * kU) {
+        float4 c[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) c[u] = q + 32 * u < q4 ? b_group(b, n, q + 32 * u) : zero;
+        const int qn = q + 32 * kU;
+        float4 w[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) w[u] = qn + 32 * u < q4 ? m[qn + 32 * u] : zero;
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            acc[u] = fmaf(v[u].x, c[u].x, fmaf(v[u].y, c[u].y, fmaf(v[u].z, c[u].z,
+                     fmaf(v[u].w, c[u].w, acc[u]))));
+        if (qn >= q4) break;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) v[u] = w[u];
+    }
+    float t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+    if (lane == 0) x[row] = t;
+}
+
 __global__ void k_gather(int n, const int32_t* __restrict__ idx, const double* x, double* y) {
     pdl_launch_dependents();
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1197,6 +1249,12 @@ void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaS
 
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s) {
     dense_gemv_impl<float>(n, M, b, x, s);
+}
+
+void launch_dense_gemv_f32(int n, int ld, const float* M, const float* b, float* x, cudaStream_t s) {
+    if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(M)) & 15 || ld % 4 || ld < n)
+        throw Error{AMG_EINVAL, "float32 coarsest solve: operands must be 16-byte aligned"};
+    launch_kernel(k_dense_gemv_f32, blocks_for((int64_t)n * 32), kBlock, 0, s, n, ld, M, b, x);
 }
 
 void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s) {

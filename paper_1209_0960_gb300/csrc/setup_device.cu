@@ -570,6 +570,22 @@ bool dense_inverse_device(const DevCsr& A, double* Minv, cudaStream_t s) {
     return herr == 0;
 }
 
+__global__ void k_to_float_padded(int n, int ld, const double* __restrict__ in, float* __restrict__ out) {
+    const size_t count = (size_t)n * ld;
+    for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < count;
+         t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = t / ld, j = t % ld;
+        out[t] = j < (size_t)n ? (float)in[i * n + j] : 0.f;
+    }
+}
+
+void to_float_padded_device(int n, int ld, const double* in, float* out, cudaStream_t s) {
+    const int64_t count = (int64_t)n * ld;
+    k_to_float_padded<<<std::max(1, (int)std::min<int64_t>(blocks_for(count), 1216 * 4)), kBlock, 0, s>>>(
+        n, ld, in, out);
+    AMG_CUDA_TRY(cudaGetLastError());
+}
+
 void scale_inverse_device(int n, const double* diag, const double* Minv, double* Minv_s,
                           cudaStream_t s) {
     k_scale_inverse<<<blocks_for((int64_t)n * n), kBlock, 0, s>>>(n, diag, Minv, Minv_s);

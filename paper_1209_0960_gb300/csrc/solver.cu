@@ -49,6 +49,8 @@ void check_params(const amg_params& p) {
     if (p.aggregation_device != 0 && p.aggregation_device != 1)
         throw Error{AMG_EINVAL, "aggregation_device must be 0 or 1"};
     if (p.autotune != 0 && p.autotune != 1) throw Error{AMG_EINVAL, "autotune must be 0 or 1"};
+    if (p.coarsest_fp32 != 0 && p.coarsest_fp32 != 1)
+        throw Error{AMG_EINVAL, "coarsest_fp32 must be 0 or 1"};
     if (p.host_threads < 0 || p.host_threads > 256)
         throw Error{AMG_EINVAL, "host_threads must be in [0, 256]"};
 }
@@ -132,8 +134,10 @@ double prolong_bytes(const DevLevel& L, int vb, bool scaled) {
 
 // modelled bytes of one V-cycle on a level, following the pass sequence of
 // vcycle64/vcycle32; the coarsest level reads its dense inverse once
-double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb) {
-    if (coarsest) return (double)L.n * L.n * 8.0 + 2.0 * L.n * vb;
+// mb: bytes per entry of the coarsest inverse as applied (8, or 4 for its
+// float32 copy in the float32 V-cycle)
+double level_vcycle_bytes(const DevLevel& L, bool coarsest, int vb, int mb = 8) {
+    if (coarsest) return (double)L.n * L.n * mb + 2.0 * L.n * vb;
     const bool scaled = vb == 4;
     const int C = L.ncolours;
     double t = first_bytes(L, vb);
@@ -163,7 +167,7 @@ void fill_info(amg_ctx* c) {
         li.n_isolated = last ? 0 : h.agg.n_isolated;
         li.n_dirichlet = last ? 0 : h.agg.n_dirichlet;
         li.vcycle_bytes_fp64 = level_vcycle_bytes(d, last, 8);
-        li.vcycle_bytes_fp32 = level_vcycle_bytes(d, last, 4);
+        li.vcycle_bytes_fp32 = level_vcycle_bytes(d, last, 4, c->p.coarsest_fp32 ? 4 : 8);
         li.lanes_per_row = last ? 0 : d.lpr;
         li.threads_per_block = last ? 0 : d.block;
         b64 += li.vcycle_bytes_fp64;
@@ -251,7 +255,10 @@ inline void k_resres(const DevLevel& L, const float* b, const float* x, float* r
 inline void k_prolong(const DevLevel& L, const double* e, double* x, double w, cudaStream_t s) { launch_prolong(L, e, x, w, s); }
 inline void k_prolong(const DevLevel& L, const float* e, float* x, double w, cudaStream_t s) { launch_prolong32(L, e, x, w, s); }
 inline void k_coarsest(amg_ctx* c, const double* b, double* x) { launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream); }
-inline void k_coarsest(amg_ctx* c, const float* b, float* x) { launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream); }
+inline void k_coarsest(amg_ctx* c, const float* b, float* x) {
+    if (c->Ainv_s32) launch_dense_gemv_f32(c->nL, c->ld32, c->Ainv_s32, b, x, c->stream);
+    else launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream);
+}
 
 template <typename T>
 void vcycle(amg_ctx* c, int l, const T* b, T* x) {
@@ -262,7 +269,8 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     DevLevel& L = c->dl[l];
     cudaStream_t s = c->stream;
     if (l == nlev - 1) {
-        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * 8.0 + 2.0 * vb * c->nL);
+        const double mb = (vb == 4 && c->Ainv_s32) ? 4.0 : 8.0;
+        ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * mb + 2.0 * vb * c->nL);
         k_coarsest(c, b, x);
         return;
     }
@@ -381,6 +389,11 @@ void ensure_fp32(amg_ctx* c) {
     }
     c->Ainv_s = c->mem.alloc<double>((size_t)c->nL * c->nL);
     scale_inverse_device(c->nL, c->dl[nlev - 1].diag, c->Ainv, c->Ainv_s, c->stream);
+    if (c->p.coarsest_fp32) {
+        c->ld32 = (c->nL + 3) & ~3;
+        c->Ainv_s32 = c->mem.alloc<float>((size_t)c->nL * c->ld32);
+        to_float_padded_device(c->nL, c->ld32, c->Ainv_s, c->Ainv_s32, c->stream);
+    }
     AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
     c->fp32_ready = true;
 }
@@ -1204,6 +1217,7 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->aggregation_tile = 0;
     p->aggregation_device = 0;
     p->autotune = 0;
+    p->coarsest_fp32 = 0;
     p->host_threads = 0;
     return AMG_OK;
 }

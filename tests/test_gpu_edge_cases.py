@@ -222,3 +222,49 @@ def test_coarsest_inverse_against_numpy(n):
         assert np.abs(z.cpu().numpy() - ref).max() <= 1e-12 * np.abs(ref).max() * np.linalg.cond(M)
     finally:
         solver.close()
+
+
+def test_float32_coarsest_inverse_single_level():
+    # one directly solved level, float32 V-cycle: with coarsest_fp32 the
+    # inverse is applied as a float32 matrix; the result is A^-1 r up to
+    # float32 rounding of the scaled inverse, the right-hand side and the sums
+    n = 130
+    rng = np.random.default_rng(11)
+    B = sp.random(n, n, density=0.2, random_state=11).toarray()
+    M = -(np.abs(B) + np.abs(B.T))
+    np.fill_diagonal(M, 0.0)
+    M += np.diag(-M.sum(axis=1) + 1.0 + rng.random(n))
+    rp, ci, va = _csr(M)
+    b = rng.standard_normal(n)
+    ref = np.linalg.solve(M, b)
+    errs = []
+    for flag in (0, 1):
+        solver = amg.AMG(rp, ci, va, dim=3, coarsen_target=1000, coarsest_fp32=flag,
+                         precision=amg.AMG_FP32_IN_FP64)
+        try:
+            z = solver.vcycle(torch.from_numpy(b).cuda())
+            torch.cuda.synchronize()
+            errs.append(np.abs(z.cpu().numpy() - ref).max() / np.abs(ref).max())
+        finally:
+            solver.close()
+    # float32 unit roundoff 6e-8 times n terms and cond(M)
+    bound = n * 6e-8 * np.linalg.cond(M)
+    assert errs[0] <= bound and errs[1] <= bound
+    assert errs[1] > 0.0
+
+
+@pytest.mark.parametrize("flex", [0, 1])
+def test_float32_coarsest_inverse_converges(flex):
+    p = P.lognormal3d((28, 24, 20), seed=3)
+    b = torch.from_numpy(p.b).cuda()
+    its = []
+    for flag in (0, 1):
+        solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, coarsest_fp32=flag,
+                         precision=amg.AMG_FP32_IN_FP64, flexible_cg=flex)
+        try:
+            x, rc, info = solver.solve(b, tol=1e-8, maxit=300)
+            assert rc == amg.AMG_OK and info["true_rel_residual"] <= 1.05e-8
+            its.append(info["iterations"])
+        finally:
+            solver.close()
+    assert abs(its[0] - its[1]) <= 1
