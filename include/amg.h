@@ -116,6 +116,12 @@ typedef struct {
                                  (computed in float64 from the float64 Cholesky factor) as
                                  a float32 matrix with float32 sums, like the rest of the
                                  float32 V-cycle; 0 (default): the float64 matrix. */
+    int32_t device_loop;      /* 1 (default): amg_pcg_solve runs its iteration loop as one
+                                 CUDA graph with a device-side WHILE node (the loop
+                                 condition is set on the device after each update; no
+                                 iteration waits for the host).  0: the host launches each
+                                 iteration and reads the residual back.  Same launches in
+                                 the same order, so results are identical. */
     int32_t autotune;         /* 0 (default): launch shapes of the smoother and residual
                                  kernels from fixed rules on the level's row lengths.
                                  1: amg_setup times each candidate shape per level (the
@@ -133,6 +139,9 @@ typedef struct {
     double rel_residual;      /* recursively updated ||r_k|| / ||r_0|| */
     double true_rel_residual; /* ||b - A x|| / ||b - A x_0||, recomputed at the end */
     double solve_ms;          /* device time of the whole solve (CUDA events) */
+    int32_t device_loop;      /* 0: the host drove the iterations; 1: they ran as a
+                                 device-side graph loop; 2: the same in plain stream
+                                 order (the runtime refused launch overlap there) */
 } amg_solve_info;
 
 typedef struct {
@@ -223,9 +232,6 @@ int amg_vcycle(amg_ctx *c, const double *r_dev, double *z_dev);
 int amg_pcg_solve(amg_ctx *c, const double *b_dev, double *x_dev, double tol,
                   int32_t maxit, amg_solve_info *info);
 
-/* As amg_pcg_solve with host buffers: copies b and x_0 to the device,
- * solves, copies x back (all on the context stream; pinned buffers make the
- * copies asynchronous DMA).  info->solve_ms includes the copies. */
 /* Preconditioned BiCGSTAB (the Krylov method of the paper's experiments,
  * Sec. 5) with the same V-cycle, two V-cycles per iteration; arguments,
  * stopping rule and errors as amg_pcg_solve (a half iteration that meets the
@@ -234,8 +240,18 @@ int amg_pcg_solve(amg_ctx *c, const double *b_dev, double *x_dev, double tol,
 int amg_bicgstab_solve(amg_ctx *c, const double *b_dev, double *x_dev, double tol,
                        int32_t maxit, amg_solve_info *info);
 
+/* As amg_pcg_solve with host buffers: copies b and x_0 to the device,
+ * solves, copies x back (all on the context stream; pinned buffers make the
+ * copies asynchronous DMA).  info->solve_ms includes the copies. */
 int amg_pcg_solve_host(amg_ctx *c, const double *b_host, double *x_host, double tol,
                        int32_t maxit, amg_solve_info *info);
+
+/* As amg_pcg_solve_host from the initial guess x_0 = 0: x_host is only
+ * written (no x_0 is read or copied to the device), so one vector fewer
+ * crosses to the device.  Results are those of amg_pcg_solve_host with
+ * x_host zeroed.  Errors as amg_pcg_solve. */
+int amg_pcg_solve_host_zero_guess(amg_ctx *c, const double *b_host, double *x_host, double tol,
+                                  int32_t maxit, amg_solve_info *info);
 
 /* ||b - A x||_2 for the level-0 matrix of the context, reduced in a fixed
  * order (deterministic).  b_dev, x_dev: device float64 [n] in the caller's

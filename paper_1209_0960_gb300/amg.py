@@ -47,12 +47,13 @@ class amg_params(ctypes.Structure):
                 ("min_coarsen_rate", _c_dbl), ("precision", _c_i32), ("flexible_cg", _c_i32),
                 ("cuda_stream", _c_vp), ("launch_overlap", _c_i32),
                 ("aggregation_tile", _c_i32), ("aggregation_device", _c_i32),
-                ("host_threads", _c_i32), ("coarsest_fp32", _c_i32), ("autotune", _c_i32)]
+                ("host_threads", _c_i32), ("coarsest_fp32", _c_i32), ("device_loop", _c_i32),
+                ("autotune", _c_i32)]
 
 
 class amg_solve_info(ctypes.Structure):
     _fields_ = [("status", _c_i32), ("iterations", _c_i32), ("rel_residual", _c_dbl),
-                ("true_rel_residual", _c_dbl), ("solve_ms", _c_dbl)]
+                ("true_rel_residual", _c_dbl), ("solve_ms", _c_dbl), ("device_loop", _c_i32)]
 
 
 class amg_level_info(ctypes.Structure):
@@ -113,6 +114,8 @@ _SIGNATURES = {
     "amg_pcg_solve": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
     "amg_bicgstab_solve": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
     "amg_pcg_solve_host": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)], ctypes.c_int),
+    "amg_pcg_solve_host_zero_guess": ([_c_vp, _c_vp, _c_vp, _c_dbl, _c_i32, ctypes.POINTER(amg_solve_info)],
+                                      ctypes.c_int),
     "amg_residual_norm": ([_c_vp, _c_vp, _c_vp, ctypes.POINTER(_c_dbl)], ctypes.c_int),
     "amg_residual_norm_noalloc": ([ctypes.POINTER(amg_csr), _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_hierarchy_info": ([_c_vp, ctypes.POINTER(amg_summary), ctypes.POINTER(amg_level_info), _c_i32], ctypes.c_int),
@@ -228,6 +231,15 @@ def amg_pcg_solve_host(ctx: int, b_host: np.ndarray, x_host: np.ndarray, tol: fl
     info = amg_solve_info()
     rc = lib().amg_pcg_solve_host(ctx, _ptr(b_host), _ptr(x_host), tol, maxit, ctypes.byref(info))
     _check(rc, "amg_pcg_solve_host", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    return rc, info
+
+
+def amg_pcg_solve_host_zero_guess(ctx: int, b_host: np.ndarray, x_host: np.ndarray, tol: float,
+                                  maxit: int):
+    info = amg_solve_info()
+    rc = lib().amg_pcg_solve_host_zero_guess(ctx, _ptr(b_host), _ptr(x_host), tol, maxit,
+                                             ctypes.byref(info))
+    _check(rc, "amg_pcg_solve_host_zero_guess", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
     return rc, info
 
 
@@ -394,8 +406,10 @@ class AMG:
         return x_dev, rc, struct_dict(info)
 
     def solve_host(self, b_host: np.ndarray, x_host: np.ndarray, tol: float = 1e-8,
-                   maxit: int = 500):
-        rc, info = amg_pcg_solve_host(self.ctx, b_host, x_host, tol, maxit)
+                   maxit: int = 500, zero_guess: bool = False):
+        """x_host holds x_0 on entry (ignored with zero_guess) and x on exit."""
+        f = amg_pcg_solve_host_zero_guess if zero_guess else amg_pcg_solve_host
+        rc, info = f(self.ctx, b_host, x_host, tol, maxit)
         return rc, struct_dict(info)
 
     def residual_norm(self, b_dev, x_dev) -> float:

@@ -100,7 +100,7 @@ struct PcgScalars {
     int32_t status;   // 0, or AMG_ENOTSPD
     int32_t flexible;
     int32_t maxit;
-    int32_t pad;
+    int32_t loops;    // device-side loop: conditions evaluated (a bound of its own)
 };
 
 // One level of the hierarchy on the device.  Rows are stored in the level's
@@ -220,6 +220,10 @@ struct CgWork {
 // matrices and index lists fixed at setup, so the overlap hides launch
 // latency and the first dependent loads of each kernel.  Set per calling
 // thread from the context at API entry.
+// Sets the condition of the device-side CG loop (a WHILE graph node) to
+// "not converged, no breakdown, fewer than maxit iterations" from the device
+// scalars; it also counts its own evaluations and stops at maxit.
+void launch_cg_continue(cudaGraphConditionalHandle h, PcgScalars* sc, cudaStream_t s);
 extern thread_local bool t_launch_overlap;
 // grids above this many blocks launch without the overlap: a wide grid that
 // starts early only occupies the SMs its predecessor is still using
@@ -392,6 +396,14 @@ struct amg_ctx {
     cudaGraphExec_t graph_a[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     cudaGraphExec_t graph_b[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
     std::vector<cudaGraphExec_t> graph_from[2];   // V-cycle from level l (profiling), per precision
+    // the whole iteration loop as one graph with a device-side WHILE node,
+    // [precision][flexible]; solve_graph_state 0 = not built yet, 1 = built,
+    // -1 = the runtime refused it (the host-driven loop runs instead)
+    cudaGraphExec_t graph_solve[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};
+    int solve_graph_state[2][2] = {{0, 0}, {0, 0}};
+    cudaStream_t stream_body = nullptr;   // capture stream of the loop body
+    bool solve_graph_plain = false;       // the loop graphs were built without launch overlap
+    int32_t last_device_loop = 0;         // the last PCG solve ran its loop on the device
     bool use_graphs = true;
     amg::DevArena mem;
     std::vector<amg::HostLevel> hl;
@@ -441,6 +453,7 @@ struct amg_ctx {
             for (int b = 0; b < 2; ++b) {
                 if (graph_a[a][b]) cudaGraphExecDestroy(graph_a[a][b]);
                 if (graph_b[a][b]) cudaGraphExecDestroy(graph_b[a][b]);
+                if (graph_solve[a][b]) cudaGraphExecDestroy(graph_solve[a][b]);
             }
         for (int a = 0; a < 2; ++a)
             for (cudaGraphExec_t g : graph_from[a])
@@ -452,6 +465,7 @@ struct amg_ctx {
             cudaStreamSynchronize(stream);
             cudaStreamDestroy(stream);
         }
+        if (stream_body) cudaStreamDestroy(stream_body);
     }
 };
 

@@ -151,6 +151,15 @@ __device__ void finish_reduction(double v0, double v1, double* partials, double*
     }
 }
 
+// Condition of the device-side PCG loop, evaluated after each x/r update:
+// continue while ||r|| > tol ||r_0||, p.Ap > 0 and fewer than maxit
+// iterations.  The evaluation count is a second, independent bound.
+__global__ void k_cg_continue(cudaGraphConditionalHandle h, PcgScalars* sc) {
+    const int32_t loops = ++sc->loops;
+    const bool go = sc->done == 0 && sc->status == 0 && sc->iters < sc->maxit && loops < sc->maxit;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
+}
+
 // ---------------------------------------------------------------------------
 // V-cycle kernels
 // ---------------------------------------------------------------------------
@@ -1249,6 +1258,11 @@ void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaS
 
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s) {
     dense_gemv_impl<float>(n, M, b, x, s);
+}
+
+void launch_cg_continue(cudaGraphConditionalHandle h, PcgScalars* sc, cudaStream_t s) {
+    k_cg_continue<<<1, 1, 0, s>>>(h, sc);
+    AMG_CUDA_TRY(cudaGetLastError());
 }
 
 void launch_dense_gemv_f32(int n, int ld, const float* M, const float* b, float* x, cudaStream_t s) {

@@ -51,6 +51,7 @@ void check_params(const amg_params& p) {
     if (p.autotune != 0 && p.autotune != 1) throw Error{AMG_EINVAL, "autotune must be 0 or 1"};
     if (p.coarsest_fp32 != 0 && p.coarsest_fp32 != 1)
         throw Error{AMG_EINVAL, "coarsest_fp32 must be 0 or 1"};
+    if (p.device_loop != 0 && p.device_loop != 1) throw Error{AMG_EINVAL, "device_loop must be 0 or 1"};
     if (p.host_threads < 0 || p.host_threads > 256)
         throw Error{AMG_EINVAL, "host_threads must be in [0, 256]"};
 }
@@ -440,7 +441,9 @@ void drop_graphs(amg_ctx* c) {
         for (int b = 0; b < 2; ++b) {
             if (c->graph_a[a][b]) cudaGraphExecDestroy(c->graph_a[a][b]);
             if (c->graph_b[a][b]) cudaGraphExecDestroy(c->graph_b[a][b]);
-            c->graph_a[a][b] = c->graph_b[a][b] = nullptr;
+            if (c->graph_solve[a][b]) cudaGraphExecDestroy(c->graph_solve[a][b]);
+            c->graph_a[a][b] = c->graph_b[a][b] = c->graph_solve[a][b] = nullptr;
+            c->solve_graph_state[a][b] = 0;
         }
         for (cudaGraphExec_t& g : c->graph_from[a]) {
             if (g) cudaGraphExecDestroy(g);
@@ -603,7 +606,7 @@ void apply_shapes(amg_ctx* c) {
 
 // One CG iteration is two parts.  A: q = A p, alpha, x/r update, copy of the
 // CG scalars to the host.  B: z = B r, beta, p update.
-void cg_part_a(amg_ctx* c) {
+void cg_part_a(amg_ctx* c, bool copy_back = true) {
     DevLevel& L0 = c->dl[0];
     const int n = L0.n;
     cudaStream_t s = c->stream;
@@ -615,7 +618,8 @@ void cg_part_a(amg_ctx* c) {
         ProfScope ps(c, kKCgUpdate, 48.0 * n);
         launch_cg_update(n, c->x, c->r, c->pv, c->q, c->work, s);
     }
-    AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
+    if (copy_back)
+        AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s));
 }
 
 void cg_part_b(amg_ctx* c) {
@@ -684,6 +688,118 @@ void cg_fill_info(const amg_ctx* c, int status, double rr_true, amg_solve_info* 
     info->iterations = h.iters;
     info->rel_residual = h.rr0 > 0 ? std::sqrt(h.rr / h.rr0) : 0.0;
     info->true_rel_residual = h.rr0 > 0 ? std::sqrt(rr_true / h.rr0) : 0.0;
+    info->device_loop = c->last_device_loop;
+}
+
+// The iteration loop of PCG as one graph: the first direction (z = B r,
+// rho, p = z) and the first update (q = A p, alpha, x, r, ||r||), then a
+// WHILE node whose body is one more iteration (z = B r, beta, p; q = A p,
+// alpha, x, r, ||r||).  A one-thread kernel after each update sets the loop
+// condition from the device scalars, so no iteration waits on the host; the
+// scalars come back once, after the loop.  The launches are those of the
+// host-driven loop, in the same order.  Returns nullptr (and clears the
+// error) when the runtime refuses the graph.
+cudaGraphExec_t build_solve_graph(amg_ctx* c) {
+    if (!c->stream_body)
+        AMG_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream_body, cudaStreamNonBlocking));
+    cudaStream_t s = c->stream;
+    cudaGraph_t g = nullptr;
+    bool body_capturing = false;
+    const auto fail = [&](cudaError_t e) {
+        if (body_capturing) {
+            cudaGraph_t b = nullptr;
+            cudaStreamEndCapture(c->stream_body, &b);   // the body belongs to g
+        }
+        c->stream = s;
+        cudaStreamEndCapture(s, &g);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return e;
+    };
+    const auto ok = [](cudaError_t e) { return e == cudaSuccess; };
+    if (!ok(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal))) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    try {
+        cg_first_direction(c);
+        cg_part_a(c, false);
+        cudaStreamCaptureStatus st;
+        cudaGraph_t cg = nullptr;
+        const cudaGraphNode_t* deps = nullptr;
+        const cudaGraphEdgeData* edges = nullptr;
+        size_t nd = 0;
+        cudaGraphConditionalHandle h;
+        cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, &edges, &nd);
+        if (ok(e)) e = cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault);
+        if (!ok(e)) { fail(e); return nullptr; }
+        launch_cg_continue(h, c->work.sc, s);
+        e = cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, &edges, &nd);
+        cudaGraphNodeParams prm = {};
+        prm.type = cudaGraphNodeTypeConditional;
+        prm.conditional.handle = h;
+        prm.conditional.type = cudaGraphCondTypeWhile;
+        prm.conditional.size = 1;
+        cudaGraphNode_t node = nullptr;
+        if (ok(e)) e = cudaGraphAddNode(&node, cg, deps, edges, nd, &prm);
+        if (ok(e)) e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+        if (ok(e)) e = cudaStreamBeginCaptureToGraph(c->stream_body, prm.conditional.phGraph_out[0], nullptr,
+                                                     nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        if (!ok(e)) { fail(e); return nullptr; }
+        body_capturing = true;
+        c->stream = c->stream_body;
+        cg_part_b(c);
+        cg_part_a(c, false);
+        launch_cg_continue(h, c->work.sc, c->stream);
+        c->stream = s;
+        cudaGraph_t body = nullptr;
+        e = cudaStreamEndCapture(c->stream_body, &body);
+        body_capturing = false;
+        if (!ok(e)) { fail(e); return nullptr; }
+        e = cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s);
+        if (!ok(e)) { fail(e); return nullptr; }
+    } catch (const Error&) {
+        fail(cudaSuccess);   // a launch the capture refused: the host-driven loop runs
+        return nullptr;
+    } catch (...) {
+        fail(cudaSuccess);
+        throw;
+    }
+    if (!ok(cudaStreamEndCapture(s, &g))) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return nullptr;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (!ok(e)) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return ex;
+}
+
+// The solve graph of the context's precision and CG variant, built on first
+// use; nullptr when device loops are off, graph-level profiling times the
+// iteration parts, or the runtime refused the graph.  Should the runtime
+// refuse programmatic dependent launches inside the loop body, the graph is
+// built once more with plain stream order.
+cudaGraphExec_t solve_graph(amg_ctx* c) {
+    if (!c->p.device_loop || !cg_graphs(c) || c->prof.graphs) return nullptr;
+    int& state = c->solve_graph_state[c->precision][c->flexible];
+    cudaGraphExec_t& ex = c->graph_solve[c->precision][c->flexible];
+    if (state == 0) {
+        ex = build_solve_graph(c);
+        if (!ex && t_launch_overlap) {
+            t_launch_overlap = false;
+            ex = build_solve_graph(c);
+            t_launch_overlap = true;
+            if (ex) c->solve_graph_plain = true;
+        }
+        state = ex ? 1 : -1;
+    }
+    return ex;
 }
 
 int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
@@ -691,7 +807,19 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     cg_start(c, tol, maxit);
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
     int status = AMG_OK;
-    if (!c->sc_host->done) {
+    c->last_device_loop = 0;
+    cudaGraphExec_t loop = (!c->sc_host->done && maxit > 0) ? solve_graph(c) : nullptr;
+    if (loop) {
+        // the whole loop on the device: one launch, one wait
+        AMG_CUDA_TRY(cudaGraphLaunch(loop, s));
+        AMG_CUDA_TRY(cudaStreamSynchronize(s));
+        c->last_device_loop = c->solve_graph_plain ? 2 : 1;
+        const PcgScalars& h = *c->sc_host;
+        if (h.status != 0) status = h.status;
+        else if (h.done) status = AMG_OK;
+        else if (h.iters >= maxit) status = AMG_ENOTCONV;
+        else throw Error{AMG_ECUDA, "device-side CG loop stopped before its condition"};
+    } else if (!c->sc_host->done) {
         cg_first_direction(c);
         while (true) {
             if (c->sc_host->iters >= maxit) { status = AMG_ENOTCONV; break; }
@@ -1218,6 +1346,7 @@ int amg_params_default(amg_params* p, int32_t dim) {
     p->aggregation_device = 0;
     p->autotune = 0;
     p->coarsest_fp32 = 0;
+    p->device_loop = 1;
     p->host_threads = 0;
     return AMG_OK;
 }
@@ -1264,7 +1393,8 @@ int amg_vcycle(amg_ctx* c, const double* r_dev, double* z_dev) {
 }
 
 static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int32_t maxit,
-                        amg_solve_info* info, bool host, bool use_bicgstab = false) {
+                        amg_solve_info* info, bool host, bool use_bicgstab = false,
+                        bool zero_guess = false) {
     int status = AMG_OK;
     std::string why;
     int rc = Guard::run([&] {
@@ -1279,12 +1409,14 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         if (host) {
             // stage through the level-0 scratch vectors q (b) and z (x0)
             AMG_CUDA_TRY(cudaMemcpyAsync(c->q, b, sizeof(double) * n, cudaMemcpyHostToDevice, s));
-            AMG_CUDA_TRY(cudaMemcpyAsync(c->z, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+            if (!zero_guess)
+                AMG_CUDA_TRY(cudaMemcpyAsync(c->z, x, sizeof(double) * n, cudaMemcpyHostToDevice, s));
             bd = c->q;
             xd = c->z;
         }
         launch_scatter(n, c->perm0, bd, c->bb, s);
-        launch_scatter(n, c->perm0, xd, c->x, s);
+        if (zero_guess) AMG_CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * n, s));
+        else launch_scatter(n, c->perm0, xd, c->x, s);
         amg_solve_info local{};
         status = use_bicgstab ? bicgstab(c, tol, maxit, &local, why) : pcg(c, tol, maxit, &local);
         if (host) {
@@ -1322,6 +1454,11 @@ int amg_bicgstab_solve(amg_ctx* c, const double* b_dev, double* x_dev, double to
 int amg_pcg_solve_host(amg_ctx* c, const double* b_host, double* x_host, double tol,
                        int32_t maxit, amg_solve_info* info) {
     return solve_common(c, b_host, x_host, tol, maxit, info, true);
+}
+
+int amg_pcg_solve_host_zero_guess(amg_ctx* c, const double* b_host, double* x_host, double tol,
+                                  int32_t maxit, amg_solve_info* info) {
+    return solve_common(c, b_host, x_host, tol, maxit, info, true, false, true);
 }
 
 int amg_residual_norm(amg_ctx* c, const double* b_dev, const double* x_dev, double* out_norm) {

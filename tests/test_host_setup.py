@@ -194,6 +194,12 @@ def test_tiled_aggregation_parameters_are_checked():
         amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
     assert e.value.code == amg.AMG_EINVAL
     assert "coarsest_fp32" in amg.amg_last_error()
+    prm.coarsest_fp32 = 0
+    prm.device_loop = 2
+    with pytest.raises(amg.AmgError) as e:
+        amg.amg_aggregate(p.row_ptr, p.col, p.val, prm)
+    assert e.value.code == amg.AMG_EINVAL
+    assert "device_loop" in amg.amg_last_error()
 
 
 def test_value_symmetry_is_checked_under_amg_check(monkeypatch):
