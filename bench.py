@@ -72,6 +72,9 @@ def parse_args():
     ap.add_argument("--aggregation-tile", type=int, default=-1, metavar="T",
                     help="decoupled aggregation (Alg. 4) in tiles of T consecutive rows "
                          "(0: Algorithm 1 over whole levels; default 0, and 4096 with --serving)")
+    ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
+                    help="run the PCG iteration loop as one graph with a device-side WHILE node "
+                         "(default 1); 0: the host launches each iteration (same kernels, same order)")
     ap.add_argument("--coarsest-fp32", type=int, choices=[0, 1], default=0,
                     help="float32 V-cycle: apply the coarsest inverse as a float32 matrix "
                          "(default 0: float64 matrix)")
@@ -324,7 +327,7 @@ def run_ours(args, dist: Dist):
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune,
-                     coarsest_fp32=args.coarsest_fp32,
+                     coarsest_fp32=args.coarsest_fp32, device_loop=args.device_loop,
                      **({"coarsen_target": args.coarsen_target} if args.coarsen_target else {}))
     apply_lanes(solver, args)
     setup_wall = time.perf_counter() - t0
@@ -469,7 +472,7 @@ def run_ours(args, dist: Dist):
                    "tol": args.tol, "l2": "inputs larger than L2 (level-0 matrix "
                    f"{(p.nnz * 12 + 4 * p.n) / 1e6:.0f} MB > 129 MB)",
                    "parallelism": f"replicas x{dist.world}", "launch_overlap": args.launch_overlap,
-                   "coarsest_fp32": args.coarsest_fp32},
+                   "coarsest_fp32": args.coarsest_fp32, "device_loop": args.device_loop},
         "iterations": info64["iterations"],
         "device_loop": info64.get("device_loop"),
         "true_rel_residual": info64["true_rel_residual"],
@@ -522,7 +525,8 @@ def profile_run(args):
     p = make_problem(args.grid)
     prec = amg.AMG_FP32_IN_FP64 if args.profile_fp32 else amg.AMG_FP64
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap,
-                     precision=prec, autotune=args.autotune, coarsest_fp32=args.coarsest_fp32)
+                     precision=prec, autotune=args.autotune, coarsest_fp32=args.coarsest_fp32,
+                     device_loop=args.device_loop)
     apply_lanes(solver, args)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)
