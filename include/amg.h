@@ -116,12 +116,12 @@ typedef struct {
                                  (computed in float64 from the float64 Cholesky factor) as
                                  a float32 matrix with float32 sums, like the rest of the
                                  float32 V-cycle; 0 (default): the float64 matrix. */
-    int32_t device_loop;      /* 1 (default): amg_pcg_solve runs its iteration loop as one
-                                 CUDA graph with a device-side WHILE node (the loop
-                                 condition is set on the device after each update; no
-                                 iteration waits for the host).  0: the host launches each
-                                 iteration and reads the residual back.  Same launches in
-                                 the same order, so results are identical. */
+    int32_t device_loop;      /* 1 (default): amg_pcg_solve (and a server's solves) run the
+                                 iteration loop as one CUDA graph with a device-side WHILE
+                                 node (the loop condition is set on the device after each
+                                 update; no iteration waits for the host).  0: the host
+                                 launches each iteration and reads the residual back.  Same
+                                 launches in the same order, so results are identical. */
     int32_t autotune;         /* 0 (default): launch shapes of the smoother and residual
                                  kernels from fixed rules on the level's row lengths.
                                  1: amg_setup times each candidate shape per level (the

@@ -375,7 +375,7 @@ void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, c
 
 // State of a CG solve driven one step at a time (pcg_async_*).
 struct AsyncCg {
-    enum State { kIdle, kStarted, kIterating, kFinishing, kDone };
+    enum State { kIdle, kStarted, kIterating, kLooping, kFinishing, kDone };
     State state = kIdle;
     double tol = 0.0;
     int32_t maxit = 0;

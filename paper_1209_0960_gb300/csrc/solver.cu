@@ -989,6 +989,15 @@ int pcg_async_step(amg_ctx* c) {
     switch (a.state) {
         case AsyncCg::kStarted:
             if (h.done) { async_finish(c, AMG_OK); break; }
+            if (cudaGraphExec_t loop = a.maxit > 0 ? solve_graph(c) : nullptr) {
+                // the whole iteration loop on the device; one more wait for this solve
+                AMG_CUDA_TRY(cudaGraphLaunch(loop, c->stream));
+                AMG_CUDA_TRY(cudaEventRecord(a.ev, c->stream));
+                c->last_device_loop = c->solve_graph_plain ? 2 : 1;
+                a.state = AsyncCg::kLooping;
+                break;
+            }
+            c->last_device_loop = 0;
             cg_first_direction(c);
             if (h.iters >= a.maxit) { async_finish(c, AMG_ENOTCONV); break; }
             run_part_a(c);
@@ -1002,6 +1011,12 @@ int pcg_async_step(amg_ctx* c) {
             run_part_b(c);
             run_part_a(c);
             AMG_CUDA_TRY(cudaEventRecord(a.ev, c->stream));
+            break;
+        case AsyncCg::kLooping:
+            if (h.status != 0) async_finish(c, h.status);
+            else if (h.done) async_finish(c, AMG_OK);
+            else if (h.iters >= a.maxit) async_finish(c, AMG_ENOTCONV);
+            else throw Error{AMG_ECUDA, "device-side CG loop stopped before its condition"};
             break;
         case AsyncCg::kFinishing:
             cg_fill_info(c, a.status, *a.rr_host, &a.info);

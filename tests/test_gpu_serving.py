@@ -59,6 +59,7 @@ def test_results_are_the_same_alone_and_in_the_mix():
         rc, x, info, times = res[t]
         assert rc == amg.AMG_OK
         assert info["true_rel_residual"] <= 1.5 * TOL
+        assert info["device_loop"] == 1      # the iteration loop ran as one device-side graph
         r = p.b - O.spmv(p.row_ptr, p.col, p.val, x)
         assert np.linalg.norm(r) <= 1.05 * TOL * np.linalg.norm(p.b)
         assert times["total_ms"] >= times["solve_ms"] >= 0 and times["hbm_bytes"] > 0
@@ -72,7 +73,10 @@ def test_tuned_shapes_and_tiled_aggregation_in_the_mix():
     # other requests solve; shapes of a level signature are shared through the
     # process-wide cache, so a standalone run reproduces each result exactly
     reqs = [P.serving_request(k, lo=12, hi=40) for k in range(60, 84)]
-    server = amg.Server(dim=3, max_slots=8, setup_threads=6, autotune=1, aggregation_tile=512)
+    # (the host-driven iteration loop here: the standalone solves below run the
+    # device-side loop, and the two give the same bits)
+    server = amg.Server(dim=3, max_slots=8, setup_threads=6, autotune=1, aggregation_tile=512,
+                        device_loop=0)
     tickets = [server.submit(p.row_ptr, p.col, p.val, p.b, TOL) for p in reqs]
     res = _drain(server, tickets, timeout_s=300.0)
     st = server.stats()
@@ -83,7 +87,9 @@ def test_tuned_shapes_and_tiled_aggregation_in_the_mix():
         rc, x, info, times = res[t]
         assert rc == amg.AMG_OK, amg.amg_last_error()
         assert info["true_rel_residual"] <= 1.5 * TOL
+        assert info["device_loop"] == 0
         rc1, x1, info1 = _standalone(p, params)
+        assert info1["device_loop"] == 1
         assert rc1 == amg.AMG_OK and info1["iterations"] == info["iterations"]
         assert np.array_equal(x, x1), p.name
 
