@@ -502,7 +502,7 @@ AggResult Aggregation::run() {
                 ++next_id_;
             }
             if (remaining_ == 0) break;
-                int32_t seed = -1;
+            int32_t seed = -1;
             for (int32_t y : na_)
                 if (inU_[y] && (seed < 0 || nna_[y] < nna_[seed] || (nna_[y] == nna_[seed] && y < seed)))
                     seed = y;
