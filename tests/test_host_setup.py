@@ -2,6 +2,7 @@
 declares, input validation, and bit-exact parity of the library's host setup
 (strength of connection, Algorithms 1-3, colouring) with the oracle."""
 
+import ctypes
 import json
 import os
 import re
@@ -239,3 +240,16 @@ def test_bounded_wait_selftest_rejects_bad_arguments():
     with pytest.raises(amg.AmgError) as e:
         amg.amg_selftest_bounded_wait(-1)
     assert e.value.code == amg.AMG_EINVAL
+
+
+@pytest.mark.parametrize("name", ["amg_pcg_solve", "amg_pcg_solve_host",
+                                  "amg_pcg_solve_host_zero_guess", "amg_bicgstab_solve"])
+def test_solve_entry_points_reject_a_null_context(name):
+    # argument checks come before any device work, so they run without a GPU
+    L = amg.lib()
+    b = np.zeros(4)
+    x = np.zeros(4)
+    info = amg.amg_solve_info()
+    rc = getattr(L, name)(None, b.ctypes.data, x.ctypes.data, 1e-8, 10, ctypes.byref(info))
+    assert rc == amg.AMG_EINVAL
+    assert "null" in amg.amg_last_error()
