@@ -559,7 +559,7 @@ def run_serving(args):
     srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads,
                      aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune,
-                     host_threads=args.host_threads)
+                     host_threads=args.host_threads, device_loop=args.device_loop)
 
     def drain(tickets, results):
         while len(results) < len(tickets):
@@ -617,7 +617,7 @@ def run_serving(args):
                       for k in ("queue_ms", "setup_ms", "solve_ms")},
         "peak_in_flight": stats["peak_running"], "slots": args.slots, "setup_threads": threads,
         "aggregation_tile": args.aggregation_tile, "aggregation_device": args.aggregation_device,
-        "autotune": args.autotune, "host_threads": args.host_threads,
+        "autotune": args.autotune, "host_threads": args.host_threads, "device_loop": args.device_loop,
         "unknowns": {"min": int(min(sizes)), "median": int(np.median(sizes)), "max": int(max(sizes))},
         "dtype": "f32 V-cycle in f64 CG", "data": "synthetic",
         "config": {"workload": "serving stream: independent 3D 7-point FV solves, box sides "
