@@ -72,9 +72,10 @@ def parse_args():
     ap.add_argument("--aggregation-tile", type=int, default=-1, metavar="T",
                     help="decoupled aggregation (Alg. 4) in tiles of T consecutive rows "
                          "(0: Algorithm 1 over whole levels; default 0, and 4096 with --serving)")
-    ap.add_argument("--device-loop", type=int, choices=[0, 1], default=1,
-                    help="run the PCG iteration loop as one graph with a device-side WHILE node "
-                         "(default 1); 0: the host launches each iteration (same kernels, same order)")
+    ap.add_argument("--device-loop", type=int, choices=[0, 1], default=None,
+                    help="1: run the PCG iteration loop as one graph with a device-side WHILE node "
+                         "(the solve default); 0: the host launches each iteration (same kernels, "
+                         "same order; the serving default)")
     ap.add_argument("--coarsest-fp32", type=int, choices=[0, 1], default=0,
                     help="float32 V-cycle: apply the coarsest inverse as a float32 matrix "
                          "(default 0: float64 matrix)")
@@ -327,7 +328,8 @@ def run_ours(args, dist: Dist):
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune,
-                     coarsest_fp32=args.coarsest_fp32, device_loop=args.device_loop,
+                     coarsest_fp32=args.coarsest_fp32,
+                     device_loop=1 if args.device_loop is None else args.device_loop,
                      **({"coarsen_target": args.coarsen_target} if args.coarsen_target else {}))
     apply_lanes(solver, args)
     setup_wall = time.perf_counter() - t0
@@ -472,7 +474,8 @@ def run_ours(args, dist: Dist):
                    "tol": args.tol, "l2": "inputs larger than L2 (level-0 matrix "
                    f"{(p.nnz * 12 + 4 * p.n) / 1e6:.0f} MB > 129 MB)",
                    "parallelism": f"replicas x{dist.world}", "launch_overlap": args.launch_overlap,
-                   "coarsest_fp32": args.coarsest_fp32, "device_loop": args.device_loop},
+                   "coarsest_fp32": args.coarsest_fp32,
+                   "device_loop": 1 if args.device_loop is None else args.device_loop},
         "iterations": info64["iterations"],
         "device_loop": info64.get("device_loop"),
         "true_rel_residual": info64["true_rel_residual"],
@@ -526,7 +529,7 @@ def profile_run(args):
     prec = amg.AMG_FP32_IN_FP64 if args.profile_fp32 else amg.AMG_FP64
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap,
                      precision=prec, autotune=args.autotune, coarsest_fp32=args.coarsest_fp32,
-                     device_loop=args.device_loop)
+                     device_loop=1 if args.device_loop is None else args.device_loop)
     apply_lanes(solver, args)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)
@@ -559,7 +562,8 @@ def run_serving(args):
     srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads,
                      aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune,
-                     host_threads=args.host_threads, device_loop=args.device_loop)
+                     host_threads=args.host_threads,
+                     **({"device_loop": args.device_loop} if args.device_loop is not None else {}))
 
     def drain(tickets, results):
         while len(results) < len(tickets):
@@ -617,7 +621,8 @@ def run_serving(args):
                       for k in ("queue_ms", "setup_ms", "solve_ms")},
         "peak_in_flight": stats["peak_running"], "slots": args.slots, "setup_threads": threads,
         "aggregation_tile": args.aggregation_tile, "aggregation_device": args.aggregation_device,
-        "autotune": args.autotune, "host_threads": args.host_threads, "device_loop": args.device_loop,
+        "autotune": args.autotune, "host_threads": args.host_threads,
+        "device_loop": srv.params.params.device_loop,
         "unknowns": {"min": int(min(sizes)), "median": int(np.median(sizes)), "max": int(max(sizes))},
         "dtype": "f32 V-cycle in f64 CG", "data": "synthetic",
         "config": {"workload": "serving stream: independent 3D 7-point FV solves, box sides "

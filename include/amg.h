@@ -406,7 +406,9 @@ typedef struct {
 
 /* Defaults: params = amg_params_default(dim) with precision
  * AMG_FP32_IN_FP64 and a coarsening target of 1000 rows (the dense coarsest
- * factorisation is per-request setup work), max_slots 32, setup_threads 4,
+ * factorisation is per-request setup work), device_loop 0 (the stepper
+ * launches each iteration: measured faster with 32 solves sharing the GPU than
+ * capturing a whole-loop graph per request), max_slots 32, setup_threads 4,
  * maxit 500, hbm_budget_bytes 0.  Errors: AMG_EINVAL. */
 int amg_server_params_default(amg_server_params *p, int32_t dim);
 

@@ -307,6 +307,9 @@ int amg_server_params_default(amg_server_params* p, int32_t dim) {
     if (rc != AMG_OK) return rc;
     p->params.precision = AMG_FP32_IN_FP64;
     p->params.coarsen_target = 1000;
+    // host-stepped iterations: with many solves sharing the GPU, the per-request
+    // capture of the whole-loop graph cost more than the per-iteration events
+    p->params.device_loop = 0;
     p->max_slots = 32;
     p->setup_threads = 4;
     p->maxit = 500;

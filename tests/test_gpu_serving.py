@@ -47,7 +47,9 @@ def _standalone(p, server_params):
 
 def test_results_are_the_same_alone_and_in_the_mix():
     reqs = [P.serving_request(k, lo=8, hi=28) for k in range(10)]
-    server = amg.Server(dim=3, max_slots=4, setup_threads=3)
+    # the device-side iteration loop here (the server's default is the
+    # host-stepped loop, which the next test runs)
+    server = amg.Server(dim=3, max_slots=4, setup_threads=3, device_loop=1)
     tickets = [server.submit(p.row_ptr, p.col, p.val, p.b, TOL) for p in reqs]
     res = _drain(server, tickets)
     st = server.stats()
@@ -73,10 +75,9 @@ def test_tuned_shapes_and_tiled_aggregation_in_the_mix():
     # other requests solve; shapes of a level signature are shared through the
     # process-wide cache, so a standalone run reproduces each result exactly
     reqs = [P.serving_request(k, lo=12, hi=40) for k in range(60, 84)]
-    # (the host-driven iteration loop here: the standalone solves below run the
-    # device-side loop, and the two give the same bits)
-    server = amg.Server(dim=3, max_slots=8, setup_threads=6, autotune=1, aggregation_tile=512,
-                        device_loop=0)
+    # (the server's default host-stepped iteration loop: the standalone solves
+    # below run the device-side loop, and the two give the same bits)
+    server = amg.Server(dim=3, max_slots=8, setup_threads=6, autotune=1, aggregation_tile=512)
     tickets = [server.submit(p.row_ptr, p.col, p.val, p.b, TOL) for p in reqs]
     res = _drain(server, tickets, timeout_s=300.0)
     st = server.stats()

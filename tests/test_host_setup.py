@@ -37,6 +37,7 @@ def test_params_default_and_errors():
     assert p.delta == pytest.approx(1 / 3) and p.omega == 1.6
     assert p.device_loop == 1 and p.coarsest_fp32 == 0 and p.autotune == 0
     assert p.launch_overlap == 1 and p.flexible_cg == -1
+    assert amg.amg_server_params_default(3).params.device_loop == 0
     p2 = amg.amg_params_default(2)
     assert (p2.s_min, p2.s_max, p2.d_max) == (4, 6, 2)
     with pytest.raises(amg.AmgError) as e:
