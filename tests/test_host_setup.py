@@ -254,3 +254,17 @@ def test_solve_entry_points_reject_a_null_context(name):
     rc = getattr(L, name)(None, b.ctypes.data, x.ctypes.data, 1e-8, 10, ctypes.byref(info))
     assert rc == amg.AMG_EINVAL
     assert "null" in amg.amg_last_error()
+
+
+def test_library_aggregation_of_a_long_chain_has_the_closed_form():
+    # the chain of the oracle pin (agg[i] = i // 3, the last single vertex
+    # joining the previous aggregate), through the library's host aggregation
+    n = 100000
+    rows = [[j for j in (i - 1, i, i + 1) if 0 <= j < n] for i in range(n)]
+    ci = np.concatenate([np.array(r, np.int32) for r in rows])
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    va = np.where(ci == np.repeat(np.arange(n), np.diff(rp)), 2.0, -1.0)
+    agg, nc = amg.amg_aggregate(rp, ci, va, amg.amg_params_default(2))
+    expect = np.arange(n) // 3
+    expect[-1] = expect[-2]
+    assert nc == expect[-1] + 1 and np.array_equal(agg, expect)

@@ -616,3 +616,34 @@ def test_openmp_build_reproduces_the_serial_oracle():
     x, it, rel, _ = H.pcg(p.b, tol=1e-10)
     xo, ito, relo, _ = Ho.pcg(p.b, tol=1e-10)
     assert it == ito and rel == relo and np.array_equal(x, xo)
+
+
+@pytest.mark.parametrize("n", [99999, 100000, 100001])
+def test_aggregation_of_a_long_chain_has_a_closed_form(n):
+    # A path with uniform coefficients (A_ii = 2, A_i,i+-1 = -1), 2D parameters
+    # (s_min 4, s_max 6, d_max 2): every coupling is 1/4, so every edge is
+    # strong both ways.  Worked by hand from Algorithms 1-3:
+    #   * the first seed is vertex 0 (N_na = 1, lowest index);
+    #   * Algorithm 2 adds the next two vertices and stops at three, since a
+    #     fourth path vertex makes the diameter 3 > d_max;
+    #   * Algorithm 3 rejects the next vertex w: it has one strong link into a
+    #     and one into U, not more into a;
+    #   * the next seed is that vertex (the only one of N(a) in U).
+    # So agg[i] = i // 3.  At the end of the chain, a last pair forms its own
+    # aggregate (n = 3k + 2), and a last single vertex (n = 3k + 1) has no link
+    # into U, so Algorithm 3 adds it to the previous aggregate.  This pins
+    # the seed order, the diameter test, the rounding rule and the tail on a
+    # graph of 1e5 vertices.
+    rows = []
+    for i in range(n):
+        rows.append([j for j in (i - 1, i, i + 1) if 0 <= j < n])
+    ci = np.concatenate([np.array(r, np.int32) for r in rows])
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    va = np.where(ci == np.repeat(np.arange(n), np.diff(rp)), 2.0, -1.0)
+    prm = O.default_params(2)
+    agg, nc = O.aggregate(rp, ci.astype(np.int32), va, prm)
+    expect = np.arange(n) // 3
+    if n % 3 == 1:
+        expect[-1] = expect[-2]
+    assert nc == expect[-1] + 1
+    assert np.array_equal(agg, expect)
