@@ -20,8 +20,9 @@
 //
 // Parity status: strength, aggregation, colouring, Galerkin product, V-cycle
 // and PCG are pinned by tests against closed forms, hand-derived maps, dense
-// direct solves and invariants.  The aggregation's tie-breaking on large
-// graphs has no independent pin beyond its invariants (see the test suite).
+// direct solves and invariants.  The aggregation's ranking and tie-breaking
+// are pinned on large graphs by hand-derived closed forms (long chains and
+// 2 x m ladders); irregular graphs rest on those rules and the invariants.
 
 #include <algorithm>
 #include <cmath>

@@ -268,3 +268,13 @@ def test_library_aggregation_of_a_long_chain_has_the_closed_form():
     expect = np.arange(n) // 3
     expect[-1] = expect[-2]
     assert nc == expect[-1] + 1 and np.array_equal(agg, expect)
+
+
+@pytest.mark.parametrize("m", [50001, 50002])
+def test_library_aggregation_of_a_long_ladder_has_the_closed_form(m):
+    # the 2 x m ladder of the oracle pin, through the library's host aggregation
+    from test_oracle_pins import _ladder, ladder_closed_form
+    rp, ci, va = _ladder(m)
+    agg, nc = amg.amg_aggregate(rp, ci, va, amg.amg_params_default(2))
+    expect = ladder_closed_form(m)
+    assert nc == expect.max() + 1 and np.array_equal(agg, expect)

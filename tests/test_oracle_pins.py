@@ -647,3 +647,56 @@ def test_aggregation_of_a_long_chain_has_a_closed_form(n):
         expect[-1] = expect[-2]
     assert nc == expect[-1] + 1
     assert np.array_equal(agg, expect)
+
+
+def _ladder(m):
+    # 2 x m grid, numbered row by row (i = r m + c), A_ii = 4, A_ij = -1
+    n = 2 * m
+    rows = []
+    for i in range(n):
+        r, c = divmod(i, m)
+        nb = [i]
+        if r == 1:
+            nb.append(i - m)
+        if r == 0:
+            nb.append(i + m)
+        if c > 0:
+            nb.append(i - 1)
+        if c < m - 1:
+            nb.append(i + 1)
+        rows.append(sorted(nb))
+    ci = np.concatenate([np.array(r, np.int32) for r in rows])
+    rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
+    va = np.where(ci == np.repeat(np.arange(n), np.diff(rp)), 4.0, -1.0)
+    return rp, ci, va
+
+
+def ladder_closed_form(m):
+    c = np.arange(2 * m) % m
+    return np.where(c < 3, 0, 1 + (c - 3) // 2)
+
+
+@pytest.mark.parametrize("m", [11, 12, 50001, 50002])
+def test_aggregation_of_a_long_ladder_has_a_closed_form(m):
+    # The 2 x m ladder with uniform couplings (all edges strong both ways) and
+    # 2D parameters (s_min 4, s_max 6, d_max 2), worked by hand through the
+    # ranking of Algorithm 2.
+    # First aggregate, from seed (0,0):
+    #   * (0,1) beats (1,0) on connect/|N| (2/3 against 1/2);
+    #   * (0,2) beats (1,1) on neighbors(v,a) (2 against 1) after a tie on
+    #     cons_2 and connect/|N|;
+    #   * the diameter limit then leaves only (1,1);
+    #   * Algorithm 3 adds (1,0) (two links into a, none into U) and (1,2)
+    #     (two against one).  The result is a 2 x 3 block.
+    # Each later aggregate, from seed (0,c):
+    #   * (1,c) wins on connect/|N| = 3/3, because its neighbour in the
+    #     previous aggregate, which is adjacent to a, counts twice;
+    #   * the index tie-break then takes (0,c+1) over (1,c+1), which follows;
+    #   * Algorithm 3 adds nothing (one link into a, two into U).
+    # A last single column forms its own aggregate.  So agg(r,c) = 0 for
+    # c < 3, else 1 + (c-3) // 2.
+    rp, ci, va = _ladder(m)
+    agg, nc = O.aggregate(rp, ci, va, O.default_params(2))
+    expect = ladder_closed_form(m)
+    assert nc == expect.max() + 1
+    assert np.array_equal(agg, expect)
