@@ -618,8 +618,9 @@ def test_openmp_build_reproduces_the_serial_oracle():
     assert it == ito and rel == relo and np.array_equal(x, xo)
 
 
-@pytest.mark.parametrize("n", [99999, 100000, 100001])
-def test_aggregation_of_a_long_chain_has_a_closed_form(n):
+@pytest.mark.parametrize("dim,n", [(2, 99999), (2, 100000), (2, 100001),
+                                   (3, 100000), (3, 100001), (3, 100002), (3, 100003)])
+def test_aggregation_of_a_long_chain_has_a_closed_form(dim, n):
     # A path with uniform coefficients (A_ii = 2, A_i,i+-1 = -1), 2D parameters
     # (s_min 4, s_max 6, d_max 2): every coupling is 1/4, so every edge is
     # strong both ways.  Worked by hand from Algorithms 1-3:
@@ -631,19 +632,22 @@ def test_aggregation_of_a_long_chain_has_a_closed_form(n):
     #   * the next seed is that vertex (the only one of N(a) in U).
     # So agg[i] = i // 3.  At the end of the chain, a last pair forms its own
     # aggregate (n = 3k + 2), and a last single vertex (n = 3k + 1) has no link
-    # into U, so Algorithm 3 adds it to the previous aggregate.  This pins
-    # the seed order, the diameter test, the rounding rule and the tail on a
-    # graph of 1e5 vertices.
+    # into U, so Algorithm 3 adds it to the previous aggregate.  With the 3D
+    # parameters (s_min 8, s_max 12, d_max 3) the same steps give blocks of
+    # four (agg[i] = i // 4) and the same tail rules.  This pins the seed
+    # order, the diameter test, the rounding rule and the tail on a graph of
+    # 1e5 vertices.
     rows = []
     for i in range(n):
         rows.append([j for j in (i - 1, i, i + 1) if 0 <= j < n])
     ci = np.concatenate([np.array(r, np.int32) for r in rows])
     rp = np.concatenate([[0], np.cumsum([len(r) for r in rows])]).astype(np.int32)
     va = np.where(ci == np.repeat(np.arange(n), np.diff(rp)), 2.0, -1.0)
-    prm = O.default_params(2)
+    prm = O.default_params(dim)
     agg, nc = O.aggregate(rp, ci.astype(np.int32), va, prm)
-    expect = np.arange(n) // 3
-    if n % 3 == 1:
+    block = dim + 1   # path vertices within the diameter limit d_max = dim
+    expect = np.arange(n) // block
+    if n % block == 1:
         expect[-1] = expect[-2]
     assert nc == expect[-1] + 1
     assert np.array_equal(agg, expect)
