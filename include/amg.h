@@ -276,18 +276,25 @@ int amg_selftest_bounded_wait(int64_t polls, void *cuda_stream, int32_t *status,
 /* ||b - A x||_2 for a CSR matrix A held in device memory (A->on_device = 1),
  * with b_dev, x_dev device float64 [n]; the result is written to the device
  * double *norm_dev, asynchronously on cuda_stream (NULL = default stream).
- * The paper has no counterpart: this is a service for callers that must not
- * allocate device memory at the point of the call -- code running while a
- * stream is captured into a CUDA graph (an allocation would break the
- * capture), code called back from inside an allocator, or programs whose
- * device memory is entirely owned by a pool they do not control.  It needs no
+ * The paper has no counterpart: this is a service for callers that cannot
+ * allocate device memory where they need a residual check -- a loop that
+ * shares the GPU with other streams and cannot afford the device-wide
+ * synchronisation cudaMalloc / cudaFree may cause, an allocator hook or
+ * callback that must not re-enter the allocator, or a program whose device
+ * memory is entirely owned by a pool it does not control.  It needs no
  * context and calls no allocator: the partial sums of its deterministic
- * reduction live in a fixed device array of 512 KiB that every GPU loading the
- * library keeps until exit, which limits n to 16,777,216 rows (larger n:
- * AMG_EINVAL).  The first call on each device looks up that array (do it
- * before any stream capture).  All calls share the array: calls that overlap
- * on the GPU race and must be serialised by the caller.
- * Errors: AMG_EINVAL (null or host pointers, n out of range), AMG_ECUDA. */
+ * reduction live in a fixed device array of 512 KiB that every GPU loading
+ * the library keeps until exit, which limits n to 16,777,216 rows (larger n:
+ * AMG_EINVAL).  The first call on each device looks up that array's address
+ * and caches it for the life of the process (a device reset invalidates the
+ * cache); make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents (each call clears its
+ * counter first): calls that overlap on the GPU race and must be serialised
+ * by the caller.  Every pointer is checked with cudaPointerGetAttributes: host
+ * memory, or device memory of another device, is AMG_EINVAL before anything
+ * is launched.
+ * Errors: AMG_EINVAL (null, host or other-device pointers, n out of range),
+ * AMG_ECUDA. */
 int amg_residual_norm_noalloc(const amg_csr *A, const double *b_dev, const double *x_dev,
                               double *norm_dev, void *cuda_stream);
 

@@ -253,8 +253,27 @@ def amg_residual_norm(ctx: int, b_dev, x_dev) -> float:
 def amg_residual_norm_noalloc(row_ptr_dev, col_dev, val_dev, b_dev, x_dev, norm_dev,
                               stream=None) -> None:
     """||b - A x|| into the device tensor norm_dev (one float64) without any
-    allocation; A given as device CSR tensors (int32, int32, float64)."""
+    allocation; A given as device CSR tensors (int32, int32, float64).
+    Raises ValueError for CPU tensors, other dtypes or non-contiguous tensors
+    before the library is called (the library itself rejects host pointers
+    with AMG_EINVAL)."""
+    want = (("row_ptr_dev", row_ptr_dev, "int32"), ("col_dev", col_dev, "int32"),
+            ("val_dev", val_dev, "float64"), ("b_dev", b_dev, "float64"),
+            ("x_dev", x_dev, "float64"), ("norm_dev", norm_dev, "float64"))
+    devs = set()
+    for name, t, dt in want:
+        if isinstance(t, np.ndarray) or not getattr(t, "is_cuda", False):
+            raise ValueError(f"amg_residual_norm_noalloc: {name} must be a CUDA tensor")
+        if str(t.dtype).replace("torch.", "") != dt:
+            raise ValueError(f"amg_residual_norm_noalloc: {name} must be {dt}, not {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"amg_residual_norm_noalloc: {name} must be contiguous")
+        devs.add(t.device)
+    if len(devs) != 1:
+        raise ValueError("amg_residual_norm_noalloc: all tensors must be on one device")
     n = int(row_ptr_dev.shape[0]) - 1
+    if b_dev.numel() != n or x_dev.numel() != n or norm_dev.numel() < 1 or val_dev.numel() != col_dev.numel():
+        raise ValueError("amg_residual_norm_noalloc: inconsistent sizes")
     A = amg_csr(n, int(col_dev.shape[0]), _ptr(row_ptr_dev), _ptr(col_dev), _ptr(val_dev), 1)
     s = None if stream is None else int(stream.cuda_stream)
     _check(lib().amg_residual_norm_noalloc(ctypes.byref(A), _ptr(b_dev), _ptr(x_dev), _ptr(norm_dev), s),

@@ -2,10 +2,11 @@
 // computed without allocating any memory.
 //
 // Why: some callers cannot call cudaMalloc at the point where they need a
-// residual check -- code running while a CUDA stream is being captured into a
-// graph (an allocation would break the capture), allocators that must not be
-// re-entered from a callback, or processes that have handed all device memory
-// to a pool they do not own.  This entry point needs no context and no
+// residual check.  cudaMalloc and cudaFree may synchronise the whole device,
+// which a latency-bound loop sharing the GPU with other streams cannot afford;
+// an allocator hook or callback must not re-enter the allocator; and a
+// process that has handed all device memory to a pool it does not control has
+// nothing left to allocate from.  This entry point needs no context and no
 // allocation: the per-block partial sums of its deterministic two-stage
 // reduction live in a fixed file-scope device array.
 //
@@ -19,8 +20,13 @@
 // caller.
 //
 // Set-up: the first call on each device looks up the array's device address
-// with cudaGetSymbolAddress while that device is current, and caches it.  That
-// first call should come before any stream capture.
+// with cudaGetSymbolAddress while that device is current, and caches it for
+// the life of the process (a device reset invalidates it).  That first call
+// should come before any stream capture.
+//
+// Every pointer argument is checked with cudaPointerGetAttributes (a query,
+// not an allocation): it must be device or managed memory of the current
+// device, else the call returns AMG_EINVAL before anything is launched.
 
 #include <cuda_runtime.h>
 
@@ -64,6 +70,22 @@ NoAllocScratch* scratch_for_current_device() {
         g_scratch_ptr[dev] = static_cast<NoAllocScratch*>(p);
     }
     return g_scratch_ptr[dev];
+}
+
+// Reject anything but device or managed memory: a host pointer handed to the
+// kernel would fault or read the wrong memory.  Returns the device that owns
+// device memory, -1 for managed memory (reachable from every device).
+int device_of_pointer(const void* p, const char* name) {
+    cudaPointerAttributes at{};
+    const cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{AMG_EINVAL, std::string(name) + ": cannot query the pointer (" +
+                                    cudaGetErrorString(e) + ")"};
+    }
+    if (at.type == cudaMemoryTypeManaged) return -1;
+    if (at.type != cudaMemoryTypeDevice) throw Error{AMG_EINVAL, std::string(name) + " is not device memory"};
+    return at.device;
 }
 
 // One thread per row: r_i = b_i - sum_k A_ik x_k, then r_i^2 summed per block
@@ -125,6 +147,17 @@ extern "C" int amg_residual_norm_noalloc(const amg_csr* A, const double* b_dev,
             throw Error{AMG_EINVAL, "n = " + std::to_string(A->n) +
                                         " exceeds the fixed scratch of this entry point (at most " +
                                         std::to_string(kMaxRows) + " rows)"};
+        const void* ptrs[] = {A->row_ptr, A->col, A->val, b_dev, x_dev, norm_dev};
+        const char* names[] = {"A->row_ptr", "A->col", "A->val", "b_dev", "x_dev", "norm_dev"};
+        int owner[6];
+        for (int k = 0; k < 6; ++k) owner[k] = device_of_pointer(ptrs[k], names[k]);
+        int dev = 0;
+        AMG_CUDA_TRY(cudaGetDevice(&dev));
+        for (int k = 0; k < 6; ++k)
+            if (owner[k] >= 0 && owner[k] != dev)
+                throw Error{AMG_EINVAL, std::string(names[k]) + " belongs to device " +
+                                            std::to_string(owner[k]) + ", not the current device " +
+                                            std::to_string(dev)};
         NoAllocScratch* scratch = scratch_for_current_device();
         cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
         AMG_CUDA_TRY(cudaMemsetAsync(&scratch->counter, 0, sizeof(unsigned int), s));

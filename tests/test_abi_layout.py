@@ -48,3 +48,33 @@ def test_binding_structures_match_the_header(c_layout, struct):
     assert ctypes.sizeof(cls) == c_layout[(struct, "size")], struct
     for name, _ in cls._fields_:
         assert getattr(cls, name).offset == c_layout[(struct, name)], f"{struct}.{name}"
+
+
+def test_noalloc_binding_refuses_cpu_tensors_and_wrong_dtypes():
+    # the Python binding checks device, dtype and contiguity before calling the
+    # library, so no CPU tensor reaches a kernel
+    torch = pytest.importorskip("torch")
+    i32 = torch.zeros(5, dtype=torch.int32)
+    f64 = torch.zeros(4, dtype=torch.float64)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amg.amg_residual_norm_noalloc(i32, i32, f64, f64, f64, f64[:1])
+    import numpy as np
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        amg.amg_residual_norm_noalloc(np.zeros(5, np.int32), i32, f64, f64, f64, f64)
+
+
+def test_noalloc_entry_point_refuses_host_pointers():
+    # the library refuses host memory itself (cudaPointerGetAttributes): on a
+    # machine without a GPU the query fails, with a GPU the pointers are
+    # reported as host memory; AMG_EINVAL either way, and nothing is launched
+    import numpy as np
+    rp = np.arange(5, dtype=np.int32)
+    ci = np.arange(4, dtype=np.int32)
+    va = np.ones(4)
+    b, x, out = np.ones(4), np.zeros(4), np.zeros(1)
+    A = amg.amg_csr(4, 4, rp.ctypes.data, ci.ctypes.data, va.ctypes.data, 1)
+    rc = amg.lib().amg_residual_norm_noalloc(ctypes.byref(A), b.ctypes.data, x.ctypes.data,
+                                             out.ctypes.data, None)
+    assert rc == amg.AMG_EINVAL
+    assert "A->row_ptr" in amg.amg_last_error()
+    assert out[0] == 0.0
