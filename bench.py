@@ -1,15 +1,21 @@
 #!/usr/bin/env python3
 """Benchmark of the AMG-preconditioned CG solve on one GB300.
 
-Workload: 3D cell-centred finite volumes, 128^3 cells (2,097,152 unknowns),
-K = exp(Z) with Z a Gaussian field (variance 4, correlation length 0.05,
-1000 cosine modes, seed 0), u = 1 at x = 0, u = 0 at x = 1, no flux elsewhere.
-A step is one complete solve to a 1e-8 relative residual (every V-cycle and CG
-operation) with the hierarchy resident in HBM.
+Headline workload (the largest single-GPU configuration): 3D cell-centred
+finite volumes, 512^3 cells (134,217,728 unknowns), diagonal anisotropic
+coefficient K = exp(Z) diag(1, 1, 1e-3) with Z a Gaussian field (variance 6,
+correlation length 0.02, 1000 cosine modes, seed 0), u = 1 at x = 0, u = 0 at
+x = 1, no flux elsewhere.  A step is one complete solve to a 1e-8 relative
+residual (every V-cycle and CG operation) with the hierarchy resident in HBM.
 
 Metric: time to a 1e-8 relative residual (ms, lower is better) of FP64
-AMG-PCG, with the FP32-in-FP64 solve and the V-cycle HBM bandwidth of both
-precisions reported beside it.
+AMG-PCG; the FP32-in-FP64 solve of the same system (time, iterations, distance
+to the FP64 solution) and the V-cycle HBM bandwidth of both precisions are
+reported beside it.  The same block is measured on the 256^3 layered workload
+(log-normal K, variance 4, with 8 slabs of contrast 1e6) and on the 128^3
+log-normal workload (variance 4, correlation length 0.05) under
+"other_workloads".  Per-kernel records go to a file (--kernels-out), not to
+the JSON line.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -33,23 +39,70 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "time to 1e-8 relative residual, FP64 AMG-PCG (FP32-in-FP64 and V-cycle HBM GB/s beside it)"
+METRIC = ("time to 1e-8 relative residual, FP64 AMG-PCG (FP32-in-FP64 and V-cycle HBM GB/s "
+          "beside it)")
 UNIT = "ms"
-WORKLOAD = "3D FV 7-point 128^3 log-normal K (variance 4, correlation length 0.05), FP64 AMG-PCG to 1e-8"
+
+# The configurations of the benchmark: name -> (description, default grid, maker)
+WORKLOADS = {
+    "anisotropic512": ("3D FV 7-point {g}^3 anisotropic K = exp(Z) diag(1,1,1e-3), Z variance 6, "
+                       "correlation length 0.02; AMG-PCG to 1e-8, FP64 and FP32-in-FP64", 512),
+    "layered256": ("3D FV 7-point {g}^3 log-normal K (variance 4, correlation length 0.05) with 8 "
+                   "horizontal layers of contrast 1e6; AMG-PCG to 1e-8, FP64 and FP32-in-FP64", 256),
+    "lognormal128": ("3D FV 7-point {g}^3 log-normal K (variance 4, correlation length 0.05); "
+                     "AMG-PCG to 1e-8, FP64 and FP32-in-FP64", 128),
+}
+
+
+def make_problem(workload: str, grid: int):
+    from paper_1209_0960_gb300 import problems
+    g = (grid, grid, grid)
+    if workload == "anisotropic512":
+        return problems.anisotropic3d(g, variance=6.0, corr_len=0.02, zfac=1e-3, seed=0)
+    if workload == "layered256":
+        return problems.layered3d(g, seed=0)
+    if workload == "lognormal128":
+        return problems.lognormal3d(g, variance=4.0, corr_len=0.05, seed=0)
+    raise KeyError(workload)
+
+
+def fv7_nnz(grid: int) -> int:
+    """Stored entries of the 7-point matrix on a grid^3 box: 7 per cell minus
+    the two missing couplings of every boundary face pair."""
+    return 7 * grid ** 3 - 6 * grid ** 2
+
+
+def workload_config(args, workload: str, grid: int, world: int) -> dict:
+    n = grid ** 3
+    nnz = fv7_nnz(grid)
+    return {"workload": WORKLOADS[workload][0].format(g=grid), "grid": grid, "unknowns": n,
+            "nnz": nnz, "tol": args.tol,
+            "l2": "inputs larger than L2 (level-0 matrix %.0f MB > 129 MB)" % ((nnz * 12 + 4 * n) / 1e6),
+            "parallelism": f"replicas x{world}"}
 
 
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--grid", type=int, default=128, help="cells per axis of the workload")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="anisotropic512",
+                    help="headline workload")
+    ap.add_argument("--grid", type=int, default=0,
+                    help="cells per axis of the headline workload (0: the workload's own)")
+    ap.add_argument("--others", type=str, default="layered256,lognormal128",
+                    help="comma-separated secondary workloads measured after the headline "
+                         "('' for none)")
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--cpu-grid", type=int, default=64,
-                    help="cells per axis of the bounded oracle sample")
+                    help="cells per axis of the oracle's sample of the headline workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="timed steps of the end-to-end leg (at most --steps)")
+    ap.add_argument("--kernels-out", type=str, default=os.path.join("gpurun_out", "bench_kernels.json"),
+                    help="file for the per-kernel records of the profiled solves")
     ap.add_argument("--launch-overlap", type=int, choices=[0, 1], default=1,
                     help="programmatic dependent launch between solve kernels")
     ap.add_argument("--profile-run", type=int, default=0, metavar="MAXIT",
@@ -97,6 +150,12 @@ def parse_args():
         args.autotune = 0
     if args.aggregation_tile < 0:
         args.aggregation_tile = 4096 if args.serving > 0 else 0
+    if args.grid <= 0:
+        args.grid = WORKLOADS[args.workload][1]
+    args.others = [w.strip() for w in args.others.split(",") if w.strip()]
+    for w in args.others:
+        if w not in WORKLOADS:
+            ap.error(f"unknown workload {w}")
     return args
 
 
@@ -217,13 +276,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def kernel_traffic(name: str):
-    """DRAM bytes per launch of `name` from the committed ncu summary, if the
-    kernel source has not changed since it was captured."""
+def kernel_traffic(name: str, workload: str):
+    """DRAM bytes per launch of kernel class `name` on `workload` from the
+    committed ncu summary, if the kernel source has not changed since it was
+    captured."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(path))
-        rec = d[name]
+        rec = d[workload][name]
         src = open(os.path.join(ROOT, "paper_1209_0960_gb300", "csrc", rec["source"]), "rb").read()
         if hashlib.sha256(src).hexdigest()[:16] != rec["sha256_16"]:
             return None
@@ -232,28 +292,48 @@ def kernel_traffic(name: str):
         return None
 
 
-def make_problem(grid: int):
-    from paper_1209_0960_gb300 import problems
-    return problems.lognormal3d((grid, grid, grid), variance=4.0, corr_len=0.05, seed=0)
+def r4(v):
+    """Round floats to 4 significant digits, recursively (keeps the line short)."""
+    if isinstance(v, float):
+        return float(f"{v:.4g}")
+    if isinstance(v, dict):
+        return {k: r4(x) for k, x in v.items()}
+    if isinstance(v, (list, tuple)):
+        return [r4(x) for x in v]
+    return v
 
 
-def oracle_sample(grid: int, tol: float, steps: int, warmup: int, min_seconds: float = 0.0,
-                  openmp: bool = False):
-    """Time the oracle's PCG solve on a grid^3 instance of the workload (the
-    serial build, or the OpenMP build of the same source on all host cores).
-    Returns (seconds per solve, iterations, n, solves)."""
+def oracle_sample(workload: str, grid: int, tol: float, steps: int, warmup: int,
+                  min_seconds: float = 0.0, openmp: bool = False):
+    """Time the oracle's PCG solve on the grid^3 instance of the workload (the
+    serial build, or the OpenMP build of the same source on all host cores),
+    hierarchy built once.  Returns a dict of seconds, iterations and sizes."""
     from oracle import oracle as O
-    p = make_problem(grid)
+    p = make_problem(workload, grid)
+    t0 = time.perf_counter()
     H = O.Hierarchy(p.row_ptr, p.col, p.val, O.default_params(3), openmp=openmp)
+    setup_s = time.perf_counter() - t0
     for _ in range(warmup):
-        H.pcg(p.b, tol=tol, maxit=500)
+        H.pcg(p.b, tol=tol, maxit=1000)
     times, it = [], 0
     t_all = time.perf_counter()
     while len(times) < steps or (time.perf_counter() - t_all) < min_seconds:
         t0 = time.perf_counter()
-        _, it, _, _ = H.pcg(p.b, tol=tol, maxit=500)
+        _, it, _, _ = H.pcg(p.b, tol=tol, maxit=1000)
         times.append(time.perf_counter() - t0)
-    return statistics.mean(times), it, p.n, len(times)
+    return {"solve_s": statistics.mean(times), "iterations": it, "n": p.n, "solves": len(times),
+            "setup_s": setup_s, "levels": H.num_levels, "problem": p}
+
+
+def cpu_model() -> str:
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 # ---------------------------------------------------------------------------
@@ -263,25 +343,23 @@ def oracle_sample(grid: int, tol: float, steps: int, warmup: int, min_seconds: f
 def run_reference(args, dist: Dist):
     if dist.rank != 0:
         return
-    sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, max(1, args.steps),
-                                         args.warmup)
-    n_full = args.grid ** 3
-    # scale to the full workload: cost per unknown per iteration is flat (every
-    # oracle step is O(nnz)); the iteration count is taken from the sample
-    value = sec * 1e3 * (n_full / n_s)
+    smp = oracle_sample(args.workload, args.cpu_grid, args.tol, max(1, args.steps), args.warmup)
+    value = smp["solve_s"] * 1e3
+    sample = (f"oracle PCG solve (single thread) on the {args.cpu_grid}^3 instance of the workload "
+              f"({smp['n']} unknowns, {smp['levels']} levels, {smp['iterations']} iterations), "
+              f"hierarchy built once ({smp['setup_s']:.1f} s, not timed); unscaled: the oracle's "
+              f"setup of the {args.grid}^3 system alone would take hours")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": reps, "warmup": args.warmup, "ms_per_step": value,
+        "n_gpus": args.gpus, "steps": smp["solves"], "warmup": args.warmup, "ms_per_step": value,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": args.grid, "tol": args.tol},
+        "config": workload_config(args, args.workload, args.grid, dist.world),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"oracle PCG solve on the {args.cpu_grid}^3 instance of the "
-                                   f"workload ({n_s} unknowns, {it_s} iterations, "
-                                   f"{sec:.3f} s per solve), scaled by unknowns to {args.grid}^3"},
+                         "sample": sample, "setup_s": smp["setup_s"], "cpu": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(r4(line)), flush=True)
 
 
 # ---------------------------------------------------------------------------
@@ -292,7 +370,7 @@ VCYCLE_KINDS = {"gs_level0", "first_level0", "gs_coarse", "residual_level0",
                 "residual_coarse", "restrict", "prolong", "coarse_solve", "zero", "convert"}
 
 
-def timed_solves(solver, b, x, steps, tol, stream, dist):
+def timed_solves(solver, b, x, steps, tol, stream, dist, maxit):
     import torch
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
@@ -302,7 +380,7 @@ def timed_solves(solver, b, x, steps, tol, stream, dist):
     infos = []
     for _ in range(steps):
         x.zero_()
-        _, rc, info = solver.solve(b, x, tol=tol, maxit=500)
+        _, rc, info = solver.solve(b, x, tol=tol, maxit=maxit)
         infos.append((rc, info))
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -315,16 +393,8 @@ def apply_lanes(solver, args):
         solver.set_level_shape(l, lanes, threads)
 
 
-def run_ours(args, dist: Dist):
-    import numpy as np
-    import torch
+def new_solver(args, p, stream):
     from paper_1209_0960_gb300 import amg
-
-    dev = dist.local_rank if dist.world > 1 else 0
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream()
-    p = make_problem(args.grid)
-    t0 = time.perf_counter()
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, stream=stream,
                      launch_overlap=args.launch_overlap, aggregation_tile=args.aggregation_tile,
                      aggregation_device=args.aggregation_device, autotune=args.autotune,
@@ -332,192 +402,234 @@ def run_ours(args, dist: Dist):
                      device_loop=1 if args.device_loop is None else args.device_loop,
                      **({"coarsen_target": args.coarsen_target} if args.coarsen_target else {}))
     apply_lanes(solver, args)
+    return solver
+
+
+def prof_iters(prof):
+    return max([d["launches"] for d in prof if d["name"] == "coarse_solve"] or [1])
+
+
+def measure_workload(args, dist, workload, grid, steps, warmup, headline, kernels_out):
+    """Set up one workload and time K FP64 and K FP32-in-FP64 solves; with
+    `headline` also the end-to-end leg, clocks and the roofline.  Returns the
+    compact record and the per-kernel records."""
+    import numpy as np
+    import torch
+    from paper_1209_0960_gb300 import amg
+
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    p = make_problem(workload, grid)
+    gen_s = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    solver = new_solver(args, p, stream)
     setup_wall = time.perf_counter() - t0
     summary, levels = solver.info()
     b = torch.from_numpy(p.b).cuda()
     x = torch.zeros_like(b)
-
-    # ---- FP64: warm-up, then K timed solves --------------------------------
-    for _ in range(args.warmup):
-        x.zero_()
-        solver.solve(b, x, tol=args.tol)
-    clocks = ClockSampler(dev)
-    ms64, infos64 = timed_solves(solver, b, x, args.steps, args.tol, stream, dist)
-    clk = clocks.stop()
-    ms64 = dist.max(ms64)
-    rc64, info64 = infos64[-1]
-    x64 = x.clone()
-
-    # one more solve with the profiler on (outside the timed region): per-kernel
-    # launches, CUDA-event durations and modelled bytes
-    solver.profile(True)
-    x.zero_()
-    solver.solve(b, x, tol=args.tol)
-    prof64 = solver.profile_read()
-    solver.profile(False)
-
-    solver.profile(2)
-    x.zero_()
-    solver.solve(b, x, tol=args.tol)
-    graph64 = solver.profile_read()
-    solver.profile(0)
-
-    # ---- FP32-in-FP64 ---------------------------------------------------------
-    solver.set_precision(amg.AMG_FP32_IN_FP64)
-    for _ in range(args.warmup):
-        x.zero_()
-        solver.solve(b, x, tol=args.tol)
-    ms32, infos32 = timed_solves(solver, b, x, args.steps, args.tol, stream, dist)
-    ms32 = dist.max(ms32)
-    rc32, info32 = infos32[-1]
-    err32 = float(torch.linalg.norm(x - x64) / torch.linalg.norm(x64))
-    solver.profile(True)
-    x.zero_()
-    solver.solve(b, x, tol=args.tol)
-    prof32 = solver.profile_read()
-    solver.profile(2)
-    x.zero_()
-    solver.solve(b, x, tol=args.tol)
-    graph32 = solver.profile_read()
-    solver.profile(0)
-    solver.set_precision(amg.AMG_FP64)
-
-    # ---- end to end through the C ABI with pinned host buffers -----------------
-    e2e = None
-    if not args.no_e2e:
-        bh = torch.from_numpy(p.b).pin_memory()
-        xh = torch.zeros(p.n, dtype=torch.float64).pin_memory()
-        bh_np, xh_np = bh.numpy(), xh.numpy()
-        solver.solve_host(bh_np, xh_np, tol=args.tol, zero_guess=True)
-        dist.barrier()
-        t0 = time.perf_counter()
-        for _ in range(args.steps):
-            solver.solve_host(bh_np, xh_np, tol=args.tol, zero_guess=True)
-        e2e_ms = dist.max((time.perf_counter() - t0) * 1e3 / args.steps)
-        e2e = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * p.n,
-               "d2h_bytes_per_step": 8 * p.n, "initial_guess": "zero"}
-
-    # ---- roofline of the dominant kernel ---------------------------------------
+    maxit = 1000
     peak, peak_src = measured_peaks()
-    top = max(prof64, key=lambda d: d["total_ms"])
-    per_launch_ms = top["total_ms"] / top["launches"]
-    per_launch_bytes = top["bytes"] / top["launches"]
-    achieved = per_launch_bytes / (per_launch_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
-                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
-                "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                "traffic": kernel_traffic(top["name"])}
+    out = {}
+    kern = {}
 
-    def kernel_roofline(name):
-        rec = [d for d in prof64 if d["name"] == name]
-        if not rec or rec[0]["launches"] == 0:
+    def vcycle_gbs(graph_ms, model_bytes, cg_extra_bytes):
+        gms = graph_ms.get("graph_vcycle_part")
+        if not gms:
             return None
-        d = rec[0]
-        ms = d["total_ms"] / d["launches"]
-        bpl = d["bytes"] / d["launches"]
-        ach = bpl / (ms * 1e-3) / 1e9
-        return {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "bytes_per_launch": bpl, "ms_per_launch": ms,
-                "traffic": kernel_traffic(name)}
+        wall = (model_bytes + cg_extra_bytes) / (gms * 1e-3) / 1e9
+        return {"ms": gms, "gbs": wall, "frac_measured": wall / peak, "frac_nominal_7900": wall / 7900.0}
 
-    def vcycle_gbs(prof, graph, model_bytes, cg_extra_bytes):
-        """V-cycle bandwidth two ways: modelled bytes over the wall time of the
-        graph-launched V-cycle (plus the direction update it carries), and over
-        the sum of the individually timed V-cycle kernels."""
-        vb = sum(d["bytes"] for d in prof if d["name"] in VCYCLE_KINDS)
-        vt = sum(d["total_ms"] for d in prof if d["name"] in VCYCLE_KINDS)
-        launches = sum(d["launches"] for d in prof if d["name"] in VCYCLE_KINDS)
-        gms = graph.get("graph_vcycle_part")
-        wall = (model_bytes + cg_extra_bytes) / (gms * 1e-3) / 1e9 if gms else None
-        return {"gbs_wall": wall, "ms_per_vcycle_wall": gms,
-                "frac_of_measured_wall": wall / peak if wall else None,
-                "frac_of_nominal_7900_wall": wall / 7900.0 if wall else None,
-                "gbs_kernel_sum": vb / (vt * 1e-3) / 1e9 if vt > 0 else None,
-                "kernels_per_vcycle": launches / max(1, prof_iters(prof))}
+    res = {}
+    clk = None
+    for prec, tag in ((amg.AMG_FP64, "fp64"), (amg.AMG_FP32_IN_FP64, "fp32")):
+        solver.set_precision(prec)
+        for _ in range(warmup):
+            x.zero_()
+            solver.solve(b, x, tol=args.tol, maxit=maxit)
+        clocks = ClockSampler(torch.cuda.current_device()) if (headline and tag == "fp64") else None
+        ms, infos = timed_solves(solver, b, x, steps, args.tol, stream, dist, maxit)
+        if clocks is not None:
+            clk = clocks.stop()
+        ms = dist.max(ms)
+        rc, info = infos[-1]
+        res[tag] = {"ms": ms, "rc": rc, "info": info, "x": x.clone()}
+        # per-kernel records (every launch bracketed by events; host-driven loop)
+        solver.profile(1)
+        x.zero_()
+        solver.solve(b, x, tol=args.tol, maxit=maxit)
+        prof = solver.profile_read()
+        # graph-part timings: CG part, V-cycle part, V-cycle from each level
+        solver.profile(2)
+        x.zero_()
+        solver.solve(b, x, tol=args.tol, maxit=maxit)
+        graph = {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in solver.profile_read()}
+        solver.profile(0)
+        res[tag]["prof"] = prof
+        res[tag]["graph"] = graph
+        kern[tag] = {"kernels": prof, "graph_parts_ms": graph}
+    solver.set_precision(amg.AMG_FP64)
+    x64, x32 = res["fp64"]["x"], res["fp32"]["x"]
+    err32 = float(torch.linalg.norm(x32 - x64) / torch.linalg.norm(x64))
+    i64, i32 = res["fp64"]["info"], res["fp32"]["info"]
+    n = p.n
+    vc = {"fp64": vcycle_gbs(res["fp64"]["graph"], summary["vcycle_bytes_fp64"], 40.0 * n),
+          "fp32": vcycle_gbs(res["fp32"]["graph"], summary["vcycle_bytes_fp32"], 80.0 * n)}
+    kern["summary"] = summary
+    kern["levels"] = levels
 
-    def prof_iters(prof):
-        return max([d["launches"] for d in prof if d["name"] == "coarse_solve"] or [1])
+    rec = {
+        "fp64": {"ms": res["fp64"]["ms"], "iterations": i64["iterations"],
+                 "true_rel_residual": i64["true_rel_residual"], "status": res["fp64"]["rc"]},
+        "fp32_in_fp64": {"ms": res["fp32"]["ms"], "iterations": i32["iterations"],
+                         "true_rel_residual": i32["true_rel_residual"], "status": res["fp32"]["rc"],
+                         "rel_diff_vs_fp64_solution": err32,
+                         "speedup_vs_fp64": res["fp64"]["ms"] / res["fp32"]["ms"]},
+        "vcycle": vc,
+        "setup": {"total_ms": summary["total_setup_ms"], "host_ms": summary["host_setup_ms"],
+                  "aggregation_ms": summary["aggregation_ms"],
+                  "gpu_galerkin_ms": summary["gpu_galerkin_ms"], "gpu_other_ms": summary["gpu_other_ms"],
+                  "levels": summary["num_levels"], "coarsest_n": summary["coarsest_n"],
+                  "operator_complexity": summary["operator_complexity"],
+                  "problem_generation_s": gen_s},
+    }
 
-    launches = sum(d["launches"] for d in prof64 if d["name"] not in ("zero",))
-    # the profiled solve drives its iterations from the host; the timed solves
-    # run the loop on the device, with one condition kernel per iteration more
-    if info64.get("device_loop"):
-        launches += info64["iterations"]
-    g64 = {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in graph64}
-    g32 = {d["name"]: d["total_ms"] / max(1, d["launches"]) for d in graph32}
+    if headline:
+        prof64 = res["fp64"]["prof"]
+        top = max(prof64, key=lambda d: d["total_ms"])
+        per_ms = top["total_ms"] / top["launches"]
+        per_b = top["bytes"] / top["launches"]
+        ach = per_b / (per_ms * 1e-3) / 1e9
+        rec["roofline"] = {"bound": "hbm", "kernel": top["name"], "achieved": ach, "peak": peak,
+                           "unit": "GB/s", "frac": ach / peak, "peak_source": peak_src,
+                           "bytes_per_launch": per_b, "ms_per_launch": per_ms,
+                           "share_of_solve": top["total_ms"] / sum(d["total_ms"] for d in prof64),
+                           "traffic": kernel_traffic(top["name"], workload)}
+        # kernels in the timed region: the profiled solve's launches (host-driven
+        # loop) plus one loop-condition kernel per iteration of the device loop
+        launches = sum(d["launches"] for d in prof64 if d["name"] != "zero")
+        if i64.get("device_loop"):
+            launches += i64["iterations"]
+        rec["gpu_launches"] = launches * steps
+        rec["clocks"] = clk
+        rec["device_loop"] = i64.get("device_loop")
+        if not args.no_e2e:
+            bh = torch.from_numpy(p.b).pin_memory()
+            xh = torch.zeros(p.n, dtype=torch.float64).pin_memory()
+            bh_np, xh_np = bh.numpy(), xh.numpy()
+            solver.solve_host(bh_np, xh_np, tol=args.tol, maxit=maxit, zero_guess=True)
+            k = max(1, min(args.e2e_steps, steps))
+            dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(k):
+                solver.solve_host(bh_np, xh_np, tol=args.tol, maxit=maxit, zero_guess=True)
+            e2e_ms = dist.max((time.perf_counter() - t0) * 1e3 / k)
+            rec["e2e"] = {"value": e2e_ms, "unit": UNIT, "h2d_bytes_per_step": 8 * p.n,
+                          "d2h_bytes_per_step": 8 * p.n, "steps": k, "initial_guess": "zero",
+                          "api": "amg_pcg_solve_host_zero_guess, pinned host buffers"}
+            del bh, xh
+    solver.close()
+    del b, x, res
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    return rec, kern, p
 
-    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) ----------------
+
+def gpu_time_on(args, p, dist):
+    """FP64 time to tolerance of our solver on problem p (hierarchy resident),
+    for a same-size comparison with the oracle sample."""
+    import torch
+    stream = torch.cuda.current_stream()
+    solver = new_solver(args, p, stream)
+    b = torch.from_numpy(p.b).cuda()
+    x = torch.zeros_like(b)
+    for _ in range(3):
+        x.zero_()
+        solver.solve(b, x, tol=args.tol, maxit=1000)
+    ms, infos = timed_solves(solver, b, x, 5, args.tol, stream, dist, 1000)
+    solver.close()
+    return ms, infos[-1][1]["iterations"]
+
+
+def run_ours(args, dist: Dist):
+    import torch
+
+    dev = dist.local_rank if dist.world > 1 else 0
+    torch.cuda.set_device(dev)
+    rec, kern, _ = measure_workload(args, dist, args.workload, args.grid, args.steps, args.warmup,
+                                    True, args.kernels_out)
+    all_kern = {args.workload: kern}
+    others = {}
+    for w in args.others:
+        if w == args.workload:
+            continue
+        g = WORKLOADS[w][1]
+        o, k2, _ = measure_workload(args, dist, w, g, args.steps, args.warmup, False, None)
+        all_kern[w] = k2
+        others[w] = {"fp64_ms": o["fp64"]["ms"], "fp64_iterations": o["fp64"]["iterations"],
+                     "fp32_in_fp64_ms": o["fp32_in_fp64"]["ms"],
+                     "fp32_in_fp64_iterations": o["fp32_in_fp64"]["iterations"],
+                     "fp32_speedup": o["fp32_in_fp64"]["speedup_vs_fp64"],
+                     "fp32_rel_diff_vs_fp64": o["fp32_in_fp64"]["rel_diff_vs_fp64_solution"],
+                     "vcycle_fp64_frac": (o["vcycle"]["fp64"] or {}).get("frac_measured"),
+                     "vcycle_fp32_frac": (o["vcycle"]["fp32"] or {}).get("frac_measured"),
+                     "levels": o["setup"]["levels"]}
+
+    # ---- CPU baseline: the oracle on the host cores (rank 0, N = 1) -------------
     cpu = None
     cpu_omp = None
     if dist.world == 1 and not args.no_cpu_baseline:
-        sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, 1, 0, min_seconds=10.0)
-        cpu = {"value": sec * 1e3 * (p.n / n_s), "unit": UNIT, "cores": 1, "kind": "oracle",
+        smp = oracle_sample(args.workload, args.cpu_grid, args.tol, 1, 0, min_seconds=10.0)
+        gpu_ms, gpu_it = gpu_time_on(args, smp["problem"], dist)
+        cpu = {"value": smp["solve_s"] * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle PCG solve on the {args.cpu_grid}^3 instance of the workload "
-                         f"({n_s} unknowns, {it_s} iterations, {sec:.3f} s per solve, "
-                         f"{reps} solves), scaled by unknowns to {args.grid}^3",
-               "host_cpu_count": os.cpu_count()}
+                         f"({smp['n']} unknowns, {smp['iterations']} iterations, {smp['solves']} "
+                         f"solves), unscaled; its setup of the {args.grid}^3 system would take hours",
+               "setup_s": smp["setup_s"], "cpu": cpu_model(), "host_cpu_count": os.cpu_count(),
+               "gpu_fp64_ms_same_sample": gpu_ms, "gpu_iterations_same_sample": gpu_it}
         from oracle import oracle as O
         threads = O.threads(os.cpu_count() or 1)
-        sec, it_s, n_s, reps = oracle_sample(args.cpu_grid, args.tol, 1, 0, min_seconds=5.0,
-                                             openmp=True)
-        cpu_omp = {"value": sec * 1e3 * (p.n / n_s), "unit": UNIT, "cores": threads,
+        so = oracle_sample(args.workload, args.cpu_grid, args.tol, 1, 0, min_seconds=5.0, openmp=True)
+        cpu_omp = {"value": so["solve_s"] * 1e3, "unit": UNIT, "cores": threads,
                    "kind": "oracle (OpenMP build of the same source)",
-                   "sample": f"as cpu_baseline, {threads} threads: {it_s} iterations, "
-                             f"{sec:.3f} s per solve, {reps} solves"}
+                   "setup_s": so["setup_s"], "iterations": so["iterations"]}
+
+    kpath = None
+    if args.kernels_out and dist.rank == 0:
+        try:
+            os.makedirs(os.path.dirname(os.path.abspath(args.kernels_out)), exist_ok=True)
+            with open(args.kernels_out, "w") as f:
+                json.dump(all_kern, f)
+            kpath = args.kernels_out
+        except OSError:
+            kpath = None
 
     line = {
-        "metric": METRIC, "value": ms64, "unit": UNIT, "n_gpus": dist.world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms64,
+        "metric": METRIC, "value": rec["fp64"]["ms"], "unit": UNIT, "n_gpus": dist.world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["fp64"]["ms"],
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": args.grid, "unknowns": p.n, "nnz": p.nnz,
-                   "tol": args.tol, "l2": "inputs larger than L2 (level-0 matrix "
-                   f"{(p.nnz * 12 + 4 * p.n) / 1e6:.0f} MB > 129 MB)",
-                   "parallelism": f"replicas x{dist.world}", "launch_overlap": args.launch_overlap,
-                   "coarsest_fp32": args.coarsest_fp32,
-                   "device_loop": 1 if args.device_loop is None else args.device_loop},
-        "iterations": info64["iterations"],
-        "device_loop": info64.get("device_loop"),
-        "true_rel_residual": info64["true_rel_residual"],
-        "fp32_in_fp64": {"ms": ms32, "iterations": info32["iterations"],
-                         "true_rel_residual": info32["true_rel_residual"],
-                         "rel_diff_vs_fp64_solution": err32, "speedup_vs_fp64": ms64 / ms32},
-        "vcycle": {"fp64": vcycle_gbs(prof64, g64, summary["vcycle_bytes_fp64"], 40.0 * p.n),
-                   "fp32": vcycle_gbs(prof32, g32, summary["vcycle_bytes_fp32"], 40.0 * p.n + 40.0 * p.n),
-                   "model_bytes_fp64": summary["vcycle_bytes_fp64"],
-                   "model_bytes_fp32": summary["vcycle_bytes_fp32"]},
-        "setup": {"host_ms": summary["host_setup_ms"], "aggregation_ms": summary["aggregation_ms"],
-                  "aggregation_tile": args.aggregation_tile,
-                  "aggregation_device": args.aggregation_device,
-                  "gpu_galerkin_ms": summary["gpu_galerkin_ms"],
-                  "gpu_other_ms": summary["gpu_other_ms"], "total_ms": summary["total_setup_ms"],
-                  "levels": summary["num_levels"], "coarsest_n": summary["coarsest_n"],
-                  "operator_complexity": summary["operator_complexity"],
-                  "level_n": [l["n"] for l in levels],
-                  "autotune": args.autotune, "autotune_ms": summary["autotune_ms"],
-                  "coarsest_inverse_ms": summary["coarsest_inverse_ms"],
-                  "lanes_per_row": [l["lanes_per_row"] for l in levels[:-1]],
-                  "threads_per_block": [l["threads_per_block"] for l in levels[:-1]],
-                  "colours": [l["ncolours"] for l in levels[:-1]]},
-        "roofline": roofline,
-        "roofline_level0": {k: kernel_roofline(k) for k in
-                            ("gs_level0", "first_level0", "residual_level0", "prolong",
-                             "cg_spmv_dot")},
-        "kernels_fp64": prof64,
-        "kernels_fp32": prof32,
-        "graph_parts_ms": {
-            "fp64": {d["name"]: round(d["total_ms"] / max(1, d["launches"]), 4) for d in graph64},
-            "fp32": {d["name"]: round(d["total_ms"] / max(1, d["launches"]), 4) for d in graph32}},
-        "gpu_launches": launches * args.steps,
-        "e2e": e2e,
-        "clocks": clk,
+        "config": dict(workload_config(args, args.workload, args.grid, dist.world),
+                       launch_overlap=args.launch_overlap, coarsest_fp32=args.coarsest_fp32,
+                       autotune=args.autotune,
+                       device_loop=1 if args.device_loop is None else args.device_loop),
+        "gpu_launches": rec["gpu_launches"],
+        "e2e": rec.get("e2e"),
+        "clocks": rec["clocks"],
         "cpu_baseline": cpu,
         "cpu_baseline_openmp": cpu_omp,
-        "status": {"fp64": rc64, "fp32_in_fp64": rc32},
+        "kernels_file": kpath,
+        "setup": rec["setup"],
+        "other_workloads": others,
+        "roofline": rec["roofline"],
+        "device_loop": rec["device_loop"],
+        "iterations": rec["fp64"]["iterations"],
+        "true_rel_residual": rec["fp64"]["true_rel_residual"],
+        "status": {"fp64": rec["fp64"]["status"], "fp32_in_fp64": rec["fp32_in_fp64"]["status"]},
+        "vcycle": rec["vcycle"],
+        "fp32_in_fp64": rec["fp32_in_fp64"],
     }
-    solver.close()
     if dist.rank == 0:
-        print(json.dumps(line), flush=True)
+        print(json.dumps(r4(line)), flush=True)
 
 
 def profile_run(args):
@@ -525,11 +637,12 @@ def profile_run(args):
     import torch
     from paper_1209_0960_gb300 import amg
     torch.cuda.set_device(0)
-    p = make_problem(args.grid)
+    p = make_problem(args.workload, args.grid)
     prec = amg.AMG_FP32_IN_FP64 if args.profile_fp32 else amg.AMG_FP64
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, launch_overlap=args.launch_overlap,
                      precision=prec, autotune=args.autotune, coarsest_fp32=args.coarsest_fp32,
-                     device_loop=1 if args.device_loop is None else args.device_loop)
+                     device_loop=1 if args.device_loop is None else args.device_loop,
+                     **({"coarsen_target": args.coarsen_target} if args.coarsen_target else {}))
     apply_lanes(solver, args)
     b = torch.from_numpy(p.b).cuda()
     x, rc, info = solver.solve(b, tol=args.tol, maxit=args.profile_run)
