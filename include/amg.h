@@ -58,12 +58,19 @@ extern "C" {
 #define AMG_ENOMEM (-2)      /* device or host allocation failed / refused */
 #define AMG_ENOTSPD (-3)     /* coarsest pivot <= 0 or p.Ap <= 0 in CG */
 #define AMG_ENOTCONV (-4)    /* maxit reached before the tolerance */
-#define AMG_ETIMEOUT (-5)    /* a bounded device-side wait gave up */
+#define AMG_ETIMEOUT (-5)    /* a bounded device-side wait gave up; the context must then be
+                                freed (copies may have been in flight, dependency counters
+                                are behind) and the system set up again */
 #define AMG_ECUDA (-6)       /* a CUDA runtime call failed */
 #define AMG_ENOTFOUND (-7)   /* unknown ticket */
 
 #define AMG_FP64 0           /* every step in float64 */
 #define AMG_FP32_IN_FP64 1   /* float32 V-cycle inside float64 CG */
+
+/* or'ed into amg_set_level_shape's lanes_per_row (1, 2, 4 or 8): run each
+ * smoothing sweep of the level (the pre- and the post-smoother) as one
+ * dependency-driven kernel instead of one launch per colour pass */
+#define AMG_SHAPE_SWEEP 0x100
 
 typedef struct amg_ctx amg_ctx;
 
@@ -160,6 +167,12 @@ typedef struct {
                                  shared memory, else 1, 2, 4 or 8 lanes per row */
     int32_t threads_per_block; /* threads per block of those kernels with lanes_per_row >= 1
                                  (256, or 128 when the autotuner chose it) */
+    int32_t sweep;            /* 1: each smoothing sweep of the level runs as one
+                                 dependency-driven kernel (AMG_SHAPE_SWEEP): the colour
+                                 passes are cut into items of threads_per_block /
+                                 lanes_per_row rows, and an item starts as soon as the items
+                                 of earlier passes it reads or overwrites have finished;
+                                 same arithmetic as one launch per pass */
 } amg_level_info;
 
 typedef struct {
@@ -317,12 +330,18 @@ int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col
 /* Launch shape of level l's smoother and residual kernels (0 <= l < number of
  * levels - 1; the coarsest level is the dense solve).  lanes_per_row: 0 = one
  * row per thread with the slices staged in shared memory (levels whose longest
- * row has at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row;
- * threads_per_block: 256 or 128 for lanes_per_row >= 1 (0 means 256; the
- * staged kernels always use 256).  Results differ only in the order of
- * floating-point sums.  The CUDA graphs of the context are rebuilt on the next
- * solve.  Errors: AMG_EINVAL (l, lanes_per_row or threads_per_block out of
- * range, 0 lanes on a level with longer rows). */
+ * row has at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row, optionally
+ * or'ed with AMG_SHAPE_SWEEP (levels of at most 2^20 rows that are not
+ * two-colour levels with the fused residual): each smoothing sweep then runs
+ * as one kernel whose blocks wait, with bounded polls, only for the earlier
+ * colour-pass blocks they depend on (planned on the host from the level's
+ * graph at the first use of a block size).  threads_per_block: 256 or 128 for
+ * lanes_per_row >= 1 (0 means 256; the staged kernels always use 256).
+ * Results differ only in the order of floating-point sums (a sweep gives the
+ * same values as the pass-per-launch kernels of its lanes and block size).
+ * The CUDA graphs of the context are rebuilt on the next solve.  Errors:
+ * AMG_EINVAL (l, lanes_per_row or threads_per_block out of range, 0 lanes on a
+ * level with longer rows, a sweep where it is not allowed). */
 int amg_set_level_shape(amg_ctx *c, int32_t l, int32_t lanes_per_row, int32_t threads_per_block);
 
 /* Aggregation of one level, exactly as amg_setup runs it (Sec. 2.1): strength

@@ -29,6 +29,7 @@ AMG_ENOTFOUND = -7
 
 AMG_FP64 = 0
 AMG_FP32_IN_FP64 = 1
+AMG_SHAPE_SWEEP = 0x100   # or'ed into lanes_per_row: one dependency-driven kernel per sweep
 
 _c_i32 = ctypes.c_int32
 _c_dbl = ctypes.c_double
@@ -60,7 +61,7 @@ class amg_level_info(ctypes.Structure):
     _fields_ = [("n", _c_i32), ("nnz", _c_i32), ("n_coarse", _c_i32), ("ncolours", _c_i32),
                 ("max_agg_size", _c_i32), ("n_isolated", _c_i32), ("n_dirichlet", _c_i32),
                 ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
-                ("lanes_per_row", _c_i32), ("threads_per_block", _c_i32)]
+                ("lanes_per_row", _c_i32), ("threads_per_block", _c_i32), ("sweep", _c_i32)]
 
 
 class amg_summary(ctypes.Structure):

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
 #include <utility>
 #include <vector>
@@ -103,6 +104,86 @@ struct PcgScalars {
     int32_t loops;    // device-side loop: conditions evaluated (a bound of its own)
 };
 
+// Scalars of the BiCGSTAB recurrence, resident on the device.
+struct BiScalars {
+    double r0;        // ||r_0||
+    double rho;       // rt . r of the current iteration
+    double rho_prev;
+    double alpha, w;
+    double rtv;       // rt . v
+    double ts, tt;    // t . s, t . t
+    double rel;       // ||r|| / ||r_0|| (||s|| / ||r_0|| after a converged half step)
+    double tol;
+    int32_t iters;    // iterations begun (a converged half step counts as one)
+    int32_t maxit;
+    int32_t status;   // 0, or AMG_ENOTCONV on breakdown / maxit
+    int32_t done;     // 1 once rel <= tol
+    int32_t half;     // 1: the first half step met the tolerance (x += alpha y only)
+    int32_t why;      // breakdown: 1 rt.r = 0, 2 rt.v = 0, 3 t.t = 0; 0 maxit
+    int32_t loops;    // loop conditions evaluated (device-side loop bound)
+    int32_t pad;
+};
+
+// Whether another BiCGSTAB iteration runs; on maxit or a zero rho it records
+// the stop in the scalars.  Shared by the device-side loop condition and the
+// host-driven loop, so both stop at the same point.
+__host__ __device__ inline bool bi_continue(BiScalars& b) {
+    if (b.done || b.status) return false;
+    if (b.iters >= b.maxit) {
+        b.status = AMG_ENOTCONV;
+        b.why = 0;
+        return false;
+    }
+    if (b.rho == 0.0) {
+        b.status = AMG_ENOTCONV;
+        b.why = 1;
+        return false;
+    }
+    return true;
+}
+
+// A symmetric Gauss-Seidel sweep of one level as a single kernel.  Each
+// colour pass of the sweep is cut into items of `rows` consecutive rows.  A
+// persistent grid of co-resident blocks (a cooperative launch) takes the
+// items in pass order, block g the items g, g + grid, g + 2 grid, ...; before
+// reading x an item waits (bounded) for what it depends on, computed at setup
+// from the level's graph:
+//   - the item of the same rows in the previous pass over its colour (its
+//     values are overwritten);
+//   - in the pass just before it, the items holding neighbours of its rows
+//     (their new values are read);
+//   - every earlier pass since its colour's previous update, complete (their
+//     reads of the old values, and the latest values of the other colours).
+// Every dependency is a smaller item and every block takes its items in
+// increasing order, so the sweep cannot deadlock.  Flags and counters are
+// never reset: a launch's epoch is its count of arriving blocks divided by
+// the grid, a flag holds the epoch of the launch that finished the item, and
+// the pass counters count finished items over all launches.
+struct SweepPass {
+    int32_t r0, r1;   // rows of the pass's colour (smoothing order)
+    int32_t jmax;     // neighbours at positions >= jmax are taken as zero
+    int32_t first;    // 1: colour 0 from a zero guess, x = b / A_ii
+    int32_t tiles;    // items of the pass
+    int32_t item0;    // index of its first item
+};
+
+constexpr int kSweepMaxPasses = 64;
+
+struct SweepPlan {
+    int32_t rows = 0;                        // rows per item
+    int32_t npass = 0;
+    int32_t items = 0;
+    double mean_deps = 0.0;
+    SweepPass* pass = nullptr;               // [npass] (device)
+    int32_t* dep_ptr = nullptr;              // [items + 1]
+    int32_t* dep = nullptr;                  // >= 0: an item; < 0: -(q + 1), all of pass q
+    uint32_t* flag = nullptr;                // [items] epoch of the last launch that finished it
+    unsigned long long* done = nullptr;      // [npass] items finished, all launches
+    unsigned long long* arrive = nullptr;    // blocks started, all launches (grid per launch)
+    int32_t grid = 0;                        // co-resident blocks of the cooperative launch
+    int32_t* failed = nullptr;               // set once a wait of this plan gave up
+};
+
 // One level of the hierarchy on the device.  Rows are stored in the level's
 // smoothing order: grouped by colour, inside a colour by coarse aggregate,
 // then by original index.  The off-diagonal part is kept in a sliced layout
@@ -118,6 +199,10 @@ struct DevLevel {
     int64_t padded = 0;               // entries of the padded sliced arrays
     int32_t width = 0;                // common slice width W (longest row)
     int64_t sw = 0;                   // slice stride 32 W
+    int64_t stage_cap = 0;            // entries a staged block (8 consecutive slices) needs at
+                                      // most when each slice keeps only its longest row's
+                                      // entries: 32 x max over 8-slice windows of the sum of
+                                      // the slices' longest rows
     int32_t ncolours = 0;
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
@@ -152,6 +237,12 @@ struct DevLevel {
     float* x32 = nullptr;
     float* b32 = nullptr;
     float* r32 = nullptr;
+    // smoothing sweeps as dependency-driven kernels (lane shapes only): the
+    // pre-smoother (first two colours from zero, forward, backward) and the
+    // post-smoother (forward, backward), planned for rows = block / lpr
+    bool sweep = false;
+    const SweepPlan* plan_pre = nullptr;
+    const SweepPlan* plan_post = nullptr;
 };
 
 // widest slice the fine-level (staged) kernels take: 256 rows x W entries of
@@ -292,6 +383,11 @@ void launch_residual_restrict(const DevLevel& L, const double* b, const double* 
 void launch_residual_restrict32(const DevLevel& L, const float* b, const float* x, float* r,
                                 float* bc, cudaStream_t s);
 void launch_prolong(const DevLevel& L, const double* e, double* x, double omega, cudaStream_t s);
+// blocks of a sweep launch: those that fit on the device at once
+int sweep_grid(int lanes, int block);
+// one smoothing sweep of plan P as one kernel (lane shapes, L.lpr lanes per row)
+void launch_sweep(const DevLevel& L, const SweepPlan& P, const double* b, double* x, cudaStream_t s);
+void launch_sweep32(const DevLevel& L, const SweepPlan& P, const float* b, float* x, cudaStream_t s);
 void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega, cudaStream_t s);
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s);
 void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaStream_t s);
@@ -315,19 +411,25 @@ void launch_cg_rz(int n, const double* r, const double* z, const double* zold, d
 void launch_cg_p(int n, const double* z, double* p, double* zold, const CgWork& w,
                  cudaStream_t s);
 
-// BiCGSTAB vector operations (level 0, float64); `out` receives up to two dot
-// products (device memory).  bi_spmv: y = A x, out = {w.y, y.y};
-// bi_axpy: outv = u + c v, out = {outv.outv}; bi_update: x += alpha y + w z,
-// r = s - w t, out = {r.r, rt.r}; bi_direction: p = r + beta (p - w v).
-void launch_bi_spmv(const DevLevel& L, const double* x, double* y, const double* w, bool self_dot,
-                    CgWork& wk, double* out, cudaStream_t s);
-void launch_bi_axpy(int n, const double* u, double c, const double* v, double* outv, CgWork& wk,
-                    double* out, cudaStream_t s);
-void launch_bi_update(int n, double* x, const double* y, const double* z, double alpha, double w,
-                      const double* sv, const double* t, double* r, const double* rt, CgWork& wk,
-                      double* out, cudaStream_t s);
-void launch_bi_direction(int n, const double* r, double beta, double w, const double* v, double* p,
+// BiCGSTAB (level 0, float64, smoothing order), scalars in *bs (device):
+// bi_start: r = b - A x, rt = r, start scalars; bi_direction: p = r (first
+// iteration) or r + beta (p - w v); bi_spmv: y = A x with rt.y -> alpha
+// (second = false) or s.y, y.y -> w (second = true); bi_half: s = r - alpha v,
+// s.s -> half-step test; bi_update: x += alpha y + w z, r = s - w t, r.r, rt.r
+// (x += alpha y only after a converged half step); bi_continue: the loop
+// condition of a WHILE graph node.
+void launch_bi_start(const DevLevel& L, const double* b, const double* x, double* r, double* rt,
+                     CgWork& wk, BiScalars* bs, cudaStream_t s);
+void launch_bi_direction(int n, const double* r, const double* v, double* p, const BiScalars* bs,
                          cudaStream_t s);
+void launch_bi_spmv(const DevLevel& L, const double* x, double* y, const double* w, bool second,
+                    CgWork& wk, BiScalars* bs, cudaStream_t s);
+void launch_bi_half(int n, const double* r, const double* v, double* sv, CgWork& wk,
+                    BiScalars* bs, cudaStream_t s);
+void launch_bi_update(int n, double* x, const double* y, const double* z, const double* sv,
+                      const double* t, double* r, const double* rt, CgWork& wk, BiScalars* bs,
+                      cudaStream_t s);
+void launch_bi_continue(cudaGraphConditionalHandle h, BiScalars* bs, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // setup on the device (setup_device.cu)
@@ -435,8 +537,12 @@ struct amg_ctx {
     AsyncCg acg;
     // BiCGSTAB vectors (level 0, smoothing order), allocated on first use
     double *rt = nullptr, *bv = nullptr, *by = nullptr, *bs = nullptr, *bt = nullptr;
-    double* dots = nullptr;           // [2] device dot products
-    double* dots_host = nullptr;      // [2] pinned mirror
+    // sweep plans by (level, lanes + 16 x block): the pre- and post-smoother
+    std::map<std::pair<int, int>, std::pair<amg::SweepPlan, amg::SweepPlan>> sweep_plans;
+    amg::BiScalars* bsc = nullptr;        // BiCGSTAB scalars (device)
+    amg::BiScalars* bsc_host = nullptr;   // pinned mirror
+    cudaGraphExec_t graph_bi[2] = {nullptr, nullptr};      // BiCGSTAB loop, per precision
+    int bi_graph_state[2] = {0, 0};       // 0 not built, 1 built, -1 refused
 
     amg_ctx() = default;
     amg_ctx(const amg_ctx&) = delete;
@@ -444,7 +550,9 @@ struct amg_ctx {
     ~amg_ctx() {
         if (sc_host) amg::pinned_free(sc_host);
         if (acg.rr_host) amg::pinned_free(acg.rr_host);
-        if (dots_host) amg::pinned_free(dots_host);
+        if (bsc_host) amg::pinned_free(bsc_host);
+        for (cudaGraphExec_t g : graph_bi)
+            if (g) cudaGraphExecDestroy(g);
         if (acg.ev) cudaEventDestroy(acg.ev);
         if (ev0) cudaEventDestroy(ev0);
         if (ev1) cudaEventDestroy(ev1);

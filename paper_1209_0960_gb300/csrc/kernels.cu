@@ -207,11 +207,19 @@ __host__ __device__ constexpr int lanes_of() { return LPR == kFine ? 1 : LPR; }
 template <int LPR>
 __host__ __device__ constexpr int unroll_of() { return LPR == 1 ? 24 : LPR == 2 ? 12 : kUnroll; }
 
-template <int LPR, int MODE, typename T, typename AccF>
+struct PdlWait {
+    __device__ void operator()() const { pdl_wait(); }
+};
+
+// Wait: what the row does between loading its first batch of setup-time
+// entries and reading the first vector value (the predecessor's completion,
+// or a dependency wait).
+template <int LPR, int MODE, typename T, typename AccF, typename Wait = PdlWait>
 __device__ __forceinline__ T row_update(int64_t base, int len, int width, int lane, int jmax,
                                         const int32_t* __restrict__ scol,
                                         const T* __restrict__ sval, const T* x,
-                                        const T* b, const T* __restrict__ dinv, AccF acc) {
+                                        const T* b, const T* __restrict__ dinv, AccF acc,
+                                        Wait wait = Wait()) {
     static_assert(LPR != kFine, "the fine level uses the staged kernels");
     // every lane of the warp runs the same number of batches (the slice width
     // bounds every row length), so the warp-wide votes below see all 32 lanes
@@ -233,7 +241,7 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
         }
     };
     load_batch(0);
-    pdl_wait();
+    wait();
     // two partial sums halve the chain of dependent float64 FMAs
     T s = lane == 0 ? acc() : T(0), s1 = T(0);
     for (int it = 0; it < batches; ++it) {
@@ -339,6 +347,125 @@ __global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
 }
 
 // ---------------------------------------------------------------------------
+// Dependency-driven sweep (see SweepPlan in device.h): every colour pass of a
+// symmetric Gauss-Seidel sweep in one launch, one block per item of rows.
+// The rows of an item are updated exactly as k_gs_pass (and, for the first
+// pass from a zero guess, k_first) updates them, so the results are those of
+// the pass-per-launch kernels; only the waits between passes differ.
+// ---------------------------------------------------------------------------
+constexpr long long kDepSpinLimit = 1LL << 20;   // polls per dependency (over a second)
+
+// polls are relaxed loads; once a warp has seen everything it waits for,
+// one acquire fence (after the warp barrier) orders the block's later reads
+__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void fence_acq_rel_gpu() { asm volatile("fence.acq_rel.gpu;" ::: "memory"); }
+__device__ __forceinline__ void st_release_u32(uint32_t* p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void red_release_add_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// A persistent grid of G co-resident blocks (a cooperative launch guarantees
+// co-residency); block g takes items g, g + G, g + 2G, ... in order.  An item
+// depends only on smaller items, and every block takes its items in
+// increasing order, so the block holding the smallest unfinished item always
+// has what it waits for: the sweep cannot deadlock.  The launch's epoch comes
+// from a counter of block arrivals (G per launch).
+template <int LPR, typename T>
+__global__ void __launch_bounds__(kBlock) k_sweep(int npass, const SweepPass* __restrict__ passes,
+                                                  int items, const int32_t* __restrict__ dep_ptr,
+                                                  const int32_t* __restrict__ dep, uint32_t* flag,
+                                                  unsigned long long* done,
+                                                  unsigned long long* arrive, int32_t* failed,
+                                                  int64_t sw, const uint16_t* __restrict__ rlen,
+                                                  const int32_t* __restrict__ scol,
+                                                  const T* __restrict__ sval,
+                                                  const T* __restrict__ dinv, const T* b, T* x,
+                                                  int32_t* err) {
+    __shared__ SweepPass sp[kSweepMaxPasses];
+    __shared__ uint32_t s_epoch;
+    __shared__ int s_ok;
+    for (int i = threadIdx.x; i < npass; i += blockDim.x) sp[i] = passes[i];
+    if (threadIdx.x == 0) {
+        s_epoch = (uint32_t)(atomicAdd(arrive, 1ull) / gridDim.x) + 1u;
+        s_ok = 1;
+    }
+    __syncthreads();
+    const uint32_t epoch = s_epoch;
+    constexpr int G = lanes_of<LPR>();
+    const int rows_per = (int)blockDim.x / G;
+    const int lane = (int)threadIdx.x % G;
+    int p = 0;
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        while (p + 1 < npass && sp[p + 1].item0 <= item) ++p;
+        const SweepPass P = sp[p];
+        const int row = (P.r0 & ~31) + (item - P.item0) * rows_per + (int)threadIdx.x / G;
+        const bool valid = row >= P.r0 && row < P.r1;
+        const int rr = valid ? row : P.r0;
+        const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
+        const T di = valid ? dinv[rr] : T(0);
+        const int len = (valid && !P.first) ? (int)rlen[rr] : 0;
+        // warp 0 polls the item's dependencies (a lane per dependency, bounded);
+        // the block then reads x
+        auto wait = [&] {
+            if (threadIdx.x < 32) {
+                bool ok = true;
+                const int k1 = dep_ptr[item + 1];
+                for (int k = dep_ptr[item] + (int)threadIdx.x; k < k1 && ok; k += 32) {
+                    const int d = dep[k];
+                    for (long long it = 0;; ++it) {
+                        bool sat;
+                        if (d >= 0) {
+                            sat = ld_relaxed_u32(flag + d) == epoch;
+                        } else {
+                            const int q = -d - 1;
+                            sat = ld_relaxed_u64(done + q) >=
+                                  (unsigned long long)epoch * (unsigned long long)sp[q].tiles;
+                        }
+                        if (sat) break;
+                        if (it >= kDepSpinLimit || *(volatile int32_t*)failed != 0) {
+                            ok = false;
+                            break;
+                        }
+                        __nanosleep(32);
+                    }
+                }
+                ok = __all_sync(0xffffffffu, ok);
+                __syncwarp();   // orders every lane's polls before lane 0's acquire fence
+                if (threadIdx.x == 0) {
+                    fence_acq_rel_gpu();
+                    if (!ok) {
+                        s_ok = 0;
+                        atomicExch(failed, 1);
+                        atomicExch(err, AMG_ETIMEOUT);
+                    }
+                }
+            }
+            __syncthreads();
+        };
+        const T v = row_update<LPR, kNbrX, T>(base, len, (int)(sw >> 5), lane, P.jmax, scol, sval, x,
+                                              b, dinv, [&] { return valid ? b[rr] : T(0); }, wait);
+        if (!s_ok) return;
+        if (valid && lane == 0) x[rr] = v * di;
+        __syncthreads();
+        if (threadIdx.x == 0) {   // release: the block's writes (ordered by the barrier) first
+            st_release_u32(flag + item, epoch);
+            red_release_add_u64(done + p, 1ull);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Fine-level kernels: the matrix staged in shared memory by the bulk-copy
 // engine.
 //
@@ -361,38 +488,6 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Start the copy of `nsl` slices from slice `slice0` (width W) into s_col /
-// s_val, completing on the mbarrier `bar` (initialised here; the caller
-// synchronises the block before any thread waits on it).  Thread 0 only.
-template <typename T>
-__device__ void stage_issue(int64_t slice0, int nsl, int width, const int32_t* scol, const T* sval,
-                            int32_t* s_col, T* s_val, uint64_t* bar) {
-    const uint32_t ub = smem_u32(bar);
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    if (width == 0 || nsl <= 0) {
-        uint64_t st;
-        asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(st) : "r"(ub) : "memory");
-        return;
-    }
-    const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
-    const uint32_t bc = ent * 4u, bv = ent * (uint32_t)sizeof(T);
-    const int64_t e0 = slice0 * 32 * width;
-    uint64_t pol, state;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                 : "=l"(state) : "r"(ub), "r"(bc + bv) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(bc), "r"(ub),
-        "l"(pol) : "memory");
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0), "r"(bv), "r"(ub),
-        "l"(pol) : "memory");
-}
-
 // Every thread of the block: wait (bounded) for the copies on `bar`.  Returns
 // false, with AMG_ETIMEOUT recorded in *err, if they have not completed within
 // the spin limit; the decision is one for the whole block, so that no thread
@@ -410,15 +505,103 @@ __device__ bool stage_wait(uint64_t* bar, int32_t* err, long long limit = kStage
     return all != 0;
 }
 
-// Stage `nsl` slices starting at slice `slice0` (width W) into s_col / s_val.
-// Every thread of the block calls it.  Returns false, with AMG_ETIMEOUT
-// recorded in *err, if the copies have not completed within the spin limit.
+// Stage the block's `nsl` slices, starting at slice `slice0` (width W of the
+// sliced layout), into shared memory.  Unpacked (levels whose rows are nearly
+// all W long, like the fine level): the block's slices as they are, two
+// copies.  Packed: slice w keeps only its first
+// K_w entries per row, K_w = the longest row of the slice inside the launch
+// (`len` is this thread's row length, 0 for rows outside it), and its entries
+// follow the previous slice's.  So the padding of a level whose rows vary in
+// length is neither copied nor allotted shared memory, and the block needs
+// only sum_w K_w * 32 entries (the level's stage capacity bounds it), which
+// keeps more blocks resident.  When every slice is full (K_w = W, as on
+// structured levels) the packed layout is the global one and two copies move
+// the whole block; otherwise one copy per array and slice.  Thread 0 issues
+// every copy against one mbarrier.  Every thread of the block calls this and
+// gets the position of its row's entry 0 (entry k at loc + 32 k).  Returns
+// false, with AMG_ETIMEOUT recorded in *err, if the copies have not completed
+// within the spin limit.
 template <typename T>
-__device__ bool stage_slices(int64_t slice0, int nsl, int width, const int32_t* scol,
-                             const T* sval, int32_t* s_col, T* s_val, uint64_t* bar,
-                             int32_t* err) {
+__device__ bool stage_slices(int64_t slice0, int nsl, int width, int len, bool packed,
+                             const int32_t* scol, const T* sval, int32_t* s_col, T* s_val,
+                             uint64_t* bar, int32_t* err, int& loc) {
+    __shared__ int ksh[kSlicesPerBlock];
+    const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+    loc = lane;
     if (width == 0) return true;   // no off-diagonal entries: nothing to stage
-    if (threadIdx.x == 0) stage_issue(slice0, nsl, width, scol, sval, s_col, s_val, bar);
+    if (!packed) {
+        // every slice at its full width: the global layout, two copies
+        loc = w * 32 * width + lane;
+        if (threadIdx.x == 0) {
+            const uint32_t ub = smem_u32(bar);
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
+            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
+            const int64_t e0 = slice0 * 32 * width;
+            uint64_t state, pol;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                         : "=l"(state) : "r"(ub), "r"(ent * (4u + (uint32_t)sizeof(T))) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(ent * 4u),
+                "r"(ub), "l"(pol) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0),
+                "r"(ent * (uint32_t)sizeof(T)), "r"(ub), "l"(pol) : "memory");
+        }
+        __syncthreads();
+        return stage_wait(bar, err);
+    }
+    const int k = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
+    if (lane == 0) ksh[w] = w < nsl ? k : 0;
+    __syncthreads();
+    int off = 0, total = 0;
+    for (int i = 0; i < nsl; ++i) {
+        off += i < w ? ksh[i] : 0;
+        total += ksh[i];
+    }
+    loc = 32 * off + lane;
+    if (threadIdx.x == 0) {
+        const uint32_t ub = smem_u32(bar);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        uint64_t state;
+        if (total == 0) {
+            asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(ub) : "memory");
+        } else {
+            const uint32_t ent = 32u * (uint32_t)total;
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                         : "=l"(state) : "r"(ub), "r"(ent * (4u + (uint32_t)sizeof(T))) : "memory");
+            uint64_t pol;
+            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+            auto copy = [&](void* dst, const void* src, uint32_t bytes) {
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                    " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(ub),
+                    "l"(pol) : "memory");
+            };
+            if (total == nsl * width) {
+                const int64_t e0 = slice0 * 32 * width;
+                copy(s_col, scol + e0, ent * 4u);
+                copy(s_val, sval + e0, ent * (uint32_t)sizeof(T));
+            } else {
+                int o = 0;
+                for (int i = 0; i < nsl; ++i) {
+                    const int ki = ksh[i];
+                    if (ki > 0) {
+                        const int64_t e0 = (slice0 + i) * 32 * width;
+                        copy(s_col + 32 * o, scol + e0, 128u * (uint32_t)ki);
+                        copy(s_val + 32 * o, sval + e0, 32u * (uint32_t)ki * (uint32_t)sizeof(T));
+                    }
+                    o += ki;
+                }
+            }
+        }
+    }
     __syncthreads();
     return stage_wait(bar, err);
 }
@@ -440,22 +623,25 @@ __global__ void k_wait_selftest(int32_t* err, long long limit) {
     stage_wait(&bar, err, limit > 0 ? limit : kStageSpinLimit);
 }
 
-// The block's slices, its shared-memory tiles and this thread's row.
+// The block's slices, its shared-memory tiles and this thread's row.  The
+// tiles hold up to `cap` entries (the level's stage capacity): column indices
+// first, then values.
 template <typename T>
 struct FineTile {
     int64_t slice0;
     int nsl;
     int row;
-    int loc;          // offset of this row's entry 0 in the tiles; entry k at loc + 32 k
+    int loc;          // offset of this row's entry 0 in the tiles (entry k at loc + 32 k),
+                      // set by stage_slices
     int32_t* s_col;
     T* s_val;
-    __device__ FineTile(int r0, int64_t nslices, int width, unsigned char* smem) {
+    __device__ FineTile(int r0, int64_t nslices, int64_t cap, unsigned char* smem) {
         slice0 = (int64_t)(r0 >> 5) + (int64_t)blockIdx.x * kSlicesPerBlock;
         nsl = (int)min((int64_t)kSlicesPerBlock, nslices - slice0);
         row = (int)(slice0 * 32) + (int)threadIdx.x;
-        loc = (int)(threadIdx.x >> 5) * 32 * width + (int)(threadIdx.x & 31);
+        loc = (int)(threadIdx.x & 31);
         s_col = reinterpret_cast<int32_t*>(smem);
-        s_val = reinterpret_cast<T*>(smem + (size_t)kFineBlock * width * sizeof(int32_t));
+        s_val = reinterpret_cast<T*>(smem + (size_t)cap * sizeof(int32_t));
     }
 };
 
@@ -506,7 +692,7 @@ __global__ void __launch_bounds__(kBlock) k_fine_first0(int c1, int nb, const T*
 // z_i = x_i / s_i (isq = 1/s).
 template <typename T>
 __global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jmax, int width,
-                                                      int64_t nslices,
+                                                      int64_t nslices, int64_t cap,
                                                       const uint16_t* __restrict__ rlen,
                                                       const int32_t* scol, const T* sval,
                                                       const T* __restrict__ dinv, const T* b, T* x,
@@ -515,11 +701,13 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jm
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     pdl_launch_dependents();
-    const FineTile<T> F(r0, nslices, width, smem);
+    FineTile<T> F(r0, nslices, cap, smem);
     const bool valid = F.row >= r0 && F.row < r1;
     const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
     const T di = valid ? __ldcs(dinv + F.row) : T(0);
-    if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
+    if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
+                      F.s_col, F.s_val, &bar, err, F.loc))
+        return;
     pdl_wait();
     if (!valid) return;
     const T xi = fine_row<T>(F, len, jmax, [&](int j) { return x[j]; }, b[F.row]) * di;
@@ -530,7 +718,7 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jm
 // k_residual on the fine level
 template <typename T>
 __global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int width,
-                                                          int64_t nslices,
+                                                          int64_t nslices, int64_t cap,
                                                           const uint16_t* __restrict__ rlen,
                                                           const int32_t* scol, const T* sval,
                                                           const T* __restrict__ diag, const T* b,
@@ -538,11 +726,13 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bar;
     pdl_launch_dependents();
-    const FineTile<T> F(r0, nslices, width, smem);
+    FineTile<T> F(r0, nslices, cap, smem);
     const bool valid = F.row >= r0 && F.row < n;
     const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
     const T dg = valid ? __ldcs(diag + F.row) : T(0);
-    if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
+    if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
+                      F.s_col, F.s_val, &bar, err, F.loc))
+        return;
     pdl_wait();
     if (!valid) return;
     r[F.row] = fine_row<T>(F, len, n, [&](int j) { return x[j]; }, fmad(-dg, x[F.row], b[F.row]));
@@ -559,7 +749,7 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int
 // the sum stays deterministic.
 template <typename T, bool SCALED>
 __global__ void __launch_bounds__(kFineBlock) k_fine_residual_restrict(
-    int c1, int n, int width, int64_t nslices, const uint16_t* __restrict__ rlen,
+    int c1, int n, int width, int64_t nslices, int64_t cap, const uint16_t* __restrict__ rlen,
     const int32_t* scol, const T* sval, const T* __restrict__ diag, const T* b, const T* x,
     const int32_t* __restrict__ agg, const T* __restrict__ t, T* bc, int32_t* err) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -567,13 +757,15 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_residual_restrict(
     __shared__ T sv[kFineBlock];
     __shared__ int sk[kFineBlock];
     pdl_launch_dependents();
-    const FineTile<T> F(c1, nslices, width, smem);
+    FineTile<T> F(c1, nslices, cap, smem);
     const bool valid = F.row >= c1 && F.row < n;
     const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
     const T dg = valid ? __ldcs(diag + F.row) : T(0);
     const int key = valid ? __ldcs(agg + F.row) : -1;
     const T ti = (SCALED && valid) ? __ldcs(t + F.row) : T(1);
-    if (!stage_slices(F.slice0, F.nsl, width, scol, sval, F.s_col, F.s_val, &bar, err)) return;
+    if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
+                      F.s_col, F.s_val, &bar, err, F.loc))
+        return;
     pdl_wait();
     T v = T(0);
     if (valid) {
@@ -933,12 +1125,19 @@ __global__ void __launch_bounds__(kBlock) k_cg_p(int n, const double* __restrict
 }
 
 // ---------------------------------------------------------------------------
-// BiCGSTAB vector operations (level 0, float64, smoothing order).  Each
-// returns up to two dot products through the deterministic last-block
-// reduction: per-block sums in a fixed grid, combined in block order.
+// BiCGSTAB (level 0, float64, smoothing order) with its scalars on the device.
+// Each kernel that ends in dot products combines them with the deterministic
+// last-block reduction and applies the scalar step of the iteration there, so
+// the iteration needs no host round trip: the host-driven loop reads the
+// scalars once per iteration, the graph loop never.  A kernel whose work the
+// iteration no longer needs (after a breakdown, or after the first half step
+// met the tolerance) returns before touching anything; the decision reads
+// scalars written by an earlier kernel, so it is the same for every block.
 // ---------------------------------------------------------------------------
-__device__ void finish_dots(double v0, double v1, double* partials, double* partials2,
-                            unsigned int* counter, double* out, double* sh) {
+enum BiMode : int { kBiStart = 0, kBiRtv = 1, kBiHalf = 2, kBiW = 3, kBiUpdate = 4 };
+
+__device__ void finish_bi(double v0, double v1, double* partials, double* partials2,
+                          unsigned int* counter, BiScalars* bs, int mode, double* sh) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
         partials[blockIdx.x] = v0;
@@ -958,67 +1157,167 @@ __device__ void finish_dots(double v0, double v1, double* partials, double* part
     b = block_sum(b, sh);
     if (threadIdx.x != 0) return;
     *counter = 0u;
-    out[0] = a;
-    out[1] = b;
+    switch (mode) {
+        case kBiStart:   // a = r.r
+            bs->r0 = sqrt(a);
+            bs->rho = a;
+            bs->rho_prev = 1.0;
+            bs->alpha = 1.0;
+            bs->w = 1.0;
+            bs->rel = bs->r0 > 0.0 ? 1.0 : 0.0;
+            bs->done = !(bs->rel > bs->tol);
+            bs->iters = 0;
+            bs->status = 0;
+            bs->half = 0;
+            bs->why = 0;
+            bs->loops = 0;
+            break;
+        case kBiRtv:     // a = rt.v
+            bs->rtv = a;
+            if (a == 0.0) {
+                bs->status = AMG_ENOTCONV;
+                bs->why = 2;
+            } else {
+                bs->alpha = bs->rho / a;
+            }
+            break;
+        case kBiHalf: {  // a = s.s
+            bs->iters += 1;
+            const double srel = sqrt(a) / bs->r0;
+            if (srel <= bs->tol) {
+                bs->half = 1;
+                bs->done = 1;
+                bs->rel = srel;
+            }
+            break;
+        }
+        case kBiW:       // a = t.s, b = t.t
+            bs->ts = a;
+            bs->tt = b;
+            if (b == 0.0) {
+                bs->status = AMG_ENOTCONV;
+                bs->why = 3;
+            } else {
+                bs->w = a / b;
+            }
+            break;
+        default:         // kBiUpdate: a = r.r, b = rt.r
+            bs->rel = sqrt(a) / bs->r0;
+            bs->rho_prev = bs->rho;
+            bs->rho = b;
+            bs->done = !(bs->rel > bs->tol);
+            break;
+    }
 }
 
-// y = A x; out[0] = w.y (w may be null), out[1] = y.y when self_dot
+// r = b - A x, rt = r, and the start scalars from r.r
+__global__ void __launch_bounds__(kBlock) k_bi_start(int n, int64_t sw,
+                                                     const uint16_t* __restrict__ rlen,
+                                                     const int32_t* __restrict__ scol,
+                                                     const double* __restrict__ sval,
+                                                     const double* __restrict__ diag,
+                                                     const double* b, const double* x, double* r,
+                                                     double* rt, double* partials, double* partials2,
+                                                     unsigned int* counter, BiScalars* bs) {
+    __shared__ double sh[kBlock / 32];
+    pdl_launch_dependents();
+    pdl_wait();
+    double a = 0.0;
+    for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
+        const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
+        const double s0 = fmad(-__ldcs(diag + row), x[row], b[row]);
+        const double v = sell_row<true>(base, __ldcs(rlen + row), scol, sval, x, s0);
+        r[row] = v;
+        rt[row] = v;
+        a = fmad(v, v, a);
+    }
+    const double ta = block_sum(a, sh);
+    finish_bi(ta, 0.0, partials, partials2, counter, bs, kBiStart, sh);
+}
+
+// search direction: p = r on the first iteration, else
+// p = r + beta (p - w v) with beta = (rho / rho_prev) (alpha / w)
+__global__ void __launch_bounds__(kBlock) k_bi_direction(int n, const double* r, const double* v,
+                                                         double* p, const BiScalars* bs) {
+    pdl_launch_dependents();
+    pdl_wait();
+    if (bs->done || bs->status) return;
+    const bool first = bs->iters == 0;
+    const double w = bs->w;
+    const double beta = (bs->rho / bs->rho_prev) * (bs->alpha / w);
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        p[i] = first ? r[i] : r[i] + beta * (p[i] - w * v[i]);
+}
+
+// y = A x with the dot products of the mode: kBiRtv: rt.y; kBiW: s.y and y.y
+// (skipped once the iteration has stopped)
 __global__ void __launch_bounds__(kBlock) k_bi_spmv(int n, int64_t sw,
                                                     const uint16_t* __restrict__ rlen,
                                                     const int32_t* __restrict__ scol,
                                                     const double* __restrict__ sval,
                                                     const double* __restrict__ diag,
                                                     const double* x, double* y, const double* w,
-                                                    int self_dot, double* partials,
-                                                    double* partials2, unsigned int* counter,
-                                                    double* out) {
+                                                    double* partials, double* partials2,
+                                                    unsigned int* counter, BiScalars* bs, int mode) {
     __shared__ double sh[kBlock / 32];
     pdl_launch_dependents();
     pdl_wait();
+    if (bs->status || (mode == kBiW && bs->half)) return;
     double a = 0.0, b = 0.0;
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double v = sell_row<false>(base, __ldcs(rlen + row), scol, sval, x,
                                          __ldcs(diag + row) * x[row]);
         y[row] = v;
-        if (w) a = fmad(w[row], v, a);
-        if (self_dot) b = fmad(v, v, b);
+        a = fmad(w[row], v, a);
+        if (mode == kBiW) b = fmad(v, v, b);
     }
     const double ta = block_sum(a, sh);
     const double tb = block_sum(b, sh);
-    finish_dots(ta, tb, partials, partials2, counter, out, sh);
+    finish_bi(ta, tb, partials, partials2, counter, bs, mode, sh);
 }
 
-// out_vec = u + c v; out[0] = out_vec.out_vec
-__global__ void __launch_bounds__(kBlock) k_bi_axpy(int n, const double* u, double c,
-                                                    const double* v, double* outv,
-                                                    double* partials, double* partials2,
-                                                    unsigned int* counter, double* out) {
+// s = r - alpha v and s.s (the half-step test)
+__global__ void __launch_bounds__(kBlock) k_bi_half(int n, const double* r, const double* v,
+                                                    double* sv, double* partials,
+                                                    double* partials2, unsigned int* counter,
+                                                    BiScalars* bs) {
     __shared__ double sh[kBlock / 32];
     pdl_launch_dependents();
     pdl_wait();
+    if (bs->status) return;
+    const double c = -bs->alpha;
     double a = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        const double o = fmad(c, v[i], u[i]);
-        outv[i] = o;
+        const double o = fmad(c, v[i], r[i]);
+        sv[i] = o;
         a = fmad(o, o, a);
     }
     const double ta = block_sum(a, sh);
-    finish_dots(ta, 0.0, partials, partials2, counter, out, sh);
+    finish_bi(ta, 0.0, partials, partials2, counter, bs, kBiHalf, sh);
 }
 
-// x += alpha y + w z; r = s - w t; out[0] = r.r, out[1] = rt.r
+// x += alpha y + w z, r = s - w t, r.r and rt.r; after a converged half step
+// only x += alpha y
 __global__ void __launch_bounds__(kBlock) k_bi_update(int n, double* x, const double* y,
-                                                      const double* z, double alpha, double w,
-                                                      const double* s, const double* t,
-                                                      double* r, const double* rt,
+                                                      const double* z, const double* s,
+                                                      const double* t, double* r, const double* rt,
                                                       double* partials, double* partials2,
-                                                      unsigned int* counter, double* out) {
+                                                      unsigned int* counter, BiScalars* bs) {
     __shared__ double sh[kBlock / 32];
     pdl_launch_dependents();
     pdl_wait();
+    if (bs->status) return;
+    const double alpha = bs->alpha;
+    const int stride = gridDim.x * blockDim.x;
+    if (bs->half) {
+        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+            x[i] = fmad(alpha, y[i], x[i]);
+        return;
+    }
+    const double w = bs->w;
     double a = 0.0, b = 0.0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         x[i] = x[i] + alpha * y[i] + w * z[i];
         const double ri = s[i] - w * t[i];
         r[i] = ri;
@@ -1027,16 +1326,16 @@ __global__ void __launch_bounds__(kBlock) k_bi_update(int n, double* x, const do
     }
     const double ta = block_sum(a, sh);
     const double tb = block_sum(b, sh);
-    finish_dots(ta, tb, partials, partials2, counter, out, sh);
+    finish_bi(ta, tb, partials, partials2, counter, bs, kBiUpdate, sh);
 }
 
-// p = r + beta (p - w v)
-__global__ void __launch_bounds__(kBlock) k_bi_direction(int n, const double* r, double beta,
-                                                         double w, const double* v, double* p) {
-    pdl_launch_dependents();
-    pdl_wait();
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        p[i] = r[i] + beta * (p[i] - w * v[i]);
+// Condition of the BiCGSTAB loop (a WHILE graph node), evaluated before every
+// iteration: stop once converged or broken down, at maxit, or when
+// rho = rt.r is zero (a breakdown); the evaluation count is a second bound.
+__global__ void k_bi_continue(cudaGraphConditionalHandle h, BiScalars* bs) {
+    const int32_t loops = ++bs->loops;
+    const int go = bi_continue(*bs) && loops <= bs->maxit + 1;
+    cudaGraphSetConditional(h, go ? 1u : 0u);
 }
 
 inline int blocks_for(int64_t threads) { return (int)((threads + kBlock - 1) / kBlock); }
@@ -1114,7 +1413,7 @@ inline int fine_blocks(int r0, int r1) {
 inline int64_t fine_nslices(const DevLevel& L) { return ((int64_t)L.n + 31) / 32; }
 template <typename K>
 size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
-    const size_t bytes = (size_t)kFineBlock * L.width * (sizeof(int32_t) + value_bytes);
+    const size_t bytes = (size_t)L.stage_cap * (sizeof(int32_t) + value_bytes);
     // the 48 KB default covers static and dynamic shared memory together
     if (bytes > kDefaultDynSmem) raise_dyn_smem(kernel, bytes);
     return bytes;
@@ -1134,7 +1433,7 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
         if (c2 > c1) {
             auto k = k_fine_pass<T>;
             launch_kernel(k, fine_blocks(c1, c2), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, c2,
-                          c1, L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x,
+                          c1, L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.dinv, b, x,
                           (double*)nullptr, (const double*)nullptr, L.err);
         }
         return;
@@ -1157,7 +1456,7 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, cudaStrea
     if (L.lpr == kFine) {
         auto k = k_fine_pass<T>;
         launch_kernel(k, fine_blocks(r0, r1), kFineBlock, fine_smem(k, L, sizeof(T)), s, r0, r1, jmax,
-                      L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.dinv, b, x, z_out, isq,
+                      L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.dinv, b, x, z_out, isq,
                       L.err);
         return;
     }
@@ -1177,7 +1476,7 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
         if (L.n > c1) {
             auto k = k_fine_residual_restrict<T, SC>;
             launch_kernel(k, fine_blocks(c1, L.n), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
-                          L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, L.agg,
+                          L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg,
                           A.t, bc, L.err);
         }
         return;
@@ -1186,7 +1485,7 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
         if (L.lpr == kFine) {
             auto k = k_fine_residual<T>;
             launch_kernel(k, fine_blocks(c1, L.n), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
-                          L.width, fine_nslices(L), L.rlen, L.scol, A.sval, A.diag, b, x, r, L.err);
+                          L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.diag, b, x, r, L.err);
         } else {
             AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1),
                              (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR, L.block),
@@ -1205,6 +1504,64 @@ void prolong_impl(const DevLevel& L, const T* e, T* x, double omega, cudaStream_
     if (L.n <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
     launch_kernel(k_prolong<T, SC>, blocks_for(L.n - r0), kBlock, 0, s, r0, L.n, L.agg, A.t, e, x, (T)omega);
+}
+
+template <int LPR, typename T>
+void sweep_launch(const DevLevel& L, const SweepPlan& P, const T* sval, const T* dinv, const T* b,
+                  T* x, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)P.grid);
+    cfg.blockDim = dim3((unsigned)L.block);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e =
+        cudaLaunchKernelEx(&cfg, k_sweep<LPR, T>, P.npass, (const SweepPass*)P.pass, P.items,
+                           (const int32_t*)P.dep_ptr, (const int32_t*)P.dep, P.flag, P.done,
+                           P.arrive, P.failed, L.sw, (const uint16_t*)L.rlen,
+                           (const int32_t*)L.scol, sval, dinv, b, x, L.err);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        throw Error{AMG_ECUDA, std::string("sweep launch (grid ") + std::to_string(P.grid) +
+                                   ") failed: " + cudaGetErrorString(e)};
+    }
+}
+
+template <typename T>
+void sweep_impl(const DevLevel& L, const SweepPlan& P, const T* b, T* x, cudaStream_t s) {
+    const LevelArrays<T> A(L);
+    if (P.items <= 0) return;
+    if (L.lpr < 1 || P.rows * L.lpr != L.block || P.npass > kSweepMaxPasses || P.grid < 1)
+        throw Error{AMG_EINVAL, "sweep plan does not match the level's launch shape"};
+    AMG_LPR_DISPATCH(L.lpr, (sweep_launch<LPR, T>(L, P, A.sval, A.dinv, b, x, s)));
+}
+
+template <int LPR>
+int sweep_blocks_per_sm(int block) {
+    int a = 0, b = 0;
+    AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_sweep<LPR, double>, block, 0));
+    AMG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_sweep<LPR, float>, block, 0));
+    return std::min(a, b);
+}
+
+// co-resident blocks of the sweep kernel with `lanes` lanes per row and
+// `block` threads, in both precisions: the grid of its cooperative launch
+int sweep_grid(int lanes, int block) {
+    int dev = 0, sms = 0, per_sm = 0;
+    AMG_CUDA_TRY(cudaGetDevice(&dev));
+    AMG_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    AMG_LPR_DISPATCH(lanes, (per_sm = sweep_blocks_per_sm<LPR>(block)));
+    return std::max(1, per_sm) * sms;
+}
+
+void launch_sweep(const DevLevel& L, const SweepPlan& P, const double* b, double* x, cudaStream_t s) {
+    sweep_impl<double>(L, P, b, x, s);
+}
+void launch_sweep32(const DevLevel& L, const SweepPlan& P, const float* b, float* x, cudaStream_t s) {
+    sweep_impl<float>(L, P, b, x, s);
 }
 
 void launch_first(const DevLevel& L, const double* b, double* x, double* bc_zero, int nc,
@@ -1342,29 +1699,40 @@ void launch_cg_p(int n, const double* z, double* p, double* zold, const CgWork& 
     launch_kernel(k_cg_p, reduction_blocks(n), kBlock, 0, s, n, z, p, zold, w.sc);
 }
 
-void launch_bi_spmv(const DevLevel& L, const double* x, double* y, const double* w, bool self_dot,
-                    CgWork& wk, double* out, cudaStream_t s) {
-    launch_kernel(k_bi_spmv, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol,
-                  L.sval, L.diag, x, y, w, (int)self_dot, wk.partials, wk.partials2,
-                  wk.counters + 4, out);
+void launch_bi_start(const DevLevel& L, const double* b, const double* x, double* r, double* rt,
+                     CgWork& wk, BiScalars* bs, cudaStream_t s) {
+    launch_kernel(k_bi_start, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol,
+                  L.sval, L.diag, b, x, r, rt, wk.partials, wk.partials2, wk.counters + 4, bs);
 }
 
-void launch_bi_axpy(int n, const double* u, double c, const double* v, double* outv, CgWork& wk,
-                    double* out, cudaStream_t s) {
-    launch_kernel(k_bi_axpy, reduction_blocks(n), kBlock, 0, s, n, u, c, v, outv, wk.partials,
-                  wk.partials2, wk.counters + 5, out);
-}
-
-void launch_bi_update(int n, double* x, const double* y, const double* z, double alpha, double w,
-                      const double* sv, const double* t, double* r, const double* rt, CgWork& wk,
-                      double* out, cudaStream_t s) {
-    launch_kernel(k_bi_update, reduction_blocks(n), kBlock, 0, s, n, x, y, z, alpha, w, sv, t, r,
-                  rt, wk.partials, wk.partials2, wk.counters + 6, out);
-}
-
-void launch_bi_direction(int n, const double* r, double beta, double w, const double* v, double* p,
+void launch_bi_direction(int n, const double* r, const double* v, double* p, const BiScalars* bs,
                          cudaStream_t s) {
-    launch_kernel(k_bi_direction, reduction_blocks(n), kBlock, 0, s, n, r, beta, w, v, p);
+    launch_kernel(k_bi_direction, reduction_blocks(n), kBlock, 0, s, n, r, v, p, bs);
+}
+
+void launch_bi_spmv(const DevLevel& L, const double* x, double* y, const double* w, bool second,
+                    CgWork& wk, BiScalars* bs, cudaStream_t s) {
+    launch_kernel(k_bi_spmv, reduction_blocks(L.n), kBlock, 0, s, L.n, L.sw, L.rlen, L.scol,
+                  L.sval, L.diag, x, y, w, wk.partials, wk.partials2, wk.counters + (second ? 6 : 5),
+                  bs, second ? (int)kBiW : (int)kBiRtv);
+}
+
+void launch_bi_half(int n, const double* r, const double* v, double* sv, CgWork& wk,
+                    BiScalars* bs, cudaStream_t s) {
+    launch_kernel(k_bi_half, reduction_blocks(n), kBlock, 0, s, n, r, v, sv, wk.partials,
+                  wk.partials2, wk.counters + 7, bs);
+}
+
+void launch_bi_update(int n, double* x, const double* y, const double* z, const double* sv,
+                      const double* t, double* r, const double* rt, CgWork& wk, BiScalars* bs,
+                      cudaStream_t s) {
+    launch_kernel(k_bi_update, reduction_blocks(n), kBlock, 0, s, n, x, y, z, sv, t, r, rt,
+                  wk.partials, wk.partials2, wk.counters + 8, bs);
+}
+
+void launch_bi_continue(cudaGraphConditionalHandle h, BiScalars* bs, cudaStream_t s) {
+    k_bi_continue<<<1, 1, 0, s>>>(h, bs);
+    AMG_CUDA_TRY(cudaGetLastError());
 }
 
 }  // namespace amg

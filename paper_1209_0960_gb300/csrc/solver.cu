@@ -76,7 +76,10 @@ void upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
 // original index).  Aggregates are numbered in the order the greedy front built
 // them, so consecutive rows stay spatially close (x gathers hit in cache) and
 // the members of one aggregate are contiguous inside each colour.  Rows outside
-// every aggregate come last inside their colour.
+// every aggregate come last inside their colour.  (Ordering the rows of each
+// 256-row window by length, to cut the padding of the sliced layout, was
+// measured slower on the 512^3 anisotropic workload: the coarse levels lost
+// more to the scattered restriction and gathers than the staging saved.)
 std::vector<int32_t> smoothing_order(const HostLevel& h) {
     const int32_t n = h.A.n;
     std::vector<int32_t> idx(n);
@@ -171,6 +174,7 @@ void fill_info(amg_ctx* c) {
         li.vcycle_bytes_fp32 = level_vcycle_bytes(d, last, 4, c->p.coarsest_fp32 ? 4 : 8);
         li.lanes_per_row = last ? 0 : d.lpr;
         li.threads_per_block = last ? 0 : d.block;
+        li.sweep = (!last && d.sweep) ? 1 : 0;
         b64 += li.vcycle_bytes_fp64;
         b32 += li.vcycle_bytes_fp32;
         if (l == 0) nnz0 = li.nnz;
@@ -207,7 +211,8 @@ struct ProfScope {
     ProfScope(amg_ctx* c_, int kind, double bytes, bool graph_level = false) : c(c_) {
         Profiler& P = c->prof;
         const bool rec = graph_level ? P.graphs : P.on;
-        if (!rec || P.next + 2 > (int)P.events.size()) return;
+        if (!rec) return;
+        if (P.next + 2 > (int)P.events.size() && !grow(P)) return;
         idx = P.next;
         P.next += 2;
         cudaEventRecord(P.events[idx], c->stream);
@@ -215,6 +220,25 @@ struct ProfScope {
     }
     ~ProfScope() {
         if (idx >= 0) cudaEventRecord(c->prof.events[idx + 1], c->stream);
+    }
+    // a long solve outgrows the event pool: double it (up to 2^21 events),
+    // never while the stream is being captured
+    bool grow(Profiler& P) {
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone) {
+            cudaGetLastError();
+            return false;
+        }
+        const size_t old = P.events.size();
+        if (old >= (size_t(1) << 21)) return false;
+        P.events.resize(std::max<size_t>(2 * old, 1024), nullptr);
+        for (size_t k = old; k < P.events.size(); ++k)
+            if (cudaEventCreate(&P.events[k]) != cudaSuccess) {
+                cudaGetLastError();
+                P.events.resize(k & ~size_t(1));
+                return P.next + 2 <= (int)P.events.size();
+            }
+        return true;
     }
 };
 
@@ -255,6 +279,8 @@ inline void k_resres(const DevLevel& L, const double* b, const double* x, double
 inline void k_resres(const DevLevel& L, const float* b, const float* x, float* r, float* bc, cudaStream_t s) { launch_residual_restrict32(L, b, x, r, bc, s); }
 inline void k_prolong(const DevLevel& L, const double* e, double* x, double w, cudaStream_t s) { launch_prolong(L, e, x, w, s); }
 inline void k_prolong(const DevLevel& L, const float* e, float* x, double w, cudaStream_t s) { launch_prolong32(L, e, x, w, s); }
+inline void k_sweep(const DevLevel& L, const SweepPlan& P, const double* b, double* x, cudaStream_t s) { launch_sweep(L, P, b, x, s); }
+inline void k_sweep(const DevLevel& L, const SweepPlan& P, const float* b, float* x, cudaStream_t s) { launch_sweep32(L, P, b, x, s); }
 inline void k_coarsest(amg_ctx* c, const double* b, double* x) { launch_dense_gemv(c->nL, c->Ainv, b, x, c->stream); }
 inline void k_coarsest(amg_ctx* c, const float* b, float* x) {
     if (c->Ainv_s32) launch_dense_gemv_f32(c->nL, c->ld32, c->Ainv_s32, b, x, c->stream);
@@ -278,17 +304,26 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     DevLevel& N = c->dl[l + 1];
     const int C = L.ncolours;
     const int kind = l == 0 ? kKGsL0 : kKGsCoarse;
-    {
-        ProfScope ps(c, l == 0 ? kKFirstL0 : kKGsCoarse, first_bytes(L, vb));
-        k_first(L, b, x, L.fused_restrict ? P::b(N) : (T*)nullptr, N.n, s);
-    }
-    for (int col = 2; col < C; ++col) {
-        ProfScope ps(c, kind, pass_bytes(L, col, L.cptr[col], vb));
-        k_pass(L, col, L.cptr[col], b, x, s);
-    }
-    for (int col = C - 2; col >= 0; --col) {
-        ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
-        k_pass(L, col, L.n, b, x, s);
+    if (L.sweep) {
+        // the whole pre-smoother as one dependency-driven kernel
+        double bytes = first_bytes(L, vb);
+        for (int col = 2; col < C; ++col) bytes += pass_bytes(L, col, L.cptr[col], vb);
+        for (int col = C - 2; col >= 0; --col) bytes += pass_bytes(L, col, L.n, vb);
+        ProfScope ps(c, kind, bytes);
+        k_sweep(L, *L.plan_pre, b, x, s);
+    } else {
+        {
+            ProfScope ps(c, l == 0 ? kKFirstL0 : kKGsCoarse, first_bytes(L, vb));
+            k_first(L, b, x, L.fused_restrict ? P::b(N) : (T*)nullptr, N.n, s);
+        }
+        for (int col = 2; col < C; ++col) {
+            ProfScope ps(c, kind, pass_bytes(L, col, L.cptr[col], vb));
+            k_pass(L, col, L.cptr[col], b, x, s);
+        }
+        for (int col = C - 2; col >= 0; --col) {
+            ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+            k_pass(L, col, L.n, b, x, s);
+        }
     }
     {
         ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_restrict_bytes(L, vb, scaled));
@@ -298,6 +333,15 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     {
         ProfScope ps(c, kKProlong, prolong_bytes(L, vb, scaled));
         k_prolong(L, P::x(N), x, c->p.omega, s);
+    }
+    if (L.sweep) {
+        // the whole post-smoother as one dependency-driven kernel
+        double bytes = 0.0;
+        for (int col = 0; col < C; ++col) bytes += pass_bytes(L, col, L.n, vb);
+        for (int col = C - 2; col >= 0; --col) bytes += pass_bytes(L, col, L.n, vb);
+        ProfScope ps(c, kind, bytes);
+        k_sweep(L, *L.plan_post, b, x, s);
+        return;
     }
     for (int col = 0; col < C; ++col) {
         ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
@@ -445,6 +489,9 @@ void drop_graphs(amg_ctx* c) {
             c->graph_a[a][b] = c->graph_b[a][b] = c->graph_solve[a][b] = nullptr;
             c->solve_graph_state[a][b] = 0;
         }
+        if (c->graph_bi[a]) cudaGraphExecDestroy(c->graph_bi[a]);
+        c->graph_bi[a] = nullptr;
+        c->bi_graph_state[a] = 0;
         for (cudaGraphExec_t& g : c->graph_from[a]) {
             if (g) cudaGraphExecDestroy(g);
             g = nullptr;
@@ -456,26 +503,156 @@ constexpr int kStaged = 0;   // DevLevel::lpr of the staged one-row-per-thread k
 
 // A launch shape as one code: lanes per row (0 = staged kernels, 1, 2, 4 or
 // 8) plus kHalfBlock for blocks of 128 instead of 256 threads (row kernels
-// only).
+// only), plus kSweep for smoothing sweeps run as one dependency-driven kernel
+// each (lane shapes only).
 constexpr int kHalfBlock = 16;
+constexpr int kSweep = 32;
+// sweeps are planned on the host from the level's graph (adjacency of every
+// item): kept to levels where a pass is short
+constexpr int32_t kSweepMaxRows = 1 << 20;
 inline int shape_lanes(int code) { return code & (kHalfBlock - 1); }
 inline int shape_block(int code) { return (code & kHalfBlock) ? 128 : 256; }
 
 bool shape_allowed(const DevLevel& L, int code) {
     const int lanes = shape_lanes(code);
-    if (code & ~(kHalfBlock | (kHalfBlock - 1))) return false;
+    if (code & ~(kSweep | kHalfBlock | (kHalfBlock - 1))) return false;
     if (lanes == kStaged) return code == kStaged && L.width <= kFineMaxWidth;
-    return lanes == 1 || lanes == 2 || lanes == 4 || lanes == 8;
+    if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return false;
+    if (code & kSweep)
+        return !L.fused_ok && L.ncolours >= 2 && 2 * L.ncolours - 1 <= kSweepMaxPasses &&
+               L.n <= kSweepMaxRows;
+    return true;
 }
 
-int shape_of(const DevLevel& L) { return L.lpr | (L.block == 128 ? kHalfBlock : 0); }
+int shape_of(const DevLevel& L) {
+    return L.lpr | (L.block == 128 ? kHalfBlock : 0) | (L.sweep ? kSweep : 0);
+}
 
-void set_shape(DevLevel& L, int code) {
+// The dependency plan of one sweep of level l (see SweepPlan) for items of
+// `rows` rows: pre = the pre-smoother (colour 0 from zero, colours 1..C-1
+// forward reading only earlier colours, C-2..0 backward), else the
+// post-smoother (0..C-1, C-2..0).  Uploaded into the context's memory.
+void plan_sweep(amg_ctx* c, int l, int rows, bool pre, SweepPlan& P) {
+    const HostLevel& h = c->hl[l];
+    const DevLevel& L = c->dl[l];
+    const int32_t n = L.n;
+    const int C = L.ncolours;
+    std::vector<int32_t> colr(n), tiles(C), tile0(C + 1, 0);
+    for (int col = 0; col < C; ++col) {
+        for (int32_t r = L.cptr[col]; r < L.cptr[col + 1]; ++r) colr[r] = col;
+        const int32_t base = L.cptr[col] & ~31;
+        tiles[col] = L.cptr[col + 1] > L.cptr[col] ? (L.cptr[col + 1] - base + rows - 1) / rows : 0;
+        tile0[col + 1] = tile0[col] + tiles[col];
+    }
+    auto gtile = [&](int32_t r) {
+        const int col = colr[r];
+        return tile0[col] + (r - (L.cptr[col] & ~31)) / rows;
+    };
+    // tiles holding neighbours of each tile's rows
+    std::vector<int32_t> inv(n);
+    for (int32_t i = 0; i < n; ++i) inv[h.perm[i]] = i;
+    std::vector<std::vector<int32_t>> adj(tile0[C]);
+    for (int32_t r = 0; r < n; ++r) {
+        const int32_t i = inv[r];
+        std::vector<int32_t>& a = adj[gtile(r)];
+        for (int32_t k = h.A.rp[i]; k < h.A.rp[i + 1]; ++k)
+            if (h.A.ci[k] != i) a.push_back(gtile(h.perm[h.A.ci[k]]));
+    }
+    for (auto& a : adj) {
+        std::sort(a.begin(), a.end());
+        a.erase(std::unique(a.begin(), a.end()), a.end());
+    }
+    // the passes, and the colour of each
+    std::vector<SweepPass> pass;
+    std::vector<int> pcol;
+    auto add = [&](int col, int32_t jmax, int first) {
+        if (tiles[col] == 0) return;
+        SweepPass q;
+        q.r0 = L.cptr[col];
+        q.r1 = L.cptr[col + 1];
+        q.jmax = jmax;
+        q.first = first;
+        q.tiles = tiles[col];
+        q.item0 = pass.empty() ? 0 : pass.back().item0 + pass.back().tiles;
+        pass.push_back(q);
+        pcol.push_back(col);
+    };
+    for (int col = 0; col < C; ++col) {
+        if (pre) add(col, col == 0 ? 0 : L.cptr[col], col == 0 ? 1 : 0);
+        else add(col, n, 0);
+    }
+    for (int col = C - 2; col >= 0; --col) add(col, n, 0);
+    const int np = (int)pass.size();
+    if (np > kSweepMaxPasses) throw Error{AMG_EINVAL, "too many colour passes for a sweep kernel"};
+    const int32_t items = np ? pass.back().item0 + pass.back().tiles : 0;
+    // dependencies of every item, in item order
+    std::vector<int32_t> dep_ptr(1, 0), dep;
+    for (int p = 0; p < np; ++p) {
+        const int col = pcol[p];
+        int prev = -1;
+        for (int q = p - 1; q >= 0; --q)
+            if (pcol[q] == col) {
+                prev = q;
+                break;
+            }
+        for (int32_t t = 0; t < pass[p].tiles; ++t) {
+            if (prev >= 0) dep.push_back(pass[prev].item0 + t);
+            for (int q = prev + 1; q < p; ++q) {
+                if (q < p - 1) {
+                    dep.push_back(-(q + 1));
+                    continue;
+                }
+                const int qc = pcol[q];
+                for (int32_t g : adj[tile0[col] + t])
+                    if (g >= tile0[qc] && g < tile0[qc + 1])
+                        dep.push_back(pass[q].item0 + (g - tile0[qc]));
+            }
+            dep_ptr.push_back((int32_t)dep.size());
+        }
+    }
+    cudaStream_t s = c->stream;
+    P.rows = rows;
+    P.npass = np;
+    P.items = items;
+    P.mean_deps = items ? (double)dep.size() / items : 0.0;
+    P.pass = c->mem.alloc<SweepPass>(std::max(np, 1));
+    P.dep_ptr = c->mem.alloc<int32_t>(dep_ptr.size());
+    P.dep = c->mem.alloc<int32_t>(std::max<size_t>(dep.size(), 1));
+    P.flag = c->mem.alloc<uint32_t>(std::max(items, 1));
+    P.done = c->mem.alloc<unsigned long long>(std::max(np, 1));
+    P.arrive = c->mem.alloc<unsigned long long>(1);
+    P.grid = std::min(items, sweep_grid(L.lpr, L.block));
+    P.failed = c->mem.alloc<int32_t>(1);
+    upload(P.pass, pass, s);
+    upload(P.dep_ptr, dep_ptr, s);
+    upload(P.dep, dep, s);
+    AMG_CUDA_TRY(cudaMemsetAsync(P.flag, 0, sizeof(uint32_t) * std::max(items, 1), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(P.done, 0, sizeof(unsigned long long) * std::max(np, 1), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(P.arrive, 0, sizeof(unsigned long long), s));
+    AMG_CUDA_TRY(cudaMemsetAsync(P.failed, 0, sizeof(int32_t), s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));   // the host vectors go out of scope
+}
+
+void set_shape(amg_ctx* c, int l, int code) {
+    DevLevel& L = c->dl[l];
     const int lanes = shape_lanes(code);
     L.lpr = lanes;
     L.lpr_wide = lanes;
     L.block = shape_block(code);
     L.fused_restrict = lanes == kStaged && L.fused_ok;
+    L.sweep = (code & kSweep) != 0 && lanes >= 1;
+    L.plan_pre = L.plan_post = nullptr;
+    if (L.sweep) {
+        // the plan (items, and the cooperative grid) depends on lanes and block
+        const int rows = L.block / lanes;
+        auto& pp = c->sweep_plans[std::make_pair(l, lanes + 16 * L.block)];
+        if (pp.first.rows == 0) {
+            plan_sweep(c, l, rows, true, pp.first);
+            plan_sweep(c, l, rows, false, pp.second);
+        }
+        L.plan_pre = &pp.first;
+        L.plan_post = &pp.second;
+    }
 }
 
 // Level signature for the process-wide cache of tuned shapes: levels that
@@ -559,7 +736,7 @@ double autotune_shapes(amg_ctx* c) {
             std::lock_guard<std::mutex> lk(g_shape_mu);
             auto it = g_shape_cache.find(key);
             if (it != g_shape_cache.end() && shape_allowed(L, it->second)) {
-                set_shape(L, it->second);
+                set_shape(c, l, it->second);
                 continue;
             }
         }
@@ -571,9 +748,10 @@ double autotune_shapes(amg_ctx* c) {
         double t_rule = 1e30, t_best = 1e30;
         int best = rule;
         for (int lanes : {kStaged, 1, 1 | kHalfBlock, 2, 2 | kHalfBlock, 4, 4 | kHalfBlock, 8,
-                          8 | kHalfBlock}) {
+                          8 | kHalfBlock, 2 | kSweep, 2 | kHalfBlock | kSweep, 4 | kSweep,
+                          4 | kHalfBlock | kSweep, 8 | kSweep, 8 | kHalfBlock | kSweep}) {
             if (!shape_allowed(L, lanes)) continue;
-            set_shape(L, lanes);
+            set_shape(c, l, lanes);
             const double t = time_vcycle_from(c, l);
             if (lanes == rule) t_rule = t;
             if (t < t_best) {
@@ -586,7 +764,7 @@ double autotune_shapes(amg_ctx* c) {
         // its choice first: every context then runs the stored one
         std::lock_guard<std::mutex> lk(g_shape_mu);
         const int stored = g_shape_cache.emplace(key, best).first->second;
-        set_shape(L, shape_allowed(L, stored) ? stored : best);
+        set_shape(c, l, shape_allowed(L, stored) ? stored : best);
     }
     for (int l = 0; l + 1 < nlev; ++l) c->shapes[c->precision][l] = shape_of(c->dl[l]);
     c->tuned[c->precision] = true;
@@ -597,7 +775,7 @@ double autotune_shapes(amg_ctx* c) {
 
 // Make the levels run the shapes of the context's precision.
 void apply_shapes(amg_ctx* c) {
-    for (int l = 0; l + 1 < (int)c->dl.size(); ++l) set_shape(c->dl[l], c->shapes[c->precision][l]);
+    for (int l = 0; l + 1 < (int)c->dl.size(); ++l) set_shape(c, l, c->shapes[c->precision][l]);
 }
 
 // ---------------------------------------------------------------------------
@@ -691,15 +869,14 @@ void cg_fill_info(const amg_ctx* c, int status, double rr_true, amg_solve_info* 
     info->device_loop = c->last_device_loop;
 }
 
-// The iteration loop of PCG as one graph: the first direction (z = B r,
-// rho, p = z) and the first update (q = A p, alpha, x, r, ||r||), then a
-// WHILE node whose body is one more iteration (z = B r, beta, p; q = A p,
-// alpha, x, r, ||r||).  A one-thread kernel after each update sets the loop
-// condition from the device scalars, so no iteration waits on the host; the
-// scalars come back once, after the loop.  The launches are those of the
-// host-driven loop, in the same order.  Returns nullptr (and clears the
-// error) when the runtime refuses the graph.
-cudaGraphExec_t build_solve_graph(amg_ctx* c) {
+// A Krylov iteration loop as one graph: `pre` on the context stream, then
+// `cond(h, stream)` (a one-thread kernel setting the loop condition h from the
+// device scalars), then a WHILE node whose body is `body` followed by `cond`
+// again, then `post`.  No iteration waits on the host; the scalars come back
+// once, in `post`.  Returns nullptr (and clears the error) when the runtime
+// refuses the graph.
+template <typename Pre, typename Cond, typename Body, typename Post>
+cudaGraphExec_t build_while_graph(amg_ctx* c, Pre&& pre, Cond&& cond, Body&& body, Post&& post) {
     if (!c->stream_body)
         AMG_CUDA_TRY(cudaStreamCreateWithFlags(&c->stream_body, cudaStreamNonBlocking));
     cudaStream_t s = c->stream;
@@ -722,8 +899,7 @@ cudaGraphExec_t build_solve_graph(amg_ctx* c) {
         return nullptr;
     }
     try {
-        cg_first_direction(c);
-        cg_part_a(c, false);
+        pre();
         cudaStreamCaptureStatus st;
         cudaGraph_t cg = nullptr;
         const cudaGraphNode_t* deps = nullptr;
@@ -733,7 +909,7 @@ cudaGraphExec_t build_solve_graph(amg_ctx* c) {
         cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, &edges, &nd);
         if (ok(e)) e = cudaGraphConditionalHandleCreate(&h, cg, 0, cudaGraphCondAssignDefault);
         if (!ok(e)) { fail(e); return nullptr; }
-        launch_cg_continue(h, c->work.sc, s);
+        cond(h, s);
         e = cudaStreamGetCaptureInfo(s, &st, nullptr, &cg, &deps, &edges, &nd);
         cudaGraphNodeParams prm = {};
         prm.type = cudaGraphNodeTypeConditional;
@@ -748,16 +924,14 @@ cudaGraphExec_t build_solve_graph(amg_ctx* c) {
         if (!ok(e)) { fail(e); return nullptr; }
         body_capturing = true;
         c->stream = c->stream_body;
-        cg_part_b(c);
-        cg_part_a(c, false);
-        launch_cg_continue(h, c->work.sc, c->stream);
+        body();
+        cond(h, c->stream);
         c->stream = s;
-        cudaGraph_t body = nullptr;
-        e = cudaStreamEndCapture(c->stream_body, &body);
+        cudaGraph_t bg = nullptr;
+        e = cudaStreamEndCapture(c->stream_body, &bg);
         body_capturing = false;
         if (!ok(e)) { fail(e); return nullptr; }
-        e = cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars), cudaMemcpyDeviceToHost, s);
-        if (!ok(e)) { fail(e); return nullptr; }
+        post();
     } catch (const Error&) {
         fail(cudaSuccess);   // a launch the capture refused: the host-driven loop runs
         return nullptr;
@@ -778,6 +952,29 @@ cudaGraphExec_t build_solve_graph(amg_ctx* c) {
         return nullptr;
     }
     return ex;
+}
+
+// The iteration loop of PCG as one graph: the first direction (z = B r,
+// rho, p = z) and the first update (q = A p, alpha, x, r, ||r||), then a
+// WHILE node whose body is one more iteration (z = B r, beta, p; q = A p,
+// alpha, x, r, ||r||).  The loop condition kernel runs after each update.
+// The launches are those of the host-driven loop, in the same order.
+cudaGraphExec_t build_solve_graph(amg_ctx* c) {
+    return build_while_graph(
+        c,
+        [&] {
+            cg_first_direction(c);
+            cg_part_a(c, false);
+        },
+        [&](cudaGraphConditionalHandle h, cudaStream_t st) { launch_cg_continue(h, c->work.sc, st); },
+        [&] {
+            cg_part_b(c);
+            cg_part_a(c, false);
+        },
+        [&] {
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->sc_host, c->work.sc, sizeof(PcgScalars),
+                                         cudaMemcpyDeviceToHost, c->stream));
+        });
 }
 
 // The solve graph of the context's precision and CG variant, built on first
@@ -863,9 +1060,56 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
 // ---------------------------------------------------------------------------
 // preconditioned BiCGSTAB (Sec. 5: the Krylov method of the paper's
 // experiments), two V-cycles per iteration; vectors in smoothing order
-// (c->bb = b, c->x = x0 in, x out).  The scalars are formed on the host from
-// the dot products, each read back once per half iteration.
+// (c->bb = b, c->x = x0 in, x out).  The scalars live on the device (the
+// reductions form alpha, w, rho and the convergence tests), so one iteration
+// is a fixed sequence of launches: by default the whole loop runs as one graph
+// with a device-side WHILE node; the host-driven loop (profiling, or a
+// refused graph) reads the scalars back once per iteration.
 // ---------------------------------------------------------------------------
+void bi_iteration(amg_ctx* c) {
+    DevLevel& L0 = c->dl[0];
+    const int n = L0.n;
+    cudaStream_t s = c->stream;
+    double* x = c->x;
+    double* r = c->r;
+    double* p = c->pv;
+    double* z = c->z;
+    launch_bi_direction(n, r, c->bv, p, c->bsc, s);
+    precondition(c, p, c->by);
+    launch_bi_spmv(L0, c->by, c->bv, c->rt, false, c->work, c->bsc, c->stream);
+    launch_bi_half(n, r, c->bv, c->bs, c->work, c->bsc, c->stream);
+    // after a converged half step this V-cycle's result is not used
+    precondition(c, c->bs, z);
+    launch_bi_spmv(L0, z, c->bt, c->bs, true, c->work, c->bsc, c->stream);
+    launch_bi_update(n, x, c->by, z, c->bs, c->bt, r, c->rt, c->work, c->bsc, c->stream);
+}
+
+cudaGraphExec_t bicgstab_graph(amg_ctx* c) {
+    if (!c->p.device_loop || !cg_graphs(c) || c->prof.graphs) return nullptr;
+    int& state = c->bi_graph_state[c->precision];
+    cudaGraphExec_t& ex = c->graph_bi[c->precision];
+    if (state == 0) {
+        auto build = [&] {
+            return build_while_graph(
+                c, [] {},
+                [&](cudaGraphConditionalHandle h, cudaStream_t st) { launch_bi_continue(h, c->bsc, st); },
+                [&] { bi_iteration(c); },
+                [&] {
+                    AMG_CUDA_TRY(cudaMemcpyAsync(c->bsc_host, c->bsc, sizeof(BiScalars),
+                                                 cudaMemcpyDeviceToHost, c->stream));
+                });
+        };
+        ex = build();
+        if (!ex && t_launch_overlap) {
+            t_launch_overlap = false;
+            ex = build();
+            t_launch_overlap = true;
+        }
+        state = ex ? 1 : -1;
+    }
+    return ex;
+}
+
 int bicgstab(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info, std::string& why) {
     DevLevel& L0 = c->dl[0];
     const int n = L0.n;
@@ -876,70 +1120,52 @@ int bicgstab(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info, std::s
         c->by = c->mem.alloc<double>(n);
         c->bs = c->mem.alloc<double>(n);
         c->bt = c->mem.alloc<double>(n);
-        c->dots = c->mem.alloc<double>(2);
-        c->dots_host = static_cast<double*>(pinned_alloc(2 * sizeof(double)));
+        c->bsc = c->mem.alloc<BiScalars>(1);
+        c->bsc_host = static_cast<BiScalars*>(pinned_alloc(sizeof(BiScalars)));
     }
-    auto read_dots = [&] {
-        AMG_CUDA_TRY(cudaMemcpyAsync(c->dots_host, c->dots, 2 * sizeof(double),
-                                     cudaMemcpyDeviceToHost, s));
-        AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    };
-    double* x = c->x;
-    double* r = c->r;
-    double* p = c->pv;
-    double* z = c->z;
-    // r = b - A x, rt = r
-    launch_cg_residual(L0, c->bb, x, r, c->work, kStore, c->dots, s);
-    AMG_CUDA_TRY(cudaMemcpyAsync(c->rt, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    read_dots();
-    const double r0 = std::sqrt(c->dots_host[0]);
-    double rel = r0 > 0.0 ? 1.0 : 0.0;
-    double rho = c->dots_host[0], rho_prev = 1.0, alpha = 1.0, w = 1.0;
-    int it = 0, status = AMG_OK;
-    while (rel > tol) {
-        if (it >= maxit) { status = AMG_ENOTCONV; break; }
-        if (rho == 0.0) { status = AMG_ENOTCONV; why = "BiCGSTAB breakdown: rt.r = 0"; break; }
-        if (it == 0)
-            AMG_CUDA_TRY(cudaMemcpyAsync(p, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-        else
-            launch_bi_direction(n, r, (rho / rho_prev) * (alpha / w), w, c->bv, p, s);
-        precondition(c, p, c->by);
-        launch_bi_spmv(L0, c->by, c->bv, c->rt, false, c->work, c->dots, s);
-        read_dots();
-        const double rtv = c->dots_host[0];
-        if (rtv == 0.0) { status = AMG_ENOTCONV; why = "BiCGSTAB breakdown: rt.v = 0"; break; }
-        alpha = rho / rtv;
-        launch_bi_axpy(n, r, -alpha, c->bv, c->bs, c->work, c->dots, s);
-        read_dots();
-        ++it;
-        const double srel = std::sqrt(c->dots_host[0]) / r0;
-        if (srel <= tol) {
-            launch_bi_axpy(n, x, alpha, c->by, x, c->work, c->dots, s);
-            rel = srel;
-            break;
+    BiScalars& h = *c->bsc_host;
+    std::memset(&h, 0, sizeof(BiScalars));
+    h.tol = tol;
+    h.maxit = maxit;
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->bsc, c->bsc_host, sizeof(BiScalars), cudaMemcpyHostToDevice, s));
+    // r = b - A x, rt = r, rho = r.r, and the start of the loop
+    launch_bi_start(L0, c->bb, c->x, c->r, c->rt, c->work, c->bsc, s);
+    AMG_CUDA_TRY(cudaMemcpyAsync(c->bsc_host, c->bsc, sizeof(BiScalars), cudaMemcpyDeviceToHost, s));
+    AMG_CUDA_TRY(cudaStreamSynchronize(s));
+    c->last_device_loop = 0;
+    if (!h.done) {
+        if (cudaGraphExec_t loop = bicgstab_graph(c)) {
+            AMG_CUDA_TRY(cudaGraphLaunch(loop, s));
+            AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            c->last_device_loop = 1;
+            if (!h.done && !h.status)
+                throw Error{AMG_ECUDA, "device-side BiCGSTAB loop stopped before its condition"};
+        } else {
+            while (bi_continue(h)) {
+                bi_iteration(c);
+                AMG_CUDA_TRY(cudaMemcpyAsync(c->bsc_host, c->bsc, sizeof(BiScalars),
+                                             cudaMemcpyDeviceToHost, s));
+                AMG_CUDA_TRY(cudaStreamSynchronize(s));
+            }
         }
-        precondition(c, c->bs, z);
-        launch_bi_spmv(L0, z, c->bt, c->bs, true, c->work, c->dots, s);
-        read_dots();
-        const double ts = c->dots_host[0], tt = c->dots_host[1];
-        if (tt == 0.0) { status = AMG_ENOTCONV; why = "BiCGSTAB breakdown: t.t = 0"; break; }
-        w = ts / tt;
-        launch_bi_update(n, x, c->by, z, alpha, w, c->bs, c->bt, r, c->rt, c->work, c->dots, s);
-        read_dots();
-        rel = std::sqrt(c->dots_host[0]) / r0;
-        rho_prev = rho;
-        rho = c->dots_host[1];
     }
     AMG_CUDA_TRY(cudaGetLastError());
+    const int status = h.status ? h.status : AMG_OK;
+    if (status != AMG_OK) {
+        static const char* kWhy[] = {"maximum iterations reached", "BiCGSTAB breakdown: rt.r = 0",
+                                     "BiCGSTAB breakdown: rt.v = 0", "BiCGSTAB breakdown: t.t = 0"};
+        why = kWhy[std::min(std::max(h.why, 0), 3)];
+    }
     if (info) {
         cg_true_residual(c);
         double rr = 0.0;
         AMG_CUDA_TRY(cudaMemcpyAsync(&rr, c->norm_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
         AMG_CUDA_TRY(cudaStreamSynchronize(s));
         info->status = status;
-        info->iterations = it;
-        info->rel_residual = rel;
-        info->true_rel_residual = r0 > 0.0 ? std::sqrt(rr) / r0 : 0.0;
+        info->iterations = h.iters;
+        info->rel_residual = h.rel;
+        info->true_rel_residual = h.r0 > 0.0 ? std::sqrt(rr) / h.r0 : 0.0;
+        info->device_loop = c->last_device_loop;
     }
     return status;
 }
@@ -1389,6 +1615,7 @@ int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
         for (int l = 0; l + 1 < (int)c->dl.size(); ++l) {
             c->linfo[l].lanes_per_row = c->dl[l].lpr;
             c->linfo[l].threads_per_block = c->dl[l].block;
+            c->linfo[l].sweep = c->dl[l].sweep ? 1 : 0;
         }
         leave(c);
     });
@@ -1553,17 +1780,22 @@ int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row, int32_t th
             throw Error{AMG_EINVAL, "level out of range (the coarsest level has no shape)"};
         if (threads_per_block != 0 && threads_per_block != 256 && threads_per_block != 128)
             throw Error{AMG_EINVAL, "threads_per_block must be 0, 256 or 128"};
-        const int code = lanes_per_row | (threads_per_block == 128 ? kHalfBlock : 0);
-        if (lanes_per_row < 0 || lanes_per_row > 8 || !shape_allowed(c->dl[l], code))
-            throw Error{AMG_EINVAL, "lanes_per_row must be 1, 2, 4 or 8, or 0 (256 threads) on a "
-                                    "level whose rows have at most 32 off-diagonals"};
+        const bool sweep = (lanes_per_row & AMG_SHAPE_SWEEP) != 0;
+        const int lanes = lanes_per_row & ~AMG_SHAPE_SWEEP;
+        const int code = lanes | (threads_per_block == 128 ? kHalfBlock : 0) | (sweep ? kSweep : 0);
+        if (lanes < 0 || lanes > 8 || !shape_allowed(c->dl[l], code))
+            throw Error{AMG_EINVAL, "lanes_per_row must be 1, 2, 4 or 8 (optionally with "
+                                    "AMG_SHAPE_SWEEP on a level of at most 2^20 rows that is not "
+                                    "two-colour fused), or 0 (256 threads) on a level whose rows "
+                                    "have at most 32 off-diagonals"};
         enter(c);
         AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
         drop_graphs(c);
-        set_shape(c->dl[l], code);
+        set_shape(c, l, code);
         c->shapes[c->precision][l] = code;
         c->linfo[l].lanes_per_row = c->dl[l].lpr;
         c->linfo[l].threads_per_block = c->dl[l].block;
+        c->linfo[l].sweep = c->dl[l].sweep ? 1 : 0;
         leave(c);
     });
 }

@@ -87,3 +87,51 @@ def test_zero_guess_host_solve_matches_zeroed_x0(problem):
         assert np.array_equal(x1.view(np.uint64), x2.view(np.uint64))
     finally:
         solver.close()
+
+
+def _solve_bi(p, device_loop, precision, tol, maxit):
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, device_loop=device_loop, precision=precision)
+    try:
+        b = torch.from_numpy(p.b).cuda()
+        out = []
+        for _ in range(2):   # the second solve replays the cached graph
+            x, rc, info = solver.solve_bicgstab(b, tol=tol, maxit=maxit)
+            torch.cuda.synchronize()
+            out.append((x.cpu().numpy(), rc, info))
+        return out
+    finally:
+        solver.close()
+
+
+@pytest.mark.parametrize("precision", [amg.AMG_FP64, amg.AMG_FP32_IN_FP64])
+@pytest.mark.parametrize("tol,maxit,rc_want", [(1e-9, 300, amg.AMG_OK), (1e-30, 4, amg.AMG_ENOTCONV)])
+def test_bicgstab_device_loop_matches_host_loop(problem, precision, tol, maxit, rc_want):
+    # BiCGSTAB keeps its scalars on the device: the graph loop and the
+    # host-driven loop launch the same kernels and stop at the same point
+    dev = _solve_bi(problem, 1, precision, tol, maxit)
+    host = _solve_bi(problem, 0, precision, tol, maxit)
+    for (xd, rcd, infod), (xh, rch, infoh) in zip(dev, host):
+        assert rcd == rch == rc_want
+        assert infod["device_loop"] == 1 and infoh["device_loop"] == 0
+        assert infod["iterations"] == infoh["iterations"]
+        if rc_want == amg.AMG_ENOTCONV:
+            assert infod["iterations"] == maxit
+        assert infod["rel_residual"] == infoh["rel_residual"]
+        assert np.array_equal(xd.view(np.uint64), xh.view(np.uint64))
+    assert np.array_equal(dev[0][0].view(np.uint64), dev[1][0].view(np.uint64))
+
+
+def test_bicgstab_zero_rhs_and_half_step_exit(problem):
+    solver = amg.AMG(problem.row_ptr, problem.col, problem.val, dim=3)
+    try:
+        b = torch.from_numpy(problem.b).cuda()
+        x, rc, info = solver.solve_bicgstab(torch.zeros_like(b), tol=1e-8)
+        assert rc == amg.AMG_OK and info["iterations"] == 0
+        assert torch.count_nonzero(x).item() == 0
+        # a loose tolerance that the first half step already meets: one
+        # iteration, x = alpha y, and the reported residual is the half step's
+        x, rc, info = solver.solve_bicgstab(b, tol=0.9)
+        assert rc == amg.AMG_OK and info["iterations"] == 1
+        assert info["true_rel_residual"] <= 0.9
+    finally:
+        solver.close()

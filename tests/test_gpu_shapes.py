@@ -31,6 +31,9 @@ CASES = {
 }
 
 
+SWEEP = amg.AMG_SHAPE_SWEEP
+
+
 def _vcycle_err(solver, H, r):
     z = solver.vcycle(torch.from_numpy(np.ascontiguousarray(r)).cuda())
     torch.cuda.synchronize()
@@ -51,14 +54,15 @@ def test_every_shape_matches_oracle(case):
         for l in range(len(levels) - 1):
             rule = levels[l]["lanes_per_row"]
             for lanes, threads in ((0, 0), (1, 0), (2, 0), (4, 0), (8, 0), (1, 128), (4, 128),
-                                   (8, 128)):
+                                   (8, 128), (2 | SWEEP, 0), (8 | SWEEP, 128)):
                 try:
                     solver.set_level_shape(l, lanes, threads)
                 except amg.AmgError as e:
-                    assert lanes == 0 and e.code == amg.AMG_EINVAL
+                    assert (lanes == 0 or lanes & SWEEP) and e.code == amg.AMG_EINVAL
                     continue
                 info_l = solver.info()[1][l]
-                assert info_l["lanes_per_row"] == lanes
+                assert info_l["lanes_per_row"] == lanes & ~SWEEP
+                assert info_l["sweep"] == (1 if lanes & SWEEP else 0)
                 assert info_l["threads_per_block"] == (threads or 256)
                 assert _vcycle_err(solver, H, r) <= 1e-12, (l, lanes, threads)
                 tried += 1
@@ -87,7 +91,8 @@ def test_shape_errors():
     try:
         nlev = solver.info()[0]["num_levels"]
         for l, lanes, threads in ((-1, 4, 0), (nlev - 1, 4, 0), (0, 3, 0), (0, 16, 0), (0, 17, 0),
-                                  (0, 4, 64), (0, 0, 128)):
+                                  (0, 4, 64), (0, 0, 128), (0, SWEEP, 0), (0, 3 | SWEEP, 0),
+                                  (0, 0x200 | 4, 0)):
             with pytest.raises(amg.AmgError) as e:
                 solver.set_level_shape(l, lanes, threads)
             assert e.value.code == amg.AMG_EINVAL
@@ -104,6 +109,7 @@ def test_autotuned_shapes_keep_parity_and_are_cached(precision):
         sa, la = a.info()
         shapes = [l["lanes_per_row"] for l in la[:-1]]
         assert all(s in (0, 1, 2, 4, 8) for s in shapes)
+        shapes = [(l["lanes_per_row"], l["threads_per_block"], l["sweep"]) for l in la[:-1]]
         H = O.Hierarchy(p.row_ptr, p.col, p.val, _oracle_params(a.params))
         xo, it_o, _, _ = H.pcg(p.b, tol=1e-10, maxit=300)
         if precision == amg.AMG_FP64:
@@ -121,9 +127,91 @@ def test_autotuned_shapes_keep_parity_and_are_cached(precision):
                     coarsen_target=300)
         try:
             sb, lb = b.info()
-            assert [l["lanes_per_row"] for l in lb[:-1]] == shapes
+            assert [(l["lanes_per_row"], l["threads_per_block"], l["sweep"]) for l in lb[:-1]] == shapes
             assert sb["autotune_ms"] == 0.0
         finally:
             b.close()
     finally:
         a.close()
+
+
+# ---------------------------------------------------------------------------
+# smoothing sweeps as one dependency-driven kernel each
+# ---------------------------------------------------------------------------
+
+SWEEP_CASES = {
+    "lognormal_deep": (lambda: P.lognormal3d((40, 36, 32), seed=4), {"coarsen_target": 60}),
+    "layered": (lambda: P.layered3d((24, 24, 28), seed=3), {"coarsen_target": 100}),
+    "hub_graph2d_48": (lambda: P.hub_graph2d(48), {"coarsen_target": 100}),
+}
+
+
+@pytest.mark.parametrize("case", list(SWEEP_CASES))
+def test_sweep_kernel_gives_the_pass_kernels_values(case):
+    # the sweep updates every row exactly as the one-launch-per-pass kernels
+    # of the same lanes and block size do: identical V-cycles, on repeated
+    # launches (the epochs of the never-reset flags advance), within the
+    # oracle bar, and through whole solves in both precisions
+    maker, over = SWEEP_CASES[case]
+    p = maker()
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=p.dim, **over)
+    try:
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _oracle_params(solver.params))
+        _, levels = solver.info()
+        rng = np.random.default_rng(5)
+        r = torch.from_numpy(rng.standard_normal(p.n)).cuda()
+        swept = 0
+        for l in range(1, len(levels) - 1):
+            for lanes, threads in ((2, 0), (4, 128), (8, 0), (1, 128)):
+                solver.set_level_shape(l, lanes, threads)
+                z_pass = solver.vcycle(r).cpu().numpy()
+                try:
+                    solver.set_level_shape(l, lanes | SWEEP, threads)
+                except amg.AmgError as e:
+                    assert e.code == amg.AMG_EINVAL
+                    continue
+                for _ in range(3):
+                    z_sweep = solver.vcycle(r).cpu().numpy()
+                    assert np.array_equal(z_sweep, z_pass), (l, lanes, threads)
+                swept += 1
+            # leave the sweep on for this level
+            solver.set_level_shape(l, 4 | SWEEP)
+        assert swept >= 1
+        z = solver.vcycle(r).cpu().numpy()
+        z_or = H.vcycle(r.cpu().numpy())
+        assert np.abs(z - z_or).max() <= 1e-12 * np.abs(z_or).max()
+        b = torch.from_numpy(p.b).cuda()
+        x, rc, info = solver.solve(b, tol=1e-10, maxit=300)
+        assert rc == amg.AMG_OK
+        xo, it_o, _, _ = H.pcg(p.b, tol=1e-10, maxit=300)
+        assert abs(info["iterations"] - it_o) <= 1
+        xo = oracle_iterate(H, p.b, info["iterations"], it_o, xo)
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+        solver.set_precision(amg.AMG_FP32_IN_FP64)
+        for l in range(1, len(levels) - 1):
+            solver.set_level_shape(l, 4 | SWEEP)
+        x, rc, info = solver.solve(b, tol=1e-8, maxit=300)
+        assert rc == amg.AMG_OK and info["true_rel_residual"] <= 1.05e-8
+    finally:
+        solver.close()
+
+
+def test_sweep_graph_loop_matches_host_loop():
+    # the same sweeps launched from the device-side loop graph and from the
+    # host-driven loop give identical iterates
+    p = P.lognormal3d((36, 30, 28), seed=9)
+    out = []
+    for device_loop in (1, 0):
+        solver = amg.AMG(p.row_ptr, p.col, p.val, dim=3, coarsen_target=80,
+                         device_loop=device_loop)
+        try:
+            nlev = solver.info()[0]["num_levels"]
+            for l in range(1, nlev - 1):
+                solver.set_level_shape(l, 2 | SWEEP, 128)
+            x, rc, info = solver.solve(torch.from_numpy(p.b).cuda(), tol=1e-10, maxit=300)
+            assert rc == amg.AMG_OK and info["device_loop"] == device_loop
+            out.append((x.cpu().numpy(), info["iterations"]))
+        finally:
+            solver.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0].view(np.uint64), out[1][0].view(np.uint64))
