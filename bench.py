@@ -140,12 +140,18 @@ def parse_args():
     ap.add_argument("--lanes-per-row", type=str, default="", metavar="L0,L1,...",
                     help="fixed launch shapes per level instead of tuning (0 = staged "
                          "kernels, else 1/2/4/8 lanes per row, with a suffix h for blocks of "
-                         "128 threads, e.g. 0,2h,4h), for reproducible profiles")
+                         "128 threads and s for one dependency-driven kernel per smoothing "
+                         "sweep, e.g. 0,2h,4hs), for reproducible profiles")
     ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
                     help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
     args = ap.parse_args()
-    args.lanes = [(int(v.strip().rstrip("h")), 128 if v.strip().endswith("h") else 0)
-                  for v in args.lanes_per_row.split(",") if v.strip()]
+    args.lanes = []
+    for v in (v.strip() for v in args.lanes_per_row.split(",")):
+        if v:
+            lanes = int(v.rstrip("hs"))
+            if "s" in v:
+                lanes |= 0x100   # AMG_SHAPE_SWEEP: one dependency-driven kernel per sweep
+            args.lanes.append((lanes, 128 if "h" in v else 0))
     if args.lanes:
         args.autotune = 0
     if args.aggregation_tile < 0:
@@ -347,8 +353,10 @@ def run_reference(args, dist: Dist):
     value = smp["solve_s"] * 1e3
     sample = (f"oracle PCG solve (single thread) on the {args.cpu_grid}^3 instance of the workload "
               f"({smp['n']} unknowns, {smp['levels']} levels, {smp['iterations']} iterations), "
-              f"hierarchy built once ({smp['setup_s']:.1f} s, not timed); unscaled: the oracle's "
-              f"setup of the {args.grid}^3 system alone would take hours")
+              f"hierarchy built once ({smp['setup_s']:.1f} s, not timed); unscaled: at "
+              f"{smp['setup_s'] / smp['n'] * 1e6:.0f} us of setup a row, the oracle's setup of the "
+              f"{args.grid}^3 system alone would take about "
+              f"{smp['setup_s'] / smp['n'] * args.grid ** 3 / 60:.0f} min")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": smp["solves"], "warmup": args.warmup, "ms_per_step": value,
@@ -583,7 +591,9 @@ def run_ours(args, dist: Dist):
         cpu = {"value": smp["solve_s"] * 1e3, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"oracle PCG solve on the {args.cpu_grid}^3 instance of the workload "
                          f"({smp['n']} unknowns, {smp['iterations']} iterations, {smp['solves']} "
-                         f"solves), unscaled; its setup of the {args.grid}^3 system would take hours",
+                         f"solves), unscaled; at its setup rate the {args.grid}^3 system would "
+                         f"need about {smp['setup_s'] / smp['n'] * args.grid ** 3 / 60:.0f} min of "
+                         f"oracle setup",
                "setup_s": smp["setup_s"], "cpu": cpu_model(), "host_cpu_count": os.cpu_count(),
                "gpu_fp64_ms_same_sample": gpu_ms, "gpu_iterations_same_sample": gpu_it}
         from oracle import oracle as O
