@@ -120,6 +120,12 @@ def parse_args():
     ap.add_argument("--host-threads", type=int, default=0,
                     help="host threads per setup for tiled aggregation (0: all host cores)")
     ap.add_argument("--slots", type=int, default=32)
+    ap.add_argument("--batch-vcycles", type=int, choices=[0, 1], default=1,
+                    help="serving: 1 runs the V-cycles of the requests that need one in a "
+                         "scheduler tick as shared launches, level by level; 0: each request "
+                         "launches its own")
+    ap.add_argument("--serving-requests", type=int, default=200, metavar="N",
+                    help="the bounded serving leg of the main line (0: none)")
     ap.add_argument("--setup-threads", type=int, default=0,
                     help="server setup threads (0: host cores - 3)")
     ap.add_argument("--aggregation-tile", type=int, default=-1, metavar="T",
@@ -603,6 +609,19 @@ def run_ours(args, dist: Dist):
                    "kind": "oracle (OpenMP build of the same source)",
                    "setup_s": so["setup_s"], "iterations": so["iterations"]}
 
+    # ---- a bounded serving leg (rank 0, N = 1) ------------------------------------
+    serving = None
+    if dist.world == 1 and args.serving_requests > 0:
+        leg = serving_leg(args, args.serving_requests, agg_tile=4096)
+        serving = {k: leg[k] for k in ("requests", "ok", "p50_ms", "p99_ms", "solves_per_s",
+                                       "saturated_solves_per_s", "requests_per_batched_vcycle")}
+        serving["median_setup_ms"] = leg["median_ms"]["setup_ms"]
+        serving["median_solve_ms"] = leg["median_ms"]["solve_ms"]
+        serving["workload"] = ("independent 3D 7-point solves, box sides U{16..96}, log-normal K "
+                               "variance U[1,6]; FP32-in-FP64 to %g, Poisson arrivals at %.1f x "
+                               "the saturated rate, host-tiled aggregation (4096 rows)"
+                               % (args.tol, args.load))
+
     kpath = None
     if args.kernels_out and dist.rank == 0:
         try:
@@ -630,6 +649,7 @@ def run_ours(args, dist: Dist):
         "kernels_file": kpath,
         "setup": rec["setup"],
         "other_workloads": others,
+        "serving": serving,
         "roofline": rec["roofline"],
         "device_loop": rec["device_loop"],
         "iterations": rec["fp64"]["iterations"],
@@ -667,25 +687,24 @@ def _gen_request(k: int):
     return k, p.row_ptr, p.col, p.val, p.b
 
 
-def run_serving(args):
-    """Continuous-batching serving on one GPU: FP32-in-FP64 AMG-PCG to --tol
-    for independent requests.  Phase 1 submits a burst to measure the
-    saturated rate; phase 2 replays all N requests with Poisson arrivals at
-    --load times that rate and reports latency percentiles."""
+def serving_leg(args, n_req, agg_tile=None):
+    """Continuous-batching serving on the current GPU: FP32-in-FP64 AMG-PCG to
+    --tol for n_req independent requests.  Phase 1 submits a burst to measure
+    the saturated rate; phase 2 replays all requests with Poisson arrivals at
+    --load times that rate and records latency percentiles.  The requests are
+    generated in spawned processes."""
     import multiprocessing as mp
     import numpy as np
-    n_req = args.serving
-    # inputs are generated before the first GPU call, in spawned processes
-    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
-        reqs = sorted(pool.map(_gen_request, range(n_req), chunksize=8), key=lambda t: t[0])
     import torch
     from paper_1209_0960_gb300 import amg
-    torch.cuda.set_device(0)
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2) - 1))) as pool:
+        reqs = sorted(pool.map(_gen_request, range(n_req), chunksize=8), key=lambda t: t[0])
     threads = args.setup_threads or max(1, (os.cpu_count() or 4) - 3)
+    tile = args.aggregation_tile if agg_tile is None else agg_tile
     srv = amg.Server(dim=3, max_slots=args.slots, setup_threads=threads,
-                     aggregation_tile=args.aggregation_tile,
-                     aggregation_device=args.aggregation_device, autotune=args.autotune,
-                     host_threads=args.host_threads,
+                     aggregation_tile=tile, aggregation_device=args.aggregation_device,
+                     autotune=args.autotune, host_threads=args.host_threads,
+                     batch_vcycles=args.batch_vcycles,
                      **({"device_loop": args.device_loop} if args.device_loop is not None else {}))
 
     def drain(tickets, results):
@@ -731,29 +750,42 @@ def run_serving(args):
     stats = srv.stats()
     srv.close()
     lat = np.array([r[3]["total_ms"] for r in res2.values()])
-    ok = sum(1 for r in res2.values() if r[0] == amg.AMG_OK)
-    worst_res = max(r[2]["true_rel_residual"] for r in res2.values())
     sizes = [reqs[k][1].shape[0] - 1 for k in range(n_req)]
-    line = {
-        "metric": "serving: p50/p99 request latency (submit to solution on the host) and solves/s",
-        "value": float(np.percentile(lat, 50)), "unit": "ms", "higher_is_better": False,
-        "p99_ms": float(np.percentile(lat, 99)), "solves_per_s": n_req / wall,
-        "saturated_solves_per_s": sat_rate, "offered_rate_per_s": rate,
-        "requests": n_req, "ok": ok, "worst_true_rel_residual": worst_res,
+    return {
+        "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+        "solves_per_s": n_req / wall, "saturated_solves_per_s": sat_rate, "offered_rate_per_s": rate,
+        "requests": n_req, "ok": sum(1 for r in res2.values() if r[0] == amg.AMG_OK),
+        "worst_true_rel_residual": max(r[2]["true_rel_residual"] for r in res2.values()),
         "median_ms": {k: float(np.median([r[3][k] for r in res2.values()]))
                       for k in ("queue_ms", "setup_ms", "solve_ms")},
         "peak_in_flight": stats["peak_running"], "slots": args.slots, "setup_threads": threads,
-        "aggregation_tile": args.aggregation_tile, "aggregation_device": args.aggregation_device,
-        "autotune": args.autotune, "host_threads": args.host_threads,
+        "aggregation_tile": tile, "batch_vcycles": args.batch_vcycles,
+        "batched_vcycles": stats["batched_vcycles"],
+        "requests_per_batched_vcycle": (stats["batched_requests"] / stats["batched_vcycles"]
+                                        if stats["batched_vcycles"] else 0.0),
         "device_loop": srv.params.params.device_loop,
         "unknowns": {"min": int(min(sizes)), "median": int(np.median(sizes)), "max": int(max(sizes))},
+    }
+
+
+def run_serving(args):
+    """The serving workload alone, with its own JSON line."""
+    import torch
+    torch.cuda.set_device(0)
+    leg = serving_leg(args, args.serving)
+    line = {
+        "metric": "serving: p50/p99 request latency (submit to solution on the host) and solves/s",
+        "value": leg["p50_ms"], "unit": "ms", "higher_is_better": False,
+        **{k: v for k, v in leg.items() if k != "p50_ms"},
+        "autotune": args.autotune, "host_threads": args.host_threads,
+        "aggregation_device": args.aggregation_device,
         "dtype": "f32 V-cycle in f64 CG", "data": "synthetic",
         "config": {"workload": "serving stream: independent 3D 7-point FV solves, box sides "
                                "U{16..96}, log-normal K variance U[1,6], correlation length 0.1, "
                                "Poisson arrivals; FP32-in-FP64 AMG-PCG to %g" % args.tol,
                    "load": args.load},
     }
-    print(json.dumps(line), flush=True)
+    print(json.dumps(r4(line)), flush=True)
 
 
 def main():

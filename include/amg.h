@@ -63,6 +63,9 @@ extern "C" {
                                 are behind) and the system set up again */
 #define AMG_ECUDA (-6)       /* a CUDA runtime call failed */
 #define AMG_ENOTFOUND (-7)   /* unknown ticket */
+#define AMG_ERANGE (-8)      /* checked build: a kernel met an index outside its range (the
+                                access was skipped); the hierarchy is corrupt */
+#define AMG_ENONFINITE (-9)  /* a NaN or infinity in a dot product of the Krylov iteration */
 
 #define AMG_FP64 0           /* every step in float64 */
 #define AMG_FP32_IN_FP64 1   /* float32 V-cycle inside float64 CG */
@@ -412,6 +415,13 @@ typedef struct {
     int32_t maxit;            /* CG iteration cap per request; default 500 */
     double hbm_budget_bytes;  /* device memory the admitted requests may reserve;
                                  <= 0: 80 % of the free device memory at creation */
+    int32_t batch_vcycles;    /* 1 (default; with params.device_loop = 0): every scheduler
+                                 tick runs the V-cycles of all requests whose next CG step
+                                 needs one as shared launches, level by level (one launch
+                                 per colour pass, residual, restriction, prolongation and
+                                 coarsest solve over all of them); each request's rows are
+                                 computed exactly as in its own V-cycle.  0: every request
+                                 issues its own launches on its own stream. */
 } amg_server_params;
 
 /* Timings of one request (host steady clock, milliseconds). */
@@ -428,6 +438,8 @@ typedef struct {
     int64_t submitted, completed, failed;
     int32_t queued, running, peak_running;
     double hbm_reserved_bytes, hbm_budget_bytes;
+    int64_t batched_vcycles;      /* batched V-cycle launch sequences issued */
+    int64_t batched_requests;     /* request V-cycles they covered */
 } amg_server_stats;
 
 /* Defaults: params = amg_params_default(dim) with precision
@@ -463,6 +475,29 @@ int amg_server_stats_read(amg_server *s, amg_server_stats *out);
 /* Stop the threads (running solves finish first; queued requests are
  * dropped), release every resource.  NULL is allowed. */
 int amg_server_destroy(amg_server *s);
+
+/* ---------------------------------------------------------------------------
+ * The checked build.  libamg_checked.so is the same library compiled with
+ * AMG_DEVICE_CHECKS: every kernel of the solve tests each index it gathers
+ * with (neighbour columns, restriction-list rows, aggregate indices) against
+ * its range before use and records AMG_ERANGE in the solve's status word
+ * instead of reading out of range; a solve then returns AMG_ERANGE.  It
+ * stands in for a memory sanitizer on a GPU where none can run.  Both builds
+ * stop a Krylov solve with AMG_ENONFINITE when a dot product is not finite.
+ * ------------------------------------------------------------------------- */
+
+/* 1 in the checked build, 0 in the regular one. */
+int amg_device_checks(void);
+
+/* Checked build only (AMG_EINVAL in the regular one): overwrite the column
+ * index of the k-th stored off-diagonal entry of row `row` (level-l
+ * numbering; l >= 1) with `col` on the device, to test that the checks catch
+ * a corrupt hierarchy.  A column >= the level's rows is never dereferenced by
+ * any kernel of either build (neighbours at positions beyond the pass bound
+ * are skipped), so this cannot make a kernel read out of range.  The context
+ * is corrupt afterwards: free it.  Errors: AMG_EINVAL (build, l, row, k, or
+ * col < the level's rows). */
+int amg_debug_set_column(amg_ctx *c, int32_t l, int32_t row, int32_t k, int32_t col);
 
 /* Thread-local description of the last error on this thread ("" if none). */
 const char *amg_last_error(void);

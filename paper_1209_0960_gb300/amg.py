@@ -26,6 +26,11 @@ AMG_ENOTCONV = -4
 AMG_ETIMEOUT = -5
 AMG_ECUDA = -6
 AMG_ENOTFOUND = -7
+AMG_ERANGE = -8
+AMG_ENONFINITE = -9
+
+# statuses a solve returns together with its info record (not raised)
+_SOLVE_STATUSES = (AMG_ENOTCONV, AMG_ENOTSPD, AMG_ENONFINITE, AMG_ERANGE, AMG_ETIMEOUT)
 
 AMG_FP64 = 0
 AMG_FP32_IN_FP64 = 1
@@ -81,7 +86,7 @@ class amg_kernel_stat(ctypes.Structure):
 
 class amg_server_params(ctypes.Structure):
     _fields_ = [("params", amg_params), ("max_slots", _c_i32), ("setup_threads", _c_i32),
-                ("maxit", _c_i32), ("hbm_budget_bytes", _c_dbl)]
+                ("maxit", _c_i32), ("hbm_budget_bytes", _c_dbl), ("batch_vcycles", _c_i32)]
 
 
 class amg_request_times(ctypes.Structure):
@@ -93,7 +98,8 @@ class amg_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("queued", _c_i32), ("running", _c_i32),
                 ("peak_running", _c_i32), ("hbm_reserved_bytes", _c_dbl),
-                ("hbm_budget_bytes", _c_dbl)]
+                ("hbm_budget_bytes", _c_dbl), ("batched_vcycles", ctypes.c_int64),
+                ("batched_requests", ctypes.c_int64)]
 
 
 def struct_dict(s) -> dict:
@@ -137,23 +143,27 @@ _SIGNATURES = {
     "amg_server_stats_read": ([_c_vp, ctypes.POINTER(amg_server_stats)], ctypes.c_int),
     "amg_server_destroy": ([_c_vp], ctypes.c_int),
     "amg_last_error": ([], ctypes.c_char_p),
+    "amg_device_checks": ([], ctypes.c_int),
+    "amg_debug_set_column": ([_c_vp, _c_i32, _c_i32, _c_i32, _c_i32], ctypes.c_int),
 }
 
 _lib = None
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """libamg.so, or libamg_checked.so (the build whose kernels test every
+    index they gather) when the environment sets AMG_LIB=checked."""
+    return _build.LIB_CHECKED if os.environ.get("AMG_LIB", "") == "checked" else _build.LIB
 
 
 def lib(build_if_missing: bool = False):
-    """The loaded libamg.so.  Raises if it has not been built."""
+    """The loaded library (see lib_path).  Raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    path = _build.LIB
+    path = lib_path()
     if build_if_missing:
-        _build.build()
+        _build.build(checked=path == _build.LIB_CHECKED)
     if not os.path.exists(path):
         raise RuntimeError(f"libamg.so is not built ({path}); run __graft_entry__.build()")
     L = ctypes.CDLL(path)
@@ -217,21 +227,21 @@ def amg_vcycle(ctx: int, r_dev, z_dev) -> None:
 def amg_pcg_solve(ctx: int, b_dev, x_dev, tol: float, maxit: int):
     info = amg_solve_info()
     rc = lib().amg_pcg_solve(ctx, _ptr(b_dev), _ptr(x_dev), tol, maxit, ctypes.byref(info))
-    _check(rc, "amg_pcg_solve", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    _check(rc, "amg_pcg_solve", allow=_SOLVE_STATUSES)
     return rc, info
 
 
 def amg_bicgstab_solve(ctx: int, b_dev, x_dev, tol: float, maxit: int):
     info = amg_solve_info()
     rc = lib().amg_bicgstab_solve(ctx, _ptr(b_dev), _ptr(x_dev), tol, maxit, ctypes.byref(info))
-    _check(rc, "amg_bicgstab_solve", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    _check(rc, "amg_bicgstab_solve", allow=_SOLVE_STATUSES)
     return rc, info
 
 
 def amg_pcg_solve_host(ctx: int, b_host: np.ndarray, x_host: np.ndarray, tol: float, maxit: int):
     info = amg_solve_info()
     rc = lib().amg_pcg_solve_host(ctx, _ptr(b_host), _ptr(x_host), tol, maxit, ctypes.byref(info))
-    _check(rc, "amg_pcg_solve_host", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    _check(rc, "amg_pcg_solve_host", allow=_SOLVE_STATUSES)
     return rc, info
 
 
@@ -240,7 +250,7 @@ def amg_pcg_solve_host_zero_guess(ctx: int, b_host: np.ndarray, x_host: np.ndarr
     info = amg_solve_info()
     rc = lib().amg_pcg_solve_host_zero_guess(ctx, _ptr(b_host), _ptr(x_host), tol, maxit,
                                              ctypes.byref(info))
-    _check(rc, "amg_pcg_solve_host_zero_guess", allow=(AMG_ENOTCONV, AMG_ENOTSPD))
+    _check(rc, "amg_pcg_solve_host_zero_guess", allow=_SOLVE_STATUSES)
     return rc, info
 
 
@@ -511,7 +521,7 @@ class Server:
         self.params = amg_server_params_default(dim)
         for k, v in overrides.items():
             if hasattr(self.params.params, k) and k not in ("max_slots", "setup_threads", "maxit",
-                                                             "hbm_budget_bytes"):
+                                                             "hbm_budget_bytes", "batch_vcycles"):
                 setattr(self.params.params, k, v)
             else:
                 setattr(self.params, k, v)

@@ -360,6 +360,66 @@ void wait_selftest(long long limit, cudaStream_t s, int32_t* status, double* ela
 extern int g_reduction_blocks;        // grid of the reduction kernels (SMs x 8)
 int reduction_blocks(int64_t work_threads);
 
+// ---------------------------------------------------------------------------
+// V-cycle launches as records
+//
+// Every V-cycle kernel is a body run(bid, gdim, VArgs) over one block: as its
+// own launch (the block and grid of the launch) or as one segment of a
+// launch that covers the same step of several contexts' V-cycles (each block
+// finds its segment and runs the body with that segment's block index and
+// arguments).  A segment's rows are computed exactly as in its own launch, so
+// a batched V-cycle gives each context the bits of its own V-cycle.
+// ---------------------------------------------------------------------------
+struct VArgs {
+    int32_t r0 = 0, r1 = 0, jmax = 0, n = 0, nc = 0, width = 0, ld = 0;
+    int64_t sw = 0, nslices = 0, cap = 0;
+    const uint16_t* rlen = nullptr;
+    const int32_t* scol = nullptr;
+    const int32_t* idx = nullptr;     // aggregate map, or restriction list pointers
+    const int32_t* idx2 = nullptr;    // restriction list rows
+    const void* sval = nullptr;
+    const void* dv = nullptr;         // 1/A_ii, A_ii, or the dense coarsest inverse
+    const void* t = nullptr;          // transfer weights of the scaled levels
+    const void* b = nullptr;          // right-hand side / residual / coarse correction
+    void* x = nullptr;
+    void* out = nullptr;              // residual, coarse right-hand side, or zeroed vector
+    const double* rin = nullptr;      // float64 residual entering the float32 V-cycle
+    const double* isq = nullptr;      // 1 / sqrt(A_ii) of level 0
+    double* z = nullptr;              // float64 output of the float32 V-cycle
+    int32_t* err = nullptr;
+    double omega = 0.0;
+};
+
+struct VRec;
+// launches up to kMaxVBatch records of one body and block size as one grid
+using VBatchLauncher = void (*)(const VRec* const* recs, int n, cudaStream_t s);
+constexpr int kMaxVBatch = 32;
+
+// A recorded V-cycle launch and its place in the V-cycle: phase (-1 entry
+// conversion, 0 descent and coarsest solve, 1 ascent, 2 exit conversion),
+// level key (the level on the descent, 64 - level on the ascent, so that
+// deeper levels come first) and step within the level.  Merging the records
+// of several contexts by (phase, level key, step) keeps each context's order.
+struct VRec {
+    VBatchLauncher launch = nullptr;
+    int grid = 0, block = 0;
+    size_t smem = 0;
+    int phase = 0, level = 0, step = 0;
+    VArgs a;
+};
+
+// When set, the V-cycle launchers append records here instead of launching;
+// t_vkey is the position the next record gets (set by the V-cycle driver).
+struct VKey {
+    int phase = 0, level = 0, step = 0;
+};
+extern thread_local std::vector<VRec>* t_vrecord;
+extern thread_local VKey t_vkey;
+
+// Launch records that share body and block size as one grid per kMaxVBatch
+// records (records of one step of different contexts: independent).
+void launch_vrecords(const VRec* const* recs, int n, cudaStream_t s);
+
 // V-cycle passes (see kernels.cu).  first: the first two forward colour passes
 // from a zero guess (optionally zeroing the next level's right-hand side);
 // pass: one colour, neighbours at positions >= jmax taken as zero;
@@ -539,6 +599,9 @@ struct amg_ctx {
     double *rt = nullptr, *bv = nullptr, *by = nullptr, *bs = nullptr, *bt = nullptr;
     // sweep plans by (level, lanes + 16 x block): the pre- and post-smoother
     std::map<std::pair<int, int>, std::pair<amg::SweepPlan, amg::SweepPlan>> sweep_plans;
+    // the V-cycle of each precision as launch records (batched serving)
+    std::vector<amg::VRec> vrec[2];
+    bool vrec_ok[2] = {false, false};
     amg::BiScalars* bsc = nullptr;        // BiCGSTAB scalars (device)
     amg::BiScalars* bsc_host = nullptr;   // pinned mirror
     cudaGraphExec_t graph_bi[2] = {nullptr, nullptr};      // BiCGSTAB loop, per precision
@@ -585,4 +648,15 @@ namespace amg {
 // next step was issued, 2 = the solve has finished and c->acg.info is final.
 void pcg_async_begin(amg_ctx* c, double tol, int32_t maxit);
 int pcg_async_step(amg_ctx* c);
+// The stepping split around the preconditioner (batched serving): poll
+// returns 0 busy, 1 issued the end of the solve, 2 finished, 3 needs
+// z = B r on c->r (first: the first direction); resume issues the rest of
+// the iteration after the caller has ordered z = B r before it.
+int pcg_async_poll(amg_ctx* c, bool* first);
+void pcg_async_resume(amg_ctx* c, bool first);
+// z = B r on the context's level-0 vectors (c->r -> c->z) on its own stream
+void precondition_context(amg_ctx* c);
+// z = B r for the contexts cs[0..n), their V-cycles merged step by step into
+// shared launches on stream s (records are built on first use)
+void batched_precondition(amg_ctx* const* cs, int n, cudaStream_t s);
 }  // namespace amg

@@ -41,6 +41,23 @@ __device__ __forceinline__ T group_sum(T s) {
 __device__ __forceinline__ double fmad(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ float fmad(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 
+// The checked build (compiled with AMG_DEVICE_CHECKS): every gathered index,
+// restriction-list row and aggregate index is tested against its range
+// before use; one outside it is recorded as AMG_ERANGE in the solve's status
+// word and contributes zero instead of being read.  In the regular build the
+// test is the constant true and costs nothing.
+#ifdef AMG_DEVICE_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+__device__ __forceinline__ bool index_ok(int j, int n, int32_t* err) {
+    if (!kChecks) return true;
+    if ((unsigned)j < (unsigned)n) return true;
+    if (err) atomicCAS(err, 0, AMG_ERANGE);
+    return false;
+}
+
 // programmatic dependent launch: let the next kernel of the stream start, and
 // wait for every predecessor to finish (both are no-ops without the launch
 // attribute)
@@ -60,12 +77,14 @@ __device__ __forceinline__ T ldm(const T* p) {
 // SELL-32 row (base = slice start + row mod 32)
 template <bool NEG, typename T, typename X>
 __device__ __forceinline__ T sell_row(int64_t base, int len, const int32_t* __restrict__ scol,
-                                      const T* __restrict__ sval, const X* x, T acc) {
+                                      const T* __restrict__ sval, const X* x, T acc, int n,
+                                      int32_t* err) {
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
         const int64_t e = base + 32 * (int64_t)k;
         const T a = __ldcs(sval + e);
-        acc = fmad(NEG ? -a : a, T(x[__ldcs(scol + e)]), acc);
+        const int j = __ldcs(scol + e);
+        acc = fmad(NEG ? -a : a, index_ok(j, n, err) ? T(x[j]) : T(0), acc);
     }
     return acc;
 }
@@ -91,6 +110,11 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // CG scalar update of `mode`.
 __device__ void finish_reduction(double v0, double v1, double* partials, double* partials2,
                                  unsigned int* counter, PcgScalars* sc, double* out, int mode,
+                                 double* sh);
+__device__ __forceinline__ bool finite_dot(double a) { return isfinite(a); }
+
+__device__ void finish_reduction(double v0, double v1, double* partials, double* partials2,
+                                 unsigned int* counter, PcgScalars* sc, double* out, int mode,
                                  double* sh) {
     __shared__ bool last;
     if (threadIdx.x == 0) {
@@ -111,6 +135,18 @@ __device__ void finish_reduction(double v0, double v1, double* partials, double*
     if (mode == kRZFlex) b = block_sum(b, sh);
     if (threadIdx.x != 0) return;
     *counter = 0u;
+    // a NaN or infinity in a dot product of the iteration ends the solve
+    if (mode != kStore && (!finite_dot(a) || (mode == kRZFlex && !finite_dot(b)))) {
+        if (mode == kRR0) {
+            sc->rr0 = a;
+            sc->rr = a;
+            sc->iters = 0;
+        }
+        sc->status = AMG_ENONFINITE;
+        sc->done = 1;
+        sc->alpha = 0.0;
+        return;
+    }
     switch (mode) {
         case kRR0:
             sc->rr0 = a;
@@ -218,8 +254,8 @@ template <int LPR, int MODE, typename T, typename AccF, typename Wait = PdlWait>
 __device__ __forceinline__ T row_update(int64_t base, int len, int width, int lane, int jmax,
                                         const int32_t* __restrict__ scol,
                                         const T* __restrict__ sval, const T* x,
-                                        const T* b, const T* __restrict__ dinv, AccF acc,
-                                        Wait wait = Wait()) {
+                                        const T* b, const T* __restrict__ dinv, int nrows,
+                                        int32_t* err, AccF acc, Wait wait = Wait()) {
     static_assert(LPR != kFine, "the fine level uses the staged kernels");
     // every lane of the warp runs the same number of batches (the slice width
     // bounds every row length), so the warp-wide votes below see all 32 lanes
@@ -238,6 +274,8 @@ __device__ __forceinline__ T row_update(int64_t base, int len, int width, int la
             const int64_t ee = base + 32 * (int64_t)(in ? k : 0);
             j[u] = in ? scol[ee] : jmax;
             a[u] = in ? sval[ee] : T(0);
+            // checked build: a stored index out of range is skipped (and recorded)
+            if (kChecks && in && !index_ok(j[u], nrows, err)) j[u] = jmax;
         }
     };
     load_batch(0);
@@ -271,9 +309,9 @@ template <int LPR>
 struct RowOf {
     int row, lane;
     bool valid;
-    __device__ RowOf(int r0, int r1) {
+    __device__ RowOf(int r0, int r1, int bid) {
         constexpr int G = lanes_of<LPR>();
-        const int64_t tt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        const int64_t tt = bid * (int64_t)blockDim.x + threadIdx.x;
         row = (r0 & ~31) + (int)(tt / G);
         lane = (int)(tt % G);
         valid = row >= r0 && row < r1;
@@ -283,68 +321,85 @@ struct RowOf {
 // Fused first two forward passes of the pre-smoother from a zero initial
 // guess: rows of colour 0 ([0, c1)) have only zero neighbours, so
 // x_i = b_i / A_ii; rows of colour 1 ([c1, c2)) see colour-0 neighbours (their
-// new values b_j / A_jj) and zeros.
+// new values b_j / A_jj) and zeros.  Arguments: c1 = jmax, c2 = r1, dv = 1/A_ii.
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_first(int c1, int c2, int64_t sw,
-                                                  const uint16_t* __restrict__ rlen,
-                                                  const int32_t* __restrict__ scol,
-                                                  const T* __restrict__ sval,
-                                                  const T* __restrict__ dinv,
-                                                  const T* b, T* x) {
-    pdl_launch_dependents();
-    const RowOf<LPR> R(0, c2);
-    const int rr = R.valid ? R.row : 0;
-    // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
-    // lane of the warp still reaches the shuffles of the group sum
-    const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
-    const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T di = R.valid ? dinv[rr] : T(0);
-    const T s = row_update<LPR, kNbrFirst, T>(base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x,
-                                               b, dinv, [&] { return R.valid ? b[rr] : T(0); });
-    if (R.valid && R.lane == 0) x[rr] = s * di;
-}
+struct FirstBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int c1 = a.jmax, c2 = a.r1;
+        const int64_t sw = a.sw;
+        const uint16_t* __restrict__ rlen = a.rlen;
+        const int32_t* __restrict__ scol = a.scol;
+        const T* __restrict__ sval = static_cast<const T*>(a.sval);
+        const T* __restrict__ dinv = static_cast<const T*>(a.dv);
+        const T* b = static_cast<const T*>(a.b);
+        T* x = static_cast<T*>(a.x);
+        pdl_launch_dependents();
+        const RowOf<LPR> R(0, c2, bid);
+        const int rr = R.valid ? R.row : 0;
+        // colour-0 rows take no neighbour term (length 0: s = b_i exactly); every
+        // lane of the warp still reaches the shuffles of the group sum
+        const int len = (R.valid && rr >= c1) ? (int)rlen[rr] : 0;
+        const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
+        const T di = R.valid ? dinv[rr] : T(0);
+        const T s = row_update<LPR, kNbrFirst, T>(base, len, (int)(sw >> 5), R.lane, c1, scol, sval, x,
+                                                   b, dinv, a.n, a.err,
+                                                   [&] { return R.valid ? b[rr] : T(0); });
+        if (R.valid && R.lane == 0) x[rr] = s * di;
+    }
+};
 
 // One Gauss-Seidel update of the rows [r0, r1) of one colour:
 //   x_i = (b_i - sum_{j != i, j < jmax} A_ij x_j) / A_ii.
 // Rows of one colour are not coupled, so they update in parallel.
+// Arguments: r0, r1, jmax, dv = 1/A_ii.
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_gs_pass(int r0, int r1, int jmax,
-                                                    int64_t sw,
-                                                    const uint16_t* __restrict__ rlen,
-                                                    const int32_t* __restrict__ scol,
-                                                    const T* __restrict__ sval,
-                                                    const T* __restrict__ dinv,
-                                                    const T* b, T* x) {
-    pdl_launch_dependents();
-    const RowOf<LPR> R(r0, r1);
-    const int rr = R.valid ? R.row : r0;
-    const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T di = R.valid ? dinv[rr] : T(0);
-    const T s = row_update<LPR, kNbrX, T>(base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5),
-                                          R.lane, jmax, scol, sval, x, b, dinv,
-                                          [&] { return R.valid ? b[rr] : T(0); });
-    if (R.valid && R.lane == 0) x[rr] = s * di;
-}
+struct PassBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int r0 = a.r0, r1 = a.r1, jmax = a.jmax;
+        const int64_t sw = a.sw;
+        const uint16_t* __restrict__ rlen = a.rlen;
+        const int32_t* __restrict__ scol = a.scol;
+        const T* __restrict__ sval = static_cast<const T*>(a.sval);
+        const T* __restrict__ dinv = static_cast<const T*>(a.dv);
+        const T* b = static_cast<const T*>(a.b);
+        T* x = static_cast<T*>(a.x);
+        pdl_launch_dependents();
+        const RowOf<LPR> R(r0, r1, bid);
+        const int rr = R.valid ? R.row : r0;
+        const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
+        const T di = R.valid ? dinv[rr] : T(0);
+        const T s = row_update<LPR, kNbrX, T>(base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5),
+                                              R.lane, jmax, scol, sval, x, b, dinv, a.n, a.err,
+                                              [&] { return R.valid ? b[rr] : T(0); });
+        if (R.valid && R.lane == 0) x[rr] = s * di;
+    }
+};
 
-// r = b - A x for rows [r0, n)
+// r = b - A x for rows [r0, n).  Arguments: r0, r1 = n, dv = A_ii, out = r.
 template <int LPR, typename T>
-__global__ void __launch_bounds__(kBlock) k_residual(int r0, int n, int64_t sw,
-                                                     const uint16_t* __restrict__ rlen,
-                                                     const int32_t* __restrict__ scol,
-                                                     const T* __restrict__ sval,
-                                                     const T* __restrict__ diag,
-                                                     const T* b, const T* x, T* r) {
-    pdl_launch_dependents();
-    const RowOf<LPR> R(r0, n);
-    const int rr = R.valid ? R.row : r0;
-    const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
-    const T dg = R.valid ? diag[rr] : T(0);
-    const T v = row_update<LPR, kNbrX, T>(
-        base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5), R.lane, n, scol, sval, x,
-        (const T*)nullptr, (const T*)nullptr,
-        [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
-    if (R.valid && R.lane == 0) r[rr] = v;
-}
+struct ResidualBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int r0 = a.r0, n = a.r1;
+        const int64_t sw = a.sw;
+        const uint16_t* __restrict__ rlen = a.rlen;
+        const int32_t* __restrict__ scol = a.scol;
+        const T* __restrict__ sval = static_cast<const T*>(a.sval);
+        const T* __restrict__ diag = static_cast<const T*>(a.dv);
+        const T* b = static_cast<const T*>(a.b);
+        const T* x = static_cast<const T*>(a.x);
+        T* r = static_cast<T*>(a.out);
+        pdl_launch_dependents();
+        const RowOf<LPR> R(r0, n, bid);
+        const int rr = R.valid ? R.row : r0;
+        const int64_t base = (int64_t)(rr >> 5) * sw + (rr & 31);
+        const T dg = R.valid ? diag[rr] : T(0);
+        const T v = row_update<LPR, kNbrX, T>(
+            base, R.valid ? (int)rlen[rr] : 0, (int)(sw >> 5), R.lane, n, scol, sval, x,
+            (const T*)nullptr, (const T*)nullptr, a.n, a.err,
+            [&] { return R.valid ? fmad(-dg, x[rr], b[rr]) : T(0); });
+        if (R.valid && R.lane == 0) r[rr] = v;
+    }
+};
 
 // ---------------------------------------------------------------------------
 // Dependency-driven sweep (see SweepPlan in device.h): every colour pass of a
@@ -391,7 +446,7 @@ __global__ void __launch_bounds__(kBlock) k_sweep(int npass, const SweepPass* __
                                                   const int32_t* __restrict__ scol,
                                                   const T* __restrict__ sval,
                                                   const T* __restrict__ dinv, const T* b, T* x,
-                                                  int32_t* err) {
+                                                  int32_t* err, int nrows) {
     __shared__ SweepPass sp[kSweepMaxPasses];
     __shared__ uint32_t s_epoch;
     __shared__ int s_ok;
@@ -454,7 +509,8 @@ __global__ void __launch_bounds__(kBlock) k_sweep(int npass, const SweepPass* __
             __syncthreads();
         };
         const T v = row_update<LPR, kNbrX, T>(base, len, (int)(sw >> 5), lane, P.jmax, scol, sval, x,
-                                              b, dinv, [&] { return valid ? b[rr] : T(0); }, wait);
+                                              b, dinv, nrows, err,
+                                              [&] { return valid ? b[rr] : T(0); }, wait);
         if (!s_ok) return;
         if (valid && lane == 0) x[rr] = v * di;
         __syncthreads();
@@ -635,8 +691,8 @@ struct FineTile {
                       // set by stage_slices
     int32_t* s_col;
     T* s_val;
-    __device__ FineTile(int r0, int64_t nslices, int64_t cap, unsigned char* smem) {
-        slice0 = (int64_t)(r0 >> 5) + (int64_t)blockIdx.x * kSlicesPerBlock;
+    __device__ FineTile(int r0, int64_t nslices, int64_t cap, unsigned char* smem, int bid) {
+        slice0 = (int64_t)(r0 >> 5) + (int64_t)bid * kSlicesPerBlock;
         nsl = (int)min((int64_t)kSlicesPerBlock, nslices - slice0);
         row = (int)(slice0 * 32) + (int)threadIdx.x;
         loc = (int)(threadIdx.x & 31);
@@ -649,12 +705,13 @@ struct FineTile {
 // A_ij nbr(j).  (Batching the gathers eight at a time was measured slower in
 // float64 on the 512^3 anisotropic workload: 3.07 s against 2.88 s a solve.)
 template <typename T, typename Nbr>
-__device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, Nbr nbr, T acc) {
+__device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, Nbr nbr, T acc,
+                                      int nrows, int32_t* err) {
 #pragma unroll 4
     for (int k = 0; k < len; ++k) {
         const int j = F.s_col[F.loc + 32 * k];
         const T a = F.s_val[F.loc + 32 * k];
-        if (j < jmax) acc = fmad(-a, nbr(j), acc);
+        if (index_ok(j, nrows, err) && j < jmax) acc = fmad(-a, nbr(j), acc);
     }
     return acc;
 }
@@ -665,79 +722,101 @@ __device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, N
 // still zero.  With r_in set (float32 V-cycle inside float64 CG) this kernel
 // first forms the scaled right-hand side b_i = r_i / s_i (isq = 1/s) of every
 // row.  It also zeroes the next level's right-hand side for the fused
-// residual-restriction kernel.
+// residual-restriction kernel.  Arguments: r1 = c1, n = rows of b, dv = 1/A_ii,
+// out = the vector to zero (nc entries), rin, isq.
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_fine_first0(int c1, int nb, const T* __restrict__ dinv,
-                                                        T* b, T* x, T* bc_zero, int nc,
-                                                        const double* r_in,
-                                                        const double* __restrict__ isq) {
-    pdl_launch_dependents();
-    pdl_wait();
-    const int stride = gridDim.x * blockDim.x;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nb; i += stride) {
-        T bi;
-        if (r_in) {
-            bi = (T)(r_in[i] * isq[i]);
-            b[i] = bi;
-        } else {
-            bi = b[i];
+struct FineFirst0Body {
+    static __device__ __forceinline__ void run(int bid, int gdim, const VArgs& a) {
+        const int c1 = a.r1, nb = a.n, nc = a.nc;
+        const T* __restrict__ dinv = static_cast<const T*>(a.dv);
+        T* b = const_cast<T*>(static_cast<const T*>(a.b));
+        T* x = static_cast<T*>(a.x);
+        T* bc_zero = static_cast<T*>(a.out);
+        const double* r_in = a.rin;
+        const double* __restrict__ isq = a.isq;
+        pdl_launch_dependents();
+        pdl_wait();
+        const int stride = gdim * blockDim.x;
+        for (int i = bid * blockDim.x + threadIdx.x; i < nb; i += stride) {
+            T bi;
+            if (r_in) {
+                bi = (T)(r_in[i] * isq[i]);
+                b[i] = bi;
+            } else {
+                bi = b[i];
+            }
+            if (i < c1) x[i] = bi * dinv[i];
         }
-        if (i < c1) x[i] = bi * dinv[i];
+        if (bc_zero)
+            for (int i = bid * blockDim.x + threadIdx.x; i < nc; i += stride) bc_zero[i] = T(0);
     }
-    if (bc_zero)
-        for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) bc_zero[i] = T(0);
-}
+};
 
-// k_gs_pass on the fine level.  With z_out set (the last pass over these rows
-// in a float32 V-cycle) the new value also goes out unscaled in float64:
-// z_i = x_i / s_i (isq = 1/s).
+// The staged pass of the rows [r0, r1) of one colour.  With z set (the last
+// pass over these rows in a float32 V-cycle) the new value also goes out
+// unscaled in float64: z_i = x_i / s_i (isq = 1/s).  Arguments: r0, r1, jmax,
+// width, nslices, cap, dv = 1/A_ii, z, isq, err.
 template <typename T>
-__global__ void __launch_bounds__(kFineBlock) k_fine_pass(int r0, int r1, int jmax, int width,
-                                                      int64_t nslices, int64_t cap,
-                                                      const uint16_t* __restrict__ rlen,
-                                                      const int32_t* scol, const T* sval,
-                                                      const T* __restrict__ dinv, const T* b, T* x,
-                                                      double* z_out, const double* __restrict__ isq,
-                                                      int32_t* err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
-    pdl_launch_dependents();
-    FineTile<T> F(r0, nslices, cap, smem);
-    const bool valid = F.row >= r0 && F.row < r1;
-    const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
-    const T di = valid ? __ldcs(dinv + F.row) : T(0);
-    if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
-                      F.s_col, F.s_val, &bar, err, F.loc))
-        return;
-    pdl_wait();
-    if (!valid) return;
-    const T xi = fine_row<T>(F, len, jmax, [&](int j) { return x[j]; }, b[F.row]) * di;
-    x[F.row] = xi;
-    if (z_out) z_out[F.row] = (double)xi * isq[F.row];
-}
+struct FinePassBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int r0 = a.r0, r1 = a.r1, jmax = a.jmax, width = a.width;
+        const int64_t nslices = a.nslices, cap = a.cap;
+        const uint16_t* __restrict__ rlen = a.rlen;
+        const int32_t* scol = a.scol;
+        const T* sval = static_cast<const T*>(a.sval);
+        const T* __restrict__ dinv = static_cast<const T*>(a.dv);
+        const T* b = static_cast<const T*>(a.b);
+        T* x = static_cast<T*>(a.x);
+        double* z_out = a.z;
+        const double* __restrict__ isq = a.isq;
+        extern __shared__ __align__(128) unsigned char smem[];
+        __shared__ uint64_t bar;
+        pdl_launch_dependents();
+        FineTile<T> F(r0, nslices, cap, smem, bid);
+        const bool valid = F.row >= r0 && F.row < r1;
+        const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
+        const T di = valid ? __ldcs(dinv + F.row) : T(0);
+        if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
+                          F.s_col, F.s_val, &bar, a.err, F.loc))
+            return;
+        pdl_wait();
+        if (!valid) return;
+        const T xi = fine_row<T>(F, len, jmax, [&](int j) { return x[j]; }, b[F.row], a.n, a.err) * di;
+        x[F.row] = xi;
+        if (z_out) z_out[F.row] = (double)xi * isq[F.row];
+    }
+};
 
-// k_residual on the fine level
+// The staged residual r = b - A x of the rows [r0, n).  Arguments: r0,
+// r1 = n, width, nslices, cap, dv = A_ii, out = r, err.
 template <typename T>
-__global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int width,
-                                                          int64_t nslices, int64_t cap,
-                                                          const uint16_t* __restrict__ rlen,
-                                                          const int32_t* scol, const T* sval,
-                                                          const T* __restrict__ diag, const T* b,
-                                                          const T* x, T* r, int32_t* err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
-    pdl_launch_dependents();
-    FineTile<T> F(r0, nslices, cap, smem);
-    const bool valid = F.row >= r0 && F.row < n;
-    const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
-    const T dg = valid ? __ldcs(diag + F.row) : T(0);
-    if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
-                      F.s_col, F.s_val, &bar, err, F.loc))
-        return;
-    pdl_wait();
-    if (!valid) return;
-    r[F.row] = fine_row<T>(F, len, n, [&](int j) { return x[j]; }, fmad(-dg, x[F.row], b[F.row]));
-}
+struct FineResidualBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int r0 = a.r0, n = a.r1, width = a.width;
+        const int64_t nslices = a.nslices, cap = a.cap;
+        const uint16_t* __restrict__ rlen = a.rlen;
+        const int32_t* scol = a.scol;
+        const T* sval = static_cast<const T*>(a.sval);
+        const T* __restrict__ diag = static_cast<const T*>(a.dv);
+        const T* b = static_cast<const T*>(a.b);
+        const T* x = static_cast<const T*>(a.x);
+        T* r = static_cast<T*>(a.out);
+        extern __shared__ __align__(128) unsigned char smem[];
+        __shared__ uint64_t bar;
+        pdl_launch_dependents();
+        FineTile<T> F(r0, nslices, cap, smem, bid);
+        const bool valid = F.row >= r0 && F.row < n;
+        const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
+        const T dg = valid ? __ldcs(diag + F.row) : T(0);
+        if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
+                          F.s_col, F.s_val, &bar, a.err, F.loc))
+            return;
+        pdl_wait();
+        if (!valid) return;
+        r[F.row] = fine_row<T>(F, len, n, [&](int j) { return x[j]; }, fmad(-dg, x[F.row], b[F.row]),
+                               a.n, a.err);
+    }
+};
 
 // Residual and restriction in one pass on a two-colour fine level: the rows
 // of colour 1 ([c1, n)) are sorted by coarse index, so the rows of one
@@ -747,132 +826,164 @@ __global__ void __launch_bounds__(kFineBlock) k_fine_residual(int r0, int n, int
 // in order and adds it to bc (zeroed by the first pass).  A run is shorter
 // than a block, so a coarse entry receives at most two additions onto zero (a
 // run cut by a block boundary), whose result does not depend on their order:
-// the sum stays deterministic.
+// the sum stays deterministic.  Arguments: r0 = c1, r1 = n, width, nslices,
+// cap, dv = A_ii, idx = aggregate map, t, out = bc, err.
 template <typename T, bool SCALED>
-__global__ void __launch_bounds__(kFineBlock) k_fine_residual_restrict(
-    int c1, int n, int width, int64_t nslices, int64_t cap, const uint16_t* __restrict__ rlen,
-    const int32_t* scol, const T* sval, const T* __restrict__ diag, const T* b, const T* x,
-    const int32_t* __restrict__ agg, const T* __restrict__ t, T* bc, int32_t* err) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint64_t bar;
-    __shared__ T sv[kFineBlock];
-    __shared__ int sk[kFineBlock];
-    pdl_launch_dependents();
-    FineTile<T> F(c1, nslices, cap, smem);
-    const bool valid = F.row >= c1 && F.row < n;
-    const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
-    const T dg = valid ? __ldcs(diag + F.row) : T(0);
-    const int key = valid ? __ldcs(agg + F.row) : -1;
-    const T ti = (SCALED && valid) ? __ldcs(t + F.row) : T(1);
-    if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
-                      F.s_col, F.s_val, &bar, err, F.loc))
-        return;
-    pdl_wait();
-    T v = T(0);
-    if (valid) {
-        const T ri = fine_row<T>(F, len, n, [&](int j) { return x[j]; },
-                                 fmad(-dg, x[F.row], b[F.row]));
-        v = SCALED ? ti * ri : ri;
+struct FineResRestrictBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int c1 = a.r0, n = a.r1, width = a.width;
+        const int64_t nslices = a.nslices, cap = a.cap;
+        const uint16_t* __restrict__ rlen = a.rlen;
+        const int32_t* scol = a.scol;
+        const T* sval = static_cast<const T*>(a.sval);
+        const T* __restrict__ diag = static_cast<const T*>(a.dv);
+        const T* b = static_cast<const T*>(a.b);
+        const T* x = static_cast<const T*>(a.x);
+        const int32_t* __restrict__ agg = a.idx;
+        const T* __restrict__ t = static_cast<const T*>(a.t);
+        T* bc = static_cast<T*>(a.out);
+        extern __shared__ __align__(128) unsigned char smem[];
+        __shared__ uint64_t bar;
+        __shared__ T sv[kFineBlock];
+        __shared__ int sk[kFineBlock];
+        pdl_launch_dependents();
+        FineTile<T> F(c1, nslices, cap, smem, bid);
+        const bool valid = F.row >= c1 && F.row < n;
+        const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
+        const T dg = valid ? __ldcs(diag + F.row) : T(0);
+        const int key = valid ? __ldcs(agg + F.row) : -1;
+        const T ti = (SCALED && valid) ? __ldcs(t + F.row) : T(1);
+        if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
+                          F.s_col, F.s_val, &bar, a.err, F.loc))
+            return;
+        pdl_wait();
+        T v = T(0);
+        if (valid) {
+            const T ri = fine_row<T>(F, len, n, [&](int j) { return x[j]; },
+                                     fmad(-dg, x[F.row], b[F.row]), a.n, a.err);
+            v = SCALED ? ti * ri : ri;
+        }
+        const int tid = threadIdx.x;
+        sv[tid] = v;
+        sk[tid] = key;
+        __syncthreads();
+        if (key < 0 || (tid > 0 && sk[tid - 1] == key)) return;
+        T sum = v;
+        for (int u = tid + 1; u < kFineBlock && sk[u] == key; ++u) sum += sv[u];
+        atomicAdd(bc + key, sum);
     }
-    const int tid = threadIdx.x;
-    sv[tid] = v;
-    sk[tid] = key;
-    __syncthreads();
-    if (key < 0 || (tid > 0 && sk[tid - 1] == key)) return;
-    T sum = v;
-    for (int u = tid + 1; u < kFineBlock && sk[u] == key; ++u) sum += sv[u];
-    atomicAdd(bc + key, sum);
-}
+};
 
 // coarse right-hand side: bc_J = sum over the fine rows i of aggregate J of
 // (t_i) r_i, in the stored order (Eq. prolongation: R = P^T).  The lists hold
 // the rows of colour >= 1 only: the pre-smoother's last pass updates colour 0,
-// whose residual is therefore zero.
+// whose residual is therefore zero.  Arguments: nc, idx = list pointers,
+// idx2 = list rows, t, b = r, out = bc.
 template <typename T, bool SCALED>
-__global__ void __launch_bounds__(kBlock) k_restrict(int nc, const int32_t* __restrict__ rptr,
-                                                     const int32_t* __restrict__ ridx,
-                                                     const T* __restrict__ t,
-                                                     const T* r, T* bc) {
-    pdl_launch_dependents();
-    const int J = blockIdx.x * blockDim.x + threadIdx.x;
-    if (J >= nc) return;
-    const int kb = rptr[J], k1 = rptr[J + 1];
-    int i[kUnroll];
+struct RestrictBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int nc = a.nc;
+        const int32_t* __restrict__ rptr = a.idx;
+        const int32_t* __restrict__ ridx = a.idx2;
+        const T* __restrict__ t = static_cast<const T*>(a.t);
+        const T* r = static_cast<const T*>(a.b);
+        T* bc = static_cast<T*>(a.out);
+        pdl_launch_dependents();
+        const int J = bid * blockDim.x + threadIdx.x;
+        if (J >= nc) return;
+        const int kb = rptr[J], k1 = rptr[J + 1];
+        int i[kUnroll];
 #pragma unroll
-    for (int u = 0; u < kUnroll; ++u) i[u] = (kb + u < k1) ? ridx[kb + u] : -1;
-    pdl_wait();
-    T s = T(0);
-    for (int k0 = kb; k0 < k1; k0 += kUnroll) {
-        if (k0 > kb) {
+        for (int u = 0; u < kUnroll; ++u) i[u] = (kb + u < k1) ? ridx[kb + u] : -1;
+        pdl_wait();
+        T s = T(0);
+        for (int k0 = kb; k0 < k1; k0 += kUnroll) {
+            if (k0 > kb) {
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) i[u] = (k0 + u < k1) ? ridx[k0 + u] : -1;
+                for (int u = 0; u < kUnroll; ++u) i[u] = (k0 + u < k1) ? ridx[k0 + u] : -1;
+            }
+            T v[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (i[u] >= 0 && !index_ok(i[u], a.n, a.err)) i[u] = -1;
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                v[u] = i[u] >= 0 ? (SCALED ? t[i[u]] * r[i[u]] : r[i[u]]) : T(0);
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+                if (i[u] >= 0) s += v[u];
         }
-        T v[kUnroll];
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            v[u] = i[u] >= 0 ? (SCALED ? t[i[u]] * r[i[u]] : r[i[u]]) : T(0);
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-            if (i[u] >= 0) s += v[u];
+        bc[J] = s;
     }
-    bc[J] = s;
-}
+};
 
 // x_i += omega (t_i) e_{agg(i)} on rows [r0, n): piecewise-constant
 // prolongation with the over-correction factor omega.  Callers pass r0 = the
 // first row of colour 1: the post-smoother's first pass recomputes colour 0
-// without reading its old values.
+// without reading its old values.  Arguments: r0, r1 = n, idx = aggregate
+// map, t, b = e, x, omega.
 template <typename T, bool SCALED>
-__global__ void __launch_bounds__(kBlock) k_prolong(int r0, int n, const int32_t* __restrict__ agg,
-                                                    const T* __restrict__ t,
-                                                    const T* e, T* x, T omega) {
-    pdl_launch_dependents();
-    const int i = r0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (i >= n) return;
-    const int a = agg[i];
-    if (a < 0) return;
-    const T w = SCALED ? omega * t[i] : omega;
-    pdl_wait();
-    x[i] = fmad(w, e[a], x[i]);
-}
+struct ProlongBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int r0 = a.r0, n = a.r1;
+        const int32_t* __restrict__ agg = a.idx;
+        const T* __restrict__ t = static_cast<const T*>(a.t);
+        const T* e = static_cast<const T*>(a.b);
+        T* x = static_cast<T*>(a.x);
+        const T omega = (T)a.omega;
+        pdl_launch_dependents();
+        const int i = r0 + (int)(bid * blockDim.x + threadIdx.x);
+        if (i >= n) return;
+        const int g = agg[i];
+        if (g < 0 || !index_ok(g, a.nc, a.err)) return;
+        const T w = SCALED ? omega * t[i] : omega;
+        pdl_wait();
+        x[i] = fmad(w, e[g], x[i]);
+    }
+};
 
 // x = M b, M dense row-major (coarsest-level solve with the inverse formed at
 // setup); one warp per row, float64 arithmetic.  A float32 b is first copied,
 // converted to float64, into shared memory by the block: every row reads all
 // of b, and reading it as float32 would cost a conversion per matrix entry on
 // the float64 pipe.  A float64 b is read directly (L1 serves the rows of the
-// block).
+// block).  Arguments: n, dv = M (float64), b, x.
 template <typename TB>
-__global__ void __launch_bounds__(kBlock) k_dense_gemv(int n, const double* __restrict__ M,
-                                                       const TB* b, TB* x) {
-    constexpr int kPre = 4;   // row entries per lane loaded before the wait
-    constexpr bool kStage = !std::is_same<TB, double>::value;
-    extern __shared__ double sbuf[];
-    pdl_launch_dependents();
-    const int lane = threadIdx.x & 31;
-    const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const double* m = M + (size_t)min(row, n - 1) * n;
-    double m0[kPre];
+struct GemvBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        constexpr int kPre = 4;   // row entries per lane loaded before the wait
+        constexpr bool kStage = !std::is_same<TB, double>::value;
+        const int n = a.n;
+        const double* __restrict__ M = static_cast<const double*>(a.dv);
+        const TB* b = static_cast<const TB*>(a.b);
+        TB* x = static_cast<TB*>(a.x);
+        extern __shared__ double sbuf[];
+        pdl_launch_dependents();
+        const int lane = threadIdx.x & 31;
+        const int row = (int)((bid * (int64_t)blockDim.x + threadIdx.x) >> 5);
+        const double* m = M + (size_t)min(row, n - 1) * n;
+        double m0[kPre];
 #pragma unroll
-    for (int u = 0; u < kPre; ++u) m0[u] = (lane + 32 * u < n) ? m[lane + 32 * u] : 0.0;
-    pdl_wait();
-    const double* sb;
-    if (kStage) {
-        for (int k = threadIdx.x; k < n; k += blockDim.x) sbuf[k] = (double)b[k];
-        __syncthreads();
-        sb = sbuf;
-    } else {
-        sb = reinterpret_cast<const double*>(b);
+        for (int u = 0; u < kPre; ++u) m0[u] = (lane + 32 * u < n) ? m[lane + 32 * u] : 0.0;
+        pdl_wait();
+        const double* sb;
+        if (kStage) {
+            for (int k = threadIdx.x; k < n; k += blockDim.x) sbuf[k] = (double)b[k];
+            __syncthreads();
+            sb = sbuf;
+        } else {
+            sb = reinterpret_cast<const double*>(b);
+        }
+        if (row >= n) return;
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < kPre; ++u)
+            if (lane + 32 * u < n) s += m0[u] * sb[lane + 32 * u];
+        for (int k = lane + 32 * kPre; k < n; k += 32) s += m[k] * sb[k];
+        s = group_sum<32>(s);
+        if (lane == 0) x[row] = (TB)s;
     }
-    if (row >= n) return;
-    double s = 0.0;
-#pragma unroll
-    for (int u = 0; u < kPre; ++u)
-        if (lane + 32 * u < n) s += m0[u] * sb[lane + 32 * u];
-    for (int k = lane + 32 * kPre; k < n; k += 32) s += m[k] * sb[k];
-    s = group_sum<32>(s);
-    if (lane == 0) x[row] = (TB)s;
-}
+};
 
 // Coarsest solve of the float32 V-cycle with the float32 copy of the inverse
 // (coarsest_fp32): rows of ld = n rounded up to 4 floats, zero beyond n, read
@@ -889,42 +1000,48 @@ __device__ __forceinline__ float4 b_group(const float* __restrict__ b, int n, in
     return c;
 }
 
-__global__ void __launch_bounds__(kBlock) k_dense_gemv_f32(int n, int ld, const float* __restrict__ M,
-                                                           const float* __restrict__ b, float* x) {
-    constexpr int kU = 4;   // float4 groups of the row per lane in flight
-    pdl_launch_dependents();
-    const int lane = threadIdx.x & 31;
-    const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-    const int q4 = ld >> 2;
-    const float4* m = reinterpret_cast<const float4*>(M + (size_t)min(row, n - 1) * ld);
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    float4 v[kU];
+// Arguments: n, ld, dv = M (float32), b, x.
+struct GemvF32Body {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        constexpr int kU = 4;   // float4 groups of the row per lane in flight
+        const int n = a.n, ld = a.ld;
+        const float* __restrict__ M = static_cast<const float*>(a.dv);
+        const float* __restrict__ b = static_cast<const float*>(a.b);
+        float* x = static_cast<float*>(a.x);
+        pdl_launch_dependents();
+        const int lane = threadIdx.x & 31;
+        const int row = (int)((bid * (int64_t)blockDim.x + threadIdx.x) >> 5);
+        const int q4 = ld >> 2;
+        const float4* m = reinterpret_cast<const float4*>(M + (size_t)min(row, n - 1) * ld);
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 v[kU];
 #pragma unroll
-    for (int u = 0; u < kU; ++u) v[u] = lane + 32 * u < q4 ? m[lane + 32 * u] : zero;
-    pdl_wait();
-    if (row >= n) return;
-    float acc[kU] = {};
-    for (int q = lane;; q += 32 * kU) {
-        float4 c[kU];
+        for (int u = 0; u < kU; ++u) v[u] = lane + 32 * u < q4 ? m[lane + 32 * u] : zero;
+        pdl_wait();
+        if (row >= n) return;
+        float acc[kU] = {};
+        for (int q = lane;; q += 32 * kU) {
+            float4 c[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) c[u] = q + 32 * u < q4 ? b_group(b, n, q + 32 * u) : zero;
-        const int qn = q + 32 * kU;
-        float4 w[kU];
+            for (int u = 0; u < kU; ++u) c[u] = q + 32 * u < q4 ? b_group(b, n, q + 32 * u) : zero;
+            const int qn = q + 32 * kU;
+            float4 w[kU];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) w[u] = qn + 32 * u < q4 ? m[qn + 32 * u] : zero;
+            for (int u = 0; u < kU; ++u) w[u] = qn + 32 * u < q4 ? m[qn + 32 * u] : zero;
 #pragma unroll
-        for (int u = 0; u < kU; ++u)
-            acc[u] = fmaf(v[u].x, c[u].x, fmaf(v[u].y, c[u].y, fmaf(v[u].z, c[u].z,
-                     fmaf(v[u].w, c[u].w, acc[u]))));
-        if (qn >= q4) break;
+            for (int u = 0; u < kU; ++u)
+                acc[u] = fmaf(v[u].x, c[u].x, fmaf(v[u].y, c[u].y, fmaf(v[u].z, c[u].z,
+                         fmaf(v[u].w, c[u].w, acc[u]))));
+            if (qn >= q4) break;
 #pragma unroll
-        for (int u = 0; u < kU; ++u) v[u] = w[u];
+            for (int u = 0; u < kU; ++u) v[u] = w[u];
+        }
+        float t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+        if (lane == 0) x[row] = t;
     }
-    float t = (acc[0] + acc[1]) + (acc[2] + acc[3]);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
-    if (lane == 0) x[row] = t;
-}
+};
 
 __global__ void k_gather(int n, const int32_t* __restrict__ idx, const double* x, double* y) {
     pdl_launch_dependents();
@@ -944,25 +1061,64 @@ __global__ void k_scatter(int n, const int32_t* __restrict__ idx, const double* 
     y[j] = x[i];
 }
 
-// float64 -> scaled float32 at V-cycle entry: rhat = r / s, s = sqrt(A_ii)
-__global__ void k_to_scaled32(int n, const double* r, const double* __restrict__ isq, float* rhat) {
-    pdl_launch_dependents();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double w = isq[i];
-    pdl_wait();
-    rhat[i] = (float)(r[i] * w);
+// float64 -> scaled float32 at V-cycle entry: rhat = r / s, s = sqrt(A_ii).
+// Arguments: n, rin = r, isq, x = rhat.
+struct ToScaledBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int n = a.n;
+        const double* r = a.rin;
+        const double* __restrict__ isq = a.isq;
+        float* rhat = static_cast<float*>(a.x);
+        pdl_launch_dependents();
+        const int i = bid * blockDim.x + threadIdx.x;
+        if (i >= n) return;
+        const double w = isq[i];
+        pdl_wait();
+        rhat[i] = (float)(r[i] * w);
+    }
+};
+
+// scaled float32 -> float64 at V-cycle exit: z = zhat / s.
+// Arguments: n, b = zhat, isq, z.
+struct FromScaledBody {
+    static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
+        const int n = a.n;
+        const float* zhat = static_cast<const float*>(a.b);
+        const double* __restrict__ isq = a.isq;
+        double* z = a.z;
+        pdl_launch_dependents();
+        const int i = bid * blockDim.x + threadIdx.x;
+        if (i >= n) return;
+        const double w = isq[i];
+        pdl_wait();
+        z[i] = (double)zhat[i] * w;
+    }
+};
+
+// ---------------------------------------------------------------------------
+// V-cycle launches: a body as its own launch (k_single), or several records
+// of one body as one launch (k_batched).  In a batched launch the records'
+// grids follow one another; each block finds its record by the running sums
+// of the grids (kernel parameters, read through the constant cache) and runs
+// the body with the block index inside that record's grid.
+// ---------------------------------------------------------------------------
+struct VBatch {
+    int nrec;
+    int bstart[kMaxVBatch + 1];
+    int grid[kMaxVBatch];
+    VArgs a[kMaxVBatch];
+};
+
+template <typename Body>
+__global__ void __launch_bounds__(kBlock) k_single(const VArgs a) {
+    Body::run((int)blockIdx.x, (int)gridDim.x, a);
 }
 
-// scaled float32 -> float64 at V-cycle exit: z = zhat / s
-__global__ void k_from_scaled32(int n, const float* zhat, const double* __restrict__ isq,
-                                double* z) {
-    pdl_launch_dependents();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double w = isq[i];
-    pdl_wait();
-    z[i] = (double)zhat[i] * w;
+template <typename Body>
+__global__ void __launch_bounds__(kBlock) k_batched(const VBatch p) {
+    int r = 0;
+    while (r + 1 < p.nrec && p.bstart[r + 1] <= (int)blockIdx.x) ++r;
+    Body::run((int)blockIdx.x - p.bstart[r], p.grid[r], p.a[r]);
 }
 
 // ---------------------------------------------------------------------------
@@ -987,7 +1143,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_residual(int n, int64_t sw,
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double s0 = fmad(-__ldcs(diag + row), x[row], b[row]);
-        const double v = sell_row<true>(base, __ldcs(rlen + row), scol, sval, x, s0);
+        const double v = sell_row<true>(base, __ldcs(rlen + row), scol, sval, x, s0, n, &sc->status);
         if (r) r[row] = v;
         acc = fmad(v, v, acc);
     }
@@ -1012,7 +1168,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv_pq(int n, int64_t sw,
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double pi = p[row];
         const double v = sell_row<false>(base, __ldcs(rlen + row), scol, sval, p,
-                                         __ldcs(diag + row) * pi);
+                                         __ldcs(diag + row) * pi, n, &sc->status);
         q[row] = v;
         acc = fmad(pi, v, acc);
     }
@@ -1158,6 +1314,17 @@ __device__ void finish_bi(double v0, double v1, double* partials, double* partia
     b = block_sum(b, sh);
     if (threadIdx.x != 0) return;
     *counter = 0u;
+    // a NaN or infinity in a dot product of the iteration ends the solve
+    if (!finite_dot(a) || !finite_dot(b)) {
+        if (mode == kBiStart) {
+            bs->r0 = sqrt(a);
+            bs->iters = 0;
+            bs->rel = 0.0;
+        }
+        bs->status = AMG_ENONFINITE;
+        bs->why = 4;
+        return;
+    }
     switch (mode) {
         case kBiStart:   // a = r.r
             bs->r0 = sqrt(a);
@@ -1227,7 +1394,7 @@ __global__ void __launch_bounds__(kBlock) k_bi_start(int n, int64_t sw,
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double s0 = fmad(-__ldcs(diag + row), x[row], b[row]);
-        const double v = sell_row<true>(base, __ldcs(rlen + row), scol, sval, x, s0);
+        const double v = sell_row<true>(base, __ldcs(rlen + row), scol, sval, x, s0, n, &bs->status);
         r[row] = v;
         rt[row] = v;
         a = fmad(v, v, a);
@@ -1268,7 +1435,7 @@ __global__ void __launch_bounds__(kBlock) k_bi_spmv(int n, int64_t sw,
     for (int row = blockIdx.x * blockDim.x + threadIdx.x; row < n; row += gridDim.x * blockDim.x) {
         const int64_t base = (int64_t)(row >> 5) * sw + (row & 31);
         const double v = sell_row<false>(base, __ldcs(rlen + row), scol, sval, x,
-                                         __ldcs(diag + row) * x[row]);
+                                         __ldcs(diag + row) * x[row], n, &bs->status);
         y[row] = v;
         a = fmad(w[row], v, a);
         if (mode == kBiW) b = fmad(v, v, b);
@@ -1412,12 +1579,67 @@ inline int fine_blocks(int r0, int r1) {
     return (int)(((int64_t)r1 - (r0 & ~31) + kFineBlock - 1) / kFineBlock);
 }
 inline int64_t fine_nslices(const DevLevel& L) { return ((int64_t)L.n + 31) / 32; }
-template <typename K>
-size_t fine_smem(K kernel, const DevLevel& L, size_t value_bytes) {
-    const size_t bytes = (size_t)L.stage_cap * (sizeof(int32_t) + value_bytes);
+inline size_t fine_smem(const DevLevel& L, size_t value_bytes) {
+    return (size_t)L.stage_cap * (sizeof(int32_t) + value_bytes);
+}
+
+// Launches records of one body as one grid (at most kMaxVBatch records).
+template <typename Body>
+void vbatch_launch(const VRec* const* recs, int n, cudaStream_t s) {
+    VBatch p;
+    p.nrec = n;
+    p.bstart[0] = 0;
+    size_t smem = 0;
+    for (int k = 0; k < n; ++k) {
+        p.grid[k] = recs[k]->grid;
+        p.a[k] = recs[k]->a;
+        p.bstart[k + 1] = p.bstart[k] + recs[k]->grid;
+        smem = std::max(smem, recs[k]->smem);
+    }
     // the 48 KB default covers static and dynamic shared memory together
-    if (bytes > kDefaultDynSmem) raise_dyn_smem(kernel, bytes);
-    return bytes;
+    if (smem > kDefaultDynSmem) raise_dyn_smem(k_batched<Body>, smem);
+    launch_kernel(k_batched<Body>, p.bstart[n], recs[0]->block, smem, s, p);
+}
+
+thread_local std::vector<VRec>* t_vrecord = nullptr;
+thread_local VKey t_vkey;
+
+// One V-cycle launch of `Body`: issued as its own kernel, or, while a V-cycle
+// is being recorded, appended to the record list at the current key.
+template <typename Body>
+void vlaunch(int grid, int block, size_t smem, cudaStream_t s, const VArgs& a) {
+    if (grid <= 0) return;
+    if (t_vrecord) {
+        VRec r;
+        r.launch = &vbatch_launch<Body>;
+        r.grid = grid;
+        r.block = block;
+        r.smem = smem;
+        r.phase = t_vkey.phase;
+        r.level = t_vkey.level;
+        r.step = t_vkey.step++;
+        r.a = a;
+        t_vrecord->push_back(r);
+        return;
+    }
+    if (smem > kDefaultDynSmem) raise_dyn_smem(k_single<Body>, smem);
+    launch_kernel(k_single<Body>, grid, block, smem, s, a);
+}
+
+// arguments shared by the row kernels of a level
+template <typename T>
+VArgs level_args(const DevLevel& L, const LevelArrays<T>& A) {
+    VArgs a;
+    a.n = L.n;
+    a.sw = L.sw;
+    a.width = L.width;
+    a.nslices = fine_nslices(L);
+    a.cap = L.stage_cap;
+    a.rlen = L.rlen;
+    a.scol = L.scol;
+    a.sval = A.sval;
+    a.err = L.err;
+    return a;
 }
 
 // r_in / isq (fine level only): form b = r * isq in the first pass (the
@@ -1429,21 +1651,39 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
     const int c1 = L.cptr[1], c2 = L.cptr[std::min(2, L.ncolours)];
     if (L.lpr == kFine) {
         const int nb = r_in ? L.n : c1;
-        launch_kernel(k_fine_first0<T>, std::max(1, blocks_for(std::max(nb, nc))), kBlock, 0, s, c1,
-                      nb, A.dinv, const_cast<T*>(b), x, bc_zero, nc, r_in, isq);
+        VArgs f;
+        f.r1 = c1;
+        f.n = nb;
+        f.nc = nc;
+        f.dv = A.dinv;
+        f.b = b;
+        f.x = x;
+        f.out = bc_zero;
+        f.rin = r_in;
+        f.isq = isq;
+        vlaunch<FineFirst0Body<T>>(std::max(1, blocks_for(std::max(nb, nc))), kBlock, 0, s, f);
         if (c2 > c1) {
-            auto k = k_fine_pass<T>;
-            launch_kernel(k, fine_blocks(c1, c2), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, c2,
-                          c1, L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.dinv, b, x,
-                          (double*)nullptr, (const double*)nullptr, L.err);
+            VArgs a = level_args<T>(L, A);
+            a.r0 = c1;
+            a.r1 = c2;
+            a.jmax = c1;
+            a.dv = A.dinv;
+            a.b = b;
+            a.x = x;
+            vlaunch<FinePassBody<T>>(fine_blocks(c1, c2), kFineBlock, fine_smem(L, sizeof(T)), s, a);
         }
         return;
     }
     if (r_in) throw Error{AMG_EINVAL, "the fused float32 entry needs the fine-level kernels"};
+    VArgs a = level_args<T>(L, A);
+    a.r1 = c2;
+    a.jmax = c1;
+    a.dv = A.dinv;
+    a.b = b;
+    a.x = x;
     AMG_LPR_DISPATCH(launch_lpr(L, c2),
-                     (launch_kernel(k_first<LPR, T>, std::max(1, row_blocks(0, c2, LPR, L.block)),
-                                    L.block, 0, s, c1, c2, L.sw, L.rlen, L.scol, A.sval, A.dinv, b,
-                                    x)));
+                     (vlaunch<FirstBody<LPR, T>>(std::max(1, row_blocks(0, c2, LPR, L.block)), L.block,
+                                                 0, s, a)));
 }
 
 // z_out / isq (fine level only): also write z = x * isq in float64 for the
@@ -1454,17 +1694,22 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, cudaStrea
     const LevelArrays<T> A(L);
     const int r0 = L.cptr[col], r1 = L.cptr[col + 1];
     if (r1 <= r0) return;
+    VArgs a = level_args<T>(L, A);
+    a.r0 = r0;
+    a.r1 = r1;
+    a.jmax = jmax;
+    a.dv = A.dinv;
+    a.b = b;
+    a.x = x;
     if (L.lpr == kFine) {
-        auto k = k_fine_pass<T>;
-        launch_kernel(k, fine_blocks(r0, r1), kFineBlock, fine_smem(k, L, sizeof(T)), s, r0, r1, jmax,
-                      L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.dinv, b, x, z_out, isq,
-                      L.err);
+        a.z = z_out;
+        a.isq = isq;
+        vlaunch<FinePassBody<T>>(fine_blocks(r0, r1), kFineBlock, fine_smem(L, sizeof(T)), s, a);
         return;
     }
     if (z_out) throw Error{AMG_EINVAL, "the fused float32 exit needs the fine-level kernels"};
     AMG_LPR_DISPATCH(launch_lpr(L, r1 - r0),
-                     (launch_kernel(k_gs_pass<LPR, T>, row_blocks(r0, r1, LPR, L.block), L.block, 0,
-                                    s, r0, r1, jmax, L.sw, L.rlen, L.scol, A.sval, A.dinv, b, x)));
+                     (vlaunch<PassBody<LPR, T>>(row_blocks(r0, r1, LPR, L.block), L.block, 0, s, a)));
 }
 
 template <typename T>
@@ -1473,29 +1718,42 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
     const LevelArrays<T> A(L);
     const int c1 = L.cptr[1];
     constexpr bool SC = std::is_same<T, float>::value;
+    VArgs a = level_args<T>(L, A);
+    a.r0 = c1;
+    a.r1 = L.n;
+    a.dv = A.diag;
+    a.b = b;
+    a.x = const_cast<T*>(x);
     if (L.fused_restrict) {
         if (L.n > c1) {
-            auto k = k_fine_residual_restrict<T, SC>;
-            launch_kernel(k, fine_blocks(c1, L.n), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
-                          L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.diag, b, x, L.agg,
-                          A.t, bc, L.err);
+            a.idx = L.agg;
+            a.t = A.t;
+            a.out = bc;
+            vlaunch<FineResRestrictBody<T, SC>>(fine_blocks(c1, L.n), kFineBlock,
+                                                fine_smem(L, sizeof(T)), s, a);
         }
         return;
     }
     if (L.n > c1) {
+        a.out = r;
         if (L.lpr == kFine) {
-            auto k = k_fine_residual<T>;
-            launch_kernel(k, fine_blocks(c1, L.n), kFineBlock, fine_smem(k, L, sizeof(T)), s, c1, L.n,
-                          L.width, fine_nslices(L), L.stage_cap, L.rlen, L.scol, A.sval, A.diag, b, x, r, L.err);
+            vlaunch<FineResidualBody<T>>(fine_blocks(c1, L.n), kFineBlock, fine_smem(L, sizeof(T)), s, a);
         } else {
             AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1),
-                             (launch_kernel(k_residual<LPR, T>, row_blocks(c1, L.n, LPR, L.block),
-                                            L.block, 0, s, c1, L.n, L.sw, L.rlen, L.scol, A.sval,
-                                            A.diag, b, x, r)));
+                             (vlaunch<ResidualBody<LPR, T>>(row_blocks(c1, L.n, LPR, L.block), L.block,
+                                                            0, s, a)));
         }
     }
-    launch_kernel(k_restrict<T, SC>, blocks_for(L.n_coarse), kBlock, 0, s, L.n_coarse, L.rptr,
-                  L.ridx, A.t, r, bc);
+    VArgs q;
+    q.n = L.n;
+    q.err = L.err;
+    q.nc = L.n_coarse;
+    q.idx = L.rptr;
+    q.idx2 = L.ridx;
+    q.t = A.t;
+    q.b = r;
+    q.out = bc;
+    vlaunch<RestrictBody<T, SC>>(blocks_for(L.n_coarse), kBlock, 0, s, q);
 }
 
 template <typename T>
@@ -1504,7 +1762,17 @@ void prolong_impl(const DevLevel& L, const T* e, T* x, double omega, cudaStream_
     const int r0 = L.cptr[1];
     if (L.n <= r0) return;
     constexpr bool SC = std::is_same<T, float>::value;
-    launch_kernel(k_prolong<T, SC>, blocks_for(L.n - r0), kBlock, 0, s, r0, L.n, L.agg, A.t, e, x, (T)omega);
+    VArgs a;
+    a.r0 = r0;
+    a.r1 = L.n;
+    a.nc = L.n_coarse;
+    a.err = L.err;
+    a.idx = L.agg;
+    a.t = A.t;
+    a.b = e;
+    a.x = x;
+    a.omega = (double)(T)omega;
+    vlaunch<ProlongBody<T, SC>>(blocks_for(L.n - r0), kBlock, 0, s, a);
 }
 
 template <int LPR, typename T>
@@ -1523,7 +1791,7 @@ void sweep_launch(const DevLevel& L, const SweepPlan& P, const T* sval, const T*
         cudaLaunchKernelEx(&cfg, k_sweep<LPR, T>, P.npass, (const SweepPass*)P.pass, P.items,
                            (const int32_t*)P.dep_ptr, (const int32_t*)P.dep, P.flag, P.done,
                            P.arrive, P.failed, L.sw, (const uint16_t*)L.rlen,
-                           (const int32_t*)L.scol, sval, dinv, b, x, L.err);
+                           (const int32_t*)L.scol, sval, dinv, b, x, L.err, L.n);
     if (e != cudaSuccess) {
         cudaGetLastError();
         throw Error{AMG_ECUDA, std::string("sweep launch (grid ") + std::to_string(P.grid) +
@@ -1604,10 +1872,13 @@ void launch_prolong32(const DevLevel& L, const float* e, float* x, double omega,
 
 template <typename TB>
 void dense_gemv_impl(int n, const double* M, const TB* b, TB* x, cudaStream_t s) {
-    auto k = k_dense_gemv<TB>;
     const size_t smem = std::is_same<TB, double>::value ? 0 : sizeof(double) * (size_t)n;
-    if (smem > kDefaultDynSmem) raise_dyn_smem(k, smem);
-    launch_kernel(k, blocks_for((int64_t)n * 32), kBlock, smem, s, n, M, b, x);
+    VArgs a;
+    a.n = n;
+    a.dv = M;
+    a.b = b;
+    a.x = x;
+    vlaunch<GemvBody<TB>>(blocks_for((int64_t)n * 32), kBlock, smem, s, a);
 }
 
 void launch_dense_gemv(int n, const double* M, const double* b, double* x, cudaStream_t s) {
@@ -1618,6 +1889,13 @@ void launch_dense_gemv32(int n, const double* M, const float* b, float* x, cudaS
     dense_gemv_impl<float>(n, M, b, x, s);
 }
 
+void launch_vrecords(const VRec* const* recs, int n, cudaStream_t s) {
+    for (int k0 = 0; k0 < n; k0 += kMaxVBatch) {
+        const int m = std::min(kMaxVBatch, n - k0);
+        recs[k0]->launch(recs + k0, m, s);
+    }
+}
+
 void launch_cg_continue(cudaGraphConditionalHandle h, PcgScalars* sc, cudaStream_t s) {
     k_cg_continue<<<1, 1, 0, s>>>(h, sc);
     AMG_CUDA_TRY(cudaGetLastError());
@@ -1626,7 +1904,13 @@ void launch_cg_continue(cudaGraphConditionalHandle h, PcgScalars* sc, cudaStream
 void launch_dense_gemv_f32(int n, int ld, const float* M, const float* b, float* x, cudaStream_t s) {
     if ((reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(M)) & 15 || ld % 4 || ld < n)
         throw Error{AMG_EINVAL, "float32 coarsest solve: operands must be 16-byte aligned"};
-    launch_kernel(k_dense_gemv_f32, blocks_for((int64_t)n * 32), kBlock, 0, s, n, ld, M, b, x);
+    VArgs a;
+    a.n = n;
+    a.ld = ld;
+    a.dv = M;
+    a.b = b;
+    a.x = x;
+    vlaunch<GemvF32Body>(blocks_for((int64_t)n * 32), kBlock, 0, s, a);
 }
 
 void launch_gather(int n, const int32_t* idx, const double* x, double* y, cudaStream_t s) {
@@ -1638,11 +1922,21 @@ void launch_scatter(int n, const int32_t* idx, const double* x, double* y, cudaS
 }
 
 void launch_to_scaled32(int n, const double* r, const double* isq, float* rhat, cudaStream_t s) {
-    launch_kernel(k_to_scaled32, blocks_for(n), kBlock, 0, s, n, r, isq, rhat);
+    VArgs a;
+    a.n = n;
+    a.rin = r;
+    a.isq = isq;
+    a.x = rhat;
+    vlaunch<ToScaledBody>(blocks_for(n), kBlock, 0, s, a);
 }
 
 void launch_from_scaled32(int n, const float* zhat, const double* isq, double* z, cudaStream_t s) {
-    launch_kernel(k_from_scaled32, blocks_for(n), kBlock, 0, s, n, zhat, isq, z);
+    VArgs a;
+    a.n = n;
+    a.b = zhat;
+    a.isq = isq;
+    a.z = z;
+    vlaunch<FromScaledBody>(blocks_for(n), kBlock, 0, s, a);
 }
 
 void launch_cg_residual(const DevLevel& L, const double* b, const double* x, double* r,

@@ -8,16 +8,25 @@
 //               request's own stream) and replaces the estimate by the bytes
 //               the hierarchy actually holds;
 //   running  -> the scheduling thread uploads b, starts the CG and then
-//               advances it one step at a time (pcg_async_step), for every
-//               running request in turn, never blocking on any of them: the
-//               iterations of all in-flight solves are in the device queues
-//               together and overlap there;
+//               advances it one step at a time, for every running request in
+//               turn, never blocking on any of them.  With batch_vcycles (the
+//               default) every scheduler tick collects the requests whose
+//               next step needs a preconditioner application and runs their
+//               V-cycles together, level by level: each step of the V-cycle
+//               (a colour pass, a residual, a restriction, a prolongation, a
+//               coarsest solve) is one launch over all those requests
+//               (batched_precondition), ordered after each request's previous
+//               work by events, and each request's CG vector work follows on
+//               its own stream.  Without it each request issues its own
+//               launches (pcg_async_step), which overlap in the device queues;
 //   draining -> the solution is copied back to pinned host memory;
 //   done     -> the context is freed (stream-ordered, no device-wide
 //               synchronisation), the slot and memory go to the next queued
 //               request, and amg_poll hands the result out.
-// A request runs exactly the launches amg_setup + amg_pcg_solve issue for it
-// alone, so its result does not depend on what else is in flight.
+// A request's rows are computed by exactly the kernel bodies amg_setup +
+// amg_pcg_solve use for it alone (a batched launch runs each request's
+// segment as its own launch would), so its result does not depend on what
+// else is in flight.
 
 #include <algorithm>
 #include <atomic>
@@ -62,6 +71,7 @@ struct Request {
     amg_ctx* ctx = nullptr;
     double* pin = nullptr;     // pinned staging of b, then of x
     double hbm = 0.0;          // bytes reserved against the budget
+    bool batch_failed = false; // its batched V-cycle could not be issued
     Clock::time_point t_submit, t_admit, t_ready, t_done;
 };
 
@@ -70,11 +80,16 @@ struct Request {
 struct amg_server {
     amg_server_params p{};
     int device = 0;
+    cudaStream_t batch_stream = nullptr;   // the batched V-cycles
+    cudaEvent_t batch_ev = nullptr;        // the last batched V-cycle has been issued
     std::mutex mu;
     std::condition_variable cv_worker, cv_setup;
     std::deque<Request*> queued, setup_q, ready_q;
     std::unordered_map<uint64_t, std::unique_ptr<Request>> reqs;
     std::vector<Request*> running;   // owned by the scheduling thread
+    std::vector<Request*> want;      // this tick: requests whose next step needs z = B r
+    std::vector<int> want_first;     // ... and whether it is their first direction
+    int64_t batches = 0, batched_requests = 0;
     bool stopping = false;
     double budget = 0.0, reserved = 0.0;
     int admitted = 0;                // requests in setup or running
@@ -178,6 +193,60 @@ void setup_main(amg_server* S) {
     }
 }
 
+bool batched(const amg_server* S) { return S->p.batch_vcycles && !S->p.params.device_loop; }
+
+// Issue the tick's batched V-cycle for the collected requests, each ordered
+// after its own stream's work, then each request's rest of the iteration on
+// its own stream after the batch.  Requests whose levels run sweep kernels
+// (cooperative launches) precondition on their own streams.
+void run_batch(amg_server* S, bool& progress) {
+    std::vector<Request*>& w = S->want;
+    if (w.empty()) return;
+    progress = true;
+    std::vector<amg_ctx*> cs;
+    std::vector<size_t> own;
+    for (size_t k = 0; k < w.size(); ++k) {
+        amg_ctx* c = w[k]->ctx;
+        bool ok = true;
+        for (const DevLevel& L : c->dl) ok = ok && !L.sweep;
+        if (!ok) own.push_back(k);
+        else cs.push_back(c);
+    }
+    if (cs.size() == 1) {
+        // a batch of one: its own launches on its own stream (the same bodies,
+        // no cross-stream events)
+        for (size_t k = 0; k < w.size(); ++k)
+            if (w[k]->ctx == cs[0]) own.push_back(k);
+        cs.clear();
+    }
+    for (amg_ctx* c : cs) {
+        AMG_CUDA_TRY(cudaEventRecord(c->acg.ev, c->stream));
+        AMG_CUDA_TRY(cudaStreamWaitEvent(S->batch_stream, c->acg.ev, 0));
+    }
+    if (!cs.empty()) {
+        t_launch_overlap = S->p.params.launch_overlap != 0;
+        batched_precondition(cs.data(), (int)cs.size(), S->batch_stream);
+        AMG_CUDA_TRY(cudaEventRecord(S->batch_ev, S->batch_stream));
+    }
+    for (size_t k = 0; k < w.size(); ++k) {
+        amg_ctx* c = w[k]->ctx;
+        const bool mine = std::find(own.begin(), own.end(), k) != own.end();
+        if (mine) {
+            t_launch_overlap = c->p.launch_overlap != 0;
+            precondition_context(c);
+        } else {
+            AMG_CUDA_TRY(cudaStreamWaitEvent(c->stream, S->batch_ev, 0));
+        }
+        pcg_async_resume(c, S->want_first[k] != 0);
+    }
+    if (!cs.empty()) {
+        S->batches += 1;
+        S->batched_requests += (int64_t)cs.size();
+    }
+    w.clear();
+    S->want_first.clear();
+}
+
 // Advance one running request; returns true when it has left the device.
 // `progress` is set when anything was issued or completed.
 bool drive(amg_server* S, Request* r, bool& progress) {
@@ -198,7 +267,19 @@ bool drive(amg_server* S, Request* r, bool& progress) {
                 return false;
             }
             case Request::kSolving: {
-                const int st = pcg_async_step(c);
+                int st;
+                if (batched(S)) {
+                    bool first = false;
+                    st = pcg_async_poll(c, &first);
+                    if (st == 3) {
+                        // next step needs z = B r: join this tick's batch
+                        S->want.push_back(r);
+                        S->want_first.push_back(first ? 1 : 0);
+                        return false;
+                    }
+                } else {
+                    st = pcg_async_step(c);
+                }
                 if (st == 0) return false;
                 progress = true;
                 if (st == 2) {
@@ -212,6 +293,7 @@ bool drive(amg_server* S, Request* r, bool& progress) {
                 return false;
             }
             case Request::kDraining: {
+                if (r->batch_failed) break;
                 const cudaError_t q = cudaEventQuery(c->acg.ev);
                 if (q == cudaErrorNotReady) return false;
                 AMG_CUDA_TRY(q);
@@ -266,6 +348,19 @@ void worker_main(amg_server* S) {
             if (drive(S, run[i], progress)) run.erase(run.begin() + (long)i);
             else ++i;
         }
+        try {
+            run_batch(S, progress);
+        } catch (const Error& e) {
+            // a failed batch fails its requests (their contexts are freed on the next drive)
+            for (Request* r : S->want) {
+                r->status = e.code;
+                r->error = e.msg;
+                r->state = Request::kDraining;
+                r->batch_failed = true;
+            }
+            S->want.clear();
+            S->want_first.clear();
+        }
         if (progress) {
             idle = 0;
         } else if (++idle > 2000) {
@@ -314,6 +409,7 @@ int amg_server_params_default(amg_server_params* p, int32_t dim) {
     p->setup_threads = 4;
     p->maxit = 500;
     p->hbm_budget_bytes = 0.0;
+    p->batch_vcycles = 1;
     return AMG_OK;
 }
 
@@ -323,12 +419,16 @@ int amg_server_create(const amg_server_params* p, amg_server** out) {
         *out = nullptr;
         if (p->max_slots < 1 || p->setup_threads < 1 || p->setup_threads > 256 || p->maxit < 0)
             throw Error{AMG_EINVAL, "max_slots >= 1, 1 <= setup_threads <= 256 and maxit >= 0"};
+        if (p->batch_vcycles != 0 && p->batch_vcycles != 1)
+            throw Error{AMG_EINVAL, "batch_vcycles must be 0 or 1"};
         auto S = std::make_unique<amg_server>();
         S->p = *p;
         AMG_CUDA_TRY(cudaGetDevice(&S->device));
         size_t free_b = 0, total_b = 0;
         AMG_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
         S->budget = p->hbm_budget_bytes > 0 ? p->hbm_budget_bytes : 0.8 * (double)free_b;
+        AMG_CUDA_TRY(cudaStreamCreateWithFlags(&S->batch_stream, cudaStreamNonBlocking));
+        AMG_CUDA_TRY(cudaEventCreateWithFlags(&S->batch_ev, cudaEventDisableTiming));
         amg_server* s = S.get();
         s->worker = std::thread(worker_main, s);
         for (int i = 0; i < p->setup_threads; ++i) s->setup_pool.emplace_back(setup_main, s);
@@ -412,6 +512,8 @@ int amg_server_stats_read(amg_server* s, amg_server_stats* out) {
     out->peak_running = s->peak_running;
     out->hbm_reserved_bytes = s->reserved;
     out->hbm_budget_bytes = s->budget;
+    out->batched_vcycles = s->batches;
+    out->batched_requests = s->batched_requests;
     return AMG_OK;
 }
 
@@ -432,6 +534,11 @@ int amg_server_destroy(amg_server* s) {
     for (auto& t : s->setup_pool) t.join();
     s->cv_worker.notify_all();
     if (s->worker.joinable()) s->worker.join();
+    if (s->batch_stream) {
+        cudaStreamSynchronize(s->batch_stream);
+        cudaStreamDestroy(s->batch_stream);
+    }
+    if (s->batch_ev) cudaEventDestroy(s->batch_ev);
     delete s;
     return AMG_OK;
 }

@@ -287,6 +287,13 @@ inline void k_coarsest(amg_ctx* c, const float* b, float* x) {
     else launch_dense_gemv32(c->nL, c->Ainv_s, b, x, c->stream);
 }
 
+// Position of the next V-cycle launches, for merging the recorded V-cycles
+// of several contexts step by step (see VRec): descent of level l (0, l,
+// step), ascent (1, 64 - l, step); within a level the first passes take steps
+// 0-1, forward colour c step 2 + c, backward colour c step 100 + (C - 2 - c),
+// residual and restriction 200-201, prolongation 0 of the ascent.
+inline void vkey(int phase, int level, int step) { t_vkey = VKey{phase, level, step}; }
+
 template <typename T>
 void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     using P = Prec<T>;
@@ -298,6 +305,7 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     if (l == nlev - 1) {
         const double mb = (vb == 4 && c->Ainv_s32) ? 4.0 : 8.0;
         ProfScope ps(c, kKCoarseSolve, (double)c->nL * c->nL * mb + 2.0 * vb * c->nL);
+        vkey(0, l, 0);
         k_coarsest(c, b, x);
         return;
     }
@@ -314,24 +322,29 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     } else {
         {
             ProfScope ps(c, l == 0 ? kKFirstL0 : kKGsCoarse, first_bytes(L, vb));
+            vkey(0, l, 0);
             k_first(L, b, x, L.fused_restrict ? P::b(N) : (T*)nullptr, N.n, s);
         }
         for (int col = 2; col < C; ++col) {
             ProfScope ps(c, kind, pass_bytes(L, col, L.cptr[col], vb));
+            vkey(0, l, 2 + col);
             k_pass(L, col, L.cptr[col], b, x, s);
         }
         for (int col = C - 2; col >= 0; --col) {
             ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+            vkey(0, l, 100 + (C - 2 - col));
             k_pass(L, col, L.n, b, x, s);
         }
     }
     {
         ProfScope ps(c, l == 0 ? kKResidualL0 : kKResidualCoarse, residual_restrict_bytes(L, vb, scaled));
+        vkey(0, l, 200);
         k_resres(L, b, x, P::r(L), P::b(N), s);
     }
     vcycle<T>(c, l + 1, P::b(N), P::x(N));
     {
         ProfScope ps(c, kKProlong, prolong_bytes(L, vb, scaled));
+        vkey(1, 64 - l, 0);
         k_prolong(L, P::x(N), x, c->p.omega, s);
     }
     if (L.sweep) {
@@ -345,10 +358,12 @@ void vcycle(amg_ctx* c, int l, const T* b, T* x) {
     }
     for (int col = 0; col < C; ++col) {
         ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+        vkey(1, 64 - l, 2 + col);
         k_pass(L, col, L.n, b, x, s);
     }
     for (int col = C - 2; col >= 0; --col) {
         ProfScope ps(c, kind, pass_bytes(L, col, L.n, vb));
+        vkey(1, 64 - l, 100 + (C - 2 - col));
         k_pass(L, col, L.n, b, x, s);
     }
 }
@@ -370,34 +385,41 @@ void vcycle32_fused(amg_ctx* c, const double* r, double* z) {
     float* x = L.x32;
     {
         ProfScope ps(c, kKFirstL0, first_bytes(L, 4) + 12.0 * L.n);
+        vkey(0, 0, 0);
         launch_first32_from64(L, r, isq, b, x, L.fused_restrict ? N.b32 : nullptr, N.n, s);
     }
     for (int col = 2; col < C; ++col) {
         ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.cptr[col], 4));
+        vkey(0, 0, 2 + col);
         launch_pass32(L, col, L.cptr[col], b, x, s);
     }
     for (int col = C - 2; col >= 0; --col) {
         ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.n, 4));
+        vkey(0, 0, 100 + (C - 2 - col));
         launch_pass32(L, col, L.n, b, x, s);
     }
     {
         ProfScope ps(c, kKResidualL0, residual_restrict_bytes(L, 4, true));
+        vkey(0, 0, 200);
         launch_residual_restrict32(L, b, x, L.r32, N.b32, s);
     }
     vcycle32(c, 1, N.b32, N.x32);
     {
         ProfScope ps(c, kKProlong, prolong_bytes(L, 4, true));
+        vkey(1, 64, 0);
         launch_prolong32(L, N.x32, x, c->p.omega, s);
     }
     // the last pass over each colour also writes z
     for (int col = 0; col < C; ++col) {
         const bool last = col == C - 1;
         ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.n, 4) + (last ? 16.0 * (L.cptr[col + 1] - L.cptr[col]) : 0.0));
+        vkey(1, 64, 2 + col);
         if (last) launch_pass32_to64(L, col, L.n, b, x, z, isq, s);
         else launch_pass32(L, col, L.n, b, x, s);
     }
     for (int col = C - 2; col >= 0; --col) {
         ProfScope ps(c, kKGsL0, pass_bytes(L, col, L.n, 4) + 16.0 * (L.cptr[col + 1] - L.cptr[col]));
+        vkey(1, 64, 100 + (C - 2 - col));
         launch_pass32_to64(L, col, L.n, b, x, z, isq, s);
     }
 }
@@ -413,11 +435,13 @@ void precondition(amg_ctx* c, const double* r, double* z) {
         DevLevel& L0 = c->dl[0];
         {
             ProfScope ps(c, kKConvert, 20.0 * L0.n);
+            vkey(-1, 0, 0);
             launch_to_scaled32(L0.n, r, c->isq0, L0.b32, c->stream);
         }
         vcycle32(c, 0, L0.b32, L0.x32);
         {
             ProfScope ps(c, kKConvert, 20.0 * L0.n);
+            vkey(2, 0, 0);
             launch_from_scaled32(L0.n, L0.x32, c->isq0, z, c->stream);
         }
     }
@@ -489,6 +513,7 @@ void drop_graphs(amg_ctx* c) {
             c->graph_a[a][b] = c->graph_b[a][b] = c->graph_solve[a][b] = nullptr;
             c->solve_graph_state[a][b] = 0;
         }
+        c->vrec_ok[a] = false;
         if (c->graph_bi[a]) cudaGraphExecDestroy(c->graph_bi[a]);
         c->graph_bi[a] = nullptr;
         c->bi_graph_state[a] = 0;
@@ -1003,7 +1028,7 @@ int pcg(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info) {
     cudaStream_t s = c->stream;
     cg_start(c, tol, maxit);
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
-    int status = AMG_OK;
+    int status = c->sc_host->status != 0 ? c->sc_host->status : AMG_OK;
     c->last_device_loop = 0;
     cudaGraphExec_t loop = (!c->sc_host->done && maxit > 0) ? solve_graph(c) : nullptr;
     if (loop) {
@@ -1153,8 +1178,10 @@ int bicgstab(amg_ctx* c, double tol, int32_t maxit, amg_solve_info* info, std::s
     const int status = h.status ? h.status : AMG_OK;
     if (status != AMG_OK) {
         static const char* kWhy[] = {"maximum iterations reached", "BiCGSTAB breakdown: rt.r = 0",
-                                     "BiCGSTAB breakdown: rt.v = 0", "BiCGSTAB breakdown: t.t = 0"};
-        why = kWhy[std::min(std::max(h.why, 0), 3)];
+                                     "BiCGSTAB breakdown: rt.v = 0", "BiCGSTAB breakdown: t.t = 0",
+                                     "a dot product of the iteration is not finite"};
+        why = status == AMG_ERANGE ? "a kernel met an index outside its range (checked build)"
+                                   : kWhy[std::min(std::max(h.why, 0), 4)];
     }
     if (info) {
         cg_true_residual(c);
@@ -1214,6 +1241,7 @@ int pcg_async_step(amg_ctx* c) {
     const PcgScalars& h = *c->sc_host;
     switch (a.state) {
         case AsyncCg::kStarted:
+            if (h.status != 0) { async_finish(c, h.status); break; }
             if (h.done) { async_finish(c, AMG_OK); break; }
             if (cudaGraphExec_t loop = a.maxit > 0 ? solve_graph(c) : nullptr) {
                 // the whole iteration loop on the device; one more wait for this solve
@@ -1253,6 +1281,127 @@ int pcg_async_step(amg_ctx* c) {
     }
     AMG_CUDA_TRY(cudaGetLastError());
     return 1;
+}
+
+// ---------------------------------------------------------------------------
+// the V-cycles of several contexts, batched step by step
+// ---------------------------------------------------------------------------
+
+// The V-cycle of the context's precision on its level-0 vectors (z = B r for
+// c->r, c->z) as launch records, recorded once per precision and launch
+// shapes.  nullptr when a level runs its sweeps as dependency-driven kernels
+// (cooperative launches, which do not batch).
+const std::vector<VRec>* vcycle_records(amg_ctx* c) {
+    const int pr = c->precision;
+    if (!c->vrec_ok[pr]) {
+        for (const DevLevel& L : c->dl)
+            if (L.sweep) return nullptr;
+        std::vector<VRec>& rec = c->vrec[pr];
+        rec.clear();
+        const bool prof = c->prof.on;
+        c->prof.on = false;
+        t_vrecord = &rec;
+        try {
+            precondition(c, c->r, c->z);
+        } catch (...) {
+            t_vrecord = nullptr;
+            c->prof.on = prof;
+            throw;
+        }
+        t_vrecord = nullptr;
+        c->prof.on = prof;
+        c->vrec_ok[pr] = true;
+    }
+    return &c->vrec[pr];
+}
+
+void precondition_context(amg_ctx* c) { precondition(c, c->r, c->z); }
+
+void batched_precondition(amg_ctx* const* cs, int n, cudaStream_t s) {
+    std::vector<const VRec*> all;
+    for (int k = 0; k < n; ++k) {
+        const std::vector<VRec>* r = vcycle_records(cs[k]);
+        if (!r) throw Error{AMG_EINVAL, "a context with sweep kernels cannot join a batched V-cycle"};
+        for (const VRec& v : *r) all.push_back(&v);
+    }
+    // each context's keys increase along its V-cycle, so a stable merge by key
+    // keeps every context's order; equal keys are independent steps of
+    // different contexts
+    auto key = [](const VRec* a) { return std::make_tuple(a->phase, a->level, a->step); };
+    std::stable_sort(all.begin(), all.end(), [&](const VRec* a, const VRec* b) { return key(a) < key(b); });
+    auto body = [](const VRec* a) { return std::make_pair(reinterpret_cast<uintptr_t>(a->launch), a->block); };
+    size_t i = 0;
+    while (i < all.size()) {
+        size_t j = i;
+        while (j < all.size() && key(all[j]) == key(all[i])) ++j;
+        std::stable_sort(all.begin() + (long)i, all.begin() + (long)j,
+                         [&](const VRec* a, const VRec* b) { return body(a) < body(b); });
+        for (size_t k = i; k < j;) {
+            size_t m = k;
+            while (m < j && body(all[m]) == body(all[k])) ++m;
+            launch_vrecords(&all[k], (int)(m - k), s);
+            k = m;
+        }
+        i = j;
+    }
+    AMG_CUDA_TRY(cudaGetLastError());
+}
+
+// The same stepping split around the preconditioner, for a scheduler that
+// applies it to several contexts at once: poll returns 0 (busy), 1 (issued
+// the end of the solve), 2 (finished) or 3 when the next step needs
+// z = B r on c->r (first: the first direction); the caller issues it after
+// the context stream's work and then calls resume, which issues the rest of
+// the iteration exactly as pcg_async_step does.
+int pcg_async_poll(amg_ctx* c, bool* first) {
+    AsyncCg& a = c->acg;
+    if (a.state == AsyncCg::kDone) return 2;
+    if (a.state == AsyncCg::kIdle) throw Error{AMG_EINVAL, "no solve in progress"};
+    const cudaError_t q = cudaEventQuery(a.ev);
+    if (q == cudaErrorNotReady) return 0;
+    AMG_CUDA_TRY(q);
+    t_launch_overlap = c->p.launch_overlap != 0;
+    const PcgScalars& h = *c->sc_host;
+    switch (a.state) {
+        case AsyncCg::kStarted:
+            c->last_device_loop = 0;
+            if (h.status != 0) { async_finish(c, h.status); return 1; }
+            if (h.done) { async_finish(c, AMG_OK); return 1; }
+            if (h.iters >= a.maxit) { async_finish(c, AMG_ENOTCONV); return 1; }
+            *first = true;
+            return 3;
+        case AsyncCg::kIterating:
+            if (h.status != 0) { async_finish(c, h.status); return 1; }
+            if (h.done) { async_finish(c, AMG_OK); return 1; }
+            if (h.iters >= a.maxit) { async_finish(c, AMG_ENOTCONV); return 1; }
+            *first = false;
+            return 3;
+        case AsyncCg::kFinishing:
+            cg_fill_info(c, a.status, *a.rr_host, &a.info);
+            a.state = AsyncCg::kDone;
+            return 2;
+        default:
+            throw Error{AMG_EINVAL, "the device-side loop does not step"};
+    }
+}
+
+void pcg_async_resume(amg_ctx* c, bool first) {
+    AsyncCg& a = c->acg;
+    t_launch_overlap = c->p.launch_overlap != 0;
+    const int n = c->dl[0].n;
+    cudaStream_t s = c->stream;
+    if (first) {
+        launch_cg_rz(n, c->r, c->z, nullptr, c->pv, c->work, kRho0, s);
+        if (c->flexible)
+            AMG_CUDA_TRY(cudaMemcpyAsync(c->zold, c->z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    } else {
+        launch_cg_rz(n, c->r, c->z, c->zold, c->pv, c->work, c->flexible ? kRZFlex : kRZ, s);
+        launch_cg_p(n, c->z, c->pv, c->flexible ? c->zold : nullptr, c->work, s);
+    }
+    run_part_a(c);
+    AMG_CUDA_TRY(cudaEventRecord(a.ev, s));
+    a.state = AsyncCg::kIterating;
+    AMG_CUDA_TRY(cudaGetLastError());
 }
 
 namespace {
@@ -1676,7 +1825,10 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         if (info) *info = local;
         if (status != AMG_OK && why.empty())
             why = status == AMG_ENOTCONV ? "maximum iterations reached"
-                                         : "p.Ap <= 0: operator or preconditioner not SPD";
+                  : status == AMG_ENONFINITE ? "a dot product of the iteration is not finite"
+                  : status == AMG_ERANGE ? "a kernel met an index outside its range (checked build)"
+                  : status == AMG_ETIMEOUT ? "a bounded device-side wait gave up: free the context"
+                                           : "p.Ap <= 0: operator or preconditioner not SPD";
     });
     if (rc != AMG_OK) return rc;
     if (status != AMG_OK) t_last_error = why;   // after the guard, which clears it on success
@@ -1893,5 +2045,39 @@ int amg_free(amg_ctx* c) {
 }
 
 const char* amg_last_error(void) { return t_last_error.c_str(); }
+
+int amg_device_checks(void) {
+#ifdef AMG_DEVICE_CHECKS
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+int amg_debug_set_column(amg_ctx* c, int32_t l, int32_t row, int32_t k, int32_t col) {
+    return Guard::run([&] {
+#ifndef AMG_DEVICE_CHECKS
+        (void)c, (void)l, (void)row, (void)k, (void)col;
+        throw Error{AMG_EINVAL, "amg_debug_set_column exists in the checked build only"};
+#else
+        if (!c || l < 1 || l >= (int32_t)c->dl.size() - 1)
+            throw Error{AMG_EINVAL, "level out of range (levels 1 .. L-2 have stored rows)"};
+        const DevLevel& L = c->dl[l];
+        if (row < 0 || row >= L.n) throw Error{AMG_EINVAL, "row out of range"};
+        // a column at or beyond the level's rows: skipped by every pass bound,
+        // so no kernel can dereference it
+        if (col < L.n) throw Error{AMG_EINVAL, "col must be >= the level's rows"};
+        const int32_t r = c->hl[l].perm[row];
+        uint16_t rl = 0;
+        AMG_CUDA_TRY(cudaMemcpy(&rl, L.rlen + r, sizeof(uint16_t), cudaMemcpyDeviceToHost));
+        const int32_t len = rl;
+        if (k < 0 || k >= len) throw Error{AMG_EINVAL, "k out of range of the row's entries"};
+        const int64_t e = (int64_t)(r >> 5) * L.sw + 32 * (int64_t)k + (r & 31);
+        AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        AMG_CUDA_TRY(cudaMemcpy(L.scol + e, &col, sizeof(int32_t), cudaMemcpyHostToDevice));
+        drop_graphs(c);
+#endif
+    });
+}
 
 }  // extern "C"

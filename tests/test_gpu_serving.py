@@ -137,3 +137,38 @@ def test_destroy_with_work_in_flight():
     t0 = time.time()
     server.close()            # running requests finish, queued ones are dropped
     assert time.time() - t0 < 60
+
+
+@pytest.mark.parametrize("precision", [amg.AMG_FP32_IN_FP64, amg.AMG_FP64])
+def test_batched_vcycles_give_each_request_its_own_bits(precision):
+    # the scheduler runs the V-cycles of all requests that need one in a tick
+    # as shared launches, level by level; every request still gets exactly the
+    # bits of its standalone solve, and the same bits as without batching
+    reqs = [P.serving_request(k, lo=8, hi=30) for k in range(100, 116)]
+    out = {}
+    for batch in (1, 0):
+        server = amg.Server(dim=3, max_slots=8, setup_threads=4, batch_vcycles=batch,
+                            precision=precision)
+        tickets = [server.submit(p.row_ptr, p.col, p.val, p.b, TOL) for p in reqs]
+        res = _drain(server, tickets)
+        st = server.stats()
+        params = server.params
+        server.close()
+        assert st["completed"] == len(reqs) and st["failed"] == 0
+        if batch:
+            assert st["batched_vcycles"] > 0
+            # several requests shared the launches of a batch on average
+            assert st["batched_requests"] > st["batched_vcycles"]
+        else:
+            assert st["batched_vcycles"] == 0
+        out[batch] = [res[t] for t in tickets]
+    for p, a, b in zip(reqs, out[1], out[0]):
+        assert a[0] == b[0] == amg.AMG_OK
+        assert a[2]["iterations"] == b[2]["iterations"]
+        assert np.array_equal(a[1], b[1]), p.name
+        r = p.b - O.spmv(p.row_ptr, p.col, p.val, a[1])
+        assert np.linalg.norm(r) <= 1.05 * TOL * np.linalg.norm(p.b)
+    for p, a in list(zip(reqs, out[1]))[:4]:
+        rc1, x1, info1 = _standalone(p, params)
+        assert rc1 == amg.AMG_OK and info1["iterations"] == a[2]["iterations"]
+        assert np.array_equal(a[1], x1), p.name

@@ -31,6 +31,30 @@ def test_library_exports_every_declared_symbol():
         assert name in amg._SIGNATURES, f"binding lacks {name}"
 
 
+def test_checked_build_exports_the_same_symbols():
+    # the checked build (device-side index checks) has the same interface;
+    # read with nm so that one process does not load both libraries
+    import shutil
+    import subprocess
+    from paper_1209_0960_gb300 import build as B
+    if shutil.which("nm") is None:
+        pytest.skip("no nm")
+    path = B.build(checked=True)
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True,
+                         check=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in _declared_functions():
+        assert name in syms, name
+    assert amg.lib().amg_device_checks() in (0, 1)
+
+
+def test_debug_column_hook_refused_outside_the_checked_build():
+    if amg.lib().amg_device_checks():
+        pytest.skip("the loaded library is the checked build")
+    assert amg.lib().amg_debug_set_column(None, 1, 0, 0, 10) == amg.AMG_EINVAL
+    assert "checked build" in amg.amg_last_error()
+
+
 def test_params_default_and_errors():
     p = amg.amg_params_default(3)
     assert (p.s_min, p.s_max, p.d_max) == (8, 12, 3)
