@@ -120,7 +120,7 @@ def parse_args():
     ap.add_argument("--host-threads", type=int, default=0,
                     help="host threads per setup for tiled aggregation (0: all host cores)")
     ap.add_argument("--slots", type=int, default=32)
-    ap.add_argument("--batch-vcycles", type=int, choices=[0, 1], default=1,
+    ap.add_argument("--batch-vcycles", type=int, choices=[0, 1], default=0,
                     help="serving: 1 runs the V-cycles of the requests that need one in a "
                          "scheduler tick as shared launches, level by level; 0: each request "
                          "launches its own")

@@ -415,13 +415,14 @@ typedef struct {
     int32_t maxit;            /* CG iteration cap per request; default 500 */
     double hbm_budget_bytes;  /* device memory the admitted requests may reserve;
                                  <= 0: 80 % of the free device memory at creation */
-    int32_t batch_vcycles;    /* 1 (default; with params.device_loop = 0): every scheduler
-                                 tick runs the V-cycles of all requests whose next CG step
-                                 needs one as shared launches, level by level (one launch
-                                 per colour pass, residual, restriction, prolongation and
-                                 coarsest solve over all of them); each request's rows are
-                                 computed exactly as in its own V-cycle.  0: every request
-                                 issues its own launches on its own stream. */
+    int32_t batch_vcycles;    /* 1 (with params.device_loop = 0): every scheduler tick runs
+                                 the V-cycles of all requests whose next CG step needs one
+                                 as shared launches, level by level (one launch per colour
+                                 pass, residual, restriction, prolongation and coarsest
+                                 solve over all of them); each request's rows are computed
+                                 exactly as in its own V-cycle.  0 (default, measured
+                                 faster on the serving stream): every request issues its
+                                 own launches on its own stream. */
 } amg_server_params;
 
 /* Timings of one request (host steady clock, milliseconds). */
@@ -442,7 +443,7 @@ typedef struct {
     int64_t batched_requests;     /* request V-cycles they covered */
 } amg_server_stats;
 
-/* Defaults: params = amg_params_default(dim) with precision
+/* Defaults: batch_vcycles 0; params = amg_params_default(dim) with precision
  * AMG_FP32_IN_FP64 and a coarsening target of 1000 rows (the dense coarsest
  * factorisation is per-request setup work), device_loop 0 (the stepper
  * launches each iteration: measured faster with 32 solves sharing the GPU than
