@@ -29,6 +29,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -147,17 +148,22 @@ def parse_args():
                     help="fixed launch shapes per level instead of tuning (0 = staged "
                          "kernels, else 1/2/4/8 lanes per row, with a suffix h for blocks of "
                          "128 threads and s for one dependency-driven kernel per smoothing "
-                         "sweep, e.g. 0,2h,4hs), for reproducible profiles")
+                         "sweep; staged levels may add cP for a shared-memory carveout of P "
+                         "percent, e.g. 0,0c58,2h,4hs), for reproducible profiles")
     ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
                     help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
     args = ap.parse_args()
     args.lanes = []
     for v in (v.strip() for v in args.lanes_per_row.split(",")):
         if v:
-            lanes = int(v.rstrip("hs"))
-            if "s" in v:
+            m = re.fullmatch(r"(\d+)(h?)(s?)(?:c(\d+))?", v)
+            if not m:
+                ap.error(f"--lanes-per-row: cannot read {v!r}")
+            lanes = int(m.group(1))
+            if m.group(3):
                 lanes |= 0x100   # AMG_SHAPE_SWEEP: one dependency-driven kernel per sweep
-            args.lanes.append((lanes, 128 if "h" in v else 0))
+            carve = int(m.group(4)) if m.group(4) else None
+            args.lanes.append((lanes, 128 if m.group(2) else 0, carve))
     if args.lanes:
         args.autotune = 0
     if args.aggregation_tile < 0:
@@ -403,8 +409,21 @@ def timed_solves(solver, b, x, steps, tol, stream, dist, maxit):
 
 
 def apply_lanes(solver, args):
-    for l, (lanes, threads) in enumerate(args.lanes):
+    for l, (lanes, threads, carve) in enumerate(args.lanes):
         solver.set_level_shape(l, lanes, threads)
+        if carve is not None:
+            solver.set_level_carveout(l, carve)
+
+
+def shape_string(levels):
+    """The levels' launch shapes in --lanes-per-row syntax."""
+    out = []
+    for lv in levels[:-1]:
+        v = str(lv["lanes_per_row"]) + ("h" if lv["threads_per_block"] == 128 else "")
+        v += "s" if lv["sweep"] else ""
+        v += f"c{lv['carveout']}" if lv["carveout"] >= 0 else ""
+        out.append(v)
+    return ",".join(out)
 
 
 def new_solver(args, p, stream):
@@ -466,7 +485,8 @@ def measure_workload(args, dist, workload, grid, steps, warmup, headline, kernel
             clk = clocks.stop()
         ms = dist.max(ms)
         rc, info = infos[-1]
-        res[tag] = {"ms": ms, "rc": rc, "info": info, "x": x.clone()}
+        res[tag] = {"ms": ms, "rc": rc, "info": info, "x": x.clone(),
+                    "shapes": shape_string(solver.info()[1])}
         # per-kernel records (every launch bracketed by events; host-driven loop)
         solver.profile(1)
         x.zero_()
@@ -490,6 +510,7 @@ def measure_workload(args, dist, workload, grid, steps, warmup, headline, kernel
           "fp32": vcycle_gbs(res["fp32"]["graph"], summary["vcycle_bytes_fp32"], 80.0 * n)}
     kern["summary"] = summary
     kern["levels"] = levels
+    kern["shapes"] = {"fp64": res["fp64"]["shapes"], "fp32": res["fp32"]["shapes"]}
 
     rec = {
         "fp64": {"ms": res["fp64"]["ms"], "iterations": i64["iterations"],
@@ -499,6 +520,7 @@ def measure_workload(args, dist, workload, grid, steps, warmup, headline, kernel
                          "rel_diff_vs_fp64_solution": err32,
                          "speedup_vs_fp64": res["fp64"]["ms"] / res["fp32"]["ms"]},
         "vcycle": vc,
+        "shapes": {"fp64": res["fp64"]["shapes"], "fp32": res["fp32"]["shapes"]},
         "setup": {"total_ms": summary["total_setup_ms"], "host_ms": summary["host_setup_ms"],
                   "aggregation_ms": summary["aggregation_ms"],
                   "gpu_galerkin_ms": summary["gpu_galerkin_ms"], "gpu_other_ms": summary["gpu_other_ms"],
@@ -656,6 +678,7 @@ def run_ours(args, dist: Dist):
         "true_rel_residual": rec["fp64"]["true_rel_residual"],
         "status": {"fp64": rec["fp64"]["status"], "fp32_in_fp64": rec["fp32_in_fp64"]["status"]},
         "vcycle": rec["vcycle"],
+        "shapes": rec["shapes"],
         "fp32_in_fp64": rec["fp32_in_fp64"],
     }
     if dist.rank == 0:

@@ -176,6 +176,17 @@ typedef struct {
                                  lanes_per_row rows, and an item starts as soon as the items
                                  of earlier passes it reads or overwrites have finished;
                                  same arithmetic as one launch per pass */
+    int32_t compact;          /* 1: the staged kernels (lanes_per_row 0) read a copy of the
+                                 level's off-diagonal entries in 32-row slices padded only
+                                 to each slice's longest row; chosen at setup where the
+                                 common width (the level's longest row) pads more than a
+                                 tenth over that.  0: they read the common-width slices */
+    int64_t staged_entries;   /* entries (index + value) that layout holds, padding
+                                 included: one pass over every row stages this many */
+    int32_t carveout;         /* preferred shared-memory carveout of the staged kernels, in
+                                 percent of the SM's maximum shared memory (the rest of the
+                                 unified L1/shared array caches the neighbour gathers);
+                                 -1: the driver's choice */
 } amg_level_info;
 
 typedef struct {
@@ -332,8 +343,10 @@ int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col
 
 /* Launch shape of level l's smoother and residual kernels (0 <= l < number of
  * levels - 1; the coarsest level is the dense solve).  lanes_per_row: 0 = one
- * row per thread with the slices staged in shared memory (levels whose longest
- * row has at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row, optionally
+ * row per thread with the slices staged in shared memory (levels where the
+ * entries of any 8 consecutive 32-row slices, in the layout those kernels read,
+ * take at most 96 KB as index and value: with the padded slices, a longest row
+ * of at most 32 off-diagonals), or 1, 2, 4, 8 lanes per row, optionally
  * or'ed with AMG_SHAPE_SWEEP (levels of at most 2^20 rows that are not
  * two-colour levels with the fused residual): each smoothing sweep then runs
  * as one kernel whose blocks wait, with bounded polls, only for the earlier
@@ -344,8 +357,20 @@ int amg_export_level(const amg_ctx *c, int32_t l, int32_t *row_ptr, int32_t *col
  * same values as the pass-per-launch kernels of its lanes and block size).
  * The CUDA graphs of the context are rebuilt on the next solve.  Errors:
  * AMG_EINVAL (l, lanes_per_row or threads_per_block out of range, 0 lanes on a
- * level with longer rows, a sweep where it is not allowed). */
+ * level whose tile does not fit, a sweep where it is not allowed). */
 int amg_set_level_shape(amg_ctx *c, int32_t l, int32_t lanes_per_row, int32_t threads_per_block);
+
+/* Preferred shared-memory carveout of level l's staged kernels (the level's
+ * shape must have lanes_per_row 0): percent (0 .. 100) of the SM's maximum
+ * shared memory to configure for those launches, the rest of the unified
+ * L1/shared array serving as L1 cache for the neighbour gathers; -1 restores
+ * the driver's choice.  A hint: the driver still configures at least what one
+ * block needs.  Fewer resident blocks and a larger L1 can be faster on levels
+ * whose passes gather many neighbour values; results are identical for every
+ * value.  The autotuner chooses it per level among a few values.  The CUDA
+ * graphs of the context are rebuilt on the next solve.  Errors: AMG_EINVAL (l
+ * or percent out of range, a level without the staged kernels). */
+int amg_set_level_carveout(amg_ctx *c, int32_t l, int32_t percent);
 
 /* Aggregation of one level, exactly as amg_setup runs it (Sec. 2.1): strength
  * of connection (Eq. symmetric_strong1/2) and Algorithm 1 with Algorithms 2

@@ -66,7 +66,8 @@ class amg_level_info(ctypes.Structure):
     _fields_ = [("n", _c_i32), ("nnz", _c_i32), ("n_coarse", _c_i32), ("ncolours", _c_i32),
                 ("max_agg_size", _c_i32), ("n_isolated", _c_i32), ("n_dirichlet", _c_i32),
                 ("vcycle_bytes_fp64", _c_dbl), ("vcycle_bytes_fp32", _c_dbl),
-                ("lanes_per_row", _c_i32), ("threads_per_block", _c_i32), ("sweep", _c_i32)]
+                ("lanes_per_row", _c_i32), ("threads_per_block", _c_i32), ("sweep", _c_i32),
+                ("compact", _c_i32), ("staged_entries", ctypes.c_int64), ("carveout", _c_i32)]
 
 
 class amg_summary(ctypes.Structure):
@@ -128,6 +129,7 @@ _SIGNATURES = {
     "amg_hierarchy_info": ([_c_vp, ctypes.POINTER(amg_summary), ctypes.POINTER(amg_level_info), _c_i32], ctypes.c_int),
     "amg_export_level": ([_c_vp, _c_i32, _c_vp, _c_vp, _c_vp, _c_vp, _c_vp], ctypes.c_int),
     "amg_set_level_shape": ([_c_vp, _c_i32, _c_i32, _c_i32], ctypes.c_int),
+    "amg_set_level_carveout": ([_c_vp, _c_i32, _c_i32], ctypes.c_int),
     "amg_selftest_bounded_wait": ([ctypes.c_int64, _c_vp, ctypes.POINTER(_c_i32),
                                    ctypes.POINTER(_c_dbl)], ctypes.c_int),
     "amg_aggregate": ([ctypes.POINTER(amg_csr), ctypes.POINTER(amg_params), _c_vp, ctypes.POINTER(_c_i32)], ctypes.c_int),
@@ -313,6 +315,10 @@ def amg_set_level_shape(ctx: int, l: int, lanes_per_row: int, threads_per_block:
            "amg_set_level_shape")
 
 
+def amg_set_level_carveout(ctx: int, l: int, percent: int) -> None:
+    _check(lib().amg_set_level_carveout(ctx, l, percent), "amg_set_level_carveout")
+
+
 def amg_export_level(ctx: int, l: int) -> dict:
     _, levels = amg_hierarchy_info(ctx)
     info = levels[l]
@@ -459,6 +465,9 @@ class AMG:
 
     def set_level_shape(self, l: int, lanes_per_row: int, threads_per_block: int = 0) -> None:
         amg_set_level_shape(self.ctx, l, lanes_per_row, threads_per_block)
+
+    def set_level_carveout(self, l: int, percent: int) -> None:
+        amg_set_level_carveout(self.ctx, l, percent)
 
 
 # ---------------------------------------------------------------------------

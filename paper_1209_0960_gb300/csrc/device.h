@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <map>
@@ -23,6 +24,16 @@ struct Error {
 };
 
 void set_last_error(const std::string& msg);
+
+// An NVTX range for the length of a scope: the setup phases, the solves and
+// the server's batches show up named in a profiler's timeline (no cost when
+// no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 #define AMG_CUDA_TRY(expr)                                                          \
     do {                                                                            \
@@ -200,16 +211,15 @@ struct DevLevel {
     int32_t width = 0;                // common slice width W (longest row)
     int64_t sw = 0;                   // slice stride 32 W
     int64_t stage_cap = 0;            // entries a staged block (8 consecutive slices) needs at
-                                      // most when each slice keeps only its longest row's
-                                      // entries: 32 x max over 8-slice windows of the sum of
-                                      // the slices' longest rows
+                                      // most: 256 W, or with per-slice widths 32 x max over
+                                      // 8-slice windows of the sum of the slices' longest rows
     int32_t ncolours = 0;
     int32_t n_coarse = 0;
     std::vector<int32_t> cptr;        // host copy: first row of each colour, [ncolours+1]
     std::vector<int64_t> cnnz;        // host copy: off-diagonal entries of each colour block
     int32_t lpr = 0;                  // lanes per row of the row kernels: 0 = the fine
                                       // level's kernels (one row per thread, slices staged
-                                      // in shared memory, width <= kFineMaxWidth), else
+                                      // in shared memory, tiles within kMaxStageBytes), else
                                       // 1, 2, 4 or 8 lanes with batched gathers
     int32_t block = 256;              // threads per block of the row kernels (lpr >= 1): 256 or 128
     int32_t lpr_wide = 0;             // lanes per row of launches over >= wide_rows rows
@@ -221,6 +231,18 @@ struct DevLevel {
     uint16_t* rlen = nullptr;         // [n] off-diagonal entries per row
     int32_t* scol = nullptr;          // [padded] permuted column indices
     double* sval = nullptr;           // [padded]
+    // sliced layout with per-slice widths, for the staged kernels on levels
+    // whose rows vary in length (null elsewhere): slice s padded only to its
+    // longest row K_s, at soff[s] = 32 (K_0 + ... + K_{s-1}), entry k of lane
+    // i at soff[s] + 32 k + i
+    int64_t* soff = nullptr;          // [nslices + 1]
+    int64_t stage_entries = 0;        // soff[nslices]
+    int32_t carve = -1;               // preferred shared-memory carveout of the staged kernels
+                                      // (percent of the SM's maximum; the rest is L1 for the
+                                      // neighbour gathers), -1: the driver's choice
+    int32_t* ccol = nullptr;
+    double* cval = nullptr;
+    float* cval32 = nullptr;
     double* diag = nullptr;           // [n]
     double* dinv = nullptr;           // [n] 1 / A_ii
     int32_t* agg = nullptr;           // [n] permuted coarse index or -1
@@ -245,9 +267,15 @@ struct DevLevel {
     const SweepPlan* plan_post = nullptr;
 };
 
-// widest slice the fine-level (staged) kernels take: 256 rows x W entries of
-// index and value stay within one block's shared memory
-constexpr int kFineMaxWidth = 32;
+// largest tile of the staged kernels (index and value of the entries of 8
+// consecutive slices): two blocks still fit on an SM.  With the common width
+// that is a longest row of at most 32 off-diagonals.
+constexpr int64_t kMaxStageBytes = 96 * 1024;
+// shared memory of a staged block's tile
+inline int64_t stage_bytes(const DevLevel& L, size_t value_bytes) {
+    return L.stage_cap * (int64_t)(sizeof(int32_t) + value_bytes);
+}
+inline bool staged_fits(const DevLevel& L) { return stage_bytes(L, sizeof(double)) <= kMaxStageBytes; }
 
 // Launch profiler: events around launches, grouped by kernel class.
 struct Profiler {
@@ -330,19 +358,31 @@ void raise_dyn_smem(void (*kernel)(KArgs...), size_t bytes) {
     raise_dyn_smem(reinterpret_cast<const void*>(kernel), bytes);
 }
 
+// carve >= 0: the launch's preferred shared-memory carveout, in percent of
+// the SM's maximum shared memory (the rest of the unified L1/shared array is
+// L1 cache); -1: the driver's choice
 template <typename... KArgs, typename... Args>
-void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
-                   Args&&... args) {
+void launch_kernel_carve(void (*kernel)(KArgs...), int grid, int block, size_t smem, int carve,
+                         cudaStream_t s, Args&&... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)grid);
     cfg.blockDim = dim3((unsigned)block);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[2];
+    unsigned n = 0;
+    if (t_launch_overlap && grid <= g_overlap_max_blocks) {
+        attr[n].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[n].val.programmaticStreamSerializationAllowed = 1;
+        ++n;
+    }
+    if (carve >= 0) {
+        attr[n].id = cudaLaunchAttributePreferredSharedMemoryCarveout;
+        attr[n].val.sharedMemCarveout = (unsigned)carve;
+        ++n;
+    }
     cfg.attrs = attr;
-    cfg.numAttrs = (t_launch_overlap && grid <= g_overlap_max_blocks) ? 1 : 0;
+    cfg.numAttrs = n;
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -350,6 +390,12 @@ void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, c
                                    ", block " + std::to_string(block) + ", shared " +
                                    std::to_string(smem) + " B) failed: " + cudaGetErrorString(e)};
     }
+}
+
+template <typename... KArgs, typename... Args>
+void launch_kernel(void (*kernel)(KArgs...), int grid, int block, size_t smem, cudaStream_t s,
+                   Args&&... args) {
+    launch_kernel_carve(kernel, grid, block, smem, -1, s, std::forward<Args>(args)...);
 }
 
 // Runs the staged kernels' bounded wait against an mbarrier that no copy
@@ -378,6 +424,8 @@ struct VArgs {
     const int32_t* idx = nullptr;     // aggregate map, or restriction list pointers
     const int32_t* idx2 = nullptr;    // restriction list rows
     const void* sval = nullptr;
+    const int64_t* soff = nullptr;    // staged kernels: slice offsets of the layout with
+                                      // per-slice widths (scol / sval then point at it)
     const void* dv = nullptr;         // 1/A_ii, A_ii, or the dense coarsest inverse
     const void* t = nullptr;          // transfer weights of the scaled levels
     const void* b = nullptr;          // right-hand side / residual / coarse correction
@@ -404,6 +452,7 @@ struct VRec {
     VBatchLauncher launch = nullptr;
     int grid = 0, block = 0;
     size_t smem = 0;
+    int carve = -1;   // preferred shared-memory carveout (percent), -1: the driver's
     int phase = 0, level = 0, step = 0;
     VArgs a;
 };

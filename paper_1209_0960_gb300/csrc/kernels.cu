@@ -561,101 +561,89 @@ __device__ bool stage_wait(uint64_t* bar, int32_t* err, long long limit = kStage
     return all != 0;
 }
 
-// Stage the block's `nsl` slices, starting at slice `slice0` (width W of the
-// sliced layout), into shared memory.  Unpacked (levels whose rows are nearly
-// all W long, like the fine level): the block's slices as they are, two
-// copies.  Packed: slice w keeps only its first
-// K_w entries per row, K_w = the longest row of the slice inside the launch
-// (`len` is this thread's row length, 0 for rows outside it), and its entries
-// follow the previous slice's.  So the padding of a level whose rows vary in
-// length is neither copied nor allotted shared memory, and the block needs
-// only sum_w K_w * 32 entries (the level's stage capacity bounds it), which
-// keeps more blocks resident.  When every slice is full (K_w = W, as on
-// structured levels) the packed layout is the global one and two copies move
-// the whole block; otherwise one copy per array and slice.  Thread 0 issues
-// every copy against one mbarrier.  Every thread of the block calls this and
-// gets the position of its row's entry 0 (entry k at loc + 32 k).  Returns
-// false, with AMG_ETIMEOUT recorded in *err, if the copies have not completed
-// within the spin limit.
+// Stage the block's `nsl` slices, starting at slice `slice0` (common width W),
+// into shared memory as they are: the block's slices are contiguous, so
+// thread 0 issues one copy per array against one mbarrier.  Every thread of
+// the block calls this and gets the position of its row's entry 0 (entry k at
+// loc + 32 k).  Returns false, with AMG_ETIMEOUT recorded in *err, if the
+// copies have not completed within the spin limit.
 template <typename T>
-__device__ bool stage_slices(int64_t slice0, int nsl, int width, int len, bool packed,
-                             const int32_t* scol, const T* sval, int32_t* s_col, T* s_val,
-                             uint64_t* bar, int32_t* err, int& loc) {
-    __shared__ int ksh[kSlicesPerBlock];
+__device__ bool stage_slices(int64_t slice0, int nsl, int width, const int32_t* scol, const T* sval,
+                             int32_t* s_col, T* s_val, uint64_t* bar, int32_t* err, int& loc) {
     const int w = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
-    loc = lane;
+    loc = w * 32 * width + lane;
     if (width == 0) return true;   // no off-diagonal entries: nothing to stage
-    if (!packed) {
-        // every slice at its full width: the global layout, two copies
-        loc = w * 32 * width + lane;
-        if (threadIdx.x == 0) {
-            const uint32_t ub = smem_u32(bar);
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
-            const int64_t e0 = slice0 * 32 * width;
-            uint64_t state, pol;
-            asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                         : "=l"(state) : "r"(ub), "r"(ent * (4u + (uint32_t)sizeof(T))) : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-                " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(ent * 4u),
-                "r"(ub), "l"(pol) : "memory");
-            asm volatile(
-                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-                " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0),
-                "r"(ent * (uint32_t)sizeof(T)), "r"(ub), "l"(pol) : "memory");
-        }
-        __syncthreads();
-        return stage_wait(bar, err);
-    }
-    const int k = (int)__reduce_max_sync(0xffffffffu, (unsigned)len);
-    if (lane == 0) ksh[w] = w < nsl ? k : 0;
-    __syncthreads();
-    int off = 0, total = 0;
-    for (int i = 0; i < nsl; ++i) {
-        off += i < w ? ksh[i] : 0;
-        total += ksh[i];
-    }
-    loc = 32 * off + lane;
     if (threadIdx.x == 0) {
         const uint32_t ub = smem_u32(bar);
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t ent = (uint32_t)nsl * 32u * (uint32_t)width;
+        const int64_t e0 = slice0 * 32 * width;
+        uint64_t state, pol;
+        asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                     : "=l"(state) : "r"(ub), "r"(ent * (4u + (uint32_t)sizeof(T))) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(scol + e0), "r"(ent * 4u),
+            "r"(ub), "l"(pol) : "memory");
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+            " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(sval + e0),
+            "r"(ent * (uint32_t)sizeof(T)), "r"(ub), "l"(pol) : "memory");
+    }
+    __syncthreads();
+    return stage_wait(bar, err);
+}
+
+// Stage the block's `nsl` slices from the layout with per-slice widths: slice
+// s is padded only to its own longest row K_s and starts at soff[s] (entry k
+// of lane i at soff[s] + 32 k + i).  The block's slices are contiguous, so
+// thread 0 issues one copy per array against one mbarrier, and the tile is
+// laid out like the global arrays.  Every thread calls this and gets the
+// position of its row's entry 0 in the tile.  Returns false, with
+// AMG_ETIMEOUT recorded in *err, if the copies have not completed within the
+// spin limit.
+// Slice offsets are read with an evict-last L2 policy: every block's copy
+// waits for them, and the level's gathers would otherwise push them out of L2.
+__device__ __forceinline__ int64_t ld_offset(const int64_t* p) {
+    uint64_t pol;
+    int64_t v;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    asm volatile("ld.global.nc.L2::cache_hint.s64 %0, [%1], %2;" : "=l"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
+template <typename T>
+__device__ bool stage_own_width(int64_t slice0, int nsl, const int64_t* soff, const int32_t* ccol,
+                                const T* cval, int32_t* s_col, T* s_val, uint64_t* bar, int32_t* err,
+                                int& loc) {
+    const int w = (int)(threadIdx.x >> 5);
+    const int64_t e0 = ld_offset(soff + slice0);
+    loc = (int)(ld_offset(soff + slice0 + min(w, nsl)) - e0) + (int)(threadIdx.x & 31);
+    if (threadIdx.x == 0) {
+        const uint32_t ub = smem_u32(bar);
+        const uint32_t ent = (uint32_t)(ld_offset(soff + slice0 + nsl) - e0);
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(ub) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         uint64_t state;
-        if (total == 0) {
+        if (ent == 0) {
             asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(ub) : "memory");
         } else {
-            const uint32_t ent = 32u * (uint32_t)total;
-            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
-                         : "=l"(state) : "r"(ub), "r"(ent * (4u + (uint32_t)sizeof(T))) : "memory");
             uint64_t pol;
             asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-            auto copy = [&](void* dst, const void* src, uint32_t bytes) {
-                asm volatile(
-                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
-                    " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(ub),
-                    "l"(pol) : "memory");
-            };
-            if (total == nsl * width) {
-                const int64_t e0 = slice0 * 32 * width;
-                copy(s_col, scol + e0, ent * 4u);
-                copy(s_val, sval + e0, ent * (uint32_t)sizeof(T));
-            } else {
-                int o = 0;
-                for (int i = 0; i < nsl; ++i) {
-                    const int ki = ksh[i];
-                    if (ki > 0) {
-                        const int64_t e0 = (slice0 + i) * 32 * width;
-                        copy(s_col + 32 * o, scol + e0, 128u * (uint32_t)ki);
-                        copy(s_val + 32 * o, sval + e0, 32u * (uint32_t)ki * (uint32_t)sizeof(T));
-                    }
-                    o += ki;
-                }
-            }
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 %0, [%1], %2;"
+                         : "=l"(state) : "r"(ub), "r"(ent * (4u + (uint32_t)sizeof(T))) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_col)), "l"(ccol + e0), "r"(ent * 4u),
+                "r"(ub), "l"(pol) : "memory");
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+                " [%0], [%1], %2, [%3], %4;" ::"r"(smem_u32(s_val)), "l"(cval + e0),
+                "r"(ent * (uint32_t)sizeof(T)), "r"(ub), "l"(pol) : "memory");
         }
     }
     __syncthreads();
@@ -716,6 +704,17 @@ __device__ __forceinline__ T fine_row(const FineTile<T>& F, int len, int jmax, N
     return acc;
 }
 
+// Stage the block's slices (per-slice widths when soff is set, else the
+// common width) and return whether the copies completed.
+template <typename T>
+__device__ __forceinline__ bool stage_tile(FineTile<T>& F, const VArgs& a, uint64_t* bar) {
+    const T* sval = static_cast<const T*>(a.sval);
+    if (a.soff)
+        return stage_own_width(F.slice0, F.nsl, a.soff, a.scol, sval, F.s_col, F.s_val, bar, a.err,
+                               F.loc);
+    return stage_slices(F.slice0, F.nsl, a.width, a.scol, sval, F.s_col, F.s_val, bar, a.err, F.loc);
+}
+
 // First forward pass from a zero guess on a level with the staged kernels,
 // colour 0 (rows [0, c1)): x_i = b_i / A_ii; the colour-1 rows follow as an
 // ordinary staged pass whose later-colour neighbours (positions >= c1) are
@@ -755,15 +754,13 @@ struct FineFirst0Body {
 // The staged pass of the rows [r0, r1) of one colour.  With z set (the last
 // pass over these rows in a float32 V-cycle) the new value also goes out
 // unscaled in float64: z_i = x_i / s_i (isq = 1/s).  Arguments: r0, r1, jmax,
-// width, nslices, cap, dv = 1/A_ii, z, isq, err.
+// width, nslices, cap, soff, dv = 1/A_ii, z, isq, err.
 template <typename T>
 struct FinePassBody {
     static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
-        const int r0 = a.r0, r1 = a.r1, jmax = a.jmax, width = a.width;
+        const int r0 = a.r0, r1 = a.r1, jmax = a.jmax;
         const int64_t nslices = a.nslices, cap = a.cap;
         const uint16_t* __restrict__ rlen = a.rlen;
-        const int32_t* scol = a.scol;
-        const T* sval = static_cast<const T*>(a.sval);
         const T* __restrict__ dinv = static_cast<const T*>(a.dv);
         const T* b = static_cast<const T*>(a.b);
         T* x = static_cast<T*>(a.x);
@@ -776,9 +773,7 @@ struct FinePassBody {
         const bool valid = F.row >= r0 && F.row < r1;
         const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
         const T di = valid ? __ldcs(dinv + F.row) : T(0);
-        if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
-                          F.s_col, F.s_val, &bar, a.err, F.loc))
-            return;
+        if (!stage_tile(F, a, &bar)) return;
         pdl_wait();
         if (!valid) return;
         const T xi = fine_row<T>(F, len, jmax, [&](int j) { return x[j]; }, b[F.row], a.n, a.err) * di;
@@ -788,15 +783,13 @@ struct FinePassBody {
 };
 
 // The staged residual r = b - A x of the rows [r0, n).  Arguments: r0,
-// r1 = n, width, nslices, cap, dv = A_ii, out = r, err.
+// r1 = n, width, nslices, cap, soff, dv = A_ii, out = r, err.
 template <typename T>
 struct FineResidualBody {
     static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
-        const int r0 = a.r0, n = a.r1, width = a.width;
+        const int r0 = a.r0, n = a.r1;
         const int64_t nslices = a.nslices, cap = a.cap;
         const uint16_t* __restrict__ rlen = a.rlen;
-        const int32_t* scol = a.scol;
-        const T* sval = static_cast<const T*>(a.sval);
         const T* __restrict__ diag = static_cast<const T*>(a.dv);
         const T* b = static_cast<const T*>(a.b);
         const T* x = static_cast<const T*>(a.x);
@@ -808,9 +801,7 @@ struct FineResidualBody {
         const bool valid = F.row >= r0 && F.row < n;
         const int len = valid ? (int)__ldcs(rlen + F.row) : 0;
         const T dg = valid ? __ldcs(diag + F.row) : T(0);
-        if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
-                          F.s_col, F.s_val, &bar, a.err, F.loc))
-            return;
+        if (!stage_tile(F, a, &bar)) return;
         pdl_wait();
         if (!valid) return;
         r[F.row] = fine_row<T>(F, len, n, [&](int j) { return x[j]; }, fmad(-dg, x[F.row], b[F.row]),
@@ -827,15 +818,13 @@ struct FineResidualBody {
 // than a block, so a coarse entry receives at most two additions onto zero (a
 // run cut by a block boundary), whose result does not depend on their order:
 // the sum stays deterministic.  Arguments: r0 = c1, r1 = n, width, nslices,
-// cap, dv = A_ii, idx = aggregate map, t, out = bc, err.
+// cap, soff, dv = A_ii, idx = aggregate map, t, out = bc, err.
 template <typename T, bool SCALED>
 struct FineResRestrictBody {
     static __device__ __forceinline__ void run(int bid, int, const VArgs& a) {
-        const int c1 = a.r0, n = a.r1, width = a.width;
+        const int c1 = a.r0, n = a.r1;
         const int64_t nslices = a.nslices, cap = a.cap;
         const uint16_t* __restrict__ rlen = a.rlen;
-        const int32_t* scol = a.scol;
-        const T* sval = static_cast<const T*>(a.sval);
         const T* __restrict__ diag = static_cast<const T*>(a.dv);
         const T* b = static_cast<const T*>(a.b);
         const T* x = static_cast<const T*>(a.x);
@@ -853,9 +842,7 @@ struct FineResRestrictBody {
         const T dg = valid ? __ldcs(diag + F.row) : T(0);
         const int key = valid ? __ldcs(agg + F.row) : -1;
         const T ti = (SCALED && valid) ? __ldcs(t + F.row) : T(1);
-        if (!stage_slices(F.slice0, F.nsl, width, len, cap < (int64_t)kFineBlock * width, scol, sval,
-                          F.s_col, F.s_val, &bar, a.err, F.loc))
-            return;
+        if (!stage_tile(F, a, &bar)) return;
         pdl_wait();
         T v = T(0);
         if (valid) {
@@ -1560,13 +1547,15 @@ template <typename T>
 struct LevelArrays;
 template <>
 struct LevelArrays<double> {
-    const double *sval, *dinv, *diag, *t;
-    explicit LevelArrays(const DevLevel& L) : sval(L.sval), dinv(L.dinv), diag(L.diag), t(nullptr) {}
+    const double *sval, *cval, *dinv, *diag, *t;
+    explicit LevelArrays(const DevLevel& L)
+        : sval(L.sval), cval(L.cval), dinv(L.dinv), diag(L.diag), t(nullptr) {}
 };
 template <>
 struct LevelArrays<float> {
-    const float *sval, *dinv, *diag, *t;
-    explicit LevelArrays(const DevLevel& L) : sval(L.sval32), dinv(L.dinv32), diag(L.diag32), t(L.t32) {}
+    const float *sval, *cval, *dinv, *diag, *t;
+    explicit LevelArrays(const DevLevel& L)
+        : sval(L.sval32), cval(L.cval32), dinv(L.dinv32), diag(L.diag32), t(L.t32) {}
 };
 
 // dynamic shared memory a kernel gets without opting in, with room for its
@@ -1579,9 +1568,7 @@ inline int fine_blocks(int r0, int r1) {
     return (int)(((int64_t)r1 - (r0 & ~31) + kFineBlock - 1) / kFineBlock);
 }
 inline int64_t fine_nslices(const DevLevel& L) { return ((int64_t)L.n + 31) / 32; }
-inline size_t fine_smem(const DevLevel& L, size_t value_bytes) {
-    return (size_t)L.stage_cap * (sizeof(int32_t) + value_bytes);
-}
+inline size_t fine_smem(const DevLevel& L, size_t value_bytes) { return (size_t)stage_bytes(L, value_bytes); }
 
 // Launches records of one body as one grid (at most kMaxVBatch records).
 template <typename Body>
@@ -1590,15 +1577,17 @@ void vbatch_launch(const VRec* const* recs, int n, cudaStream_t s) {
     p.nrec = n;
     p.bstart[0] = 0;
     size_t smem = 0;
+    int carve = recs[0]->carve;
     for (int k = 0; k < n; ++k) {
         p.grid[k] = recs[k]->grid;
         p.a[k] = recs[k]->a;
         p.bstart[k + 1] = p.bstart[k] + recs[k]->grid;
         smem = std::max(smem, recs[k]->smem);
+        if (recs[k]->carve != carve) carve = -1;
     }
     // the 48 KB default covers static and dynamic shared memory together
     if (smem > kDefaultDynSmem) raise_dyn_smem(k_batched<Body>, smem);
-    launch_kernel(k_batched<Body>, p.bstart[n], recs[0]->block, smem, s, p);
+    launch_kernel_carve(k_batched<Body>, p.bstart[n], recs[0]->block, smem, carve, s, p);
 }
 
 thread_local std::vector<VRec>* t_vrecord = nullptr;
@@ -1607,7 +1596,7 @@ thread_local VKey t_vkey;
 // One V-cycle launch of `Body`: issued as its own kernel, or, while a V-cycle
 // is being recorded, appended to the record list at the current key.
 template <typename Body>
-void vlaunch(int grid, int block, size_t smem, cudaStream_t s, const VArgs& a) {
+void vlaunch(int grid, int block, size_t smem, cudaStream_t s, const VArgs& a, int carve = -1) {
     if (grid <= 0) return;
     if (t_vrecord) {
         VRec r;
@@ -1615,6 +1604,7 @@ void vlaunch(int grid, int block, size_t smem, cudaStream_t s, const VArgs& a) {
         r.grid = grid;
         r.block = block;
         r.smem = smem;
+        r.carve = carve;
         r.phase = t_vkey.phase;
         r.level = t_vkey.level;
         r.step = t_vkey.step++;
@@ -1623,7 +1613,7 @@ void vlaunch(int grid, int block, size_t smem, cudaStream_t s, const VArgs& a) {
         return;
     }
     if (smem > kDefaultDynSmem) raise_dyn_smem(k_single<Body>, smem);
-    launch_kernel(k_single<Body>, grid, block, smem, s, a);
+    launch_kernel_carve(k_single<Body>, grid, block, smem, carve, s, a);
 }
 
 // arguments shared by the row kernels of a level
@@ -1640,6 +1630,15 @@ VArgs level_args(const DevLevel& L, const LevelArrays<T>& A) {
     a.sval = A.sval;
     a.err = L.err;
     return a;
+}
+
+// the staged kernels read the compact layout where the level has one
+template <typename T>
+void use_compact(const DevLevel& L, const LevelArrays<T>& A, VArgs& a) {
+    if (!L.soff) return;
+    a.soff = L.soff;
+    a.scol = L.ccol;
+    a.sval = A.cval;
 }
 
 // r_in / isq (fine level only): form b = r * isq in the first pass (the
@@ -1670,7 +1669,9 @@ void first_impl(const DevLevel& L, const T* b, T* x, T* bc_zero, int nc, cudaStr
             a.dv = A.dinv;
             a.b = b;
             a.x = x;
-            vlaunch<FinePassBody<T>>(fine_blocks(c1, c2), kFineBlock, fine_smem(L, sizeof(T)), s, a);
+            use_compact(L, A, a);
+            vlaunch<FinePassBody<T>>(fine_blocks(c1, c2), kFineBlock, fine_smem(L, sizeof(T)), s, a,
+                                     L.carve);
         }
         return;
     }
@@ -1704,7 +1705,9 @@ void pass_impl(const DevLevel& L, int col, int jmax, const T* b, T* x, cudaStrea
     if (L.lpr == kFine) {
         a.z = z_out;
         a.isq = isq;
-        vlaunch<FinePassBody<T>>(fine_blocks(r0, r1), kFineBlock, fine_smem(L, sizeof(T)), s, a);
+        use_compact(L, A, a);
+        vlaunch<FinePassBody<T>>(fine_blocks(r0, r1), kFineBlock, fine_smem(L, sizeof(T)), s, a,
+                                 L.carve);
         return;
     }
     if (z_out) throw Error{AMG_EINVAL, "the fused float32 exit needs the fine-level kernels"};
@@ -1729,15 +1732,18 @@ void residual_restrict_impl(const DevLevel& L, const T* b, const T* x, T* r, T* 
             a.idx = L.agg;
             a.t = A.t;
             a.out = bc;
+            use_compact(L, A, a);
             vlaunch<FineResRestrictBody<T, SC>>(fine_blocks(c1, L.n), kFineBlock,
-                                                fine_smem(L, sizeof(T)), s, a);
+                                                fine_smem(L, sizeof(T)), s, a, L.carve);
         }
         return;
     }
     if (L.n > c1) {
         a.out = r;
         if (L.lpr == kFine) {
-            vlaunch<FineResidualBody<T>>(fine_blocks(c1, L.n), kFineBlock, fine_smem(L, sizeof(T)), s, a);
+            use_compact(L, A, a);
+            vlaunch<FineResidualBody<T>>(fine_blocks(c1, L.n), kFineBlock, fine_smem(L, sizeof(T)), s, a,
+                                         L.carve);
         } else {
             AMG_LPR_DISPATCH(launch_lpr(L, L.n - c1),
                              (vlaunch<ResidualBody<LPR, T>>(row_blocks(c1, L.n, LPR, L.block), L.block,

@@ -130,6 +130,25 @@ __global__ void k_csr_to_sell(int n, const int32_t* __restrict__ nrp, const int3
     }
 }
 
+// Copy the sliced arrays (common width W) into the layout with per-slice
+// widths: slice s starts at soff[s] and keeps K_s = (soff[s+1] - soff[s]) / 32
+// entries a row, entry k of lane i at soff[s] + 32 k + i (padding entries as
+// in the common layout: the row itself with value 0).  One thread per row.
+template <typename T>
+__global__ void k_sell_own_width(int n, int width, const int64_t* __restrict__ soff,
+                                 const int32_t* __restrict__ scol, const T* __restrict__ sval,
+                                 int32_t* __restrict__ ccol, T* __restrict__ cval) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t src = (int64_t)(r >> 5) * 32 * width + (r & 31);
+    const int64_t dst = soff[r >> 5] + (r & 31);
+    const int ks = (int)((soff[(r >> 5) + 1] - soff[r >> 5]) >> 5);
+    for (int k = 0; k < ks; ++k) {
+        if (ccol) ccol[dst + 32 * (int64_t)k] = scol[src + 32 * (int64_t)k];
+        cval[dst + 32 * (int64_t)k] = sval[src + 32 * (int64_t)k];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // coarsest level: dense Cholesky factor (lower triangle, row-major, in place)
 // and the inverse through two triangular solves per unit vector
@@ -501,24 +520,27 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
     L.width = width;
     L.sw = 32 * (int64_t)width;
     L.padded = (int64_t)nslices * L.sw;
-    {
-        // packed staging of a block of 8 slices (256 rows): each slice keeps
-        // its longest row's entries; the bound over every window of 8
-        // consecutive slices (blocks start at any slice: colours start
-        // anywhere)
-        constexpr int kSlicesPerStage = 8;
-        std::vector<int64_t> kmax(nslices, 0);
-        for (int32_t r = 0; r < n; ++r) kmax[r >> 5] = std::max<int64_t>(kmax[r >> 5], rlen[r]);
+    // staged blocks cover 8 consecutive slices (256 rows) starting at any
+    // slice (colours start anywhere): their tile bounds are maxima over every
+    // window of 8 slices
+    constexpr int kSlicesPerStage = 8;
+    auto window_max = [&](const std::vector<int64_t>& per_slice) {
         int64_t run = 0, best = 0;
         for (int32_t sl = 0; sl < nslices; ++sl) {
-            run += kmax[sl];
-            if (sl >= kSlicesPerStage) run -= kmax[sl - kSlicesPerStage];
+            run += per_slice[sl];
+            if (sl >= kSlicesPerStage) run -= per_slice[sl - kSlicesPerStage];
             best = std::max(best, run);
         }
-        // pack only where it saves a quarter of the tile: on nearly uniform
-        // levels the plain two-copy staging is cheaper than per-slice copies
-        L.stage_cap = 4 * 32 * best < 3 * 256 * (int64_t)width ? 32 * best : 256 * (int64_t)width;
-    }
+        return best;
+    };
+    // per-slice widths: each slice padded only to its own longest row
+    std::vector<int64_t> kmax(nslices, 0), soff(nslices + 1, 0);
+    for (int32_t r = 0; r < n; ++r) kmax[r >> 5] = std::max<int64_t>(kmax[r >> 5], rlen[r]);
+    for (int32_t sl = 0; sl < nslices; ++sl) soff[sl + 1] = soff[sl] + 32 * kmax[sl];
+    // kept where the common width pads more than a tenth over that (the
+    // coarse levels; the fine level's rows are nearly all W long)
+    const bool compact = width > 0 && 10 * L.padded > 11 * soff[nslices];
+    L.stage_cap = compact ? 32 * window_max(kmax) : 256 * (int64_t)width;
     L.rlen = arena.alloc<uint16_t>(n);
     L.scol = arena.alloc<int32_t>(L.padded);
     L.sval = arena.alloc<double>(L.padded);
@@ -538,11 +560,26 @@ void build_level_device(const DevCsr& A, const HostCsr& Ah, const std::vector<in
                                                     d_nva, L.diag, L.dinv);
     k_csr_to_sell<<<blocks_for(n), kBlock, 0, s>>>(n, d_nrp, d_nci, d_nva, width, L.scol, L.sval);
     AMG_CUDA_TRY(cudaGetLastError());
+    if (compact) {
+        const int64_t ce = soff[nslices];
+        L.stage_entries = ce;
+        L.soff = arena.alloc<int64_t>(nslices + 1);
+        L.ccol = arena.alloc<int32_t>(ce);
+        L.cval = arena.alloc<double>(ce);
+        AMG_CUDA_TRY(cudaMemcpyAsync(L.soff, soff.data(), sizeof(int64_t) * (nslices + 1),
+                                     cudaMemcpyHostToDevice, s));
+        // rows past n in the last slice: padding entries of no row
+        AMG_CUDA_TRY(cudaMemsetAsync(L.ccol, 0, sizeof(int32_t) * ce, s));
+        AMG_CUDA_TRY(cudaMemsetAsync(L.cval, 0, sizeof(double) * ce, s));
+        k_sell_own_width<double><<<blocks_for(n), kBlock, 0, s>>>(n, width, L.soff, L.scol, L.sval,
+                                                                   L.ccol, L.cval);
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
     // lanes per row: the staged one-row-per-thread kernels on sparse rows
     // (bandwidth bound), several lanes on the denser coarse rows (gather
     // latency bound)
     const double avg = n > 0 ? (double)L.nnz_off / n : 0.0;
-    L.lpr = (avg <= 7.0 && width <= kFineMaxWidth) ? 0 : avg <= 16.0 ? 4 : 8;
+    L.lpr = (avg <= 7.0 && staged_fits(L)) ? 0 : avg <= 16.0 ? 4 : 8;
     L.lpr_wide = L.lpr;
     AMG_CUDA_TRY(cudaStreamSynchronize(s));
 }
@@ -622,6 +659,14 @@ void build_level_fp32(DevLevel& L, const double* coarse_diag, DevArena& arena, c
     k_level_fp32<<<blocks_for(n), kBlock, 0, s>>>(n, L.width, L.scol, L.sval, L.diag, L.agg, coarse_diag,
                                                   L.sval32, L.diag32, L.dinv32, L.t32);
     AMG_CUDA_TRY(cudaGetLastError());
+    if (L.soff) {
+        const int64_t ce = L.stage_entries;
+        L.cval32 = arena.alloc<float>(ce);
+        AMG_CUDA_TRY(cudaMemsetAsync(L.cval32, 0, sizeof(float) * ce, s));
+        k_sell_own_width<float><<<blocks_for(n), kBlock, 0, s>>>(n, L.width, L.soff, nullptr,
+                                                                  L.sval32, nullptr, L.cval32);
+        AMG_CUDA_TRY(cudaGetLastError());
+    }
 }
 
 }  // namespace amg

@@ -175,6 +175,9 @@ void fill_info(amg_ctx* c) {
         li.lanes_per_row = last ? 0 : d.lpr;
         li.threads_per_block = last ? 0 : d.block;
         li.sweep = (!last && d.sweep) ? 1 : 0;
+        li.carveout = last ? -1 : d.carve;
+        li.compact = d.soff ? 1 : 0;
+        li.staged_entries = d.soff ? d.stage_entries : d.padded;
         b64 += li.vcycle_bytes_fp64;
         b32 += li.vcycle_bytes_fp32;
         if (l == 0) nnz0 = li.nnz;
@@ -529,19 +532,26 @@ constexpr int kStaged = 0;   // DevLevel::lpr of the staged one-row-per-thread k
 // A launch shape as one code: lanes per row (0 = staged kernels, 1, 2, 4 or
 // 8) plus kHalfBlock for blocks of 128 instead of 256 threads (row kernels
 // only), plus kSweep for smoothing sweeps run as one dependency-driven kernel
-// each (lane shapes only).
+// each (lane shapes only), plus (staged kernels only) the preferred
+// shared-memory carveout + 1 in the bits from kCarveShift (0: the driver's).
 constexpr int kHalfBlock = 16;
 constexpr int kSweep = 32;
+constexpr int kCarveShift = 8;
+constexpr int kCarveMask = 0x7f << kCarveShift;
 // sweeps are planned on the host from the level's graph (adjacency of every
 // item): kept to levels where a pass is short
 constexpr int32_t kSweepMaxRows = 1 << 20;
 inline int shape_lanes(int code) { return code & (kHalfBlock - 1); }
 inline int shape_block(int code) { return (code & kHalfBlock) ? 128 : 256; }
+inline int shape_carve(int code) { return ((code & kCarveMask) >> kCarveShift) - 1; }
+inline int with_carve(int code, int carve) { return (code & ~kCarveMask) | ((carve + 1) << kCarveShift); }
 
 bool shape_allowed(const DevLevel& L, int code) {
     const int lanes = shape_lanes(code);
-    if (code & ~(kSweep | kHalfBlock | (kHalfBlock - 1))) return false;
-    if (lanes == kStaged) return code == kStaged && L.width <= kFineMaxWidth;
+    if (code & ~(kSweep | kHalfBlock | (kHalfBlock - 1) | kCarveMask)) return false;
+    if (shape_carve(code) > 100) return false;
+    if (lanes == kStaged) return (code & ~kCarveMask) == kStaged && staged_fits(L);
+    if (code & kCarveMask) return false;
     if (lanes != 1 && lanes != 2 && lanes != 4 && lanes != 8) return false;
     if (code & kSweep)
         return !L.fused_ok && L.ncolours >= 2 && 2 * L.ncolours - 1 <= kSweepMaxPasses &&
@@ -550,7 +560,8 @@ bool shape_allowed(const DevLevel& L, int code) {
 }
 
 int shape_of(const DevLevel& L) {
-    return L.lpr | (L.block == 128 ? kHalfBlock : 0) | (L.sweep ? kSweep : 0);
+    const int code = L.lpr | (L.block == 128 ? kHalfBlock : 0) | (L.sweep ? kSweep : 0);
+    return L.lpr == kStaged && L.carve >= 0 ? with_carve(code, L.carve) : code;
 }
 
 // The dependency plan of one sweep of level l (see SweepPlan) for items of
@@ -666,6 +677,7 @@ void set_shape(amg_ctx* c, int l, int code) {
     L.block = shape_block(code);
     L.fused_restrict = lanes == kStaged && L.fused_ok;
     L.sweep = (code & kSweep) != 0 && lanes >= 1;
+    L.carve = lanes == kStaged ? shape_carve(code) : -1;
     L.plan_pre = L.plan_post = nullptr;
     if (L.sweep) {
         // the plan (items, and the cooperative grid) depends on lanes and block
@@ -741,6 +753,7 @@ double time_vcycle_from(amg_ctx* c, int l) {
 // rule's shape is kept unless a candidate is more than 3 % faster, which keeps
 // the choice stable against timing noise.  Returns the milliseconds spent.
 double autotune_shapes(amg_ctx* c) {
+    NvtxRange nvtx("autotune");
     const int nlev = (int)c->dl.size();
     if (nlev < 2) return 0.0;
     const double t0 = now_ms();
@@ -772,9 +785,13 @@ double autotune_shapes(amg_ctx* c) {
         const int rule = L.lpr;
         double t_rule = 1e30, t_best = 1e30;
         int best = rule;
-        for (int lanes : {kStaged, 1, 1 | kHalfBlock, 2, 2 | kHalfBlock, 4, 4 | kHalfBlock, 8,
-                          8 | kHalfBlock, 2 | kSweep, 2 | kHalfBlock | kSweep, 4 | kSweep,
-                          4 | kHalfBlock | kSweep, 8 | kSweep, 8 | kHalfBlock | kSweep}) {
+        // staged kernels also with a smaller shared-memory carveout (percent
+        // of the maximum 228 KB: 100, 132 or 164 KB), leaving more L1 for the
+        // neighbour gathers
+        for (int lanes : {kStaged, with_carve(kStaged, 44), with_carve(kStaged, 58),
+                          with_carve(kStaged, 72), 1, 1 | kHalfBlock, 2, 2 | kHalfBlock, 4,
+                          4 | kHalfBlock, 8, 8 | kHalfBlock, 2 | kSweep, 2 | kHalfBlock | kSweep,
+                          4 | kSweep, 4 | kHalfBlock | kSweep, 8 | kSweep, 8 | kHalfBlock | kSweep}) {
             if (!shape_allowed(L, lanes)) continue;
             set_shape(c, l, lanes);
             const double t = time_vcycle_from(c, l);
@@ -1318,6 +1335,7 @@ const std::vector<VRec>* vcycle_records(amg_ctx* c) {
 void precondition_context(amg_ctx* c) { precondition(c, c->r, c->z); }
 
 void batched_precondition(amg_ctx* const* cs, int n, cudaStream_t s) {
+    NvtxRange nvtx("batched V-cycle");
     std::vector<const VRec*> all;
     for (int k = 0; k < n; ++k) {
         const std::vector<VRec>* r = vcycle_records(cs[k]);
@@ -1478,6 +1496,7 @@ void init_device_pool(int device) {
 }
 
 void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
+    NvtxRange nvtx("amg_setup");
     if (!A || !prm || !out) throw Error{AMG_EINVAL, "null argument"};
     *out = nullptr;
     check_params(*prm);
@@ -1547,6 +1566,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
         HostLevel& cur = c->hl[l];
         if (cur.A.n <= prm->coarsen_target || l >= prm->max_levels - 1) break;
         double t0 = now_ms();
+        NvtxRange nvtx_level("setup level: aggregation, colouring, Galerkin");
         AggResult R = aggregate_level(cur.A, &dA[l], *prm, s);
         agg_ms += now_ms() - t0;
         host_ms += now_ms() - t0;
@@ -1640,6 +1660,7 @@ void setup_impl(const amg_csr* A, const amg_params* prm, amg_ctx** out) {
     // coarsest level: dense inverse
     c->Ainv = c->mem.alloc<double>((size_t)c->nL * c->nL);
     const double t_inv0 = now_ms();
+    NvtxRange nvtx_inv("coarsest inverse");
     if (!dense_inverse_device(dA[nlev - 1], c->Ainv, s))
         throw Error{AMG_ENOTSPD, "coarsest matrix is not positive definite"};
     const double inverse_ms = now_ms() - t_inv0;
@@ -1765,6 +1786,7 @@ int amg_set_precision(amg_ctx* c, int32_t precision, int32_t flexible_cg) {
             c->linfo[l].lanes_per_row = c->dl[l].lpr;
             c->linfo[l].threads_per_block = c->dl[l].block;
             c->linfo[l].sweep = c->dl[l].sweep ? 1 : 0;
+            c->linfo[l].carveout = c->dl[l].carve;
         }
         leave(c);
     });
@@ -1809,7 +1831,10 @@ static int solve_common(amg_ctx* c, const double* b, double* x, double tol, int3
         if (zero_guess) AMG_CUDA_TRY(cudaMemsetAsync(c->x, 0, sizeof(double) * n, s));
         else launch_scatter(n, c->perm0, xd, c->x, s);
         amg_solve_info local{};
-        status = use_bicgstab ? bicgstab(c, tol, maxit, &local, why) : pcg(c, tol, maxit, &local);
+        {
+            NvtxRange nvtx(use_bicgstab ? "bicgstab" : "pcg");
+            status = use_bicgstab ? bicgstab(c, tol, maxit, &local, why) : pcg(c, tol, maxit, &local);
+        }
         if (host) {
             launch_gather(n, c->perm0, c->x, c->z, s);
             AMG_CUDA_TRY(cudaMemcpyAsync(x, c->z, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
@@ -1938,8 +1963,8 @@ int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row, int32_t th
         if (lanes < 0 || lanes > 8 || !shape_allowed(c->dl[l], code))
             throw Error{AMG_EINVAL, "lanes_per_row must be 1, 2, 4 or 8 (optionally with "
                                     "AMG_SHAPE_SWEEP on a level of at most 2^20 rows that is not "
-                                    "two-colour fused), or 0 (256 threads) on a level whose rows "
-                                    "have at most 32 off-diagonals"};
+                                    "two-colour fused), or 0 (256 threads) on a level whose staged "
+                                    "tile fits in 96 KB"};
         enter(c);
         AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
         drop_graphs(c);
@@ -1948,6 +1973,26 @@ int amg_set_level_shape(amg_ctx* c, int32_t l, int32_t lanes_per_row, int32_t th
         c->linfo[l].lanes_per_row = c->dl[l].lpr;
         c->linfo[l].threads_per_block = c->dl[l].block;
         c->linfo[l].sweep = c->dl[l].sweep ? 1 : 0;
+        c->linfo[l].carveout = c->dl[l].carve;
+        leave(c);
+    });
+}
+
+int amg_set_level_carveout(amg_ctx* c, int32_t l, int32_t percent) {
+    return Guard::run([&] {
+        if (!c) throw Error{AMG_EINVAL, "null context"};
+        if (l < 0 || l >= (int32_t)c->dl.size() - 1)
+            throw Error{AMG_EINVAL, "level out of range (the coarsest level has no shape)"};
+        if (percent < -1 || percent > 100) throw Error{AMG_EINVAL, "percent must be -1 .. 100"};
+        if (c->dl[l].lpr != kStaged)
+            throw Error{AMG_EINVAL, "the carveout applies to the staged kernels (lanes_per_row 0)"};
+        enter(c);
+        AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));   // no graph of this context in flight
+        drop_graphs(c);
+        const int code = with_carve(shape_of(c->dl[l]), percent);
+        set_shape(c, l, code);
+        c->shapes[c->precision][l] = code;
+        c->linfo[l].carveout = c->dl[l].carve;
         leave(c);
     });
 }
@@ -2075,6 +2120,13 @@ int amg_debug_set_column(amg_ctx* c, int32_t l, int32_t row, int32_t k, int32_t 
         const int64_t e = (int64_t)(r >> 5) * L.sw + 32 * (int64_t)k + (r & 31);
         AMG_CUDA_TRY(cudaStreamSynchronize(c->stream));
         AMG_CUDA_TRY(cudaMemcpy(L.scol + e, &col, sizeof(int32_t), cudaMemcpyHostToDevice));
+        if (L.soff) {
+            // the same entry in the copy with per-slice widths
+            int64_t pos = 0;
+            AMG_CUDA_TRY(cudaMemcpy(&pos, L.soff + (r >> 5), sizeof(int64_t), cudaMemcpyDeviceToHost));
+            pos += 32 * (int64_t)k + (r & 31);
+            AMG_CUDA_TRY(cudaMemcpy(L.ccol + pos, &col, sizeof(int32_t), cudaMemcpyHostToDevice));
+        }
         drop_graphs(c);
 #endif
     });

@@ -63,6 +63,11 @@ rc = amg.lib().amg_debug_set_column(s.ctx, 1, 5, 0, n1 + 3)
 out["poke"] = rc
 x, rc, info = s.solve(b, tol=1e-10, maxit=50)
 out["corrupt_solve"] = [rc, amg.amg_last_error()]
+# the same entry read by the staged kernels from the level's compact copy
+s.set_level_shape(1, 0)
+out["staged_compact"] = s.info()[1][1]["compact"]
+x, rc, info = s.solve(b, tol=1e-10, maxit=50)
+out["corrupt_solve_staged"] = [rc, amg.amg_last_error()]
 s.close()
 print("RESULT " + json.dumps(out))
 """
@@ -108,6 +113,10 @@ def test_checked_build_matches_the_regular_build(checked):
 def test_checked_build_reports_a_corrupt_index(checked):
     assert checked["poke"] == amg.AMG_OK
     rc, msg = checked["corrupt_solve"]
+    assert rc == amg.AMG_ERANGE
+    assert "outside its range" in msg
+    assert checked["staged_compact"] == 1
+    rc, msg = checked["corrupt_solve_staged"]
     assert rc == amg.AMG_ERANGE
     assert "outside its range" in msg
 

@@ -85,6 +85,109 @@ def test_every_shape_matches_oracle(case):
         solver.close()
 
 
+def _own_width_entries(level):
+    """Entries of a level in the sliced layout with per-slice widths: rows in
+    the smoothing order (colour, then aggregate, then index), 32-row slices,
+    each padded to its longest row; and the same with one common width."""
+    n = level["n"]
+    lens = np.diff(level["row_ptr"]) - 1
+    agg = np.where(level["agg"] >= 0, level["agg"], np.iinfo(np.int32).max)
+    order = np.lexsort((np.arange(n), agg, level["colour"]))
+    ns = (n + 31) // 32
+    padded = np.zeros(ns * 32, dtype=np.int64)
+    padded[:n] = lens[order]
+    kmax = padded.reshape(ns, 32).max(axis=1)
+    return int(32 * kmax.sum()), int(32 * ns * lens.max())
+
+
+def test_per_slice_width_layout_of_varying_levels():
+    # Coarse levels whose rows vary in length keep a copy of their entries in
+    # 32-row slices padded only to each slice's longest row, for the staged
+    # kernels; the fine 7-point level keeps the common width.  The copy's size
+    # follows from the oracle's levels, and the staged kernels on it give the
+    # oracle's V-cycle, in FP64 to the parity bar and in FP32 through a solve,
+    # over colours that start inside a slice and blocks cut short at the end
+    # of a level.
+    p = P.anisotropic3d((48, 48, 48), seed=0)
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=p.dim)
+    try:
+        H = O.Hierarchy(p.row_ptr, p.col, p.val, _oracle_params(solver.params))
+        _, levels = solver.info()
+        assert levels[0]["compact"] == 0
+        compact = []
+        for l in range(len(levels) - 1):
+            own, common = _own_width_entries(H.level(l))
+            want = 10 * common > 11 * own
+            assert levels[l]["compact"] == int(want), l
+            assert levels[l]["staged_entries"] == (own if want else common), l
+            if want:
+                compact.append(l)
+        assert compact and compact[0] == 1
+        r = np.random.default_rng(11).standard_normal(p.n)
+        staged = 0
+        for l in range(len(levels) - 1):
+            try:
+                solver.set_level_shape(l, 0)
+                staged += l in compact
+            except amg.AmgError:
+                pass
+        assert staged >= 1
+        assert _vcycle_err(solver, H, r) <= 1e-12
+        x, rc, info = solver.solve(torch.from_numpy(p.b).cuda(), tol=1e-10, maxit=300)
+        assert rc == amg.AMG_OK
+        xo, it_o, _, _ = H.pcg(p.b, tol=1e-10, maxit=300)
+        assert abs(info["iterations"] - it_o) <= 1
+        xo = oracle_iterate(H, p.b, info["iterations"], it_o, xo)
+        assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-9 * np.linalg.norm(xo)
+        solver.set_precision(amg.AMG_FP32_IN_FP64)
+        x, rc, info = solver.solve(torch.from_numpy(p.b).cuda(), tol=1e-8, maxit=300)
+        assert rc == amg.AMG_OK and info["true_rel_residual"] <= 1.05e-8
+    finally:
+        solver.close()
+
+
+def test_carveout_keeps_the_vcycle_bit_identical():
+    # The shared-memory carveout of the staged kernels changes only how the
+    # SM splits its L1/shared array: the V-cycle is bit-identical for every
+    # value, the level info reports it, and it is refused where it has no
+    # meaning.
+    maker, over = CASES["lognormal_3lev"]
+    p = maker()
+    solver = amg.AMG(p.row_ptr, p.col, p.val, dim=p.dim, **over)
+    try:
+        _, levels = solver.info()
+        r = torch.from_numpy(np.random.default_rng(5).standard_normal(p.n)).cuda()
+        staged = []
+        for l in range(len(levels) - 1):
+            try:
+                solver.set_level_shape(l, 0)
+                staged.append(l)
+            except amg.AmgError:
+                pass
+        assert staged
+        z0 = solver.vcycle(r).cpu().numpy()
+        for pct in (0, 44, 58, 72, 100, -1):
+            for l in staged:
+                solver.set_level_carveout(l, pct)
+                assert solver.info()[1][l]["carveout"] == pct
+            z = solver.vcycle(r).cpu().numpy()
+            assert np.array_equal(z, z0), pct
+        for bad in (-2, 101):
+            with pytest.raises(amg.AmgError) as e:
+                solver.set_level_carveout(staged[0], bad)
+            assert e.value.code == amg.AMG_EINVAL
+        solver.set_level_shape(staged[0], 4)
+        assert solver.info()[1][staged[0]]["carveout"] == -1
+        with pytest.raises(amg.AmgError) as e:
+            solver.set_level_carveout(staged[0], 50)
+        assert e.value.code == amg.AMG_EINVAL
+        with pytest.raises(amg.AmgError) as e:
+            solver.set_level_carveout(len(levels) - 1, 50)
+        assert e.value.code == amg.AMG_EINVAL
+    finally:
+        solver.close()
+
+
 def test_shape_errors():
     p = P.laplace2d_random_rhs(32)
     solver = amg.AMG(p.row_ptr, p.col, p.val, dim=2, coarsen_target=100)
