@@ -153,17 +153,10 @@ def parse_args():
     ap.add_argument("--aggregation-device", type=int, choices=[0, 1], default=0,
                     help="with --aggregation-tile: run the tiles on the GPU (1) or on host threads")
     args = ap.parse_args()
-    args.lanes = []
-    for v in (v.strip() for v in args.lanes_per_row.split(",")):
-        if v:
-            m = re.fullmatch(r"(\d+)(h?)(s?)(?:c(\d+))?", v)
-            if not m:
-                ap.error(f"--lanes-per-row: cannot read {v!r}")
-            lanes = int(m.group(1))
-            if m.group(3):
-                lanes |= 0x100   # AMG_SHAPE_SWEEP: one dependency-driven kernel per sweep
-            carve = int(m.group(4)) if m.group(4) else None
-            args.lanes.append((lanes, 128 if m.group(2) else 0, carve))
+    try:
+        args.lanes = parse_lanes(args.lanes_per_row)
+    except ValueError as e:
+        ap.error(str(e))
     if args.lanes:
         args.autotune = 0
     if args.aggregation_tile < 0:
@@ -406,6 +399,22 @@ def timed_solves(solver, b, x, steps, tol, stream, dist, maxit):
     torch.cuda.synchronize()
     dist.barrier()
     return ev0.elapsed_time(ev1) / steps, infos
+
+
+def parse_lanes(text: str) -> list:
+    """--lanes-per-row text -> [(lanes_per_row, threads_per_block, carveout or None)]."""
+    out = []
+    for v in (v.strip() for v in text.split(",")):
+        if v:
+            m = re.fullmatch(r"(\d+)(h?)(s?)(?:c(\d+))?", v)
+            if not m:
+                raise ValueError(f"--lanes-per-row: cannot read {v!r}")
+            lanes = int(m.group(1))
+            if m.group(3):
+                lanes |= 0x100   # AMG_SHAPE_SWEEP: one dependency-driven kernel per sweep
+            carve = int(m.group(4)) if m.group(4) else None
+            out.append((lanes, 128 if m.group(2) else 0, carve))
+    return out
 
 
 def apply_lanes(solver, args):

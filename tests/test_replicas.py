@@ -87,3 +87,4 @@ def test_a_dead_rank_ends_the_others_collectives_with_an_error():
         assert not alive, "the surviving rank hung"
         assert procs[1].exitcode == 3
         assert 0 in out and out[0] != "no error"
+
