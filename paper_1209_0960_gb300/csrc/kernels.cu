@@ -535,6 +535,10 @@ __global__ void __launch_bounds__(kBlock) k_sweep(int npass, const SweepPass* __
 // policy: the fine matrix is read once per pass and is larger than L2, and
 // keeping it out of L2 leaves the coarse levels resident there from one
 // V-cycle to the next.  Row lengths and diagonals are loaded evict-first too.
+// The same kernels run on the coarse levels, from a copy whose slices are
+// padded only to their own longest row where that saves more than a tenth
+// (the block's start and its warps' slices then come from the slice offsets),
+// with a per-level preferred L1/shared-memory split for their gathers.
 // ---------------------------------------------------------------------------
 constexpr int kFineBlock = 256;                    // rows (threads) per fine-level block
 constexpr int kSlicesPerBlock = kFineBlock / 32;
@@ -676,7 +680,7 @@ struct FineTile {
     int nsl;
     int row;
     int loc;          // offset of this row's entry 0 in the tiles (entry k at loc + 32 k),
-                      // set by stage_slices
+                      // set by the staging (stage_tile)
     int32_t* s_col;
     T* s_val;
     __device__ FineTile(int r0, int64_t nslices, int64_t cap, unsigned char* smem, int bid) {
