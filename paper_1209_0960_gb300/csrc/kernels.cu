@@ -404,8 +404,8 @@ struct ResidualBody {
 // ---------------------------------------------------------------------------
 // Dependency-driven sweep (see SweepPlan in device.h): every colour pass of a
 // symmetric Gauss-Seidel sweep in one launch, one block per item of rows.
-// The rows of an item are updated exactly as k_gs_pass (and, for the first
-// pass from a zero guess, k_first) updates them, so the results are those of
+// The rows of an item are updated exactly as PassBody (and, for the first
+// pass from a zero guess, FirstBody) updates them, so the results are those of
 // the pass-per-launch kernels; only the waits between passes differ.
 // ---------------------------------------------------------------------------
 constexpr long long kDepSpinLimit = 1LL << 20;   // polls per dependency (over a second)
