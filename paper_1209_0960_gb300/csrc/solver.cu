@@ -80,17 +80,24 @@ void upload(T* dst, const std::vector<T>& src, cudaStream_t s) {
 // 256-row window by length, to cut the padding of the sliced layout, was
 // measured slower on the 512^3 anisotropic workload: the coarse levels lost
 // more to the scattered restriction and gathers than the staging saved.)
+// Two stable counting sorts (by aggregate, then by colour) give that order in
+// O(n + aggregates + colours); a comparison sort of the 134M rows of a 512^3
+// level took about 20 s of setup.
 std::vector<int32_t> smoothing_order(const HostLevel& h) {
     const int32_t n = h.A.n;
-    std::vector<int32_t> idx(n);
-    std::iota(idx.begin(), idx.end(), 0);
-    auto key = [&](int32_t i) {
-        const int32_t a = h.agg.agg[i];
-        return std::make_pair(h.colour[i], a >= 0 ? a : INT32_MAX);
-    };
-    std::stable_sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) { return key(x) < key(y); });
+    const int32_t nc = h.agg.nc, ncol = h.ncolours;
+    const std::vector<int32_t>& agg = h.agg.agg;
+    const std::vector<int32_t>& colour = h.colour;
+    auto slot = [&](int32_t i) { return agg[i] >= 0 ? agg[i] : nc; };   // unaggregated last
+    std::vector<int32_t> by_agg(n), cnt((size_t)std::max(nc, ncol) + 2, 0);
+    for (int32_t i = 0; i < n; ++i) ++cnt[slot(i) + 1];
+    for (int32_t q = 0; q <= nc; ++q) cnt[q + 1] += cnt[q];
+    for (int32_t i = 0; i < n; ++i) by_agg[cnt[slot(i)]++] = i;
+    std::fill(cnt.begin(), cnt.end(), 0);
+    for (int32_t i = 0; i < n; ++i) ++cnt[colour[i] + 1];
+    for (int32_t q = 0; q < ncol; ++q) cnt[q + 1] += cnt[q];
     std::vector<int32_t> perm(n);
-    for (int32_t r = 0; r < n; ++r) perm[idx[r]] = r;
+    for (int32_t i : by_agg) perm[i] = cnt[colour[i]]++;
     return perm;
 }
 
