@@ -51,6 +51,48 @@
 
 namespace amg {
 
+namespace {
+
+// Matrices of at least this many rows run the per-row passes of validation
+// and strength on several host threads.  Each row writes only its own results
+// and errors are reported for the lowest failing row, so the outcome does not
+// depend on the thread count.  (Smaller matrices, like the serving requests
+// set up several at a time, stay on the calling thread.)
+constexpr int32_t kParallelRows = 1 << 20;
+
+// fn(lo, hi, chunk) over consecutive chunks of [0, n)
+template <typename F>
+int for_row_chunks(int32_t n, F fn) {
+    const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+    const int threads = n >= kParallelRows ? (int)std::min(16u, hw) : 1;
+    const int32_t chunk = (int32_t)(((int64_t)n + threads - 1) / threads);
+    std::vector<std::thread> pool;
+    for (int t = 1; t < threads; ++t) {
+        const int32_t lo = (int32_t)std::min<int64_t>(n, (int64_t)t * chunk);
+        const int32_t hi = (int32_t)std::min<int64_t>(n, (int64_t)lo + chunk);
+        pool.emplace_back(fn, lo, hi, t);
+    }
+    fn(0, std::min(n, chunk), 0);
+    for (auto& th : pool) th.join();
+    return threads;
+}
+
+// the first failing row of each chunk and its message
+struct RowError {
+    int32_t row = INT32_MAX;
+    std::string msg;
+};
+bool first_error(const std::vector<RowError>& e, std::string& err) {
+    const RowError* best = nullptr;
+    for (const RowError& x : e)
+        if (x.row != INT32_MAX && (!best || x.row < best->row)) best = &x;
+    if (!best) return false;
+    err = best->msg;
+    return true;
+}
+
+}  // namespace
+
 bool validate_csr(const HostCsr& A, std::string& err) {
     const int32_t n = A.n;
     if (n <= 0) { err = "matrix has no rows"; return false; }
@@ -61,34 +103,50 @@ bool validate_csr(const HostCsr& A, std::string& err) {
         err = "col/val length differs from row_ptr[n]";
         return false;
     }
-    for (int32_t i = 0; i < n; ++i) {
-        bool has_diag = false;
-        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-            int32_t j = A.ci[k];
-            if (j < 0 || j >= n) { err = "column index out of range in row " + std::to_string(i); return false; }
-            if (k > A.rp[i] && A.ci[k - 1] >= j) {
-                err = "columns not sorted/unique in row " + std::to_string(i);
-                return false;
+    std::vector<RowError> errs(16);
+    for_row_chunks(n, [&](int32_t lo, int32_t hi, int t) {
+        for (int32_t i = lo; i < hi; ++i) {
+            bool has_diag = false;
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                int32_t j = A.ci[k];
+                if (j < 0 || j >= n) {
+                    errs[t] = {i, "column index out of range in row " + std::to_string(i)};
+                    return;
+                }
+                if (k > A.rp[i] && A.ci[k - 1] >= j) {
+                    errs[t] = {i, "columns not sorted/unique in row " + std::to_string(i)};
+                    return;
+                }
+                if (j == i) {
+                    has_diag = true;
+                    if (!(A.va[k] > 0.0)) {
+                        errs[t] = {i, "non-positive diagonal in row " + std::to_string(i)};
+                        return;
+                    }
+                }
             }
-            if (j == i) {
-                has_diag = true;
-                if (!(A.va[k] > 0.0)) { err = "non-positive diagonal in row " + std::to_string(i); return false; }
+            if (!has_diag) {
+                errs[t] = {i, "missing diagonal in row " + std::to_string(i)};
+                return;
             }
         }
-        if (!has_diag) { err = "missing diagonal in row " + std::to_string(i); return false; }
-    }
+    });
+    if (first_error(errs, err)) return false;
     // symmetric pattern: every (i,j) has a stored (j,i)
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-            int32_t j = A.ci[k];
-            const int32_t* b = A.ci.data() + A.rp[j];
-            const int32_t* e = A.ci.data() + A.rp[j + 1];
-            if (!std::binary_search(b, e, i)) {
-                err = "pattern not symmetric at (" + std::to_string(i) + "," + std::to_string(j) + ")";
-                return false;
+    for_row_chunks(n, [&](int32_t lo, int32_t hi, int t) {
+        for (int32_t i = lo; i < hi; ++i)
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                int32_t j = A.ci[k];
+                const int32_t* b = A.ci.data() + A.rp[j];
+                const int32_t* e = A.ci.data() + A.rp[j + 1];
+                if (!std::binary_search(b, e, i)) {
+                    errs[t] = {i, "pattern not symmetric at (" + std::to_string(i) + "," + std::to_string(j) +
+                                      ")"};
+                    return;
+                }
             }
-        }
-    return true;
+    });
+    return !first_error(errs, err);
 }
 
 bool check_values_symmetric(const HostCsr& A, std::string& err) {
@@ -132,38 +190,46 @@ void compute_strength(const HostCsr& A, const amg_params& p, Strength& S) {
     S.isolated.assign(n, 0);
     S.dirichlet.assign(n, 0);
     S.deg.assign(n, 0);
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
-            if (A.ci[k] == i) S.diag[i] = A.va[k];
-            else ++S.deg[i];
+    // three per-row passes (each reads the previous pass's results of other
+    // rows), on host threads for large matrices
+    for_row_chunks(n, [&](int32_t lo, int32_t hi, int) {
+        for (int32_t i = lo; i < hi; ++i)
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k)
+                if (A.ci[k] == i) S.diag[i] = A.va[k];
+                else ++S.deg[i];
+    });
     std::vector<double> s(nnz, 0.0);
-    for (int32_t i = 0; i < n; ++i) {
-        double m = 0.0;
-        bool nonzero = false;
-        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-            int32_t j = A.ci[k];
-            if (j == i) continue;
-            if (A.va[k] != 0.0) nonzero = true;
-            const int32_t* b = A.ci.data() + A.rp[j];
-            const int32_t* e = A.ci.data() + A.rp[j + 1];
-            const int32_t* f = std::lower_bound(b, e, i);
-            int32_t t = (f != e && *f == i) ? (int32_t)(f - A.ci.data()) : -1;
-            S.tpos[k] = t;
-            double wji = t >= 0 ? edge_w(A.va[t]) : 0.0;
-            double c = (edge_w(A.va[k]) * wji) / (S.diag[i] * S.diag[j]);
-            s[k] = c;
-            m = std::max(m, c);
+    for_row_chunks(n, [&](int32_t lo, int32_t hi, int) {
+        for (int32_t i = lo; i < hi; ++i) {
+            double m = 0.0;
+            bool nonzero = false;
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                int32_t j = A.ci[k];
+                if (j == i) continue;
+                if (A.va[k] != 0.0) nonzero = true;
+                const int32_t* b = A.ci.data() + A.rp[j];
+                const int32_t* e = A.ci.data() + A.rp[j + 1];
+                const int32_t* f = std::lower_bound(b, e, i);
+                int32_t t = (f != e && *f == i) ? (int32_t)(f - A.ci.data()) : -1;
+                S.tpos[k] = t;
+                double wji = t >= 0 ? edge_w(A.va[t]) : 0.0;
+                double c = (edge_w(A.va[k]) * wji) / (S.diag[i] * S.diag[j]);
+                s[k] = c;
+                m = std::max(m, c);
+            }
+            S.eta[i] = m;
+            S.isolated[i] = m < p.beta;
+            S.dirichlet[i] = !nonzero;
         }
-        S.eta[i] = m;
-        S.isolated[i] = m < p.beta;
-        S.dirichlet[i] = !nonzero;
-    }
-    for (int32_t i = 0; i < n; ++i)
-        for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
-            int32_t j = A.ci[k];
-            if (j == i) continue;
-            S.strong[k] = (s[k] > 0.0 && s[k] > p.delta * std::min(S.eta[i], S.eta[j])) ? 1 : 0;
-        }
+    });
+    for_row_chunks(n, [&](int32_t lo, int32_t hi, int) {
+        for (int32_t i = lo; i < hi; ++i)
+            for (int32_t k = A.rp[i]; k < A.rp[i + 1]; ++k) {
+                int32_t j = A.ci[k];
+                if (j == i) continue;
+                S.strong[k] = (s[k] > 0.0 && s[k] > p.delta * std::min(S.eta[i], S.eta[j])) ? 1 : 0;
+            }
+    });
 }
 
 class Aggregation {
