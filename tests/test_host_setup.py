@@ -302,3 +302,40 @@ def test_library_aggregation_of_a_long_ladder_has_the_closed_form(m):
     agg, nc = amg.amg_aggregate(rp, ci, va, amg.amg_params_default(2))
     expect = ladder_closed_form(m)
     assert nc == expect.max() + 1 and np.array_equal(agg, expect)
+
+
+def test_large_matrix_validation_reports_the_lowest_failing_row():
+    # Matrices of 2^20 rows or more are validated on several host threads; the
+    # message still names the lowest failing row, whichever chunk holds it.
+    n = (1 << 20) + 12345
+    i = np.arange(n)
+    rows = np.concatenate([i, i[1:], i[:-1]])
+    cols = np.concatenate([i, i[:-1], i[1:]])
+    vals = np.concatenate([np.full(n, 2.0), np.full(n - 1, -1.0), np.full(n - 1, -1.0)])
+    order = np.lexsort((cols, rows))
+    rp = np.zeros(n + 1, dtype=np.int32)
+    np.add.at(rp, rows + 1, 1)
+    rp = np.cumsum(rp).astype(np.int32)
+    ci, va = cols[order].astype(np.int32), vals[order].copy()
+    prm = amg.amg_params_default(1)
+
+    def diag_pos(r):
+        return [k for k in range(rp[r], rp[r + 1]) if ci[k] == r][0]
+
+    # errors of the first pass in several chunks: the lowest row wins
+    va2 = va.copy()
+    for r in (n - 7, 700_001, 300_017):
+        va2[diag_pos(r)] = -1.0
+    with pytest.raises(amg.AmgError):
+        amg.amg_aggregate(rp, ci, va2, prm)
+    assert amg.amg_last_error().endswith("non-positive diagonal in row 300017")
+    # a pattern error is reported only when every row passes the first pass
+    ci3 = ci.copy()
+    k = [k for k in range(rp[900_000], rp[900_001]) if ci3[k] == 900_001][0]
+    ci3[k] = 900_002   # (900000, 900002) without (900002, 900000)
+    with pytest.raises(amg.AmgError):
+        amg.amg_aggregate(rp, ci3, va, prm)
+    assert "pattern not symmetric at (900000,900002)" in amg.amg_last_error()
+    # and the well-formed matrix aggregates: a chain in blocks of s_min = 2
+    agg, nc = amg.amg_aggregate(rp, ci, va, prm)
+    assert nc > 0 and agg.min() >= 0
