@@ -275,17 +275,27 @@ private:
 
     int32_t next_id_ = 0;
 
+    // v leaves U: its neighbours in U lose one N_na.  Their bucket entries
+    // are refreshed once per aggregate (requeue_neighbours): every such
+    // neighbour is in N(a), and the global minimum is only asked for between
+    // aggregates.
     void remove_from_U(int32_t v) {
         inU_[v] = 0;
         --remaining_;
         for (int32_t k = A_.rp[v]; k < A_.rp[v + 1]; ++k) {
             int32_t j = A_.ci[k];
             if (j == v || !inU_[j]) continue;
-            int32_t c = --nna_[j];
-            buckets_[c].push(j);
-            if (c < min_bucket_) min_bucket_ = c;
+            --nna_[j];
             const int32_t t = S_.tpos[k];
             if (t >= 0 && S_.strong[t]) --su_[j];
+        }
+    }
+    void requeue_neighbours() {
+        for (int32_t y : na_) {
+            if (!inU_[y]) continue;
+            const int32_t c = nna_[y];
+            buckets_[c].push(y);
+            if (c < min_bucket_) min_bucket_ = c;
         }
     }
 
@@ -568,6 +578,7 @@ AggResult Aggregation::run() {
                 ++next_id_;
             }
             if (remaining_ == 0) break;
+            requeue_neighbours();
             int32_t seed = -1;
             for (int32_t y : na_)
                 if (inU_[y] && (seed < 0 || nna_[y] < nna_[seed] || (nna_[y] == nna_[seed] && y < seed)))
