@@ -314,7 +314,7 @@ int amg_selftest_bounded_wait(int64_t polls, void *cuda_stream, int32_t *status,
  * the library keeps until exit, which limits n to 16,777,216 rows (larger n:
  * AMG_EINVAL).  The first call on each device looks up that array's address
  * and caches it for the life of the process (a device reset invalidates the
- * cache); make that first call before any stream capture.  All calls share
+ * cache).  All calls share
  * the array and it keeps the last call's contents (each call clears its
  * counter first): calls that overlap on the GPU race and must be serialised
  * by the caller.  Every pointer is checked with cudaPointerGetAttributes: host

@@ -21,8 +21,7 @@
 //
 // Set-up: the first call on each device looks up the array's device address
 // with cudaGetSymbolAddress while that device is current, and caches it for
-// the life of the process (a device reset invalidates it).  That first call
-// should come before any stream capture.
+// the life of the process (a device reset invalidates it).
 //
 // Every pointer argument is checked with cudaPointerGetAttributes (a query,
 // not an allocation): it must be device or managed memory of the current
